@@ -1,0 +1,148 @@
+"""Geometric multigrid used as the inner solves of the block preconditioners
+(oracle; TEST INFRASTRUCTURE).
+
+The paper approximates the inverses of its diagonal blocks with algebraic
+multigrid from PyAMG (Sec. 4, Sec. 5).  On the structured meshes used here the
+hierarchy is geometric: meshes n, n/2, ... while the size is even and at least
+4; coarse operators are rediscretised with coefficients injected to the coarse
+nodes; prolongation is nodal interpolation (linear for P1, quadratic for P2,
+exact for the nested spaces) and restriction its transpose.  One V-cycle:
+Chebyshev-Jacobi pre-smoothing of degree 2 from x = 0, coarse correction,
+degree-2 post-smoothing; dense LU with partial pivoting on the coarsest mesh.
+Smoother interval [hi / 4, hi] with hi the Gershgorin bound
+max_i sum_j |a_ij| / |a_ii| of D^{-1} A.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from .krylov import chebyshev
+from .mesh import Mesh
+from . import fem
+
+SMOOTH_DEGREE = 2
+LO_RATIO = 4.0
+
+
+def level_sizes(n: int):
+    sizes = [n]
+    while sizes[-1] % 2 == 0 and sizes[-1] >= 4:
+        sizes.append(sizes[-1] // 2)
+    return sizes
+
+
+def _bary(xi, eta):
+    """Containing triangle (0 lower / 1 upper) and barycentric coordinates of
+    a point with cell-local coordinates (xi, eta) in [0,1]^2."""
+    lower = xi >= eta
+    lam = np.where(lower[:, None],
+                   np.stack([1 - xi, xi - eta, eta], axis=1),
+                   np.stack([1 - eta, xi, eta - xi], axis=1))
+    return lower, lam
+
+
+def _locate(nc, X, Y):
+    """X, Y in units of coarse cells; returns cell (i, j), local (xi, eta)."""
+    i = np.minimum(np.floor(X).astype(np.int64), nc - 1)
+    j = np.minimum(np.floor(Y).astype(np.int64), nc - 1)
+    return i, j, X - i, Y - j
+
+
+def prolongation_p1(coarse: Mesh):
+    """Interpolate coarse P1 functions at the fine (2nc) P1 nodes."""
+    nc = coarse.n
+    nf = 2 * nc
+    I, J = np.meshgrid(np.arange(nf + 1), np.arange(nf + 1), indexing="xy")
+    X, Y = I.ravel() / 2.0, J.ravel() / 2.0
+    i, j, xi, eta = _locate(nc, X, Y)
+    lower, lam = _bary(xi, eta)
+    e = 2 * (j * nc + i) + (~lower).astype(np.int64)
+    cols = coarse.tri[e]                                       # (Nf,3)
+    rows = np.repeat(np.arange(X.size), 3)
+    P = sp.coo_matrix((lam.ravel(), (rows, cols.ravel())), shape=(X.size, coarse.N1)).tocsr()
+    P.eliminate_zeros()
+    return P
+
+
+def prolongation_p2(coarse: Mesh):
+    """Interpolate coarse P2 functions at the fine P2 nodes."""
+    nc = coarse.n
+    m = 4 * nc + 1                                             # fine refined lattice
+    I, J = np.meshgrid(np.arange(m), np.arange(m), indexing="xy")
+    X, Y = I.ravel() / 4.0, J.ravel() / 4.0
+    i, j, xi, eta = _locate(nc, X, Y)
+    lower, lam = _bary(xi, eta)
+    e = 2 * (j * nc + i) + (~lower).astype(np.int64)
+    w = fem.p2_values(lam)                                    # (Nf,6)
+    cols = coarse.tri2[e]
+    rows = np.repeat(np.arange(X.size), 6)
+    P = sp.coo_matrix((w.ravel(), (rows, cols.ravel())), shape=(X.size, coarse.N2)).tocsr()
+    P.sum_duplicates()
+    P.eliminate_zeros()
+    return P
+
+
+def prolongation_velocity(coarse: Mesh, fine: Mesh):
+    """Quadratic interpolation per component, restricted to interior
+    (non-Dirichlet) nodes on both meshes."""
+    P = prolongation_p2(coarse)
+    Df = sp.diags((~fine.p2_boundary()).astype(float))
+    Dc = sp.diags((~coarse.p2_boundary()).astype(float))
+    P = (Df @ P @ Dc).tocsr()
+    P.eliminate_zeros()
+    return sp.kron(P, sp.eye(2), format="csr")
+
+
+def inject_p1(f, nf):
+    """Values of a fine P1 field at the coarse (nf/2) vertices."""
+    F = f.reshape(nf + 1, nf + 1)
+    return np.ascontiguousarray(F[::2, ::2]).ravel()
+
+
+def inject_velocity(v, nf):
+    """Values of a fine P2 velocity at the coarse P2 nodes (fine lattice
+    points (2a, 2b) of the refined lattice)."""
+    m = 2 * nf + 1
+    V = v.reshape(m, m, 2)
+    return np.ascontiguousarray(V[::2, ::2, :]).ravel()
+
+
+class MG:
+    """One V-cycle of geometric multigrid for a hierarchy of matrices."""
+
+    def __init__(self, mats, prolongs, singular=False):
+        self.mats = mats
+        self.P = prolongs                     # P[l]: level l+1 -> level l
+        self.singular = singular
+        self.dinv, self.hi = [], []
+        for A in mats[:-1]:
+            d = A.diagonal()
+            self.dinv.append(1.0 / d)
+            absA = abs(A)
+            self.hi.append(float(np.max(np.asarray(absA.sum(axis=1)).ravel() / np.abs(d))))
+        Ac = mats[-1].toarray()
+        if singular:
+            Ac = Ac + np.ones_like(Ac)
+        self.lu = sla.lu_factor(Ac)
+
+    def vcycle(self, b, level=0):
+        if level == len(self.mats) - 1:
+            return sla.lu_solve(self.lu, b)
+        A = self.mats[level]
+        dinv, hi = self.dinv[level], self.hi[level]
+        lo = hi / LO_RATIO
+        x = chebyshev(lambda y: A @ y, dinv, b, None, lo, hi, SMOOTH_DEGREE)
+        r = b - A @ x
+        P = self.P[level]
+        ec = self.vcycle(P.T @ r, level + 1)
+        x = x + P @ ec
+        return chebyshev(lambda y: A @ y, dinv, b, x, lo, hi, SMOOTH_DEGREE)
+
+    def __call__(self, b):
+        if self.singular:
+            b = b - b.mean()
+            x = self.vcycle(b)
+            return x - x.mean()
+        return self.vcycle(b)

@@ -1,0 +1,121 @@
+"""Seeded synthetic inputs and named parameter sets.
+
+This module holds no arithmetic of the method: it only draws the initial
+fields (counter-based SplitMix64 noise) and spells out the parameter sets of
+the thin-film workloads. Both the CUDA path's tests/bench and the CPU oracle
+take their inputs from here.
+
+Initial data (paper Sec. 5, Fig. "Initial condition in 2D"): polymer and NFA
+volume fractions a +- 0.01 uniform noise, solvent b, vapour order parameter 0,
+velocity 0.  The configurations used here fill the whole unit square with
+liquid (a = 0.3, b = 0.4), the chemical potentials start at 0 and the
+pressure at 0.
+
+Noise generator: SplitMix64 (Steele, Lea, Flood 2014) started from state 0,
+output number key = seed * 2^40 + field * 2^32 + node, mapped to [0, 1) by
+its top 53 bits, then to [-amp, amp).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(keys: np.ndarray) -> np.ndarray:
+    """Output number ``key`` (0-based) of SplitMix64 started from state 0:
+    mix((key + 1) * 0x9E3779B97F4A7C15 mod 2^64)."""
+    with np.errstate(over="ignore"):
+        z = (keys.astype(np.uint64) + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform_noise(seed: int, field: int, count: int, amp: float = 0.01) -> np.ndarray:
+    """``count`` values in [-amp, amp) keyed by (seed, field, node index)."""
+    node = np.arange(count, dtype=np.uint64)
+    key = (np.uint64(seed) << np.uint64(40)) + (np.uint64(field) << np.uint64(32)) + node
+    u = (splitmix64(key) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    return (2.0 * u - 1.0) * amp
+
+
+FIELD_POLYMER = 0
+FIELD_NFA = 1
+
+
+def p1_count(n: int) -> int:
+    return (n + 1) * (n + 1)
+
+
+def p2_count(n: int) -> int:
+    return (2 * n + 1) * (2 * n + 1)
+
+
+def initial_state(n: int, seed: int = 0, a: float = 0.3, b: float = 0.4, amp: float = 0.01) -> dict:
+    """Initial state on an n x n structured mesh, as float64 numpy arrays.
+
+    Keys: phi (3, N1) for polymer, NFA, solvent; mu (4, N1) for polymer, NFA,
+    solvent, air; Phi_v (N1,); v (2*N2,) interleaved (x, y) per P2 node;
+    p (N1,).
+    """
+    n1, n2 = p1_count(n), p2_count(n)
+    phi = np.empty((3, n1))
+    phi[0] = a + uniform_noise(seed, FIELD_POLYMER, n1, amp)
+    phi[1] = a + uniform_noise(seed, FIELD_NFA, n1, amp)
+    phi[2] = b
+    return {
+        "phi": phi,
+        "mu": np.zeros((4, n1)),
+        "Phi_v": np.zeros(n1),
+        "v": np.zeros(2 * n2),
+        "p": np.zeros(n1),
+    }
+
+
+def default_params() -> dict:
+    """Parameter set of the 32 x 32 FP64 parity workload.
+
+    eps = 0.02 gives beta_i = eps^2 for all four species; dt = 1e-3; constant
+    mobility 1; viscosity 1; evaporation rate 0.1; alpha_i = 1e-8 and
+    beta_v = gamma_v = delta_v = 1 as in the caption of the paper's 2D
+    all-species runs; Krylov tolerance 1e-8 relative.
+    """
+    eps = 0.02
+    return {
+        "tau": 1e-3,
+        "beta": [eps * eps] * 4,
+        "gamma": [1.0, 1.0, 1.0],
+        "mobility_kind": 0,
+        "mobility_m0": 1e-3,
+        "eta": 1.0,
+        "alpha": [1e-8] * 4,
+        "beta_v": 1.0,
+        "gamma_v": 1.0,
+        "delta_v": 1.0,
+        "evap_rate": 0.1,
+        "phi_s_inf": 0.0,
+        "ac_top_flux": 1,
+        "precision": 0,
+        "rtol": 1e-8,
+        "atol": 0.0,
+        "restart": 30,
+        "maxit": 600,
+    }
+
+
+def workload(name: str) -> dict:
+    """Named workloads: mesh size n, parameters, number of steps."""
+    p = default_params()
+    if name == "film32_fp64":
+        return {"n": 32, "params": p, "steps": 1}
+    if name == "film256_mobility":
+        eps = 0.01
+        p.update(beta=[eps * eps] * 4, mobility_kind=1)
+        return {"n": 256, "params": p, "steps": 20}
+    if name == "film1024_mixed":
+        eps = 0.005
+        p.update(beta=[eps * eps] * 4, tau=5e-4, precision=1)
+        return {"n": 1024, "params": p, "steps": 10}
+    raise KeyError(name)
