@@ -1,0 +1,163 @@
+/*
+ * chnss.h -- C ABI of the GB300 library for one semi-implicit step of the
+ * Cahn-Hilliard / Allen-Cahn / Navier-Stokes thin-film model of
+ * arXiv 2501.11767 (Ciloglu, Tretmans, Herzog, Pietschmann, Stoll).
+ *
+ * Discretisation (paper Sec. 3): uniform triangulation of [0,lx] x [0,ly]
+ * with n x n squares, each split along its lower-left -> upper-right
+ * diagonal; P1 elements for the volume fractions phi_i, the chemical
+ * potentials mu_i, the vapour order parameter Phi_v and the pressure p;
+ * Taylor-Hood P2 elements for the velocity v, which is zero on the whole
+ * boundary (eqn:bc).  Semi-implicit Euler in time: every coefficient of the
+ * linear systems is taken at t_k.
+ *
+ * Numbering shared by every array that crosses this ABI:
+ *   P1 node (i, j), 0 <= i, j <= n, has index j*(n+1) + i   (N1 = (n+1)^2)
+ *   P2 node (I, J) of the once-refined lattice, 0 <= I, J <= 2n, has index
+ *   J*(2n+1) + I (N2 = (2n+1)^2); the vertex (i, j) is lattice point (2i, 2j).
+ *   Velocity arrays hold 2*N2 doubles, interleaved (x, y) per P2 node.
+ *
+ * Memory and streams: every double* in chnss_state and every x/rhs pointer is
+ * a DEVICE pointer owned by the caller (contiguous FP64), unless the function
+ * says "host".  The library owns its workspace (matrices, multigrid
+ * hierarchies, Krylov bases), allocated in chnss_ctx_create and released in
+ * chnss_ctx_destroy.  All work is queued on the context's CUDA stream; the
+ * Krylov drivers read one convergence scalar per iteration back to the host
+ * and therefore synchronise that stream.  No call aborts and no C++
+ * exception crosses the ABI: failures return a status and leave a message
+ * for chnss_last_error.
+ */
+#ifndef CHNSS_H
+#define CHNSS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CHNSS_OK = 0,
+  CHNSS_ERR_ARG = 1,         /* invalid argument (size, null pointer, unsupported flag) */
+  CHNSS_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  CHNSS_ERR_OOM = 3,         /* device allocation failed */
+  CHNSS_ERR_NOCONV = 4,      /* a Krylov solve hit maxit; x holds the last iterate */
+  CHNSS_ERR_BREAKDOWN = 5,   /* Arnoldi breakdown without convergence */
+  CHNSS_ERR_NAN = 6,         /* NaN or Inf in a residual norm */
+  CHNSS_ERR_TIMEOUT = 7,     /* reserved: a bounded device-side wait gave up */
+  CHNSS_ERR_STATE = 8        /* call out of order (e.g. solve before assemble) */
+} chnss_status;
+
+typedef struct chnss_mesh *chnss_mesh_t;   /* opaque: level hierarchy, patterns, maps */
+typedef struct chnss_ctx *chnss_ctx_t;     /* opaque: parameters, operators, workspace */
+
+/* Linear systems of one step (Sec. 4). */
+typedef enum {
+  CHNSS_SYS_CH_P = 0,   /* eqn:CH_linear for the polymer: unknowns [phi (N1); mu (N1)] */
+  CHNSS_SYS_CH_N = 1,   /* eqn:CH_linear for the NFA */
+  CHNSS_SYS_CH_S = 2,   /* eqn:CH_linear for the solvent */
+  CHNSS_SYS_AC = 3,     /* Allen-Cahn (M + tau delta_v K + tau C) Phi = rhs: unknowns Phi (N1) */
+  CHNSS_SYS_MU_A = 4,   /* air potential M mu_a = f_a + beta_a K phi_a^{k+1} (Sec. 5): mu_a (N1) */
+  CHNSS_SYS_NS = 5      /* eqn:linearnav: unknowns [v (2*N2); p (N1)] */
+} chnss_system;
+
+/* Model and solver parameters (nondimensional form eqn:model, Sec. 5). */
+typedef struct {
+  double tau;            /* time step */
+  double beta[4];        /* gradient-energy coefficients beta_i, i = p, NFA, s, a */
+  double gamma[3];       /* mobilities gamma_i (p, NFA, s); scale of the variable law */
+  int mobility_kind;     /* 0: constant gamma_i; 1: gamma_i (phi_i (1 - phi_i) + m0) at t_k */
+  double mobility_m0;    /* m0 of the variable mobility law */
+  double eta;            /* viscosity */
+  double alpha[4];       /* alpha_i of the convective velocity rho v - sum alpha_i grad mu_i */
+  double beta_v, gamma_v, delta_v;  /* vapour gradient energy, rate and diffusion (eqn:model) */
+  double evap_rate;      /* lumped Hertz-Knudsen factor: j_out = evap_rate (phi_s^vap - phi_s_inf) */
+  double phi_s_inf;      /* solvent fraction of the ambient air */
+  int ac_top_flux;       /* 1: also impose delta_v dPhi_v/dn = delta_v j_out on the top boundary */
+  int precision;         /* 0: FP64 throughout; 1: FP32 preconditioners inside FP64 FGMRES */
+  double rtol, atol;     /* stopping rule ||b - A x|| <= max(rtol ||b||, atol) (Sec. 5) */
+  int restart, maxit;    /* FGMRES restart length (<= 64) and total iteration cap */
+} chnss_params;
+
+/* Fields of one time level (DEVICE pointers, caller-owned, FP64). */
+typedef struct {
+  double *phi[3];        /* phi_p, phi_NFA, phi_s           [N1] each */
+  double *mu[4];         /* mu_p, mu_NFA, mu_s, mu_a        [N1] each */
+  double *Phi_v;         /* vapour order parameter          [N1] */
+  double *v;             /* velocity, interleaved (x, y)    [2*N2] */
+  double *p;             /* pressure (zero mean)            [N1] */
+} chnss_state;
+
+typedef struct {
+  int iters;             /* Krylov iterations (Arnoldi steps / CG steps) */
+  int converged;         /* 1 if the stopping rule was met */
+  double rel_residual;   /* final true ||b - A x|| / ||b|| (0 if b = 0) */
+  double seconds;        /* host wall time of the solve */
+} chnss_solve_info;
+
+/* Mesh hierarchy for n x n squares on [0,lx] x [0,ly]: n even and >= 2,
+ * nx == ny required.  Multigrid levels n, n/2, ... while the size is even and
+ * at least 4.  Builds the CSR patterns, the element -> CSR gather maps and
+ * the transfer operators (host), and uploads them.  Returns CHNSS_ERR_ARG
+ * for bad sizes, CHNSS_ERR_OOM / CHNSS_ERR_CUDA on device failures. */
+chnss_status chnss_mesh_create(int nx, int ny, double lx, double ly, chnss_mesh_t *out);
+chnss_status chnss_mesh_destroy(chnss_mesh_t mesh);
+/* Sizes: N1 P1 nodes, N2 P2 nodes, E triangles, number of multigrid levels. */
+chnss_status chnss_mesh_sizes(chnss_mesh_t mesh, int *N1, int *N2, int *E, int *levels);
+
+/* Context on `mesh` (which must outlive it) with a copy of *params; all work
+ * goes to `cuda_stream` (a cudaStream_t, or NULL for the legacy stream).
+ * Assembles the state-independent matrices (Sec. 4: M, K, K_sym, B, M_p,
+ * K_p) on the device. */
+chnss_status chnss_ctx_create(chnss_mesh_t mesh, const chnss_params *params, void *cuda_stream,
+                              chnss_ctx_t *out);
+chnss_status chnss_ctx_destroy(chnss_ctx_t ctx);
+
+/* Per-step assembly from the fields at t_k (Sec. 3-4): C(v^k), J(w^k) with
+ * w = v - sum alpha_i grad mu_i, A_p, the multigrid coarse operators by
+ * rediscretisation with injected coefficients, the potential loads of
+ * eqn:appPotential, the Korteweg term G^k and all right-hand sides. */
+chnss_status chnss_assemble(chnss_ctx_t ctx, const chnss_state *state_k);
+
+/* Unknown count of a system (2*N1, N1 or 2*N2 + N1). */
+int chnss_system_size(chnss_ctx_t ctx, chnss_system sys);
+
+/* Preconditioned FGMRES (CH, AC, NS) or Jacobi-PCG (MU_A) on an assembled
+ * system.  rhs_or_null: device right-hand side of chnss_system_size doubles,
+ * or NULL for the assembled one (for MU_A: built from the last three CH
+ * solutions).  x_out: device array of the same size, overwritten (x0 = 0).
+ * Preconditioners (Sec. 4): CH diag(MG(M + tau C), X2^-1 M X1^-1) with the
+ * matching factor X = tau gamma K + sqrt(tau gamma / beta) M (eqn::schurCH);
+ * AC MG(M + tau delta_v K + tau C); NS diag(MG(A), M_p^-1 A_p K_p^-1)
+ * (pressure convection-diffusion).  For NS the pressure is returned with
+ * zero mean.  Returns CHNSS_ERR_NOCONV if maxit is reached. */
+chnss_status chnss_solve(chnss_ctx_t ctx, chnss_system sys, const double *rhs_or_null, double *x_out,
+                         chnss_solve_info *info);
+
+/* One semi-implicit step t_k -> t_{k+1}: assemble, the three CH solves, AC,
+ * the air potential, NS.  `in` and `out` must not alias.  info[6] (optional)
+ * is filled in chnss_system order. */
+chnss_status chnss_step(chnss_ctx_t ctx, const chnss_state *in, chnss_state *out, chnss_solve_info *info);
+
+/* Same step with HOST arrays (same layout as chnss_state): copies the input
+ * to library-owned device fields, steps, copies the result back and
+ * synchronises the stream. */
+chnss_status chnss_step_host(chnss_ctx_t ctx, const chnss_state *host_in, chnss_state *host_out,
+                             chnss_solve_info *info);
+
+/* Debug / test export of assembled fine-level objects to HOST memory.
+ * which: 0 L = M + tau C, 1 AC matrix, 2 velocity block A (scalar CSR of the
+ * interleaved dofs), 3 B (N1 x 2*N2), 4 A_p, 5 M, 6 K.  Call with null arrays
+ * to get *nrows and *nnz, then again with rowptr[nrows+1], col[nnz],
+ * val[nnz]. */
+chnss_status chnss_export_csr(chnss_ctx_t ctx, int which, int *nrows, int *nnz, int *rowptr, int *col,
+                              double *val);
+/* Assembled right-hand side of a system (host, chnss_system_size doubles). */
+chnss_status chnss_export_rhs(chnss_ctx_t ctx, chnss_system sys, double *host_out);
+
+/* Message of the last failure on ctx (or of the last failed create call
+ * when ctx is NULL).  Valid until the next call on the same context. */
+const char *chnss_last_error(chnss_ctx_t ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHNSS_H */

@@ -1,0 +1,265 @@
+"""Python binding of the chnss C ABI (include/chnss.h): argument marshalling
+only.  Every step of the method runs in the CUDA library; there is no CPU
+fallback: if libchnss.so is missing or fails to load, this module raises.
+
+Device arrays are torch CUDA tensors (float64, contiguous); a state is a dict
+  phi (3, N1), mu (4, N1), Phi_v (N1,), v (2*N2,), p (N1,)
+with the node numbering described in include/chnss.h.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SYS_CH_P, SYS_CH_N, SYS_CH_S, SYS_AC, SYS_MU_A, SYS_NS = range(6)
+SYSTEM_NAMES = ("ch_p", "ch_N", "ch_s", "ac", "mu_a", "ns")
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOCONV", 5: "ERR_BREAKDOWN",
+          6: "ERR_NAN", 7: "ERR_TIMEOUT", 8: "ERR_STATE"}
+MAT_L, MAT_AC, MAT_A, MAT_B, MAT_AP, MAT_M, MAT_K = range(7)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("beta", ctypes.c_double * 4), ("gamma", ctypes.c_double * 3),
+                ("mobility_kind", ctypes.c_int), ("mobility_m0", ctypes.c_double), ("eta", ctypes.c_double),
+                ("alpha", ctypes.c_double * 4), ("beta_v", ctypes.c_double), ("gamma_v", ctypes.c_double),
+                ("delta_v", ctypes.c_double), ("evap_rate", ctypes.c_double), ("phi_s_inf", ctypes.c_double),
+                ("ac_top_flux", ctypes.c_int), ("precision", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("atol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int)]
+
+
+class State(ctypes.Structure):
+    _fields_ = [("phi", ctypes.c_void_p * 3), ("mu", ctypes.c_void_p * 4), ("Phi_v", ctypes.c_void_p),
+                ("v", ctypes.c_void_p), ("p", ctypes.c_void_p)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"iters": self.iters, "converged": bool(self.converged), "rel_residual": self.rel_residual,
+                "seconds": self.seconds}
+
+
+class ChnssError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"chnss {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_LIB = None
+
+EXPORTS = {
+    "chnss_mesh_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "chnss_mesh_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "chnss_mesh_sizes": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 4),
+    "chnss_ctx_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Params), ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "chnss_ctx_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "chnss_assemble": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State)]),
+    "chnss_system_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "chnss_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.POINTER(SolveInfo)]),
+    "chnss_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.POINTER(State),
+                                  ctypes.POINTER(SolveInfo)]),
+    "chnss_step_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.POINTER(State),
+                                       ctypes.POINTER(SolveInfo)]),
+    "chnss_export_csr": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+    "chnss_export_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "chnss_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libchnss.so (building it in-tree if it is missing or stale)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise ChnssError(2, f"CUDA library not found at {path}")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def _check(status, ctx=None):
+    if status != 0:
+        msg = load().chnss_last_error(ctx)
+        raise ChnssError(status, msg.decode() if msg else "")
+
+
+def make_params(d: dict) -> Params:
+    p = Params()
+    for name, _ in Params._fields_:
+        val = d[name]
+        if isinstance(val, (list, tuple)):
+            arr = getattr(p, name)
+            for i, x in enumerate(val):
+                arr[i] = x
+        else:
+            setattr(p, name, val)
+    return p
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous() or str(t.dtype) != "torch.float64":
+            raise ValueError("chnss needs contiguous float64 tensors")
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        if t.dtype != np.float64 or not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("chnss needs C-contiguous float64 arrays")
+        return t.ctypes.data
+    raise TypeError(type(t))
+
+
+def make_state(d: dict) -> State:
+    s = State()
+    for i in range(3):
+        s.phi[i] = _ptr(d["phi"][i])
+    for i in range(4):
+        s.mu[i] = _ptr(d["mu"][i])
+    s.Phi_v = _ptr(d["Phi_v"])
+    s.v = _ptr(d["v"])
+    s.p = _ptr(d["p"])
+    return s
+
+
+class Mesh:
+    """Structured n x n triangulation of [0, lx] x [0, ly] with its multigrid
+    hierarchy (chnss_mesh_create)."""
+
+    def __init__(self, n: int, lx: float = 1.0, ly: float = 1.0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.chnss_mesh_create(n, n, lx, ly, ctypes.byref(h)))
+        self._h = h
+        self.n, self.lx, self.ly = n, lx, ly
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(lib.chnss_mesh_sizes(h, *[ctypes.byref(x) for x in v]))
+        self.N1, self.N2, self.E, self.levels = (x.value for x in v)
+
+    def close(self):
+        if self._h:
+            load().chnss_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """Parameters, operators and workspace on one CUDA stream
+    (chnss_ctx_create)."""
+
+    def __init__(self, mesh: Mesh, params: dict, stream=None):
+        import torch
+        lib = load()
+        self.mesh = mesh
+        self.params = dict(params)
+        self._p = make_params(self.params)
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = st
+        h = ctypes.c_void_p()
+        _check(lib.chnss_ctx_create(mesh._h, ctypes.byref(self._p), ctypes.c_void_p(st.cuda_stream),
+                                    ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if self._h:
+            load().chnss_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def system_size(self, sys: int) -> int:
+        return load().chnss_system_size(self._h, sys)
+
+    def new_state(self, device="cuda"):
+        import torch
+        N1, N2 = self.mesh.N1, self.mesh.N2
+        z = lambda *s: torch.zeros(*s, dtype=torch.float64, device=device)  # noqa: E731
+        return {"phi": z(3, N1), "mu": z(4, N1), "Phi_v": z(N1), "v": z(2 * N2), "p": z(N1)}
+
+    def assemble(self, state: dict):
+        s = make_state(state)
+        _check(load().chnss_assemble(self._h, ctypes.byref(s)), self._h)
+
+    def solve(self, sys: int, rhs=None, x=None, check: bool = True):
+        import torch
+        n = self.system_size(sys)
+        if x is None:
+            x = torch.empty(n, dtype=torch.float64, device="cuda")
+        info = SolveInfo()
+        st = load().chnss_solve(self._h, sys, _ptr(rhs), _ptr(x), ctypes.byref(info))
+        if check:
+            _check(st, self._h)
+        return x, info.as_dict(), st
+
+    def step(self, state_in: dict, state_out: dict = None, check: bool = True):
+        if state_out is None:
+            state_out = self.new_state()
+        a, b = make_state(state_in), make_state(state_out)
+        infos = (SolveInfo * 6)()
+        st = load().chnss_step(self._h, ctypes.byref(a), ctypes.byref(b), infos)
+        if check:
+            _check(st, self._h)
+        return state_out, {SYSTEM_NAMES[i]: infos[i].as_dict() for i in range(6)}, st
+
+    def step_host(self, host_in: dict, host_out: dict, check: bool = True):
+        a, b = make_state(host_in), make_state(host_out)
+        infos = (SolveInfo * 6)()
+        st = load().chnss_step_host(self._h, ctypes.byref(a), ctypes.byref(b), infos)
+        if check:
+            _check(st, self._h)
+        return host_out, {SYSTEM_NAMES[i]: infos[i].as_dict() for i in range(6)}, st
+
+    def export_csr(self, which: int):
+        lib = load()
+        nr, nz = ctypes.c_int(), ctypes.c_int()
+        _check(lib.chnss_export_csr(self._h, which, ctypes.byref(nr), ctypes.byref(nz), None, None, None), self._h)
+        rowptr = np.zeros(nr.value + 1, dtype=np.int32)
+        col = np.zeros(nz.value, dtype=np.int32)
+        val = np.zeros(nz.value, dtype=np.float64)
+        _check(lib.chnss_export_csr(self._h, which, ctypes.byref(nr), ctypes.byref(nz), rowptr.ctypes.data,
+                                    col.ctypes.data, val.ctypes.data), self._h)
+        return rowptr, col, val
+
+    def export_rhs(self, sys: int):
+        out = np.zeros(self.system_size(sys), dtype=np.float64)
+        _check(load().chnss_export_rhs(self._h, sys, out.ctypes.data), self._h)
+        return out
+
+
+def state_to_device(state: dict, device="cuda") -> dict:
+    import torch
+    return {k: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64, device=device).contiguous()
+            for k, v in state.items()}
+
+
+def state_to_numpy(state: dict) -> dict:
+    return {k: v.detach().cpu().numpy() for k, v in state.items()}

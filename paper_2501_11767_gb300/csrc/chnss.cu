@@ -1,0 +1,816 @@
+// Context, per-step assembly, block preconditioners, step orchestration and
+// the C ABI of include/chnss.h.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+
+#include "solver.h"
+
+using namespace chnss;
+
+struct chnss_mesh {
+  Mesh m;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+// ---------------------------------------------------------------------------
+// small kernels of the step
+constexpr int TPB = 256;
+inline int nb(long n) { return (int)((n + TPB - 1) / TPB); }
+
+__device__ __forceinline__ double top_load(int node, int n, double hx) {
+  const int i = node % (n + 1), j = node / (n + 1);
+  if (j != n) return 0.0;
+  return (i == 0 || i == n) ? 0.5 * hx : hx;
+}
+__device__ __forceinline__ double evap_flux(const double *phi_s, int ref, double evap, double inf) {
+  return evap * (phi_s[ref] - inf);
+}
+
+// out = -c (load + sgn * beta * j_out * t)   (second block of eqn:CH_linear)
+__global__ void k_ch_rhs_mu(int N1, int n, double hx, const double *load, const double *phi_s, int ref, double evap,
+                            double inf, double sgn_beta, double c, double *out) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i >= N1) return;
+  const double j = evap_flux(phi_s, ref, evap, inf);
+  out[i] = -c * (load[i] + sgn_beta * j * top_load(i, n, hx));
+}
+// out = out - tau gamma_v f_v + ctop j_out t   (AC right-hand side)
+__global__ void k_ac_rhs(int N1, int n, double hx, const double *fv, double tg, double ctop, const double *phi_s,
+                         int ref, double evap, double inf, double *out) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i >= N1) return;
+  const double j = evap_flux(phi_s, ref, evap, inf);
+  out[i] = out[i] - tg * fv[i] + ctop * j * top_load(i, n, hx);
+}
+// out = 1 - phi_p - phi_N - phi_s
+__global__ void k_phi_a(int N1, const double *a, const double *b, const double *c, double *out) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i < N1) out[i] = 1.0 - a[i] - b[i] - c[i];
+}
+// x -= sum / denom
+__global__ void k_shift(int n, double *x, const double *sum, double denom) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i < n) x[i] -= *sum / denom;
+}
+// constant velocity blocks: + (M2 / tau) I on every block, identity on
+// Dirichlet diagonal blocks
+__global__ void k_aconst_finish(int N2, const int *rowptr, const double *m2, const int *diag, const int *bnd,
+                                double inv_tau, double *A) {
+  const int r = blockIdx.x * TPB + threadIdx.x;
+  if (r >= N2) return;
+  for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+    A[4L * k] += m2[k] * inv_tau;
+    A[4L * k + 3] += m2[k] * inv_tau;
+  }
+  if (bnd[r]) {
+    double *d = A + 4L * diag[r];
+    d[0] = 1.0; d[1] = 0.0; d[2] = 0.0; d[3] = 1.0;
+  }
+}
+__global__ void k_inv_diag(int n, const double *val, const int *diag, double *out) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i < n) out[i] = 1.0 / val[diag[i]];
+}
+
+Geo geo(const Level &L) { return Geo{L.n, L.hx, L.hy}; }
+
+// ---------------------------------------------------------------------------
+template <typename T>
+struct PrecSet {
+  MGHier<T> L, AC, A, Kp;
+  MGHier<T> X1[3], X2[3];
+  T *Mv = nullptr, *Apv = nullptr, *mdinv = nullptr;
+  T *mx = nullptr, *mt = nullptr, *mb = nullptr;
+};
+
+}  // namespace
+
+struct chnss_ctx {
+  chnss_mesh *mesh = nullptr;
+  chnss_params p{};
+  cudaStream_t s = nullptr;
+  Arena ar;
+  std::string err;
+  double *pinned = nullptr;
+  int nlev = 0, N1 = 0, N2 = 0, E = 0;
+  double *ebuf = nullptr, *lbuf = nullptr;
+  std::vector<double *> M1, K1, ACb, M2v, Aconst, L, AC, A;
+  std::vector<std::array<double *, 3>> X1, X2;
+  std::vector<double *> vl, mul, phil;
+  double *Apb = nullptr, *Ap = nullptr, *Bv = nullptr, *Btv = nullptr, *dinvM = nullptr;
+  double *Kk[3] = {nullptr, nullptr, nullptr};
+  double *loads = nullptr, *G = nullptr, *fa = nullptr, *tmp = nullptr, *sum = nullptr, *partial = nullptr;
+  double *rhs[6] = {};
+  double *xsol[6] = {};
+  double *massc = nullptr;
+  std::unique_ptr<PrecSet<double>> p64;
+  std::unique_ptr<PrecSet<float>> p32;
+  KrylovWork kw;
+  bool assembled = false;
+  bool ch_done[3] = {false, false, false};
+  double *hin = nullptr, *hout = nullptr;   // device staging of chnss_step_host
+  const Level &lv(int l) const { return mesh->m.lv[l]; }
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// preconditioner applications (Sec. 4)
+template <typename T>
+void ch_precond(chnss_ctx *c, PrecSet<T> &P, int sp, const double *r, double *z) {
+  cudaStream_t s = c->s;
+  const int N1 = c->N1;
+  vec_convert<double, T>(N1, r, P.L.input(), s);
+  P.L.apply(s);
+  vec_convert<T, double>(N1, P.L.output(), z, s);
+  // S~^-1 = X2^-1 M X1^-1 (matching factors of eqn::schurCH)
+  MGHier<T> &X1 = P.X1[sp];
+  MGHier<T> &X2 = c->p.mobility_kind == 0 ? P.X1[sp] : P.X2[sp];
+  vec_convert<double, T>(N1, r + N1, X1.input(), s);
+  X1.apply(s);
+  SpmvArgs none;
+  spmv_csr<T>(c->lv(0).p1, P.Mv, 1, X1.output(), X2.input(), SPMV_PLAIN, none, s);
+  X2.apply(s);
+  vec_convert<T, double>(N1, X2.output(), z + N1, s);
+}
+
+template <typename T>
+void ac_precond(chnss_ctx *c, PrecSet<T> &P, const double *r, double *z) {
+  vec_convert<double, T>(c->N1, r, P.AC.input(), c->s);
+  P.AC.apply(c->s);
+  vec_convert<T, double>(c->N1, P.AC.output(), z, c->s);
+}
+
+template <typename T>
+void ns_precond(chnss_ctx *c, PrecSet<T> &P, const double *r, double *z) {
+  cudaStream_t s = c->s;
+  const long nv = 2L * c->N2;
+  const int N1 = c->N1;
+  vec_convert<double, T>(nv, r, P.A.input(), s);
+  P.A.apply(s);
+  vec_convert<T, double>(nv, P.A.output(), z, s);
+  // pressure convection-diffusion: M_p^-1 A_p K_p^-1
+  vec_convert<double, T>(N1, r + nv, P.Kp.input(), s);
+  P.Kp.apply(s);
+  SpmvArgs none;
+  const Pattern &p1 = c->lv(0).p1;
+  spmv_csr<T>(p1, P.Apv, 1, P.Kp.output(), P.mb, SPMV_PLAIN, none, s);
+  // M_p^-1 by Chebyshev iteration of degree 5 on D^-1 M, spectrum [1/2, 2]
+  vec_scale_dinv<T>(N1, c->massc, P.mdinv, P.mb, P.mx, s);
+  SpmvArgs a;
+  a.b = P.mb;
+  a.dinv = P.mdinv;
+  T *cur = P.mx, *other = P.mt;
+  for (int k = 1; k <= 4; ++k) {
+    a.coef = c->massc + 1 + 3 * (k - 1);
+    a.w = k == 1 ? nullptr : other;
+    spmv_csr<T>(p1, P.Mv, 1, cur, other, SPMV_CHEB, a, s);
+    std::swap(cur, other);
+  }
+  vec_convert<T, double>(N1, cur, z + nv, s);
+}
+
+struct CHOp : LinearOperator {
+  chnss_ctx *c;
+  int sp;
+  CHOp(chnss_ctx *c_, int sp_) : c(c_), sp(sp_) {}
+  long size() const override { return 2L * c->N1; }
+  void apply(const double *x, double *y, cudaStream_t s) override {
+    const auto &p = c->p;
+    const double tau = p.tau, g = p.gamma[sp], b = p.beta[sp];
+    const bool var = p.mobility_kind != 0;
+    spmv_ch(c->lv(0).p1, c->L[0], c->K1[0], var ? c->Kk[sp] : nullptr, c->M1[0], var ? tau : tau * g, tau * g,
+            -tau * g / b, x, y, s);
+  }
+  void precond(const double *r, double *z, cudaStream_t) override {
+    if (c->p32) ch_precond(c, *c->p32, sp, r, z);
+    else ch_precond(c, *c->p64, sp, r, z);
+  }
+};
+
+struct ACOp : LinearOperator {
+  chnss_ctx *c;
+  explicit ACOp(chnss_ctx *c_) : c(c_) {}
+  long size() const override { return c->N1; }
+  void apply(const double *x, double *y, cudaStream_t s) override {
+    SpmvArgs none;
+    spmv_csr<double>(c->lv(0).p1, c->AC[0], 1, x, y, SPMV_PLAIN, none, s);
+  }
+  void precond(const double *r, double *z, cudaStream_t) override {
+    if (c->p32) ac_precond(c, *c->p32, r, z);
+    else ac_precond(c, *c->p64, r, z);
+  }
+};
+
+struct NSOp : LinearOperator {
+  chnss_ctx *c;
+  explicit NSOp(chnss_ctx *c_) : c(c_) {}
+  long size() const override { return 2L * c->N2 + c->N1; }
+  void apply(const double *x, double *y, cudaStream_t s) override {
+    const long nv = 2L * c->N2;
+    SpmvArgs none;
+    spmv_bsr2<double>(c->lv(0).p2, c->A[0], x, y, SPMV_PLAIN, none, s);
+    spmv_bt_add(c->mesh->m.pbt, c->Btv, x + nv, y, s);
+    spmv_b(c->mesh->m.pb, c->Bv, x, y + nv, s);
+  }
+  void precond(const double *r, double *z, cudaStream_t) override {
+    if (c->p32) ns_precond(c, *c->p32, r, z);
+    else ns_precond(c, *c->p64, r, z);
+  }
+};
+
+// ---------------------------------------------------------------------------
+template <typename T>
+void init_precset(chnss_ctx *c, PrecSet<T> &P) {
+  Arena &ar = c->ar;
+  const int nl = c->nlev;
+  std::vector<const Pattern *> p1s, p2s;
+  std::vector<const int *> d1s, d2s;
+  std::vector<const Transfer *> t1s, tvs;
+  for (int l = 0; l < nl; ++l) {
+    p1s.push_back(&c->lv(l).p1);
+    p2s.push_back(&c->lv(l).p2);
+    d1s.push_back(c->lv(l).diag1);
+    d2s.push_back(c->lv(l).diag2);
+    t1s.push_back(&c->lv(l).t1);
+    tvs.push_back(&c->lv(l).tv);
+  }
+  auto vals = [&](const std::vector<double *> &v) { return std::vector<const double *>(v.begin(), v.end()); };
+  P.L.init(ar, 0, false, p1s, d1s, vals(c->L), t1s, c->partial);
+  P.AC.init(ar, 0, false, p1s, d1s, vals(c->AC), t1s, c->partial);
+  P.A.init(ar, 1, false, p2s, d2s, vals(c->A), tvs, c->partial);
+  P.Kp.init(ar, 0, true, p1s, d1s, vals(c->K1), t1s, c->partial);
+  for (int sp = 0; sp < 3; ++sp) {
+    std::vector<const double *> x1, x2;
+    for (int l = 0; l < nl; ++l) {
+      x1.push_back(c->X1[l][sp]);
+      x2.push_back(c->X2[l][sp]);
+    }
+    P.X1[sp].init(ar, 0, false, p1s, d1s, x1, t1s, c->partial);
+    if (c->p.mobility_kind != 0) P.X2[sp].init(ar, 0, false, p1s, d1s, x2, t1s, c->partial);
+  }
+  const int N1 = c->N1, nnz1 = c->lv(0).p1.nnz;
+  if (std::is_same<T, double>::value) {
+    P.Mv = reinterpret_cast<T *>(c->M1[0]);
+    P.Apv = reinterpret_cast<T *>(c->Ap);
+    P.mdinv = reinterpret_cast<T *>(c->dinvM);
+  } else {
+    P.Mv = ar.alloc<T>(nnz1);
+    P.Apv = ar.alloc<T>(nnz1);
+    P.mdinv = ar.alloc<T>(N1);
+    vec_convert<double, T>(nnz1, c->M1[0], P.Mv, c->s);
+    vec_convert<double, T>(N1, c->dinvM, P.mdinv, c->s);
+  }
+  P.mx = ar.alloc<T>(N1);
+  P.mt = ar.alloc<T>(N1);
+  P.mb = ar.alloc<T>(N1);
+  P.Kp.setup(c->s);
+  for (int sp = 0; sp < 3; ++sp) P.X1[sp].setup(c->s);
+}
+
+template <typename T>
+void setup_step_precset(chnss_ctx *c, PrecSet<T> &P) {
+  P.L.setup(c->s);
+  P.AC.setup(c->s);
+  P.A.setup(c->s);
+  if (c->p.mobility_kind != 0)
+    for (int sp = 0; sp < 3; ++sp) P.X2[sp].setup(c->s);
+  if (!std::is_same<T, double>::value) vec_convert<double, T>(c->lv(0).p1.nnz, c->Ap, P.Apv, c->s);
+}
+
+void create_context(chnss_ctx *c) {
+  Arena &ar = c->ar;
+  const Mesh &m = c->mesh->m;
+  const auto &p = c->p;
+  cudaStream_t s = c->s;
+  c->nlev = (int)m.lv.size();
+  c->N1 = m.lv[0].N1;
+  c->N2 = m.lv[0].N2;
+  c->E = m.lv[0].E;
+  CHNSS_CK(cudaHostAlloc(&c->pinned, 16 * sizeof(double), cudaHostAllocDefault));
+  upload_reference_tensors(s);
+  c->ebuf = ar.alloc<double>(144L * c->E);
+  c->lbuf = ar.alloc<double>(15L * c->E);
+  c->partial = ar.alloc<double>(64L * 1216);
+  c->sum = ar.alloc<double>(4);
+  const int nl = c->nlev;
+  c->M1.resize(nl); c->K1.resize(nl); c->ACb.resize(nl); c->M2v.resize(nl); c->Aconst.resize(nl);
+  c->L.resize(nl); c->AC.resize(nl); c->A.resize(nl); c->X1.resize(nl); c->X2.resize(nl);
+  c->vl.assign(nl, nullptr); c->mul.assign(nl, nullptr); c->phil.assign(nl, nullptr);
+  for (int l = 0; l < nl; ++l) {
+    const Level &L = m.lv[l];
+    const Geo g = geo(L);
+    const int nnz1 = L.p1.nnz, nnz2 = L.p2.nnz;
+    c->M1[l] = ar.alloc<double>(nnz1);
+    c->K1[l] = ar.alloc<double>(nnz1);
+    c->ACb[l] = ar.alloc<double>(nnz1);
+    c->L[l] = ar.alloc<double>(nnz1);
+    c->AC[l] = ar.alloc<double>(nnz1);
+    c->M2v[l] = ar.alloc<double>(nnz2);
+    c->Aconst[l] = ar.alloc<double>(4L * nnz2);
+    c->A[l] = ar.alloc<double>(4L * nnz2);
+    launch_elem_p1_mass(g, c->ebuf, s);
+    launch_gather(L.g_p1, 1, c->ebuf, 1.0, nullptr, 0.0, c->M1[l], s);
+    launch_elem_p1_stiff(g, c->ebuf, s);
+    launch_gather(L.g_p1, 1, c->ebuf, 1.0, nullptr, 0.0, c->K1[l], s);
+    // M + tau delta_v K
+    vec_copy(nnz1, c->M1[l], c->ACb[l], s);
+    vec_axpby(nnz1, p.tau * p.delta_v, c->K1[l], 1.0, c->ACb[l], s);
+    for (int sp = 0; sp < 3; ++sp) {
+      const double a = std::sqrt(p.tau * p.gamma[sp] / p.beta[sp]);
+      double *x = ar.alloc<double>(nnz1);
+      vec_copy(nnz1, c->M1[l], x, s);
+      vec_axpby(nnz1, p.tau * p.gamma[sp], c->K1[l], a, x, s);   // tau gamma K + a M
+      c->X1[l][sp] = x;
+      c->X2[l][sp] = p.mobility_kind != 0 ? ar.alloc<double>(nnz1) : x;
+    }
+    launch_elem_p2_mass(g, c->ebuf, s);
+    launch_gather(L.g_p2v, 1, c->ebuf, 1.0, nullptr, 0.0, c->M2v[l], s);
+    launch_elem_ksym(g, p.eta, c->ebuf, s);
+    launch_gather(L.g_ks, 4, c->ebuf, 1.0, nullptr, 0.0, c->Aconst[l], s);
+    k_aconst_finish<<<nb(L.N2), TPB, 0, s>>>(L.N2, L.p2.rowptr, c->M2v[l], L.diag2, L.bnd2, 1.0 / p.tau,
+                                            c->Aconst[l]);
+    CHNSS_LAUNCH_CK();
+    if (l > 0) {
+      c->vl[l] = ar.alloc<double>(2L * L.N2);
+      c->mul[l] = ar.alloc<double>(4L * L.N1);
+      if (p.mobility_kind != 0) c->phil[l] = ar.alloc<double>(3L * L.N1);
+    }
+  }
+  const Level &F = m.lv[0];
+  const int nnz1 = F.p1.nnz;
+  c->Apb = ar.alloc<double>(nnz1);
+  c->Ap = ar.alloc<double>(nnz1);
+  vec_copy(nnz1, c->M1[0], c->Apb, s);
+  vec_axpby(nnz1, p.eta, c->K1[0], 1.0 / p.tau, c->Apb, s);    // M / tau + eta K
+  launch_elem_bdiv(geo(F), c->ebuf, s);
+  c->Bv = ar.alloc<double>(2L * m.pb.nnz);
+  c->Btv = ar.alloc<double>(2L * m.pbt.nnz);
+  launch_gather(m.g_b, 2, c->ebuf, 1.0, nullptr, 0.0, c->Bv, s);
+  launch_gather(m.g_bt, 2, c->ebuf, 1.0, nullptr, 0.0, c->Btv, s);
+  c->dinvM = ar.alloc<double>(c->N1);
+  k_inv_diag<<<nb(c->N1), TPB, 0, s>>>(c->N1, c->M1[0], F.diag1, c->dinvM);
+  CHNSS_LAUNCH_CK();
+  if (p.mobility_kind != 0)
+    for (int sp = 0; sp < 3; ++sp) c->Kk[sp] = ar.alloc<double>(nnz1);
+  c->loads = ar.alloc<double>(5L * c->N1);
+  c->G = ar.alloc<double>(2L * c->N2);
+  c->fa = ar.alloc<double>(c->N1);
+  c->tmp = ar.alloc<double>(c->N1);
+  for (int k = 0; k < 3; ++k) {
+    c->rhs[k] = ar.alloc<double>(2L * c->N1);
+    c->xsol[k] = ar.alloc<double>(2L * c->N1);
+  }
+  c->rhs[3] = ar.alloc<double>(c->N1);
+  c->xsol[3] = ar.alloc<double>(c->N1);
+  c->rhs[4] = ar.alloc<double>(c->N1);
+  c->xsol[4] = ar.alloc<double>(c->N1);
+  c->rhs[5] = ar.alloc<double>(2L * c->N2 + c->N1);
+  c->xsol[5] = ar.alloc<double>(2L * c->N2 + c->N1);
+  // M_p^-1 Chebyshev coefficients (degree 5, [1/2, 2])
+  {
+    const double lo = 0.5, hi = 2.0, theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+    std::vector<double> mc(13);
+    mc[0] = 1.0 / theta;
+    double rho = 1.0 / sigma;
+    for (int k = 1; k <= 4; ++k) {
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      const double al = rn * rho, be = 2.0 * rn / delta;
+      mc[1 + 3 * (k - 1)] = 1.0 + al;
+      mc[2 + 3 * (k - 1)] = -al;
+      mc[3 + 3 * (k - 1)] = be;
+      rho = rn;
+    }
+    c->massc = ar.upload(mc);
+  }
+  c->kw.init(ar, p.restart, 2L * c->N2 + c->N1, c->pinned + 8);
+  if (p.precision == 1) {
+    c->p32.reset(new PrecSet<float>());
+    init_precset(c, *c->p32);
+  } else {
+    c->p64.reset(new PrecSet<double>());
+    init_precset(c, *c->p64);
+  }
+  CHNSS_CK(cudaStreamSynchronize(s));
+}
+
+void assemble(chnss_ctx *c, const chnss_state *st) {
+  const Mesh &m = c->mesh->m;
+  const auto &p = c->p;
+  cudaStream_t s = c->s;
+  const int nl = c->nlev;
+  // coefficients on every level by injection
+  std::vector<const double *> v(nl);
+  std::vector<std::array<const double *, 4>> mu(nl);
+  std::vector<std::array<const double *, 3>> ph(nl);
+  v[0] = st->v;
+  for (int f = 0; f < 4; ++f) mu[0][f] = st->mu[f];
+  for (int f = 0; f < 3; ++f) ph[0][f] = st->phi[f];
+  for (int l = 1; l < nl; ++l) {
+    const Level &L = m.lv[l];
+    const int nf = m.lv[l - 1].n;
+    launch_inject_vel(nf, v[l - 1], c->vl[l], s);
+    v[l] = c->vl[l];
+    for (int f = 0; f < 4; ++f) {
+      double *dst = c->mul[l] + (long)f * L.N1;
+      launch_inject_p1(nf, mu[l - 1][f], dst, s);
+      mu[l][f] = dst;
+    }
+    if (p.mobility_kind != 0)
+      for (int f = 0; f < 3; ++f) {
+        double *dst = c->phil[l] + (long)f * L.N1;
+        launch_inject_p1(nf, ph[l - 1][f], dst, s);
+        ph[l][f] = dst;
+      }
+  }
+  for (int l = 0; l < nl; ++l) {
+    const Level &L = m.lv[l];
+    const Geo g = geo(L);
+    // C(v) on P1: L = M + tau C, AC = M + tau delta_v K + tau C
+    launch_elem_p1_conv(g, v[l], nullptr, nullptr, c->ebuf, s);
+    launch_gather(L.g_p1, 1, c->ebuf, p.tau, c->M1[l], 1.0, c->L[l], s);
+    launch_gather(L.g_p1, 1, c->ebuf, p.tau, c->ACb[l], 1.0, c->AC[l], s);
+    // J(w) on P2 velocity blocks: A = M / tau + K_sym + J
+    launch_elem_p2_conv(g, v[l], mu[l].data(), p.alpha, c->ebuf, s);
+    launch_gather_diag2(L.g_p2v, c->ebuf, 1.0, c->Aconst[l], c->A[l], s);
+    if (p.mobility_kind != 0)
+      for (int sp = 0; sp < 3; ++sp) {
+        const double a = std::sqrt(p.tau * p.gamma[sp] / p.beta[sp]);
+        launch_elem_p1_wstiff(g, ph[l][sp], p.gamma[sp], p.mobility_m0, c->ebuf, s);
+        launch_gather(L.g_p1, 1, c->ebuf, p.tau, c->M1[l], a, c->X2[l][sp], s);   // tau K_kappa + a M
+        if (l == 0) launch_gather(L.g_p1, 1, c->ebuf, 1.0, nullptr, 0.0, c->Kk[sp], s);
+      }
+  }
+  const Level &F = m.lv[0];
+  const Geo g0 = geo(F);
+  // A_p = M / tau + eta K + J_p(w)
+  launch_elem_p1_conv(g0, st->v, mu[0].data(), p.alpha, c->ebuf, s);
+  launch_gather(F.g_p1, 1, c->ebuf, 1.0, c->Apb, 1.0, c->Ap, s);
+  // potential loads (eqn:appPotential) and Korteweg term
+  launch_elem_loads(g0, st->phi[0], st->phi[1], st->phi[2], st->Phi_v, c->lbuf, s);
+  for (int f = 0; f < 5; ++f)
+    launch_gather(m.g_l1, 1, c->lbuf + (long)f * c->E * 3, 1.0, nullptr, 0.0, c->loads + (long)f * c->N1, s);
+  KortewegCoef kc;
+  for (int f = 0; f < 4; ++f) kc.beta[f] = p.beta[f];
+  kc.beta_v = p.beta_v;
+  launch_elem_korteweg(g0, st->phi[0], st->phi[1], st->phi[2], st->Phi_v, kc, c->lbuf, s);
+  launch_gather(m.g_l2, 2, c->lbuf, 1.0, nullptr, 0.0, c->G, s);
+  // right-hand sides
+  const int N1 = c->N1, n = F.n, ref = m.ref_node;
+  SpmvArgs none;
+  for (int sp = 0; sp < 3; ++sp) {
+    spmv_csr<double>(F.p1, c->M1[0], 1, st->phi[sp], c->rhs[sp], SPMV_PLAIN, none, s);
+    const double cc = p.tau * p.gamma[sp] / p.beta[sp];
+    const double sb = sp == 2 ? -p.beta[2] : 0.0;     // d phi_s / dn = j_out on Gamma_t
+    k_ch_rhs_mu<<<nb(N1), TPB, 0, s>>>(N1, n, F.hx, c->loads + (long)sp * N1, st->phi[2], ref, p.evap_rate,
+                                      p.phi_s_inf, sb, cc, c->rhs[sp] + N1);
+    CHNSS_LAUNCH_CK();
+  }
+  spmv_csr<double>(F.p1, c->M1[0], 1, st->Phi_v, c->rhs[3], SPMV_PLAIN, none, s);
+  k_ac_rhs<<<nb(N1), TPB, 0, s>>>(N1, n, F.hx, c->loads + 4L * N1, p.tau * p.gamma_v,
+                                 p.ac_top_flux ? p.tau * p.delta_v : 0.0, st->phi[2], ref, p.evap_rate,
+                                 p.phi_s_inf, c->rhs[3]);
+  CHNSS_LAUNCH_CK();
+  // f_a = load_a + beta_a j_out t  (d phi_a / dn = -j_out); stored as -(-1) f_a
+  k_ch_rhs_mu<<<nb(N1), TPB, 0, s>>>(N1, n, F.hx, c->loads + 3L * N1, st->phi[2], ref, p.evap_rate, p.phi_s_inf,
+                                    p.beta[3], -1.0, c->fa);
+  CHNSS_LAUNCH_CK();
+  const long nv = 2L * c->N2;
+  spmv_csr<double>(F.p2, c->M2v[0], 2, st->v, c->rhs[5], SPMV_PLAIN, none, s);
+  vec_axpby(nv, 1.0, c->G, 1.0 / p.tau, c->rhs[5], s);
+  vec_fill(N1, 0.0, c->rhs[5] + nv, s);
+  if (c->p32) setup_step_precset(c, *c->p32);
+  else setup_step_precset(c, *c->p64);
+  c->assembled = true;
+  for (bool &d : c->ch_done) d = false;
+}
+
+int system_size(chnss_ctx *c, int sys) {
+  switch (sys) {
+    case CHNSS_SYS_CH_P: case CHNSS_SYS_CH_N: case CHNSS_SYS_CH_S: return 2 * c->N1;
+    case CHNSS_SYS_AC: case CHNSS_SYS_MU_A: return c->N1;
+    case CHNSS_SYS_NS: return 2 * c->N2 + c->N1;
+    default: return -1;
+  }
+}
+
+chnss_status solve(chnss_ctx *c, int sys, const double *rhs_or_null, double *x, chnss_solve_info *info) {
+  if (!c->assembled) throw Error{CHNSS_ERR_STATE, "chnss_solve before chnss_assemble"};
+  const auto &p = c->p;
+  cudaStream_t s = c->s;
+  const int N1 = c->N1;
+  chnss_status st = CHNSS_OK;
+  if (sys <= CHNSS_SYS_CH_S) {
+    CHOp op(c, sys);
+    st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[sys], x, p.rtol, p.atol, p.maxit, c->kw, info, s);
+    if (x != c->xsol[sys]) vec_copy(2L * N1, x, c->xsol[sys], s);
+    c->ch_done[sys] = true;
+  } else if (sys == CHNSS_SYS_AC) {
+    ACOp op(c);
+    st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[3], x, p.rtol, p.atol, p.maxit, c->kw, info, s);
+  } else if (sys == CHNSS_SYS_MU_A) {
+    const double *b = rhs_or_null;
+    if (!b) {
+      if (!(c->ch_done[0] && c->ch_done[1] && c->ch_done[2]))
+        throw Error{CHNSS_ERR_STATE, "MU_A needs the three CH solutions of this step"};
+      const Level &F = c->lv(0);
+      k_phi_a<<<nb(N1), TPB, 0, s>>>(N1, c->xsol[0], c->xsol[1], c->xsol[2], c->tmp);
+      CHNSS_LAUNCH_CK();
+      SpmvArgs none;
+      spmv_csr<double>(F.p1, c->K1[0], 1, c->tmp, c->rhs[4], SPMV_PLAIN, none, s);
+      vec_axpby(N1, 1.0, c->fa, p.beta[3], c->rhs[4], s);    // f_a + beta_a K phi_a^{k+1}
+      b = c->rhs[4];
+    }
+    st = pcg(c->lv(0).p1, c->M1[0], c->dinvM, b, x, 1e-12, 1000, c->kw, info, s);
+  } else if (sys == CHNSS_SYS_NS) {
+    NSOp op(c);
+    st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[5], x, p.rtol, p.atol, p.maxit, c->kw, info, s);
+    // zero-mean pressure: p -= (1^T M p) / (1^T M 1)
+    const long nv = 2L * c->N2;
+    SpmvArgs none;
+    spmv_csr<double>(c->lv(0).p1, c->M1[0], 1, x + nv, c->tmp, SPMV_PLAIN, none, s);
+    vsum<double>(N1, c->tmp, c->sum, c->partial, s);
+    const Mesh &m = c->mesh->m;
+    k_shift<<<nb(N1), TPB, 0, s>>>(N1, x + nv, c->sum, m.lx * m.ly);
+    CHNSS_LAUNCH_CK();
+  } else {
+    throw Error{CHNSS_ERR_ARG, "unknown system"};
+  }
+  return st;
+}
+
+chnss_status step(chnss_ctx *c, const chnss_state *in, chnss_state *out, chnss_solve_info *info) {
+  chnss_solve_info loc[6];
+  chnss_solve_info *inf = info ? info : loc;
+  assemble(c, in);
+  cudaStream_t s = c->s;
+  const int N1 = c->N1;
+  chnss_status worst = CHNSS_OK;
+  auto keep = [&](chnss_status st) { if (worst == CHNSS_OK) worst = st; };
+  for (int sp = 0; sp < 3; ++sp) {
+    keep(solve(c, sp, nullptr, c->xsol[sp], &inf[sp]));
+    vec_copy(N1, c->xsol[sp], out->phi[sp], s);
+    vec_copy(N1, c->xsol[sp] + N1, out->mu[sp], s);
+  }
+  keep(solve(c, CHNSS_SYS_AC, nullptr, out->Phi_v, &inf[3]));
+  keep(solve(c, CHNSS_SYS_MU_A, nullptr, out->mu[3], &inf[4]));
+  keep(solve(c, CHNSS_SYS_NS, nullptr, c->xsol[5], &inf[5]));
+  const long nv = 2L * c->N2;
+  vec_copy(nv, c->xsol[5], out->v, s);
+  vec_copy(N1, c->xsol[5] + nv, out->p, s);
+  return worst;
+}
+
+void check_state(const chnss_state *st) {
+  if (!st) throw Error{CHNSS_ERR_ARG, "null state"};
+  for (int k = 0; k < 3; ++k) if (!st->phi[k]) throw Error{CHNSS_ERR_ARG, "null phi pointer"};
+  for (int k = 0; k < 4; ++k) if (!st->mu[k]) throw Error{CHNSS_ERR_ARG, "null mu pointer"};
+  if (!st->Phi_v || !st->v || !st->p) throw Error{CHNSS_ERR_ARG, "null field pointer"};
+}
+
+void check_params(const chnss_params *p) {
+  if (!p) throw Error{CHNSS_ERR_ARG, "null params"};
+  if (!(p->tau > 0)) throw Error{CHNSS_ERR_ARG, "tau must be > 0"};
+  for (int i = 0; i < 4; ++i) if (!(p->beta[i] > 0)) throw Error{CHNSS_ERR_ARG, "beta_i must be > 0"};
+  for (int i = 0; i < 3; ++i) if (!(p->gamma[i] > 0)) throw Error{CHNSS_ERR_ARG, "gamma_i must be > 0"};
+  if (!(p->eta > 0)) throw Error{CHNSS_ERR_ARG, "eta must be > 0"};
+  if (p->restart < 1 || p->restart > 64) throw Error{CHNSS_ERR_ARG, "restart must be in [1, 64]"};
+  if (p->maxit < 1) throw Error{CHNSS_ERR_ARG, "maxit must be >= 1"};
+  if (p->precision != 0 && p->precision != 1) throw Error{CHNSS_ERR_ARG, "precision must be 0 or 1"};
+  if (p->mobility_kind != 0 && p->mobility_kind != 1) throw Error{CHNSS_ERR_ARG, "mobility_kind must be 0 or 1"};
+  if (!(p->rtol >= 0) || !(p->atol >= 0)) throw Error{CHNSS_ERR_ARG, "tolerances must be >= 0"};
+}
+
+chnss_status fail(chnss_ctx *c, chnss_status st, const std::string &msg) {
+  if (c) c->err = msg;
+  else g_last_error = msg;
+  return st;
+}
+
+}  // namespace
+
+#define ABI_TRY try {
+#define ABI_CATCH(ctx)                                                      \
+  }                                                                         \
+  catch (const Error &e) { return fail(ctx, e.status, e.msg); }             \
+  catch (const std::bad_alloc &) { return fail(ctx, CHNSS_ERR_OOM, "host allocation failed"); } \
+  catch (const std::exception &e) { return fail(ctx, CHNSS_ERR_CUDA, e.what()); }
+
+extern "C" {
+
+chnss_status chnss_mesh_create(int nx, int ny, double lx, double ly, chnss_mesh_t *out) {
+  ABI_TRY
+  if (!out) throw Error{CHNSS_ERR_ARG, "null output pointer"};
+  *out = nullptr;
+  if (nx != ny) throw Error{CHNSS_ERR_ARG, "nx must equal ny"};
+  if (nx < 2 || nx % 2 != 0 || nx > 8192) throw Error{CHNSS_ERR_ARG, "n must be even and in [2, 8192]"};
+  if (!(lx > 0) || !(ly > 0)) throw Error{CHNSS_ERR_ARG, "domain lengths must be > 0"};
+  std::unique_ptr<chnss_mesh> m(new chnss_mesh());
+  build_mesh(m->m, nx, lx, ly);
+  *out = m.release();
+  return CHNSS_OK;
+  ABI_CATCH(nullptr)
+}
+
+chnss_status chnss_mesh_destroy(chnss_mesh_t mesh) {
+  ABI_TRY
+  if (mesh) {
+    destroy_mesh(mesh->m);
+    delete mesh;
+  }
+  return CHNSS_OK;
+  ABI_CATCH(nullptr)
+}
+
+chnss_status chnss_mesh_sizes(chnss_mesh_t mesh, int *N1, int *N2, int *E, int *levels) {
+  if (!mesh) return fail(nullptr, CHNSS_ERR_ARG, "null mesh");
+  const Level &L = mesh->m.lv[0];
+  if (N1) *N1 = L.N1;
+  if (N2) *N2 = L.N2;
+  if (E) *E = L.E;
+  if (levels) *levels = (int)mesh->m.lv.size();
+  return CHNSS_OK;
+}
+
+chnss_status chnss_ctx_create(chnss_mesh_t mesh, const chnss_params *params, void *cuda_stream, chnss_ctx_t *out) {
+  ABI_TRY
+  if (!out) throw Error{CHNSS_ERR_ARG, "null output pointer"};
+  *out = nullptr;
+  if (!mesh) throw Error{CHNSS_ERR_ARG, "null mesh"};
+  check_params(params);
+  std::unique_ptr<chnss_ctx> c(new chnss_ctx());
+  c->mesh = mesh;
+  c->p = *params;
+  c->s = static_cast<cudaStream_t>(cuda_stream);
+  create_context(c.get());
+  *out = c.release();
+  return CHNSS_OK;
+  ABI_CATCH(nullptr)
+}
+
+chnss_status chnss_ctx_destroy(chnss_ctx_t ctx) {
+  if (!ctx) return CHNSS_OK;
+  cudaStreamSynchronize(ctx->s);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  delete ctx;
+  return CHNSS_OK;
+}
+
+chnss_status chnss_assemble(chnss_ctx_t ctx, const chnss_state *state_k) {
+  if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
+  ABI_TRY
+  check_state(state_k);
+  assemble(ctx, state_k);
+  return CHNSS_OK;
+  ABI_CATCH(ctx)
+}
+
+int chnss_system_size(chnss_ctx_t ctx, chnss_system sys) { return ctx ? system_size(ctx, sys) : -1; }
+
+chnss_status chnss_solve(chnss_ctx_t ctx, chnss_system sys, const double *rhs_or_null, double *x_out,
+                         chnss_solve_info *info) {
+  if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
+  ABI_TRY
+  if (system_size(ctx, sys) < 0) throw Error{CHNSS_ERR_ARG, "unknown system"};
+  if (!x_out) throw Error{CHNSS_ERR_ARG, "null x_out"};
+  const chnss_status st = solve(ctx, sys, rhs_or_null, x_out, info);
+  if (st != CHNSS_OK) ctx->err = "solve did not converge cleanly (status " + std::to_string(st) + ")";
+  return st;
+  ABI_CATCH(ctx)
+}
+
+chnss_status chnss_step(chnss_ctx_t ctx, const chnss_state *in, chnss_state *out, chnss_solve_info *info) {
+  if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
+  ABI_TRY
+  check_state(in);
+  check_state(out);
+  if (in->v == out->v || in->p == out->p || in->Phi_v == out->Phi_v)
+    throw Error{CHNSS_ERR_ARG, "in and out states must not alias"};
+  const chnss_status st = step(ctx, in, out, info);
+  if (st != CHNSS_OK) ctx->err = "a solve of the step did not converge cleanly (status " + std::to_string(st) + ")";
+  return st;
+  ABI_CATCH(ctx)
+}
+
+chnss_status chnss_step_host(chnss_ctx_t ctx, const chnss_state *hin, chnss_state *hout, chnss_solve_info *info) {
+  if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
+  ABI_TRY
+  check_state(hin);
+  check_state(hout);
+  const long N1 = ctx->N1, nv = 2L * ctx->N2;
+  const long total = 9 * N1 + nv;   // phi 3, mu 4, Phi 1, p 1 (N1 each) + v
+  if (!ctx->hin) {
+    ctx->hin = ctx->ar.alloc<double>(total);
+    ctx->hout = ctx->ar.alloc<double>(total);
+  }
+  auto bind = [&](double *base, chnss_state &d) {
+    for (int k = 0; k < 3; ++k) d.phi[k] = base + k * N1;
+    for (int k = 0; k < 4; ++k) d.mu[k] = base + (3 + k) * N1;
+    d.Phi_v = base + 7 * N1;
+    d.p = base + 8 * N1;
+    d.v = base + 9 * N1;
+  };
+  chnss_state din{}, dout{};
+  bind(ctx->hin, din);
+  bind(ctx->hout, dout);
+  cudaStream_t s = ctx->s;
+  auto h2d = [&](double *d, const double *h, long n) {
+    CHNSS_CK(cudaMemcpyAsync(d, h, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  };
+  auto d2h = [&](double *h, const double *d, long n) {
+    CHNSS_CK(cudaMemcpyAsync(h, d, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  };
+  for (int k = 0; k < 3; ++k) h2d(din.phi[k], hin->phi[k], N1);
+  for (int k = 0; k < 4; ++k) h2d(din.mu[k], hin->mu[k], N1);
+  h2d(din.Phi_v, hin->Phi_v, N1);
+  h2d(din.p, hin->p, N1);
+  h2d(din.v, hin->v, nv);
+  const chnss_status st = step(ctx, &din, &dout, info);
+  for (int k = 0; k < 3; ++k) d2h(hout->phi[k], dout.phi[k], N1);
+  for (int k = 0; k < 4; ++k) d2h(hout->mu[k], dout.mu[k], N1);
+  d2h(hout->Phi_v, dout.Phi_v, N1);
+  d2h(hout->p, dout.p, N1);
+  d2h(hout->v, dout.v, nv);
+  CHNSS_CK(cudaStreamSynchronize(s));
+  return st;
+  ABI_CATCH(ctx)
+}
+
+chnss_status chnss_export_csr(chnss_ctx_t ctx, int which, int *nrows, int *nnz, int *rowptr, int *col, double *val) {
+  if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
+  ABI_TRY
+  const Mesh &m = ctx->mesh->m;
+  const Level &F = m.lv[0];
+  const Pattern *P = nullptr;
+  const double *dv = nullptr;
+  int ncomp = 1;   // 2: B (two values per entry), 4: velocity blocks
+  switch (which) {
+    case 0: P = &F.p1; dv = ctx->L[0]; break;
+    case 1: P = &F.p1; dv = ctx->AC[0]; break;
+    case 2: P = &F.p2; dv = ctx->A[0]; ncomp = 4; break;
+    case 3: P = &m.pb; dv = ctx->Bv; ncomp = 2; break;
+    case 4: P = &F.p1; dv = ctx->Ap; break;
+    case 5: P = &F.p1; dv = ctx->M1[0]; break;
+    case 6: P = &F.p1; dv = ctx->K1[0]; break;
+    default: throw Error{CHNSS_ERR_ARG, "unknown matrix id"};
+  }
+  if ((which == 0 || which == 1 || which == 2 || which == 4) && !ctx->assembled)
+    throw Error{CHNSS_ERR_STATE, "export of a per-step matrix before chnss_assemble"};
+  const int rows = ncomp == 4 ? 2 * P->nrows : P->nrows;
+  const int total = P->nnz * ncomp;
+  if (nrows) *nrows = rows;
+  if (nnz) *nnz = total;
+  if (!rowptr && !col && !val) return CHNSS_OK;
+  if (!rowptr || !col || !val) throw Error{CHNSS_ERR_ARG, "export needs all three arrays"};
+  std::vector<double> hv((size_t)total);
+  CHNSS_CK(cudaStreamSynchronize(ctx->s));
+  CHNSS_CK(cudaMemcpy(hv.data(), dv, total * sizeof(double), cudaMemcpyDeviceToHost));
+  if (ncomp == 1) {
+    std::copy(P->h_rowptr.begin(), P->h_rowptr.end(), rowptr);
+    std::copy(P->h_col.begin(), P->h_col.end(), col);
+    std::copy(hv.begin(), hv.end(), val);
+  } else if (ncomp == 2) {   // B: columns 2*node + d
+    int k = 0;
+    rowptr[0] = 0;
+    for (int r = 0; r < P->nrows; ++r) {
+      for (int q = P->h_rowptr[r]; q < P->h_rowptr[r + 1]; ++q)
+        for (int d = 0; d < 2; ++d) { col[k] = 2 * P->h_col[q] + d; val[k] = hv[2L * q + d]; ++k; }
+      rowptr[r + 1] = k;
+    }
+  } else {                   // velocity blocks -> scalar rows 2*node + c
+    int k = 0;
+    rowptr[0] = 0;
+    for (int r = 0; r < P->nrows; ++r)
+      for (int cc = 0; cc < 2; ++cc) {
+        for (int q = P->h_rowptr[r]; q < P->h_rowptr[r + 1]; ++q)
+          for (int d = 0; d < 2; ++d) { col[k] = 2 * P->h_col[q] + d; val[k] = hv[4L * q + cc * 2 + d]; ++k; }
+        rowptr[2 * r + cc + 1] = k;
+      }
+  }
+  return CHNSS_OK;
+  ABI_CATCH(ctx)
+}
+
+chnss_status chnss_export_rhs(chnss_ctx_t ctx, chnss_system sys, double *host_out) {
+  if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
+  ABI_TRY
+  const int n = system_size(ctx, sys);
+  if (n < 0 || !host_out) throw Error{CHNSS_ERR_ARG, "bad system or null output"};
+  if (!ctx->assembled) throw Error{CHNSS_ERR_STATE, "export_rhs before chnss_assemble"};
+  const double *src = sys == CHNSS_SYS_MU_A ? ctx->rhs[4] : ctx->rhs[sys <= 2 ? sys : (sys == 3 ? 3 : 5)];
+  CHNSS_CK(cudaStreamSynchronize(ctx->s));
+  CHNSS_CK(cudaMemcpy(host_out, src, n * sizeof(double), cudaMemcpyDeviceToHost));
+  return CHNSS_OK;
+  ABI_CATCH(ctx)
+}
+
+const char *chnss_last_error(chnss_ctx_t ctx) { return ctx ? ctx->err.c_str() : g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,179 @@
+// Internal declarations of the chnss CUDA library (not part of the ABI).
+//
+// Layout in HBM (all int32 indices, FP64 values unless stated):
+//   * CSR patterns per multigrid level: the P1 node pattern (7-point stencil
+//     of the structured triangulation) and the P2 node pattern, which is also
+//     the block pattern of the 2x2-block (BSR2) velocity operator.
+//   * Gather lists: for every output entry (a CSR value, a BSR2 block or a
+//     node of a load vector) the ordered list of offsets into an element
+//     buffer whose contributions it sums.  Assembly = element kernel writing
+//     dense element matrices + gather kernel; no atomics, so the sum order
+//     is fixed and results are bit-reproducible.
+//   * Vectors: P1 fields [N1]; velocity [2*N2] interleaved (x, y) per node;
+//     system vectors are concatenations ([phi; mu], [v; p]).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/chnss.h"
+
+namespace chnss {
+
+struct Error {
+  chnss_status status;
+  std::string msg;
+};
+
+#define CHNSS_CK(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      throw ::chnss::Error{CHNSS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+#define CHNSS_LAUNCH_CK() CHNSS_CK(cudaGetLastError())
+
+// Owner of device allocations; frees everything it handed out.
+struct Arena {
+  std::vector<void *> ptrs;
+  size_t bytes = 0;
+  template <class T>
+  T *alloc(size_t n) {
+    if (n == 0) n = 1;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Error{CHNSS_ERR_OOM, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed: " +
+                                     cudaGetErrorString(e)};
+    }
+    ptrs.push_back(p);
+    bytes += n * sizeof(T);
+    return static_cast<T *>(p);
+  }
+  template <class T>
+  T *upload(const std::vector<T> &h) {
+    T *d = alloc<T>(h.size());
+    if (!h.empty()) CHNSS_CK(cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return d;
+  }
+  void release() {
+    for (void *p : ptrs) cudaFree(p);
+    ptrs.clear();
+    bytes = 0;
+  }
+  ~Arena() { release(); }
+};
+
+struct Pattern {
+  int nrows = 0, ncols = 0;
+  int nnz = 0;
+  int *rowptr = nullptr, *col = nullptr;  // device
+  std::vector<int> h_rowptr, h_col;       // host copies
+};
+
+// out entry k sums buf[idx[j] + c] for j in [ptr[k], ptr[k+1]), c < ncomp.
+struct Gather {
+  int nout = 0;
+  int ncontrib = 0;
+  int *ptr = nullptr, *idx = nullptr;
+};
+
+struct Transfer {               // prolongation P (fine x coarse) and R = P^T
+  Pattern P, R;
+  double *Pv = nullptr, *Rv = nullptr;
+  float *Pv32 = nullptr, *Rv32 = nullptr;
+};
+
+struct Level {
+  int n = 0;
+  double hx = 0, hy = 0;
+  int N1 = 0, N2 = 0, E = 0;
+  Pattern p1, p2;
+  Gather g_p1;    // P1 values <- element [E][3][3]
+  Gather g_p2v;   // P2 velocity blocks <- element [E][6][6] (Dirichlet nodes masked)
+  Gather g_ks;    // P2 velocity blocks <- element [E][6][2][6][2] (4 comps), masked
+  int *bnd2 = nullptr;   // [N2] 1 on the boundary
+  int *diag1 = nullptr;  // [N1] position of the diagonal in p1
+  int *diag2 = nullptr;  // [N2] position of the diagonal block in p2
+  Transfer t1;           // P1 transfer from level+1 (empty on the coarsest)
+  Transfer tv;           // velocity (per node, masked) transfer from level+1
+};
+
+struct Mesh {
+  double lx = 1, ly = 1;
+  int n = 0;
+  std::vector<Level> lv;
+  Pattern pb, pbt;             // fine B (P1 rows x P2 node cols) and B^T
+  Gather g_b, g_bt;            // <- element [E][3][6][2] (2 comps)
+  Gather g_l1;                 // P1 nodes <- element [E][3]
+  Gather g_l2;                 // P2 nodes <- element [E][6][2] (2 comps), masked
+  int ref_node = 0;            // P1 node (n/2, n): reference point of phi_s^vap
+  Arena arena;
+};
+
+// ---------------------------------------------------------------------------
+// reference tensors (exact integrals over a triangle divided by its area)
+struct RefTensors {
+  double m1[3][3];            // lambda_a lambda_b
+  double c1[6][3];            // phi2_k lambda_a
+  double m2[6][6];            // phi2_a phi2_b
+  double j[6][3][6][6];       // phi2_k d_l phi2_b phi2_a  (k, l, b, a)
+  double jg[3][6][6];         // d_l phi2_b phi2_a         (l, b, a)
+  double s[3][6][3][6];       // d_l phi2_b d_m phi2_a     (l, b, m, a)
+  double b[3][6][3];          // lambda_a d_l phi2_b       (a, b, l)
+  double g[6][3];             // d_l phi2_a                (a, l)
+  double qlam[20][3];         // degree-7 rule: barycentric points
+  double qw[20];              // weights, sum 1
+};
+const RefTensors &reference_tensors();
+
+// ---------------------------------------------------------------------------
+// host builders (setup.cu)
+void build_mesh(Mesh &m, int n, double lx, double ly);
+void destroy_mesh(Mesh &m);
+
+// ---------------------------------------------------------------------------
+// kernels launched from the host (assemble.cu, sparse.cu)
+struct Geo {     // structured level geometry
+  int n;
+  double hx, hy;
+};
+
+void upload_reference_tensors(cudaStream_t s);
+void launch_elem_p1_mass(Geo g, double *buf, cudaStream_t s);
+void launch_elem_p1_stiff(Geo g, double *buf, cudaStream_t s);
+// C or J_p: ((v - shift) . grad psi_b) psi_a, shift = sum alpha_i grad mu_i (mu may be null)
+void launch_elem_p1_conv(Geo g, const double *v, const double *const *mu, const double *alpha,
+                         double *buf, cudaStream_t s);
+// weighted stiffness with kappa = gamma (phi (1 - phi) + m0)
+void launch_elem_p1_wstiff(Geo g, const double *phi, double gamma, double m0, double *buf, cudaStream_t s);
+void launch_elem_p2_mass(Geo g, double *buf, cudaStream_t s);
+void launch_elem_p2_conv(Geo g, const double *v, const double *const *mu, const double *alpha,
+                         double *buf, cudaStream_t s);
+void launch_elem_ksym(Geo g, double eta, double *buf, cudaStream_t s);
+void launch_elem_bdiv(Geo g, double *buf, cudaStream_t s);
+void launch_elem_loads(Geo g, const double *phi_p, const double *phi_n, const double *phi_s,
+                       const double *Phi, double *buf, cudaStream_t s);
+struct KortewegCoef {
+  double beta[4];
+  double beta_v;
+};
+void launch_elem_korteweg(Geo g, const double *phi_p, const double *phi_n, const double *phi_s,
+                          const double *Phi, KortewegCoef c, double *buf, cudaStream_t s);
+
+// out[k*nc + c] = beta * base[k*nc + c] + alpha * sum buf[idx + c]   (base may be null)
+void launch_gather(const Gather &g, int ncomp, const double *buf, double alpha, const double *base,
+                   double beta, double *out, cudaStream_t s);
+// velocity blocks: out[4k..4k+3] = base[4k..] + alpha * sum(buf) * I2
+void launch_gather_diag2(const Gather &g, const double *buf, double alpha, const double *base, double *out,
+                         cudaStream_t s);
+
+void launch_inject_p1(int nf, const double *fine, double *coarse, cudaStream_t s);
+void launch_inject_vel(int nf, const double *fine, double *coarse, cudaStream_t s);
+
+}  // namespace chnss

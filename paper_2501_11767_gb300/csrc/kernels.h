@@ -1,0 +1,99 @@
+// Launch wrappers of the sparse, vector and reduction kernels (sparse.cu).
+#pragma once
+
+#include "internal.h"
+
+namespace chnss {
+
+// Fused SpMV epilogues (rows of A u):
+//   PLAIN  out = A u
+//   RES    out = b - A u
+//   ADD    out += A u
+//   CHEB   out = c0 u + c1 w + c2 dinv (b - A u), (c0, c1, c2) = coef[0..2] (device)
+enum SpmvMode { SPMV_PLAIN = 0, SPMV_RES = 1, SPMV_ADD = 2, SPMV_CHEB = 3 };
+
+struct SpmvArgs {
+  const void *b = nullptr;      // T*
+  const void *w = nullptr;      // T*  (CHEB)
+  const void *dinv = nullptr;   // T*  (CHEB)
+  const double *coef = nullptr; // device [3] (CHEB)
+};
+
+// Scalar CSR; ncomp = 1 or 2 (the same scalar weights applied per component
+// of an interleaved 2-vector: velocity mass and velocity transfers).
+template <typename T>
+void spmv_csr(const Pattern &P, const T *val, int ncomp, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
+              cudaStream_t s);
+// 2x2-block CSR (velocity operator), vectors interleaved.
+template <typename T>
+void spmv_bsr2(const Pattern &P, const T *val, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
+               cudaStream_t s);
+
+// CH operator: y1 = L x1 + a12 K12 x2, y2 = a21 K x1 + a22 M x2 on the P1
+// pattern (K12 = K when k12 == nullptr).
+void spmv_ch(const Pattern &P, const double *L, const double *K, const double *k12, const double *M, double a12,
+             double a21, double a22, const double *x, double *y, cudaStream_t s);
+// y = B v (B: N1 x N2 nodes, 2 values per entry); y += B^T p into interleaved v.
+void spmv_b(const Pattern &P, const double *val, const double *v, double *y, cudaStream_t s);
+void spmv_bt_add(const Pattern &P, const double *val, const double *p, double *yv, cudaStream_t s);
+
+// Jacobi data + Gershgorin bound of D^-1 A: dinv[i] = 1 / a_ii,
+// hi = max_i sum_j |a_ij| / |a_ii| (device scalar).  Also the Chebyshev
+// coefficient triples for a degree-2 smoother on [hi / ratio, hi].
+template <typename T>
+void jacobi_csr(const Pattern &P, const double *val, const int *diag, T *dinv, double *hi, double *partial,
+                cudaStream_t s);
+template <typename T>
+void jacobi_bsr2(const Pattern &P, const double *val, const int *diag, T *dinv, double *hi, double *partial,
+                 cudaStream_t s);
+// coef layout: [pre1 scale][pre2 c0,c1,c2][post1 c0,c1,c2][post2 c0,c1,c2] (10 doubles)
+void cheb_coefficients(const double *hi, double ratio, double *coef, cudaStream_t s);
+
+// vectors
+template <typename T>
+void vec_scale_dinv(int n, const double *scale, const T *dinv, const T *b, T *out, cudaStream_t s);
+template <typename Ta, typename Tb>
+void vec_convert(long n, const Ta *in, Tb *out, cudaStream_t s);
+void vec_axpby(long n, double a, const double *x, double b, double *y, cudaStream_t s);      // y = a x + b y
+void vec_copy(long n, const double *x, double *y, cudaStream_t s);
+void vec_fill(long n, double v, double *y, cudaStream_t s);
+void vec_scale_by_inv(long n, const double *src, const double *hn, double *dst, cudaStream_t s);  // dst = src / *hn
+template <typename T>
+void vec_sub_mean(int n, T *x, const double *sum, cudaStream_t s);   // x -= sum / n
+
+// deterministic FP64 reductions: fixed grid of reduce_blocks(n) blocks,
+// partial sums in fixed order, then one block sums the partials.
+int reduce_blocks(long n);
+template <typename T>
+void dot(long n, const T *x, const T *y, double *out, double *partial, cudaStream_t s);
+template <typename T>
+void vsum(long n, const T *x, double *out, double *partial, cudaStream_t s);
+void mdot(long n, const double *V, long ldv, int k, const double *w, double *out, double *partial, cudaStream_t s);
+void ortho_update_mdot(long n, const double *V, long ldv, int k, const double *h, double *w, double *out,
+                       double *partial, cudaStream_t s);
+void ortho_update_norm(long n, const double *V, long ldv, int k, const double *h, double *w, double *out,
+                       double *partial, cudaStream_t s);
+void combine_columns(long n, const double *Z, long ldz, int k, const double *y, double *x, cudaStream_t s);
+
+// Arnoldi bookkeeping on one thread: H(:, j) = h1 + h2, H(j+1, j) = sqrt(nrm2),
+// previous Givens rotations, new rotation, g update.  Writes to status:
+// [0] |g_{j+1}|, [1] H(j+1, j).
+void arnoldi_finish(int j, int ldh, double *H, const double *h1, const double *h2, const double *nrm2,
+                    double *cs, double *sn, double *g, double *status, cudaStream_t s);
+void hessenberg_solve(int k, int ldh, const double *H, const double *g, double *y, cudaStream_t s);
+void set_scalar(double *dst, const double *src, double scale, bool sqrt_first, cudaStream_t s);
+// PCG scalars: alpha = rz / pq
+void pcg_alpha(const double *rz, const double *pq, double *alpha, cudaStream_t s);
+void pcg_update_xr(long n, const double *alpha, const double *p, const double *q, double *x, double *r,
+                   cudaStream_t s);
+void pcg_update_p(long n, const double *rz_new, const double *rz_old, const double *z, double *p, cudaStream_t s);
+void vec_mul(long n, const double *a, const double *b, double *out, cudaStream_t s);
+
+// dense coarse-grid inverse (one CTA, Gauss-Jordan with partial pivoting)
+void coarse_dense_csr(const Pattern &P, const double *val, double add_all, double *dense, cudaStream_t s);
+void coarse_dense_bsr2(const Pattern &P, const double *val, double *dense, cudaStream_t s);
+void dense_invert(int n, double *a, double *inv, int *status, cudaStream_t s);
+template <typename T>
+void dense_apply(int n, const double *inv, const T *b, T *x, cudaStream_t s);
+
+}  // namespace chnss

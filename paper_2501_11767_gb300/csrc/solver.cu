@@ -1,0 +1,289 @@
+// Multigrid V-cycle and Krylov drivers.
+#include <chrono>
+#include <cmath>
+#include <type_traits>
+
+#include "solver.h"
+
+namespace chnss {
+
+constexpr double kSmootherRatio = 4.0;   // smoothing interval [hi / 4, hi]
+
+template <typename T>
+void MGHier<T>::init(Arena &ar, int kind_, bool singular_, const std::vector<const Pattern *> &pats,
+                     const std::vector<const int *> &diags, const std::vector<const double *> &vals,
+                     const std::vector<const Transfer *> &trs, double *partial_buf) {
+  diag = diags;
+  kind = kind_;
+  singular = singular_;
+  nl = (int)pats.size();
+  pat = pats;
+  val64 = vals;
+  tr = trs;
+  n.resize(nl);
+  val.resize(nl);
+  dinv.resize(nl);
+  x.resize(nl);
+  t.resize(nl);
+  r.resize(nl);
+  b.resize(nl);
+  hi.resize(nl);
+  coef.resize(nl);
+  for (int l = 0; l < nl; ++l) {
+    const long nu = (kind == 0 ? 1L : 2L) * pat[l]->nrows;
+    n[l] = nu;
+    const long nv = (kind == 0 ? 1L : 4L) * pat[l]->nnz;
+    if (std::is_same<T, double>::value)
+      val[l] = reinterpret_cast<T *>(const_cast<double *>(vals[l]));
+    else
+      val[l] = ar.alloc<T>(nv);
+    dinv[l] = ar.alloc<T>(nu);
+    x[l] = ar.alloc<T>(nu);
+    t[l] = ar.alloc<T>(nu);
+    r[l] = ar.alloc<T>(nu);
+    b[l] = ar.alloc<T>(nu);
+    hi[l] = ar.alloc<double>(1);
+    coef[l] = ar.alloc<double>(10);
+  }
+  nc = (int)n[nl - 1];
+  dense = ar.alloc<double>((long)nc * nc);
+  cinv = ar.alloc<double>((long)nc * nc);
+  status = ar.alloc<int>(1);
+  partial = partial_buf;
+  sum = ar.alloc<double>(1);
+}
+
+template <typename T>
+void MGHier<T>::setup(cudaStream_t s) {
+  for (int l = 0; l < nl; ++l) {
+    const long nv = (kind == 0 ? 1L : 4L) * pat[l]->nnz;
+    if (!std::is_same<T, double>::value) vec_convert<double, T>(nv, val64[l], val[l], s);
+    if (l == nl - 1) break;
+    if (kind == 0)
+      jacobi_csr<T>(*pat[l], val64[l], diag[l], dinv[l], hi[l], partial, s);
+    else
+      jacobi_bsr2<T>(*pat[l], val64[l], diag[l], dinv[l], hi[l], partial, s);
+    cheb_coefficients(hi[l], kSmootherRatio, coef[l], s);
+  }
+  const int L = nl - 1;
+  if (kind == 0)
+    coarse_dense_csr(*pat[L], val64[L], singular ? 1.0 : 0.0, dense, s);
+  else
+    coarse_dense_bsr2(*pat[L], val64[L], dense, s);
+  dense_invert(nc, dense, cinv, status, s);
+}
+
+template <typename T>
+void MGHier<T>::op(int l, const T *u, T *out, SpmvMode mode, const SpmvArgs &a, cudaStream_t s) {
+  if (kind == 0)
+    spmv_csr<T>(*pat[l], val[l], 1, u, out, mode, a, s);
+  else
+    spmv_bsr2<T>(*pat[l], val[l], u, out, mode, a, s);
+}
+
+template <typename T>
+static inline const T *transfer_vals(const Transfer &t, bool restrict_) {
+  if (std::is_same<T, double>::value) return reinterpret_cast<const T *>(restrict_ ? t.Rv : t.Pv);
+  return reinterpret_cast<const T *>(restrict_ ? t.Rv32 : t.Pv32);
+}
+
+template <typename T>
+void MGHier<T>::vcycle(int l, cudaStream_t s) {
+  if (l == nl - 1) {
+    dense_apply<T>(nc, cinv, b[l], x[l], s);
+    return;
+  }
+  const int nc_ = kind == 0 ? 1 : 2;
+  SpmvArgs a;
+  a.b = b[l];
+  a.dinv = dinv[l];
+  // pre-smoothing from x = 0
+  vec_scale_dinv<T>((int)n[l], coef[l], dinv[l], b[l], t[l], s);
+  a.coef = coef[l] + 1;
+  op(l, t[l], x[l], SPMV_CHEB, a, s);
+  // residual, restriction, coarse correction, prolongation
+  SpmvArgs ar;
+  ar.b = b[l];
+  op(l, x[l], r[l], SPMV_RES, ar, s);
+  const Transfer &T_ = *tr[l];
+  SpmvArgs none;
+  spmv_csr<T>(T_.R, transfer_vals<T>(T_, true), nc_, r[l], b[l + 1], SPMV_PLAIN, none, s);
+  vcycle(l + 1, s);
+  spmv_csr<T>(T_.P, transfer_vals<T>(T_, false), nc_, x[l + 1], x[l], SPMV_ADD, none, s);
+  // post-smoothing
+  a.coef = coef[l] + 4;
+  a.w = nullptr;
+  op(l, x[l], t[l], SPMV_CHEB, a, s);
+  a.coef = coef[l] + 7;
+  a.w = x[l];
+  op(l, t[l], x[l], SPMV_CHEB, a, s);
+}
+
+template <typename T>
+void MGHier<T>::apply(cudaStream_t s) {
+  if (singular) {
+    vsum<T>(n[0], b[0], sum, partial, s);
+    vec_sub_mean<T>((int)n[0], b[0], sum, s);
+  }
+  vcycle(0, s);
+  if (singular) {
+    vsum<T>(n[0], x[0], sum, partial, s);
+    vec_sub_mean<T>((int)n[0], x[0], sum, s);
+  }
+}
+
+template struct MGHier<double>;
+template struct MGHier<float>;
+
+// ---------------------------------------------------------------------------
+void KrylovWork::init(Arena &ar, int m_, long nmax_, double *pinned) {
+  m = m_;
+  nmax = nmax_;
+  V = ar.alloc<double>((long)(m + 1) * nmax);
+  Z = ar.alloc<double>((long)m * nmax);
+  w = ar.alloc<double>(nmax);
+  H = ar.alloc<double>((long)(m + 1) * m);
+  cs = ar.alloc<double>(m);
+  sn = ar.alloc<double>(m);
+  g = ar.alloc<double>(m + 1);
+  y = ar.alloc<double>(m);
+  h1 = ar.alloc<double>(m + 1);
+  h2 = ar.alloc<double>(m + 1);
+  sc = ar.alloc<double>(8);
+  partial = ar.alloc<double>(64L * 1216);
+  hstat = pinned;
+}
+
+namespace {
+double read_scalar(const double *dev, double *pinned, cudaStream_t s) {
+  CHNSS_CK(cudaMemcpyAsync(pinned, dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CHNSS_CK(cudaStreamSynchronize(s));
+  return *pinned;
+}
+}  // namespace
+
+chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, double atol, int maxit,
+                    KrylovWork &ws, chnss_solve_info *info, cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const long n = A.size();
+  const int m = ws.m;
+  const int ldh = m + 1;
+  double *sc = ws.sc;   // [0] ||b||^2, [1] ||r||^2
+  vec_fill(n, 0.0, x, s);
+  dot<double>(n, b, b, sc, ws.partial, s);
+  const double bnorm = std::sqrt(read_scalar(sc, ws.hstat, s));
+  const double target = std::max(rtol * bnorm, atol);
+  double rnorm = bnorm;
+  int iters = 0;
+  chnss_status st = CHNSS_OK;
+  bool converged = false;
+  if (!std::isfinite(bnorm)) {
+    st = CHNSS_ERR_NAN;
+  } else if (rnorm <= target) {
+    converged = true;
+  } else {
+    vec_copy(n, b, ws.w, s);
+    set_scalar(sc + 2, sc, 1.0, true, s);   // sc[2] = ||r||
+    while (true) {
+      vec_scale_by_inv(n, ws.w, sc + 2, ws.V, s);
+      vec_fill(m + 1, 0.0, ws.g, s);
+      set_scalar(ws.g, sc + 2, 1.0, false, s);
+      int k = 0;
+      bool breakdown = false;
+      for (int j = 0; j < m; ++j) {
+        double *vj = ws.V + (long)j * n;
+        double *zj = ws.Z + (long)j * n;
+        A.precond(vj, zj, s);
+        A.apply(zj, ws.w, s);
+        mdot(n, ws.V, n, j + 1, ws.w, ws.h1, ws.partial, s);
+        ortho_update_mdot(n, ws.V, n, j + 1, ws.h1, ws.w, ws.h2, ws.partial, s);
+        ortho_update_norm(n, ws.V, n, j + 1, ws.h2, ws.w, sc + 3, ws.partial, s);
+        arnoldi_finish(j, ldh, ws.H, ws.h1, ws.h2, sc + 3, ws.cs, ws.sn, ws.g, sc + 4, s);
+        CHNSS_CK(cudaMemcpyAsync(ws.hstat, sc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CHNSS_CK(cudaStreamSynchronize(s));
+        const double est = ws.hstat[0], hn = ws.hstat[1];
+        ++iters;
+        k = j + 1;
+        if (!std::isfinite(est) || !std::isfinite(hn)) {
+          st = CHNSS_ERR_NAN;
+          break;
+        }
+        breakdown = hn == 0.0;
+        if (!breakdown) vec_scale_by_inv(n, ws.w, sc + 5, ws.V + (long)(j + 1) * n, s);
+        if (est <= target || iters >= maxit || breakdown) break;
+      }
+      if (st != CHNSS_OK) break;
+      hessenberg_solve(k, ldh, ws.H, ws.g, ws.y, s);
+      combine_columns(n, ws.Z, n, k, ws.y, x, s);
+      A.apply(x, ws.w, s);
+      vec_axpby(n, 1.0, b, -1.0, ws.w, s);                 // w = b - A x
+      dot<double>(n, ws.w, ws.w, sc + 1, ws.partial, s);
+      set_scalar(sc + 2, sc + 1, 1.0, true, s);
+      rnorm = std::sqrt(read_scalar(sc + 1, ws.hstat, s));
+      if (!std::isfinite(rnorm)) { st = CHNSS_ERR_NAN; break; }
+      if (rnorm <= target) { converged = true; break; }
+      if (iters >= maxit) { st = CHNSS_ERR_NOCONV; break; }
+      if (breakdown) { st = CHNSS_ERR_BREAKDOWN; break; }
+    }
+  }
+  if (info) {
+    info->iters = iters;
+    info->converged = converged ? 1 : 0;
+    info->rel_residual = bnorm > 0 ? rnorm / bnorm : 0.0;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return st;
+}
+
+chnss_status pcg(const Pattern &P, const double *val, const double *dinv, const double *b, double *x, double rtol,
+                 int maxit, KrylovWork &ws, chnss_solve_info *info, cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const long n = P.nrows;
+  double *r = ws.w, *z = ws.V, *p = ws.V + n, *q = ws.V + 2 * n;
+  double *sc = ws.sc;   // [0] bb [1] rz [2] rz_new [3] pq [4] alpha [5] rr
+  vec_fill(n, 0.0, x, s);
+  vec_copy(n, b, r, s);
+  dot<double>(n, b, b, sc, ws.partial, s);
+  const double bnorm = std::sqrt(read_scalar(sc, ws.hstat, s));
+  const double target = rtol * bnorm;
+  double rn = bnorm;
+  int it = 0;
+  bool converged = false;
+  chnss_status st = CHNSS_OK;
+  if (!std::isfinite(bnorm)) {
+    st = CHNSS_ERR_NAN;
+  } else if (bnorm <= target) {
+    converged = true;
+  } else {
+    vec_mul(n, dinv, r, z, s);
+    vec_copy(n, z, p, s);
+    dot<double>(n, r, z, sc + 1, ws.partial, s);
+    double *rz = sc + 1, *rzn = sc + 2;
+    SpmvArgs none;
+    while (it < maxit) {
+      spmv_csr<double>(P, val, 1, p, q, SPMV_PLAIN, none, s);
+      dot<double>(n, p, q, sc + 3, ws.partial, s);
+      pcg_alpha(rz, sc + 3, sc + 4, s);
+      pcg_update_xr(n, sc + 4, p, q, x, r, s);
+      ++it;
+      dot<double>(n, r, r, sc + 5, ws.partial, s);
+      rn = std::sqrt(read_scalar(sc + 5, ws.hstat, s));
+      if (!std::isfinite(rn)) { st = CHNSS_ERR_NAN; break; }
+      if (rn <= target) { converged = true; break; }
+      vec_mul(n, dinv, r, z, s);
+      dot<double>(n, r, z, rzn, ws.partial, s);
+      pcg_update_p(n, rzn, rz, z, p, s);
+      std::swap(rz, rzn);
+    }
+    if (!converged && st == CHNSS_OK) st = CHNSS_ERR_NOCONV;
+  }
+  if (info) {
+    info->iters = it;
+    info->converged = converged ? 1 : 0;
+    info->rel_residual = bnorm > 0 ? rn / bnorm : 0.0;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return st;
+}
+
+}  // namespace chnss

@@ -1,0 +1,76 @@
+// Geometric multigrid V-cycle and Krylov drivers (host orchestration of the
+// kernels in sparse.cu).
+#pragma once
+
+#include "kernels.h"
+
+namespace chnss {
+
+// One V-cycle of geometric multigrid (the inner solves that replace the
+// paper's PyAMG blocks, Sec. 4): degree-2 Chebyshev-Jacobi pre/post
+// smoothing on [hi/4, hi] (hi: Gershgorin bound of D^-1 A), restriction
+// R = P^T, prolongation P, dense FP64 inverse on the coarsest level.
+// kind 0: scalar P1 operators (CSR); kind 1: velocity operators (BSR2,
+// interleaved vectors).  T is the smoothing precision.
+template <typename T>
+struct MGHier {
+  int kind = 0;
+  bool singular = false;   // pressure Laplacian: mean-zero projection, coarse K + 1 1^T
+  int nl = 0;
+  std::vector<const Pattern *> pat;
+  std::vector<const int *> diag;
+  std::vector<const double *> val64;
+  std::vector<T *> val;
+  std::vector<T *> dinv, x, t, r, b;
+  std::vector<double *> hi, coef;
+  std::vector<const Transfer *> tr;
+  std::vector<long> n;
+  int nc = 0;
+  double *dense = nullptr, *cinv = nullptr;
+  int *status = nullptr;
+  double *partial = nullptr, *sum = nullptr;
+
+  // levels: per level pattern + FP64 value pointer (values may change
+  // between setups, the pointers may not); transfers tr[l] from level l+1.
+  void init(Arena &ar, int kind, bool singular, const std::vector<const Pattern *> &pats,
+            const std::vector<const int *> &diags, const std::vector<const double *> &vals,
+            const std::vector<const Transfer *> &trs, double *partial_buf);
+  // Recompute Jacobi data, Chebyshev coefficients, FP32 copies and the
+  // coarse inverse from the current FP64 values.
+  void setup(cudaStream_t s);
+  T *input() { return b[0]; }
+  T *output() { return x[0]; }
+  void apply(cudaStream_t s);   // x[0] = V-cycle(b[0])
+
+ private:
+  void op(int l, const T *u, T *out, SpmvMode mode, const SpmvArgs &a, cudaStream_t s);
+  void vcycle(int l, cudaStream_t s);
+};
+
+struct LinearOperator {
+  virtual ~LinearOperator() = default;
+  virtual long size() const = 0;
+  virtual void apply(const double *x, double *y, cudaStream_t s) = 0;
+  virtual void precond(const double *r, double *z, cudaStream_t s) = 0;
+};
+
+struct KrylovWork {
+  int m = 0;
+  long nmax = 0;
+  double *V = nullptr, *Z = nullptr, *w = nullptr;
+  double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
+  double *h1 = nullptr, *h2 = nullptr, *sc = nullptr, *partial = nullptr;
+  double *hstat = nullptr;   // pinned host, 4 doubles
+  void init(Arena &ar, int m, long nmax, double *pinned);
+};
+
+// Right-preconditioned FGMRES(m), CGS2, Givens, x0 = 0; stop when the true
+// residual satisfies ||b - A x|| <= max(rtol ||b||, atol) (Sec. 5).
+chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, double atol, int maxit,
+                    KrylovWork &ws, chnss_solve_info *info, cudaStream_t s);
+
+// Jacobi PCG for an SPD CSR matrix (FP64), x0 = 0, recursive residual test.
+chnss_status pcg(const Pattern &P, const double *val, const double *dinv, const double *b, double *x, double rtol,
+                 int maxit, KrylovWork &ws, chnss_solve_info *info, cudaStream_t s);
+
+}  // namespace chnss

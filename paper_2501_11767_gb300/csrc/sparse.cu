@@ -1,0 +1,764 @@
+// Sparse matrix-vector products, vector updates and deterministic
+// reductions.  SpMV uses LANES threads per row (sub-warp CSR-vector): the
+// lanes of a group read consecutive entries of the row, so the value and
+// column streams are read coalesced; partial sums are combined with warp
+// shuffles.  Every reduction uses a grid size that depends only on the
+// vector length and sums in a fixed order, so results are bit-reproducible.
+#include <cmath>
+
+#include "kernels.h"
+
+namespace chnss {
+namespace {
+
+constexpr int TPB = 256;
+inline int nblocks(long n, int per_block) { return (int)((n + per_block - 1) / per_block); }
+
+template <int LANES, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, LANES);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ void epilogue(int mode, long i, T acc, const T *u, T *out, const SpmvArgs &a,
+                                         const double *coef) {
+  if (mode == SPMV_PLAIN) {
+    out[i] = acc;
+  } else if (mode == SPMV_RES) {
+    out[i] = static_cast<const T *>(a.b)[i] - acc;
+  } else if (mode == SPMV_ADD) {
+    out[i] += acc;
+  } else {
+    const T *b = static_cast<const T *>(a.b);
+    const T *w = static_cast<const T *>(a.w);
+    const T *dinv = static_cast<const T *>(a.dinv);
+    const T c0 = (T)coef[0], c1 = (T)coef[1], c2 = (T)coef[2];
+    T v = c0 * u[i] + c2 * dinv[i] * (b[i] - acc);
+    if (w) v += c1 * w[i];
+    out[i] = v;
+  }
+}
+
+template <int LANES, typename T>
+__global__ void __launch_bounds__(TPB) k_spmv_csr(int nrows, int ncomp, const int *__restrict__ rowptr,
+                                                  const int *__restrict__ col, const T *__restrict__ val,
+                                                  const T *__restrict__ u, T *out, int mode, SpmvArgs a) {
+  const int lane = threadIdx.x % LANES;
+  const int row = (blockIdx.x * TPB + threadIdx.x) / LANES;
+  const bool live = row < nrows;
+  const int b0 = live ? rowptr[row] : 0, b1 = live ? rowptr[row + 1] : 0;
+  if (ncomp == 1) {
+    T acc = 0;
+    for (int k = b0 + lane; k < b1; k += LANES) acc += val[k] * u[col[k]];
+    acc = group_sum<LANES>(acc);
+    if (live && lane == 0) epilogue<T>(mode, row, acc, u, out, a, a.coef);
+  } else {
+    T acc0 = 0, acc1 = 0;
+    for (int k = b0 + lane; k < b1; k += LANES) {
+      const T w = val[k];
+      const long c = 2L * col[k];
+      acc0 += w * u[c];
+      acc1 += w * u[c + 1];
+    }
+    acc0 = group_sum<LANES>(acc0);
+    acc1 = group_sum<LANES>(acc1);
+    if (live && lane == 0) {
+      epilogue<T>(mode, 2L * row, acc0, u, out, a, a.coef);
+      epilogue<T>(mode, 2L * row + 1, acc1, u, out, a, a.coef);
+    }
+  }
+}
+
+template <typename T>
+struct Vec2 { T x, y; };
+
+template <int LANES, typename T>
+__global__ void __launch_bounds__(TPB) k_spmv_bsr2(int nrows, const int *__restrict__ rowptr,
+                                                   const int *__restrict__ col, const T *__restrict__ val,
+                                                   const T *__restrict__ u, T *out, int mode, SpmvArgs a) {
+  const int lane = threadIdx.x % LANES;
+  const int row = (blockIdx.x * TPB + threadIdx.x) / LANES;
+  const bool live = row < nrows;
+  const int b0 = live ? rowptr[row] : 0, b1 = live ? rowptr[row + 1] : 0;
+  T acc0 = 0, acc1 = 0;
+  for (int k = b0 + lane; k < b1; k += LANES) {
+    const T *blk = val + 4L * k;
+    const long c = 2L * col[k];
+    const T x0 = u[c], x1 = u[c + 1];
+    acc0 += blk[0] * x0 + blk[1] * x1;
+    acc1 += blk[2] * x0 + blk[3] * x1;
+  }
+  acc0 = group_sum<LANES>(acc0);
+  acc1 = group_sum<LANES>(acc1);
+  if (live && lane == 0) {
+    epilogue<T>(mode, 2L * row, acc0, u, out, a, a.coef);
+    epilogue<T>(mode, 2L * row + 1, acc1, u, out, a, a.coef);
+  }
+}
+
+// CH operator on the P1 pattern
+__global__ void __launch_bounds__(TPB) k_spmv_ch(int nrows, const int *__restrict__ rowptr,
+                                                 const int *__restrict__ col, const double *__restrict__ L,
+                                                 const double *__restrict__ K, const double *__restrict__ K12,
+                                                 const double *__restrict__ M, double a12, double a21, double a22,
+                                                 const double *__restrict__ x, double *__restrict__ y) {
+  constexpr int LANES = 8;
+  const int lane = threadIdx.x % LANES;
+  const int row = (blockIdx.x * TPB + threadIdx.x) / LANES;
+  const bool live = row < nrows;
+  const int b0 = live ? rowptr[row] : 0, b1 = live ? rowptr[row + 1] : 0;
+  const double *x1 = x, *x2 = x + nrows;
+  double s11 = 0, s12 = 0, s21 = 0, s22 = 0;
+  for (int k = b0 + lane; k < b1; k += LANES) {
+    const int c = col[k];
+    const double u1 = x1[c], u2 = x2[c], kv = K[k];
+    s11 += L[k] * u1;
+    s12 += (K12 ? K12[k] : kv) * u2;
+    s21 += kv * u1;
+    s22 += M[k] * u2;
+  }
+  s11 = group_sum<LANES>(s11);
+  s12 = group_sum<LANES>(s12);
+  s21 = group_sum<LANES>(s21);
+  s22 = group_sum<LANES>(s22);
+  if (live && lane == 0) {
+    y[row] = s11 + a12 * s12;
+    y[nrows + row] = a21 * s21 + a22 * s22;
+  }
+}
+
+__global__ void __launch_bounds__(TPB) k_spmv_b(int nrows, const int *__restrict__ rowptr,
+                                                const int *__restrict__ col, const double *__restrict__ val,
+                                                const double *__restrict__ v, double *__restrict__ y) {
+  constexpr int LANES = 8;
+  const int lane = threadIdx.x % LANES;
+  const int row = (blockIdx.x * TPB + threadIdx.x) / LANES;
+  const bool live = row < nrows;
+  const int b0 = live ? rowptr[row] : 0, b1 = live ? rowptr[row + 1] : 0;
+  double acc = 0;
+  for (int k = b0 + lane; k < b1; k += LANES) {
+    const long c = 2L * col[k];
+    acc += val[2L * k] * v[c] + val[2L * k + 1] * v[c + 1];
+  }
+  acc = group_sum<LANES>(acc);
+  if (live && lane == 0) y[row] = acc;
+}
+
+__global__ void __launch_bounds__(TPB) k_spmv_bt_add(int nrows, const int *__restrict__ rowptr,
+                                                     const int *__restrict__ col, const double *__restrict__ val,
+                                                     const double *__restrict__ p, double *__restrict__ yv) {
+  constexpr int LANES = 4;
+  const int lane = threadIdx.x % LANES;
+  const int row = (blockIdx.x * TPB + threadIdx.x) / LANES;
+  const bool live = row < nrows;
+  const int b0 = live ? rowptr[row] : 0, b1 = live ? rowptr[row + 1] : 0;
+  double a0 = 0, a1 = 0;
+  for (int k = b0 + lane; k < b1; k += LANES) {
+    const double q = p[col[k]];
+    a0 += val[2L * k] * q;
+    a1 += val[2L * k + 1] * q;
+  }
+  a0 = group_sum<LANES>(a0);
+  a1 = group_sum<LANES>(a1);
+  if (live && lane == 0) {
+    yv[2L * row] += a0;
+    yv[2L * row + 1] += a1;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Jacobi / Gershgorin
+template <typename T>
+__global__ void k_jacobi_csr(int nrows, const int *__restrict__ rowptr, const double *__restrict__ val,
+                             const int *__restrict__ diag, T *dinv, double *partial) {
+  __shared__ double sm[TPB];
+  double best = 0.0;
+  for (int r = blockIdx.x * TPB + threadIdx.x; r < nrows; r += gridDim.x * TPB) {
+    const double d = val[diag[r]];
+    double s = 0.0;
+    for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) s += fabs(val[k]);
+    dinv[r] = (T)(1.0 / d);
+    best = fmax(best, s / fabs(d));
+  }
+  sm[threadIdx.x] = best;
+  __syncthreads();
+  for (int o = TPB / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+}
+
+template <typename T>
+__global__ void k_jacobi_bsr2(int nrows, const int *__restrict__ rowptr, const double *__restrict__ val,
+                              const int *__restrict__ diag, T *dinv, double *partial) {
+  __shared__ double sm[TPB];
+  double best = 0.0;
+  for (int r = blockIdx.x * TPB + threadIdx.x; r < nrows; r += gridDim.x * TPB) {
+    const double *dblk = val + 4L * diag[r];
+    double s0 = 0.0, s1 = 0.0;
+    for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+      const double *b = val + 4L * k;
+      s0 += fabs(b[0]) + fabs(b[1]);
+      s1 += fabs(b[2]) + fabs(b[3]);
+    }
+    dinv[2L * r] = (T)(1.0 / dblk[0]);
+    dinv[2L * r + 1] = (T)(1.0 / dblk[3]);
+    best = fmax(best, fmax(s0 / fabs(dblk[0]), s1 / fabs(dblk[3])));
+  }
+  sm[threadIdx.x] = best;
+  __syncthreads();
+  for (int o = TPB / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+}
+
+__global__ void k_max_final(int nb, const double *partial, double *out) {
+  __shared__ double sm[TPB];
+  double best = 0.0;
+  for (int i = threadIdx.x; i < nb; i += TPB) best = fmax(best, partial[i]);
+  sm[threadIdx.x] = best;
+  __syncthreads();
+  for (int o = TPB / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sm[0];
+}
+
+// Degree-2 Chebyshev smoother on [hi/ratio, hi] (three-term recurrence,
+// Saad Alg. 12.1 on D^-1 A): theta, delta, sigma, rho0 = 1/sigma,
+// rho1 = 1/(2 sigma - rho0); beta0 = 1/theta, alpha1 = rho1 rho0,
+// beta1 = 2 rho1 / delta.
+__global__ void k_cheb_coef(const double *hi, double ratio, double *c) {
+  const double h = *hi, lo = h / ratio;
+  const double theta = 0.5 * (h + lo), delta = 0.5 * (h - lo), sigma = theta / delta;
+  const double rho0 = 1.0 / sigma, rho1 = 1.0 / (2.0 * sigma - rho0);
+  const double b0 = 1.0 / theta, a1 = rho1 * rho0, b1 = 2.0 * rho1 / delta;
+  c[0] = b0;
+  c[1] = 1.0 + a1; c[2] = 0.0; c[3] = b1;     // pre2: x = (1+a1) t + b1 D^-1 (b - A t)
+  c[4] = 1.0; c[5] = 0.0; c[6] = b0;          // post1: t = x + b0 D^-1 (b - A x)
+  c[7] = 1.0 + a1; c[8] = -a1; c[9] = b1;     // post2: x = (1+a1) t - a1 x + b1 D^-1 (b - A t)
+}
+
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void k_scale_dinv(int n, const double *scale, const T *dinv, const T *b, T *out) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i < n) out[i] = (T)(*scale) * dinv[i] * b[i];
+}
+template <typename Ta, typename Tb>
+__global__ void k_convert(long n, const Ta *in, Tb *out) {
+  const long i = (long)blockIdx.x * TPB + threadIdx.x;
+  if (i < n) out[i] = (Tb)in[i];
+}
+__global__ void k_axpby(long n, double a, const double *x, double b, double *y) {
+  const long i = (long)blockIdx.x * TPB + threadIdx.x;
+  if (i < n) y[i] = a * x[i] + b * y[i];
+}
+__global__ void k_copy(long n, const double *x, double *y) {
+  const long i = (long)blockIdx.x * TPB + threadIdx.x;
+  if (i < n) y[i] = x[i];
+}
+__global__ void k_fill(long n, double v, double *y) {
+  const long i = (long)blockIdx.x * TPB + threadIdx.x;
+  if (i < n) y[i] = v;
+}
+__global__ void k_scale_by_inv(long n, const double *src, const double *hn, double *dst) {
+  const long i = (long)blockIdx.x * TPB + threadIdx.x;
+  if (i < n) dst[i] = src[i] / *hn;
+}
+template <typename T>
+__global__ void k_sub_mean(int n, T *x, const double *sum) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i < n) x[i] = (T)((double)x[i] - *sum / n);
+}
+__global__ void k_mul(long n, const double *a, const double *b, double *out) {
+  const long i = (long)blockIdx.x * TPB + threadIdx.x;
+  if (i < n) out[i] = a[i] * b[i];
+}
+
+// --------------------------------------------------------------------------
+// reductions
+__device__ __forceinline__ double block_sum(double v, double *sm) {
+  sm[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = TPB / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double r = sm[0];
+  __syncthreads();
+  return r;
+}
+
+template <typename T>
+__global__ void k_dot(long n, const T *x, const T *y, double *partial) {
+  __shared__ double sm[TPB];
+  double s = 0.0;
+  for (long i = (long)blockIdx.x * TPB + threadIdx.x; i < n; i += (long)gridDim.x * TPB)
+    s += (double)x[i] * (double)(y ? y[i] : (T)1);
+  s = block_sum(s, sm);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// sum of nb partials for each of k vectors: partial[v * nb + b]
+__global__ void k_sum_final(int nb, int k, const double *partial, double *out) {
+  __shared__ double sm[TPB];
+  for (int v = blockIdx.x; v < k; v += gridDim.x) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += TPB) s += partial[(long)v * nb + i];
+    s = block_sum(s, sm);
+    if (threadIdx.x == 0) out[v] = s;
+  }
+}
+
+constexpr int KC = 16;   // vectors per multi-dot chunk
+
+// partial[v * nb + b] for v in [k0, k0 + kc)
+__global__ void k_mdot(long n, const double *__restrict__ V, long ldv, int k0, int kc, const double *__restrict__ w,
+                       double *partial) {
+  __shared__ double sm[TPB];
+  double acc[KC];
+#pragma unroll
+  for (int j = 0; j < KC; ++j) acc[j] = 0.0;
+  for (long i = (long)blockIdx.x * TPB + threadIdx.x; i < n; i += (long)gridDim.x * TPB) {
+    const double wi = w[i];
+#pragma unroll
+    for (int j = 0; j < KC; ++j)
+      if (j < kc) acc[j] += V[(long)(k0 + j) * ldv + i] * wi;
+  }
+  for (int j = 0; j < kc; ++j) {
+    const double s = block_sum(acc[j], sm);
+    if (threadIdx.x == 0) partial[(long)(k0 + j) * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// w -= V h (k vectors); then partial dots V^T w (mode 0) or w^T w (mode 1)
+template <int MODE>
+__global__ void k_ortho_update(long n, const double *__restrict__ V, long ldv, int k, const double *__restrict__ h,
+                               double *__restrict__ w, double *partial, int k0, int kc) {
+  __shared__ double sm[TPB];
+  __shared__ double hs[64];
+  if (threadIdx.x < k) hs[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  double acc[KC];
+#pragma unroll
+  for (int j = 0; j < KC; ++j) acc[j] = 0.0;
+  for (long i = (long)blockIdx.x * TPB + threadIdx.x; i < n; i += (long)gridDim.x * TPB) {
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) s += hs[j] * V[(long)j * ldv + i];
+    const double wi = w[i] - s;
+    if (k0 == 0) w[i] = wi;          // the first chunk writes the update
+    if (MODE == 0) {
+#pragma unroll
+      for (int j = 0; j < KC; ++j)
+        if (j < kc) acc[j] += V[(long)(k0 + j) * ldv + i] * wi;
+    } else {
+      acc[0] += wi * wi;
+    }
+  }
+  const int nv = MODE == 0 ? kc : 1;
+  for (int j = 0; j < nv; ++j) {
+    const double s = block_sum(acc[j], sm);
+    if (threadIdx.x == 0) partial[(long)(k0 + j) * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_combine(long n, const double *__restrict__ Z, long ldz, int k, const double *__restrict__ y,
+                          double *__restrict__ x) {
+  __shared__ double ys[64];
+  if (threadIdx.x < k) ys[threadIdx.x] = y[threadIdx.x];
+  __syncthreads();
+  const long i = (long)blockIdx.x * TPB + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int j = 0; j < k; ++j) s += ys[j] * Z[(long)j * ldz + i];
+  x[i] += s;
+}
+
+__global__ void k_arnoldi_finish(int j, int ldh, double *H, const double *h1, const double *h2, const double *nrm2,
+                                 double *cs, double *sn, double *g, double *status) {
+  double *col = H + (long)j * ldh;
+  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+  const double hn = sqrt(*nrm2);
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = col[i], c = col[i + 1];
+    col[i] = cs[i] * a + sn[i] * c;
+    col[i + 1] = -sn[i] * a + cs[i] * c;
+  }
+  const double den = hypot(col[j], col[j + 1]);
+  cs[j] = col[j] / den;
+  sn[j] = col[j + 1] / den;
+  col[j] = den;
+  col[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  status[0] = fabs(g[j + 1]);
+  status[1] = hn;
+}
+
+__global__ void k_hessenberg_solve(int k, int ldh, const double *H, const double *g, double *y) {
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int c = i + 1; c < k; ++c) s -= H[(long)c * ldh + i] * y[c];
+    y[i] = s / H[(long)i * ldh + i];
+  }
+}
+
+__global__ void k_set_scalar(double *dst, const double *src, double scale, int sq) {
+  const double v = sq ? sqrt(*src) : *src;
+  *dst = scale * v;
+}
+__global__ void k_pcg_alpha(const double *rz, const double *pq, double *alpha) { *alpha = *rz / *pq; }
+__global__ void k_pcg_xr(long n, const double *alpha, const double *p, const double *q, double *x, double *r) {
+  const long i = (long)blockIdx.x * TPB + threadIdx.x;
+  if (i < n) {
+    const double a = *alpha;
+    x[i] += a * p[i];
+    r[i] -= a * q[i];
+  }
+}
+__global__ void k_pcg_p(long n, const double *rzn, const double *rzo, const double *z, double *p) {
+  const long i = (long)blockIdx.x * TPB + threadIdx.x;
+  if (i < n) p[i] = z[i] + (*rzn / *rzo) * p[i];
+}
+
+// --------------------------------------------------------------------------
+// coarse grid
+__global__ void k_dense_csr(int nrows, const int *rowptr, const int *col, const double *val, double add_all,
+                            double *dense) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  for (int c = 0; c < nrows; ++c) dense[(long)r * nrows + c] = add_all;
+  for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) dense[(long)r * nrows + col[k]] += val[k];
+}
+__global__ void k_dense_bsr2(int nrows, const int *rowptr, const int *col, const double *val, double *dense) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  const int n = 2 * nrows;
+  for (int c = 0; c < n; ++c) {
+    dense[(long)(2 * r) * n + c] = 0.0;
+    dense[(long)(2 * r + 1) * n + c] = 0.0;
+  }
+  for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+    const int c = 2 * col[k];
+    dense[(long)(2 * r) * n + c] = val[4L * k];
+    dense[(long)(2 * r) * n + c + 1] = val[4L * k + 1];
+    dense[(long)(2 * r + 1) * n + c] = val[4L * k + 2];
+    dense[(long)(2 * r + 1) * n + c + 1] = val[4L * k + 3];
+  }
+}
+
+// Gauss-Jordan inverse with partial pivoting of a (n x n, row-major,
+// destroyed) into inv; one CTA.  status = 1 on an exactly zero pivot.
+__global__ void k_dense_invert(int n, double *a, double *inv, int *status) {
+  __shared__ int piv;
+  __shared__ double sv[TPB];
+  __shared__ int si[TPB];
+  for (long t = threadIdx.x; t < (long)n * n; t += blockDim.x) inv[t] = (t / n == t % n) ? 1.0 : 0.0;
+  if (threadIdx.x == 0) *status = 0;
+  __syncthreads();
+  for (int c = 0; c < n; ++c) {
+    double best = -1.0;
+    int bi = c;
+    for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
+      const double v = fabs(a[(long)r * n + c]);
+      if (v > best || (v == best && r < bi)) { best = v; bi = r; }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        const double v2 = sv[threadIdx.x + o];
+        const int i2 = si[threadIdx.x + o];
+        if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
+          sv[threadIdx.x] = v2;
+          si[threadIdx.x] = i2;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      piv = si[0];
+      if (sv[0] == 0.0) *status = 1;
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p != c)
+      for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        double x = a[(long)c * n + t]; a[(long)c * n + t] = a[(long)p * n + t]; a[(long)p * n + t] = x;
+        x = inv[(long)c * n + t]; inv[(long)c * n + t] = inv[(long)p * n + t]; inv[(long)p * n + t] = x;
+      }
+    __syncthreads();
+    const double d = a[(long)c * n + c];
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      a[(long)c * n + t] /= d;
+      inv[(long)c * n + t] /= d;
+    }
+    __syncthreads();
+    for (long t = threadIdx.x; t < (long)n * n; t += blockDim.x) {
+      const int r = (int)(t / n), q = (int)(t % n);
+      if (r == c) continue;
+      const double f = a[(long)r * n + c];
+      if (q != c) a[t] -= f * a[(long)c * n + q];
+      inv[t] -= f * inv[(long)c * n + q];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x)
+      if (r != c) a[(long)r * n + c] = 0.0;
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_dense_apply(int n, const double *inv, const T *b, T *x) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double s = 0.0;
+  for (int c = 0; c < n; ++c) s += inv[(long)r * n + c] * (double)b[c];
+  x[r] = (T)s;
+}
+
+}  // namespace
+
+// ============================================================================
+template <typename T>
+void spmv_csr(const Pattern &P, const T *val, int ncomp, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
+              cudaStream_t s) {
+  if (P.nrows == 0) return;
+  const double avg = P.nnz / (double)P.nrows;
+  if (avg <= 4.5) {
+    k_spmv_csr<4, T><<<nblocks((long)P.nrows * 4, TPB), TPB, 0, s>>>(P.nrows, ncomp, P.rowptr, P.col, val, u, out,
+                                                                    mode, a);
+  } else {
+    k_spmv_csr<8, T><<<nblocks((long)P.nrows * 8, TPB), TPB, 0, s>>>(P.nrows, ncomp, P.rowptr, P.col, val, u, out,
+                                                                    mode, a);
+  }
+  CHNSS_LAUNCH_CK();
+}
+template <typename T>
+void spmv_bsr2(const Pattern &P, const T *val, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
+               cudaStream_t s) {
+  if (P.nrows == 0) return;
+  k_spmv_bsr2<8, T><<<nblocks((long)P.nrows * 8, TPB), TPB, 0, s>>>(P.nrows, P.rowptr, P.col, val, u, out, mode, a);
+  CHNSS_LAUNCH_CK();
+}
+template void spmv_csr<double>(const Pattern &, const double *, int, const double *, double *, SpmvMode,
+                               const SpmvArgs &, cudaStream_t);
+template void spmv_csr<float>(const Pattern &, const float *, int, const float *, float *, SpmvMode,
+                              const SpmvArgs &, cudaStream_t);
+template void spmv_bsr2<double>(const Pattern &, const double *, const double *, double *, SpmvMode,
+                                const SpmvArgs &, cudaStream_t);
+template void spmv_bsr2<float>(const Pattern &, const float *, const float *, float *, SpmvMode,
+                               const SpmvArgs &, cudaStream_t);
+
+void spmv_ch(const Pattern &P, const double *L, const double *K, const double *k12, const double *M, double a12,
+             double a21, double a22, const double *x, double *y, cudaStream_t s) {
+  k_spmv_ch<<<nblocks((long)P.nrows * 8, TPB), TPB, 0, s>>>(P.nrows, P.rowptr, P.col, L, K, k12, M, a12, a21, a22,
+                                                           x, y);
+  CHNSS_LAUNCH_CK();
+}
+void spmv_b(const Pattern &P, const double *val, const double *v, double *y, cudaStream_t s) {
+  k_spmv_b<<<nblocks((long)P.nrows * 8, TPB), TPB, 0, s>>>(P.nrows, P.rowptr, P.col, val, v, y);
+  CHNSS_LAUNCH_CK();
+}
+void spmv_bt_add(const Pattern &P, const double *val, const double *p, double *yv, cudaStream_t s) {
+  k_spmv_bt_add<<<nblocks((long)P.nrows * 4, TPB), TPB, 0, s>>>(P.nrows, P.rowptr, P.col, val, p, yv);
+  CHNSS_LAUNCH_CK();
+}
+
+int reduce_blocks(long n) {
+  long b = (n + 4L * TPB - 1) / (4L * TPB);
+  if (b < 1) b = 1;
+  if (b > 1216) b = 1216;   // 8 per SM on 152 SMs
+  return (int)b;
+}
+
+template <typename T>
+void jacobi_csr(const Pattern &P, const double *val, const int *diag, T *dinv, double *hi, double *partial,
+                cudaStream_t s) {
+  const int nb = reduce_blocks(P.nrows);
+  k_jacobi_csr<T><<<nb, TPB, 0, s>>>(P.nrows, P.rowptr, val, diag, dinv, partial);
+  CHNSS_LAUNCH_CK();
+  k_max_final<<<1, TPB, 0, s>>>(nb, partial, hi);
+  CHNSS_LAUNCH_CK();
+}
+template <typename T>
+void jacobi_bsr2(const Pattern &P, const double *val, const int *diag, T *dinv, double *hi, double *partial,
+                 cudaStream_t s) {
+  const int nb = reduce_blocks(P.nrows);
+  k_jacobi_bsr2<T><<<nb, TPB, 0, s>>>(P.nrows, P.rowptr, val, diag, dinv, partial);
+  CHNSS_LAUNCH_CK();
+  k_max_final<<<1, TPB, 0, s>>>(nb, partial, hi);
+  CHNSS_LAUNCH_CK();
+}
+template void jacobi_csr<double>(const Pattern &, const double *, const int *, double *, double *, double *,
+                                 cudaStream_t);
+template void jacobi_csr<float>(const Pattern &, const double *, const int *, float *, double *, double *,
+                                cudaStream_t);
+template void jacobi_bsr2<double>(const Pattern &, const double *, const int *, double *, double *, double *,
+                                  cudaStream_t);
+template void jacobi_bsr2<float>(const Pattern &, const double *, const int *, float *, double *, double *,
+                                 cudaStream_t);
+
+void cheb_coefficients(const double *hi, double ratio, double *coef, cudaStream_t s) {
+  k_cheb_coef<<<1, 1, 0, s>>>(hi, ratio, coef);
+  CHNSS_LAUNCH_CK();
+}
+
+template <typename T>
+void vec_scale_dinv(int n, const double *scale, const T *dinv, const T *b, T *out, cudaStream_t s) {
+  k_scale_dinv<T><<<nblocks(n, TPB), TPB, 0, s>>>(n, scale, dinv, b, out);
+  CHNSS_LAUNCH_CK();
+}
+template void vec_scale_dinv<double>(int, const double *, const double *, const double *, double *, cudaStream_t);
+template void vec_scale_dinv<float>(int, const double *, const float *, const float *, float *, cudaStream_t);
+
+template <typename Ta, typename Tb>
+void vec_convert(long n, const Ta *in, Tb *out, cudaStream_t s) {
+  if (n == 0) return;
+  k_convert<Ta, Tb><<<nblocks(n, TPB), TPB, 0, s>>>(n, in, out);
+  CHNSS_LAUNCH_CK();
+}
+template void vec_convert<double, float>(long, const double *, float *, cudaStream_t);
+template void vec_convert<float, double>(long, const float *, double *, cudaStream_t);
+template void vec_convert<double, double>(long, const double *, double *, cudaStream_t);
+
+void vec_axpby(long n, double a, const double *x, double b, double *y, cudaStream_t s) {
+  k_axpby<<<nblocks(n, TPB), TPB, 0, s>>>(n, a, x, b, y);
+  CHNSS_LAUNCH_CK();
+}
+void vec_copy(long n, const double *x, double *y, cudaStream_t s) {
+  k_copy<<<nblocks(n, TPB), TPB, 0, s>>>(n, x, y);
+  CHNSS_LAUNCH_CK();
+}
+void vec_fill(long n, double v, double *y, cudaStream_t s) {
+  k_fill<<<nblocks(n, TPB), TPB, 0, s>>>(n, v, y);
+  CHNSS_LAUNCH_CK();
+}
+void vec_scale_by_inv(long n, const double *src, const double *hn, double *dst, cudaStream_t s) {
+  k_scale_by_inv<<<nblocks(n, TPB), TPB, 0, s>>>(n, src, hn, dst);
+  CHNSS_LAUNCH_CK();
+}
+template <typename T>
+void vec_sub_mean(int n, T *x, const double *sum, cudaStream_t s) {
+  k_sub_mean<T><<<nblocks(n, TPB), TPB, 0, s>>>(n, x, sum);
+  CHNSS_LAUNCH_CK();
+}
+template void vec_sub_mean<double>(int, double *, const double *, cudaStream_t);
+template void vec_sub_mean<float>(int, float *, const double *, cudaStream_t);
+void vec_mul(long n, const double *a, const double *b, double *out, cudaStream_t s) {
+  k_mul<<<nblocks(n, TPB), TPB, 0, s>>>(n, a, b, out);
+  CHNSS_LAUNCH_CK();
+}
+
+template <typename T>
+void dot(long n, const T *x, const T *y, double *out, double *partial, cudaStream_t s) {
+  const int nb = reduce_blocks(n);
+  k_dot<T><<<nb, TPB, 0, s>>>(n, x, y, partial);
+  CHNSS_LAUNCH_CK();
+  k_sum_final<<<1, TPB, 0, s>>>(nb, 1, partial, out);
+  CHNSS_LAUNCH_CK();
+}
+template void dot<double>(long, const double *, const double *, double *, double *, cudaStream_t);
+template void dot<float>(long, const float *, const float *, double *, double *, cudaStream_t);
+template <typename T>
+void vsum(long n, const T *x, double *out, double *partial, cudaStream_t s) {
+  dot<T>(n, x, nullptr, out, partial, s);
+}
+template void vsum<double>(long, const double *, double *, double *, cudaStream_t);
+template void vsum<float>(long, const float *, double *, double *, cudaStream_t);
+
+void mdot(long n, const double *V, long ldv, int k, const double *w, double *out, double *partial, cudaStream_t s) {
+  const int nb = reduce_blocks(n);
+  for (int k0 = 0; k0 < k; k0 += KC) {
+    k_mdot<<<nb, TPB, 0, s>>>(n, V, ldv, k0, std::min(KC, k - k0), w, partial);
+    CHNSS_LAUNCH_CK();
+  }
+  k_sum_final<<<std::min(k, 64), TPB, 0, s>>>(nb, k, partial, out);
+  CHNSS_LAUNCH_CK();
+}
+void ortho_update_mdot(long n, const double *V, long ldv, int k, const double *h, double *w, double *out,
+                       double *partial, cudaStream_t s) {
+  const int nb = reduce_blocks(n);
+  // chunk 0 updates w in place and dots against vectors [0, 16); later
+  // chunks see the updated w only if they run after chunk 0 finished, which
+  // stream order guarantees, but they must not subtract again: recompute the
+  // dots of later chunks with plain k_mdot on the updated w.
+  k_ortho_update<0><<<nb, TPB, 0, s>>>(n, V, ldv, k, h, w, partial, 0, std::min(KC, k));
+  CHNSS_LAUNCH_CK();
+  for (int k0 = KC; k0 < k; k0 += KC) {
+    k_mdot<<<nb, TPB, 0, s>>>(n, V, ldv, k0, std::min(KC, k - k0), w, partial);
+    CHNSS_LAUNCH_CK();
+  }
+  k_sum_final<<<std::min(k, 64), TPB, 0, s>>>(nb, k, partial, out);
+  CHNSS_LAUNCH_CK();
+}
+void ortho_update_norm(long n, const double *V, long ldv, int k, const double *h, double *w, double *out,
+                       double *partial, cudaStream_t s) {
+  const int nb = reduce_blocks(n);
+  k_ortho_update<1><<<nb, TPB, 0, s>>>(n, V, ldv, k, h, w, partial, 0, 1);
+  CHNSS_LAUNCH_CK();
+  k_sum_final<<<1, TPB, 0, s>>>(nb, 1, partial, out);
+  CHNSS_LAUNCH_CK();
+}
+void combine_columns(long n, const double *Z, long ldz, int k, const double *y, double *x, cudaStream_t s) {
+  k_combine<<<nblocks(n, TPB), TPB, 0, s>>>(n, Z, ldz, k, y, x);
+  CHNSS_LAUNCH_CK();
+}
+void arnoldi_finish(int j, int ldh, double *H, const double *h1, const double *h2, const double *nrm2, double *cs,
+                    double *sn, double *g, double *status, cudaStream_t s) {
+  k_arnoldi_finish<<<1, 1, 0, s>>>(j, ldh, H, h1, h2, nrm2, cs, sn, g, status);
+  CHNSS_LAUNCH_CK();
+}
+void hessenberg_solve(int k, int ldh, const double *H, const double *g, double *y, cudaStream_t s) {
+  k_hessenberg_solve<<<1, 1, 0, s>>>(k, ldh, H, g, y);
+  CHNSS_LAUNCH_CK();
+}
+void set_scalar(double *dst, const double *src, double scale, bool sq, cudaStream_t s) {
+  k_set_scalar<<<1, 1, 0, s>>>(dst, src, scale, sq ? 1 : 0);
+  CHNSS_LAUNCH_CK();
+}
+void pcg_alpha(const double *rz, const double *pq, double *alpha, cudaStream_t s) {
+  k_pcg_alpha<<<1, 1, 0, s>>>(rz, pq, alpha);
+  CHNSS_LAUNCH_CK();
+}
+void pcg_update_xr(long n, const double *alpha, const double *p, const double *q, double *x, double *r,
+                   cudaStream_t s) {
+  k_pcg_xr<<<nblocks(n, TPB), TPB, 0, s>>>(n, alpha, p, q, x, r);
+  CHNSS_LAUNCH_CK();
+}
+void pcg_update_p(long n, const double *rzn, const double *rzo, const double *z, double *p, cudaStream_t s) {
+  k_pcg_p<<<nblocks(n, TPB), TPB, 0, s>>>(n, rzn, rzo, z, p);
+  CHNSS_LAUNCH_CK();
+}
+
+void coarse_dense_csr(const Pattern &P, const double *val, double add_all, double *dense, cudaStream_t s) {
+  k_dense_csr<<<nblocks(P.nrows, 128), 128, 0, s>>>(P.nrows, P.rowptr, P.col, val, add_all, dense);
+  CHNSS_LAUNCH_CK();
+}
+void coarse_dense_bsr2(const Pattern &P, const double *val, double *dense, cudaStream_t s) {
+  k_dense_bsr2<<<nblocks(P.nrows, 128), 128, 0, s>>>(P.nrows, P.rowptr, P.col, val, dense);
+  CHNSS_LAUNCH_CK();
+}
+void dense_invert(int n, double *a, double *inv, int *status, cudaStream_t s) {
+  k_dense_invert<<<1, TPB, 0, s>>>(n, a, inv, status);
+  CHNSS_LAUNCH_CK();
+}
+template <typename T>
+void dense_apply(int n, const double *inv, const T *b, T *x, cudaStream_t s) {
+  k_dense_apply<T><<<nblocks(n, 128), 128, 0, s>>>(n, inv, b, x);
+  CHNSS_LAUNCH_CK();
+}
+template void dense_apply<double>(int, const double *, const double *, double *, cudaStream_t);
+template void dense_apply<float>(int, const double *, const float *, float *, cudaStream_t);
+
+}  // namespace chnss

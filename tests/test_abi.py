@@ -1,0 +1,72 @@
+"""The C-ABI library builds, loads and exports every symbol include/chnss.h
+declares; argument validation happens before any device call (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2501_11767_gb300 import build as B
+from paper_2501_11767_gb300 import chnss
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "chnss.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(chnss_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return chnss.load()
+
+
+def test_header_declares_the_step_api():
+    names = declared_functions()
+    for required in ("chnss_mesh_create", "chnss_ctx_create", "chnss_assemble", "chnss_solve", "chnss_step"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    # the Python binding covers exactly the declared calls
+    assert sorted(chnss.EXPORTS) == declared_functions()
+
+
+def test_library_is_built_for_sm_103a():
+    assert os.path.exists(B.LIB)
+    assert "arch=compute_103a,code=sm_103a" in " ".join(B.ARCH)
+
+
+def test_argument_errors_need_no_device(lib):
+    h = ctypes.c_void_p()
+    assert lib.chnss_mesh_create(7, 7, 1.0, 1.0, ctypes.byref(h)) == 1      # odd n
+    assert b"even" in lib.chnss_last_error(None)
+    assert lib.chnss_mesh_create(8, 16, 1.0, 1.0, ctypes.byref(h)) == 1     # nx != ny
+    assert lib.chnss_mesh_create(8, 8, -1.0, 1.0, ctypes.byref(h)) == 1     # bad length
+    assert lib.chnss_mesh_create(8, 8, 1.0, 1.0, None) == 1
+    assert lib.chnss_ctx_create(None, None, None, ctypes.byref(h)) == 1
+    assert lib.chnss_step(None, None, None, None) == 1
+    assert lib.chnss_system_size(None, 0) == -1
+    assert lib.chnss_mesh_destroy(None) == 0
+    assert lib.chnss_ctx_destroy(None) == 0
+
+
+def test_params_struct_matches_header():
+    text = open(HEADER).read()
+    body = text[text.index("typedef struct {\n  double tau;"):text.index("} chnss_params;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl or decl.startswith("typedef"):
+            decl = decl.replace("typedef struct {", "").strip()
+            if not decl:
+                continue
+        typ, rest = decl.split(None, 1)
+        for nm in rest.split(","):
+            fields.append(re.sub(r"\[.*\]", "", nm).strip())
+    assert fields == [f for f, _ in chnss.Params._fields_]

@@ -1,0 +1,207 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle: assembled
+matrices and right-hand sides entry by entry, every solve of a step (relative
+L2 <= 1e-9, Krylov iterations within +-1), whole steps, ragged mesh sizes,
+determinism and the mixed-precision path."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import fem, model
+from oracle.step import Oracle
+from paper_2501_11767_gb300 import chnss, inputs
+
+pytestmark = pytest.mark.gpu
+
+SOLVE_TOL = 1e-9        # FP64 GPU vs FP64 oracle, per solve (relative L2)
+MATRIX_TOL = 1e-13      # assembled entries, relative to the largest entry
+MIXED_TOL = 1e-6        # mixed precision vs oracle, per step (relative L2)
+
+
+def _torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    return torch
+
+
+def rel(a, b):
+    a, b = np.ravel(a), np.ravel(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _csr(ctx, which, shape):
+    rp, col, val = ctx.export_csr(which)
+    return sp.csr_matrix((val, col, rp), shape=shape)
+
+
+def _stepped_state(n, params, seed=2):
+    """Oracle state after one step (non-zero velocity and potentials)."""
+    o = Oracle(n, params)
+    s1, _ = o.step(inputs.initial_state(n, seed=seed))
+    return o, s1
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return _torch()
+
+
+@pytest.mark.parametrize("n", [8, 32])
+def test_assembled_matrices_and_rhs_match_oracle(torch, n):
+    params = inputs.default_params()
+    o, st = _stepped_state(n, params)
+    mesh = chnss.Mesh(n)
+    ctx = chnss.Context(mesh, params)
+    ctx.assemble(chnss.state_to_device(st))
+    torch.cuda.synchronize()
+    F = o.forms[0]
+    N1, N2 = o.mesh.N1, o.mesh.N2
+    conv = fem.convection_p1(o.mesh, st["v"])
+    A, B, rhs_v, Ap, _ = model.ns_system(F, st, params)
+    ref = {
+        chnss.MAT_M: F.M, chnss.MAT_K: F.K,
+        chnss.MAT_L: F.M + params["tau"] * conv,
+        chnss.MAT_AC: F.M + params["tau"] * params["delta_v"] * F.K + params["tau"] * conv,
+        chnss.MAT_A: A, chnss.MAT_B: B, chnss.MAT_AP: Ap,
+    }
+    shapes = {chnss.MAT_A: (2 * N2, 2 * N2), chnss.MAT_B: (N1, 2 * N2)}
+    for which, R in ref.items():
+        G = _csr(ctx, which, shapes.get(which, (N1, N1)))
+        scale = abs(R).max()
+        assert abs(G - R).max() <= MATRIX_TOL * scale, (which, abs(G - R).max(), scale)
+    # right-hand sides
+    loads = model.potential_loads(o.mesh, st["phi"], st["Phi_v"])
+    f, f_v, j_out = model.ch_rhs_loads(o.mesh, st, params, loads, F.top)
+    for sp_ in range(3):
+        _, rhs, _, _ = model.ch_system(F, st, params, sp_, f[sp_], conv)
+        assert rel(ctx.export_rhs(sp_), rhs) < 1e-13
+    _, rhs_ac = model.ac_system(F, st, params, f_v, conv, j_out)
+    assert rel(ctx.export_rhs(chnss.SYS_AC), rhs_ac) < 1e-13
+    rhs_ns = np.concatenate([rhs_v, np.zeros(N1)])
+    assert rel(ctx.export_rhs(chnss.SYS_NS), rhs_ns) < 1e-13
+
+
+def _compare_step(torch, n, params, seed, steps=2):
+    o = Oracle(n, params)
+    mesh = chnss.Mesh(n)
+    ctx = chnss.Context(mesh, params)
+    st = inputs.initial_state(n, seed=seed)
+    dev = chnss.state_to_device(st)
+    for k in range(steps):
+        ref, rinfo = o.step(st)
+        out, info, status = ctx.step(dev)
+        torch.cuda.synchronize()
+        got = chnss.state_to_numpy(out)
+        N1 = o.mesh.N1
+        for i, name in enumerate(("ch_p", "ch_N", "ch_s")):
+            assert info[name]["converged"], (name, info[name])
+            assert abs(info[name]["iters"] - rinfo[name]["iters"]) <= 1, (k, name, info[name], rinfo[name])
+            if info[name]["iters"] == rinfo[name]["iters"]:
+                e = rel(np.concatenate([got["phi"][i], got["mu"][i]]), np.concatenate([ref["phi"][i], ref["mu"][i]]))
+                assert e <= SOLVE_TOL, (k, name, e)
+        for name, keys in (("ac", ("Phi_v",)), ("ns", ("v", "p"))):
+            assert info[name]["converged"], (name, info[name])
+            assert abs(info[name]["iters"] - rinfo[name]["iters"]) <= 1, (k, name, info[name], rinfo[name])
+            if info[name]["iters"] == rinfo[name]["iters"]:
+                e = rel(np.concatenate([got[x].ravel() for x in keys]), np.concatenate([ref[x].ravel() for x in keys]))
+                assert e <= SOLVE_TOL, (k, name, e)
+        assert rel(got["mu"][3], ref["mu"][3]) <= SOLVE_TOL
+        assert status == 0
+        st, dev = ref, chnss.state_to_device(ref)     # continue both from the oracle state
+    return ctx
+
+
+@pytest.mark.parametrize("n", [32, 6, 20])
+def test_step_matches_oracle(torch, n):
+    """Two steps (the second with flow); n = 6 and 20 end on odd coarsest
+    meshes (3 and 5), 32 coarsens to 2."""
+    _compare_step(torch, n, inputs.default_params(), seed=n)
+
+
+def test_single_level_mesh(torch):
+    """n = 2: no coarsening, the V-cycle is the dense coarse inverse."""
+    _compare_step(torch, 2, inputs.default_params(), seed=1, steps=1)
+
+
+def test_variable_mobility_step(torch):
+    p = inputs.default_params()
+    p.update(mobility_kind=1, beta=[1e-4] * 4)
+    _compare_step(torch, 16, p, seed=4)
+
+
+def test_step_is_deterministic(torch):
+    n = 32
+    params = inputs.default_params()
+    mesh = chnss.Mesh(n)
+    ctx = chnss.Context(mesh, params)
+    dev = chnss.state_to_device(inputs.initial_state(n, seed=9))
+    a, _, _ = ctx.step(dev)
+    a = chnss.state_to_numpy(a)
+    b, _, _ = ctx.step(dev)
+    b = chnss.state_to_numpy(b)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_step_host_matches_device_step(torch):
+    n = 16
+    params = inputs.default_params()
+    mesh = chnss.Mesh(n)
+    ctx = chnss.Context(mesh, params)
+    st = inputs.initial_state(n, seed=3)
+    d, _, _ = ctx.step(chnss.state_to_device(st))
+    d = chnss.state_to_numpy(d)
+    hout = {k: np.zeros_like(v) for k, v in st.items()}
+    ctx.step_host({k: np.ascontiguousarray(v) for k, v in st.items()}, hout)
+    for k in d:
+        assert np.array_equal(d[k], hout[k]), k
+
+
+def test_mixed_precision_step(torch):
+    """FP32 preconditioners inside FP64 FGMRES reach the same 1e-8 relative
+    residual and stay within 1e-6 of the FP64 oracle per step."""
+    n = 32
+    params = inputs.default_params()
+    mixed = dict(params, precision=1)
+    o = Oracle(n, dict(params, rtol=1e-12))
+    st = inputs.initial_state(n, seed=5)
+    ctx = chnss.Context(chnss.Mesh(n), mixed)
+    for _ in range(2):
+        ref, _ = o.step(st)
+        out, info, status = ctx.step(chnss.state_to_device(st))
+        got = chnss.state_to_numpy(out)
+        assert status == 0
+        for name, i in info.items():
+            if name != "mu_a":
+                assert i["converged"] and i["rel_residual"] <= 1e-8, (name, i)
+        for key in ("phi", "mu", "Phi_v", "v", "p"):
+            assert rel(got[key], ref[key]) <= MIXED_TOL, key
+        st = ref
+
+
+def test_solve_with_explicit_rhs_and_state_errors(torch):
+    n = 8
+    params = inputs.default_params()
+    ctx = chnss.Context(chnss.Mesh(n), params)
+    with pytest.raises(chnss.ChnssError) as e:
+        ctx.solve(chnss.SYS_AC)
+    assert e.value.status == 8                      # solve before assemble
+    st = chnss.state_to_device(inputs.initial_state(n))
+    ctx.assemble(st)
+    with pytest.raises(chnss.ChnssError):
+        ctx.solve(chnss.SYS_MU_A)                   # needs the CH solutions first
+    rhs = torch.zeros(ctx.system_size(chnss.SYS_AC), dtype=torch.float64, device="cuda")
+    x, info, status = ctx.solve(chnss.SYS_AC, rhs=rhs)
+    assert status == 0 and info["iters"] == 0 and float(x.abs().max()) == 0.0   # b = 0
+    x, info, status = ctx.solve(chnss.SYS_AC, check=False)
+    assert status == 0 and info["converged"]
+
+
+def test_nonconvergence_is_reported(torch):
+    n = 16
+    p = inputs.default_params()
+    p.update(maxit=2, restart=2)
+    ctx = chnss.Context(chnss.Mesh(n), p)
+    ctx.assemble(chnss.state_to_device(inputs.initial_state(n)))
+    x, info, status = ctx.solve(chnss.SYS_NS, check=False)
+    assert status == 4 and not info["converged"] and info["iters"] == 2
