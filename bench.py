@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Throughput of one semi-implicit CH / AC / NS step on GB300.
+
+Workload (default): the 1024 x 1024 structured thin-film mesh (1,050,625 P1
+nodes, 4,198,401 P2 velocity nodes), eps = 0.005, dt = 5e-4, FP32
+multigrid / Chebyshev preconditioners inside FP64 FGMRES at a 1e-8 relative
+residual.  Inputs are synthetic (seeded SplitMix64 noise on the polymer and
+NFA fractions); the per-step working set (> 10 GB) is far larger than L2.
+
+A timed step = assembly + 3 Cahn-Hilliard solves + Allen-Cahn + air
+potential + Navier-Stokes (chnss_step on device buffers); the trajectory
+advances from step to step.  One JSON line on rank 0.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N]
+  python bench.py --impl reference     # the CPU oracle on the same metric
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "film1024_mixed"
+CPU_SAMPLE_N = 256          # cpu_baseline: one oracle step on 256 x 256 (~10-30 s)
+REF_SAMPLE_N = 128          # --impl reference: one oracle step on 128 x 128 per timed step
+METRIC = "time steps/s at 1M nodes (1024x1024 P1 mesh, FGMRES to 1e-8 relative residual)"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def nodes(n):
+    return (n + 1) ** 2
+
+
+# ---------------------------------------------------------------------------
+def cpu_sample(n: int, workload: str, steps: int = 1) -> dict:
+    """One oracle step (plain numpy/scipy, FP64) of the workload's parameter
+    set on an n x n mesh; returns seconds per step."""
+    from oracle.step import Oracle
+    from paper_2501_11767_gb300 import inputs
+    w = inputs.workload(workload)
+    params = dict(w["params"], precision=0)
+    o = Oracle(n, params)
+    st = inputs.initial_state(n, seed=0)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        st, info = o.step(st)
+        times.append(time.perf_counter() - t0)
+    return {"n": n, "seconds": times, "iters": {k: v["iters"] for k, v in info.items() if isinstance(v, dict)}}
+
+
+def run_cpu_sample_subprocess(n: int, workload: str, steps: int = 1) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(n), "--cpu-steps", str(steps),
+                        "--workload", workload], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id=None):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.device_id = device_id
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.device_id:
+                cmd[1:1] = ["-i", self.device_id]
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2501_11767_gb300 import chnss, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = inputs.workload(args.workload)
+    n, params = w["n"], w["params"]
+    mesh = chnss.Mesh(n)
+    N1, N2 = mesh.N1, mesh.N2
+    stream = torch.cuda.current_stream()
+    st0 = chnss.state_to_device(inputs.initial_state(n, seed=rank))
+
+    def timed_run(prm, warmup, steps, profile):
+        ctx = chnss.Context(mesh, prm, stream)
+        a, b = {k: v.clone() for k, v in st0.items()}, ctx.new_state()
+        for _ in range(warmup):
+            ctx.step(a, b)
+            a, b = b, a
+        torch.cuda.synchronize()
+        ctx.profile_enable(profile)
+        launches0 = ctx.profile_read()["launches"]
+        sampler = ClockSampler(_device_uuid(torch, local))
+        barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        infos = []
+        e0.record(stream)
+        for _ in range(steps):
+            _, info, status = ctx.step(a, b)
+            infos.append(info)
+            a, b = b, a
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        prof = ctx.profile_read()
+        ctx.profile_enable(False)
+        return ctx, ms, infos, prof, prof["launches"] - launches0, clocks
+
+    ctx, ms, infos, prof, launches, clocks = timed_run(params, args.warmup, args.steps, True)
+    ms_t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * args.steps / (ms_max / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    e2e = None
+    if not args.no_e2e:
+        host_in = {k: torch.empty(v.shape, dtype=torch.float64, pin_memory=True).numpy() for k, v in st0.items()}
+        host_out = {k: torch.empty(v.shape, dtype=torch.float64, pin_memory=True).numpy() for k, v in st0.items()}
+        for k, v in st0.items():
+            host_in[k][...] = v.cpu().numpy()
+        ctx.step_host(host_in, host_out)            # warm-up (allocates the staging buffers)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ctx.step_host(host_in, host_out)
+            host_in, host_out = host_out, host_in
+        t_e2e = time.perf_counter() - t0
+        t_t = torch.tensor([t_e2e], device=dev)
+        if world > 1:
+            dist.all_reduce(t_t, op=dist.ReduceOp.MAX)
+        nbytes = (9 * N1 + 2 * N2) * 8
+        e2e = {"value": world * args.e2e_steps / float(t_t.item()), "unit": "steps/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps,
+               "how": "chnss_step_host: pinned host state in, H2D copy, step, D2H copy, stream sync; wall clock"}
+    del ctx
+
+    fp64 = None
+    if not args.no_fp64:
+        p64 = dict(params, precision=0)
+        ctx64, ms64, infos64, _, _, _ = timed_run(p64, 1, args.fp64_steps, False)
+        del ctx64
+        fp64 = {"value": args.fp64_steps / (ms64 / 1e3), "unit": "steps/s", "steps": args.fp64_steps,
+                "ms_per_step": ms64 / args.fp64_steps,
+                "iters_last_step": {k: v["iters"] for k, v in infos64[-1].items()}}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel family (largest summed event time)
+    peak, peak_kind = peaks()
+    kinds = {k: v for k, v in prof["kinds"].items() if v["launches"] > 0 and v["bytes"] > 0}
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    d = kinds[dom]
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+    traffic = _traffic(dom)
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                "bytes_per_launch": d["bytes"] / d["launches"], "ms_per_launch": d["ms"] / d["launches"],
+                "launches": d["launches"], "traffic": traffic}
+    families = {k: {"ms_total": round(v["ms"], 3), "launches": v["launches"],
+                    "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 and v["bytes"] > 0 else None,
+                    "share_of_step": round(v["ms"] / ms, 4)}
+                for k, v in prof["kinds"].items() if v["launches"] > 0}
+
+    cpu = None
+    if not args.no_cpu and world == 1:
+        try:
+            smp = run_cpu_sample_subprocess(CPU_SAMPLE_N, args.workload)
+            sec = smp["seconds"][0]
+            cpu = {"value": (1.0 / sec) * nodes(CPU_SAMPLE_N) / nodes(n), "unit": "steps/s", "cores": 1,
+                   "kind": "oracle",
+                   "sample": f"one oracle step (numpy/scipy FP64, 1 thread) of the same parameter set on a "
+                             f"{CPU_SAMPLE_N}x{CPU_SAMPLE_N} mesh ({nodes(CPU_SAMPLE_N)} nodes) in {sec:.1f} s, "
+                             f"scaled by the node ratio to the {n}x{n} mesh",
+                   "cpu": cpu_model(), "host_cores": os.cpu_count(), "iters": smp["iters"]}
+        except Exception as e:  # reported, not fatal
+            cpu = {"value": None, "error": str(e)[-300:]}
+
+    last = infos[-1]
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 outer / f32 preconditioner",
+        "data": "synthetic (seeded SplitMix64 noise on phi_p, phi_NFA; paper-shaped thin film)",
+        "config": {"workload": args.workload, "n": n, "p1_nodes": N1, "p2_nodes": N2,
+                   "velocity_dofs": 2 * N2, "precision": "mixed" if params["precision"] == 1 else "fp64",
+                   "rtol": params["rtol"], "restart": params["restart"], "tau": params["tau"],
+                   "beta": params["beta"],
+                   "l2": "inputs larger than L2 (per-step working set > 10 GB)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "iters_last_step": {k: v["iters"] for k, v in last.items()},
+        "iters_mean": {k: round(sum(i[k]["iters"] for i in infos) / len(infos), 2) for k in last},
+        "converged": all(i[k]["converged"] for i in infos for k in last),
+        "fp64": fp64,
+        "speedup_mixed_vs_fp64": round(value / fp64["value"], 3) if fp64 else None,
+        "roofline": roofline,
+        "kernel_families": families,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _device_uuid(torch, idx):
+    try:
+        u = str(torch.cuda.get_device_properties(idx).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary of the kernel,
+    if one exists for the current source (profiles/traffic.json)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d.get(kernel, {}).get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2501_11767_gb300 import inputs
+    n = inputs.workload(args.workload)["n"]
+    smp = run_cpu_sample_subprocess(REF_SAMPLE_N, args.workload, steps=args.warmup + args.steps)
+    secs = smp["seconds"][args.warmup:]
+    total = sum(secs)
+    scale = nodes(REF_SAMPLE_N) / nodes(n)
+    value = len(secs) / total * scale
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n},
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each timed step is one oracle step (numpy/scipy FP64, 1 thread) on a "
+                                   f"{REF_SAMPLE_N}x{REF_SAMPLE_N} mesh of the same parameter set, scaled by the "
+                                   f"node ratio {nodes(REF_SAMPLE_N)}/{nodes(n)}",
+                         "cpu": cpu_model()},
+        "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-steps", type=int, default=1, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and not args.cpu_sample:
+        ap.error("--warmup must be >= 3")
+    if args.cpu_sample:
+        print(json.dumps(cpu_sample(args.cpu_sample, args.workload, args.cpu_steps)))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

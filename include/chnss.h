@@ -153,6 +153,25 @@ chnss_status chnss_export_csr(chnss_ctx_t ctx, int which, int *nrows, int *nnz, 
 /* Assembled right-hand side of a system (host, chnss_system_size doubles). */
 chnss_status chnss_export_rhs(chnss_ctx_t ctx, chnss_system sys, double *host_out);
 
+/* Tracing: CUDA-event durations and algorithmic bytes of the hot kernel
+ * families of one context, plus the number of kernels the library launched
+ * in this process.  Families: multigrid fine-level velocity SpMV (smoother
+ * and residual sweeps), multigrid fine-level P1 SpMV, Navier-Stokes operator
+ * SpMV, Krylov orthogonalisation (one record per Arnoldi step), assembly
+ * with preconditioner setup (bytes not counted). */
+typedef struct {
+  long long launches;          /* kernels launched by the library in this process */
+  int nkinds;
+  char name[8][32];
+  long long kind_launches[8];  /* timed launches (or Arnoldi steps) per family */
+  double kind_ms[8];           /* summed CUDA-event durations */
+  double kind_bytes[8];        /* summed algorithmic bytes */
+} chnss_profile;
+/* on != 0: reset the counters and start recording (synchronises the stream). */
+chnss_status chnss_profile_enable(chnss_ctx_t ctx, int on);
+/* Read the counters (synchronises the stream). */
+chnss_status chnss_profile_read(chnss_ctx_t ctx, chnss_profile *out);
+
 /* Message of the last failure on ctx (or of the last failed create call
  * when ctx is NULL).  Valid until the next call on the same context. */
 const char *chnss_last_error(chnss_ctx_t ctx);

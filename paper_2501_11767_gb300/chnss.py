@@ -45,6 +45,19 @@ class SolveInfo(ctypes.Structure):
                 "seconds": self.seconds}
 
 
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("nkinds", ctypes.c_int), ("name", (ctypes.c_char * 32) * 8),
+                ("kind_launches", ctypes.c_longlong * 8), ("kind_ms", ctypes.c_double * 8),
+                ("kind_bytes", ctypes.c_double * 8)]
+
+    def as_dict(self):
+        kinds = {}
+        for k in range(self.nkinds):
+            kinds[self.name[k].value.decode()] = {"launches": self.kind_launches[k], "ms": self.kind_ms[k],
+                                                  "bytes": self.kind_bytes[k]}
+        return {"launches": self.launches, "kinds": kinds}
+
+
 class ChnssError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"chnss {STATUS.get(status, status)}: {msg}")
@@ -73,6 +86,8 @@ EXPORTS = {
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p]),
     "chnss_export_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "chnss_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "chnss_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
     "chnss_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
 }
 
@@ -248,6 +263,14 @@ class Context:
         _check(lib.chnss_export_csr(self._h, which, ctypes.byref(nr), ctypes.byref(nz), rowptr.ctypes.data,
                                     col.ctypes.data, val.ctypes.data), self._h)
         return rowptr, col, val
+
+    def profile_enable(self, on: bool = True):
+        _check(load().chnss_profile_enable(self._h, 1 if on else 0), self._h)
+
+    def profile_read(self) -> dict:
+        p = Profile()
+        _check(load().chnss_profile_read(self._h, ctypes.byref(p)), self._h)
+        return p.as_dict()
 
     def export_rhs(self, sys: int):
         out = np.zeros(self.system_size(sys), dtype=np.float64)

@@ -113,6 +113,7 @@ struct chnss_ctx {
   std::unique_ptr<PrecSet<double>> p64;
   std::unique_ptr<PrecSet<float>> p32;
   KrylovWork kw;
+  Profiler prof;
   bool assembled = false;
   bool ch_done[3] = {false, false, false};
   double *hin = nullptr, *hout = nullptr;   // device staging of chnss_step_host
@@ -216,7 +217,10 @@ struct NSOp : LinearOperator {
   void apply(const double *x, double *y, cudaStream_t s) override {
     const long nv = 2L * c->N2;
     SpmvArgs none;
-    spmv_bsr2<double>(c->lv(0).p2, c->A[0], x, y, SPMV_PLAIN, none, s);
+    const Pattern &p2 = c->lv(0).p2;
+    c->prof.start(Profiler::NS_OUTER_SPMV, s);
+    spmv_bsr2<double>(p2, c->A[0], x, y, SPMV_PLAIN, none, s);
+    c->prof.stop(Profiler::NS_OUTER_SPMV, s, (double)p2.nnz * 36.0 + 4.0 * (p2.nrows + 1) + 2.0 * nv * 8.0);
     spmv_bt_add(c->mesh->m.pbt, c->Btv, x + nv, y, s);
     spmv_b(c->mesh->m.pb, c->Bv, x, y + nv, s);
   }
@@ -271,6 +275,8 @@ void init_precset(chnss_ctx *c, PrecSet<T> &P) {
   P.mx = ar.alloc<T>(N1);
   P.mt = ar.alloc<T>(N1);
   P.mb = ar.alloc<T>(N1);
+  for (MGHier<T> *h : {&P.L, &P.AC, &P.A, &P.Kp, &P.X1[0], &P.X1[1], &P.X1[2], &P.X2[0], &P.X2[1], &P.X2[2]})
+    h->prof = &c->prof;
   P.Kp.setup(c->s);
   for (int sp = 0; sp < 3; ++sp) P.X1[sp].setup(c->s);
 }
@@ -405,6 +411,7 @@ void assemble(chnss_ctx *c, const chnss_state *st) {
   const Mesh &m = c->mesh->m;
   const auto &p = c->p;
   cudaStream_t s = c->s;
+  c->prof.start(Profiler::ASSEMBLY, s);
   const int nl = c->nlev;
   // coefficients on every level by injection
   std::vector<const double *> v(nl);
@@ -488,6 +495,7 @@ void assemble(chnss_ctx *c, const chnss_state *st) {
   vec_fill(N1, 0.0, c->rhs[5] + nv, s);
   if (c->p32) setup_step_precset(c, *c->p32);
   else setup_step_precset(c, *c->p64);
+  c->prof.stop(Profiler::ASSEMBLY, s, 0.0);
   c->assembled = true;
   for (bool &d : c->ch_done) d = false;
 }
@@ -509,12 +517,12 @@ chnss_status solve(chnss_ctx *c, int sys, const double *rhs_or_null, double *x, 
   chnss_status st = CHNSS_OK;
   if (sys <= CHNSS_SYS_CH_S) {
     CHOp op(c, sys);
-    st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[sys], x, p.rtol, p.atol, p.maxit, c->kw, info, s);
+    st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[sys], x, p.rtol, p.atol, p.maxit, c->kw, info, s, &c->prof);
     if (x != c->xsol[sys]) vec_copy(2L * N1, x, c->xsol[sys], s);
     c->ch_done[sys] = true;
   } else if (sys == CHNSS_SYS_AC) {
     ACOp op(c);
-    st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[3], x, p.rtol, p.atol, p.maxit, c->kw, info, s);
+    st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[3], x, p.rtol, p.atol, p.maxit, c->kw, info, s, &c->prof);
   } else if (sys == CHNSS_SYS_MU_A) {
     const double *b = rhs_or_null;
     if (!b) {
@@ -531,7 +539,7 @@ chnss_status solve(chnss_ctx *c, int sys, const double *rhs_or_null, double *x, 
     st = pcg(c->lv(0).p1, c->M1[0], c->dinvM, b, x, 1e-12, 1000, c->kw, info, s);
   } else if (sys == CHNSS_SYS_NS) {
     NSOp op(c);
-    st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[5], x, p.rtol, p.atol, p.maxit, c->kw, info, s);
+    st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[5], x, p.rtol, p.atol, p.maxit, c->kw, info, s, &c->prof);
     // zero-mean pressure: p -= (1^T M p) / (1^T M 1)
     const long nv = 2L * c->N2;
     SpmvArgs none;
@@ -807,6 +815,33 @@ chnss_status chnss_export_rhs(chnss_ctx_t ctx, chnss_system sys, double *host_ou
   const double *src = sys == CHNSS_SYS_MU_A ? ctx->rhs[4] : ctx->rhs[sys <= 2 ? sys : (sys == 3 ? 3 : 5)];
   CHNSS_CK(cudaStreamSynchronize(ctx->s));
   CHNSS_CK(cudaMemcpy(host_out, src, n * sizeof(double), cudaMemcpyDeviceToHost));
+  return CHNSS_OK;
+  ABI_CATCH(ctx)
+}
+
+chnss_status chnss_profile_enable(chnss_ctx_t ctx, int on) {
+  if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
+  ABI_TRY
+  CHNSS_CK(cudaStreamSynchronize(ctx->s));
+  ctx->prof.reset();
+  ctx->prof.on = on != 0;
+  return CHNSS_OK;
+  ABI_CATCH(ctx)
+}
+
+chnss_status chnss_profile_read(chnss_ctx_t ctx, chnss_profile *out) {
+  if (!ctx || !out) return fail(ctx, CHNSS_ERR_ARG, "null argument");
+  ABI_TRY
+  CHNSS_CK(cudaStreamSynchronize(ctx->s));
+  std::memset(out, 0, sizeof(*out));
+  out->launches = g_launch_count.load();
+  out->nkinds = Profiler::NKINDS;
+  for (int k = 0; k < Profiler::NKINDS; ++k) {
+    std::strncpy(out->name[k], Profiler::name(k), sizeof(out->name[k]) - 1);
+    out->kind_launches[k] = ctx->prof.rec[k].launches;
+    out->kind_ms[k] = ctx->prof.elapsed_ms(k);
+    out->kind_bytes[k] = ctx->prof.rec[k].bytes;
+  }
   return CHNSS_OK;
   ABI_CATCH(ctx)
 }

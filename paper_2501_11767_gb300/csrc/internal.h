@@ -15,6 +15,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -35,7 +36,14 @@ struct Error {
       throw ::chnss::Error{CHNSS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
   } while (0)
 
-#define CHNSS_LAUNCH_CK() CHNSS_CK(cudaGetLastError())
+// kernels launched by the library in this process (gpu_launches of the bench)
+extern std::atomic<long long> g_launch_count;
+
+#define CHNSS_LAUNCH_CK()                                                \
+  do {                                                                   \
+    ::chnss::g_launch_count.fetch_add(1, std::memory_order_relaxed);     \
+    CHNSS_CK(cudaGetLastError());                                        \
+  } while (0)
 
 // Owner of device allocations; frees everything it handed out.
 struct Arena {

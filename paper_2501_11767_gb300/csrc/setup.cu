@@ -8,6 +8,9 @@
 #include "internal.h"
 
 namespace chnss {
+
+std::atomic<long long> g_launch_count{0};
+
 namespace {
 
 // Nodes of element e on an n x n level: P1 vertex ids and P2 lattice ids

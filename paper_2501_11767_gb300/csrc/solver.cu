@@ -9,6 +9,76 @@ namespace chnss {
 
 constexpr double kSmootherRatio = 4.0;   // smoothing interval [hi / 4, hi]
 
+const char *Profiler::name(int k) {
+  static const char *names[NKINDS] = {"mg_velocity_spmv_fine", "mg_p1_spmv_fine", "ns_operator_spmv",
+                                      "krylov_orthogonalisation", "assembly"};
+  return k >= 0 && k < NKINDS ? names[k] : "?";
+}
+
+void Profiler::start(int k, cudaStream_t s) {
+  if (!on) return;
+  Rec &r = rec[k];
+  if (r.used + 2 > r.ev.size()) {
+    if (r.ev.size() >= 16384) return;   // pool full: later launches are counted, not timed
+    for (int i = 0; i < 256; ++i) {
+      cudaEvent_t e;
+      CHNSS_CK(cudaEventCreate(&e));
+      r.ev.push_back(e);
+    }
+  }
+  CHNSS_CK(cudaEventRecord(r.ev[r.used], s));
+}
+
+void Profiler::stop(int k, cudaStream_t s, double bytes) {
+  if (!on) return;
+  Rec &r = rec[k];
+  if (r.used + 2 > r.ev.size()) return;
+  CHNSS_CK(cudaEventRecord(r.ev[r.used + 1], s));
+  r.used += 2;
+  r.launches += 1;
+  r.bytes += bytes;
+}
+
+void Profiler::reset() {
+  for (Rec &r : rec) {
+    r.launches = 0;
+    r.bytes = 0.0;
+    r.used = 0;
+  }
+}
+
+double Profiler::elapsed_ms(int k) {
+  Rec &r = rec[k];
+  double ms = 0.0;
+  for (size_t i = 0; i + 1 < r.used; i += 2) {
+    float t = 0.f;
+    CHNSS_CK(cudaEventElapsedTime(&t, r.ev[i], r.ev[i + 1]));
+    ms += t;
+  }
+  return ms;
+}
+
+void Profiler::release() {
+  for (Rec &r : rec) {
+    for (cudaEvent_t e : r.ev) cudaEventDestroy(e);
+    r.ev.clear();
+    r.used = 0;
+  }
+}
+
+namespace {
+// algorithmic bytes of one SpMV launch: values + column indices + row
+// pointers + one read of u, one write of out, plus the extra vector streams
+// of the epilogue (b for RES, b + dinv (+ w) for CHEB, out read for ADD)
+double spmv_bytes(long nrows, long nnz, int vals_per_entry, long vec_len, size_t s, SpmvMode mode, bool has_w) {
+  double extra = 0.0;
+  if (mode == SPMV_RES) extra = 1.0;
+  if (mode == SPMV_ADD) extra = 1.0;
+  if (mode == SPMV_CHEB) extra = has_w ? 3.0 : 2.0;
+  return (double)nnz * (vals_per_entry * (double)s + 4.0) + 4.0 * (nrows + 1) + (2.0 + extra) * vec_len * s;
+}
+}  // namespace
+
 template <typename T>
 void MGHier<T>::init(Arena &ar, int kind_, bool singular_, const std::vector<const Pattern *> &pats,
                      const std::vector<const int *> &diags, const std::vector<const double *> &vals,
@@ -75,10 +145,15 @@ void MGHier<T>::setup(cudaStream_t s) {
 
 template <typename T>
 void MGHier<T>::op(int l, const T *u, T *out, SpmvMode mode, const SpmvArgs &a, cudaStream_t s) {
+  const int k = kind == 0 ? Profiler::P1_SPMV_L0 : Profiler::VEL_SPMV_L0;
+  const bool timed = prof && l == 0;
+  if (timed) prof->start(k, s);
   if (kind == 0)
     spmv_csr<T>(*pat[l], val[l], 1, u, out, mode, a, s);
   else
     spmv_bsr2<T>(*pat[l], val[l], u, out, mode, a, s);
+  if (timed)
+    prof->stop(k, s, spmv_bytes(pat[l]->nrows, pat[l]->nnz, kind == 0 ? 1 : 4, n[l], sizeof(T), mode, a.w != nullptr));
 }
 
 template <typename T>
@@ -163,7 +238,7 @@ double read_scalar(const double *dev, double *pinned, cudaStream_t s) {
 }  // namespace
 
 chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, double atol, int maxit,
-                    KrylovWork &ws, chnss_solve_info *info, cudaStream_t s) {
+                    KrylovWork &ws, chnss_solve_info *info, cudaStream_t s, Profiler *prof) {
   const auto t0 = std::chrono::steady_clock::now();
   const long n = A.size();
   const int m = ws.m;
@@ -195,9 +270,12 @@ chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, 
         double *zj = ws.Z + (long)j * n;
         A.precond(vj, zj, s);
         A.apply(zj, ws.w, s);
+        if (prof) prof->start(Profiler::ORTHO, s);
         mdot(n, ws.V, n, j + 1, ws.w, ws.h1, ws.partial, s);
         ortho_update_mdot(n, ws.V, n, j + 1, ws.h1, ws.w, ws.h2, ws.partial, s);
         ortho_update_norm(n, ws.V, n, j + 1, ws.h2, ws.w, sc + 3, ws.partial, s);
+        // CGS2: three passes over V_0..V_j; w read 3x, written 2x
+        if (prof) prof->stop(Profiler::ORTHO, s, 8.0 * n * (3.0 * (j + 1) + 5.0));
         arnoldi_finish(j, ldh, ws.H, ws.h1, ws.h2, sc + 3, ws.cs, ws.sn, ws.g, sc + 4, s);
         CHNSS_CK(cudaMemcpyAsync(ws.hstat, sc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CHNSS_CK(cudaStreamSynchronize(s));

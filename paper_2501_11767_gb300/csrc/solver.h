@@ -6,6 +6,26 @@
 
 namespace chnss {
 
+// CUDA-event timing of the hot kernel families, with their algorithmic
+// bytes (values + indices + the vectors each launch must read or write).
+struct Profiler {
+  enum Kind { VEL_SPMV_L0 = 0, P1_SPMV_L0, NS_OUTER_SPMV, ORTHO, ASSEMBLY, NKINDS };
+  static const char *name(int k);
+  bool on = false;
+  struct Rec {
+    long long launches = 0;
+    double bytes = 0.0;
+    std::vector<cudaEvent_t> ev;   // start/stop pairs
+    size_t used = 0;
+  } rec[NKINDS];
+  void start(int k, cudaStream_t s);
+  void stop(int k, cudaStream_t s, double bytes);
+  void reset();
+  double elapsed_ms(int k);        // after a stream synchronisation
+  void release();
+  ~Profiler() { release(); }
+};
+
 // One V-cycle of geometric multigrid (the inner solves that replace the
 // paper's PyAMG blocks, Sec. 4): degree-2 Chebyshev-Jacobi pre/post
 // smoothing on [hi/4, hi] (hi: Gershgorin bound of D^-1 A), restriction
@@ -29,6 +49,7 @@ struct MGHier {
   double *dense = nullptr, *cinv = nullptr;
   int *status = nullptr;
   double *partial = nullptr, *sum = nullptr;
+  Profiler *prof = nullptr;
 
   // levels: per level pattern + FP64 value pointer (values may change
   // between setups, the pointers may not); transfers tr[l] from level l+1.
@@ -67,7 +88,7 @@ struct KrylovWork {
 // Right-preconditioned FGMRES(m), CGS2, Givens, x0 = 0; stop when the true
 // residual satisfies ||b - A x|| <= max(rtol ||b||, atol) (Sec. 5).
 chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, double atol, int maxit,
-                    KrylovWork &ws, chnss_solve_info *info, cudaStream_t s);
+                    KrylovWork &ws, chnss_solve_info *info, cudaStream_t s, Profiler *prof = nullptr);
 
 // Jacobi PCG for an SPD CSR matrix (FP64), x0 = 0, recursive residual test.
 chnss_status pcg(const Pattern &P, const double *val, const double *dinv, const double *b, double *x, double rtol,

