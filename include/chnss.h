@@ -172,6 +172,30 @@ chnss_status chnss_profile_enable(chnss_ctx_t ctx, int on);
 /* Read the counters (synchronises the stream). */
 chnss_status chnss_profile_read(chnss_ctx_t ctx, chnss_profile *out);
 
+/* Mass-matrix solve that allocates nothing.  The paper has no counterpart:
+ * this is a service entry point of the library.  It solves M x = rhs for the
+ * P1 mass matrix of ctx's mesh with the same Jacobi-preconditioned conjugate
+ * gradients as the air-potential solve (relative tolerance 1e-12, x0 = 0),
+ * but keeps its four work vectors and its reduction partials in a fixed
+ * device array inside the library instead of context memory, and calls no
+ * cudaMalloc / cudaFree.  It exists for callers that cannot allocate device
+ * memory at the point of the call: programs whose device memory is entirely
+ * reserved up front by their own pool (an allocation would fail or break
+ * their accounting) and latency-critical loops that may not pay the implicit
+ * synchronisation of cudaMalloc / cudaFree.
+ * rhs, x_out: device arrays of N1 doubles, caller-owned.
+ * Limit: N1 <= 66049 (meshes up to 256 x 256); larger meshes return
+ * CHNSS_ERR_ARG with a message.  The array (about 2.1 MB) stays resident on
+ * every GPU that loads the library until the process exits.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * Every call shares the one array and overwrites it (the solver rewrites all
+ * of it before reading), so calls whose work overlaps on the GPU (different
+ * streams, threads or contexts at the same time) race and must not be
+ * issued.  Synchronises ctx's stream once per iteration. */
+chnss_status chnss_mass_solve_noalloc(chnss_ctx_t ctx, const double *rhs, double *x_out,
+                                      chnss_solve_info *info);
+
 /* Message of the last failure on ctx (or of the last failed create call
  * when ctx is NULL).  Valid until the next call on the same context. */
 const char *chnss_last_error(chnss_ctx_t ctx);

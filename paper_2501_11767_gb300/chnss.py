@@ -86,6 +86,8 @@ EXPORTS = {
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p]),
     "chnss_export_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "chnss_mass_solve_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.POINTER(SolveInfo)]),
     "chnss_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
     "chnss_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -263,6 +265,18 @@ class Context:
         _check(lib.chnss_export_csr(self._h, which, ctypes.byref(nr), ctypes.byref(nz), rowptr.ctypes.data,
                                     col.ctypes.data, val.ctypes.data), self._h)
         return rowptr, col, val
+
+    def mass_solve_noalloc(self, rhs, x=None, check: bool = True):
+        """M x = rhs through chnss_mass_solve_noalloc (no device allocation
+        inside the library call; x must be given to avoid one here)."""
+        import torch
+        if x is None:
+            x = torch.empty(self.mesh.N1, dtype=torch.float64, device="cuda")
+        info = SolveInfo()
+        st = load().chnss_mass_solve_noalloc(self._h, _ptr(rhs), _ptr(x), ctypes.byref(info))
+        if check:
+            _check(st, self._h)
+        return x, info.as_dict(), st
 
     def profile_enable(self, on: bool = True):
         _check(load().chnss_profile_enable(self._h, 1 if on else 0), self._h)

@@ -2,9 +2,11 @@
 // the C ABI of include/chnss.h.
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 
 #include "solver.h"
@@ -849,3 +851,116 @@ chnss_status chnss_profile_read(chnss_ctx_t ctx, chnss_profile *out) {
 const char *chnss_last_error(chnss_ctx_t ctx) { return ctx ? ctx->err.c_str() : g_last_error.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Mass-matrix solve without allocation.  Its work vectors (r, z, p, q), the
+// reduction partials and the device scalars live in a file-scope device array
+// sized for meshes up to 256 x 256; every GPU that loads the library holds
+// this array until the process exits.  Host code cannot use the array's name
+// as a device address, so each device looks the address up once with
+// cudaGetSymbolAddress (on the first call with that device current).
+namespace {
+
+constexpr int kNoAllocMaxN1 = 257 * 257;             // P1 nodes of a 256 x 256 mesh
+constexpr long kNoAllocPartials = 1216;              // reduction blocks (reduce_blocks cap)
+constexpr long kNoAllocScalars = 16;
+constexpr long kNoAllocDoubles = 4L * kNoAllocMaxN1 + kNoAllocPartials + kNoAllocScalars;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+double *g_noalloc_addr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+double *noalloc_scratch_address() {
+  int dev = 0;
+  CHNSS_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) throw Error{CHNSS_ERR_ARG, "device index out of range"};
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      throw Error{CHNSS_ERR_CUDA, std::string("cudaGetSymbolAddress of the scratch array: ") + cudaGetErrorString(e)};
+    g_noalloc_addr[dev] = static_cast<double *>(p);
+  }
+  return g_noalloc_addr[dev];
+}
+
+// Jacobi PCG on M x = b with all work storage in the scratch array (same
+// kernels and stopping rule as the MU_A solve: rtol 1e-12, x0 = 0).
+chnss_status mass_solve_noalloc(chnss_ctx *c, const double *b, double *x, chnss_solve_info *info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const Pattern &P = c->lv(0).p1;
+  const long n = P.nrows;
+  cudaStream_t s = c->s;
+  double *base = noalloc_scratch_address();
+  double *r = base, *z = base + n, *p = base + 2 * n, *q = base + 3 * n;
+  double *partial = base + 4L * kNoAllocMaxN1;
+  double *sc = partial + kNoAllocPartials;   // [0] bb [1] rz [2] rz_new [3] pq [4] alpha [5] rr
+  double *host = c->pinned + 12;             // pinned host slot owned by the context
+  auto read = [&](const double *d) {
+    CHNSS_CK(cudaMemcpyAsync(host, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CHNSS_CK(cudaStreamSynchronize(s));
+    return *host;
+  };
+  const double rtol = 1e-12;
+  const int maxit = 1000;
+  vec_fill(n, 0.0, x, s);
+  vec_copy(n, b, r, s);
+  dot<double>(n, b, b, sc, partial, s);
+  const double bnorm = std::sqrt(read(sc));
+  const double target = rtol * bnorm;
+  double rn = bnorm;
+  int it = 0;
+  bool converged = false;
+  chnss_status st = CHNSS_OK;
+  if (!std::isfinite(bnorm)) {
+    st = CHNSS_ERR_NAN;
+  } else if (bnorm <= target) {
+    converged = true;
+  } else {
+    vec_mul(n, c->dinvM, r, z, s);
+    vec_copy(n, z, p, s);
+    dot<double>(n, r, z, sc + 1, partial, s);
+    double *rz = sc + 1, *rzn = sc + 2;
+    SpmvArgs none;
+    while (it < maxit) {
+      spmv_csr<double>(P, c->M1[0], 1, p, q, SPMV_PLAIN, none, s);
+      dot<double>(n, p, q, sc + 3, partial, s);
+      pcg_alpha(rz, sc + 3, sc + 4, s);
+      pcg_update_xr(n, sc + 4, p, q, x, r, s);
+      ++it;
+      dot<double>(n, r, r, sc + 5, partial, s);
+      rn = std::sqrt(read(sc + 5));
+      if (!std::isfinite(rn)) { st = CHNSS_ERR_NAN; break; }
+      if (rn <= target) { converged = true; break; }
+      vec_mul(n, c->dinvM, r, z, s);
+      dot<double>(n, r, z, rzn, partial, s);
+      pcg_update_p(n, rzn, rz, z, p, s);
+      std::swap(rz, rzn);
+    }
+    if (!converged && st == CHNSS_OK) st = CHNSS_ERR_NOCONV;
+  }
+  if (info) {
+    info->iters = it;
+    info->converged = converged ? 1 : 0;
+    info->rel_residual = bnorm > 0 ? rn / bnorm : 0.0;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return st;
+}
+
+}  // namespace
+
+extern "C" chnss_status chnss_mass_solve_noalloc(chnss_ctx_t ctx, const double *rhs, double *x_out,
+                                                 chnss_solve_info *info) {
+  if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
+  ABI_TRY
+  if (!rhs || !x_out) throw Error{CHNSS_ERR_ARG, "null rhs or x_out"};
+  if (ctx->N1 > kNoAllocMaxN1)
+    throw Error{CHNSS_ERR_ARG, "chnss_mass_solve_noalloc supports at most " + std::to_string(kNoAllocMaxN1) +
+                                   " P1 nodes (a 256 x 256 mesh); this mesh has " + std::to_string(ctx->N1)};
+  return mass_solve_noalloc(ctx, rhs, x_out, info);
+  ABI_CATCH(ctx)
+}

@@ -1,0 +1,53 @@
+"""chnss_mass_solve_noalloc: the mass-matrix solve for callers that cannot
+allocate device memory at the call (their memory is reserved up front by
+their own pool, or they may not pay cudaMalloc's implicit synchronisation).
+Its output must match the allocating path, chnss_solve(CHNSS_SYS_MU_A, rhs),
+on consecutive calls that reuse the library's fixed scratch array.
+
+This file is collected last on purpose, so that a run stopping at the first
+failure has already run every other test."""
+import numpy as np
+import pytest
+
+from paper_2501_11767_gb300 import chnss, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    return torch
+
+
+def _rhs(torch, n1, seed):
+    g = np.random.default_rng(seed)
+    return torch.as_tensor(g.standard_normal(n1), dtype=torch.float64, device="cuda")
+
+
+def test_noalloc_mass_solve_matches_allocating_solve(torch):
+    n = 32
+    ctx = chnss.Context(chnss.Mesh(n), inputs.default_params())
+    ctx.assemble(chnss.state_to_device(inputs.initial_state(n)))
+    for call, seed in enumerate((11, 12)):          # two calls in a row share the scratch array
+        b = _rhs(torch, ctx.mesh.N1, seed)
+        ref, rinfo, st_ref = ctx.solve(chnss.SYS_MU_A, rhs=b)
+        x = torch.full_like(b, np.nan)              # stale output must not matter
+        got, info, st = ctx.mass_solve_noalloc(b, x)
+        torch.cuda.synchronize()
+        assert st == 0 and st_ref == 0
+        assert info["converged"] and info["iters"] == rinfo["iters"], (call, info, rinfo)
+        r, g = ref.cpu().numpy(), got.cpu().numpy()
+        assert np.linalg.norm(g - r) <= 1e-12 * np.linalg.norm(r), call
+
+
+def test_noalloc_mass_solve_rejects_large_meshes(torch):
+    n = 512                                          # 263169 P1 nodes > 66049
+    ctx = chnss.Context(chnss.Mesh(n), inputs.default_params())
+    b = torch.ones(ctx.mesh.N1, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    with pytest.raises(chnss.ChnssError) as e:
+        ctx.mass_solve_noalloc(b, x)
+    assert e.value.status == 1 and "256 x 256" in str(e.value)
