@@ -107,6 +107,9 @@ struct chnss_ctx {
   std::vector<std::array<double *, 3>> X1, X2;
   std::vector<double *> vl, mul, phil;
   double *Apb = nullptr, *Ap = nullptr, *Bv = nullptr, *Btv = nullptr, *dinvM = nullptr;
+  // SELL-ordered copies of the fine FP64 operators applied inside FGMRES
+  double *Ls = nullptr, *ACs = nullptr, *As = nullptr, *Ks = nullptr, *Ms = nullptr, *Bs = nullptr, *Bts = nullptr;
+  double *Kks[3] = {nullptr, nullptr, nullptr};
   double *Kk[3] = {nullptr, nullptr, nullptr};
   double *loads = nullptr, *G = nullptr, *fa = nullptr, *tmp = nullptr, *sum = nullptr, *partial = nullptr;
   double *rhs[6] = {};
@@ -139,7 +142,7 @@ void ch_precond(chnss_ctx *c, PrecSet<T> &P, int sp, const double *r, double *z)
   vec_convert<double, T>(N1, r + N1, X1.input(), s);
   X1.apply(s);
   SpmvArgs none;
-  spmv_csr<T>(c->lv(0).p1, P.Mv, 1, X1.output(), X2.input(), SPMV_PLAIN, none, s);
+  spmv_sell<T>(c->lv(0).p1, P.Mv, 1, X1.output(), X2.input(), SPMV_PLAIN, none, s);
   X2.apply(s);
   vec_convert<T, double>(N1, X2.output(), z + N1, s);
 }
@@ -164,7 +167,7 @@ void ns_precond(chnss_ctx *c, PrecSet<T> &P, const double *r, double *z) {
   P.Kp.apply(s);
   SpmvArgs none;
   const Pattern &p1 = c->lv(0).p1;
-  spmv_csr<T>(p1, P.Apv, 1, P.Kp.output(), P.mb, SPMV_PLAIN, none, s);
+  spmv_sell<T>(p1, P.Apv, 1, P.Kp.output(), P.mb, SPMV_PLAIN, none, s);
   // M_p^-1 by Chebyshev iteration of degree 5 on D^-1 M, spectrum [1/2, 2]
   vec_scale_dinv<T>(N1, c->massc, P.mdinv, P.mb, P.mx, s);
   SpmvArgs a;
@@ -174,7 +177,7 @@ void ns_precond(chnss_ctx *c, PrecSet<T> &P, const double *r, double *z) {
   for (int k = 1; k <= 4; ++k) {
     a.coef = c->massc + 1 + 3 * (k - 1);
     a.w = k == 1 ? nullptr : other;
-    spmv_csr<T>(p1, P.Mv, 1, cur, other, SPMV_CHEB, a, s);
+    spmv_sell<T>(p1, P.Mv, 1, cur, other, SPMV_CHEB, a, s);
     std::swap(cur, other);
   }
   vec_convert<T, double>(N1, cur, z + nv, s);
@@ -189,7 +192,7 @@ struct CHOp : LinearOperator {
     const auto &p = c->p;
     const double tau = p.tau, g = p.gamma[sp], b = p.beta[sp];
     const bool var = p.mobility_kind != 0;
-    spmv_ch(c->lv(0).p1, c->L[0], c->K1[0], var ? c->Kk[sp] : nullptr, c->M1[0], var ? tau : tau * g, tau * g,
+    spmv_sell_ch(c->lv(0).p1, c->Ls, c->Ks, var ? c->Kks[sp] : nullptr, c->Ms, var ? tau : tau * g, tau * g,
             -tau * g / b, x, y, s);
   }
   void precond(const double *r, double *z, cudaStream_t) override {
@@ -204,7 +207,7 @@ struct ACOp : LinearOperator {
   long size() const override { return c->N1; }
   void apply(const double *x, double *y, cudaStream_t s) override {
     SpmvArgs none;
-    spmv_csr<double>(c->lv(0).p1, c->AC[0], 1, x, y, SPMV_PLAIN, none, s);
+    spmv_sell<double>(c->lv(0).p1, c->ACs, 1, x, y, SPMV_PLAIN, none, s);
   }
   void precond(const double *r, double *z, cudaStream_t) override {
     if (c->p32) ac_precond(c, *c->p32, r, z);
@@ -221,10 +224,10 @@ struct NSOp : LinearOperator {
     SpmvArgs none;
     const Pattern &p2 = c->lv(0).p2;
     c->prof.start(Profiler::NS_OUTER_SPMV, s);
-    spmv_bsr2<double>(p2, c->A[0], x, y, SPMV_PLAIN, none, s);
+    spmv_sell_bsr2<double>(p2, c->As, x, y, SPMV_PLAIN, none, s);
     c->prof.stop(Profiler::NS_OUTER_SPMV, s, (double)p2.nnz * 36.0 + 4.0 * (p2.nrows + 1) + 2.0 * nv * 8.0);
-    spmv_bt_add(c->mesh->m.pbt, c->Btv, x + nv, y, s);
-    spmv_b(c->mesh->m.pb, c->Bv, x, y + nv, s);
+    spmv_sell_bt_add(c->mesh->m.pbt, c->Bts, x + nv, y, s);
+    spmv_sell_b(c->mesh->m.pb, c->Bs, x, y + nv, s);
   }
   void precond(const double *r, double *z, cudaStream_t) override {
     if (c->p32) ns_precond(c, *c->p32, r, z);
@@ -263,15 +266,14 @@ void init_precset(chnss_ctx *c, PrecSet<T> &P) {
     if (c->p.mobility_kind != 0) P.X2[sp].init(ar, 0, false, p1s, d1s, x2, t1s, c->partial);
   }
   const int N1 = c->N1, nnz1 = c->lv(0).p1.nnz;
+  const long nent1 = c->lv(0).p1.sell.nent;
+  P.Mv = ar.alloc<T>(nent1);
+  P.Apv = ar.alloc<T>(nent1);
+  sell_gather<T>(c->lv(0).p1.sell, 1, c->M1[0], P.Mv, c->s);
   if (std::is_same<T, double>::value) {
-    P.Mv = reinterpret_cast<T *>(c->M1[0]);
-    P.Apv = reinterpret_cast<T *>(c->Ap);
     P.mdinv = reinterpret_cast<T *>(c->dinvM);
   } else {
-    P.Mv = ar.alloc<T>(nnz1);
-    P.Apv = ar.alloc<T>(nnz1);
     P.mdinv = ar.alloc<T>(N1);
-    vec_convert<double, T>(nnz1, c->M1[0], P.Mv, c->s);
     vec_convert<double, T>(N1, c->dinvM, P.mdinv, c->s);
   }
   P.mx = ar.alloc<T>(N1);
@@ -290,7 +292,7 @@ void setup_step_precset(chnss_ctx *c, PrecSet<T> &P) {
   P.A.setup(c->s);
   if (c->p.mobility_kind != 0)
     for (int sp = 0; sp < 3; ++sp) P.X2[sp].setup(c->s);
-  if (!std::is_same<T, double>::value) vec_convert<double, T>(c->lv(0).p1.nnz, c->Ap, P.Apv, c->s);
+  sell_gather<T>(c->lv(0).p1.sell, 1, c->Ap, P.Apv, c->s);
 }
 
 void create_context(chnss_ctx *c) {
@@ -363,11 +365,26 @@ void create_context(chnss_ctx *c) {
   c->Btv = ar.alloc<double>(2L * m.pbt.nnz);
   launch_gather(m.g_b, 2, c->ebuf, 1.0, nullptr, 0.0, c->Bv, s);
   launch_gather(m.g_bt, 2, c->ebuf, 1.0, nullptr, 0.0, c->Btv, s);
+  c->Bs = ar.alloc<double>(2L * m.pb.sell.nent);
+  c->Bts = ar.alloc<double>(2L * m.pbt.sell.nent);
+  sell_gather<double>(m.pb.sell, 2, c->Bv, c->Bs, s);
+  sell_gather<double>(m.pbt.sell, 2, c->Btv, c->Bts, s);
+  const long nent1 = F.p1.sell.nent;
+  c->Ls = ar.alloc<double>(nent1);
+  c->ACs = ar.alloc<double>(nent1);
+  c->Ks = ar.alloc<double>(nent1);
+  c->Ms = ar.alloc<double>(nent1);
+  c->As = ar.alloc<double>(4L * F.p2.sell.nent);
+  sell_gather<double>(F.p1.sell, 1, c->K1[0], c->Ks, s);
+  sell_gather<double>(F.p1.sell, 1, c->M1[0], c->Ms, s);
   c->dinvM = ar.alloc<double>(c->N1);
   k_inv_diag<<<nb(c->N1), TPB, 0, s>>>(c->N1, c->M1[0], F.diag1, c->dinvM);
   CHNSS_LAUNCH_CK();
   if (p.mobility_kind != 0)
-    for (int sp = 0; sp < 3; ++sp) c->Kk[sp] = ar.alloc<double>(nnz1);
+    for (int sp = 0; sp < 3; ++sp) {
+      c->Kk[sp] = ar.alloc<double>(nnz1);
+      c->Kks[sp] = ar.alloc<double>(nent1);
+    }
   c->loads = ar.alloc<double>(5L * c->N1);
   c->G = ar.alloc<double>(2L * c->N2);
   c->fa = ar.alloc<double>(c->N1);
@@ -495,6 +512,12 @@ void assemble(chnss_ctx *c, const chnss_state *st) {
   spmv_csr<double>(F.p2, c->M2v[0], 2, st->v, c->rhs[5], SPMV_PLAIN, none, s);
   vec_axpby(nv, 1.0, c->G, 1.0 / p.tau, c->rhs[5], s);
   vec_fill(N1, 0.0, c->rhs[5] + nv, s);
+  // SELL copies of the fine operators applied by FGMRES
+  sell_gather<double>(F.p1.sell, 1, c->L[0], c->Ls, s);
+  sell_gather<double>(F.p1.sell, 1, c->AC[0], c->ACs, s);
+  sell_gather<double>(F.p2.sell, 4, c->A[0], c->As, s);
+  if (p.mobility_kind != 0)
+    for (int sp = 0; sp < 3; ++sp) sell_gather<double>(F.p1.sell, 1, c->Kk[sp], c->Kks[sp], s);
   if (c->p32) setup_step_precset(c, *c->p32);
   else setup_step_precset(c, *c->p64);
   c->prof.stop(Profiler::ASSEMBLY, s, 0.0);

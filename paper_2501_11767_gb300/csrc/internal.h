@@ -77,11 +77,28 @@ struct Arena {
   ~Arena() { release(); }
 };
 
+// SELL-C-sigma view of a CSR pattern (C = 32): rows are sorted by length
+// (descending) inside windows of sigma rows and cut into slices of 32; a
+// slice stores its entries column-major (entry j of the 32 rows is
+// contiguous), padded to the slice's longest row.  One thread per row, every
+// value / column load is one coalesced warp access.
+struct Sell {
+  static constexpr int C = 32;
+  static constexpr int SIGMA = 256;
+  int nslices = 0;
+  long nent = 0;                 // padded entries
+  int *slice_ptr = nullptr;      // [nslices + 1] first entry of each slice
+  int *rowid = nullptr;          // [nslices * 32] CSR row of each slot, -1 = padding
+  int *col = nullptr;            // [nent] column (padding: a valid column, value 0)
+  int *map = nullptr;            // [nent] CSR position, -1 = padding
+};
+
 struct Pattern {
   int nrows = 0, ncols = 0;
   int nnz = 0;
   int *rowptr = nullptr, *col = nullptr;  // device
   std::vector<int> h_rowptr, h_col;       // host copies
+  Sell sell;
 };
 
 // out entry k sums buf[idx[j] + c] for j in [ptr[k], ptr[k+1]), c < ncomp.
@@ -93,8 +110,9 @@ struct Gather {
 
 struct Transfer {               // prolongation P (fine x coarse) and R = P^T
   Pattern P, R;
-  double *Pv = nullptr, *Rv = nullptr;
-  float *Pv32 = nullptr, *Rv32 = nullptr;
+  double *Pv = nullptr, *Rv = nullptr;          // CSR order
+  double *Ps = nullptr, *Rs = nullptr;          // SELL order
+  float *Ps32 = nullptr, *Rs32 = nullptr;       // SELL order, FP32
 };
 
 struct Level {

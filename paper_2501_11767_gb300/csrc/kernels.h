@@ -29,6 +29,21 @@ template <typename T>
 void spmv_bsr2(const Pattern &P, const T *val, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
                cudaStream_t s);
 
+// SELL-C-sigma variants (see Sell in internal.h).  Values in SELL order:
+// ncomp (1, 2 or 4) values per entry, out[e * ncomp + c].
+template <typename Tout>
+void sell_gather(const Sell &S, int ncomp, const double *csr_vals, Tout *out, cudaStream_t s);
+template <typename T>
+void spmv_sell(const Pattern &P, const T *sval, int ncomp, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
+               cudaStream_t s);
+template <typename T>
+void spmv_sell_bsr2(const Pattern &P, const T *sval, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
+                    cudaStream_t s);
+void spmv_sell_ch(const Pattern &P, const double *L, const double *K, const double *k12, const double *M, double a12,
+                  double a21, double a22, const double *x, double *y, cudaStream_t s);
+void spmv_sell_b(const Pattern &P, const double *sval2, const double *v, double *y, cudaStream_t s);
+void spmv_sell_bt_add(const Pattern &P, const double *sval2, const double *p, double *yv, cudaStream_t s);
+
 // CH operator: y1 = L x1 + a12 K12 x2, y2 = a21 K x1 + a22 M x2 on the P1
 // pattern (K12 = K when k12 == nullptr).
 void spmv_ch(const Pattern &P, const double *L, const double *K, const double *k12, const double *M, double a12,

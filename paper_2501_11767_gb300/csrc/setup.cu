@@ -119,9 +119,64 @@ void node_gather(int nnodes, int E, int nl, NodeFn nodes, OffFn off, KeepFn keep
   G.ncontrib = (int)hidx.size();
 }
 
-void upload_pattern(Arena &ar, Pattern &P) {
+// SELL-C-sigma view of P (see internal.h); also returns the host map from
+// SELL entries to CSR positions when hmap is given.
+void build_sell(Arena &ar, Pattern &P, std::vector<int> *hmap = nullptr) {
+  const int C = Sell::C, S = Sell::SIGMA, n = P.nrows;
+  std::vector<int> perm(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  auto len = [&](int r) { return P.h_rowptr[r + 1] - P.h_rowptr[r]; };
+  for (int w0 = 0; w0 < n; w0 += S) {
+    const int w1 = std::min(n, w0 + S);
+    std::stable_sort(perm.begin() + w0, perm.begin() + w1, [&](int a, int b) { return len(a) > len(b); });
+  }
+  Sell &s = P.sell;
+  s.nslices = (n + C - 1) / C;
+  std::vector<int> sp(s.nslices + 1, 0), rowid((size_t)s.nslices * C, -1);
+  for (int k = 0; k < s.nslices; ++k) {
+    int w = 0;
+    for (int r = 0; r < C; ++r) {
+      const int i = k * C + r;
+      if (i < n) {
+        rowid[i] = perm[i];
+        w = std::max(w, len(perm[i]));
+      }
+    }
+    sp[k + 1] = sp[k] + w * C;
+  }
+  s.nent = sp[s.nslices];
+  std::vector<int> col(s.nent), map(s.nent);
+  for (int k = 0; k < s.nslices; ++k) {
+    const int w = (sp[k + 1] - sp[k]) / C;
+    for (int r = 0; r < C; ++r) {
+      const int row = rowid[(size_t)k * C + r];
+      const int l = row >= 0 ? len(row) : 0;
+      int last = row >= 0 && l > 0 ? P.h_col[P.h_rowptr[row]] : 0;
+      for (int j = 0; j < w; ++j) {
+        const long e = sp[k] + (long)j * C + r;
+        if (j < l) {
+          const int q = P.h_rowptr[row] + j;
+          col[e] = P.h_col[q];
+          map[e] = q;
+          last = col[e];
+        } else {
+          col[e] = last;   // padding: a column this row already touches, value 0
+          map[e] = -1;
+        }
+      }
+    }
+  }
+  s.slice_ptr = ar.upload(sp);
+  s.rowid = ar.upload(rowid);
+  s.col = ar.upload(col);
+  s.map = ar.upload(map);
+  if (hmap) *hmap = std::move(map);
+}
+
+void upload_pattern(Arena &ar, Pattern &P, std::vector<int> *hmap = nullptr) {
   P.rowptr = ar.upload(P.h_rowptr);
   P.col = ar.upload(P.h_col);
+  build_sell(ar, P, hmap);
 }
 
 void upload_gather(Arena &ar, Gather &G, const std::vector<int> &ptr, const std::vector<int> &idx) {
@@ -150,13 +205,21 @@ void transpose(const Pattern &A, const std::vector<double> &av, Pattern &T, std:
 void finish_transfer(Arena &ar, Transfer &t, const std::vector<double> &pv) {
   std::vector<double> rv;
   transpose(t.P, pv, t.R, rv);
-  upload_pattern(ar, t.P);
-  upload_pattern(ar, t.R);
+  std::vector<int> pmap, rmap;
+  upload_pattern(ar, t.P, &pmap);
+  upload_pattern(ar, t.R, &rmap);
   t.Pv = ar.upload(pv);
   t.Rv = ar.upload(rv);
-  std::vector<float> p32(pv.begin(), pv.end()), r32(rv.begin(), rv.end());
-  t.Pv32 = ar.upload(p32);
-  t.Rv32 = ar.upload(r32);
+  auto sell_vals = [](const std::vector<int> &map, const std::vector<double> &v) {
+    std::vector<double> out(map.size());
+    for (size_t e = 0; e < map.size(); ++e) out[e] = map[e] >= 0 ? v[map[e]] : 0.0;
+    return out;
+  };
+  const std::vector<double> ps = sell_vals(pmap, pv), rs = sell_vals(rmap, rv);
+  t.Ps = ar.upload(ps);
+  t.Rs = ar.upload(rs);
+  t.Ps32 = ar.upload(std::vector<float>(ps.begin(), ps.end()));
+  t.Rs32 = ar.upload(std::vector<float>(rs.begin(), rs.end()));
 }
 
 // Linear interpolation of coarse P1 functions at the fine P1 nodes.

@@ -102,11 +102,7 @@ void MGHier<T>::init(Arena &ar, int kind_, bool singular_, const std::vector<con
   for (int l = 0; l < nl; ++l) {
     const long nu = (kind == 0 ? 1L : 2L) * pat[l]->nrows;
     n[l] = nu;
-    const long nv = (kind == 0 ? 1L : 4L) * pat[l]->nnz;
-    if (std::is_same<T, double>::value)
-      val[l] = reinterpret_cast<T *>(const_cast<double *>(vals[l]));
-    else
-      val[l] = ar.alloc<T>(nv);
+    val[l] = ar.alloc<T>((kind == 0 ? 1L : 4L) * pat[l]->sell.nent);   // SELL order
     dinv[l] = ar.alloc<T>(nu);
     x[l] = ar.alloc<T>(nu);
     t[l] = ar.alloc<T>(nu);
@@ -126,8 +122,7 @@ void MGHier<T>::init(Arena &ar, int kind_, bool singular_, const std::vector<con
 template <typename T>
 void MGHier<T>::setup(cudaStream_t s) {
   for (int l = 0; l < nl; ++l) {
-    const long nv = (kind == 0 ? 1L : 4L) * pat[l]->nnz;
-    if (!std::is_same<T, double>::value) vec_convert<double, T>(nv, val64[l], val[l], s);
+    sell_gather<T>(pat[l]->sell, kind == 0 ? 1 : 4, val64[l], val[l], s);
     if (l == nl - 1) break;
     if (kind == 0)
       jacobi_csr<T>(*pat[l], val64[l], diag[l], dinv[l], hi[l], partial, s);
@@ -149,17 +144,17 @@ void MGHier<T>::op(int l, const T *u, T *out, SpmvMode mode, const SpmvArgs &a, 
   const bool timed = prof && l == 0;
   if (timed) prof->start(k, s);
   if (kind == 0)
-    spmv_csr<T>(*pat[l], val[l], 1, u, out, mode, a, s);
+    spmv_sell<T>(*pat[l], val[l], 1, u, out, mode, a, s);
   else
-    spmv_bsr2<T>(*pat[l], val[l], u, out, mode, a, s);
+    spmv_sell_bsr2<T>(*pat[l], val[l], u, out, mode, a, s);
   if (timed)
     prof->stop(k, s, spmv_bytes(pat[l]->nrows, pat[l]->nnz, kind == 0 ? 1 : 4, n[l], sizeof(T), mode, a.w != nullptr));
 }
 
 template <typename T>
 static inline const T *transfer_vals(const Transfer &t, bool restrict_) {
-  if (std::is_same<T, double>::value) return reinterpret_cast<const T *>(restrict_ ? t.Rv : t.Pv);
-  return reinterpret_cast<const T *>(restrict_ ? t.Rv32 : t.Pv32);
+  if (std::is_same<T, double>::value) return reinterpret_cast<const T *>(restrict_ ? t.Rs : t.Ps);
+  return reinterpret_cast<const T *>(restrict_ ? t.Rs32 : t.Ps32);
 }
 
 template <typename T>
@@ -182,9 +177,9 @@ void MGHier<T>::vcycle(int l, cudaStream_t s) {
   op(l, x[l], r[l], SPMV_RES, ar, s);
   const Transfer &T_ = *tr[l];
   SpmvArgs none;
-  spmv_csr<T>(T_.R, transfer_vals<T>(T_, true), nc_, r[l], b[l + 1], SPMV_PLAIN, none, s);
+  spmv_sell<T>(T_.R, transfer_vals<T>(T_, true), nc_, r[l], b[l + 1], SPMV_PLAIN, none, s);
   vcycle(l + 1, s);
-  spmv_csr<T>(T_.P, transfer_vals<T>(T_, false), nc_, x[l + 1], x[l], SPMV_ADD, none, s);
+  spmv_sell<T>(T_.P, transfer_vals<T>(T_, false), nc_, x[l + 1], x[l], SPMV_ADD, none, s);
   // post-smoothing
   a.coef = coef[l] + 4;
   a.w = nullptr;
@@ -214,8 +209,9 @@ template struct MGHier<float>;
 void KrylovWork::init(Arena &ar, int m_, long nmax_, double *pinned) {
   m = m_;
   nmax = nmax_;
-  V = ar.alloc<double>((long)(m + 1) * nmax);
-  Z = ar.alloc<double>((long)m * nmax);
+  const long ldmax = (nmax + 31) / 32 * 32;   // basis stride: 256-byte aligned vectors
+  V = ar.alloc<double>((long)(m + 1) * ldmax);
+  Z = ar.alloc<double>((long)m * ldmax);
   w = ar.alloc<double>(nmax);
   H = ar.alloc<double>((long)(m + 1) * m);
   cs = ar.alloc<double>(m);
@@ -241,6 +237,7 @@ chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, 
                     KrylovWork &ws, chnss_solve_info *info, cudaStream_t s, Profiler *prof) {
   const auto t0 = std::chrono::steady_clock::now();
   const long n = A.size();
+  const long ld = (n + 31) / 32 * 32;   // basis stride (keeps every V_j, Z_j 256-byte aligned)
   const int m = ws.m;
   const int ldh = m + 1;
   double *sc = ws.sc;   // [0] ||b||^2, [1] ||r||^2
@@ -266,14 +263,14 @@ chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, 
       int k = 0;
       bool breakdown = false;
       for (int j = 0; j < m; ++j) {
-        double *vj = ws.V + (long)j * n;
-        double *zj = ws.Z + (long)j * n;
+        double *vj = ws.V + (long)j * ld;
+        double *zj = ws.Z + (long)j * ld;
         A.precond(vj, zj, s);
         A.apply(zj, ws.w, s);
         if (prof) prof->start(Profiler::ORTHO, s);
-        mdot(n, ws.V, n, j + 1, ws.w, ws.h1, ws.partial, s);
-        ortho_update_mdot(n, ws.V, n, j + 1, ws.h1, ws.w, ws.h2, ws.partial, s);
-        ortho_update_norm(n, ws.V, n, j + 1, ws.h2, ws.w, sc + 3, ws.partial, s);
+        mdot(n, ws.V, ld, j + 1, ws.w, ws.h1, ws.partial, s);
+        ortho_update_mdot(n, ws.V, ld, j + 1, ws.h1, ws.w, ws.h2, ws.partial, s);
+        ortho_update_norm(n, ws.V, ld, j + 1, ws.h2, ws.w, sc + 3, ws.partial, s);
         // CGS2: three passes over V_0..V_j; w read 3x, written 2x
         if (prof) prof->stop(Profiler::ORTHO, s, 8.0 * n * (3.0 * (j + 1) + 5.0));
         arnoldi_finish(j, ldh, ws.H, ws.h1, ws.h2, sc + 3, ws.cs, ws.sn, ws.g, sc + 4, s);
@@ -287,12 +284,12 @@ chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, 
           break;
         }
         breakdown = hn == 0.0;
-        if (!breakdown) vec_scale_by_inv(n, ws.w, sc + 5, ws.V + (long)(j + 1) * n, s);
+        if (!breakdown) vec_scale_by_inv(n, ws.w, sc + 5, ws.V + (long)(j + 1) * ld, s);
         if (est <= target || iters >= maxit || breakdown) break;
       }
       if (st != CHNSS_OK) break;
       hessenberg_solve(k, ldh, ws.H, ws.g, ws.y, s);
-      combine_columns(n, ws.Z, n, k, ws.y, x, s);
+      combine_columns(n, ws.Z, ld, k, ws.y, x, s);
       A.apply(x, ws.w, s);
       vec_axpby(n, 1.0, b, -1.0, ws.w, s);                 // w = b - A x
       dot<double>(n, ws.w, ws.w, sc + 1, ws.partial, s);

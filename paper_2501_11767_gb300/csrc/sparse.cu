@@ -169,6 +169,179 @@ __global__ void __launch_bounds__(TPB) k_spmv_bt_add(int nrows, const int *__res
 }
 
 // --------------------------------------------------------------------------
+// SELL-C-sigma kernels: one warp per slice of 32 rows, one thread per row,
+// entry j of the slice's rows is contiguous, so every value and column load
+// is one coalesced warp access and a thread's loads are independent.
+template <typename T> struct V2t;
+template <> struct V2t<float> { using type = float2; };
+template <> struct V2t<double> { using type = double2; };
+
+__device__ __forceinline__ void load_blk(const float *p, float b[4]) {
+  const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+  b[0] = v.x; b[1] = v.y; b[2] = v.z; b[3] = v.w;
+}
+__device__ __forceinline__ void load_blk(const double *p, double b[4]) {
+  const double2 v0 = __ldg(reinterpret_cast<const double2 *>(p));
+  const double2 v1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+  b[0] = v0.x; b[1] = v0.y; b[2] = v1.x; b[3] = v1.y;
+}
+
+template <typename T>
+__global__ void k_sell_gather(long nent, int ncomp, const int *__restrict__ map, const double *__restrict__ csr,
+                              T *__restrict__ out) {
+  const long e = (long)blockIdx.x * TPB + threadIdx.x;
+  if (e >= nent) return;
+  const int q = map[e];
+  for (int c = 0; c < ncomp; ++c) out[e * ncomp + c] = q >= 0 ? (T)csr[(long)q * ncomp + c] : (T)0;
+}
+
+template <typename T, int NC, bool VEC>
+__global__ void __launch_bounds__(TPB) k_sell(int nslices, const int *__restrict__ sp, const int *__restrict__ rowid,
+                                              const int *__restrict__ col, const T *__restrict__ val,
+                                              const T *__restrict__ u, T *out, int mode, SpmvArgs a) {
+  const int slice = (blockIdx.x * TPB + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (slice >= nslices) return;
+  const int row = rowid[slice * 32 + lane];
+  const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
+  const int *cp = col + b0 + lane;
+  const T *vp = val + b0 + lane;
+  T acc0 = 0, acc1 = 0;
+#pragma unroll 4
+  for (int j = 0; j < w; ++j) {
+    const int c = cp[j * 32];
+    const T v = vp[j * 32];
+    if (NC == 1) {
+      acc0 += v * u[c];
+    } else if (VEC) {
+      const typename V2t<T>::type x = reinterpret_cast<const typename V2t<T>::type *>(u)[c];
+      acc0 += v * x.x;
+      acc1 += v * x.y;
+    } else {
+      acc0 += v * u[2L * c];
+      acc1 += v * u[2L * c + 1];
+    }
+  }
+  if (row < 0) return;
+  if (NC == 1) {
+    epilogue<T>(mode, row, acc0, u, out, a, a.coef);
+  } else {
+    epilogue<T>(mode, 2L * row, acc0, u, out, a, a.coef);
+    epilogue<T>(mode, 2L * row + 1, acc1, u, out, a, a.coef);
+  }
+}
+
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(TPB) k_sell_bsr2(int nslices, const int *__restrict__ sp,
+                                                   const int *__restrict__ rowid, const int *__restrict__ col,
+                                                   const T *__restrict__ val, const T *__restrict__ u, T *out,
+                                                   int mode, SpmvArgs a) {
+  const int slice = (blockIdx.x * TPB + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (slice >= nslices) return;
+  const int row = rowid[slice * 32 + lane];
+  const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
+  const typename V2t<T>::type *u2 = reinterpret_cast<const typename V2t<T>::type *>(u);
+  T acc0 = 0, acc1 = 0;
+#pragma unroll 4
+  for (int j = 0; j < w; ++j) {
+    const long e = b0 + (long)j * 32 + lane;
+    const int c = col[e];
+    T b[4];
+    load_blk(val + 4 * e, b);
+    T x0, x1;
+    if (VEC) {
+      const typename V2t<T>::type x = u2[c];
+      x0 = x.x;
+      x1 = x.y;
+    } else {
+      x0 = u[2L * c];
+      x1 = u[2L * c + 1];
+    }
+    acc0 += b[0] * x0 + b[1] * x1;
+    acc1 += b[2] * x0 + b[3] * x1;
+  }
+  if (row < 0) return;
+  epilogue<T>(mode, 2L * row, acc0, u, out, a, a.coef);
+  epilogue<T>(mode, 2L * row + 1, acc1, u, out, a, a.coef);
+}
+
+__global__ void __launch_bounds__(TPB) k_sell_ch(int nslices, int nrows, const int *__restrict__ sp,
+                                                 const int *__restrict__ rowid, const int *__restrict__ col,
+                                                 const double *__restrict__ L, const double *__restrict__ K,
+                                                 const double *__restrict__ K12, const double *__restrict__ M,
+                                                 double a12, double a21, double a22, const double *__restrict__ x,
+                                                 double *__restrict__ y) {
+  const int slice = (blockIdx.x * TPB + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (slice >= nslices) return;
+  const int row = rowid[slice * 32 + lane];
+  const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
+  const double *x1 = x, *x2 = x + nrows;
+  double s11 = 0, s12 = 0, s21 = 0, s22 = 0;
+#pragma unroll 4
+  for (int j = 0; j < w; ++j) {
+    const int e = b0 + j * 32 + lane;
+    const int c = col[e];
+    const double u1 = x1[c], u2 = x2[c], kv = K[e];
+    s11 += L[e] * u1;
+    s12 += (K12 ? K12[e] : kv) * u2;
+    s21 += kv * u1;
+    s22 += M[e] * u2;
+  }
+  if (row < 0) return;
+  y[row] = s11 + a12 * s12;
+  y[nrows + row] = a21 * s21 + a22 * s22;
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(TPB) k_sell_b(int nslices, const int *__restrict__ sp, const int *__restrict__ rowid,
+                                                const int *__restrict__ col, const double *__restrict__ val2,
+                                                const double *__restrict__ v, double *__restrict__ y) {
+  const int slice = (blockIdx.x * TPB + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (slice >= nslices) return;
+  const int row = rowid[slice * 32 + lane];
+  const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
+  const double2 *v2 = reinterpret_cast<const double2 *>(v);
+  const double2 *w2 = reinterpret_cast<const double2 *>(val2);
+  double acc = 0;
+#pragma unroll 4
+  for (int j = 0; j < w; ++j) {
+    const int e = b0 + j * 32 + lane;
+    const double2 b = __ldg(w2 + e);
+    const int c = col[e];
+    if (VEC) {
+      const double2 x = v2[c];
+      acc += b.x * x.x + b.y * x.y;
+    } else {
+      acc += b.x * v[2L * c] + b.y * v[2L * c + 1];
+    }
+  }
+  if (row >= 0) y[row] = acc;
+}
+
+__global__ void __launch_bounds__(TPB) k_sell_bt_add(int nslices, const int *__restrict__ sp,
+                                                     const int *__restrict__ rowid, const int *__restrict__ col,
+                                                     const double *__restrict__ val2, const double *__restrict__ p,
+                                                     double *__restrict__ yv) {
+  const int slice = (blockIdx.x * TPB + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (slice >= nslices) return;
+  const int row = rowid[slice * 32 + lane];
+  const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
+  const double2 *w2 = reinterpret_cast<const double2 *>(val2);
+  double a0 = 0, a1 = 0;
+#pragma unroll 4
+  for (int j = 0; j < w; ++j) {
+    const int e = b0 + j * 32 + lane;
+    const double2 b = __ldg(w2 + e);
+    const double q = p[col[e]];
+    a0 += b.x * q;
+    a1 += b.y * q;
+  }
+  if (row >= 0) {
+    yv[2L * row] += a0;
+    yv[2L * row + 1] += a1;
+  }
+}
+
+// --------------------------------------------------------------------------
 // Jacobi / Gershgorin
 template <typename T>
 __global__ void k_jacobi_csr(int nrows, const int *__restrict__ rowptr, const double *__restrict__ val,
@@ -559,6 +732,78 @@ template void spmv_bsr2<double>(const Pattern &, const double *, const double *,
                                 const SpmvArgs &, cudaStream_t);
 template void spmv_bsr2<float>(const Pattern &, const float *, const float *, float *, SpmvMode,
                                const SpmvArgs &, cudaStream_t);
+
+inline bool aligned(const void *p, size_t bytes) { return (reinterpret_cast<uintptr_t>(p) % bytes) == 0; }
+
+template <typename Tout>
+void sell_gather(const Sell &S, int ncomp, const double *csr_vals, Tout *out, cudaStream_t s) {
+  if (S.nent == 0) return;
+  k_sell_gather<Tout><<<nblocks(S.nent, TPB), TPB, 0, s>>>(S.nent, ncomp, S.map, csr_vals, out);
+  CHNSS_LAUNCH_CK();
+}
+template void sell_gather<double>(const Sell &, int, const double *, double *, cudaStream_t);
+template void sell_gather<float>(const Sell &, int, const double *, float *, cudaStream_t);
+
+template <typename T>
+void spmv_sell(const Pattern &P, const T *sval, int ncomp, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
+               cudaStream_t s) {
+  const Sell &S = P.sell;
+  if (S.nslices == 0) return;
+  const int nb = nblocks((long)S.nslices * 32, TPB);
+  if (ncomp == 1)
+    k_sell<T, 1, false><<<nb, TPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
+  else if (aligned(u, 2 * sizeof(T)))
+    k_sell<T, 2, true><<<nb, TPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
+  else
+    k_sell<T, 2, false><<<nb, TPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
+  CHNSS_LAUNCH_CK();
+}
+template void spmv_sell<double>(const Pattern &, const double *, int, const double *, double *, SpmvMode,
+                                const SpmvArgs &, cudaStream_t);
+template void spmv_sell<float>(const Pattern &, const float *, int, const float *, float *, SpmvMode,
+                               const SpmvArgs &, cudaStream_t);
+
+template <typename T>
+void spmv_sell_bsr2(const Pattern &P, const T *sval, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
+                    cudaStream_t s) {
+  const Sell &S = P.sell;
+  if (S.nslices == 0) return;
+  const int nb = nblocks((long)S.nslices * 32, TPB);
+  if (!aligned(sval, 4 * sizeof(T)))
+    throw Error{CHNSS_ERR_ARG, "2x2-block values must be 16-byte aligned"};
+  if (aligned(u, 2 * sizeof(T)))
+    k_sell_bsr2<T, true><<<nb, TPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
+  else
+    k_sell_bsr2<T, false><<<nb, TPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
+  CHNSS_LAUNCH_CK();
+}
+template void spmv_sell_bsr2<double>(const Pattern &, const double *, const double *, double *, SpmvMode,
+                                     const SpmvArgs &, cudaStream_t);
+template void spmv_sell_bsr2<float>(const Pattern &, const float *, const float *, float *, SpmvMode,
+                                    const SpmvArgs &, cudaStream_t);
+
+void spmv_sell_ch(const Pattern &P, const double *L, const double *K, const double *k12, const double *M, double a12,
+                  double a21, double a22, const double *x, double *y, cudaStream_t s) {
+  const Sell &S = P.sell;
+  k_sell_ch<<<nblocks((long)S.nslices * 32, TPB), TPB, 0, s>>>(S.nslices, P.nrows, S.slice_ptr, S.rowid, S.col, L, K,
+                                                               k12, M, a12, a21, a22, x, y);
+  CHNSS_LAUNCH_CK();
+}
+void spmv_sell_b(const Pattern &P, const double *sval2, const double *v, double *y, cudaStream_t s) {
+  const Sell &S = P.sell;
+  const int nb = nblocks((long)S.nslices * 32, TPB);
+  if (aligned(v, 16))
+    k_sell_b<true><<<nb, TPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval2, v, y);
+  else
+    k_sell_b<false><<<nb, TPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval2, v, y);
+  CHNSS_LAUNCH_CK();
+}
+void spmv_sell_bt_add(const Pattern &P, const double *sval2, const double *p, double *yv, cudaStream_t s) {
+  const Sell &S = P.sell;
+  k_sell_bt_add<<<nblocks((long)S.nslices * 32, TPB), TPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval2, p,
+                                                                   yv);
+  CHNSS_LAUNCH_CK();
+}
 
 void spmv_ch(const Pattern &P, const double *L, const double *K, const double *k12, const double *M, double a12,
              double a21, double a22, const double *x, double *y, cudaStream_t s) {
