@@ -24,7 +24,8 @@ import scipy.sparse as sp
 from . import fem
 from .krylov import chebyshev, fgmres, pcg
 from .mesh import Mesh
-from .mg import MG, inject_p1, inject_velocity, level_sizes, prolongation_p1, prolongation_velocity
+from .mg import (MG, VEL_LO_RATIO, VEL_SMOOTH_DEGREE, inject_p1, inject_velocity, level_sizes, prolongation_p1,
+                 prolongation_velocity)
 from .model import (Forms, ac_system, ch_rhs_loads, ch_system, mobility_at, ns_shift, ns_system,
                     potential_loads)
 
@@ -139,7 +140,7 @@ class Oracle:
             J2 = fem.convection_p2(f.mesh, st["v"], shift)
             Al = vf["Mv"] / tau + sp.kron(J2, sp.eye(2), format="csr") + vf["Ksym"]
             mats.append(fem.velocity_dirichlet(Al.tocsr(), vf["bnd"]))
-        mgA = MG(mats, self.Pv())
+        mgA = MG(mats, self.Pv(), degree=VEL_SMOOTH_DEGREE, ratio=VEL_LO_RATIO)
         if self._Kp is None:
             self._Kp = MG([f.K for f in self.forms], self.P1, singular=True)
         mgK = self._Kp

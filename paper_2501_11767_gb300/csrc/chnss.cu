@@ -84,6 +84,15 @@ __global__ void k_inv_diag(int n, const double *val, const int *diag, double *ou
 Geo geo(const Level &L) { return Geo{L.n, L.hx, L.hy}; }
 
 // ---------------------------------------------------------------------------
+constexpr int kNumPrec = 5;
+constexpr int kMaxProbes = 32;
+struct PrecGraph {
+  cudaGraphExec_t plain = nullptr, prof = nullptr;
+  std::vector<Profiler::Probe> probes;
+  size_t nprobes = 0;
+  long long nodes = 0;          // kernels launched by one replay
+};
+
 template <typename T>
 struct PrecSet {
   MGHier<T> L, AC, A, Kp;
@@ -117,53 +126,74 @@ struct chnss_ctx {
   double *massc = nullptr;
   std::unique_ptr<PrecSet<double>> p64;
   std::unique_ptr<PrecSet<float>> p32;
+  // captured preconditioner graphs (0..2 CH species, 3 AC, 4 NS)
+  double **slots = nullptr;   // device [2 * kNumPrec] input / output pointers
+  cudaStream_t cap = nullptr; // private stream used for capture only
+  PrecGraph pg[kNumPrec];
+  int pending_probe = -1;
   KrylovWork kw;
   Profiler prof;
   bool assembled = false;
   bool ch_done[3] = {false, false, false};
   double *hin = nullptr, *hout = nullptr;   // device staging of chnss_step_host
   const Level &lv(int l) const { return mesh->m.lv[l]; }
+  ~chnss_ctx() {
+    for (PrecGraph &g : pg) {
+      if (g.plain) cudaGraphExecDestroy(g.plain);
+      if (g.prof) cudaGraphExecDestroy(g.prof);
+      for (Profiler::Probe &pr : g.probes) {
+        if (pr.e0) cudaEventDestroy(pr.e0);
+        if (pr.e1) cudaEventDestroy(pr.e1);
+      }
+    }
+    if (cap) cudaStreamDestroy(cap);
+  }
 };
 
 namespace {
 
 // ---------------------------------------------------------------------------
-// preconditioner applications (Sec. 4)
+// preconditioner applications (Sec. 4).  The input r and output z are read
+// and written through a device pointer slot (slot[0] = r, slot[1] = z), so
+// the whole launch sequence is captured once into a CUDA graph and replayed
+// for any pair of Krylov vectors.
 template <typename T>
-void ch_precond(chnss_ctx *c, PrecSet<T> &P, int sp, const double *r, double *z) {
-  cudaStream_t s = c->s;
+void ch_precond(chnss_ctx *c, PrecSet<T> &P, int sp, double **slot, cudaStream_t s) {
   const int N1 = c->N1;
-  vec_convert<double, T>(N1, r, P.L.input(), s);
+  const double *const *in = const_cast<const double *const *>(slot);
+  double *const *out = slot + 1;
+  vec_convert_from_slot<double, T>(N1, in, 0, P.L.input(), s);
   P.L.apply(s);
-  vec_convert<T, double>(N1, P.L.output(), z, s);
+  vec_convert_to_slot<T, double>(N1, P.L.output(), out, 0, s);
   // S~^-1 = X2^-1 M X1^-1 (matching factors of eqn::schurCH)
   MGHier<T> &X1 = P.X1[sp];
   MGHier<T> &X2 = c->p.mobility_kind == 0 ? P.X1[sp] : P.X2[sp];
-  vec_convert<double, T>(N1, r + N1, X1.input(), s);
+  vec_convert_from_slot<double, T>(N1, in, N1, X1.input(), s);
   X1.apply(s);
   SpmvArgs none;
   spmv_sell<T>(c->lv(0).p1, P.Mv, 1, X1.output(), X2.input(), SPMV_PLAIN, none, s);
   X2.apply(s);
-  vec_convert<T, double>(N1, X2.output(), z + N1, s);
+  vec_convert_to_slot<T, double>(N1, X2.output(), out, N1, s);
 }
 
 template <typename T>
-void ac_precond(chnss_ctx *c, PrecSet<T> &P, const double *r, double *z) {
-  vec_convert<double, T>(c->N1, r, P.AC.input(), c->s);
-  P.AC.apply(c->s);
-  vec_convert<T, double>(c->N1, P.AC.output(), z, c->s);
+void ac_precond(chnss_ctx *c, PrecSet<T> &P, double **slot, cudaStream_t s) {
+  vec_convert_from_slot<double, T>(c->N1, const_cast<const double *const *>(slot), 0, P.AC.input(), s);
+  P.AC.apply(s);
+  vec_convert_to_slot<T, double>(c->N1, P.AC.output(), slot + 1, 0, s);
 }
 
 template <typename T>
-void ns_precond(chnss_ctx *c, PrecSet<T> &P, const double *r, double *z) {
-  cudaStream_t s = c->s;
+void ns_precond(chnss_ctx *c, PrecSet<T> &P, double **slot, cudaStream_t s) {
   const long nv = 2L * c->N2;
   const int N1 = c->N1;
-  vec_convert<double, T>(nv, r, P.A.input(), s);
+  const double *const *in = const_cast<const double *const *>(slot);
+  double *const *out = slot + 1;
+  vec_convert_from_slot<double, T>(nv, in, 0, P.A.input(), s);
   P.A.apply(s);
-  vec_convert<T, double>(nv, P.A.output(), z, s);
+  vec_convert_to_slot<T, double>(nv, P.A.output(), out, 0, s);
   // pressure convection-diffusion: M_p^-1 A_p K_p^-1
-  vec_convert<double, T>(N1, r + nv, P.Kp.input(), s);
+  vec_convert_from_slot<double, T>(N1, in, nv, P.Kp.input(), s);
   P.Kp.apply(s);
   SpmvArgs none;
   const Pattern &p1 = c->lv(0).p1;
@@ -180,7 +210,41 @@ void ns_precond(chnss_ctx *c, PrecSet<T> &P, const double *r, double *z) {
     spmv_sell<T>(p1, P.Mv, 1, cur, other, SPMV_CHEB, a, s);
     std::swap(cur, other);
   }
-  vec_convert<T, double>(N1, cur, z + nv, s);
+  vec_convert_to_slot<T, double>(N1, cur, out, nv, s);
+}
+
+// preconditioner g: 0..2 CH species, 3 AC, 4 NS
+template <typename T>
+void prec_body_t(chnss_ctx *c, PrecSet<T> &P, int g, cudaStream_t s) {
+  double **slot = c->slots + 2 * g;
+  if (g < 3) ch_precond(c, P, g, slot, s);
+  else if (g == 3) ac_precond(c, P, slot, s);
+  else ns_precond(c, P, slot, s);
+}
+void prec_body(chnss_ctx *c, int g, cudaStream_t s) {
+  if (c->p32) prec_body_t(c, *c->p32, g, s);
+  else prec_body_t(c, *c->p64, g, s);
+}
+
+void run_prec(chnss_ctx *c, int g, const double *r, double *z) {
+  set_ptr_slots(reinterpret_cast<void **>(c->slots + 2 * g), r, z, c->s);
+  PrecGraph &pg = c->pg[g];
+  if (!pg.plain) {
+    prec_body(c, g, c->s);
+    return;
+  }
+  const bool prof = c->prof.on && pg.prof;
+  CHNSS_CK(cudaGraphLaunch(prof ? pg.prof : pg.plain, c->s));
+  g_launch_count.fetch_add(pg.nodes, std::memory_order_relaxed);
+  if (prof) c->pending_probe = g;
+}
+
+void harvest_probes(chnss_ctx *c) {
+  if (c->pending_probe >= 0) {
+    const PrecGraph &pg = c->pg[c->pending_probe];
+    c->prof.harvest(pg.probes, pg.nprobes);
+    c->pending_probe = -1;
+  }
 }
 
 struct CHOp : LinearOperator {
@@ -195,10 +259,8 @@ struct CHOp : LinearOperator {
     spmv_sell_ch(c->lv(0).p1, c->Ls, c->Ks, var ? c->Kks[sp] : nullptr, c->Ms, var ? tau : tau * g, tau * g,
             -tau * g / b, x, y, s);
   }
-  void precond(const double *r, double *z, cudaStream_t) override {
-    if (c->p32) ch_precond(c, *c->p32, sp, r, z);
-    else ch_precond(c, *c->p64, sp, r, z);
-  }
+  void precond(const double *r, double *z, cudaStream_t) override { run_prec(c, sp, r, z); }
+  void after_sync() override { harvest_probes(c); }
 };
 
 struct ACOp : LinearOperator {
@@ -209,10 +271,8 @@ struct ACOp : LinearOperator {
     SpmvArgs none;
     spmv_sell<double>(c->lv(0).p1, c->ACs, 1, x, y, SPMV_PLAIN, none, s);
   }
-  void precond(const double *r, double *z, cudaStream_t) override {
-    if (c->p32) ac_precond(c, *c->p32, r, z);
-    else ac_precond(c, *c->p64, r, z);
-  }
+  void precond(const double *r, double *z, cudaStream_t) override { run_prec(c, 3, r, z); }
+  void after_sync() override { harvest_probes(c); }
 };
 
 struct NSOp : LinearOperator {
@@ -229,11 +289,48 @@ struct NSOp : LinearOperator {
     spmv_sell_bt_add(c->mesh->m.pbt, c->Bts, x + nv, y, s);
     spmv_sell_b(c->mesh->m.pb, c->Bs, x, y + nv, s);
   }
-  void precond(const double *r, double *z, cudaStream_t) override {
-    if (c->p32) ns_precond(c, *c->p32, r, z);
-    else ns_precond(c, *c->p64, r, z);
-  }
+  void precond(const double *r, double *z, cudaStream_t) override { run_prec(c, 4, r, z); }
+  void after_sync() override { harvest_probes(c); }
 };
+
+// Capture every preconditioner into two graphs: plain, and with probe
+// events around the fine-level sweeps (used while profiling is on).
+void capture_graphs(chnss_ctx *c) {
+  CHNSS_CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  for (int g = 0; g < kNumPrec; ++g) {
+    PrecGraph &pg = c->pg[g];
+    pg.probes.resize(kMaxProbes);
+    for (Profiler::Probe &pr : pg.probes) {
+      CHNSS_CK(cudaEventCreate(&pr.e0));
+      CHNSS_CK(cudaEventCreate(&pr.e1));
+    }
+    for (int variant = 0; variant < 2; ++variant) {
+      const long long before = g_launch_count.load();
+      c->prof.sink = variant == 1 ? &pg.probes : nullptr;
+      c->prof.sink_used = 0;
+      CHNSS_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+      cudaGraph_t graph = nullptr;
+      try {
+        prec_body(c, g, c->cap);
+      } catch (...) {
+        c->prof.sink = nullptr;
+        cudaStreamEndCapture(c->cap, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+      }
+      if (variant == 1) pg.nprobes = c->prof.sink_used;
+      c->prof.sink = nullptr;
+      CHNSS_CK(cudaStreamEndCapture(c->cap, &graph));
+      cudaGraphExec_t exec = nullptr;
+      const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      CHNSS_CK(e);
+      (variant == 0 ? pg.plain : pg.prof) = exec;
+      pg.nodes = g_launch_count.load() - before;
+      g_launch_count.store(before);
+    }
+  }
+}
 
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -255,6 +352,8 @@ void init_precset(chnss_ctx *c, PrecSet<T> &P) {
   P.L.init(ar, 0, false, p1s, d1s, vals(c->L), t1s, c->partial);
   P.AC.init(ar, 0, false, p1s, d1s, vals(c->AC), t1s, c->partial);
   P.A.init(ar, 1, false, p2s, d2s, vals(c->A), tvs, c->partial);
+  P.A.degree = 4;        // velocity smoothing: degree 4 on [hi / 16, hi]
+  P.A.ratio = 16.0;
   P.Kp.init(ar, 0, true, p1s, d1s, vals(c->K1), t1s, c->partial);
   for (int sp = 0; sp < 3; ++sp) {
     std::vector<const double *> x1, x2;
@@ -423,6 +522,9 @@ void create_context(chnss_ctx *c) {
     c->p64.reset(new PrecSet<double>());
     init_precset(c, *c->p64);
   }
+  c->slots = ar.alloc<double *>(2 * kNumPrec);
+  CHNSS_CK(cudaStreamSynchronize(s));
+  capture_graphs(c);
   CHNSS_CK(cudaStreamSynchronize(s));
 }
 

@@ -61,14 +61,24 @@ void jacobi_csr(const Pattern &P, const double *val, const int *diag, T *dinv, d
 template <typename T>
 void jacobi_bsr2(const Pattern &P, const double *val, const int *diag, T *dinv, double *hi, double *partial,
                  cudaStream_t s);
-// coef layout: [pre1 scale][pre2 c0,c1,c2][post1 c0,c1,c2][post2 c0,c1,c2] (10 doubles)
-void cheb_coefficients(const double *hi, double ratio, double *coef, cudaStream_t s);
+// Chebyshev smoother of degree d on [hi / ratio, hi]; coef layout (4 + 3(d-1)
+// doubles): [beta0][first post step: 1, 0, beta0][(c0, c1, c2) for k = 1..d-1]
+// with x_{k+1} = c0 x_k + c1 x_{k-1} + c2 D^-1 (b - A x_k).
+constexpr int kMaxSmoothDegree = 8;
+void cheb_coefficients(const double *hi, double ratio, int degree, double *coef, cudaStream_t s);
 
 // vectors
 template <typename T>
 void vec_scale_dinv(int n, const double *scale, const T *dinv, const T *b, T *out, cudaStream_t s);
 template <typename Ta, typename Tb>
 void vec_convert(long n, const Ta *in, Tb *out, cudaStream_t s);
+// conversions through a device pointer slot (*slot + off), so that a
+// captured CUDA graph can read / write vectors chosen at replay time
+template <typename Ta, typename Tb>
+void vec_convert_from_slot(long n, const Ta *const *slot, long off, Tb *out, cudaStream_t s);
+template <typename Ta, typename Tb>
+void vec_convert_to_slot(long n, const Ta *in, Tb *const *slot, long off, cudaStream_t s);
+void set_ptr_slots(void **slots, const void *a, const void *b, cudaStream_t s);   // slots[0] = a, slots[1] = b
 void vec_axpby(long n, double a, const double *x, double b, double *y, cudaStream_t s);      // y = a x + b y
 void vec_copy(long n, const double *x, double *y, cudaStream_t s);
 void vec_fill(long n, double v, double *y, cudaStream_t s);

@@ -7,7 +7,6 @@
 
 namespace chnss {
 
-constexpr double kSmootherRatio = 4.0;   // smoothing interval [hi / 4, hi]
 
 const char *Profiler::name(int k) {
   static const char *names[NKINDS] = {"mg_velocity_spmv_fine", "mg_p1_spmv_fine", "ns_operator_spmv",
@@ -16,6 +15,15 @@ const char *Profiler::name(int k) {
 }
 
 void Profiler::start(int k, cudaStream_t s) {
+  if (sink) {
+    if (sink_used < sink->size()) {
+      Probe &p = (*sink)[sink_used];
+      p.kind = k;
+      // during capture only an external record becomes an event node
+      CHNSS_CK(cudaEventRecordWithFlags(p.e0, s, cudaEventRecordExternal));
+    }
+    return;
+  }
   if (!on) return;
   Rec &r = rec[k];
   if (r.used + 2 > r.ev.size()) {
@@ -30,6 +38,14 @@ void Profiler::start(int k, cudaStream_t s) {
 }
 
 void Profiler::stop(int k, cudaStream_t s, double bytes) {
+  if (sink) {
+    if (sink_used < sink->size()) {
+      Probe &p = (*sink)[sink_used++];
+      p.bytes = bytes;
+      CHNSS_CK(cudaEventRecordWithFlags(p.e1, s, cudaEventRecordExternal));
+    }
+    return;
+  }
   if (!on) return;
   Rec &r = rec[k];
   if (r.used + 2 > r.ev.size()) return;
@@ -39,17 +55,31 @@ void Profiler::stop(int k, cudaStream_t s, double bytes) {
   r.bytes += bytes;
 }
 
+void Profiler::harvest(const std::vector<Probe> &probes, size_t count) {
+  if (!on) return;
+  for (size_t i = 0; i < count && i < probes.size(); ++i) {
+    const Probe &p = probes[i];
+    float t = 0.f;
+    CHNSS_CK(cudaEventElapsedTime(&t, p.e0, p.e1));
+    Rec &r = rec[p.kind];
+    r.ms_graph += t;
+    r.launches += 1;
+    r.bytes += p.bytes;
+  }
+}
+
 void Profiler::reset() {
   for (Rec &r : rec) {
     r.launches = 0;
     r.bytes = 0.0;
+    r.ms_graph = 0.0;
     r.used = 0;
   }
 }
 
 double Profiler::elapsed_ms(int k) {
   Rec &r = rec[k];
-  double ms = 0.0;
+  double ms = r.ms_graph;
   for (size_t i = 0; i + 1 < r.used; i += 2) {
     float t = 0.f;
     CHNSS_CK(cudaEventElapsedTime(&t, r.ev[i], r.ev[i + 1]));
@@ -109,7 +139,7 @@ void MGHier<T>::init(Arena &ar, int kind_, bool singular_, const std::vector<con
     r[l] = ar.alloc<T>(nu);
     b[l] = ar.alloc<T>(nu);
     hi[l] = ar.alloc<double>(1);
-    coef[l] = ar.alloc<double>(10);
+    coef[l] = ar.alloc<double>(4 + 3 * (kMaxSmoothDegree - 1));
   }
   nc = (int)n[nl - 1];
   dense = ar.alloc<double>((long)nc * nc);
@@ -128,7 +158,7 @@ void MGHier<T>::setup(cudaStream_t s) {
       jacobi_csr<T>(*pat[l], val64[l], diag[l], dinv[l], hi[l], partial, s);
     else
       jacobi_bsr2<T>(*pat[l], val64[l], diag[l], dinv[l], hi[l], partial, s);
-    cheb_coefficients(hi[l], kSmootherRatio, coef[l], s);
+    cheb_coefficients(hi[l], ratio, degree, coef[l], s);
   }
   const int L = nl - 1;
   if (kind == 0)
@@ -167,10 +197,18 @@ void MGHier<T>::vcycle(int l, cudaStream_t s) {
   SpmvArgs a;
   a.b = b[l];
   a.dinv = dinv[l];
-  // pre-smoothing from x = 0
-  vec_scale_dinv<T>((int)n[l], coef[l], dinv[l], b[l], t[l], s);
-  a.coef = coef[l] + 1;
-  op(l, t[l], x[l], SPMV_CHEB, a, s);
+  // pre-smoothing from x = 0: x_1 = D^-1 b / theta, then degree - 1 steps of
+  // the three-term recurrence; x_{k+1} overwrites x_{k-1}, so x_1 starts in
+  // the buffer that makes x_degree land in x[l]
+  T *cur = (degree - 1) % 2 == 0 ? x[l] : t[l];
+  T *oth = cur == x[l] ? t[l] : x[l];
+  vec_scale_dinv<T>((int)n[l], coef[l], dinv[l], b[l], cur, s);
+  for (int k = 1; k < degree; ++k) {
+    a.coef = coef[l] + 4 + 3 * (k - 1);
+    a.w = k == 1 ? nullptr : oth;
+    op(l, cur, oth, SPMV_CHEB, a, s);
+    std::swap(cur, oth);
+  }
   // residual, restriction, coarse correction, prolongation
   SpmvArgs ar;
   ar.b = b[l];
@@ -180,13 +218,19 @@ void MGHier<T>::vcycle(int l, cudaStream_t s) {
   spmv_sell<T>(T_.R, transfer_vals<T>(T_, true), nc_, r[l], b[l + 1], SPMV_PLAIN, none, s);
   vcycle(l + 1, s);
   spmv_sell<T>(T_.P, transfer_vals<T>(T_, false), nc_, x[l + 1], x[l], SPMV_ADD, none, s);
-  // post-smoothing
-  a.coef = coef[l] + 4;
+  // post-smoothing from x_0 = x[l]
+  a.coef = coef[l] + 1;
   a.w = nullptr;
   op(l, x[l], t[l], SPMV_CHEB, a, s);
-  a.coef = coef[l] + 7;
-  a.w = x[l];
-  op(l, t[l], x[l], SPMV_CHEB, a, s);
+  cur = t[l];
+  oth = x[l];
+  for (int k = 1; k < degree; ++k) {
+    a.coef = coef[l] + 4 + 3 * (k - 1);
+    a.w = oth;
+    op(l, cur, oth, SPMV_CHEB, a, s);
+    std::swap(cur, oth);
+  }
+  if (cur != x[l]) vec_convert<T, T>(n[l], cur, x[l], s);
 }
 
 template <typename T>
@@ -276,6 +320,7 @@ chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, 
         arnoldi_finish(j, ldh, ws.H, ws.h1, ws.h2, sc + 3, ws.cs, ws.sn, ws.g, sc + 4, s);
         CHNSS_CK(cudaMemcpyAsync(ws.hstat, sc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CHNSS_CK(cudaStreamSynchronize(s));
+        A.after_sync();
         const double est = ws.hstat[0], hn = ws.hstat[1];
         ++iters;
         k = j + 1;

@@ -15,11 +15,23 @@ struct Profiler {
   struct Rec {
     long long launches = 0;
     double bytes = 0.0;
+    double ms_graph = 0.0;          // harvested from graph probes
     std::vector<cudaEvent_t> ev;   // start/stop pairs
     size_t used = 0;
   } rec[NKINDS];
+  // A probe is a start/stop event pair recorded as nodes of a captured CUDA
+  // graph; while `sink` is set, start/stop append probes instead of using the
+  // eager pool.  After a replay has completed, harvest() adds the probes.
+  struct Probe {
+    int kind;
+    double bytes;
+    cudaEvent_t e0, e1;
+  };
+  std::vector<Probe> *sink = nullptr;   // preallocated events (created before capture)
+  size_t sink_used = 0;
   void start(int k, cudaStream_t s);
   void stop(int k, cudaStream_t s, double bytes);
+  void harvest(const std::vector<Probe> &probes, size_t count);
   void reset();
   double elapsed_ms(int k);        // after a stream synchronisation
   void release();
@@ -50,6 +62,8 @@ struct MGHier {
   int *status = nullptr;
   double *partial = nullptr, *sum = nullptr;
   Profiler *prof = nullptr;
+  int degree = 2;          // Chebyshev smoothing degree (pre and post)
+  double ratio = 4.0;      // smoothing interval [hi / ratio, hi]
 
   // levels: per level pattern + FP64 value pointer (values may change
   // between setups, the pointers may not); transfers tr[l] from level l+1.
@@ -73,6 +87,8 @@ struct LinearOperator {
   virtual long size() const = 0;
   virtual void apply(const double *x, double *y, cudaStream_t s) = 0;
   virtual void precond(const double *r, double *z, cudaStream_t s) = 0;
+  // called by the Krylov driver after each host synchronisation of the stream
+  virtual void after_sync() {}
 };
 
 struct KrylovWork {

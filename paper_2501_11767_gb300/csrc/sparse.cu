@@ -403,19 +403,25 @@ __global__ void k_max_final(int nb, const double *partial, double *out) {
   if (threadIdx.x == 0) *out = sm[0];
 }
 
-// Degree-2 Chebyshev smoother on [hi/ratio, hi] (three-term recurrence,
-// Saad Alg. 12.1 on D^-1 A): theta, delta, sigma, rho0 = 1/sigma,
-// rho1 = 1/(2 sigma - rho0); beta0 = 1/theta, alpha1 = rho1 rho0,
-// beta1 = 2 rho1 / delta.
-__global__ void k_cheb_coef(const double *hi, double ratio, double *c) {
+// Chebyshev smoother of degree d on [hi/ratio, hi] (three-term recurrence,
+// Saad Alg. 12.1 on D^-1 A): theta = (hi+lo)/2, delta = (hi-lo)/2,
+// sigma = theta/delta, rho_0 = 1/sigma, rho_k = 1/(2 sigma - rho_{k-1});
+// x_1 = x_0 + D^-1 r_0 / theta, x_{k+1} = x_k + rho_k rho_{k-1} (x_k - x_{k-1})
+// + (2 rho_k / delta) D^-1 (b - A x_k).
+__global__ void k_cheb_coef(const double *hi, double ratio, int degree, double *c) {
   const double h = *hi, lo = h / ratio;
   const double theta = 0.5 * (h + lo), delta = 0.5 * (h - lo), sigma = theta / delta;
-  const double rho0 = 1.0 / sigma, rho1 = 1.0 / (2.0 * sigma - rho0);
-  const double b0 = 1.0 / theta, a1 = rho1 * rho0, b1 = 2.0 * rho1 / delta;
-  c[0] = b0;
-  c[1] = 1.0 + a1; c[2] = 0.0; c[3] = b1;     // pre2: x = (1+a1) t + b1 D^-1 (b - A t)
-  c[4] = 1.0; c[5] = 0.0; c[6] = b0;          // post1: t = x + b0 D^-1 (b - A x)
-  c[7] = 1.0 + a1; c[8] = -a1; c[9] = b1;     // post2: x = (1+a1) t - a1 x + b1 D^-1 (b - A t)
+  double rho = 1.0 / sigma;
+  c[0] = 1.0 / theta;                          // pre: x_1 = D^-1 b / theta
+  c[1] = 1.0; c[2] = 0.0; c[3] = 1.0 / theta;  // post: x_1 = x_0 + D^-1 (b - A x_0) / theta
+  for (int k = 1; k < degree; ++k) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    const double al = rn * rho;
+    c[4 + 3 * (k - 1)] = 1.0 + al;
+    c[5 + 3 * (k - 1)] = -al;
+    c[6 + 3 * (k - 1)] = 2.0 * rn / delta;
+    rho = rn;
+  }
 }
 
 // --------------------------------------------------------------------------
@@ -428,6 +434,20 @@ template <typename Ta, typename Tb>
 __global__ void k_convert(long n, const Ta *in, Tb *out) {
   const long i = (long)blockIdx.x * TPB + threadIdx.x;
   if (i < n) out[i] = (Tb)in[i];
+}
+template <typename Ta, typename Tb>
+__global__ void k_convert_from_slot(long n, const Ta *const *slot, long off, Tb *out) {
+  const long i = (long)blockIdx.x * TPB + threadIdx.x;
+  if (i < n) out[i] = (Tb)((*slot)[off + i]);
+}
+template <typename Ta, typename Tb>
+__global__ void k_convert_to_slot(long n, const Ta *in, Tb *const *slot, long off) {
+  const long i = (long)blockIdx.x * TPB + threadIdx.x;
+  if (i < n) (*slot)[off + i] = (Tb)in[i];
+}
+__global__ void k_set_ptrs(void **slots, const void *a, const void *b) {
+  slots[0] = const_cast<void *>(a);
+  slots[1] = const_cast<void *>(b);
 }
 __global__ void k_axpby(long n, double a, const double *x, double b, double *y) {
   const long i = (long)blockIdx.x * TPB + threadIdx.x;
@@ -854,8 +874,9 @@ template void jacobi_bsr2<double>(const Pattern &, const double *, const int *, 
 template void jacobi_bsr2<float>(const Pattern &, const double *, const int *, float *, double *, double *,
                                  cudaStream_t);
 
-void cheb_coefficients(const double *hi, double ratio, double *coef, cudaStream_t s) {
-  k_cheb_coef<<<1, 1, 0, s>>>(hi, ratio, coef);
+void cheb_coefficients(const double *hi, double ratio, int degree, double *coef, cudaStream_t s) {
+  if (degree < 1 || degree > kMaxSmoothDegree) throw Error{CHNSS_ERR_ARG, "smoother degree out of range"};
+  k_cheb_coef<<<1, 1, 0, s>>>(hi, ratio, degree, coef);
   CHNSS_LAUNCH_CK();
 }
 
@@ -876,6 +897,28 @@ void vec_convert(long n, const Ta *in, Tb *out, cudaStream_t s) {
 template void vec_convert<double, float>(long, const double *, float *, cudaStream_t);
 template void vec_convert<float, double>(long, const float *, double *, cudaStream_t);
 template void vec_convert<double, double>(long, const double *, double *, cudaStream_t);
+template void vec_convert<float, float>(long, const float *, float *, cudaStream_t);
+
+template <typename Ta, typename Tb>
+void vec_convert_from_slot(long n, const Ta *const *slot, long off, Tb *out, cudaStream_t s) {
+  if (n == 0) return;
+  k_convert_from_slot<Ta, Tb><<<nblocks(n, TPB), TPB, 0, s>>>(n, slot, off, out);
+  CHNSS_LAUNCH_CK();
+}
+template <typename Ta, typename Tb>
+void vec_convert_to_slot(long n, const Ta *in, Tb *const *slot, long off, cudaStream_t s) {
+  if (n == 0) return;
+  k_convert_to_slot<Ta, Tb><<<nblocks(n, TPB), TPB, 0, s>>>(n, in, slot, off);
+  CHNSS_LAUNCH_CK();
+}
+template void vec_convert_from_slot<double, float>(long, const double *const *, long, float *, cudaStream_t);
+template void vec_convert_from_slot<double, double>(long, const double *const *, long, double *, cudaStream_t);
+template void vec_convert_to_slot<float, double>(long, const float *, double *const *, long, cudaStream_t);
+template void vec_convert_to_slot<double, double>(long, const double *, double *const *, long, cudaStream_t);
+void set_ptr_slots(void **slots, const void *a, const void *b, cudaStream_t s) {
+  k_set_ptrs<<<1, 1, 0, s>>>(slots, a, b);
+  CHNSS_LAUNCH_CK();
+}
 
 void vec_axpby(long n, double a, const double *x, double b, double *y, cudaStream_t s) {
   k_axpby<<<nblocks(n, TPB), TPB, 0, s>>>(n, a, x, b, y);

@@ -131,4 +131,7 @@ def workload(name: str) -> dict:
     if name == "film1024_mixed":
         p.update(beta=film_betas(0.005), tau=5e-4, precision=1)
         return {"n": 1024, "params": p, "steps": 10}
+    if name == "film512_mixed":      # the same parameters on 512 x 512 (profiling captures)
+        p.update(beta=film_betas(0.005), tau=5e-4, precision=1)
+        return {"n": 512, "params": p, "steps": 10}
     raise KeyError(name)
