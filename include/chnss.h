@@ -166,6 +166,7 @@ typedef struct {
   long long kind_launches[8];  /* timed launches (or Arnoldi steps) per family */
   double kind_ms[8];           /* summed CUDA-event durations */
   double kind_bytes[8];        /* summed algorithmic bytes */
+  double kind_flops[8];        /* summed floating-point operations (orthogonalisation only) */
 } chnss_profile;
 /* on != 0: reset the counters and start recording (synchronises the stream). */
 chnss_status chnss_profile_enable(chnss_ctx_t ctx, int on);

@@ -33,8 +33,22 @@ MASS_CHEB_DEGREE = 5
 MASS_CHEB_BOUNDS = (0.5, 2.0)      # spectrum of D^{-1} M for P1 triangles (Wathen)
 
 
+def _direct(A, b):
+    """Sparse LU solve (used by the exact-solve mode of the oracle)."""
+    import scipy.sparse.linalg as spla
+    x = spla.spsolve(A.tocsc(), b)
+    r = float(np.linalg.norm(b - A @ x))
+    nb = float(np.linalg.norm(b))
+    return x, {"iters": 0, "rel_residual": r / nb if nb else 0.0, "converged": True}
+
+
 class Oracle:
-    def __init__(self, n: int, params: dict, lx: float = 1.0, ly: float = 1.0):
+    """exact=True replaces every Krylov solve by a sparse LU solve of the same
+    system (finite-difference and adjoint checks need solves free of the
+    stopping-rule error)."""
+
+    def __init__(self, n: int, params: dict, lx: float = 1.0, ly: float = 1.0, exact: bool = False):
+        self.exact = exact
         self.params = dict(params)
         self.sizes = level_sizes(n)
         self.meshes = [Mesh(s, lx, ly) for s in self.sizes]
@@ -97,8 +111,11 @@ class Oracle:
     def solve_ch(self, state, species, f_i, lstates, convs):
         p = self.params
         A, rhs, _, _ = ch_system(self.forms[0], state, p, species, f_i, convs[0])
-        prec = self.ch_preconditioner(species, lstates, convs)
-        x, info = fgmres(lambda y: A @ y, prec, rhs, p["rtol"], p["atol"], p["restart"], p["maxit"])
+        if self.exact:
+            x, info = _direct(A, rhs)
+        else:
+            prec = self.ch_preconditioner(species, lstates, convs)
+            x, info = fgmres(lambda y: A @ y, prec, rhs, p["rtol"], p["atol"], p["restart"], p["maxit"])
         N = self.mesh.N1
         return x[:N], x[N:], info, (A, rhs)
 
@@ -106,6 +123,9 @@ class Oracle:
         p = self.params
         A, rhs = ac_system(self.forms[0], state, p, f_v, convs[0], j_out)
         tau = p["tau"]
+        if self.exact:
+            x, info = _direct(A, rhs)
+            return x, info, (A, rhs)
         mats = [(f.M + tau * p["delta_v"] * f.K + tau * C).tocsr() for f, C in zip(self.forms, convs)]
         mg = MG(mats, self.P1)
         x, info = fgmres(lambda y: A @ y, mg, rhs, p["rtol"], p["atol"], p["restart"], p["maxit"])
@@ -116,6 +136,8 @@ class Oracle:
         F = self.forms[0]
         phi_a = 1.0 - phi_new[0] - phi_new[1] - phi_new[2]
         rhs = f_a + p["beta"][3] * (F.K @ phi_a)
+        if self.exact:
+            return _direct(F.M, rhs)
         x, info = pcg(F.M, rhs, 1.0 / F.M.diagonal(), rtol=1e-12)
         return x, info
 
@@ -162,8 +184,15 @@ class Oracle:
         A, B, rhs_v, Ap, _ = ns_system(self.forms[0], state, p)
         nv = A.shape[0]
         rhs = np.concatenate([rhs_v, np.zeros(self.mesh.N1)])
-        prec = self.ns_preconditioner(A, Ap, lstates)
-        x, info = fgmres(self.ns_operator(A, B), prec, rhs, p["rtol"], p["atol"], p["restart"], p["maxit"])
+        if self.exact:
+            m = self.forms[0].M @ np.ones(self.mesh.N1)
+            K = sp.bmat([[A, B.T, None], [B, None, sp.csr_matrix(m[:, None])],
+                         [None, sp.csr_matrix(m[None, :]), None]], format="csc")
+            x, info = _direct(K, np.concatenate([rhs, [0.0]]))
+            x = x[:-1]
+        else:
+            prec = self.ns_preconditioner(A, Ap, lstates)
+            x, info = fgmres(self.ns_operator(A, B), prec, rhs, p["rtol"], p["atol"], p["restart"], p["maxit"])
         v, pr = x[:nv], x[nv:]
         Mp = self.forms[0].M
         one = np.ones(self.mesh.N1)

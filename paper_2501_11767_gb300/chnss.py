@@ -48,13 +48,13 @@ class SolveInfo(ctypes.Structure):
 class Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("nkinds", ctypes.c_int), ("name", (ctypes.c_char * 32) * 8),
                 ("kind_launches", ctypes.c_longlong * 8), ("kind_ms", ctypes.c_double * 8),
-                ("kind_bytes", ctypes.c_double * 8)]
+                ("kind_bytes", ctypes.c_double * 8), ("kind_flops", ctypes.c_double * 8)]
 
     def as_dict(self):
         kinds = {}
         for k in range(self.nkinds):
             kinds[self.name[k].value.decode()] = {"launches": self.kind_launches[k], "ms": self.kind_ms[k],
-                                                  "bytes": self.kind_bytes[k]}
+                                                  "bytes": self.kind_bytes[k], "flops": self.kind_flops[k]}
         return {"launches": self.launches, "kinds": kinds}
 
 

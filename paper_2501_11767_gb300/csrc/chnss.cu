@@ -968,6 +968,7 @@ chnss_status chnss_profile_read(chnss_ctx_t ctx, chnss_profile *out) {
     out->kind_launches[k] = ctx->prof.rec[k].launches;
     out->kind_ms[k] = ctx->prof.elapsed_ms(k);
     out->kind_bytes[k] = ctx->prof.rec[k].bytes;
+    out->kind_flops[k] = ctx->prof.rec[k].flops;
   }
   return CHNSS_OK;
   ABI_CATCH(ctx)

@@ -37,7 +37,7 @@ void Profiler::start(int k, cudaStream_t s) {
   CHNSS_CK(cudaEventRecord(r.ev[r.used], s));
 }
 
-void Profiler::stop(int k, cudaStream_t s, double bytes) {
+void Profiler::stop(int k, cudaStream_t s, double bytes, double flops) {
   if (sink) {
     if (sink_used < sink->size()) {
       Probe &p = (*sink)[sink_used++];
@@ -53,6 +53,7 @@ void Profiler::stop(int k, cudaStream_t s, double bytes) {
   r.used += 2;
   r.launches += 1;
   r.bytes += bytes;
+  r.flops += flops;
 }
 
 void Profiler::harvest(const std::vector<Probe> &probes, size_t count) {
@@ -72,6 +73,7 @@ void Profiler::reset() {
   for (Rec &r : rec) {
     r.launches = 0;
     r.bytes = 0.0;
+    r.flops = 0.0;
     r.ms_graph = 0.0;
     r.used = 0;
   }
@@ -315,8 +317,9 @@ chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, 
         mdot(n, ws.V, ld, j + 1, ws.w, ws.h1, ws.partial, s);
         ortho_update_mdot(n, ws.V, ld, j + 1, ws.h1, ws.w, ws.h2, ws.partial, s);
         ortho_update_norm(n, ws.V, ld, j + 1, ws.h2, ws.w, sc + 3, ws.partial, s);
-        // CGS2: three passes over V_0..V_j; w read 3x, written 2x
-        if (prof) prof->stop(Profiler::ORTHO, s, 8.0 * n * (3.0 * (j + 1) + 5.0));
+        // CGS2: three passes over V_0..V_j (w read 3x, written 2x) and
+        // 4(j+1)+1 FP64 FMAs per vector element (dot, update + dot, update + norm)
+        if (prof) prof->stop(Profiler::ORTHO, s, 8.0 * n * (3.0 * (j + 1) + 5.0), 2.0 * n * (4.0 * (j + 1) + 1.0));
         arnoldi_finish(j, ldh, ws.H, ws.h1, ws.h2, sc + 3, ws.cs, ws.sn, ws.g, sc + 4, s);
         CHNSS_CK(cudaMemcpyAsync(ws.hstat, sc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CHNSS_CK(cudaStreamSynchronize(s));

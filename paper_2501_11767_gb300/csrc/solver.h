@@ -15,6 +15,7 @@ struct Profiler {
   struct Rec {
     long long launches = 0;
     double bytes = 0.0;
+    double flops = 0.0;             // FP64 (or FP32) floating-point operations
     double ms_graph = 0.0;          // harvested from graph probes
     std::vector<cudaEvent_t> ev;   // start/stop pairs
     size_t used = 0;
@@ -30,7 +31,7 @@ struct Profiler {
   std::vector<Probe> *sink = nullptr;   // preallocated events (created before capture)
   size_t sink_used = 0;
   void start(int k, cudaStream_t s);
-  void stop(int k, cudaStream_t s, double bytes);
+  void stop(int k, cudaStream_t s, double bytes, double flops = 0.0);
   void harvest(const std::vector<Probe> &probes, size_t count);
   void reset();
   double elapsed_ms(int k);        // after a stream synchronisation
