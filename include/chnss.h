@@ -143,6 +143,28 @@ chnss_status chnss_step(chnss_ctx_t ctx, const chnss_state *in, chnss_state *out
 chnss_status chnss_step_host(chnss_ctx_t ctx, const chnss_state *host_in, chnss_state *host_out,
                              chnss_solve_info *info);
 
+/* Adjoint of one step (discrete adjoint of chnss_step; constant mobility).
+ * Every solve x = A(u)^-1 b(u) of the step contributes, with
+ * y = A^-T xbar (FGMRES on the transposed operator to a relative residual of
+ * 1e-12, preconditioned by the forward block preconditioner),
+ * ubar += (db/du)^T y - (d(A(u) x)/du)^T y: the transposed convection
+ * derivatives of C(v) (CH, AC) and J(w) (Oseen, w = v - sum alpha_i grad
+ * mu_i), the Hessian of eqn:appPotential in the potential loads, the
+ * Korteweg load, and the evaporation flux j_out.
+ * state_k: fields at t_k; state_k1: the step's output at t_{k+1};
+ * adj_k1: adjoint of the state at t_{k+1}; adj_k (out, overwritten):
+ * adjoint of the state at t_k (all DEVICE arrays, chnss_state layout;
+ * velocity adjoints are zero on the no-slip boundary, the pressure adjoint
+ * is zero because p^k does not enter the step).  grad_params (HOST, 2
+ * doubles, accumulated): d/d(evap_rate) and d/d(gamma) where gamma scales
+ * all three mobilities.  info[6] (optional): the transposed solves. */
+chnss_status chnss_adjoint_step(chnss_ctx_t ctx, const chnss_state *state_k, const chnss_state *state_k1,
+                                const chnss_state *adj_k1, chnss_state *adj_k, double *grad_params,
+                                chnss_solve_info *info);
+/* Final-morphology functional J = int |grad phi_p|^2 = phi_p^T K phi_p of a
+ * device polymer field; *J on the host; grad_phi_p (device, optional) = 2 K phi_p. */
+chnss_status chnss_objective(chnss_ctx_t ctx, const double *phi_p, double *J, double *grad_phi_p);
+
 /* Debug / test export of assembled fine-level objects to HOST memory.
  * which: 0 L = M + tau C, 1 AC matrix, 2 velocity block A (scalar CSR of the
  * interleaved dofs), 3 B (N1 x 2*N2), 4 A_p, 5 M, 6 K.  Call with null arrays

@@ -88,6 +88,11 @@ EXPORTS = {
     "chnss_export_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "chnss_mass_solve_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.POINTER(SolveInfo)]),
+    "chnss_adjoint_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.POINTER(State),
+                                          ctypes.POINTER(State), ctypes.POINTER(State),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo)]),
+    "chnss_objective": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.c_void_p]),
     "chnss_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
     "chnss_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -265,6 +270,25 @@ class Context:
         _check(lib.chnss_export_csr(self._h, which, ctypes.byref(nr), ctypes.byref(nz), rowptr.ctypes.data,
                                     col.ctypes.data, val.ctypes.data), self._h)
         return rowptr, col, val
+
+    def adjoint_step(self, state_k: dict, state_k1: dict, adj_k1: dict, adj_k: dict = None, check: bool = True):
+        """Returns (adj_k, [d/d evap_rate, d/d gamma], infos, status)."""
+        if adj_k is None:
+            adj_k = self.new_state()
+        a, b, c, d = make_state(state_k), make_state(state_k1), make_state(adj_k1), make_state(adj_k)
+        grad = (ctypes.c_double * 2)(0.0, 0.0)
+        infos = (SolveInfo * 6)()
+        st = load().chnss_adjoint_step(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d),
+                                       grad, infos)
+        if check:
+            _check(st, self._h)
+        return adj_k, [grad[0], grad[1]], {SYSTEM_NAMES[i]: infos[i].as_dict() for i in range(6)}, st
+
+    def objective(self, phi_p, grad=None):
+        """J = int |grad phi_p|^2 and, if grad is a device array, 2 K phi_p."""
+        J = ctypes.c_double()
+        _check(load().chnss_objective(self._h, _ptr(phi_p), ctypes.byref(J), _ptr(grad)), self._h)
+        return J.value
 
     def mass_solve_noalloc(self, rhs, x=None, check: bool = True):
         """M x = rhs through chnss_mass_solve_noalloc (no device allocation

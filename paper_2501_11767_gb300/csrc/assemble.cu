@@ -466,3 +466,219 @@ void launch_inject_vel(int nf, const double *fine, double *coarse, cudaStream_t 
 }
 
 }  // namespace chnss
+
+// ===========================================================================
+// Adjoint (transposed Jacobian) element kernels.  Each writes per-element
+// contributions that the node gather lists sum in element order.
+namespace chnss {
+namespace {
+
+// d/dv of y^T C(v) x (P1 x, y): int zeta_k (d_d x) y -> buf [E][6][2]
+__global__ void k_adj_conv_p1(Geo g, const double *__restrict__ x, const double *__restrict__ y, double *buf) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * g.n * g.n) return;
+  Elem el;
+  element(g, e, el);
+  double gx[2] = {0.0, 0.0}, ya[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double xv = x[el.v1[k]];
+    gx[0] += xv * el.gl[k][0];
+    gx[1] += xv * el.gl[k][1];
+    ya[k] = y[el.v1[k]];
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double s = el.area * (ya[0] * c_ref.c1[k][0] + ya[1] * c_ref.c1[k][1] + ya[2] * c_ref.c1[k][2]);
+    buf[(long)e * 12 + k * 2] = s * gx[0];
+    buf[(long)e * 12 + k * 2 + 1] = s * gx[1];
+  }
+}
+
+// d/dw of y^T J(w) x (velocities): nodal part int zeta_k sum_c (d_d x_c) y_c
+// -> bufv [E][6][2]; shift part (w = v - s, s per element) projected on the
+// P1 gradients: (ds-gradient) . grad psi_m -> bufm [E][3]
+__global__ void k_adj_conv_p2(Geo g, const double *__restrict__ x, const double *__restrict__ y, double *bufv,
+                              double *bufm) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * g.n * g.n) return;
+  Elem el;
+  element(g, e, el);
+  double xy[6][6];   // sum_c x_(b,c) y_(a,c)
+#pragma unroll
+  for (int b = 0; b < 6; ++b) {
+    const double x0 = x[2 * el.v2[b]], x1 = x[2 * el.v2[b] + 1];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) xy[b][a] = x0 * y[2 * el.v2[a]] + x1 * y[2 * el.v2[a] + 1];
+  }
+  double tg[3];
+  for (int l = 0; l < 3; ++l) {
+    double s = 0.0;
+    for (int b = 0; b < 6; ++b)
+#pragma unroll
+      for (int a = 0; a < 6; ++a) s += xy[b][a] * c_ref.jg[l][b][a];
+    tg[l] = s;
+  }
+  for (int k = 0; k < 6; ++k) {
+    double t[3];
+    for (int l = 0; l < 3; ++l) {
+      double s = 0.0;
+      for (int b = 0; b < 6; ++b)
+#pragma unroll
+        for (int a = 0; a < 6; ++a) s += xy[b][a] * c_ref.j[k][l][b][a];
+      t[l] = s;
+    }
+#pragma unroll
+    for (int d = 0; d < 2; ++d)
+      bufv[(long)e * 12 + k * 2 + d] = el.area * (el.gl[0][d] * t[0] + el.gl[1][d] * t[1] + el.gl[2][d] * t[2]);
+  }
+  double sb[2];
+#pragma unroll
+  for (int d = 0; d < 2; ++d) sb[d] = -el.area * (el.gl[0][d] * tg[0] + el.gl[1][d] * tg[1] + el.gl[2][d] * tg[2]);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) bufm[(long)e * 3 + m] = sb[0] * el.gl[m][0] + sb[1] * el.gl[m][1];
+}
+
+struct LoadWeights {
+  const double *z[5];   // adjoint weights of the loads of df/dphi_p, _N, _s, _a, df/dPhi (may be null)
+};
+
+// gradient of sum_i z_i^T F_i with respect to (phi_p, phi_N, phi_s, Phi):
+// int (sum_i d g_i / d var) z_i psi_m, Hessian of eqn:appPotential at the
+// 20-point rule -> buf [4][E][3]
+__global__ void k_adj_loads(Geo g, const double *__restrict__ pp, const double *__restrict__ pn,
+                            const double *__restrict__ ps, const double *__restrict__ Ph, LoadWeights lw,
+                            double *buf) {
+  const int E = 2 * g.n * g.n;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  Elem el;
+  element(g, e, el);
+  double fp[3], fn[3], fs[3], fv[3], zz[5][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    fp[k] = pp[el.v1[k]]; fn[k] = pn[el.v1[k]]; fs[k] = ps[el.v1[k]]; fv[k] = Ph[el.v1[k]];
+  }
+  for (int i = 0; i < 5; ++i)
+    for (int k = 0; k < 3; ++k) zz[i][k] = lw.z[i] ? lw.z[i][el.v1[k]] : 0.0;
+  double acc[4][3];
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) acc[f][a] = 0.0;
+  for (int q = 0; q < 20; ++q) {
+    const double l0 = c_ref.qlam[q][0], l1 = c_ref.qlam[q][1], l2 = c_ref.qlam[q][2], w = c_ref.qw[q];
+    const double p = l0 * fp[0] + l1 * fp[1] + l2 * fp[2];
+    const double nn = l0 * fn[0] + l1 * fn[1] + l2 * fn[2];
+    const double s = l0 * fs[0] + l1 * fs[1] + l2 * fs[2];
+    const double V = l0 * fv[0] + l1 * fv[1] + l2 * fv[2];
+    const double a = 1.0 - p - nn - s;
+    double z[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) z[i] = l0 * zz[i][0] + l1 * zz[i][1] + l2 * zz[i][2];
+    const double q_ = V * V * (3.0 - 2.0 * V), dq = 6.0 * V * (1.0 - V), ddq = 6.0 - 12.0 * V;
+    const double liq = 3.5 * p * p * nn * nn + 0.3 * s * s + 0.3 * a * a - 10.0 * s * a;
+    const double gas = 3.5 * p * p + 3.5 * nn * nn + 2.0 * s * s + 0.1 * a * a;
+    // Hessian in (p, N, s, a, Phi)
+    const double Hpp = (1 - q_) * 7.0 * nn * nn + 7.0 * q_, HpN = (1 - q_) * 14.0 * p * nn;
+    const double HNN = (1 - q_) * 7.0 * p * p + 7.0 * q_;
+    const double Hss = (1 - q_) * 0.6 + 4.0 * q_, Hsa = -(1 - q_) * 10.0, Haa = (1 - q_) * 0.6 + 0.2 * q_;
+    const double HpV = dq * 7.0 * p * (1 - nn * nn), HNV = dq * 7.0 * nn * (1 - p * p);
+    const double HsV = dq * (3.4 * s + 10.0 * a), HaV = dq * (10.0 * s - 0.4 * a), HVV = ddq * (gas - liq);
+    // sum_i z_i dg_i/dphi_j with dg_i/dphi_j = H_ij - H_ia (phi_a = 1 - sum phi)
+    const double gp = z[0] * Hpp + z[1] * HpN + z[4] * HpV;                 // H_ia = 0 for i = p, N
+    const double gn = z[0] * HpN + z[1] * HNN + z[4] * HNV;
+    const double gs = z[2] * (Hss - Hsa) + z[3] * (Hsa - Haa) + z[4] * (HsV - HaV);
+    const double ga_s = -(z[2] * Hsa + z[3] * Haa + z[4] * HaV);            // the -H_ia part for j = p, N
+    const double gV = z[0] * HpV + z[1] * HNV + z[2] * HsV + z[3] * HaV + z[4] * HVV;
+    const double gj[4] = {gp + ga_s, gn + ga_s, gs, gV};
+    const double lam[3] = {l0, l1, l2};
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int aa = 0; aa < 3; ++aa) acc[f][aa] += w * gj[f] * lam[aa];
+  }
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa) buf[(long)f * E * 3 + (long)e * 3 + aa] = el.area * acc[f][aa];
+}
+
+// gradient of y^T G (Korteweg load) with respect to (phi_p, phi_N, phi_s,
+// Phi): grad psi_m . (Y + Y^T)(beta_j g_j - beta_a g_a), Y = int grad y
+// -> buf [4][E][3]
+__global__ void k_adj_korteweg(Geo g, const double *__restrict__ pp, const double *__restrict__ pn,
+                               const double *__restrict__ ps, const double *__restrict__ Ph,
+                               const double *__restrict__ y, KortewegCoef kc, double *buf) {
+  const int E = 2 * g.n * g.n;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  Elem el;
+  element(g, e, el);
+  double Y[2][2] = {{0, 0}, {0, 0}};   // Y[c][b] = int d_b y_c
+  for (int a = 0; a < 6; ++a) {
+    double ga[2];
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+      ga[b] = el.gl[0][b] * c_ref.g[a][0] + el.gl[1][b] * c_ref.g[a][1] + el.gl[2][b] * c_ref.g[a][2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const double yc = y[2 * el.v2[a] + c];
+      Y[c][0] += el.area * yc * ga[0];
+      Y[c][1] += el.area * yc * ga[1];
+    }
+  }
+  const double S[2][2] = {{2 * Y[0][0], Y[0][1] + Y[1][0]}, {Y[0][1] + Y[1][0], 2 * Y[1][1]}};
+  double gr[5][2];
+  const double *fld[4] = {pp, pn, ps, Ph};
+  for (int f = 0; f < 4; ++f) {
+    const int dst = f < 3 ? f : 4;
+    gr[dst][0] = gr[dst][1] = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double xv = fld[f][el.v1[k]];
+      gr[dst][0] += xv * el.gl[k][0];
+      gr[dst][1] += xv * el.gl[k][1];
+    }
+  }
+  gr[3][0] = -(gr[0][0] + gr[1][0] + gr[2][0]);
+  gr[3][1] = -(gr[0][1] + gr[1][1] + gr[2][1]);
+  for (int f = 0; f < 4; ++f) {
+    double u[2];
+    if (f < 3) {
+      u[0] = kc.beta[f] * gr[f][0] - kc.beta[3] * gr[3][0];
+      u[1] = kc.beta[f] * gr[f][1] - kc.beta[3] * gr[3][1];
+    } else {
+      u[0] = kc.beta_v * gr[4][0];
+      u[1] = kc.beta_v * gr[4][1];
+    }
+    const double su0 = S[0][0] * u[0] + S[0][1] * u[1], su1 = S[1][0] * u[0] + S[1][1] * u[1];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) buf[(long)f * E * 3 + (long)e * 3 + m] = el.gl[m][0] * su0 + el.gl[m][1] * su1;
+  }
+}
+
+}  // namespace
+
+void launch_adj_conv_p1(Geo g, const double *x, const double *y, double *buf, cudaStream_t s) {
+  k_adj_conv_p1<<<blocks_for(2L * g.n * g.n), TPB, 0, s>>>(g, x, y, buf);
+  CHNSS_LAUNCH_CK();
+}
+void launch_adj_conv_p2(Geo g, const double *x, const double *y, double *bufv, double *bufm, cudaStream_t s) {
+  k_adj_conv_p2<<<blocks_for(2L * g.n * g.n), TPB, 0, s>>>(g, x, y, bufv, bufm);
+  CHNSS_LAUNCH_CK();
+}
+void launch_adj_loads(Geo g, const double *pp, const double *pn, const double *ps, const double *Ph,
+                      const double *const *z, double *buf, cudaStream_t s) {
+  LoadWeights lw;
+  for (int i = 0; i < 5; ++i) lw.z[i] = z[i];
+  k_adj_loads<<<blocks_for(2L * g.n * g.n), TPB, 0, s>>>(g, pp, pn, ps, Ph, lw, buf);
+  CHNSS_LAUNCH_CK();
+}
+void launch_adj_korteweg(Geo g, const double *pp, const double *pn, const double *ps, const double *Ph,
+                         const double *y, KortewegCoef c, double *buf, cudaStream_t s) {
+  k_adj_korteweg<<<blocks_for(2L * g.n * g.n), TPB, 0, s>>>(g, pp, pn, ps, Ph, y, c, buf);
+  CHNSS_LAUNCH_CK();
+}
+
+}  // namespace chnss

@@ -136,6 +136,12 @@ struct chnss_ctx {
   bool assembled = false;
   bool ch_done[3] = {false, false, false};
   double *hin = nullptr, *hout = nullptr;   // device staging of chnss_step_host
+  // adjoint step (allocated on first use): transposed fine operators, work
+  double *LsT = nullptr, *ACsT = nullptr, *AsT = nullptr;
+  double *topv = nullptr, *mvec = nullptr;  // int_Gt psi, M 1
+  double *arhs = nullptr, *ay = nullptr, *alam = nullptr, *az = nullptr, *atmp = nullptr, *atv = nullptr;
+  double *alw[5] = {};
+  double *adots = nullptr;                  // device scalars of the parameter gradients
   const Level &lv(int l) const { return mesh->m.lv[l]; }
   ~chnss_ctx() {
     for (PrecGraph &g : pg) {
@@ -1088,5 +1094,270 @@ extern "C" chnss_status chnss_mass_solve_noalloc(chnss_ctx_t ctx, const double *
     throw Error{CHNSS_ERR_ARG, "chnss_mass_solve_noalloc supports at most " + std::to_string(kNoAllocMaxN1) +
                                    " P1 nodes (a 256 x 256 mesh); this mesh has " + std::to_string(ctx->N1)};
   return mass_solve_noalloc(ctx, rhs, x_out, info);
+  ABI_CATCH(ctx)
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint step: for each solve x = A(u)^-1 b(u) of the step, given the
+// adjoint xbar of its solution, y = A^-T xbar (FGMRES on the transposed
+// operator, preconditioned by the forward preconditioner), then
+// ubar += (db/du)^T y - (d(A(u) x)/du)^T y (adjoint element kernels).
+namespace {
+
+constexpr double kAdjointRtol = 1e-12;
+
+__global__ void k_top_load_vec(int N1, int n, double hx, double *out) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i < N1) out[i] = top_load(i, n, hx);
+}
+__global__ void k_mask_velocity(int N2, const double *in, const int *bnd, double *out) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i >= N2) return;
+  out[2 * i] = bnd[i] ? 0.0 : in[2 * i];
+  out[2 * i + 1] = bnd[i] ? 0.0 : in[2 * i + 1];
+}
+// out = lp - m * sum(lp) / area (transpose of the zero-mean pressure shift)
+__global__ void k_mean_shift_T(int N1, const double *lp, const double *m, const double *sum, double area, double *out) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i < N1) out[i] = lp[i] - m[i] * (*sum) / area;
+}
+__global__ void k_add_at(double *x, int idx, double v) { x[idx] += v; }
+
+struct CHOpT : LinearOperator {   // [[L^T, a21 K], [a12 K12, a22 M]]
+  chnss_ctx *c;
+  int sp;
+  CHOpT(chnss_ctx *c_, int sp_) : c(c_), sp(sp_) {}
+  long size() const override { return 2L * c->N1; }
+  void apply(const double *x, double *y, cudaStream_t s) override {
+    const auto &p = c->p;
+    const double tau = p.tau, g = p.gamma[sp], b = p.beta[sp];
+    const bool var = p.mobility_kind != 0;
+    // y1 = L^T x1 + tau g K x2 ; y2 = (var ? tau K_kappa : tau g K) x1 - (tau g / b) M x2
+    spmv_sell_ch(c->lv(0).p1, c->LsT, c->Ks, nullptr, c->Ms, tau * g, tau * g, -tau * g / b, x, y, s);
+    if (var) throw Error{CHNSS_ERR_ARG, "the adjoint step supports constant mobility only"};
+  }
+  void precond(const double *r, double *z, cudaStream_t) override { run_prec(c, sp, r, z); }
+  void after_sync() override { harvest_probes(c); }
+};
+
+struct ACOpT : LinearOperator {
+  chnss_ctx *c;
+  explicit ACOpT(chnss_ctx *c_) : c(c_) {}
+  long size() const override { return c->N1; }
+  void apply(const double *x, double *y, cudaStream_t s) override {
+    SpmvArgs none;
+    spmv_sell<double>(c->lv(0).p1, c->ACsT, 1, x, y, SPMV_PLAIN, none, s);
+  }
+  void precond(const double *r, double *z, cudaStream_t) override { run_prec(c, 3, r, z); }
+  void after_sync() override { harvest_probes(c); }
+};
+
+struct NSOpT : LinearOperator {   // [[A^T, B^T], [B, 0]]
+  chnss_ctx *c;
+  explicit NSOpT(chnss_ctx *c_) : c(c_) {}
+  long size() const override { return 2L * c->N2 + c->N1; }
+  void apply(const double *x, double *y, cudaStream_t s) override {
+    const long nv = 2L * c->N2;
+    SpmvArgs none;
+    spmv_sell_bsr2<double>(c->lv(0).p2, c->AsT, x, y, SPMV_PLAIN, none, s);
+    spmv_sell_bt_add(c->mesh->m.pbt, c->Bts, x + nv, y, s);
+    spmv_sell_b(c->mesh->m.pb, c->Bs, x, y + nv, s);
+  }
+  void precond(const double *r, double *z, cudaStream_t) override { run_prec(c, 4, r, z); }
+  void after_sync() override { harvest_probes(c); }
+};
+
+void adjoint_alloc(chnss_ctx *c) {
+  if (c->LsT) return;
+  Arena &ar = c->ar;
+  const Level &F = c->lv(0);
+  const long N1 = c->N1, nmax = 2L * c->N2 + c->N1;
+  c->LsT = ar.alloc<double>(F.p1.sell.nent);
+  c->ACsT = ar.alloc<double>(F.p1.sell.nent);
+  c->AsT = ar.alloc<double>(4L * F.p2.sell.nent);
+  c->topv = ar.alloc<double>(N1);
+  c->mvec = ar.alloc<double>(N1);
+  c->arhs = ar.alloc<double>(nmax);
+  c->ay = ar.alloc<double>(nmax);
+  c->alam = ar.alloc<double>(3 * N1);
+  c->az = ar.alloc<double>(N1);
+  c->atmp = ar.alloc<double>(N1);
+  c->atv = ar.alloc<double>(2L * c->N2);
+  for (double *&w : c->alw) w = ar.alloc<double>(N1);
+  c->adots = ar.alloc<double>(32);
+  k_top_load_vec<<<nb(N1), TPB, 0, c->s>>>((int)N1, F.n, F.hx, c->topv);
+  CHNSS_LAUNCH_CK();
+  vec_fill(N1, 1.0, c->atmp, c->s);
+  SpmvArgs none;
+  spmv_csr<double>(F.p1, c->M1[0], 1, c->atmp, c->mvec, SPMV_PLAIN, none, c->s);
+}
+
+// out += alpha * (per-element P1 contributions gathered to nodes)
+void gather_p1_add(chnss_ctx *c, const double *buf, double alpha, double *out) {
+  launch_gather(c->mesh->m.g_l1, 1, buf, alpha, out, 1.0, out, c->s);
+}
+
+chnss_status adjoint_step(chnss_ctx *c, const chnss_state *stk, const chnss_state *st1, const chnss_state *lam,
+                          chnss_state *out, double *grad, chnss_solve_info *info) {
+  const auto &p = c->p;
+  if (p.mobility_kind != 0) throw Error{CHNSS_ERR_ARG, "the adjoint step supports constant mobility only"};
+  adjoint_alloc(c);
+  assemble(c, stk);
+  cudaStream_t s = c->s;
+  const Mesh &m = c->mesh->m;
+  const Level &F = m.lv[0];
+  const Geo g0 = geo(F);
+  const int N1 = c->N1, E = c->E;
+  const long nv = 2L * c->N2;
+  const double tau = p.tau;
+  chnss_solve_info loc[6];
+  chnss_solve_info *inf = info ? info : loc;
+  chnss_status worst = CHNSS_OK;
+  auto keep = [&](chnss_status st) { if (worst == CHNSS_OK) worst = st; };
+  SpmvArgs none;
+  // transposed fine operators
+  sell_gather_transposed(F.p1.sell, 1, c->L[0], c->LsT, s);
+  sell_gather_transposed(F.p1.sell, 1, c->AC[0], c->ACsT, s);
+  sell_gather_transposed(F.p2.sell, 4, c->A[0], c->AsT, s);
+  for (int k = 0; k < 3; ++k) vec_fill(N1, 0.0, out->phi[k], s);
+  for (int k = 0; k < 4; ++k) vec_fill(N1, 0.0, out->mu[k], s);
+  vec_fill(N1, 0.0, out->Phi_v, s);
+  vec_fill(nv, 0.0, out->v, s);
+  vec_fill(N1, 0.0, out->p, s);
+  vec_fill(32, 0.0, c->adots, s);
+  double *D = c->adots;
+  // ---- Navier-Stokes -------------------------------------------------------
+  k_mask_velocity<<<nb(c->N2), TPB, 0, s>>>(c->N2, lam->v, F.bnd2, c->arhs);
+  CHNSS_LAUNCH_CK();
+  vsum<double>(N1, lam->p, c->sum, c->partial, s);
+  k_mean_shift_T<<<nb(N1), TPB, 0, s>>>(N1, lam->p, c->mvec, c->sum, m.lx * m.ly, c->arhs + nv);
+  CHNSS_LAUNCH_CK();
+  {
+    NSOpT op(c);
+    keep(fgmres(op, c->arhs, c->ay, kAdjointRtol, 0.0, p.maxit, c->kw, &inf[5], s, &c->prof));
+  }
+  const double *yv = c->ay;
+  spmv_csr<double>(F.p2, c->M2v[0], 2, yv, c->atv, SPMV_PLAIN, none, s);
+  vec_axpby(nv, 1.0 / tau, c->atv, 1.0, out->v, s);                       // (M_v / tau)^T y_v
+  KortewegCoef kc;
+  for (int f = 0; f < 4; ++f) kc.beta[f] = p.beta[f];
+  kc.beta_v = p.beta_v;
+  launch_adj_korteweg(g0, stk->phi[0], stk->phi[1], stk->phi[2], stk->Phi_v, yv, kc, c->lbuf, s);
+  for (int f = 0; f < 3; ++f) gather_p1_add(c, c->lbuf + (long)f * E * 3, 1.0, out->phi[f]);
+  gather_p1_add(c, c->lbuf + 3L * E * 3, 1.0, out->Phi_v);
+  launch_adj_conv_p2(g0, st1->v, yv, c->ebuf, c->ebuf + 12L * E, s);
+  launch_gather(m.g_l2, 2, c->ebuf, -1.0, out->v, 1.0, out->v, s);       // - (dJ(w)x/dv)^T y
+  launch_gather(m.g_l1, 1, c->ebuf + 12L * E, 1.0, nullptr, 0.0, c->atmp, s);
+  for (int i = 0; i < 4; ++i) vec_axpby(N1, -p.alpha[i], c->atmp, 1.0, out->mu[i], s);
+  // ---- air potential -------------------------------------------------------
+  keep(pcg(F.p1, c->M1[0], c->dinvM, lam->mu[3], c->az, kAdjointRtol, 1000, c->kw, &inf[4], s));
+  spmv_csr<double>(F.p1, c->K1[0], 1, c->az, c->atmp, SPMV_PLAIN, none, s);
+  for (int i = 0; i < 3; ++i) {
+    vec_copy(N1, lam->phi[i], c->alam + (long)i * N1, s);
+    vec_axpby(N1, -p.beta[3], c->atmp, 1.0, c->alam + (long)i * N1, s);
+  }
+  vec_copy(N1, c->az, c->alw[3], s);
+  dot<double>(N1, c->topv, c->az, D + 0, c->partial, s);
+  // ---- Allen-Cahn ----------------------------------------------------------
+  {
+    ACOpT op(c);
+    keep(fgmres(op, lam->Phi_v, c->ay, kAdjointRtol, 0.0, p.maxit, c->kw, &inf[3], s, &c->prof));
+  }
+  spmv_csr<double>(F.p1, c->M1[0], 1, c->ay, c->atmp, SPMV_PLAIN, none, s);
+  vec_axpby(N1, 1.0, c->atmp, 1.0, out->Phi_v, s);
+  vec_fill(N1, 0.0, c->alw[4], s);
+  vec_axpby(N1, -tau * p.gamma_v, c->ay, 0.0, c->alw[4], s);
+  launch_adj_conv_p1(g0, st1->Phi_v, c->ay, c->ebuf, s);
+  launch_gather(m.g_l2, 2, c->ebuf, -tau, out->v, 1.0, out->v, s);
+  dot<double>(N1, c->topv, c->ay, D + 1, c->partial, s);
+  // ---- Cahn-Hilliard -------------------------------------------------------
+  for (int i = 0; i < 3; ++i) {
+    vec_copy(N1, c->alam + (long)i * N1, c->arhs, s);
+    vec_copy(N1, lam->mu[i], c->arhs + N1, s);
+    {
+      CHOpT op(c, i);
+      keep(fgmres(op, c->arhs, c->ay, kAdjointRtol, 0.0, p.maxit, c->kw, &inf[i], s, &c->prof));
+    }
+    const double *y1 = c->ay, *y2 = c->ay + N1;
+    const double cc = tau * p.gamma[i] / p.beta[i];
+    spmv_csr<double>(F.p1, c->M1[0], 1, y1, c->atmp, SPMV_PLAIN, none, s);
+    vec_axpby(N1, 1.0, c->atmp, 1.0, out->phi[i], s);
+    vec_fill(N1, 0.0, c->alw[i], s);
+    vec_axpby(N1, -cc, y2, 0.0, c->alw[i], s);
+    launch_adj_conv_p1(g0, st1->phi[i], y1, c->ebuf, s);
+    launch_gather(m.g_l2, 2, c->ebuf, -tau, out->v, 1.0, out->v, s);
+    double *d = D + 4 + 5 * i;
+    dot<double>(N1, c->loads + (long)i * N1, y2, d + 0, c->partial, s);    // F_i . y2
+    dot<double>(N1, c->topv, y2, d + 1, c->partial, s);                     // t . y2
+    spmv_csr<double>(F.p1, c->K1[0], 1, st1->mu[i], c->atmp, SPMV_PLAIN, none, s);
+    dot<double>(N1, y1, c->atmp, d + 2, c->partial, s);                     // y1 . K mu'
+    spmv_csr<double>(F.p1, c->K1[0], 1, st1->phi[i], c->atmp, SPMV_PLAIN, none, s);
+    dot<double>(N1, y2, c->atmp, d + 3, c->partial, s);                     // y2 . K phi'
+    spmv_csr<double>(F.p1, c->M1[0], 1, st1->mu[i], c->atmp, SPMV_PLAIN, none, s);
+    dot<double>(N1, y2, c->atmp, d + 4, c->partial, s);                     // y2 . M mu'
+  }
+  // ---- potential loads ------------------------------------------------------
+  const double *lw[5] = {c->alw[0], c->alw[1], c->alw[2], c->alw[3], c->alw[4]};
+  launch_adj_loads(g0, stk->phi[0], stk->phi[1], stk->phi[2], stk->Phi_v, lw, c->lbuf, s);
+  for (int f = 0; f < 3; ++f) gather_p1_add(c, c->lbuf + (long)f * E * 3, 1.0, out->phi[f]);
+  gather_p1_add(c, c->lbuf + 3L * E * 3, 1.0, out->Phi_v);
+  // ---- parameter gradients --------------------------------------------------
+  double h[24], phis_ref = 0.0;
+  CHNSS_CK(cudaMemcpyAsync(h, D, 24 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CHNSS_CK(cudaMemcpyAsync(&phis_ref, stk->phi[2] + m.ref_node, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CHNSS_CK(cudaStreamSynchronize(s));
+  const double j_out = p.evap_rate * (phis_ref - p.phi_s_inf);
+  double jbar = p.beta[3] * h[0] + (p.ac_top_flux ? tau * p.delta_v * h[1] : 0.0);
+  double gbar = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    const double *d = h + 4 + 5 * i;
+    const double b_i = p.beta[i];
+    const double cc = tau * p.gamma[i] / b_i;
+    if (i == 2) jbar += cc * b_i * d[1];                                      // f_s = F_s - beta_s j t
+    const double fy = d[0] - (i == 2 ? b_i * j_out * d[1] : 0.0);
+    gbar += -(tau / b_i) * fy - tau * d[2] - (tau * d[3] - (tau / b_i) * d[4]);
+  }
+  k_add_at<<<1, 1, 0, s>>>(out->phi[2], m.ref_node, jbar * p.evap_rate);
+  CHNSS_LAUNCH_CK();
+  if (grad) {
+    grad[0] += jbar * (phis_ref - p.phi_s_inf);
+    grad[1] += gbar;
+  }
+  return worst;
+}
+
+}  // namespace
+
+extern "C" chnss_status chnss_adjoint_step(chnss_ctx_t ctx, const chnss_state *state_k, const chnss_state *state_k1,
+                                           const chnss_state *adj_k1, chnss_state *adj_k, double *grad_params,
+                                           chnss_solve_info *info) {
+  if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
+  ABI_TRY
+  check_state(state_k);
+  check_state(state_k1);
+  check_state(adj_k1);
+  check_state(adj_k);
+  const chnss_status st = adjoint_step(ctx, state_k, state_k1, adj_k1, adj_k, grad_params, info);
+  if (st != CHNSS_OK) ctx->err = "an adjoint solve did not converge cleanly (status " + std::to_string(st) + ")";
+  return st;
+  ABI_CATCH(ctx)
+}
+
+extern "C" chnss_status chnss_objective(chnss_ctx_t ctx, const double *phi_p, double *J, double *grad_phi_p) {
+  if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
+  ABI_TRY
+  if (!phi_p || !J) throw Error{CHNSS_ERR_ARG, "null phi_p or J"};
+  adjoint_alloc(ctx);
+  const Level &F = ctx->lv(0);
+  SpmvArgs none;
+  spmv_csr<double>(F.p1, ctx->K1[0], 1, phi_p, ctx->atmp, SPMV_PLAIN, none, ctx->s);
+  dot<double>(ctx->N1, phi_p, ctx->atmp, ctx->adots + 30, ctx->partial, ctx->s);
+  if (grad_phi_p) {
+    vec_fill(ctx->N1, 0.0, grad_phi_p, ctx->s);
+    vec_axpby(ctx->N1, 2.0, ctx->atmp, 0.0, grad_phi_p, ctx->s);
+  }
+  CHNSS_CK(cudaMemcpyAsync(J, ctx->adots + 30, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+  CHNSS_CK(cudaStreamSynchronize(ctx->s));
+  return CHNSS_OK;
   ABI_CATCH(ctx)
 }

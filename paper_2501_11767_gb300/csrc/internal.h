@@ -91,6 +91,7 @@ struct Sell {
   int *rowid = nullptr;          // [nslices * 32] CSR row of each slot, -1 = padding
   int *col = nullptr;            // [nent] column (padding: a valid column, value 0)
   int *map = nullptr;            // [nent] CSR position, -1 = padding
+  int *mapT = nullptr;           // [nent] CSR position of the transposed entry (square symmetric patterns)
 };
 
 struct Pattern {
@@ -198,6 +199,15 @@ void launch_gather(const Gather &g, int ncomp, const double *buf, double alpha, 
 // velocity blocks: out[4k..4k+3] = base[4k..] + alpha * sum(buf) * I2
 void launch_gather_diag2(const Gather &g, const double *buf, double alpha, const double *base, double *out,
                          cudaStream_t s);
+
+// adjoint (transposed Jacobian) element kernels
+void launch_adj_conv_p1(Geo g, const double *x, const double *y, double *buf, cudaStream_t s);   // [E][6][2]
+void launch_adj_conv_p2(Geo g, const double *x, const double *y, double *bufv, double *bufm,
+                        cudaStream_t s);                                                        // [E][6][2], [E][3]
+void launch_adj_loads(Geo g, const double *pp, const double *pn, const double *ps, const double *Ph,
+                      const double *const *z, double *buf, cudaStream_t s);                   // [4][E][3]
+void launch_adj_korteweg(Geo g, const double *pp, const double *pn, const double *ps, const double *Ph,
+                         const double *y, KortewegCoef c, double *buf, cudaStream_t s);       // [4][E][3]
 
 void launch_inject_p1(int nf, const double *fine, double *coarse, cudaStream_t s);
 void launch_inject_vel(int nf, const double *fine, double *coarse, cudaStream_t s);

@@ -33,6 +33,9 @@ void spmv_bsr2(const Pattern &P, const T *val, const T *u, T *out, SpmvMode mode
 // ncomp (1, 2 or 4) values per entry, out[e * ncomp + c].
 template <typename Tout>
 void sell_gather(const Sell &S, int ncomp, const double *csr_vals, Tout *out, cudaStream_t s);
+// SELL values of the transposed matrix (square symmetric patterns; for
+// ncomp = 4 each 2x2 block is transposed as well)
+void sell_gather_transposed(const Sell &S, int ncomp, const double *csr_vals, double *out, cudaStream_t s);
 template <typename T>
 void spmv_sell(const Pattern &P, const T *sval, int ncomp, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
                cudaStream_t s);

@@ -170,6 +170,26 @@ void build_sell(Arena &ar, Pattern &P, std::vector<int> *hmap = nullptr) {
   s.rowid = ar.upload(rowid);
   s.col = ar.upload(col);
   s.map = ar.upload(map);
+  if (P.nrows == P.ncols) {   // transposed values: entry (i, j) takes the CSR value at (j, i)
+    bool symmetric = true;
+    std::vector<int> mapT(s.nent, -1);
+    for (int k = 0; k < s.nslices && symmetric; ++k) {
+      const int w = (sp[k + 1] - sp[k]) / C;
+      for (int r = 0; r < C && symmetric; ++r) {
+        const int row = rowid[(size_t)k * C + r];
+        for (int j = 0; j < w; ++j) {
+          const long e = sp[k] + (long)j * C + r;
+          if (map[e] < 0) continue;
+          const int c = col[e];
+          const int *b = P.h_col.data() + P.h_rowptr[c], *en = P.h_col.data() + P.h_rowptr[c + 1];
+          const int *it = std::lower_bound(b, en, row);
+          if (it == en || *it != row) { symmetric = false; break; }
+          mapT[e] = (int)(it - P.h_col.data());
+        }
+      }
+    }
+    if (symmetric) s.mapT = ar.upload(mapT);
+  }
   if (hmap) *hmap = std::move(map);
 }
 

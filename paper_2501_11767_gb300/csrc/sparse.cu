@@ -195,6 +195,21 @@ __global__ void k_sell_gather(long nent, int ncomp, const int *__restrict__ map,
   for (int c = 0; c < ncomp; ++c) out[e * ncomp + c] = q >= 0 ? (T)csr[(long)q * ncomp + c] : (T)0;
 }
 
+__global__ void k_sell_gather_t(long nent, int ncomp, const int *__restrict__ mapT, const double *__restrict__ csr,
+                                double *__restrict__ out) {
+  const long e = (long)blockIdx.x * TPB + threadIdx.x;
+  if (e >= nent) return;
+  const int q = mapT[e];
+  if (ncomp == 1) {
+    out[e] = q >= 0 ? csr[q] : 0.0;
+  } else {   // 2x2 block: (c, d) <- (d, c)
+    out[4 * e + 0] = q >= 0 ? csr[4L * q + 0] : 0.0;
+    out[4 * e + 1] = q >= 0 ? csr[4L * q + 2] : 0.0;
+    out[4 * e + 2] = q >= 0 ? csr[4L * q + 1] : 0.0;
+    out[4 * e + 3] = q >= 0 ? csr[4L * q + 3] : 0.0;
+  }
+}
+
 template <typename T, int NC, bool VEC>
 __global__ void __launch_bounds__(TPB) k_sell(int nslices, const int *__restrict__ sp, const int *__restrict__ rowid,
                                               const int *__restrict__ col, const T *__restrict__ val,
@@ -763,6 +778,13 @@ void sell_gather(const Sell &S, int ncomp, const double *csr_vals, Tout *out, cu
 }
 template void sell_gather<double>(const Sell &, int, const double *, double *, cudaStream_t);
 template void sell_gather<float>(const Sell &, int, const double *, float *, cudaStream_t);
+
+void sell_gather_transposed(const Sell &S, int ncomp, const double *csr_vals, double *out, cudaStream_t s) {
+  if (!S.mapT) throw Error{CHNSS_ERR_ARG, "transposed values need a square symmetric pattern"};
+  if (ncomp != 1 && ncomp != 4) throw Error{CHNSS_ERR_ARG, "transposed values: ncomp must be 1 or 4"};
+  k_sell_gather_t<<<nblocks(S.nent, TPB), TPB, 0, s>>>(S.nent, ncomp, S.mapT, csr_vals, out);
+  CHNSS_LAUNCH_CK();
+}
 
 template <typename T>
 void spmv_sell(const Pattern &P, const T *sval, int ncomp, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
