@@ -13,6 +13,7 @@ advances from step to step.  One JSON line on rank 0.
 
   python bench.py [--steps K] [--warmup W] [--gpus N]
   python bench.py --impl reference     # the CPU oracle on the same metric
+  python bench.py --sweep              # 64 independent instances, chnss_step_batched
 """
 from __future__ import annotations
 
@@ -228,6 +229,21 @@ def run_gpu(args):
                "how": "chnss_step_host: pinned host state in, H2D copy, step, D2H copy, stream sync; wall clock"}
     del ctx
 
+    bf16 = None
+    if args.bf16_steps > 0:
+        pb = dict(params, precision=2)
+        ctxb, msb, infosb, profb, _, _ = timed_run(pb, 1, args.bf16_steps, True)
+        del ctxb
+        bf16 = {"value": args.bf16_steps / (msb / 1e3), "unit": "steps/s", "steps": args.bf16_steps,
+                "ms_per_step": msb / args.bf16_steps,
+                "what": "precision 2: velocity multigrid values stored in BF16, FP32 vectors, FP64 FGMRES",
+                "converged": all(i[k]["converged"] for i in infosb for k in i),
+                "kernel_families": {k: {"ms_total": round(v["ms"], 3), "launches": v["launches"],
+                                        "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)
+                                        if v["ms"] > 0 and v["bytes"] > 0 else None}
+                                    for k, v in profb["kinds"].items() if v["launches"] > 0},
+                "iters_last_step": {k: v["iters"] for k, v in infosb[-1].items()}}
+
     fp64 = None
     if not args.no_fp64:
         p64 = dict(params, precision=0)
@@ -304,6 +320,7 @@ def run_gpu(args):
         "converged": all(i[k]["converged"] for i in infos for k in last),
         "fp64": fp64,
         "speedup_mixed_vs_fp64": round(value / fp64["value"], 3) if fp64 else None,
+        "bf16_preconditioner": bf16,
         "roofline": roofline,
         "rooflines": rooflines,
         "kernel_families": families,
@@ -335,6 +352,86 @@ def _traffic(kernel):
         return d.get(kernel, {}).get("dram_bytes_per_launch")
     except Exception:
         return None
+
+
+# ---------------------------------------------------------------------------
+SWEEP_METRIC = "aggregate time steps/s of a 64-instance parameter sweep (meshes 128^2..512^2, FGMRES to 1e-8)"
+
+
+def run_sweep(args):
+    """Batched parameter sweep: independent instances of uneven mesh size
+    and evaporation rate, one context (and stream) each, advanced together
+    by chnss_step_batched after the SpMV launch shapes of every mesh have
+    been autotuned.  Also times the same instances stepped one after the
+    other (one chnss_step at a time) for comparison."""
+    import torch
+
+    from paper_2501_11767_gb300 import chnss, inputs
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    inst = inputs.sweep_instances(args.sweep_count)
+    meshes = {n: chnss.Mesh(n) for n in sorted({i["n"] for i in inst})}
+    tuning = {}
+    for n, m in meshes.items():          # tune each mesh on a throw-away context
+        c = chnss.Context(m, inst[0]["params"])
+        c.step(chnss.state_to_device(inputs.initial_state(n, seed=0)))
+        tuning[n] = c.autotune()
+        del c
+    ctxs = [chnss.Context(meshes[i["n"]], i["params"], stream=torch.cuda.Stream()) for i in inst]
+    a = [chnss.state_to_device(inputs.initial_state(i["n"], seed=i["seed"])) for i in inst]
+    b = [c.new_state() for c in ctxs]
+    threads = args.sweep_threads or min(16, os.cpu_count() or 1)
+    for _ in range(args.warmup):
+        chnss.step_batched(ctxs, a, b, max_threads=threads)
+        a, b = b, a
+    torch.cuda.synchronize()
+    launches0 = ctxs[0].profile_read()["launches"]
+    sampler = ClockSampler(_device_uuid(torch, 0))
+    sampler.start()
+    t0 = time.perf_counter()
+    recs = None
+    for _ in range(args.steps):
+        _, recs, _ = chnss.step_batched(ctxs, a, b, max_threads=threads)
+        a, b = b, a
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    clocks = sampler.stop()
+    launches = ctxs[0].profile_read()["launches"] - launches0
+    value = len(inst) * args.steps / sec
+
+    # the same instances one at a time (one step each)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c, x, y in zip(ctxs, a, b):
+        c.step(x, y)
+        c.stream.synchronize()
+    seq = len(inst) / (time.perf_counter() - t0)
+
+    out = {
+        "metric": SWEEP_METRIC, "value": round(value, 3), "unit": "instance steps/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 outer / f32 preconditioner", "data": "synthetic (seeded SplitMix64 draws)",
+        "config": {"workload": f"sweep{len(inst)}", "instances": len(inst),
+                   "meshes": {str(n): sum(1 for i in inst if i["n"] == n) for n in meshes},
+                   "total_p1_nodes": sum((i["n"] + 1) ** 2 for i in inst),
+                   "evap_rate": [round(min(i["params"]["evap_rate"] for i in inst), 4),
+                                 round(max(i["params"]["evap_rate"] for i in inst), 4)],
+                   "host_threads": threads, "l2": "inputs larger than L2 (tens of GB resident)",
+                   "timing": "wall clock around chnss_step_batched (it returns after every stream is synchronised)"},
+        "tuning": {str(n): {"block_p1": t["block_p1"], "block_p2": t["block_p2"],
+                            "ms_p1": [round(x, 4) for x in t["ms_p1"]], "ms_p2": [round(x, 4) for x in t["ms_p2"]]}
+                   for n, t in tuning.items()},
+        "sequential": {"value": round(seq, 3), "unit": "instance steps/s",
+                       "how": "one chnss_step per instance, one after the other, same contexts"},
+        "speedup_batched_vs_sequential": round(value / seq, 3),
+        "converged": all(r[k]["converged"] for r in recs for k in r),
+        "iters_mean": {k: round(sum(r[k]["iters"] for r in recs) / len(recs), 2) for k in recs[0]},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(out))
 
 
 # ---------------------------------------------------------------------------
@@ -373,9 +470,13 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--bf16-steps", type=int, default=3)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sweep", action="store_true", help="batched 64-instance parameter sweep instead")
+    ap.add_argument("--sweep-count", type=int, default=64)
+    ap.add_argument("--sweep-threads", type=int, default=0)
     ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-steps", type=int, default=1, help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -386,6 +487,9 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     run_gpu(args)
 

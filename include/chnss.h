@@ -72,7 +72,9 @@ typedef struct {
   double evap_rate;      /* lumped Hertz-Knudsen factor: j_out = evap_rate (phi_s^vap - phi_s_inf) */
   double phi_s_inf;      /* solvent fraction of the ambient air */
   int ac_top_flux;       /* 1: also impose delta_v dPhi_v/dn = delta_v j_out on the top boundary */
-  int precision;         /* 0: FP64 throughout; 1: FP32 preconditioners inside FP64 FGMRES */
+  int precision;         /* 0: FP64 throughout; 1: FP32 preconditioners inside FP64 FGMRES;
+                            2: as 1, with the velocity multigrid's matrix values stored in BF16
+                            on every level (FP32 vectors, Jacobi diagonals and accumulation) */
   double rtol, atol;     /* stopping rule ||b - A x|| <= max(rtol ||b||, atol) (Sec. 5) */
   int restart, maxit;    /* FGMRES restart length (<= 64) and total iteration cap */
 } chnss_params;
@@ -180,7 +182,9 @@ chnss_status chnss_export_rhs(chnss_ctx_t ctx, chnss_system sys, double *host_ou
  * in this process.  Families: multigrid fine-level velocity SpMV (smoother
  * and residual sweeps), multigrid fine-level P1 SpMV, Navier-Stokes operator
  * SpMV, Krylov orthogonalisation (one record per Arnoldi step), assembly
- * with preconditioner setup (bytes not counted). */
+ * with preconditioner setup (bytes not counted), and the time of every
+ * multigrid level below the finest, per V-cycle, for the P1 and the velocity
+ * hierarchies (bytes not counted). */
 typedef struct {
   long long launches;          /* kernels launched by the library in this process */
   int nkinds;
@@ -218,6 +222,46 @@ chnss_status chnss_profile_read(chnss_ctx_t ctx, chnss_profile *out);
  * issued.  Synchronises ctx's stream once per iteration. */
 chnss_status chnss_mass_solve_noalloc(chnss_ctx_t ctx, const double *rhs, double *x_out,
                                       chnss_solve_info *info);
+
+/* Batched step for parameter sweeps (Sec. 5 runs the model over ranges of
+ * evaporation rates and mesh sizes; every run is an independent time
+ * integration).  Advances n_inst independent contexts by one chnss_step
+ * each, concurrently: up to max_threads host threads (<= 0: one per
+ * instance) each drive whole steps of one context at a time on that
+ * context's own stream, so the instances' kernels overlap on the GPU.
+ * ctxs[i] must be distinct (one context is not thread-safe), may differ in
+ * mesh and parameters, and must all belong to the calling thread's current
+ * device.  in[i] / out[i]: DEVICE states of ctxs[i] (chnss_step aliasing
+ * rules); info (optional): 6 records per instance, instance i at
+ * info + 6 i.  Each out[i] is bit-identical to chnss_step(ctxs[i], ...).
+ * On failure every instance has still been attempted; the status and
+ * message (chnss_last_error(NULL)) are those of the lowest failing index.
+ * Returns after all instances' streams are synchronised. */
+chnss_status chnss_step_batched(int n_inst, chnss_ctx_t *ctxs, const chnss_state *in, chnss_state *out,
+                                chnss_solve_info *info, int max_threads);
+
+/* Launch-shape autotuner.  Times the fine-level SpMV of the scalar (P1) and
+ * of the velocity (2x2-block) multigrid operator of ctx for threads-per-block
+ * 128, 256 and 512, keeps the fastest for each family (all levels and the
+ * transfers of that family), and re-captures ctx's preconditioner graphs.
+ * The choice is stored in the MESH, so it applies to every context sharing
+ * it (contexts created earlier keep their captured shapes until they are
+ * re-tuned).  Results do not depend on the launch shape: every row is summed
+ * by one thread in the same order for any block size.  Needs an assembled
+ * context (CHNSS_ERR_STATE otherwise).  out (host, optional): the timings
+ * (ms per SpMV) and the choices. */
+typedef struct {
+  int candidates[3];   /* threads per block tried */
+  double ms_p1[3];     /* fine scalar SpMV, ms */
+  double ms_p2[3];     /* fine velocity SpMV, ms */
+  int block_p1, block_p2;
+} chnss_tuning;
+chnss_status chnss_autotune(chnss_ctx_t ctx, chnss_tuning *out);
+/* Set the SpMV threads-per-block of the scalar and velocity families by hand
+ * (128, 256 or 512; CHNSS_ERR_ARG otherwise), with the same scope as
+ * chnss_autotune (stored in the mesh; ctx's graphs are re-captured).  Do not
+ * call it while another context on the same mesh is stepping. */
+chnss_status chnss_set_spmv_block(chnss_ctx_t ctx, int block_p1, int block_p2);
 
 /* Message of the last failure on ctx (or of the last failed create call
  * when ctx is NULL).  Valid until the next call on the same context. */

@@ -58,6 +58,15 @@ class Profile(ctypes.Structure):
         return {"launches": self.launches, "kinds": kinds}
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int * 3), ("ms_p1", ctypes.c_double * 3), ("ms_p2", ctypes.c_double * 3),
+                ("block_p1", ctypes.c_int), ("block_p2", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"candidates": list(self.candidates), "ms_p1": list(self.ms_p1), "ms_p2": list(self.ms_p2),
+                "block_p1": self.block_p1, "block_p2": self.block_p2}
+
+
 class ChnssError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"chnss {STATUS.get(status, status)}: {msg}")
@@ -95,6 +104,10 @@ EXPORTS = {
                                        ctypes.c_void_p]),
     "chnss_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
+    "chnss_step_batched": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(State),
+                                          ctypes.POINTER(State), ctypes.POINTER(SolveInfo), ctypes.c_int]),
+    "chnss_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Tuning)]),
+    "chnss_set_spmv_block": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "chnss_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
 }
 
@@ -302,6 +315,19 @@ class Context:
             _check(st, self._h)
         return x, info.as_dict(), st
 
+    def autotune(self) -> dict:
+        """Pick the SpMV threads-per-block of the mesh's scalar and velocity
+        operators by timing (chnss_autotune); re-captures this context's
+        preconditioner graphs."""
+        t = Tuning()
+        _check(load().chnss_autotune(self._h, ctypes.byref(t)), self._h)
+        return t.as_dict()
+
+    def set_spmv_block(self, block_p1: int, block_p2: int):
+        """Pin the SpMV threads-per-block of the mesh's scalar and velocity
+        operators (chnss_set_spmv_block)."""
+        _check(load().chnss_set_spmv_block(self._h, block_p1, block_p2), self._h)
+
     def profile_enable(self, on: bool = True):
         _check(load().chnss_profile_enable(self._h, 1 if on else 0), self._h)
 
@@ -314,6 +340,27 @@ class Context:
         out = np.zeros(self.system_size(sys), dtype=np.float64)
         _check(load().chnss_export_rhs(self._h, sys, out.ctypes.data), self._h)
         return out
+
+
+def step_batched(ctxs, states_in, states_out=None, max_threads: int = 0, check: bool = True):
+    """One chnss_step of every context, concurrently (chnss_step_batched).
+    Give each context its own stream (Context(..., stream=torch.cuda.Stream()))
+    or the instances serialise on the shared one.  Returns (states_out,
+    per-instance solve records, status)."""
+    n = len(ctxs)
+    if len(states_in) != n or (states_out is not None and len(states_out) != n):
+        raise ValueError("one input (and output) state per context")
+    if states_out is None:
+        states_out = [c.new_state() for c in ctxs]
+    hs = (ctypes.c_void_p * n)(*[c._h.value for c in ctxs])
+    a = (State * n)(*[make_state(x) for x in states_in])
+    b = (State * n)(*[make_state(x) for x in states_out])
+    infos = (SolveInfo * (6 * n))()
+    st = load().chnss_step_batched(n, hs, a, b, infos, max_threads)
+    if check:
+        _check(st, None)
+    recs = [{SYSTEM_NAMES[k]: infos[6 * i + k].as_dict() for k in range(6)} for i in range(n)]
+    return states_out, recs, st
 
 
 def state_to_device(state: dict, device="cuda") -> dict:

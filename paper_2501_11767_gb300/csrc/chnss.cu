@@ -8,6 +8,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 
 #include "solver.h"
 
@@ -355,6 +356,10 @@ void init_precset(chnss_ctx *c, PrecSet<T> &P) {
     tvs.push_back(&c->lv(l).tv);
   }
   auto vals = [&](const std::vector<double *> &v) { return std::vector<const double *>(v.begin(), v.end()); };
+  // precision 2: BF16 values for the velocity hierarchy, where they cut the
+  // dominant SpMV stream by 40 %.  (The P1 hierarchies save only 25 % per
+  // entry and cost more CH iterations than they save: 39 -> 48 at 1024^2.)
+  P.A.bf16 = c->p.precision == 2;
   P.L.init(ar, 0, false, p1s, d1s, vals(c->L), t1s, c->partial);
   P.AC.init(ar, 0, false, p1s, d1s, vals(c->AC), t1s, c->partial);
   P.A.init(ar, 1, false, p2s, d2s, vals(c->A), tvs, c->partial);
@@ -521,7 +526,7 @@ void create_context(chnss_ctx *c) {
     c->massc = ar.upload(mc);
   }
   c->kw.init(ar, p.restart, 2L * c->N2 + c->N1, c->pinned + 8);
-  if (p.precision == 1) {
+  if (p.precision >= 1) {
     c->p32.reset(new PrecSet<float>());
     init_precset(c, *c->p32);
   } else {
@@ -724,7 +729,7 @@ void check_params(const chnss_params *p) {
   if (!(p->eta > 0)) throw Error{CHNSS_ERR_ARG, "eta must be > 0"};
   if (p->restart < 1 || p->restart > 64) throw Error{CHNSS_ERR_ARG, "restart must be in [1, 64]"};
   if (p->maxit < 1) throw Error{CHNSS_ERR_ARG, "maxit must be >= 1"};
-  if (p->precision != 0 && p->precision != 1) throw Error{CHNSS_ERR_ARG, "precision must be 0 or 1"};
+  if (p->precision < 0 || p->precision > 2) throw Error{CHNSS_ERR_ARG, "precision must be 0, 1 or 2"};
   if (p->mobility_kind != 0 && p->mobility_kind != 1) throw Error{CHNSS_ERR_ARG, "mobility_kind must be 0 or 1"};
   if (!(p->rtol >= 0) || !(p->atol >= 0)) throw Error{CHNSS_ERR_ARG, "tolerances must be >= 0"};
 }
@@ -1360,4 +1365,164 @@ extern "C" chnss_status chnss_objective(chnss_ctx_t ctx, const double *phi_p, do
   CHNSS_CK(cudaStreamSynchronize(ctx->s));
   return CHNSS_OK;
   ABI_CATCH(ctx)
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the SpMV launch shape and the batched step.
+namespace {
+
+constexpr int kTuneCandidates[3] = {128, 256, 512};
+
+void destroy_graphs(chnss_ctx *c) {
+  for (PrecGraph &g : c->pg) {
+    if (g.plain) cudaGraphExecDestroy(g.plain);
+    if (g.prof) cudaGraphExecDestroy(g.prof);
+    g.plain = g.prof = nullptr;
+    for (Profiler::Probe &pr : g.probes) {
+      if (pr.e0) cudaEventDestroy(pr.e0);
+      if (pr.e1) cudaEventDestroy(pr.e1);
+    }
+    g.probes.clear();
+    g.nprobes = 0;
+  }
+  if (c->cap) {
+    cudaStreamDestroy(c->cap);
+    c->cap = nullptr;
+  }
+}
+
+template <typename T>
+double time_spmv(chnss_ctx *c, MGHier<T> &h, int reps) {
+  cudaStream_t s = c->s;
+  SpmvArgs none;
+  cudaEvent_t e0, e1;
+  CHNSS_CK(cudaEventCreate(&e0));
+  CHNSS_CK(cudaEventCreate(&e1));
+  auto run = [&]() { h.spmv_level(0, h.b[0], h.t[0], SPMV_PLAIN, none, s); };
+  run();
+  run();
+  CHNSS_CK(cudaEventRecord(e0, s));
+  for (int i = 0; i < reps; ++i) run();
+  CHNSS_CK(cudaEventRecord(e1, s));
+  CHNSS_CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CHNSS_CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms / reps;
+}
+
+void set_block(chnss_ctx *c, bool velocity, int block) {
+  Mesh &m = c->mesh->m;
+  for (Level &L : m.lv) {
+    if (velocity) {
+      L.p2.sell.block = block;
+      L.tv.P.sell.block = block;
+      L.tv.R.sell.block = block;
+    } else {
+      L.p1.sell.block = block;
+      L.t1.P.sell.block = block;
+      L.t1.R.sell.block = block;
+    }
+  }
+  if (velocity) {
+    m.pbt.sell.block = block;
+  } else {
+    m.pb.sell.block = block;
+  }
+}
+
+template <typename T>
+void autotune_t(chnss_ctx *c, PrecSet<T> &P, chnss_tuning *out) {
+  for (int group = 0; group < 2; ++group) {
+    MGHier<T> &h = group == 0 ? P.L : P.A;
+    double best = 1e300;
+    int best_b = 256;
+    for (int i = 0; i < 3; ++i) {
+      set_block(c, group == 1, kTuneCandidates[i]);
+      const double ms = time_spmv(c, h, 10);
+      (group == 0 ? out->ms_p1 : out->ms_p2)[i] = ms;
+      if (ms < best) { best = ms; best_b = kTuneCandidates[i]; }
+    }
+    set_block(c, group == 1, best_b);
+    (group == 0 ? out->block_p1 : out->block_p2) = best_b;
+  }
+  for (int i = 0; i < 3; ++i) out->candidates[i] = kTuneCandidates[i];
+}
+
+}  // namespace
+
+extern "C" chnss_status chnss_autotune(chnss_ctx_t ctx, chnss_tuning *out) {
+  if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
+  ABI_TRY
+  if (!ctx->assembled) throw Error{CHNSS_ERR_STATE, "chnss_autotune needs an assembled context"};
+  chnss_tuning t{};
+  if (ctx->p32) autotune_t(ctx, *ctx->p32, &t);
+  else autotune_t(ctx, *ctx->p64, &t);
+  CHNSS_CK(cudaStreamSynchronize(ctx->s));
+  destroy_graphs(ctx);          // launch shapes are baked into captured graphs
+  capture_graphs(ctx);
+  if (out) *out = t;
+  return CHNSS_OK;
+  ABI_CATCH(ctx)
+}
+
+extern "C" chnss_status chnss_set_spmv_block(chnss_ctx_t ctx, int block_p1, int block_p2) {
+  if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
+  for (int b : {block_p1, block_p2})
+    if (b != kTuneCandidates[0] && b != kTuneCandidates[1] && b != kTuneCandidates[2])
+      return fail(ctx, CHNSS_ERR_ARG, "threads per block must be 128, 256 or 512");
+  ABI_TRY
+  CHNSS_CK(cudaStreamSynchronize(ctx->s));
+  set_block(ctx, false, block_p1);
+  set_block(ctx, true, block_p2);
+  destroy_graphs(ctx);
+  capture_graphs(ctx);
+  return CHNSS_OK;
+  ABI_CATCH(ctx)
+}
+
+extern "C" chnss_status chnss_step_batched(int n_inst, chnss_ctx_t *ctxs, const chnss_state *in, chnss_state *out,
+                                           chnss_solve_info *info, int max_threads) {
+  ABI_TRY
+  if (n_inst < 0 || (n_inst > 0 && (!ctxs || !in || !out))) throw Error{CHNSS_ERR_ARG, "bad batch arguments"};
+  for (int i = 0; i < n_inst; ++i) {
+    if (!ctxs[i]) throw Error{CHNSS_ERR_ARG, "null context in batch"};
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) throw Error{CHNSS_ERR_ARG, "a context appears twice in the batch"};
+    check_state(&in[i]);
+    check_state(&out[i]);
+  }
+  if (n_inst == 0) return CHNSS_OK;
+  int dev = 0;
+  CHNSS_CK(cudaGetDevice(&dev));
+  std::vector<chnss_status> st(n_inst, CHNSS_OK);
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (int i = next++; i < n_inst; i = next++) {
+      chnss_ctx *c = ctxs[i];
+      try {
+        st[i] = step(c, &in[i], &out[i], info ? info + 6L * i : nullptr);
+      } catch (const Error &e) {
+        c->err = e.msg;
+        st[i] = e.status;
+      } catch (const std::exception &e) {
+        c->err = e.what();
+        st[i] = CHNSS_ERR_CUDA;
+      }
+    }
+  };
+  const int nt = std::max(1, std::min(max_threads > 0 ? max_threads : n_inst, n_inst));
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+  for (std::thread &t : pool) t.join();
+  for (int i = 0; i < n_inst; ++i)
+    if (st[i] != CHNSS_OK) {
+      g_last_error = "instance " + std::to_string(i) + " failed with status " + std::to_string((int)st[i]) +
+                     (ctxs[i]->err.empty() ? std::string() : ": " + ctxs[i]->err);
+      return st[i];
+    }
+  return CHNSS_OK;
+  ABI_CATCH(nullptr)
 }

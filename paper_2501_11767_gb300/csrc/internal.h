@@ -82,9 +82,11 @@ struct Arena {
 // slice stores its entries column-major (entry j of the 32 rows is
 // contiguous), padded to the slice's longest row.  One thread per row, every
 // value / column load is one coalesced warp access.
+constexpr int kSellMaxBlock = 512;   // largest threads-per-block of the SELL kernels
 struct Sell {
   static constexpr int C = 32;
   static constexpr int SIGMA = 256;
+  int block = 256;               // threads per block of its SpMV launches (autotuned)
   int nslices = 0;
   long nent = 0;                 // padded entries
   int *slice_ptr = nullptr;      // [nslices + 1] first entry of each slice

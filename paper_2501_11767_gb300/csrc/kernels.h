@@ -1,6 +1,8 @@
 // Launch wrappers of the sparse, vector and reduction kernels (sparse.cu).
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "internal.h"
 
 namespace chnss {
@@ -42,6 +44,11 @@ void spmv_sell(const Pattern &P, const T *sval, int ncomp, const T *u, T *out, S
 template <typename T>
 void spmv_sell_bsr2(const Pattern &P, const T *sval, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
                     cudaStream_t s);
+// BF16-stored values, FP32 vectors and accumulation (preconditioner variant)
+void spmv_sell(const Pattern &P, const __nv_bfloat16 *sval, int ncomp, const float *u, float *out, SpmvMode mode,
+               const SpmvArgs &a, cudaStream_t s);
+void spmv_sell_bsr2(const Pattern &P, const __nv_bfloat16 *sval, const float *u, float *out, SpmvMode mode,
+                    const SpmvArgs &a, cudaStream_t s);
 void spmv_sell_ch(const Pattern &P, const double *L, const double *K, const double *k12, const double *M, double a12,
                   double a21, double a22, const double *x, double *y, cudaStream_t s);
 void spmv_sell_b(const Pattern &P, const double *sval2, const double *v, double *y, cudaStream_t s);
@@ -103,11 +110,26 @@ void ortho_update_norm(long n, const double *V, long ldv, int k, const double *h
                        double *partial, cudaStream_t s);
 void combine_columns(long n, const double *Z, long ldz, int k, const double *y, double *x, cudaStream_t s);
 
+// CGS2 in three passes with the vector count k as a compile-time constant
+// (k <= 31; cgs2_fast(k) says whether it applies):
+//   h1 = V^T w;   w -= V h1, h2w[0..k) = V^T w, h2w[k] = w^T w;
+//   vout = (w - V h2) / *hn   (the next basis vector).
+bool cgs2_fast(int k);
+void cgs2_dots(long n, const double *V, long ld, int k, const double *w, double *h1, double *partial,
+               cudaStream_t s);
+void cgs2_update_dots(long n, const double *V, long ld, int k, const double *h1, double *w, double *h2w,
+                      double *partial, cudaStream_t s);
+void cgs2_update_scale(long n, const double *V, long ld, int k, const double *h2, const double *w, const double *hn,
+                       double *vout, cudaStream_t s);
+
 // Arnoldi bookkeeping on one thread: H(:, j) = h1 + h2, H(j+1, j) = sqrt(nrm2),
 // previous Givens rotations, new rotation, g update.  Writes to status:
 // [0] |g_{j+1}|, [1] H(j+1, j).
 void arnoldi_finish(int j, int ldh, double *H, const double *h1, const double *h2, const double *nrm2,
                     double *cs, double *sn, double *g, double *status, cudaStream_t s);
+// the same with hn^2 = h2w[j+1] - ||h2w[0..j]||^2 (Pythagoras after CGS2)
+void arnoldi_finish_pyth(int j, int ldh, double *H, const double *h1, const double *h2w, double *cs, double *sn,
+                         double *g, double *status, cudaStream_t s);
 void hessenberg_solve(int k, int ldh, const double *H, const double *g, double *y, cudaStream_t s);
 void set_scalar(double *dst, const double *src, double scale, bool sqrt_first, cudaStream_t s);
 // PCG scalars: alpha = rz / pq

@@ -10,7 +10,8 @@ namespace chnss {
 
 const char *Profiler::name(int k) {
   static const char *names[NKINDS] = {"mg_velocity_spmv_fine", "mg_p1_spmv_fine", "ns_operator_spmv",
-                                      "krylov_orthogonalisation", "assembly"};
+                                      "krylov_orthogonalisation", "assembly", "mg_p1_coarse_levels",
+                                      "mg_velocity_coarse_levels"};
   return k >= 0 && k < NKINDS ? names[k] : "?";
 }
 
@@ -37,7 +38,7 @@ void Profiler::start(int k, cudaStream_t s) {
   CHNSS_CK(cudaEventRecord(r.ev[r.used], s));
 }
 
-void Profiler::stop(int k, cudaStream_t s, double bytes, double flops) {
+void Profiler::stop(int k, cudaStream_t s, double bytes, double flops, int count) {
   if (sink) {
     if (sink_used < sink->size()) {
       Probe &p = (*sink)[sink_used++];
@@ -51,7 +52,7 @@ void Profiler::stop(int k, cudaStream_t s, double bytes, double flops) {
   if (r.used + 2 > r.ev.size()) return;
   CHNSS_CK(cudaEventRecord(r.ev[r.used + 1], s));
   r.used += 2;
-  r.launches += 1;
+  r.launches += count;
   r.bytes += bytes;
   r.flops += flops;
 }
@@ -102,12 +103,13 @@ namespace {
 // algorithmic bytes of one SpMV launch: values + column indices + row
 // pointers + one read of u, one write of out, plus the extra vector streams
 // of the epilogue (b for RES, b + dinv (+ w) for CHEB, out read for ADD)
-double spmv_bytes(long nrows, long nnz, int vals_per_entry, long vec_len, size_t s, SpmvMode mode, bool has_w) {
+double spmv_bytes(long nrows, long nnz, int vals_per_entry, long vec_len, size_t sv, size_t s, SpmvMode mode,
+                  bool has_w) {
   double extra = 0.0;
   if (mode == SPMV_RES) extra = 1.0;
   if (mode == SPMV_ADD) extra = 1.0;
   if (mode == SPMV_CHEB) extra = has_w ? 3.0 : 2.0;
-  return (double)nnz * (vals_per_entry * (double)s + 4.0) + 4.0 * (nrows + 1) + (2.0 + extra) * vec_len * s;
+  return (double)nnz * (vals_per_entry * (double)sv + 4.0) + 4.0 * (nrows + 1) + (2.0 + extra) * vec_len * s;
 }
 }  // namespace
 
@@ -122,8 +124,10 @@ void MGHier<T>::init(Arena &ar, int kind_, bool singular_, const std::vector<con
   pat = pats;
   val64 = vals;
   tr = trs;
+  if (bf16 && !std::is_same<T, float>::value) throw Error{CHNSS_ERR_ARG, "BF16 values need FP32 vectors"};
   n.resize(nl);
   val.resize(nl);
+  val16.assign(nl, nullptr);
   dinv.resize(nl);
   x.resize(nl);
   t.resize(nl);
@@ -134,7 +138,13 @@ void MGHier<T>::init(Arena &ar, int kind_, bool singular_, const std::vector<con
   for (int l = 0; l < nl; ++l) {
     const long nu = (kind == 0 ? 1L : 2L) * pat[l]->nrows;
     n[l] = nu;
-    val[l] = ar.alloc<T>((kind == 0 ? 1L : 4L) * pat[l]->sell.nent);   // SELL order
+    const long nv = (kind == 0 ? 1L : 4L) * pat[l]->sell.nent;   // SELL order
+    if (bf16) {
+      val[l] = nullptr;
+      val16[l] = ar.alloc<__nv_bfloat16>(nv);
+    } else {
+      val[l] = ar.alloc<T>(nv);
+    }
     dinv[l] = ar.alloc<T>(nu);
     x[l] = ar.alloc<T>(nu);
     t[l] = ar.alloc<T>(nu);
@@ -154,7 +164,8 @@ void MGHier<T>::init(Arena &ar, int kind_, bool singular_, const std::vector<con
 template <typename T>
 void MGHier<T>::setup(cudaStream_t s) {
   for (int l = 0; l < nl; ++l) {
-    sell_gather<T>(pat[l]->sell, kind == 0 ? 1 : 4, val64[l], val[l], s);
+    if (bf16) sell_gather<__nv_bfloat16>(pat[l]->sell, kind == 0 ? 1 : 4, val64[l], val16[l], s);
+    else sell_gather<T>(pat[l]->sell, kind == 0 ? 1 : 4, val64[l], val[l], s);
     if (l == nl - 1) break;
     if (kind == 0)
       jacobi_csr<T>(*pat[l], val64[l], diag[l], dinv[l], hi[l], partial, s);
@@ -175,12 +186,25 @@ void MGHier<T>::op(int l, const T *u, T *out, SpmvMode mode, const SpmvArgs &a, 
   const int k = kind == 0 ? Profiler::P1_SPMV_L0 : Profiler::VEL_SPMV_L0;
   const bool timed = prof && l == 0;
   if (timed) prof->start(k, s);
+  spmv_level(l, u, out, mode, a, s);
+  if (timed)
+    prof->stop(k, s, spmv_bytes(pat[l]->nrows, pat[l]->nnz, kind == 0 ? 1 : 4, n[l], bf16 ? 2 : sizeof(T), sizeof(T),
+                                mode, a.w != nullptr));
+}
+
+template <typename T>
+void MGHier<T>::spmv_level(int l, const T *u, T *out, SpmvMode mode, const SpmvArgs &a, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (bf16) {
+      if (kind == 0) spmv_sell(*pat[l], val16[l], 1, u, out, mode, a, s);
+      else spmv_sell_bsr2(*pat[l], val16[l], u, out, mode, a, s);
+      return;
+    }
+  }
   if (kind == 0)
     spmv_sell<T>(*pat[l], val[l], 1, u, out, mode, a, s);
   else
     spmv_sell_bsr2<T>(*pat[l], val[l], u, out, mode, a, s);
-  if (timed)
-    prof->stop(k, s, spmv_bytes(pat[l]->nrows, pat[l]->nnz, kind == 0 ? 1 : 4, n[l], sizeof(T), mode, a.w != nullptr));
 }
 
 template <typename T>
@@ -218,7 +242,10 @@ void MGHier<T>::vcycle(int l, cudaStream_t s) {
   const Transfer &T_ = *tr[l];
   SpmvArgs none;
   spmv_sell<T>(T_.R, transfer_vals<T>(T_, true), nc_, r[l], b[l + 1], SPMV_PLAIN, none, s);
+  const int kc = kind == 0 ? Profiler::P1_MG_COARSE : Profiler::VEL_MG_COARSE;
+  if (prof && l == 0) prof->start(kc, s);
   vcycle(l + 1, s);
+  if (prof && l == 0) prof->stop(kc, s, 0.0);   // time only: every level below the finest
   spmv_sell<T>(T_.P, transfer_vals<T>(T_, false), nc_, x[l + 1], x[l], SPMV_ADD, none, s);
   // post-smoothing from x_0 = x[l]
   a.coef = coef[l] + 1;
@@ -313,14 +340,26 @@ chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, 
         double *zj = ws.Z + (long)j * ld;
         A.precond(vj, zj, s);
         A.apply(zj, ws.w, s);
+        const int kv = j + 1;
+        const bool fast = cgs2_fast(kv);
         if (prof) prof->start(Profiler::ORTHO, s);
-        mdot(n, ws.V, ld, j + 1, ws.w, ws.h1, ws.partial, s);
-        ortho_update_mdot(n, ws.V, ld, j + 1, ws.h1, ws.w, ws.h2, ws.partial, s);
-        ortho_update_norm(n, ws.V, ld, j + 1, ws.h2, ws.w, sc + 3, ws.partial, s);
-        // CGS2: three passes over V_0..V_j (w read 3x, written 2x) and
-        // 4(j+1)+1 FP64 FMAs per vector element (dot, update + dot, update + norm)
-        if (prof) prof->stop(Profiler::ORTHO, s, 8.0 * n * (3.0 * (j + 1) + 5.0), 2.0 * n * (4.0 * (j + 1) + 1.0));
-        arnoldi_finish(j, ldh, ws.H, ws.h1, ws.h2, sc + 3, ws.cs, ws.sn, ws.g, sc + 4, s);
+        if (fast) {
+          // CGS2 passes 1-2: h1 = V^T w; w -= V h1, h2 = V^T w and ||w||^2 in
+          // one sweep (V read twice, w read twice and written once; 3k+1 FMAs
+          // per element).  Pass 3 forms the next basis vector after the sync.
+          cgs2_dots(n, ws.V, ld, kv, ws.w, ws.h1, ws.partial, s);
+          cgs2_update_dots(n, ws.V, ld, kv, ws.h1, ws.w, ws.h2, ws.partial, s);
+          if (prof) prof->stop(Profiler::ORTHO, s, 8.0 * n * (2.0 * kv + 3.0), 2.0 * n * (3.0 * kv + 1.0));
+          arnoldi_finish_pyth(j, ldh, ws.H, ws.h1, ws.h2, ws.cs, ws.sn, ws.g, sc + 4, s);
+        } else {
+          mdot(n, ws.V, ld, kv, ws.w, ws.h1, ws.partial, s);
+          ortho_update_mdot(n, ws.V, ld, kv, ws.h1, ws.w, ws.h2, ws.partial, s);
+          ortho_update_norm(n, ws.V, ld, kv, ws.h2, ws.w, sc + 3, ws.partial, s);
+          // CGS2: three passes over V_0..V_j (w read 3x, written 2x) and
+          // 4k+1 FP64 FMAs per vector element (dot, update + dot, update + norm)
+          if (prof) prof->stop(Profiler::ORTHO, s, 8.0 * n * (3.0 * kv + 5.0), 2.0 * n * (4.0 * kv + 1.0));
+          arnoldi_finish(j, ldh, ws.H, ws.h1, ws.h2, sc + 3, ws.cs, ws.sn, ws.g, sc + 4, s);
+        }
         CHNSS_CK(cudaMemcpyAsync(ws.hstat, sc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CHNSS_CK(cudaStreamSynchronize(s));
         A.after_sync();
@@ -332,7 +371,14 @@ chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, 
           break;
         }
         breakdown = hn == 0.0;
-        if (!breakdown) vec_scale_by_inv(n, ws.w, sc + 5, ws.V + (long)(j + 1) * ld, s);
+        if (!breakdown && fast) {
+          // pass 3: V_{j+1} = (w - V h2) / hn (V read once, w read once, V_{j+1} written; k FMAs)
+          if (prof) prof->start(Profiler::ORTHO, s);
+          cgs2_update_scale(n, ws.V, ld, kv, ws.h2, ws.w, sc + 5, ws.V + (long)(j + 1) * ld, s);
+          if (prof) prof->stop(Profiler::ORTHO, s, 8.0 * n * (kv + 2.0), 2.0 * n * kv, 0);
+        } else if (!breakdown) {
+          vec_scale_by_inv(n, ws.w, sc + 5, ws.V + (long)(j + 1) * ld, s);
+        }
         if (est <= target || iters >= maxit || breakdown) break;
       }
       if (st != CHNSS_OK) break;

@@ -9,7 +9,7 @@ namespace chnss {
 // CUDA-event timing of the hot kernel families, with their algorithmic
 // bytes (values + indices + the vectors each launch must read or write).
 struct Profiler {
-  enum Kind { VEL_SPMV_L0 = 0, P1_SPMV_L0, NS_OUTER_SPMV, ORTHO, ASSEMBLY, NKINDS };
+  enum Kind { VEL_SPMV_L0 = 0, P1_SPMV_L0, NS_OUTER_SPMV, ORTHO, ASSEMBLY, P1_MG_COARSE, VEL_MG_COARSE, NKINDS };
   static const char *name(int k);
   bool on = false;
   struct Rec {
@@ -31,7 +31,8 @@ struct Profiler {
   std::vector<Probe> *sink = nullptr;   // preallocated events (created before capture)
   size_t sink_used = 0;
   void start(int k, cudaStream_t s);
-  void stop(int k, cudaStream_t s, double bytes, double flops = 0.0);
+  // count: launches (or steps) the interval adds to the family
+  void stop(int k, cudaStream_t s, double bytes, double flops = 0.0, int count = 1);
   void harvest(const std::vector<Probe> &probes, size_t count);
   void reset();
   double elapsed_ms(int k);        // after a stream synchronisation
@@ -63,6 +64,8 @@ struct MGHier {
   int *status = nullptr;
   double *partial = nullptr, *sum = nullptr;
   Profiler *prof = nullptr;
+  bool bf16 = false;       // level values stored in BF16 (T = float only; set before init)
+  std::vector<__nv_bfloat16 *> val16;
   int degree = 2;          // Chebyshev smoothing degree (pre and post)
   double ratio = 4.0;      // smoothing interval [hi / ratio, hi]
 
@@ -77,6 +80,8 @@ struct MGHier {
   T *input() { return b[0]; }
   T *output() { return x[0]; }
   void apply(cudaStream_t s);   // x[0] = V-cycle(b[0])
+  // out = A_l u with the given epilogue (no profiling)
+  void spmv_level(int l, const T *u, T *out, SpmvMode mode, const SpmvArgs &a, cudaStream_t s);
 
  private:
   void op(int l, const T *u, T *out, SpmvMode mode, const SpmvArgs &a, cudaStream_t s);

@@ -176,6 +176,16 @@ template <typename T> struct V2t;
 template <> struct V2t<float> { using type = float2; };
 template <> struct V2t<double> { using type = double2; };
 
+__device__ __forceinline__ float ldv(const float *p) { return *p; }
+__device__ __forceinline__ double ldv(const double *p) { return *p; }
+__device__ __forceinline__ float ldv(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+
+__device__ __forceinline__ void load_blk(const __nv_bfloat16 *p, float b[4]) {   // 8-byte aligned
+  const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+  const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.x));
+  const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.y));
+  b[0] = lo.x; b[1] = lo.y; b[2] = hi.x; b[3] = hi.y;
+}
 __device__ __forceinline__ void load_blk(const float *p, float b[4]) {
   const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
   b[0] = v.x; b[1] = v.y; b[2] = v.z; b[3] = v.w;
@@ -186,13 +196,18 @@ __device__ __forceinline__ void load_blk(const double *p, double b[4]) {
   b[0] = v0.x; b[1] = v0.y; b[2] = v1.x; b[3] = v1.y;
 }
 
+template <typename T> __device__ __forceinline__ T from_double(double x) { return (T)x; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double x) {
+  return __double2bfloat16(x);   // round to nearest even
+}
+
 template <typename T>
 __global__ void k_sell_gather(long nent, int ncomp, const int *__restrict__ map, const double *__restrict__ csr,
                               T *__restrict__ out) {
   const long e = (long)blockIdx.x * TPB + threadIdx.x;
   if (e >= nent) return;
   const int q = map[e];
-  for (int c = 0; c < ncomp; ++c) out[e * ncomp + c] = q >= 0 ? (T)csr[(long)q * ncomp + c] : (T)0;
+  for (int c = 0; c < ncomp; ++c) out[e * ncomp + c] = from_double<T>(q >= 0 ? csr[(long)q * ncomp + c] : 0.0);
 }
 
 __global__ void k_sell_gather_t(long nent, int ncomp, const int *__restrict__ mapT, const double *__restrict__ csr,
@@ -210,21 +225,21 @@ __global__ void k_sell_gather_t(long nent, int ncomp, const int *__restrict__ ma
   }
 }
 
-template <typename T, int NC, bool VEC>
-__global__ void __launch_bounds__(TPB) k_sell(int nslices, const int *__restrict__ sp, const int *__restrict__ rowid,
-                                              const int *__restrict__ col, const T *__restrict__ val,
+template <typename T, typename VT, int NC, bool VEC>
+__global__ void __launch_bounds__(kSellMaxBlock) k_sell(int nslices, const int *__restrict__ sp, const int *__restrict__ rowid,
+                                              const int *__restrict__ col, const VT *__restrict__ val,
                                               const T *__restrict__ u, T *out, int mode, SpmvArgs a) {
-  const int slice = (blockIdx.x * TPB + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int slice = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (slice >= nslices) return;
   const int row = rowid[slice * 32 + lane];
   const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
   const int *cp = col + b0 + lane;
-  const T *vp = val + b0 + lane;
+  const VT *vp = val + b0 + lane;
   T acc0 = 0, acc1 = 0;
 #pragma unroll 4
   for (int j = 0; j < w; ++j) {
     const int c = cp[j * 32];
-    const T v = vp[j * 32];
+    const T v = ldv(vp + j * 32);
     if (NC == 1) {
       acc0 += v * u[c];
     } else if (VEC) {
@@ -245,12 +260,12 @@ __global__ void __launch_bounds__(TPB) k_sell(int nslices, const int *__restrict
   }
 }
 
-template <typename T, bool VEC>
-__global__ void __launch_bounds__(TPB) k_sell_bsr2(int nslices, const int *__restrict__ sp,
+template <typename T, typename VT, bool VEC>
+__global__ void __launch_bounds__(kSellMaxBlock) k_sell_bsr2(int nslices, const int *__restrict__ sp,
                                                    const int *__restrict__ rowid, const int *__restrict__ col,
-                                                   const T *__restrict__ val, const T *__restrict__ u, T *out,
+                                                   const VT *__restrict__ val, const T *__restrict__ u, T *out,
                                                    int mode, SpmvArgs a) {
-  const int slice = (blockIdx.x * TPB + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int slice = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (slice >= nslices) return;
   const int row = rowid[slice * 32 + lane];
   const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
@@ -279,13 +294,13 @@ __global__ void __launch_bounds__(TPB) k_sell_bsr2(int nslices, const int *__res
   epilogue<T>(mode, 2L * row + 1, acc1, u, out, a, a.coef);
 }
 
-__global__ void __launch_bounds__(TPB) k_sell_ch(int nslices, int nrows, const int *__restrict__ sp,
+__global__ void __launch_bounds__(kSellMaxBlock) k_sell_ch(int nslices, int nrows, const int *__restrict__ sp,
                                                  const int *__restrict__ rowid, const int *__restrict__ col,
                                                  const double *__restrict__ L, const double *__restrict__ K,
                                                  const double *__restrict__ K12, const double *__restrict__ M,
                                                  double a12, double a21, double a22, const double *__restrict__ x,
                                                  double *__restrict__ y) {
-  const int slice = (blockIdx.x * TPB + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int slice = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (slice >= nslices) return;
   const int row = rowid[slice * 32 + lane];
   const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
@@ -307,10 +322,10 @@ __global__ void __launch_bounds__(TPB) k_sell_ch(int nslices, int nrows, const i
 }
 
 template <bool VEC>
-__global__ void __launch_bounds__(TPB) k_sell_b(int nslices, const int *__restrict__ sp, const int *__restrict__ rowid,
+__global__ void __launch_bounds__(kSellMaxBlock) k_sell_b(int nslices, const int *__restrict__ sp, const int *__restrict__ rowid,
                                                 const int *__restrict__ col, const double *__restrict__ val2,
                                                 const double *__restrict__ v, double *__restrict__ y) {
-  const int slice = (blockIdx.x * TPB + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int slice = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (slice >= nslices) return;
   const int row = rowid[slice * 32 + lane];
   const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
@@ -332,11 +347,11 @@ __global__ void __launch_bounds__(TPB) k_sell_b(int nslices, const int *__restri
   if (row >= 0) y[row] = acc;
 }
 
-__global__ void __launch_bounds__(TPB) k_sell_bt_add(int nslices, const int *__restrict__ sp,
+__global__ void __launch_bounds__(kSellMaxBlock) k_sell_bt_add(int nslices, const int *__restrict__ sp,
                                                      const int *__restrict__ rowid, const int *__restrict__ col,
                                                      const double *__restrict__ val2, const double *__restrict__ p,
                                                      double *__restrict__ yv) {
-  const int slice = (blockIdx.x * TPB + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int slice = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (slice >= nslices) return;
   const int row = rowid[slice * 32 + lane];
   const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
@@ -589,11 +604,18 @@ __global__ void k_combine(long n, const double *__restrict__ Z, long ldz, int k,
   x[i] += s;
 }
 
+// pyth = 1: *nrm2 holds ||w||^2 after the first correction and the norm
+// after the second one is ||w||^2 - ||h2||^2 (the basis is orthonormal)
 __global__ void k_arnoldi_finish(int j, int ldh, double *H, const double *h1, const double *h2, const double *nrm2,
-                                 double *cs, double *sn, double *g, double *status) {
+                                 double *cs, double *sn, double *g, double *status, int pyth) {
   double *col = H + (long)j * ldh;
   for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
-  const double hn = sqrt(*nrm2);
+  double q = *nrm2;
+  if (pyth) {
+    for (int i = 0; i <= j; ++i) q -= h2[i] * h2[i];
+    q = fmax(q, 0.0);
+  }
+  const double hn = sqrt(q);
   col[j + 1] = hn;
   for (int i = 0; i < j; ++i) {
     const double a = col[i], c = col[i + 1];
@@ -735,6 +757,127 @@ __global__ void k_dense_apply(int n, const double *inv, const T *b, T *x) {
   x[r] = (T)s;
 }
 
+
+// ---------------------------------------------------------------------------
+// CGS2 orthogonalisation kernels for k <= kCgsMaxK basis vectors.  The vector
+// count is a template parameter, so every issued FP64 FMA is useful work (the
+// FP64 pipe bounds these kernels on this part).  Each block reduces its NV
+// partial sums with a transposing warp butterfly: NV is padded to P = 2^LP,
+// LP halving steps leave lane l with the warp sum of vector l >> (5 - LP),
+// the remaining steps fold the duplicate lanes; the warps' results are then
+// summed in fixed order through shared memory.  Bit-reproducible.
+constexpr int kCgsBlock = 256;
+constexpr int kCgsMaxBlocks = 304;   // 2 per SM
+constexpr int kCgsMaxK = 31;
+
+constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 * pow2_at_least((x + 1) / 2); }
+constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
+template <int P>
+__device__ __forceinline__ double warp_transpose_sum(double (&v)[P]) {
+  constexpr int LP = ilog2(P);
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int st = 0; st < LP; ++st) {
+    const int mask = 16 >> st;
+    const int c = P >> (st + 1);
+    const bool up = (lane & mask) != 0;
+#pragma unroll
+    for (int q = 0; q < c; ++q) {
+      const double send = up ? v[q] : v[q + c];
+      const double keep = up ? v[q + c] : v[q];
+      v[q] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+    }
+  }
+#pragma unroll
+  for (int st = LP; st < 5; ++st) v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16 >> st);
+  return v[0];
+}
+
+// partial[j * gridDim.x + blockIdx.x] = block sum of a[j], j < NV
+template <int NV>
+__device__ __forceinline__ void cgs_block_reduce(double (&a)[pow2_at_least(NV)], double *__restrict__ partial) {
+  constexpr int P = pow2_at_least(NV);
+  constexpr int LP = ilog2(P);
+  __shared__ double red[kCgsBlock / 32][P];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double v = warp_transpose_sum<P>(a);
+  if ((lane & ((1 << (5 - LP)) - 1)) == 0) red[warp][lane >> (5 - LP)] = v;
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kCgsBlock / 32; ++w) t += red[w][threadIdx.x];
+    partial[(long)threadIdx.x * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// h = V^T w over KC vectors (partials)
+template <int KC>
+__global__ void __launch_bounds__(kCgsBlock) k_cgs_dots(long n, const double *__restrict__ V, long ld,
+                                                        const double *__restrict__ w, double *__restrict__ partial) {
+  double acc[pow2_at_least(KC)];
+#pragma unroll
+  for (int j = 0; j < pow2_at_least(KC); ++j) acc[j] = 0.0;
+  for (long i = (long)blockIdx.x * kCgsBlock + threadIdx.x; i < n; i += (long)gridDim.x * kCgsBlock) {
+    const double wi = w[i];
+#pragma unroll
+    for (int j = 0; j < KC; ++j) acc[j] += V[(long)j * ld + i] * wi;
+  }
+  cgs_block_reduce<KC>(acc, partial);
+}
+
+// w -= V h; then partials of V^T w (KC values) and w^T w (one more)
+template <int KC>
+__global__ void __launch_bounds__(kCgsBlock) k_cgs_update_dots(long n, const double *__restrict__ V, long ld,
+                                                               const double *__restrict__ h, double *__restrict__ w,
+                                                               double *__restrict__ partial) {
+  __shared__ double hs[KC];
+  if (threadIdx.x < KC) hs[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  double acc[pow2_at_least(KC + 1)];
+#pragma unroll
+  for (int j = 0; j < pow2_at_least(KC + 1); ++j) acc[j] = 0.0;
+  for (long i = (long)blockIdx.x * kCgsBlock + threadIdx.x; i < n; i += (long)gridDim.x * kCgsBlock) {
+    double v[KC];
+#pragma unroll
+    for (int j = 0; j < KC; ++j) v[j] = V[(long)j * ld + i];
+    double s0 = 0.0, s1 = 0.0;     // two chains: half the FP64 latency on the critical path
+#pragma unroll
+    for (int j = 0; j < KC; j += 2) s0 += hs[j] * v[j];
+#pragma unroll
+    for (int j = 1; j < KC; j += 2) s1 += hs[j] * v[j];
+    const double wi = w[i] - (s0 + s1);
+    w[i] = wi;
+#pragma unroll
+    for (int j = 0; j < KC; ++j) acc[j] += v[j] * wi;
+    acc[KC] += wi * wi;
+  }
+  cgs_block_reduce<KC + 1>(acc, partial);
+}
+
+// out = (w - V h) / hn  (the next basis vector; no reduction)
+template <int KC>
+__global__ void __launch_bounds__(kCgsBlock) k_cgs_update_scale(long n, const double *__restrict__ V, long ld,
+                                                                const double *__restrict__ h,
+                                                                const double *__restrict__ w,
+                                                                const double *__restrict__ hn,
+                                                                double *__restrict__ out) {
+  __shared__ double hs[KC];
+  __shared__ double inv;
+  if (threadIdx.x < KC) hs[threadIdx.x] = h[threadIdx.x];
+  if (threadIdx.x == 0) inv = 1.0 / *hn;
+  __syncthreads();
+  const long i = (long)blockIdx.x * kCgsBlock + threadIdx.x;
+  if (i >= n) return;
+  double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+  for (int j = 0; j < KC; j += 2) s0 += hs[j] * V[(long)j * ld + i];
+#pragma unroll
+  for (int j = 1; j < KC; j += 2) s1 += hs[j] * V[(long)j * ld + i];
+  out[i] = (w[i] - (s0 + s1)) * inv;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -778,6 +921,7 @@ void sell_gather(const Sell &S, int ncomp, const double *csr_vals, Tout *out, cu
 }
 template void sell_gather<double>(const Sell &, int, const double *, double *, cudaStream_t);
 template void sell_gather<float>(const Sell &, int, const double *, float *, cudaStream_t);
+template void sell_gather<__nv_bfloat16>(const Sell &, int, const double *, __nv_bfloat16 *, cudaStream_t);
 
 void sell_gather_transposed(const Sell &S, int ncomp, const double *csr_vals, double *out, cudaStream_t s) {
   if (!S.mapT) throw Error{CHNSS_ERR_ARG, "transposed values need a square symmetric pattern"};
@@ -786,63 +930,83 @@ void sell_gather_transposed(const Sell &S, int ncomp, const double *csr_vals, do
   CHNSS_LAUNCH_CK();
 }
 
+template <typename T, typename VT>
+void spmv_sell_impl(const Pattern &P, const VT *sval, int ncomp, const T *u, T *out, SpmvMode mode,
+                    const SpmvArgs &a, cudaStream_t s) {
+  const Sell &S = P.sell;
+  if (S.nslices == 0) return;
+  const int nb = nblocks((long)S.nslices * 32, S.block);
+  if (ncomp == 1)
+    k_sell<T, VT, 1, false><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
+  else if (aligned(u, 2 * sizeof(T)))
+    k_sell<T, VT, 2, true><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
+  else
+    k_sell<T, VT, 2, false><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
+  CHNSS_LAUNCH_CK();
+}
+
+template <typename T, typename VT>
+void spmv_sell_bsr2_impl(const Pattern &P, const VT *sval, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
+                         cudaStream_t s) {
+  const Sell &S = P.sell;
+  if (S.nslices == 0) return;
+  const int nb = nblocks((long)S.nslices * 32, S.block);
+  if (!aligned(sval, 4 * sizeof(VT)))
+    throw Error{CHNSS_ERR_ARG, "2x2-block values must be aligned to one block"};
+  if (aligned(u, 2 * sizeof(T)))
+    k_sell_bsr2<T, VT, true><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
+  else
+    k_sell_bsr2<T, VT, false><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
+  CHNSS_LAUNCH_CK();
+}
+
 template <typename T>
 void spmv_sell(const Pattern &P, const T *sval, int ncomp, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
                cudaStream_t s) {
-  const Sell &S = P.sell;
-  if (S.nslices == 0) return;
-  const int nb = nblocks((long)S.nslices * 32, TPB);
-  if (ncomp == 1)
-    k_sell<T, 1, false><<<nb, TPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
-  else if (aligned(u, 2 * sizeof(T)))
-    k_sell<T, 2, true><<<nb, TPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
-  else
-    k_sell<T, 2, false><<<nb, TPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
-  CHNSS_LAUNCH_CK();
+  spmv_sell_impl<T, T>(P, sval, ncomp, u, out, mode, a, s);
 }
 template void spmv_sell<double>(const Pattern &, const double *, int, const double *, double *, SpmvMode,
                                 const SpmvArgs &, cudaStream_t);
 template void spmv_sell<float>(const Pattern &, const float *, int, const float *, float *, SpmvMode,
                                const SpmvArgs &, cudaStream_t);
+void spmv_sell(const Pattern &P, const __nv_bfloat16 *sval, int ncomp, const float *u, float *out, SpmvMode mode,
+               const SpmvArgs &a, cudaStream_t s) {
+  spmv_sell_impl<float, __nv_bfloat16>(P, sval, ncomp, u, out, mode, a, s);
+}
 
 template <typename T>
 void spmv_sell_bsr2(const Pattern &P, const T *sval, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
                     cudaStream_t s) {
-  const Sell &S = P.sell;
-  if (S.nslices == 0) return;
-  const int nb = nblocks((long)S.nslices * 32, TPB);
-  if (!aligned(sval, 4 * sizeof(T)))
-    throw Error{CHNSS_ERR_ARG, "2x2-block values must be 16-byte aligned"};
-  if (aligned(u, 2 * sizeof(T)))
-    k_sell_bsr2<T, true><<<nb, TPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
-  else
-    k_sell_bsr2<T, false><<<nb, TPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
-  CHNSS_LAUNCH_CK();
+  spmv_sell_bsr2_impl<T, T>(P, sval, u, out, mode, a, s);
 }
 template void spmv_sell_bsr2<double>(const Pattern &, const double *, const double *, double *, SpmvMode,
                                      const SpmvArgs &, cudaStream_t);
 template void spmv_sell_bsr2<float>(const Pattern &, const float *, const float *, float *, SpmvMode,
                                     const SpmvArgs &, cudaStream_t);
+void spmv_sell_bsr2(const Pattern &P, const __nv_bfloat16 *sval, const float *u, float *out, SpmvMode mode,
+                    const SpmvArgs &a, cudaStream_t s) {
+  spmv_sell_bsr2_impl<float, __nv_bfloat16>(P, sval, u, out, mode, a, s);
+}
 
 void spmv_sell_ch(const Pattern &P, const double *L, const double *K, const double *k12, const double *M, double a12,
                   double a21, double a22, const double *x, double *y, cudaStream_t s) {
   const Sell &S = P.sell;
-  k_sell_ch<<<nblocks((long)S.nslices * 32, TPB), TPB, 0, s>>>(S.nslices, P.nrows, S.slice_ptr, S.rowid, S.col, L, K,
+  k_sell_ch<<<nblocks((long)S.nslices * 32, S.block), S.block, 0, s>>>(S.nslices, P.nrows, S.slice_ptr, S.rowid, S.col, L, K,
                                                                k12, M, a12, a21, a22, x, y);
   CHNSS_LAUNCH_CK();
 }
 void spmv_sell_b(const Pattern &P, const double *sval2, const double *v, double *y, cudaStream_t s) {
   const Sell &S = P.sell;
-  const int nb = nblocks((long)S.nslices * 32, TPB);
+  const int nb = nblocks((long)S.nslices * 32, S.block);
   if (aligned(v, 16))
-    k_sell_b<true><<<nb, TPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval2, v, y);
+    k_sell_b<true><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval2, v, y);
   else
-    k_sell_b<false><<<nb, TPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval2, v, y);
+    k_sell_b<false><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval2, v, y);
   CHNSS_LAUNCH_CK();
 }
 void spmv_sell_bt_add(const Pattern &P, const double *sval2, const double *p, double *yv, cudaStream_t s) {
   const Sell &S = P.sell;
-  k_sell_bt_add<<<nblocks((long)S.nslices * 32, TPB), TPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval2, p,
+  k_sell_bt_add<<<nblocks((long)S.nslices * 32, S.block), S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval2, p,
                                                                    yv);
   CHNSS_LAUNCH_CK();
 }
@@ -1026,8 +1190,70 @@ void combine_columns(long n, const double *Z, long ldz, int k, const double *y, 
 }
 void arnoldi_finish(int j, int ldh, double *H, const double *h1, const double *h2, const double *nrm2, double *cs,
                     double *sn, double *g, double *status, cudaStream_t s) {
-  k_arnoldi_finish<<<1, 1, 0, s>>>(j, ldh, H, h1, h2, nrm2, cs, sn, g, status);
+  k_arnoldi_finish<<<1, 1, 0, s>>>(j, ldh, H, h1, h2, nrm2, cs, sn, g, status, 0);
   CHNSS_LAUNCH_CK();
+}
+void arnoldi_finish_pyth(int j, int ldh, double *H, const double *h1, const double *h2w, double *cs, double *sn,
+                         double *g, double *status, cudaStream_t s) {
+  k_arnoldi_finish<<<1, 1, 0, s>>>(j, ldh, H, h1, h2w, h2w + j + 1, cs, sn, g, status, 1);
+  CHNSS_LAUNCH_CK();
+}
+
+// ---- CGS2 passes with the vector count as a template parameter ----
+bool cgs2_fast(int k) { return k >= 1 && k <= kCgsMaxK; }
+
+namespace {
+int cgs_blocks(long n) {
+  long b = (n + kCgsBlock - 1) / kCgsBlock;
+  return (int)std::max(1L, std::min(b, (long)kCgsMaxBlocks));
+}
+template <int KC>
+void cgs_pass(int pass, long n, const double *V, long ld, const double *h, const double *w_in, double *w,
+              const double *hn, double *out, double *partial, cudaStream_t s) {
+  if (pass == 1) {
+    const int nb = cgs_blocks(n);
+    k_cgs_dots<KC><<<nb, kCgsBlock, 0, s>>>(n, V, ld, w_in, partial);
+    CHNSS_LAUNCH_CK();
+    k_sum_final<<<KC, TPB, 0, s>>>(nb, KC, partial, out);
+  } else if (pass == 2) {
+    const int nb = cgs_blocks(n);
+    k_cgs_update_dots<KC><<<nb, kCgsBlock, 0, s>>>(n, V, ld, h, w, partial);
+    CHNSS_LAUNCH_CK();
+    k_sum_final<<<KC + 1, TPB, 0, s>>>(nb, KC + 1, partial, out);
+  } else {
+    k_cgs_update_scale<KC><<<nblocks(n, kCgsBlock), kCgsBlock, 0, s>>>(n, V, ld, h, w_in, hn, out);
+  }
+  CHNSS_LAUNCH_CK();
+}
+void cgs_dispatch(int k, int pass, long n, const double *V, long ld, const double *h, const double *w_in, double *w,
+                  const double *hn, double *out, double *partial, cudaStream_t s) {
+  switch (k) {
+#define CHNSS_CGS_CASE(K) \
+  case K: cgs_pass<K>(pass, n, V, ld, h, w_in, w, hn, out, partial, s); break;
+    CHNSS_CGS_CASE(1) CHNSS_CGS_CASE(2) CHNSS_CGS_CASE(3) CHNSS_CGS_CASE(4) CHNSS_CGS_CASE(5)
+    CHNSS_CGS_CASE(6) CHNSS_CGS_CASE(7) CHNSS_CGS_CASE(8) CHNSS_CGS_CASE(9) CHNSS_CGS_CASE(10)
+    CHNSS_CGS_CASE(11) CHNSS_CGS_CASE(12) CHNSS_CGS_CASE(13) CHNSS_CGS_CASE(14) CHNSS_CGS_CASE(15)
+    CHNSS_CGS_CASE(16) CHNSS_CGS_CASE(17) CHNSS_CGS_CASE(18) CHNSS_CGS_CASE(19) CHNSS_CGS_CASE(20)
+    CHNSS_CGS_CASE(21) CHNSS_CGS_CASE(22) CHNSS_CGS_CASE(23) CHNSS_CGS_CASE(24) CHNSS_CGS_CASE(25)
+    CHNSS_CGS_CASE(26) CHNSS_CGS_CASE(27) CHNSS_CGS_CASE(28) CHNSS_CGS_CASE(29) CHNSS_CGS_CASE(30)
+    CHNSS_CGS_CASE(31)
+#undef CHNSS_CGS_CASE
+    default: throw Error{CHNSS_ERR_ARG, "CGS2 fast path: k must be in [1, 31]"};
+  }
+}
+}  // namespace
+
+void cgs2_dots(long n, const double *V, long ld, int k, const double *w, double *h1, double *partial,
+               cudaStream_t s) {
+  cgs_dispatch(k, 1, n, V, ld, nullptr, w, nullptr, nullptr, h1, partial, s);
+}
+void cgs2_update_dots(long n, const double *V, long ld, int k, const double *h1, double *w, double *h2w,
+                      double *partial, cudaStream_t s) {
+  cgs_dispatch(k, 2, n, V, ld, h1, nullptr, w, nullptr, h2w, partial, s);
+}
+void cgs2_update_scale(long n, const double *V, long ld, int k, const double *h2, const double *w, const double *hn,
+                       double *vout, cudaStream_t s) {
+  cgs_dispatch(k, 3, n, V, ld, h2, w, nullptr, hn, vout, nullptr, s);
 }
 void hessenberg_solve(int k, int ldh, const double *H, const double *g, double *y, cudaStream_t s) {
   k_hessenberg_solve<<<1, 1, 0, s>>>(k, ldh, H, g, y);

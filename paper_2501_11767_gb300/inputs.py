@@ -135,3 +135,23 @@ def workload(name: str) -> dict:
         p.update(beta=film_betas(0.005), tau=5e-4, precision=1)
         return {"n": 512, "params": p, "steps": 10}
     raise KeyError(name)
+
+
+SWEEP_MESHES = (128, 192, 256, 384, 512)
+FIELD_SWEEP = 7          # key space of the sweep draws (fields 0, 1 are the noise)
+
+
+def sweep_instances(count: int = 64, seed: int = 0) -> list:
+    """A parameter sweep of independent thin-film runs (Sec. 5 varies the
+    evaporation rate and the resolution): instance i gets a mesh drawn
+    uniformly from SWEEP_MESHES, an evaporation rate uniform in [0.05, 0.5],
+    noise seed 1000 + i, and otherwise the default parameters with FP32
+    preconditioners.  Returns [{"n", "params", "seed"}]."""
+    u = uniform_noise(seed, FIELD_SWEEP, 2 * count, amp=1.0) * 0.5 + 0.5     # U[0, 1)
+    out = []
+    for i in range(count):
+        n = SWEEP_MESHES[min(int(u[2 * i] * len(SWEEP_MESHES)), len(SWEEP_MESHES) - 1)]
+        p = default_params()
+        p.update(evap_rate=0.05 + 0.45 * float(u[2 * i + 1]), precision=1)
+        out.append({"n": n, "params": p, "seed": 1000 + i})
+    return out

@@ -53,6 +53,13 @@ def test_argument_errors_need_no_device(lib):
     assert lib.chnss_system_size(None, 0) == -1
     assert lib.chnss_mesh_destroy(None) == 0
     assert lib.chnss_ctx_destroy(None) == 0
+    assert lib.chnss_step_batched(-1, None, None, None, None, 0) == 1
+    assert lib.chnss_step_batched(0, None, None, None, None, 0) == 0     # empty batch: nothing to do
+    hs = (ctypes.c_void_p * 2)(None, None)
+    two = (chnss.State * 2)()
+    assert lib.chnss_step_batched(2, hs, two, two, None, 0) == 1         # null context
+    assert lib.chnss_autotune(None, None) == 1
+    assert lib.chnss_set_spmv_block(None, 256, 256) == 1
 
 
 def test_params_struct_matches_header():

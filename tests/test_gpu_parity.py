@@ -157,20 +157,22 @@ def test_step_host_matches_device_step(torch):
         assert np.array_equal(d[k], hout[k]), k
 
 
-def test_mixed_precision_step(torch):
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_precision_step(torch, precision):
     """FP32 preconditioners inside FP64 FGMRES reach the same 1e-8 relative
     residual as the FP64 path; with the outer FGMRES at 1e-10 the step stays
     within 1e-6 of the FP64 oracle (solved to 1e-12).  At a 1e-8 residual the
     distance to the exact solution is bounded by kappa * 1e-8 for either
     precision (mu_a amplifies it through beta_a K phi_a), so the 1e-6 gate is
-    taken at the tighter outer tolerance."""
+    taken at the tighter outer tolerance.  precision = 2 stores the
+    velocity multigrid values in BF16 and must meet the same gates."""
     n = 32
     params = inputs.default_params()
     mesh = chnss.Mesh(n)
     o = Oracle(n, dict(params, rtol=1e-12))
-    ctx8 = chnss.Context(mesh, dict(params, precision=1))
+    ctx8 = chnss.Context(mesh, dict(params, precision=precision))
     ctx64 = chnss.Context(mesh, dict(params, precision=0))
-    ctx10 = chnss.Context(mesh, dict(params, precision=1, rtol=1e-10))
+    ctx10 = chnss.Context(mesh, dict(params, precision=precision, rtol=1e-10))
     st = inputs.initial_state(n, seed=5)
     for _ in range(2):
         ref, _ = o.step(st)
@@ -187,6 +189,12 @@ def test_mixed_precision_step(torch):
             assert rel(g10[key], ref[key]) <= MIXED_TOL, key
             assert rel(g8[key], g64[key]) <= 1e-4, key     # both at a 1e-8 residual
         st = ref
+
+
+def test_restart_longer_than_the_templated_cgs2(torch):
+    """FGMRES(40): Arnoldi steps with more than 31 basis vectors take the
+    generic CGS2 kernels; the step must still match the oracle."""
+    _compare_step(torch, 16, dict(inputs.default_params(), restart=40), seed=16, steps=1)
 
 
 def test_solve_with_explicit_rhs_and_state_errors(torch):
