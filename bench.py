@@ -232,12 +232,13 @@ def run_gpu(args):
     bf16 = None
     if args.bf16_steps > 0:
         pb = dict(params, precision=2)
-        ctxb, msb, infosb, profb, _, _ = timed_run(pb, 1, args.bf16_steps, True)
+        ctxb, msb, infosb, profb, _, _ = timed_run(pb, args.warmup, args.bf16_steps, True)
         del ctxb
         bf16 = {"value": args.bf16_steps / (msb / 1e3), "unit": "steps/s", "steps": args.bf16_steps,
                 "ms_per_step": msb / args.bf16_steps,
                 "what": "precision 2: velocity multigrid values stored in BF16, FP32 vectors, FP64 FGMRES",
                 "converged": all(i[k]["converged"] for i in infosb for k in i),
+                "iters_mean": {k: round(sum(i[k]["iters"] for i in infosb) / len(infosb), 2) for k in infosb[-1]},
                 "kernel_families": {k: {"ms_total": round(v["ms"], 3), "launches": v["launches"],
                                         "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)
                                         if v["ms"] > 0 and v["bytes"] > 0 else None}
@@ -358,19 +359,39 @@ def _traffic(kernel):
 SWEEP_METRIC = "aggregate time steps/s of a 64-instance parameter sweep (meshes 128^2..512^2, FGMRES to 1e-8)"
 
 
+def shard(items: list, rank: int, world: int) -> list:
+    """Instances of one rank: round-robin over the sweep (independent
+    problems, no data-path collective)."""
+    return [x for i, x in enumerate(items) if i % world == rank]
+
+
 def run_sweep(args):
     """Batched parameter sweep: independent instances of uneven mesh size
     and evaporation rate, one context (and stream) each, advanced together
     by chnss_step_batched after the SpMV launch shapes of every mesh have
     been autotuned.  Also times the same instances stepped one after the
-    other (one chnss_step at a time) for comparison."""
+    other (one chnss_step at a time) for comparison.  Under torchrun the
+    instances are sharded round-robin over the ranks (weak scaling of the
+    per-rank batch is not kept: the sweep is fixed, so this is strong)."""
     import torch
+    import torch.distributed as dist
 
     from paper_2501_11767_gb300 import chnss, inputs
 
-    dev = torch.device("cuda", 0)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    inst = inputs.sweep_instances(args.sweep_count)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    all_inst = inputs.sweep_instances(args.sweep_count)
+    inst = shard(all_inst, rank, world)
     meshes = {n: chnss.Mesh(n) for n in sorted({i["n"] for i in inst})}
     tuning = {}
     for n, m in meshes.items():          # tune each mesh on a throw-away context
@@ -387,7 +408,8 @@ def run_sweep(args):
         a, b = b, a
     torch.cuda.synchronize()
     launches0 = ctxs[0].profile_read()["launches"]
-    sampler = ClockSampler(_device_uuid(torch, 0))
+    sampler = ClockSampler(_device_uuid(torch, local))
+    barrier()
     sampler.start()
     t0 = time.perf_counter()
     recs = None
@@ -396,9 +418,14 @@ def run_sweep(args):
         a, b = b, a
     torch.cuda.synchronize()
     sec = time.perf_counter() - t0
+    barrier()
     clocks = sampler.stop()
     launches = ctxs[0].profile_read()["launches"] - launches0
-    value = len(inst) * args.steps / sec
+    if world > 1:
+        t = torch.tensor([sec], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec = float(t.item())
+    value = len(all_inst) * args.steps / sec
 
     # the same instances one at a time (one step each)
     torch.cuda.synchronize()
@@ -407,31 +434,38 @@ def run_sweep(args):
         c.step(x, y)
         c.stream.synchronize()
     seq = len(inst) / (time.perf_counter() - t0)
+    if rank != 0:
+        dist.destroy_process_group()
+        return
 
     out = {
-        "metric": SWEEP_METRIC, "value": round(value, 3), "unit": "instance steps/s", "n_gpus": 1,
+        "metric": SWEEP_METRIC, "value": round(value, 3), "unit": "instance steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec / args.steps * 1e3, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
         "dtype": "f64 outer / f32 preconditioner", "data": "synthetic (seeded SplitMix64 draws)",
-        "config": {"workload": f"sweep{len(inst)}", "instances": len(inst),
-                   "meshes": {str(n): sum(1 for i in inst if i["n"] == n) for n in meshes},
-                   "total_p1_nodes": sum((i["n"] + 1) ** 2 for i in inst),
-                   "evap_rate": [round(min(i["params"]["evap_rate"] for i in inst), 4),
-                                 round(max(i["params"]["evap_rate"] for i in inst), 4)],
+        "config": {"workload": f"sweep{len(all_inst)}", "instances": len(all_inst),
+                   "instances_rank0": len(inst), "parallelism": f"instances sharded over {world} GPU(s)",
+                   "meshes": {str(n): sum(1 for i in all_inst if i["n"] == n)
+                              for n in sorted({i["n"] for i in all_inst})},
+                   "total_p1_nodes": sum((i["n"] + 1) ** 2 for i in all_inst),
+                   "evap_rate": [round(min(i["params"]["evap_rate"] for i in all_inst), 4),
+                                 round(max(i["params"]["evap_rate"] for i in all_inst), 4)],
                    "host_threads": threads, "l2": "inputs larger than L2 (tens of GB resident)",
                    "timing": "wall clock around chnss_step_batched (it returns after every stream is synchronised)"},
         "tuning": {str(n): {"block_p1": t["block_p1"], "block_p2": t["block_p2"],
                             "ms_p1": [round(x, 4) for x in t["ms_p1"]], "ms_p2": [round(x, 4) for x in t["ms_p2"]]}
                    for n, t in tuning.items()},
         "sequential": {"value": round(seq, 3), "unit": "instance steps/s",
-                       "how": "one chnss_step per instance, one after the other, same contexts"},
-        "speedup_batched_vs_sequential": round(value / seq, 3),
+                       "how": "rank 0: one chnss_step per instance, one after the other, same contexts"},
+        "speedup_batched_vs_sequential": round(value / world / seq, 3),
         "converged": all(r[k]["converged"] for r in recs for k in r),
         "iters_mean": {k: round(sum(r[k]["iters"] for r in recs) / len(recs), 2) for k in recs[0]},
         "gpu_launches": launches,
         "clocks": clocks,
     }
     print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
 
 
 # ---------------------------------------------------------------------------
@@ -470,7 +504,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--bf16-steps", type=int, default=3)
+    ap.add_argument("--bf16-steps", type=int, default=5)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

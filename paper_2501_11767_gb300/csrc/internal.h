@@ -88,6 +88,7 @@ struct Sell {
   static constexpr int SIGMA = 256;
   int block = 256;               // threads per block of its SpMV launches (autotuned)
   int nslices = 0;
+  int wmax = 0;                  // widest slice (entries per row incl. padding)
   long nent = 0;                 // padded entries
   int *slice_ptr = nullptr;      // [nslices + 1] first entry of each slice
   int *rowid = nullptr;          // [nslices * 32] CSR row of each slot, -1 = padding

@@ -143,6 +143,7 @@ void build_sell(Arena &ar, Pattern &P, std::vector<int> *hmap = nullptr) {
       }
     }
     sp[k + 1] = sp[k] + w * C;
+    s.wmax = std::max(s.wmax, w);
   }
   s.nent = sp[s.nslices];
   std::vector<int> col(s.nent), map(s.nent);

@@ -21,6 +21,15 @@ __device__ __forceinline__ T group_sum(T v) {
   return v;
 }
 
+// Chebyshev step of one row: c0 u + c2 dinv (b - A u) (+ c1 w)
+template <typename T>
+__device__ __forceinline__ T cheb_row(const double *coef, T ui, T di, T bi, T acc, bool has_w, T wi) {
+  const T c0 = (T)coef[0], c1 = (T)coef[1], c2 = (T)coef[2];
+  T v = c0 * ui + c2 * di * (bi - acc);
+  if (has_w) v += c1 * wi;
+  return v;
+}
+
 template <typename T>
 __device__ __forceinline__ void epilogue(int mode, long i, T acc, const T *u, T *out, const SpmvArgs &a,
                                          const double *coef) {
@@ -31,13 +40,9 @@ __device__ __forceinline__ void epilogue(int mode, long i, T acc, const T *u, T 
   } else if (mode == SPMV_ADD) {
     out[i] += acc;
   } else {
-    const T *b = static_cast<const T *>(a.b);
     const T *w = static_cast<const T *>(a.w);
-    const T *dinv = static_cast<const T *>(a.dinv);
-    const T c0 = (T)coef[0], c1 = (T)coef[1], c2 = (T)coef[2];
-    T v = c0 * u[i] + c2 * dinv[i] * (b[i] - acc);
-    if (w) v += c1 * w[i];
-    out[i] = v;
+    out[i] = cheb_row<T>(coef, u[i], static_cast<const T *>(a.dinv)[i], static_cast<const T *>(a.b)[i], acc,
+                         w != nullptr, w ? w[i] : (T)0);
   }
 }
 
@@ -258,6 +263,52 @@ __global__ void __launch_bounds__(kSellMaxBlock) k_sell(int nslices, const int *
     epilogue<T>(mode, 2L * row, acc0, u, out, a, a.coef);
     epilogue<T>(mode, 2L * row + 1, acc1, u, out, a, a.coef);
   }
+}
+
+// Scalar rows of at most 8 entries (every P1 operator: 7-point stencil):
+// the epilogue operands are loaded first and all column / value loads are
+// issued before the gathers, so a thread waits for two memory round trips.
+// Same per-row summation order as k_sell.
+template <typename T, typename VT>
+__global__ void __launch_bounds__(kSellMaxBlock) k_sell_w8(int nslices, const int *__restrict__ sp,
+                                                  const int *__restrict__ rowid, const int *__restrict__ col,
+                                                  const VT *__restrict__ val, const T *__restrict__ u, T *out,
+                                                  int mode, SpmvArgs a) {
+  const int slice = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (slice >= nslices) return;
+  const int row = rowid[slice * 32 + lane];
+  const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
+  const T *wv = static_cast<const T *>(a.w);
+  T bi = 0, di = 0, ui = 0, wi = 0, oi = 0;
+  if (row >= 0) {
+    if (mode == SPMV_RES || mode == SPMV_CHEB) bi = static_cast<const T *>(a.b)[row];
+    if (mode == SPMV_CHEB) {
+      di = static_cast<const T *>(a.dinv)[row];
+      ui = u[row];
+      if (wv) wi = wv[row];
+    }
+    if (mode == SPMV_ADD) oi = out[row];
+  }
+  int c[8];
+  T v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    if (j < w) {
+      c[j] = col[b0 + j * 32 + lane];
+      v[j] = ldv(val + b0 + j * 32 + lane);
+    }
+  }
+  T acc = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    if (j < w) acc += v[j] * u[c[j]];
+  if (row < 0) return;
+  T r;
+  if (mode == SPMV_PLAIN) r = acc;
+  else if (mode == SPMV_RES) r = bi - acc;
+  else if (mode == SPMV_ADD) r = oi + acc;
+  else r = cheb_row<T>(a.coef, ui, di, bi, acc, wv != nullptr, wi);
+  out[row] = r;
 }
 
 template <typename T, typename VT, bool VEC>
@@ -936,7 +987,9 @@ void spmv_sell_impl(const Pattern &P, const VT *sval, int ncomp, const T *u, T *
   const Sell &S = P.sell;
   if (S.nslices == 0) return;
   const int nb = nblocks((long)S.nslices * 32, S.block);
-  if (ncomp == 1)
+  if (ncomp == 1 && S.wmax <= 8)
+    k_sell_w8<T, VT><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
+  else if (ncomp == 1)
     k_sell<T, VT, 1, false><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
   else if (aligned(u, 2 * sizeof(T)))
     k_sell<T, VT, 2, true><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
