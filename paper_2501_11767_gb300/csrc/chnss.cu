@@ -85,7 +85,8 @@ __global__ void k_inv_diag(int n, const double *val, const int *diag, double *ou
 Geo geo(const Level &L) { return Geo{L.n, L.hx, L.hy}; }
 
 // ---------------------------------------------------------------------------
-constexpr int kNumPrec = 5;
+constexpr int kNumPrec = 6;          // 0..2 CH species, 3 AC, 4 NS, 5 the three CH species together
+constexpr int kBatchSlot = 2 * kNumPrec;   // slots of preconditioner 5: in0, out0, in1, out1, in2, out2
 constexpr int kMaxProbes = 32;
 struct PrecGraph {
   cudaGraphExec_t plain = nullptr, prof = nullptr;
@@ -98,6 +99,10 @@ template <typename T>
 struct PrecSet {
   MGHier<T> L, AC, A, Kp;
   MGHier<T> X1[3], X2[3];
+  // the three CH species together (constant mobility): MG(L) on three
+  // vectors, and one X1 V-cycle per group of species with equal X1
+  MGBatch<T> LB, XB[3];
+  int ngroups = 0, gsize[3] = {0, 0, 0}, gmem[3][3] = {};
   T *Mv = nullptr, *Apv = nullptr, *mdinv = nullptr;
   T *mx = nullptr, *mt = nullptr, *mb = nullptr;
 };
@@ -131,6 +136,9 @@ struct chnss_ctx {
   double **slots = nullptr;   // device [2 * kNumPrec] input / output pointers
   cudaStream_t cap = nullptr; // private stream used for capture only
   PrecGraph pg[kNumPrec];
+  bool ch_batch = false;                    // step() solves the CH species together
+  KrylovWork kwb[2];                        // Krylov work of the 2nd and 3rd CH species
+  double *dummy_in = nullptr, *dummy_out = nullptr;   // idle batch members (2 N1 each)
   int pending_probe = -1;
   KrylovWork kw;
   Profiler prof;
@@ -183,6 +191,30 @@ void ch_precond(chnss_ctx *c, PrecSet<T> &P, int sp, double **slot, cudaStream_t
   vec_convert_to_slot<T, double>(N1, X2.output(), out, N1, s);
 }
 
+// The three species' preconditioners in one pass (slots kBatchSlot..+5):
+// per species the same operations as ch_precond, with the matrix sweeps of
+// MG(L) and of each X1 group shared by the group's vectors.
+template <typename T>
+void ch_precond_batched(chnss_ctx *c, PrecSet<T> &P, cudaStream_t s) {
+  const int N1 = c->N1;
+  double **slot = c->slots + kBatchSlot;
+  const double *const *in = const_cast<const double *const *>(slot);
+  for (int k = 0; k < 3; ++k) vec_convert_from_slot<double, T>(N1, in + 2 * k, 0, P.LB.input(k), s);
+  P.LB.apply(s);
+  for (int k = 0; k < 3; ++k) vec_convert_to_slot<T, double>(N1, P.LB.output(k), slot + 2 * k + 1, 0, s);
+  const Pattern &p1 = c->lv(0).p1;
+  for (int g = 0; g < P.ngroups; ++g) {
+    MGBatch<T> &X = P.XB[g];
+    for (int j = 0; j < P.gsize[g]; ++j) vec_convert_from_slot<double, T>(N1, in + 2 * P.gmem[g][j], N1, X.input(j), s);
+    X.apply(s);
+    MultiArgs<T> none;
+    spmv_sell_multi<T>(p1, P.Mv, P.gsize[g], X.x[0], X.b[0], SPMV_PLAIN, none, s);   // X2 = X1 (constant mobility)
+    X.apply(s);
+    for (int j = 0; j < P.gsize[g]; ++j)
+      vec_convert_to_slot<T, double>(N1, X.output(j), slot + 2 * P.gmem[g][j] + 1, N1, s);
+  }
+}
+
 template <typename T>
 void ac_precond(chnss_ctx *c, PrecSet<T> &P, double **slot, cudaStream_t s) {
   vec_convert_from_slot<double, T>(c->N1, const_cast<const double *const *>(slot), 0, P.AC.input(), s);
@@ -226,7 +258,8 @@ void prec_body_t(chnss_ctx *c, PrecSet<T> &P, int g, cudaStream_t s) {
   double **slot = c->slots + 2 * g;
   if (g < 3) ch_precond(c, P, g, slot, s);
   else if (g == 3) ac_precond(c, P, slot, s);
-  else ns_precond(c, P, slot, s);
+  else if (g == 4) ns_precond(c, P, slot, s);
+  else ch_precond_batched(c, P, s);
 }
 void prec_body(chnss_ctx *c, int g, cudaStream_t s) {
   if (c->p32) prec_body_t(c, *c->p32, g, s);
@@ -246,6 +279,15 @@ void run_prec(chnss_ctx *c, int g, const double *r, double *z) {
   if (prof) c->pending_probe = g;
 }
 
+// batch members: inputs / outputs of the three species; idle members read
+// zeros and write a scratch vector
+struct CHBatchPrec : BatchPrecond {
+  chnss_ctx *c;
+  explicit CHBatchPrec(chnss_ctx *c_) : c(c_) {}
+  void apply(int K, const double *const *r, double *const *z, cudaStream_t s) override;
+  void after_sync() override;
+};
+
 void harvest_probes(chnss_ctx *c) {
   if (c->pending_probe >= 0) {
     const PrecGraph &pg = c->pg[c->pending_probe];
@@ -253,6 +295,25 @@ void harvest_probes(chnss_ctx *c) {
     c->pending_probe = -1;
   }
 }
+
+void CHBatchPrec::apply(int K, const double *const *r, double *const *z, cudaStream_t s) {
+  const void *ptrs[6];
+  for (int k = 0; k < 3; ++k) {
+    ptrs[2 * k] = k < K && r[k] ? r[k] : c->dummy_in;
+    ptrs[2 * k + 1] = k < K && z[k] ? z[k] : c->dummy_out;
+  }
+  set_ptr_slots_n(reinterpret_cast<void **>(c->slots + kBatchSlot), 6, ptrs, s);
+  PrecGraph &pg = c->pg[5];
+  if (!pg.plain) {
+    prec_body(c, 5, s);
+    return;
+  }
+  const bool prof = c->prof.on && pg.prof;
+  CHNSS_CK(cudaGraphLaunch(prof ? pg.prof : pg.plain, s));
+  g_launch_count.fetch_add(pg.nodes, std::memory_order_relaxed);
+  if (prof) c->pending_probe = 5;
+}
+void CHBatchPrec::after_sync() { harvest_probes(c); }
 
 struct CHOp : LinearOperator {
   chnss_ctx *c;
@@ -305,6 +366,7 @@ struct NSOp : LinearOperator {
 void capture_graphs(chnss_ctx *c) {
   CHNSS_CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   for (int g = 0; g < kNumPrec; ++g) {
+    if (g == 5 && !c->ch_batch) continue;
     PrecGraph &pg = c->pg[g];
     pg.probes.resize(kMaxProbes);
     for (Profiler::Probe &pr : pg.probes) {
@@ -393,6 +455,18 @@ void init_precset(chnss_ctx *c, PrecSet<T> &P) {
     h->prof = &c->prof;
   P.Kp.setup(c->s);
   for (int sp = 0; sp < 3; ++sp) P.X1[sp].setup(c->s);
+  if (c->p.mobility_kind == 0) {
+    // species with equal (gamma, beta) have bitwise equal X1 = tau gamma K + sqrt(tau gamma / beta) M
+    P.LB.init(ar, &P.L, 3);
+    for (int sp = 0; sp < 3; ++sp) {
+      int g = 0;
+      while (g < P.ngroups && !(c->p.gamma[P.gmem[g][0]] == c->p.gamma[sp] && c->p.beta[P.gmem[g][0]] == c->p.beta[sp])) ++g;
+      if (g == P.ngroups) ++P.ngroups;
+      P.gmem[g][P.gsize[g]++] = sp;
+    }
+    for (int g = 0; g < P.ngroups; ++g) P.XB[g].init(ar, &P.X1[P.gmem[g][0]], P.gsize[g]);
+    c->ch_batch = true;
+  }
 }
 
 template <typename T>
@@ -414,7 +488,7 @@ void create_context(chnss_ctx *c) {
   c->N1 = m.lv[0].N1;
   c->N2 = m.lv[0].N2;
   c->E = m.lv[0].E;
-  CHNSS_CK(cudaHostAlloc(&c->pinned, 16 * sizeof(double), cudaHostAllocDefault));
+  CHNSS_CK(cudaHostAlloc(&c->pinned, 32 * sizeof(double), cudaHostAllocDefault));
   upload_reference_tensors(s);
   c->ebuf = ar.alloc<double>(144L * c->E);
   c->lbuf = ar.alloc<double>(15L * c->E);
@@ -526,6 +600,13 @@ void create_context(chnss_ctx *c) {
     c->massc = ar.upload(mc);
   }
   c->kw.init(ar, p.restart, 2L * c->N2 + c->N1, c->pinned + 8);
+  if (p.mobility_kind == 0) {
+    c->kwb[0].init(ar, p.restart, 2L * c->N1, c->pinned + 16);
+    c->kwb[1].init(ar, p.restart, 2L * c->N1, c->pinned + 20);
+    c->dummy_in = ar.alloc<double>(2L * c->N1);
+    c->dummy_out = ar.alloc<double>(2L * c->N1);
+    vec_fill(2L * c->N1, 0.0, c->dummy_in, s);
+  }
   if (p.precision >= 1) {
     c->p32.reset(new PrecSet<float>());
     init_precset(c, *c->p32);
@@ -533,7 +614,7 @@ void create_context(chnss_ctx *c) {
     c->p64.reset(new PrecSet<double>());
     init_precset(c, *c->p64);
   }
-  c->slots = ar.alloc<double *>(2 * kNumPrec);
+  c->slots = ar.alloc<double *>(2 * kNumPrec + 6);
   CHNSS_CK(cudaStreamSynchronize(s));
   capture_graphs(c);
   CHNSS_CK(cudaStreamSynchronize(s));
@@ -700,8 +781,20 @@ chnss_status step(chnss_ctx *c, const chnss_state *in, chnss_state *out, chnss_s
   const int N1 = c->N1;
   chnss_status worst = CHNSS_OK;
   auto keep = [&](chnss_status st) { if (worst == CHNSS_OK) worst = st; };
+  if (c->ch_batch) {
+    // the three CH systems together: one batched preconditioner per tick
+    CHOp o0(c, 0), o1(c, 1), o2(c, 2);
+    LinearOperator *ops[3] = {&o0, &o1, &o2};
+    const double *bs[3] = {c->rhs[0], c->rhs[1], c->rhs[2]};
+    double *xs[3] = {c->xsol[0], c->xsol[1], c->xsol[2]};
+    KrylovWork *wss[3] = {&c->kw, &c->kwb[0], &c->kwb[1]};
+    CHBatchPrec bp(c);
+    keep(fgmres_batch(3, ops, bs, xs, c->p.rtol, c->p.atol, c->p.maxit, wss, inf, bp, s, &c->prof));
+    for (int sp = 0; sp < 3; ++sp) c->ch_done[sp] = true;
+  } else {
+    for (int sp = 0; sp < 3; ++sp) keep(solve(c, sp, nullptr, c->xsol[sp], &inf[sp]));
+  }
   for (int sp = 0; sp < 3; ++sp) {
-    keep(solve(c, sp, nullptr, c->xsol[sp], &inf[sp]));
     vec_copy(N1, c->xsol[sp], out->phi[sp], s);
     vec_copy(N1, c->xsol[sp] + N1, out->mu[sp], s);
   }

@@ -14,6 +14,19 @@ namespace chnss {
 //   CHEB   out = c0 u + c1 w + c2 dinv (b - A u), (c0, c1, c2) = coef[0..2] (device)
 enum SpmvMode { SPMV_PLAIN = 0, SPMV_RES = 1, SPMV_ADD = 2, SPMV_CHEB = 3 };
 
+// Up to kMaxRhs vectors that share one matrix (multi-right-hand-side kernels).
+constexpr int kMaxRhs = 3;
+template <typename T>
+struct MultiPtr {
+  T *p[kMaxRhs] = {nullptr, nullptr, nullptr};
+};
+template <typename T>
+struct MultiArgs {              // per-vector b and w, shared Jacobi diagonal and coefficients
+  MultiPtr<T> b, w;
+  const T *dinv = nullptr;
+  const double *coef = nullptr;
+};
+
 struct SpmvArgs {
   const void *b = nullptr;      // T*
   const void *w = nullptr;      // T*  (CHEB)
@@ -44,6 +57,19 @@ void spmv_sell(const Pattern &P, const T *sval, int ncomp, const T *u, T *out, S
 template <typename T>
 void spmv_sell_bsr2(const Pattern &P, const T *sval, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
                     cudaStream_t s);
+// nr (1..3) vectors through one scalar matrix with rows of at most 8 entries;
+// each output is bitwise the single-vector result (same per-row order).
+template <typename T>
+void spmv_sell_multi(const Pattern &P, const T *sval, int nr, const MultiPtr<T> &u, const MultiPtr<T> &out,
+                     SpmvMode mode, const MultiArgs<T> &a, cudaStream_t s);
+template <typename T>
+void vec_scale_dinv_multi(int n, int nr, const double *scale, const T *dinv, const MultiPtr<T> &b,
+                          const MultiPtr<T> &out, cudaStream_t s);
+template <typename T>
+void dense_apply_multi(int n, int nr, const double *inv, const MultiPtr<T> &b, const MultiPtr<T> &x,
+                       cudaStream_t s);
+template <typename T>
+void vec_copy_multi(long n, int nr, const MultiPtr<T> &in, const MultiPtr<T> &out, cudaStream_t s);
 // BF16-stored values, FP32 vectors and accumulation (preconditioner variant)
 void spmv_sell(const Pattern &P, const __nv_bfloat16 *sval, int ncomp, const float *u, float *out, SpmvMode mode,
                const SpmvArgs &a, cudaStream_t s);
@@ -88,7 +114,9 @@ template <typename Ta, typename Tb>
 void vec_convert_from_slot(long n, const Ta *const *slot, long off, Tb *out, cudaStream_t s);
 template <typename Ta, typename Tb>
 void vec_convert_to_slot(long n, const Ta *in, Tb *const *slot, long off, cudaStream_t s);
-void set_ptr_slots(void **slots, const void *a, const void *b, cudaStream_t s);   // slots[0] = a, slots[1] = b
+void set_ptr_slots(void **slots, const void *a, const void *b, cudaStream_t s);
+// slots[0..n) = ptrs[0..n) (host array of device pointers, n <= 8)
+void set_ptr_slots_n(void **slots, int n, const void *const *ptrs, cudaStream_t s);   // slots[0] = a, slots[1] = b
 void vec_axpby(long n, double a, const double *x, double b, double *y, cudaStream_t s);      // y = a x + b y
 void vec_copy(long n, const double *x, double *y, cudaStream_t s);
 void vec_fill(long n, double v, double *y, cudaStream_t s);

@@ -279,6 +279,103 @@ template struct MGHier<double>;
 template struct MGHier<float>;
 
 // ---------------------------------------------------------------------------
+template <typename T>
+void MGBatch<T>::init(Arena &ar, MGHier<T> *hier, int nr_) {
+  if (hier->kind != 0 || hier->singular || hier->bf16)
+    throw Error{CHNSS_ERR_ARG, "batched V-cycle: scalar, non-singular, non-BF16 hierarchies only"};
+  if (nr_ < 1 || nr_ > kMaxRhs) throw Error{CHNSS_ERR_ARG, "batched V-cycle: 1 to 3 vectors"};
+  h = hier;
+  nr = nr_;
+  const int nl = h->nl;
+  x.assign(nl, MultiPtr<T>());
+  t.assign(nl, MultiPtr<T>());
+  r.assign(nl, MultiPtr<T>());
+  b.assign(nl, MultiPtr<T>());
+  for (int l = 0; l < nl; ++l)
+    for (int k = 0; k < nr; ++k) {
+      x[l].p[k] = ar.alloc<T>(h->n[l]);
+      t[l].p[k] = ar.alloc<T>(h->n[l]);
+      r[l].p[k] = ar.alloc<T>(h->n[l]);
+      b[l].p[k] = ar.alloc<T>(h->n[l]);
+    }
+}
+
+template <typename T>
+void MGBatch<T>::op(int l, const MultiPtr<T> &u, const MultiPtr<T> &out, SpmvMode mode, const MultiArgs<T> &a,
+                    cudaStream_t s) {
+  Profiler *prof = h->prof;
+  const bool timed = prof && l == 0;
+  if (timed) prof->start(Profiler::P1_SPMV_L0, s);
+  spmv_sell_multi<T>(*h->pat[l], h->val[l], nr, u, out, mode, a, s);
+  if (timed) {
+    // one matrix stream for nr vectors
+    const long nnz = h->pat[l]->nnz, nrows = h->pat[l]->nrows;
+    double extra = 0.0;
+    if (mode == SPMV_RES || mode == SPMV_ADD) extra = 1.0;
+    if (mode == SPMV_CHEB) extra = a.w.p[0] ? 3.0 : 2.0;
+    const double bytes = (double)nnz * (sizeof(T) + 4.0) + 4.0 * (nrows + 1) +
+                         (double)nr * (2.0 + extra) * h->n[l] * sizeof(T) + (mode == SPMV_CHEB ? h->n[l] * sizeof(T) : 0.0);
+    prof->stop(Profiler::P1_SPMV_L0, s, bytes);
+  }
+}
+
+template <typename T>
+void MGBatch<T>::vcycle(int l, cudaStream_t s) {
+  const int nl = h->nl;
+  if (l == nl - 1) {
+    dense_apply_multi<T>(h->nc, nr, h->cinv, b[l], x[l], s);
+    return;
+  }
+  const int n = (int)h->n[l];
+  const int degree = h->degree;
+  MultiArgs<T> a;
+  a.b = b[l];
+  a.dinv = h->dinv[l];
+  // same buffer rotation as MGHier<T>::vcycle
+  MultiPtr<T> cur = (degree - 1) % 2 == 0 ? x[l] : t[l];
+  MultiPtr<T> oth = (degree - 1) % 2 == 0 ? t[l] : x[l];
+  vec_scale_dinv_multi<T>(n, nr, h->coef[l], h->dinv[l], b[l], cur, s);
+  for (int k = 1; k < degree; ++k) {
+    a.coef = h->coef[l] + 4 + 3 * (k - 1);
+    a.w = k == 1 ? MultiPtr<T>() : oth;
+    op(l, cur, oth, SPMV_CHEB, a, s);
+    std::swap(cur, oth);
+  }
+  MultiArgs<T> ar;
+  ar.b = b[l];
+  op(l, x[l], r[l], SPMV_RES, ar, s);
+  const Transfer &T_ = *h->tr[l];
+  const T *Rv = std::is_same<T, double>::value ? reinterpret_cast<const T *>(T_.Rs) : reinterpret_cast<const T *>(T_.Rs32);
+  const T *Pv = std::is_same<T, double>::value ? reinterpret_cast<const T *>(T_.Ps) : reinterpret_cast<const T *>(T_.Ps32);
+  MultiArgs<T> none;
+  spmv_sell_multi<T>(T_.R, Rv, nr, r[l], b[l + 1], SPMV_PLAIN, none, s);
+  if (h->prof && l == 0) h->prof->start(Profiler::P1_MG_COARSE, s);
+  vcycle(l + 1, s);
+  if (h->prof && l == 0) h->prof->stop(Profiler::P1_MG_COARSE, s, 0.0);
+  spmv_sell_multi<T>(T_.P, Pv, nr, x[l + 1], x[l], SPMV_ADD, none, s);
+  a.coef = h->coef[l] + 1;
+  a.w = MultiPtr<T>();
+  op(l, x[l], t[l], SPMV_CHEB, a, s);
+  cur = t[l];
+  oth = x[l];
+  for (int k = 1; k < degree; ++k) {
+    a.coef = h->coef[l] + 4 + 3 * (k - 1);
+    a.w = oth;
+    op(l, cur, oth, SPMV_CHEB, a, s);
+    std::swap(cur, oth);
+  }
+  if (cur.p[0] != x[l].p[0]) vec_copy_multi<T>(n, nr, cur, x[l], s);
+}
+
+template <typename T>
+void MGBatch<T>::apply(cudaStream_t s) {
+  vcycle(0, s);
+}
+
+template struct MGBatch<double>;
+template struct MGBatch<float>;
+
+// ---------------------------------------------------------------------------
 void KrylovWork::init(Arena &ar, int m_, long nmax_, double *pinned) {
   m = m_;
   nmax = nmax_;
@@ -402,6 +499,168 @@ chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, 
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   return st;
+}
+
+chnss_status fgmres_batch(int K, LinearOperator *const *A, const double *const *b, double *const *x, double rtol,
+                          double atol, int maxit, KrylovWork *const *ws, chnss_solve_info *info, BatchPrecond &P,
+                          cudaStream_t s, Profiler *prof) {
+  const auto t0 = std::chrono::steady_clock::now();
+  struct Run {
+    long n = 0, ld = 0;
+    int m = 0, ldh = 0, j = 0, k = 0, iters = 0;
+    double bnorm = 0, target = 0, rnorm = 0;
+    chnss_status st = CHNSS_OK;
+    bool converged = false, done = false, breakdown = false, cycle_start = false, end_cycle = false, fast = false;
+  };
+  std::vector<Run> R(K);
+  // ||b|| of every system, one synchronisation
+  for (int q = 0; q < K; ++q) {
+    Run &r = R[q];
+    KrylovWork &w = *ws[q];
+    r.n = A[q]->size();
+    r.ld = (r.n + 31) / 32 * 32;
+    r.m = w.m;
+    r.ldh = r.m + 1;
+    vec_fill(r.n, 0.0, x[q], s);
+    dot<double>(r.n, b[q], b[q], w.sc, w.partial, s);
+    CHNSS_CK(cudaMemcpyAsync(w.hstat, w.sc, sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  CHNSS_CK(cudaStreamSynchronize(s));
+  for (int q = 0; q < K; ++q) {
+    Run &r = R[q];
+    KrylovWork &w = *ws[q];
+    r.bnorm = std::sqrt(w.hstat[0]);
+    r.target = std::max(rtol * r.bnorm, atol);
+    r.rnorm = r.bnorm;
+    if (!std::isfinite(r.bnorm)) {
+      r.st = CHNSS_ERR_NAN;
+      r.done = true;
+    } else if (r.rnorm <= r.target) {
+      r.converged = true;
+      r.done = true;
+    } else {
+      vec_copy(r.n, b[q], w.w, s);
+      set_scalar(w.sc + 2, w.sc, 1.0, true, s);   // ||r||
+      r.cycle_start = true;
+    }
+  }
+  std::vector<const double *> rin(K);
+  std::vector<double *> zout(K);
+  while (true) {
+    bool any = false;
+    for (int q = 0; q < K; ++q) {
+      Run &r = R[q];
+      KrylovWork &w = *ws[q];
+      rin[q] = nullptr;
+      zout[q] = nullptr;
+      if (r.done) continue;
+      if (r.cycle_start) {
+        vec_scale_by_inv(r.n, w.w, w.sc + 2, w.V, s);
+        vec_fill(r.m + 1, 0.0, w.g, s);
+        set_scalar(w.g, w.sc + 2, 1.0, false, s);
+        r.j = 0;
+        r.breakdown = false;
+        r.cycle_start = false;
+      }
+      rin[q] = w.V + (long)r.j * r.ld;
+      zout[q] = w.Z + (long)r.j * r.ld;
+      any = true;
+    }
+    if (!any) break;
+    P.apply(K, rin.data(), zout.data(), s);
+    for (int q = 0; q < K; ++q) {
+      Run &r = R[q];
+      if (!rin[q]) continue;
+      KrylovWork &w = *ws[q];
+      const long n = r.n, ld = r.ld;
+      double *sc = w.sc;
+      A[q]->apply(zout[q], w.w, s);
+      const int kv = r.j + 1;
+      r.fast = cgs2_fast(kv);
+      if (prof) prof->start(Profiler::ORTHO, s);
+      if (r.fast) {
+        cgs2_dots(n, w.V, ld, kv, w.w, w.h1, w.partial, s);
+        cgs2_update_dots(n, w.V, ld, kv, w.h1, w.w, w.h2, w.partial, s);
+        if (prof) prof->stop(Profiler::ORTHO, s, 8.0 * n * (2.0 * kv + 3.0), 2.0 * n * (3.0 * kv + 1.0));
+        arnoldi_finish_pyth(r.j, r.ldh, w.H, w.h1, w.h2, w.cs, w.sn, w.g, sc + 4, s);
+      } else {
+        mdot(n, w.V, ld, kv, w.w, w.h1, w.partial, s);
+        ortho_update_mdot(n, w.V, ld, kv, w.h1, w.w, w.h2, w.partial, s);
+        ortho_update_norm(n, w.V, ld, kv, w.h2, w.w, sc + 3, w.partial, s);
+        if (prof) prof->stop(Profiler::ORTHO, s, 8.0 * n * (3.0 * kv + 5.0), 2.0 * n * (4.0 * kv + 1.0));
+        arnoldi_finish(r.j, r.ldh, w.H, w.h1, w.h2, sc + 3, w.cs, w.sn, w.g, sc + 4, s);
+      }
+      CHNSS_CK(cudaMemcpyAsync(w.hstat, sc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    CHNSS_CK(cudaStreamSynchronize(s));
+    P.after_sync();
+    for (int q = 0; q < K; ++q)
+      if (rin[q]) A[q]->after_sync();
+    bool any_end = false;
+    for (int q = 0; q < K; ++q) {
+      Run &r = R[q];
+      if (!rin[q]) continue;
+      KrylovWork &w = *ws[q];
+      const double est = w.hstat[0], hn = w.hstat[1];
+      ++r.iters;
+      r.k = r.j + 1;
+      if (!std::isfinite(est) || !std::isfinite(hn)) {
+        r.st = CHNSS_ERR_NAN;
+        r.done = true;
+        continue;
+      }
+      r.breakdown = hn == 0.0;
+      if (!r.breakdown && r.fast) {
+        if (prof) prof->start(Profiler::ORTHO, s);
+        cgs2_update_scale(r.n, w.V, r.ld, r.k, w.h2, w.w, w.sc + 5, w.V + (long)(r.j + 1) * r.ld, s);
+        if (prof) prof->stop(Profiler::ORTHO, s, 8.0 * r.n * (r.k + 2.0), 2.0 * r.n * r.k, 0);
+      } else if (!r.breakdown) {
+        vec_scale_by_inv(r.n, w.w, w.sc + 5, w.V + (long)(r.j + 1) * r.ld, s);
+      }
+      if (est <= r.target || r.iters >= maxit || r.breakdown) {
+        r.end_cycle = true;
+      } else if (++r.j == r.m) {
+        r.end_cycle = true;
+      }
+      if (r.end_cycle) {
+        // x += Z y; true residual
+        hessenberg_solve(r.k, r.ldh, w.H, w.g, w.y, s);
+        combine_columns(r.n, w.Z, r.ld, r.k, w.y, x[q], s);
+        A[q]->apply(x[q], w.w, s);
+        vec_axpby(r.n, 1.0, b[q], -1.0, w.w, s);
+        dot<double>(r.n, w.w, w.w, w.sc + 1, w.partial, s);
+        set_scalar(w.sc + 2, w.sc + 1, 1.0, true, s);
+        CHNSS_CK(cudaMemcpyAsync(w.hstat, w.sc + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+        any_end = true;
+      }
+    }
+    if (!any_end) continue;
+    CHNSS_CK(cudaStreamSynchronize(s));
+    for (int q = 0; q < K; ++q) {
+      Run &r = R[q];
+      if (!r.end_cycle) continue;
+      r.end_cycle = false;
+      r.rnorm = std::sqrt(ws[q]->hstat[0]);
+      if (!std::isfinite(r.rnorm)) { r.st = CHNSS_ERR_NAN; r.done = true; }
+      else if (r.rnorm <= r.target) { r.converged = true; r.done = true; }
+      else if (r.iters >= maxit) { r.st = CHNSS_ERR_NOCONV; r.done = true; }
+      else if (r.breakdown) { r.st = CHNSS_ERR_BREAKDOWN; r.done = true; }
+      else r.cycle_start = true;
+    }
+  }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  chnss_status worst = CHNSS_OK;
+  for (int q = 0; q < K; ++q) {
+    const Run &r = R[q];
+    if (info) {
+      info[q].iters = r.iters;
+      info[q].converged = r.converged ? 1 : 0;
+      info[q].rel_residual = r.bnorm > 0 ? r.rnorm / r.bnorm : 0.0;
+      info[q].seconds = secs;
+    }
+    if (worst == CHNSS_OK) worst = r.st;
+  }
+  return worst;
 }
 
 chnss_status pcg(const Pattern &P, const double *val, const double *dinv, const double *b, double *x, double rtol,

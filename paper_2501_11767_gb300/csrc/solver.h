@@ -88,6 +88,27 @@ struct MGHier {
   void vcycle(int l, cudaStream_t s);
 };
 
+// The same V-cycle as MGHier<T> (kind 0: scalar P1 operators, non-singular)
+// on nr <= kMaxRhs vectors at once: the hierarchy's matrices, Jacobi data,
+// coefficients, transfers and coarse inverse are shared; every sweep reads
+// the matrix once for all vectors (spmv_sell_multi).  Vector k's result is
+// bitwise the one MGHier<T>::apply gives for it alone.
+template <typename T>
+struct MGBatch {
+  MGHier<T> *h = nullptr;
+  int nr = 0;
+  std::vector<MultiPtr<T>> x, t, r, b;     // per level
+  void init(Arena &ar, MGHier<T> *hier, int nr);
+  T *input(int k) { return b[0].p[k]; }
+  T *output(int k) { return x[0].p[k]; }
+  void apply(cudaStream_t s);
+
+ private:
+  void op(int l, const MultiPtr<T> &u, const MultiPtr<T> &out, SpmvMode mode, const MultiArgs<T> &a,
+          cudaStream_t s);
+  void vcycle(int l, cudaStream_t s);
+};
+
 struct LinearOperator {
   virtual ~LinearOperator() = default;
   virtual long size() const = 0;
@@ -111,6 +132,22 @@ struct KrylovWork {
 // residual satisfies ||b - A x|| <= max(rtol ||b||, atol) (Sec. 5).
 chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, double atol, int maxit,
                     KrylovWork &ws, chnss_solve_info *info, cudaStream_t s, Profiler *prof = nullptr);
+
+// Several independent FGMRES solves advanced together: every tick applies
+// one batched preconditioner to the current basis vector of each active
+// solve (one call, e.g. one graph launch), then runs each solve's operator,
+// CGS2 and Givens step, and synchronises the stream once for all of them.
+// Per solve, the arithmetic and its order are those of fgmres(), so the
+// iterates are bitwise the same as solving one system after the other.
+struct BatchPrecond {
+  virtual ~BatchPrecond() = default;
+  // z[k] = P_k r[k] for k < K; r[k] == nullptr: solve k is idle this tick
+  virtual void apply(int K, const double *const *r, double *const *z, cudaStream_t s) = 0;
+  virtual void after_sync() {}
+};
+chnss_status fgmres_batch(int K, LinearOperator *const *A, const double *const *b, double *const *x, double rtol,
+                          double atol, int maxit, KrylovWork *const *ws, chnss_solve_info *info, BatchPrecond &P,
+                          cudaStream_t s, Profiler *prof = nullptr);
 
 // Jacobi PCG for an SPD CSR matrix (FP64), x0 = 0, recursive residual test.
 chnss_status pcg(const Pattern &P, const double *val, const double *dinv, const double *b, double *x, double rtol,

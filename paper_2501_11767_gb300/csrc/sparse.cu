@@ -810,6 +810,90 @@ __global__ void k_dense_apply(int n, const double *inv, const T *b, T *x) {
 
 
 // ---------------------------------------------------------------------------
+// Multi-right-hand-side variants (up to kMaxRhs vectors sharing one matrix):
+// the matrix stream is read once, each right-hand side is summed in the same
+// order as by the single-vector kernels, so every output is bitwise the one
+// the single-vector kernel would give.
+template <typename T, int NR>
+__global__ void __launch_bounds__(kSellMaxBlock) k_sell_w8m(int nslices, const int *__restrict__ sp,
+                                                   const int *__restrict__ rowid, const int *__restrict__ col,
+                                                   const T *__restrict__ val, MultiPtr<T> u, MultiPtr<T> out,
+                                                   int mode, MultiArgs<T> a) {
+  const int slice = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (slice >= nslices) return;
+  const int row = rowid[slice * 32 + lane];
+  const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
+  T bi[NR], ui[NR], wi[NR], oi[NR];
+  T di = 0;
+#pragma unroll
+  for (int k = 0; k < NR; ++k) bi[k] = ui[k] = wi[k] = oi[k] = 0;
+  if (row >= 0) {
+    if (mode == SPMV_CHEB) di = a.dinv[row];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      if (mode == SPMV_RES || mode == SPMV_CHEB) bi[k] = a.b.p[k][row];
+      if (mode == SPMV_CHEB) {
+        ui[k] = u.p[k][row];
+        if (a.w.p[k]) wi[k] = a.w.p[k][row];
+      }
+      if (mode == SPMV_ADD) oi[k] = out.p[k][row];
+    }
+  }
+  int c[8];
+  T v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    if (j < w) {
+      c[j] = col[b0 + j * 32 + lane];
+      v[j] = val[b0 + j * 32 + lane];
+    }
+  }
+  T acc[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    acc[k] = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (j < w) acc[k] += v[j] * u.p[k][c[j]];
+  }
+  if (row < 0) return;
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    T r;
+    if (mode == SPMV_PLAIN) r = acc[k];
+    else if (mode == SPMV_RES) r = bi[k] - acc[k];
+    else if (mode == SPMV_ADD) r = oi[k] + acc[k];
+    else r = cheb_row<T>(a.coef, ui[k], di, bi[k], acc[k], a.w.p[k] != nullptr, wi[k]);
+    out.p[k][row] = r;
+  }
+}
+
+template <typename T>
+__global__ void k_scale_dinv_m(int n, int nr, const double *scale, const T *dinv, MultiPtr<T> b, MultiPtr<T> out) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i >= n) return;
+  for (int k = 0; k < nr; ++k) out.p[k][i] = (T)(*scale) * dinv[i] * b.p[k][i];
+}
+
+template <typename T>
+__global__ void k_dense_apply_m(int n, int nr, const double *inv, MultiPtr<T> b, MultiPtr<T> x) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  for (int k = 0; k < nr; ++k) {
+    double s = 0.0;
+    for (int c = 0; c < n; ++c) s += inv[(long)r * n + c] * (double)b.p[k][c];
+    x.p[k][r] = (T)s;
+  }
+}
+
+template <typename T>
+__global__ void k_copy_m(long n, int nr, MultiPtr<T> in, MultiPtr<T> out) {
+  const long i = (long)blockIdx.x * TPB + threadIdx.x;
+  if (i >= n) return;
+  for (int k = 0; k < nr; ++k) out.p[k][i] = in.p[k][i];
+}
+
+// ---------------------------------------------------------------------------
 // CGS2 orthogonalisation kernels for k <= kCgsMaxK basis vectors.  The vector
 // count is a template parameter, so every issued FP64 FMA is useful work (the
 // FP64 pipe bounds these kernels on this part).  Each block reduces its NV
@@ -1154,6 +1238,20 @@ template void vec_convert_from_slot<double, float>(long, const double *const *, 
 template void vec_convert_from_slot<double, double>(long, const double *const *, long, double *, cudaStream_t);
 template void vec_convert_to_slot<float, double>(long, const float *, double *const *, long, cudaStream_t);
 template void vec_convert_to_slot<double, double>(long, const double *, double *const *, long, cudaStream_t);
+struct PtrPack {
+  const void *p[8];
+};
+__global__ void k_set_ptrs_n(void **slots, int n, PtrPack pk) {
+  for (int i = 0; i < n; ++i) slots[i] = const_cast<void *>(pk.p[i]);
+}
+void set_ptr_slots_n(void **slots, int n, const void *const *ptrs, cudaStream_t s) {
+  if (n < 1 || n > 8) throw Error{CHNSS_ERR_ARG, "set_ptr_slots_n: 1 to 8 pointers"};
+  PtrPack pk{};
+  for (int i = 0; i < n; ++i) pk.p[i] = ptrs[i];
+  k_set_ptrs_n<<<1, 1, 0, s>>>(slots, n, pk);
+  CHNSS_LAUNCH_CK();
+}
+
 void set_ptr_slots(void **slots, const void *a, const void *b, cudaStream_t s) {
   k_set_ptrs<<<1, 1, 0, s>>>(slots, a, b);
   CHNSS_LAUNCH_CK();
@@ -1349,5 +1447,56 @@ void dense_apply(int n, const double *inv, const T *b, T *x, cudaStream_t s) {
 }
 template void dense_apply<double>(int, const double *, const double *, double *, cudaStream_t);
 template void dense_apply<float>(int, const double *, const float *, float *, cudaStream_t);
+
+template <typename T>
+void spmv_sell_multi(const Pattern &P, const T *sval, int nr, const MultiPtr<T> &u, const MultiPtr<T> &out,
+                     SpmvMode mode, const MultiArgs<T> &a, cudaStream_t s) {
+  const Sell &S = P.sell;
+  if (S.nslices == 0) return;
+  if (S.wmax > 8) throw Error{CHNSS_ERR_ARG, "multi-vector SpMV needs rows of at most 8 entries"};
+  const int nb = nblocks((long)S.nslices * 32, S.block);
+  switch (nr) {
+    case 1: k_sell_w8m<T, 1><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a); break;
+    case 2: k_sell_w8m<T, 2><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a); break;
+    case 3: k_sell_w8m<T, 3><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a); break;
+    default: throw Error{CHNSS_ERR_ARG, "multi-vector SpMV: 1 to 3 vectors"};
+  }
+  CHNSS_LAUNCH_CK();
+}
+template void spmv_sell_multi<double>(const Pattern &, const double *, int, const MultiPtr<double> &,
+                                      const MultiPtr<double> &, SpmvMode, const MultiArgs<double> &, cudaStream_t);
+template void spmv_sell_multi<float>(const Pattern &, const float *, int, const MultiPtr<float> &,
+                                     const MultiPtr<float> &, SpmvMode, const MultiArgs<float> &, cudaStream_t);
+
+template <typename T>
+void vec_scale_dinv_multi(int n, int nr, const double *scale, const T *dinv, const MultiPtr<T> &b,
+                          const MultiPtr<T> &out, cudaStream_t s) {
+  k_scale_dinv_m<T><<<nblocks(n, TPB), TPB, 0, s>>>(n, nr, scale, dinv, b, out);
+  CHNSS_LAUNCH_CK();
+}
+template void vec_scale_dinv_multi<double>(int, int, const double *, const double *, const MultiPtr<double> &,
+                                           const MultiPtr<double> &, cudaStream_t);
+template void vec_scale_dinv_multi<float>(int, int, const double *, const float *, const MultiPtr<float> &,
+                                          const MultiPtr<float> &, cudaStream_t);
+
+template <typename T>
+void dense_apply_multi(int n, int nr, const double *inv, const MultiPtr<T> &b, const MultiPtr<T> &x,
+                       cudaStream_t s) {
+  k_dense_apply_m<T><<<nblocks(n, 128), 128, 0, s>>>(n, nr, inv, b, x);
+  CHNSS_LAUNCH_CK();
+}
+template void dense_apply_multi<double>(int, int, const double *, const MultiPtr<double> &, const MultiPtr<double> &,
+                                        cudaStream_t);
+template void dense_apply_multi<float>(int, int, const double *, const MultiPtr<float> &, const MultiPtr<float> &,
+                                       cudaStream_t);
+
+template <typename T>
+void vec_copy_multi(long n, int nr, const MultiPtr<T> &in, const MultiPtr<T> &out, cudaStream_t s) {
+  if (n == 0) return;
+  k_copy_m<T><<<nblocks(n, TPB), TPB, 0, s>>>(n, nr, in, out);
+  CHNSS_LAUNCH_CK();
+}
+template void vec_copy_multi<double>(long, int, const MultiPtr<double> &, const MultiPtr<double> &, cudaStream_t);
+template void vec_copy_multi<float>(long, int, const MultiPtr<float> &, const MultiPtr<float> &, cudaStream_t);
 
 }  // namespace chnss

@@ -191,6 +191,30 @@ def test_mixed_precision_step(torch, precision):
         st = ref
 
 
+@pytest.mark.parametrize("precision,beta", [(0, None), (1, None), (1, [0.02, 0.03, 0.1, 1.0]),
+                                            (0, [0.05, 0.05, 0.05, 1.0])])
+def test_batched_ch_solves_equal_single_solves(torch, precision, beta):
+    """chnss_step solves the three CH systems together (one batched
+    preconditioner per Krylov tick, shared matrix sweeps); each species must
+    come out bitwise as its own chnss_solve, for 1, 2 and 3 groups of equal
+    Schur factors."""
+    n = 32
+    p = dict(inputs.default_params(), precision=precision)
+    if beta:
+        p["beta"] = beta
+    mesh = chnss.Mesh(n)
+    st = chnss.state_to_device(inputs.initial_state(n, seed=11))
+    out, info, status = chnss.Context(mesh, p).step(st)
+    assert status == 0
+    c2 = chnss.Context(mesh, p)
+    c2.assemble(st)
+    N1 = mesh.N1
+    for sp, name in enumerate(("ch_p", "ch_N", "ch_s")):
+        x, i2, _ = c2.solve(sp)
+        assert i2["iters"] == info[name]["iters"], name
+        assert bool((x[:N1] == out["phi"][sp]).all()) and bool((x[N1:] == out["mu"][sp]).all()), name
+
+
 def test_restart_longer_than_the_templated_cgs2(torch):
     """FGMRES(40): Arnoldi steps with more than 31 basis vectors take the
     generic CGS2 kernels; the step must still match the oracle."""
