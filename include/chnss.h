@@ -136,8 +136,20 @@ chnss_status chnss_solve(chnss_ctx_t ctx, chnss_system sys, const double *rhs_or
 
 /* One semi-implicit step t_k -> t_{k+1}: assemble, the three CH solves, AC,
  * the air potential, NS.  `in` and `out` must not alias.  info[6] (optional)
- * is filled in chnss_system order. */
+ * is filled in chnss_system order.  With every coefficient taken at t_k
+ * (Sec. 3) the CH systems (+ air potential), AC and NS are independent once
+ * assembled: by default they run concurrently on three library-owned
+ * streams driven by three host threads (the call spawns two), ordered after
+ * the assembly on the context stream, which waits for all three before the
+ * call returns.  With constant mobility the three CH systems are solved
+ * together (one batched preconditioner per Krylov iteration).  Results are
+ * bitwise the same as solving every system alone with chnss_solve.  The
+ * returned status is the first failure in the order CH (p, NFA, s), AC, air
+ * potential, NS. */
 chnss_status chnss_step(chnss_ctx_t ctx, const chnss_state *in, chnss_state *out, chnss_solve_info *info);
+/* on = 0: chnss_step runs the three solve groups one after the other on the
+ * context stream's host thread (same results); on != 0 (default): concurrently. */
+chnss_status chnss_set_step_concurrency(chnss_ctx_t ctx, int on);
 
 /* Same step with HOST arrays (same layout as chnss_state): copies the input
  * to library-owned device fields, steps, copies the result back and

@@ -108,6 +108,7 @@ EXPORTS = {
                                           ctypes.POINTER(State), ctypes.POINTER(SolveInfo), ctypes.c_int]),
     "chnss_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Tuning)]),
     "chnss_set_spmv_block": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "chnss_set_step_concurrency": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
 }
 
@@ -322,6 +323,11 @@ class Context:
         t = Tuning()
         _check(load().chnss_autotune(self._h, ctypes.byref(t)), self._h)
         return t.as_dict()
+
+    def set_step_concurrency(self, on: bool):
+        """chnss_set_step_concurrency: solve CH, AC and NS of a step on three
+        streams at once (default) or one after the other."""
+        _check(load().chnss_set_step_concurrency(self._h, 1 if on else 0), self._h)
 
     def set_spmv_block(self, block_p1: int, block_p2: int):
         """Pin the SpMV threads-per-block of the mesh's scalar and velocity

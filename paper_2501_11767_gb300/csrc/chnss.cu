@@ -139,8 +139,15 @@ struct chnss_ctx {
   bool ch_batch = false;                    // step() solves the CH species together
   KrylovWork kwb[2];                        // Krylov work of the 2nd and 3rd CH species
   double *dummy_in = nullptr, *dummy_out = nullptr;   // idle batch members (2 N1 each)
-  int pending_probe = -1;
-  KrylovWork kw;
+  bool probe_pending[kNumPrec] = {};        // graph replays whose probes await harvesting
+  KrylovWork kw;                            // NS (and single solves on the context stream)
+  KrylovWork kwc0, kwa;                     // CH species 0 (step), AC (step)
+  // step(): CH (+ air potential), AC and NS are independent given the step-k
+  // data (Sec. 3), so they run on three streams driven by three host threads
+  cudaStream_t sx[3] = {nullptr, nullptr, nullptr};
+  bool concurrent = true;                   // chnss_set_step_concurrency
+  cudaEvent_t ev_asm = nullptr, ev_done[3] = {nullptr, nullptr, nullptr};
+  double *tmp_ns = nullptr;
   Profiler prof;
   bool assembled = false;
   bool ch_done[3] = {false, false, false};
@@ -162,6 +169,11 @@ struct chnss_ctx {
       }
     }
     if (cap) cudaStreamDestroy(cap);
+    for (cudaStream_t q : sx)
+      if (q) cudaStreamDestroy(q);
+    if (ev_asm) cudaEventDestroy(ev_asm);
+    for (cudaEvent_t e : ev_done)
+      if (e) cudaEventDestroy(e);
   }
 };
 
@@ -266,17 +278,17 @@ void prec_body(chnss_ctx *c, int g, cudaStream_t s) {
   else prec_body_t(c, *c->p64, g, s);
 }
 
-void run_prec(chnss_ctx *c, int g, const double *r, double *z) {
-  set_ptr_slots(reinterpret_cast<void **>(c->slots + 2 * g), r, z, c->s);
+void run_prec(chnss_ctx *c, int g, const double *r, double *z, cudaStream_t s) {
+  set_ptr_slots(reinterpret_cast<void **>(c->slots + 2 * g), r, z, s);
   PrecGraph &pg = c->pg[g];
   if (!pg.plain) {
-    prec_body(c, g, c->s);
+    prec_body(c, g, s);
     return;
   }
   const bool prof = c->prof.on && pg.prof;
-  CHNSS_CK(cudaGraphLaunch(prof ? pg.prof : pg.plain, c->s));
+  CHNSS_CK(cudaGraphLaunch(prof ? pg.prof : pg.plain, s));
   g_launch_count.fetch_add(pg.nodes, std::memory_order_relaxed);
-  if (prof) c->pending_probe = g;
+  if (prof) c->probe_pending[g] = true;
 }
 
 // batch members: inputs / outputs of the three species; idle members read
@@ -288,11 +300,12 @@ struct CHBatchPrec : BatchPrecond {
   void after_sync() override;
 };
 
-void harvest_probes(chnss_ctx *c) {
-  if (c->pending_probe >= 0) {
-    const PrecGraph &pg = c->pg[c->pending_probe];
+// after the stream that replayed graph g has been synchronised
+void harvest_probes(chnss_ctx *c, int g) {
+  if (c->probe_pending[g]) {
+    const PrecGraph &pg = c->pg[g];
     c->prof.harvest(pg.probes, pg.nprobes);
-    c->pending_probe = -1;
+    c->probe_pending[g] = false;
   }
 }
 
@@ -311,9 +324,9 @@ void CHBatchPrec::apply(int K, const double *const *r, double *const *z, cudaStr
   const bool prof = c->prof.on && pg.prof;
   CHNSS_CK(cudaGraphLaunch(prof ? pg.prof : pg.plain, s));
   g_launch_count.fetch_add(pg.nodes, std::memory_order_relaxed);
-  if (prof) c->pending_probe = 5;
+  if (prof) c->probe_pending[5] = true;
 }
-void CHBatchPrec::after_sync() { harvest_probes(c); }
+void CHBatchPrec::after_sync() { harvest_probes(c, 5); }
 
 struct CHOp : LinearOperator {
   chnss_ctx *c;
@@ -327,8 +340,8 @@ struct CHOp : LinearOperator {
     spmv_sell_ch(c->lv(0).p1, c->Ls, c->Ks, var ? c->Kks[sp] : nullptr, c->Ms, var ? tau : tau * g, tau * g,
             -tau * g / b, x, y, s);
   }
-  void precond(const double *r, double *z, cudaStream_t) override { run_prec(c, sp, r, z); }
-  void after_sync() override { harvest_probes(c); }
+  void precond(const double *r, double *z, cudaStream_t s) override { run_prec(c, sp, r, z, s); }
+  void after_sync() override { harvest_probes(c, sp); }
 };
 
 struct ACOp : LinearOperator {
@@ -339,8 +352,8 @@ struct ACOp : LinearOperator {
     SpmvArgs none;
     spmv_sell<double>(c->lv(0).p1, c->ACs, 1, x, y, SPMV_PLAIN, none, s);
   }
-  void precond(const double *r, double *z, cudaStream_t) override { run_prec(c, 3, r, z); }
-  void after_sync() override { harvest_probes(c); }
+  void precond(const double *r, double *z, cudaStream_t s) override { run_prec(c, 3, r, z, s); }
+  void after_sync() override { harvest_probes(c, 3); }
 };
 
 struct NSOp : LinearOperator {
@@ -351,14 +364,14 @@ struct NSOp : LinearOperator {
     const long nv = 2L * c->N2;
     SpmvArgs none;
     const Pattern &p2 = c->lv(0).p2;
-    c->prof.start(Profiler::NS_OUTER_SPMV, s);
+    const int tk = c->prof.start(Profiler::NS_OUTER_SPMV, s);
     spmv_sell_bsr2<double>(p2, c->As, x, y, SPMV_PLAIN, none, s);
-    c->prof.stop(Profiler::NS_OUTER_SPMV, s, (double)p2.nnz * 36.0 + 4.0 * (p2.nrows + 1) + 2.0 * nv * 8.0);
+    c->prof.stop(Profiler::NS_OUTER_SPMV, tk, s, (double)p2.nnz * 36.0 + 4.0 * (p2.nrows + 1) + 2.0 * nv * 8.0);
     spmv_sell_bt_add(c->mesh->m.pbt, c->Bts, x + nv, y, s);
     spmv_sell_b(c->mesh->m.pb, c->Bs, x, y + nv, s);
   }
-  void precond(const double *r, double *z, cudaStream_t) override { run_prec(c, 4, r, z); }
-  void after_sync() override { harvest_probes(c); }
+  void precond(const double *r, double *z, cudaStream_t s) override { run_prec(c, 4, r, z, s); }
+  void after_sync() override { harvest_probes(c, 4); }
 };
 
 // Capture every preconditioner into two graphs: plain, and with probe
@@ -600,9 +613,15 @@ void create_context(chnss_ctx *c) {
     c->massc = ar.upload(mc);
   }
   c->kw.init(ar, p.restart, 2L * c->N2 + c->N1, c->pinned + 8);
+  c->kwb[0].init(ar, p.restart, 2L * c->N1, c->pinned + 16);
+  c->kwb[1].init(ar, p.restart, 2L * c->N1, c->pinned + 20);
+  c->kwc0.init(ar, p.restart, 2L * c->N1, c->pinned + 24);
+  c->kwa.init(ar, p.restart, c->N1, c->pinned + 28);
+  c->tmp_ns = ar.alloc<double>(c->N1);
+  for (cudaStream_t &q : c->sx) CHNSS_CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+  CHNSS_CK(cudaEventCreateWithFlags(&c->ev_asm, cudaEventDisableTiming));
+  for (cudaEvent_t &e : c->ev_done) CHNSS_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   if (p.mobility_kind == 0) {
-    c->kwb[0].init(ar, p.restart, 2L * c->N1, c->pinned + 16);
-    c->kwb[1].init(ar, p.restart, 2L * c->N1, c->pinned + 20);
     c->dummy_in = ar.alloc<double>(2L * c->N1);
     c->dummy_out = ar.alloc<double>(2L * c->N1);
     vec_fill(2L * c->N1, 0.0, c->dummy_in, s);
@@ -624,7 +643,7 @@ void assemble(chnss_ctx *c, const chnss_state *st) {
   const Mesh &m = c->mesh->m;
   const auto &p = c->p;
   cudaStream_t s = c->s;
-  c->prof.start(Profiler::ASSEMBLY, s);
+  const int tka = c->prof.start(Profiler::ASSEMBLY, s);
   const int nl = c->nlev;
   // coefficients on every level by injection
   std::vector<const double *> v(nl);
@@ -714,7 +733,7 @@ void assemble(chnss_ctx *c, const chnss_state *st) {
     for (int sp = 0; sp < 3; ++sp) sell_gather<double>(F.p1.sell, 1, c->Kk[sp], c->Kks[sp], s);
   if (c->p32) setup_step_precset(c, *c->p32);
   else setup_step_precset(c, *c->p64);
-  c->prof.stop(Profiler::ASSEMBLY, s, 0.0);
+  c->prof.stop(Profiler::ASSEMBLY, tka, s, 0.0);
   c->assembled = true;
   for (bool &d : c->ch_done) d = false;
 }
@@ -728,42 +747,43 @@ int system_size(chnss_ctx *c, int sys) {
   }
 }
 
-chnss_status solve(chnss_ctx *c, int sys, const double *rhs_or_null, double *x, chnss_solve_info *info) {
+// One system on stream s with Krylov work kw and an N1 scratch vector tmp.
+chnss_status solve_on(chnss_ctx *c, int sys, const double *rhs_or_null, double *x, chnss_solve_info *info,
+                      cudaStream_t s, KrylovWork &kwk, double *tmp) {
   if (!c->assembled) throw Error{CHNSS_ERR_STATE, "chnss_solve before chnss_assemble"};
   const auto &p = c->p;
-  cudaStream_t s = c->s;
   const int N1 = c->N1;
   chnss_status st = CHNSS_OK;
   if (sys <= CHNSS_SYS_CH_S) {
     CHOp op(c, sys);
-    st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[sys], x, p.rtol, p.atol, p.maxit, c->kw, info, s, &c->prof);
+    st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[sys], x, p.rtol, p.atol, p.maxit, kwk, info, s, &c->prof);
     if (x != c->xsol[sys]) vec_copy(2L * N1, x, c->xsol[sys], s);
     c->ch_done[sys] = true;
   } else if (sys == CHNSS_SYS_AC) {
     ACOp op(c);
-    st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[3], x, p.rtol, p.atol, p.maxit, c->kw, info, s, &c->prof);
+    st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[3], x, p.rtol, p.atol, p.maxit, kwk, info, s, &c->prof);
   } else if (sys == CHNSS_SYS_MU_A) {
     const double *b = rhs_or_null;
     if (!b) {
       if (!(c->ch_done[0] && c->ch_done[1] && c->ch_done[2]))
         throw Error{CHNSS_ERR_STATE, "MU_A needs the three CH solutions of this step"};
       const Level &F = c->lv(0);
-      k_phi_a<<<nb(N1), TPB, 0, s>>>(N1, c->xsol[0], c->xsol[1], c->xsol[2], c->tmp);
+      k_phi_a<<<nb(N1), TPB, 0, s>>>(N1, c->xsol[0], c->xsol[1], c->xsol[2], tmp);
       CHNSS_LAUNCH_CK();
       SpmvArgs none;
-      spmv_csr<double>(F.p1, c->K1[0], 1, c->tmp, c->rhs[4], SPMV_PLAIN, none, s);
+      spmv_csr<double>(F.p1, c->K1[0], 1, tmp, c->rhs[4], SPMV_PLAIN, none, s);
       vec_axpby(N1, 1.0, c->fa, p.beta[3], c->rhs[4], s);    // f_a + beta_a K phi_a^{k+1}
       b = c->rhs[4];
     }
-    st = pcg(c->lv(0).p1, c->M1[0], c->dinvM, b, x, 1e-12, 1000, c->kw, info, s);
+    st = pcg(c->lv(0).p1, c->M1[0], c->dinvM, b, x, 1e-12, 1000, kwk, info, s);
   } else if (sys == CHNSS_SYS_NS) {
     NSOp op(c);
-    st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[5], x, p.rtol, p.atol, p.maxit, c->kw, info, s, &c->prof);
+    st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[5], x, p.rtol, p.atol, p.maxit, kwk, info, s, &c->prof);
     // zero-mean pressure: p -= (1^T M p) / (1^T M 1)
     const long nv = 2L * c->N2;
     SpmvArgs none;
-    spmv_csr<double>(c->lv(0).p1, c->M1[0], 1, x + nv, c->tmp, SPMV_PLAIN, none, s);
-    vsum<double>(N1, c->tmp, c->sum, c->partial, s);
+    spmv_csr<double>(c->lv(0).p1, c->M1[0], 1, x + nv, tmp, SPMV_PLAIN, none, s);
+    vsum<double>(N1, tmp, c->sum, c->partial, s);   // c->sum, c->partial: NS only during a step
     const Mesh &m = c->mesh->m;
     k_shift<<<nb(N1), TPB, 0, s>>>(N1, x + nv, c->sum, m.lx * m.ly);
     CHNSS_LAUNCH_CK();
@@ -773,38 +793,83 @@ chnss_status solve(chnss_ctx *c, int sys, const double *rhs_or_null, double *x, 
   return st;
 }
 
+chnss_status solve(chnss_ctx *c, int sys, const double *rhs_or_null, double *x, chnss_solve_info *info) {
+  return solve_on(c, sys, rhs_or_null, x, info, c->s, c->kw, c->tmp);
+}
+
+// The three CH systems (together when the mobility is constant), then the air
+// potential, on stream s; outputs to out->phi, out->mu.
+chnss_status step_ch(chnss_ctx *c, chnss_state *out, chnss_solve_info *inf, cudaStream_t s, chnss_status *st_mu) {
+  const int N1 = c->N1;
+  chnss_status worst = CHNSS_OK;
+  auto keep = [&](chnss_status st) { if (worst == CHNSS_OK) worst = st; };
+  if (c->ch_batch) {
+    // one batched preconditioner per Krylov tick
+    CHOp o0(c, 0), o1(c, 1), o2(c, 2);
+    LinearOperator *ops[3] = {&o0, &o1, &o2};
+    const double *bs[3] = {c->rhs[0], c->rhs[1], c->rhs[2]};
+    double *xs[3] = {c->xsol[0], c->xsol[1], c->xsol[2]};
+    KrylovWork *wss[3] = {&c->kwc0, &c->kwb[0], &c->kwb[1]};
+    CHBatchPrec bp(c);
+    keep(fgmres_batch(3, ops, bs, xs, c->p.rtol, c->p.atol, c->p.maxit, wss, inf, bp, s, &c->prof));
+    for (int sp = 0; sp < 3; ++sp) c->ch_done[sp] = true;
+  } else {
+    for (int sp = 0; sp < 3; ++sp) keep(solve_on(c, sp, nullptr, c->xsol[sp], &inf[sp], s, c->kwc0, c->tmp));
+  }
+  for (int sp = 0; sp < 3; ++sp) {
+    vec_copy(N1, c->xsol[sp], out->phi[sp], s);
+    vec_copy(N1, c->xsol[sp] + N1, out->mu[sp], s);
+  }
+  *st_mu = solve_on(c, CHNSS_SYS_MU_A, nullptr, out->mu[3], &inf[4], s, c->kwb[0], c->tmp);
+  return worst;
+}
+
 chnss_status step(chnss_ctx *c, const chnss_state *in, chnss_state *out, chnss_solve_info *info) {
   chnss_solve_info loc[6];
   chnss_solve_info *inf = info ? info : loc;
   assemble(c, in);
   cudaStream_t s = c->s;
   const int N1 = c->N1;
-  chnss_status worst = CHNSS_OK;
-  auto keep = [&](chnss_status st) { if (worst == CHNSS_OK) worst = st; };
-  if (c->ch_batch) {
-    // the three CH systems together: one batched preconditioner per tick
-    CHOp o0(c, 0), o1(c, 1), o2(c, 2);
-    LinearOperator *ops[3] = {&o0, &o1, &o2};
-    const double *bs[3] = {c->rhs[0], c->rhs[1], c->rhs[2]};
-    double *xs[3] = {c->xsol[0], c->xsol[1], c->xsol[2]};
-    KrylovWork *wss[3] = {&c->kw, &c->kwb[0], &c->kwb[1]};
-    CHBatchPrec bp(c);
-    keep(fgmres_batch(3, ops, bs, xs, c->p.rtol, c->p.atol, c->p.maxit, wss, inf, bp, s, &c->prof));
-    for (int sp = 0; sp < 3; ++sp) c->ch_done[sp] = true;
-  } else {
-    for (int sp = 0; sp < 3; ++sp) keep(solve(c, sp, nullptr, c->xsol[sp], &inf[sp]));
-  }
-  for (int sp = 0; sp < 3; ++sp) {
-    vec_copy(N1, c->xsol[sp], out->phi[sp], s);
-    vec_copy(N1, c->xsol[sp] + N1, out->mu[sp], s);
-  }
-  keep(solve(c, CHNSS_SYS_AC, nullptr, out->Phi_v, &inf[3]));
-  keep(solve(c, CHNSS_SYS_MU_A, nullptr, out->mu[3], &inf[4]));
-  keep(solve(c, CHNSS_SYS_NS, nullptr, c->xsol[5], &inf[5]));
   const long nv = 2L * c->N2;
-  vec_copy(nv, c->xsol[5], out->v, s);
-  vec_copy(N1, c->xsol[5] + nv, out->p, s);
-  return worst;
+  CHNSS_CK(cudaEventRecord(c->ev_asm, s));
+  chnss_status st[4] = {CHNSS_OK, CHNSS_OK, CHNSS_OK, CHNSS_OK};   // CH, AC, NS, air potential
+  std::exception_ptr err[3];
+  int dev = 0;
+  CHNSS_CK(cudaGetDevice(&dev));
+  auto run = [&](int w) {
+    try {
+      CHNSS_CK(cudaSetDevice(dev));
+      cudaStream_t q = c->sx[w];
+      CHNSS_CK(cudaStreamWaitEvent(q, c->ev_asm, 0));
+      if (w == 0) {
+        st[0] = step_ch(c, out, inf, q, &st[3]);
+      } else if (w == 1) {
+        st[1] = solve_on(c, CHNSS_SYS_AC, nullptr, out->Phi_v, &inf[3], q, c->kwa, nullptr);
+      } else {
+        st[2] = solve_on(c, CHNSS_SYS_NS, nullptr, c->xsol[5], &inf[5], q, c->kw, c->tmp_ns);
+        vec_copy(nv, c->xsol[5], out->v, q);
+        vec_copy(N1, c->xsol[5] + nv, out->p, q);
+      }
+      CHNSS_CK(cudaEventRecord(c->ev_done[w], q));
+    } catch (...) {
+      err[w] = std::current_exception();
+    }
+  };
+  if (c->concurrent) {
+    std::thread t_ac(run, 1), t_ns(run, 2);
+    run(0);
+    t_ac.join();
+    t_ns.join();
+  } else {
+    for (int w = 0; w < 3; ++w) run(w);
+  }
+  for (std::exception_ptr &e : err)
+    if (e) std::rethrow_exception(e);
+  for (cudaEvent_t e : c->ev_done) CHNSS_CK(cudaStreamWaitEvent(s, e, 0));
+  // the first failure in the order of the sequential step: CH, AC, air potential, NS
+  for (chnss_status x : {st[0], st[1], st[3], st[2]})
+    if (x != CHNSS_OK) return x;
+  return CHNSS_OK;
 }
 
 void check_state(const chnss_state *st) {
@@ -1234,8 +1299,8 @@ struct CHOpT : LinearOperator {   // [[L^T, a21 K], [a12 K12, a22 M]]
     spmv_sell_ch(c->lv(0).p1, c->LsT, c->Ks, nullptr, c->Ms, tau * g, tau * g, -tau * g / b, x, y, s);
     if (var) throw Error{CHNSS_ERR_ARG, "the adjoint step supports constant mobility only"};
   }
-  void precond(const double *r, double *z, cudaStream_t) override { run_prec(c, sp, r, z); }
-  void after_sync() override { harvest_probes(c); }
+  void precond(const double *r, double *z, cudaStream_t s) override { run_prec(c, sp, r, z, s); }
+  void after_sync() override { harvest_probes(c, sp); }
 };
 
 struct ACOpT : LinearOperator {
@@ -1246,8 +1311,8 @@ struct ACOpT : LinearOperator {
     SpmvArgs none;
     spmv_sell<double>(c->lv(0).p1, c->ACsT, 1, x, y, SPMV_PLAIN, none, s);
   }
-  void precond(const double *r, double *z, cudaStream_t) override { run_prec(c, 3, r, z); }
-  void after_sync() override { harvest_probes(c); }
+  void precond(const double *r, double *z, cudaStream_t s) override { run_prec(c, 3, r, z, s); }
+  void after_sync() override { harvest_probes(c, 3); }
 };
 
 struct NSOpT : LinearOperator {   // [[A^T, B^T], [B, 0]]
@@ -1261,8 +1326,8 @@ struct NSOpT : LinearOperator {   // [[A^T, B^T], [B, 0]]
     spmv_sell_bt_add(c->mesh->m.pbt, c->Bts, x + nv, y, s);
     spmv_sell_b(c->mesh->m.pb, c->Bs, x, y + nv, s);
   }
-  void precond(const double *r, double *z, cudaStream_t) override { run_prec(c, 4, r, z); }
-  void after_sync() override { harvest_probes(c); }
+  void precond(const double *r, double *z, cudaStream_t s) override { run_prec(c, 4, r, z, s); }
+  void after_sync() override { harvest_probes(c, 4); }
 };
 
 void adjoint_alloc(chnss_ctx *c) {
@@ -1573,6 +1638,12 @@ extern "C" chnss_status chnss_set_spmv_block(chnss_ctx_t ctx, int block_p1, int 
   capture_graphs(ctx);
   return CHNSS_OK;
   ABI_CATCH(ctx)
+}
+
+extern "C" chnss_status chnss_set_step_concurrency(chnss_ctx_t ctx, int on) {
+  if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
+  ctx->concurrent = on != 0;
+  return CHNSS_OK;
 }
 
 extern "C" chnss_status chnss_step_batched(int n_inst, chnss_ctx_t *ctxs, const chnss_state *in, chnss_state *out,

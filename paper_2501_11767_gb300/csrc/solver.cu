@@ -15,43 +15,46 @@ const char *Profiler::name(int k) {
   return k >= 0 && k < NKINDS ? names[k] : "?";
 }
 
-void Profiler::start(int k, cudaStream_t s) {
+int Profiler::start(int k, cudaStream_t s) {
   if (sink) {
-    if (sink_used < sink->size()) {
-      Probe &p = (*sink)[sink_used];
-      p.kind = k;
-      // during capture only an external record becomes an event node
-      CHNSS_CK(cudaEventRecordWithFlags(p.e0, s, cudaEventRecordExternal));
-    }
-    return;
+    if (sink_used >= sink->size()) return -1;
+    Probe &p = (*sink)[sink_used];
+    p.kind = k;
+    p.bytes = 0.0;
+    // during capture only an external record becomes an event node
+    CHNSS_CK(cudaEventRecordWithFlags(p.e0, s, cudaEventRecordExternal));
+    return (int)sink_used++;
   }
-  if (!on) return;
+  if (!on) return -1;
+  std::lock_guard<std::mutex> lock(mu);
   Rec &r = rec[k];
   if (r.used + 2 > r.ev.size()) {
-    if (r.ev.size() >= 16384) return;   // pool full: later launches are counted, not timed
+    if (r.ev.size() >= 16384) return -1;   // pool full: later launches are counted, not timed
     for (int i = 0; i < 256; ++i) {
       cudaEvent_t e;
       CHNSS_CK(cudaEventCreate(&e));
       r.ev.push_back(e);
     }
   }
-  CHNSS_CK(cudaEventRecord(r.ev[r.used], s));
+  const int tok = (int)r.used;
+  r.used += 2;
+  CHNSS_CK(cudaEventRecord(r.ev[tok], s));
+  return tok;
 }
 
-void Profiler::stop(int k, cudaStream_t s, double bytes, double flops, int count) {
+void Profiler::stop(int k, int token, cudaStream_t s, double bytes, double flops, int count) {
   if (sink) {
-    if (sink_used < sink->size()) {
-      Probe &p = (*sink)[sink_used++];
-      p.bytes = bytes;
-      CHNSS_CK(cudaEventRecordWithFlags(p.e1, s, cudaEventRecordExternal));
-    }
+    if (token < 0) return;
+    Probe &p = (*sink)[token];
+    p.bytes = bytes;
+    CHNSS_CK(cudaEventRecordWithFlags(p.e1, s, cudaEventRecordExternal));
     return;
   }
   if (!on) return;
+  std::lock_guard<std::mutex> lock(mu);
   Rec &r = rec[k];
-  if (r.used + 2 > r.ev.size()) return;
-  CHNSS_CK(cudaEventRecord(r.ev[r.used + 1], s));
-  r.used += 2;
+  if (token < 0) return;   // not timed (pool full, or profiling switched on mid-interval)
+  CHNSS_CK(cudaEventRecord(r.ev[token + 1], s));
   r.launches += count;
   r.bytes += bytes;
   r.flops += flops;
@@ -59,6 +62,7 @@ void Profiler::stop(int k, cudaStream_t s, double bytes, double flops, int count
 
 void Profiler::harvest(const std::vector<Probe> &probes, size_t count) {
   if (!on) return;
+  std::lock_guard<std::mutex> lock(mu);
   for (size_t i = 0; i < count && i < probes.size(); ++i) {
     const Probe &p = probes[i];
     float t = 0.f;
@@ -185,10 +189,10 @@ template <typename T>
 void MGHier<T>::op(int l, const T *u, T *out, SpmvMode mode, const SpmvArgs &a, cudaStream_t s) {
   const int k = kind == 0 ? Profiler::P1_SPMV_L0 : Profiler::VEL_SPMV_L0;
   const bool timed = prof && l == 0;
-  if (timed) prof->start(k, s);
+  const int tk = timed ? prof->start(k, s) : -1;
   spmv_level(l, u, out, mode, a, s);
   if (timed)
-    prof->stop(k, s, spmv_bytes(pat[l]->nrows, pat[l]->nnz, kind == 0 ? 1 : 4, n[l], bf16 ? 2 : sizeof(T), sizeof(T),
+    prof->stop(k, tk, s, spmv_bytes(pat[l]->nrows, pat[l]->nnz, kind == 0 ? 1 : 4, n[l], bf16 ? 2 : sizeof(T), sizeof(T),
                                 mode, a.w != nullptr));
 }
 
@@ -243,9 +247,9 @@ void MGHier<T>::vcycle(int l, cudaStream_t s) {
   SpmvArgs none;
   spmv_sell<T>(T_.R, transfer_vals<T>(T_, true), nc_, r[l], b[l + 1], SPMV_PLAIN, none, s);
   const int kc = kind == 0 ? Profiler::P1_MG_COARSE : Profiler::VEL_MG_COARSE;
-  if (prof && l == 0) prof->start(kc, s);
+  const int tkc = prof && l == 0 ? prof->start(kc, s) : -1;
   vcycle(l + 1, s);
-  if (prof && l == 0) prof->stop(kc, s, 0.0);   // time only: every level below the finest
+  if (prof && l == 0) prof->stop(kc, tkc, s, 0.0);   // time only: every level below the finest
   spmv_sell<T>(T_.P, transfer_vals<T>(T_, false), nc_, x[l + 1], x[l], SPMV_ADD, none, s);
   // post-smoothing from x_0 = x[l]
   a.coef = coef[l] + 1;
@@ -305,7 +309,7 @@ void MGBatch<T>::op(int l, const MultiPtr<T> &u, const MultiPtr<T> &out, SpmvMod
                     cudaStream_t s) {
   Profiler *prof = h->prof;
   const bool timed = prof && l == 0;
-  if (timed) prof->start(Profiler::P1_SPMV_L0, s);
+  const int tk = timed ? prof->start(Profiler::P1_SPMV_L0, s) : -1;
   spmv_sell_multi<T>(*h->pat[l], h->val[l], nr, u, out, mode, a, s);
   if (timed) {
     // one matrix stream for nr vectors
@@ -315,7 +319,7 @@ void MGBatch<T>::op(int l, const MultiPtr<T> &u, const MultiPtr<T> &out, SpmvMod
     if (mode == SPMV_CHEB) extra = a.w.p[0] ? 3.0 : 2.0;
     const double bytes = (double)nnz * (sizeof(T) + 4.0) + 4.0 * (nrows + 1) +
                          (double)nr * (2.0 + extra) * h->n[l] * sizeof(T) + (mode == SPMV_CHEB ? h->n[l] * sizeof(T) : 0.0);
-    prof->stop(Profiler::P1_SPMV_L0, s, bytes);
+    prof->stop(Profiler::P1_SPMV_L0, tk, s, bytes);
   }
 }
 
@@ -349,9 +353,9 @@ void MGBatch<T>::vcycle(int l, cudaStream_t s) {
   const T *Pv = std::is_same<T, double>::value ? reinterpret_cast<const T *>(T_.Ps) : reinterpret_cast<const T *>(T_.Ps32);
   MultiArgs<T> none;
   spmv_sell_multi<T>(T_.R, Rv, nr, r[l], b[l + 1], SPMV_PLAIN, none, s);
-  if (h->prof && l == 0) h->prof->start(Profiler::P1_MG_COARSE, s);
+  const int tkc = h->prof && l == 0 ? h->prof->start(Profiler::P1_MG_COARSE, s) : -1;
   vcycle(l + 1, s);
-  if (h->prof && l == 0) h->prof->stop(Profiler::P1_MG_COARSE, s, 0.0);
+  if (h->prof && l == 0) h->prof->stop(Profiler::P1_MG_COARSE, tkc, s, 0.0);
   spmv_sell_multi<T>(T_.P, Pv, nr, x[l + 1], x[l], SPMV_ADD, none, s);
   a.coef = h->coef[l] + 1;
   a.w = MultiPtr<T>();
@@ -439,14 +443,14 @@ chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, 
         A.apply(zj, ws.w, s);
         const int kv = j + 1;
         const bool fast = cgs2_fast(kv);
-        if (prof) prof->start(Profiler::ORTHO, s);
+        const int tko = prof ? prof->start(Profiler::ORTHO, s) : -1;
         if (fast) {
           // CGS2 passes 1-2: h1 = V^T w; w -= V h1, h2 = V^T w and ||w||^2 in
           // one sweep (V read twice, w read twice and written once; 3k+1 FMAs
           // per element).  Pass 3 forms the next basis vector after the sync.
           cgs2_dots(n, ws.V, ld, kv, ws.w, ws.h1, ws.partial, s);
           cgs2_update_dots(n, ws.V, ld, kv, ws.h1, ws.w, ws.h2, ws.partial, s);
-          if (prof) prof->stop(Profiler::ORTHO, s, 8.0 * n * (2.0 * kv + 3.0), 2.0 * n * (3.0 * kv + 1.0));
+          if (prof) prof->stop(Profiler::ORTHO, tko, s, 8.0 * n * (2.0 * kv + 3.0), 2.0 * n * (3.0 * kv + 1.0));
           arnoldi_finish_pyth(j, ldh, ws.H, ws.h1, ws.h2, ws.cs, ws.sn, ws.g, sc + 4, s);
         } else {
           mdot(n, ws.V, ld, kv, ws.w, ws.h1, ws.partial, s);
@@ -454,7 +458,7 @@ chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, 
           ortho_update_norm(n, ws.V, ld, kv, ws.h2, ws.w, sc + 3, ws.partial, s);
           // CGS2: three passes over V_0..V_j (w read 3x, written 2x) and
           // 4k+1 FP64 FMAs per vector element (dot, update + dot, update + norm)
-          if (prof) prof->stop(Profiler::ORTHO, s, 8.0 * n * (3.0 * kv + 5.0), 2.0 * n * (4.0 * kv + 1.0));
+          if (prof) prof->stop(Profiler::ORTHO, tko, s, 8.0 * n * (3.0 * kv + 5.0), 2.0 * n * (4.0 * kv + 1.0));
           arnoldi_finish(j, ldh, ws.H, ws.h1, ws.h2, sc + 3, ws.cs, ws.sn, ws.g, sc + 4, s);
         }
         CHNSS_CK(cudaMemcpyAsync(ws.hstat, sc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -470,9 +474,9 @@ chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, 
         breakdown = hn == 0.0;
         if (!breakdown && fast) {
           // pass 3: V_{j+1} = (w - V h2) / hn (V read once, w read once, V_{j+1} written; k FMAs)
-          if (prof) prof->start(Profiler::ORTHO, s);
+          const int tk3 = prof ? prof->start(Profiler::ORTHO, s) : -1;
           cgs2_update_scale(n, ws.V, ld, kv, ws.h2, ws.w, sc + 5, ws.V + (long)(j + 1) * ld, s);
-          if (prof) prof->stop(Profiler::ORTHO, s, 8.0 * n * (kv + 2.0), 2.0 * n * kv, 0);
+          if (prof) prof->stop(Profiler::ORTHO, tk3, s, 8.0 * n * (kv + 2.0), 2.0 * n * kv, 0);
         } else if (!breakdown) {
           vec_scale_by_inv(n, ws.w, sc + 5, ws.V + (long)(j + 1) * ld, s);
         }
@@ -577,17 +581,17 @@ chnss_status fgmres_batch(int K, LinearOperator *const *A, const double *const *
       A[q]->apply(zout[q], w.w, s);
       const int kv = r.j + 1;
       r.fast = cgs2_fast(kv);
-      if (prof) prof->start(Profiler::ORTHO, s);
+      const int tko = prof ? prof->start(Profiler::ORTHO, s) : -1;
       if (r.fast) {
         cgs2_dots(n, w.V, ld, kv, w.w, w.h1, w.partial, s);
         cgs2_update_dots(n, w.V, ld, kv, w.h1, w.w, w.h2, w.partial, s);
-        if (prof) prof->stop(Profiler::ORTHO, s, 8.0 * n * (2.0 * kv + 3.0), 2.0 * n * (3.0 * kv + 1.0));
+        if (prof) prof->stop(Profiler::ORTHO, tko, s, 8.0 * n * (2.0 * kv + 3.0), 2.0 * n * (3.0 * kv + 1.0));
         arnoldi_finish_pyth(r.j, r.ldh, w.H, w.h1, w.h2, w.cs, w.sn, w.g, sc + 4, s);
       } else {
         mdot(n, w.V, ld, kv, w.w, w.h1, w.partial, s);
         ortho_update_mdot(n, w.V, ld, kv, w.h1, w.w, w.h2, w.partial, s);
         ortho_update_norm(n, w.V, ld, kv, w.h2, w.w, sc + 3, w.partial, s);
-        if (prof) prof->stop(Profiler::ORTHO, s, 8.0 * n * (3.0 * kv + 5.0), 2.0 * n * (4.0 * kv + 1.0));
+        if (prof) prof->stop(Profiler::ORTHO, tko, s, 8.0 * n * (3.0 * kv + 5.0), 2.0 * n * (4.0 * kv + 1.0));
         arnoldi_finish(r.j, r.ldh, w.H, w.h1, w.h2, sc + 3, w.cs, w.sn, w.g, sc + 4, s);
       }
       CHNSS_CK(cudaMemcpyAsync(w.hstat, sc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -611,9 +615,9 @@ chnss_status fgmres_batch(int K, LinearOperator *const *A, const double *const *
       }
       r.breakdown = hn == 0.0;
       if (!r.breakdown && r.fast) {
-        if (prof) prof->start(Profiler::ORTHO, s);
+        const int tk3 = prof ? prof->start(Profiler::ORTHO, s) : -1;
         cgs2_update_scale(r.n, w.V, r.ld, r.k, w.h2, w.w, w.sc + 5, w.V + (long)(r.j + 1) * r.ld, s);
-        if (prof) prof->stop(Profiler::ORTHO, s, 8.0 * r.n * (r.k + 2.0), 2.0 * r.n * r.k, 0);
+        if (prof) prof->stop(Profiler::ORTHO, tk3, s, 8.0 * r.n * (r.k + 2.0), 2.0 * r.n * r.k, 0);
       } else if (!r.breakdown) {
         vec_scale_by_inv(r.n, w.w, w.sc + 5, w.V + (long)(r.j + 1) * r.ld, s);
       }

@@ -2,6 +2,8 @@
 // kernels in sparse.cu).
 #pragma once
 
+#include <mutex>
+
 #include "kernels.h"
 
 namespace chnss {
@@ -30,9 +32,11 @@ struct Profiler {
   };
   std::vector<Probe> *sink = nullptr;   // preallocated events (created before capture)
   size_t sink_used = 0;
-  void start(int k, cudaStream_t s);
+  std::mutex mu;                        // solves of one step run on several host threads
+  // start returns a token for the matching stop (-1: not recorded)
+  int start(int k, cudaStream_t s);
   // count: launches (or steps) the interval adds to the family
-  void stop(int k, cudaStream_t s, double bytes, double flops = 0.0, int count = 1);
+  void stop(int k, int token, cudaStream_t s, double bytes, double flops = 0.0, int count = 1);
   void harvest(const std::vector<Probe> &probes, size_t count);
   void reset();
   double elapsed_ms(int k);        // after a stream synchronisation

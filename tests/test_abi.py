@@ -60,6 +60,7 @@ def test_argument_errors_need_no_device(lib):
     assert lib.chnss_step_batched(2, hs, two, two, None, 0) == 1         # null context
     assert lib.chnss_autotune(None, None) == 1
     assert lib.chnss_set_spmv_block(None, 256, 256) == 1
+    assert lib.chnss_set_step_concurrency(None, 1) == 1
 
 
 def test_params_struct_matches_header():

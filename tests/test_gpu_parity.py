@@ -215,6 +215,26 @@ def test_batched_ch_solves_equal_single_solves(torch, precision, beta):
         assert bool((x[:N1] == out["phi"][sp]).all()) and bool((x[N1:] == out["mu"][sp]).all()), name
 
 
+@pytest.mark.parametrize("mobility_kind", [0, 1])
+def test_concurrent_step_equals_serial_step(torch, mobility_kind):
+    """The three solve groups on three streams give bitwise the serial step,
+    with and without the batched CH solves."""
+    n = 32
+    p = dict(inputs.default_params(), precision=1, mobility_kind=mobility_kind)
+    mesh = chnss.Mesh(n)
+    st = chnss.state_to_device(inputs.initial_state(n, seed=12))
+    conc = chnss.Context(mesh, p)
+    ser = chnss.Context(mesh, p)
+    ser.set_step_concurrency(False)
+    a, b = st, st
+    for _ in range(2):
+        a, ia, _ = conc.step(a)
+        b, ib, _ = ser.step(b)
+        for k in a:
+            assert bool((a[k] == b[k]).all()), k
+        assert all(ia[k]["iters"] == ib[k]["iters"] for k in ia)
+
+
 def test_restart_longer_than_the_templated_cgs2(torch):
     """FGMRES(40): Arnoldi steps with more than 31 basis vectors take the
     generic CGS2 kernels; the step must still match the oracle."""
