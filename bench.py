@@ -197,10 +197,12 @@ def run_gpu(args):
         ms = e0.elapsed_time(e1)
         prof = ctx.profile_read()
         ctx.profile_enable(False)
+        timed_run.launches_before = launches0
         return ctx, ms, infos, prof, prof["launches"] - launches0, clocks
 
     # headline: the library's default step (CH, AC and NS solved concurrently), no probes
     ctx, ms, infos, _, launches, clocks = timed_run(params, args.warmup, args.steps, False)
+    launches_before_timed = timed_run.launches_before
     ms_t = torch.tensor([ms], device=dev)
     if world > 1:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
@@ -336,6 +338,7 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
+        "gpu_launches_before_timed": launches_before_timed,
         "clocks": clocks,
     }
     print(json.dumps(out))

@@ -70,6 +70,31 @@ void dense_apply_multi(int n, int nr, const double *inv, const MultiPtr<T> &b, c
                        cudaStream_t s);
 template <typename T>
 void vec_copy_multi(long n, int nr, const MultiPtr<T> &in, const MultiPtr<T> &out, cudaStream_t s);
+// Coarse end of a scalar V-cycle run by one 512-thread block (see k_mg_tail):
+// level 0 of the descriptor is the first level handled by the block, the last
+// one is the coarsest (dense inverse).  Level sizes must allow every sweep's
+// rows to be spread over the block; all pointers are device pointers.
+constexpr int kMaxTailLevels = 8;
+struct TailSell {                 // SELL view of one operator (rows of at most 8 entries)
+  int nslices = 0;
+  const int *sp = nullptr, *rowid = nullptr, *col = nullptr;
+};
+template <typename T>
+struct TailLevel {
+  int n = 0;                      // rows (vector length)
+  TailSell A, R, P;               // operator; restriction to / prolongation from the next level
+  const T *val = nullptr, *Rval = nullptr, *Pval = nullptr, *dinv = nullptr;
+  const double *coef = nullptr;   // Chebyshev coefficients of the level
+  MultiPtr<T> x, t, r, b;
+};
+template <typename T>
+struct TailDesc {
+  int nlev = 0, degree = 2, nc = 0;
+  const double *cinv = nullptr;   // coarsest level, row-major nc x nc
+  TailLevel<T> lv[kMaxTailLevels];
+};
+template <typename T>
+void mg_tail(const TailDesc<T> *d_desc, int nr, cudaStream_t s);
 // BF16-stored values, FP32 vectors and accumulation (preconditioner variant)
 void spmv_sell(const Pattern &P, const __nv_bfloat16 *sval, int ncomp, const float *u, float *out, SpmvMode mode,
                const SpmvArgs &a, cudaStream_t s);

@@ -163,6 +163,68 @@ void MGHier<T>::init(Arena &ar, int kind_, bool singular_, const std::vector<con
   status = ar.alloc<int>(1);
   partial = partial_buf;
   sum = ar.alloc<double>(1);
+  if (kind == 0 && !bf16) {
+    for (int l = 1; l < nl; ++l)
+      if (n[l] <= kTailRows) {
+        tail_l0 = l;
+        break;
+      }
+    if (tail_l0 > 0 && nl - tail_l0 <= kMaxTailLevels) {
+      std::vector<MultiPtr<T>> X(nl), Tt(nl), Rr(nl), B(nl);
+      for (int l = 0; l < nl; ++l) {
+        X[l].p[0] = x[l];
+        Tt[l].p[0] = t[l];
+        Rr[l].p[0] = r[l];
+        B[l].p[0] = b[l];
+      }
+      tail = make_tail(ar, X, Tt, Rr, B);
+    } else {
+      tail_l0 = -1;
+    }
+  }
+}
+
+template <typename T>
+static inline const T *transfer_vals(const Transfer &t, bool restrict_);
+
+template <typename T>
+TailDesc<T> *MGHier<T>::make_tail(Arena &ar, const std::vector<MultiPtr<T>> &X, const std::vector<MultiPtr<T>> &Tt,
+                                  const std::vector<MultiPtr<T>> &Rr, const std::vector<MultiPtr<T>> &B) const {
+  TailDesc<T> d;
+  d.nlev = nl - tail_l0;
+  d.degree = degree;
+  d.nc = nc;
+  d.cinv = cinv;
+  auto view = [](const Pattern &P) {
+    if (P.sell.wmax > 8) throw Error{CHNSS_ERR_ARG, "coarse-level block: rows of at most 8 entries"};
+    TailSell v;
+    v.nslices = P.sell.nslices;
+    v.sp = P.sell.slice_ptr;
+    v.rowid = P.sell.rowid;
+    v.col = P.sell.col;
+    return v;
+  };
+  for (int l = tail_l0; l < nl; ++l) {
+    TailLevel<T> &q = d.lv[l - tail_l0];
+    q.n = (int)n[l];
+    q.A = view(*pat[l]);
+    q.val = val[l];
+    q.dinv = dinv[l];
+    q.coef = coef[l];
+    q.x = X[l];
+    q.t = Tt[l];
+    q.r = Rr[l];
+    q.b = B[l];
+    if (l < nl - 1) {
+      q.R = view(tr[l]->R);
+      q.P = view(tr[l]->P);
+      q.Rval = transfer_vals<T>(*tr[l], true);
+      q.Pval = transfer_vals<T>(*tr[l], false);
+    }
+  }
+  TailDesc<T> *dd = ar.alloc<TailDesc<T>>(1);
+  CHNSS_CK(cudaMemcpy(dd, &d, sizeof(d), cudaMemcpyHostToDevice));
+  return dd;
 }
 
 template <typename T>
@@ -219,6 +281,10 @@ static inline const T *transfer_vals(const Transfer &t, bool restrict_) {
 
 template <typename T>
 void MGHier<T>::vcycle(int l, cudaStream_t s) {
+  if (l == tail_l0) {
+    mg_tail<T>(tail, 1, s);
+    return;
+  }
   if (l == nl - 1) {
     dense_apply<T>(nc, cinv, b[l], x[l], s);
     return;
@@ -302,6 +368,7 @@ void MGBatch<T>::init(Arena &ar, MGHier<T> *hier, int nr_) {
       r[l].p[k] = ar.alloc<T>(h->n[l]);
       b[l].p[k] = ar.alloc<T>(h->n[l]);
     }
+  if (h->tail_l0 > 0) tail = h->make_tail(ar, x, t, r, b);
 }
 
 template <typename T>
@@ -326,6 +393,10 @@ void MGBatch<T>::op(int l, const MultiPtr<T> &u, const MultiPtr<T> &out, SpmvMod
 template <typename T>
 void MGBatch<T>::vcycle(int l, cudaStream_t s) {
   const int nl = h->nl;
+  if (l == h->tail_l0) {
+    mg_tail<T>(tail, nr, s);
+    return;
+  }
   if (l == nl - 1) {
     dense_apply_multi<T>(h->nc, nr, h->cinv, b[l], x[l], s);
     return;

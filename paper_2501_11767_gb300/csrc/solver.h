@@ -44,6 +44,10 @@ struct Profiler {
   ~Profiler() { release(); }
 };
 
+// Scalar levels of at most this many rows (32 x 32 P1 meshes and coarser) are
+// smoothed by one 512-thread block (mg_tail).
+constexpr long kTailRows = 1100;
+
 // One V-cycle of geometric multigrid (the inner solves that replace the
 // paper's PyAMG blocks, Sec. 4): degree-2 Chebyshev-Jacobi pre/post
 // smoothing on [hi/4, hi] (hi: Gershgorin bound of D^-1 A), restriction
@@ -72,6 +76,9 @@ struct MGHier {
   std::vector<__nv_bfloat16 *> val16;
   int degree = 2;          // Chebyshev smoothing degree (pre and post)
   double ratio = 4.0;      // smoothing interval [hi / ratio, hi]
+  // levels tail_l0.. (at most kTailRows rows each) run as one block launch
+  int tail_l0 = -1;
+  TailDesc<T> *tail = nullptr;   // device
 
   // levels: per level pattern + FP64 value pointer (values may change
   // between setups, the pointers may not); transfers tr[l] from level l+1.
@@ -84,6 +91,9 @@ struct MGHier {
   T *input() { return b[0]; }
   T *output() { return x[0]; }
   void apply(cudaStream_t s);   // x[0] = V-cycle(b[0])
+  // descriptor of levels tail_l0.. with the given vectors (device copy)
+  TailDesc<T> *make_tail(Arena &ar, const std::vector<MultiPtr<T>> &X, const std::vector<MultiPtr<T>> &Tt,
+                         const std::vector<MultiPtr<T>> &Rr, const std::vector<MultiPtr<T>> &B) const;
   // out = A_l u with the given epilogue (no profiling)
   void spmv_level(int l, const T *u, T *out, SpmvMode mode, const SpmvArgs &a, cudaStream_t s);
 
@@ -102,6 +112,7 @@ struct MGBatch {
   MGHier<T> *h = nullptr;
   int nr = 0;
   std::vector<MultiPtr<T>> x, t, r, b;     // per level
+  TailDesc<T> *tail = nullptr;             // device, levels h->tail_l0..
   void init(Arena &ar, MGHier<T> *hier, int nr);
   T *input(int k) { return b[0].p[k]; }
   T *output(int k) { return x[0].p[k]; }

@@ -814,13 +814,12 @@ __global__ void k_dense_apply(int n, const double *inv, const T *b, T *x) {
 // the matrix stream is read once, each right-hand side is summed in the same
 // order as by the single-vector kernels, so every output is bitwise the one
 // the single-vector kernel would give.
+// One slice (32 rows) of a multi-vector scalar SpMV with rows of at most 8
+// entries; shared by k_sell_w8m and the one-block coarse-level kernel.
 template <typename T, int NR>
-__global__ void __launch_bounds__(kSellMaxBlock) k_sell_w8m(int nslices, const int *__restrict__ sp,
-                                                   const int *__restrict__ rowid, const int *__restrict__ col,
-                                                   const T *__restrict__ val, MultiPtr<T> u, MultiPtr<T> out,
-                                                   int mode, MultiArgs<T> a) {
-  const int slice = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (slice >= nslices) return;
+__device__ __forceinline__ void sell_w8m_slice(int slice, int lane, const int *sp, const int *rowid, const int *col,
+                                               const T *val, const MultiPtr<T> &u, const MultiPtr<T> &out, int mode,
+                                               const MultiArgs<T> &a) {
   const int row = rowid[slice * 32 + lane];
   const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
   T bi[NR], ui[NR], wi[NR], oi[NR];
@@ -865,6 +864,100 @@ __global__ void __launch_bounds__(kSellMaxBlock) k_sell_w8m(int nslices, const i
     else if (mode == SPMV_ADD) r = oi[k] + acc[k];
     else r = cheb_row<T>(a.coef, ui[k], di, bi[k], acc[k], a.w.p[k] != nullptr, wi[k]);
     out.p[k][row] = r;
+  }
+}
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(kSellMaxBlock) k_sell_w8m(int nslices, const int *__restrict__ sp,
+                                                   const int *__restrict__ rowid, const int *__restrict__ col,
+                                                   const T *__restrict__ val, MultiPtr<T> u, MultiPtr<T> out,
+                                                   int mode, MultiArgs<T> a) {
+  const int slice = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (slice >= nslices) return;
+  sell_w8m_slice<T, NR>(slice, lane, sp, rowid, col, val, u, out, mode, a);
+}
+
+// ---------------------------------------------------------------------------
+// The coarse end of a scalar V-cycle in one block: levels l0..L of the
+// hierarchy (a few thousand rows at most) are swept by the block's warps,
+// with a block barrier between sweeps, instead of one launch per sweep.
+// Every row is computed by the same code as in the per-sweep kernels
+// (sell_w8m_slice, the same scale / copy / dense expressions), so the
+// result is bitwise the multi-launch V-cycle's.
+template <typename T, int NR>
+__device__ void tail_sweep(const TailSell &S, const T *val, const MultiPtr<T> &u, const MultiPtr<T> &out, int mode,
+                           const MultiArgs<T> &a) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int slice = threadIdx.x >> 5; slice < S.nslices; slice += nw)
+    sell_w8m_slice<T, NR>(slice, lane, S.sp, S.rowid, S.col, val, u, out, mode, a);
+  __syncthreads();
+}
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(512) k_mg_tail(const TailDesc<T> *__restrict__ dp) {
+  const TailDesc<T> &d = *dp;
+  const int L = d.nlev - 1;
+  const int degree = d.degree;
+  // down: pre-smoothing, residual, restriction
+  for (int l = 0; l < L; ++l) {
+    const TailLevel<T> &q = d.lv[l];
+    MultiPtr<T> cur = (degree - 1) % 2 == 0 ? q.x : q.t;
+    MultiPtr<T> oth = (degree - 1) % 2 == 0 ? q.t : q.x;
+    for (int i = threadIdx.x; i < q.n; i += blockDim.x)
+      for (int k = 0; k < NR; ++k) cur.p[k][i] = (T)(*q.coef) * q.dinv[i] * q.b.p[k][i];
+    __syncthreads();
+    MultiArgs<T> a;
+    a.b = q.b;
+    a.dinv = q.dinv;
+    for (int s = 1; s < degree; ++s) {
+      a.coef = q.coef + 4 + 3 * (s - 1);
+      a.w = s == 1 ? MultiPtr<T>() : oth;
+      tail_sweep<T, NR>(q.A, q.val, cur, oth, SPMV_CHEB, a);
+      const MultiPtr<T> tmp = cur;
+      cur = oth;
+      oth = tmp;
+    }
+    MultiArgs<T> ar;
+    ar.b = q.b;
+    tail_sweep<T, NR>(q.A, q.val, q.x, q.r, SPMV_RES, ar);
+    MultiArgs<T> none;
+    tail_sweep<T, NR>(q.R, q.Rval, q.r, d.lv[l + 1].b, SPMV_PLAIN, none);
+  }
+  // coarsest: dense inverse
+  {
+    const TailLevel<T> &q = d.lv[L];
+    for (int r = threadIdx.x; r < d.nc; r += blockDim.x)
+      for (int k = 0; k < NR; ++k) {
+        double s = 0.0;
+        for (int c = 0; c < d.nc; ++c) s += d.cinv[(long)r * d.nc + c] * (double)q.b.p[k][c];
+        q.x.p[k][r] = (T)s;
+      }
+    __syncthreads();
+  }
+  // up: prolongation, post-smoothing
+  for (int l = L - 1; l >= 0; --l) {
+    const TailLevel<T> &q = d.lv[l];
+    MultiArgs<T> none;
+    tail_sweep<T, NR>(q.P, q.Pval, d.lv[l + 1].x, q.x, SPMV_ADD, none);
+    MultiArgs<T> a;
+    a.b = q.b;
+    a.dinv = q.dinv;
+    a.coef = q.coef + 1;
+    tail_sweep<T, NR>(q.A, q.val, q.x, q.t, SPMV_CHEB, a);
+    MultiPtr<T> cur = q.t, oth = q.x;
+    for (int s = 1; s < degree; ++s) {
+      a.coef = q.coef + 4 + 3 * (s - 1);
+      a.w = oth;
+      tail_sweep<T, NR>(q.A, q.val, cur, oth, SPMV_CHEB, a);
+      const MultiPtr<T> tmp = cur;
+      cur = oth;
+      oth = tmp;
+    }
+    if (cur.p[0] != q.x.p[0]) {
+      for (int i = threadIdx.x; i < q.n; i += blockDim.x)
+        for (int k = 0; k < NR; ++k) q.x.p[k][i] = cur.p[k][i];
+      __syncthreads();
+    }
   }
 }
 
@@ -1489,6 +1582,19 @@ template void dense_apply_multi<double>(int, int, const double *, const MultiPtr
                                         cudaStream_t);
 template void dense_apply_multi<float>(int, int, const double *, const MultiPtr<float> &, const MultiPtr<float> &,
                                        cudaStream_t);
+
+template <typename T>
+void mg_tail(const TailDesc<T> *d_desc, int nr, cudaStream_t s) {
+  switch (nr) {
+    case 1: k_mg_tail<T, 1><<<1, 512, 0, s>>>(d_desc); break;
+    case 2: k_mg_tail<T, 2><<<1, 512, 0, s>>>(d_desc); break;
+    case 3: k_mg_tail<T, 3><<<1, 512, 0, s>>>(d_desc); break;
+    default: throw Error{CHNSS_ERR_ARG, "coarse-level block: 1 to 3 vectors"};
+  }
+  CHNSS_LAUNCH_CK();
+}
+template void mg_tail<double>(const TailDesc<double> *, int, cudaStream_t);
+template void mg_tail<float>(const TailDesc<float> *, int, cudaStream_t);
 
 template <typename T>
 void vec_copy_multi(long n, int nr, const MultiPtr<T> &in, const MultiPtr<T> &out, cudaStream_t s) {
