@@ -282,11 +282,11 @@ def run_gpu(args):
                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz (FMA probe measured 1.20)",
                     "flops_per_launch": d["flops"] / d["launches"], "bytes_per_launch": d["bytes"] / d["launches"],
                     "ms_per_launch": ms_l, "launches": d["launches"], "hbm_GBps": round(gbps, 1),
-                    "hbm_frac": round(gbps / peak, 4), "traffic": _traffic(name)}
+                    "hbm_frac": round(gbps / peak, 4), "traffic": _traffic(name, d["bytes"] / d["launches"])}
         return {"kernel": name, "bound": "hbm", "achieved": round(gbps, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(gbps / peak, 4), "peak_source": peak_kind,
                 "bytes_per_launch": d["bytes"] / d["launches"], "ms_per_launch": ms_l,
-                "launches": d["launches"], "traffic": _traffic(name)}
+                "launches": d["launches"], "traffic": _traffic(name, d["bytes"] / d["launches"])}
 
     dom = max(kinds, key=lambda k: kinds[k]["ms"])
     roofline = family_roofline(dom)
@@ -354,14 +354,17 @@ def _device_uuid(torch, idx):
         return None
 
 
-def _traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary of the kernel,
-    if one exists for the current source (profiles/traffic.json)."""
+def _traffic(kernel, bytes_per_launch):
+    """DRAM bytes per launch of a family from the committed ncu summary
+    (profiles/traffic.json): the measured DRAM / algorithmic byte ratio of
+    the family's kernels on a smaller capture, times this launch's
+    algorithmic bytes (traffic grows with the vectors swept)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        return d.get(kernel, {}).get("dram_bytes_per_launch")
+        ratio = d[kernel]["dram_per_algorithmic_byte"]
+        return round(ratio * bytes_per_launch)
     except Exception:
         return None
 

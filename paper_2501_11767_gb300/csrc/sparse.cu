@@ -1451,11 +1451,27 @@ int cgs_blocks(long n) {
   long b = (n + kCgsBlock - 1) / kCgsBlock;
   return (int)std::max(1L, std::min(b, (long)kCgsMaxBlocks));
 }
+// pass 1 reads KC + 1 streams per element with little FP64 work per load, so
+// it needs every resident block the registers allow (latency-bound at 2 per SM)
+template <int KC>
+int cgs_dots_blocks(long n) {
+  static const int cap = [] {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgs_dots<KC>, kCgsBlock, 0);
+    cudaGetLastError();
+    return std::max(kCgsMaxBlocks, std::min(sms * occ, 1216));
+  }();
+  const long b = (n + kCgsBlock - 1) / kCgsBlock;
+  return (int)std::max(1L, std::min(b, (long)cap));
+}
+
 template <int KC>
 void cgs_pass(int pass, long n, const double *V, long ld, const double *h, const double *w_in, double *w,
               const double *hn, double *out, double *partial, cudaStream_t s) {
   if (pass == 1) {
-    const int nb = cgs_blocks(n);
+    const int nb = cgs_dots_blocks<KC>(n);
     k_cgs_dots<KC><<<nb, kCgsBlock, 0, s>>>(n, V, ld, w_in, partial);
     CHNSS_LAUNCH_CK();
     k_sum_final<<<KC, TPB, 0, s>>>(nb, KC, partial, out);
