@@ -8,6 +8,13 @@ Potential: the polynomial fit eqn:appPotential,
 with partial derivatives taken before phi_a = 1 - phi_p - phi_N - phi_s is
 substituted (Sec. 5 keeps mu_a as a separate field).
 
+Solvent-air sub-model (Sec. 5.1, params["model"] = 1): only solvent and air,
+the Flory-Huggins density of Sec. 2.2 with the polymer and NFA terms removed,
+  f_liq = g(phi_s) / N_s + g(phi_a) / N_a + chi_sa phi_s phi_a,
+  f_gas = g(phi_s) - phi_s ln phi_sat(s) + g(phi_a) - phi_a ln phi_sat(a),
+where every phi ln phi is replaced by its Taylor polynomial g of degree 4 at
+phi = 1/2 (Sec. 5), RT / V_0 = 1, and the same interpolation p(Phi).
+
 Systems (Sec. 4):
   CH  eqn:CH_linear   [[M + tau C, tau K_gamma], [tau gamma K, -(tau gamma / beta) M]]
   AC                  (M + tau delta_v K + tau C) Phi = M Phi^k - tau gamma_v f_v^k
@@ -42,6 +49,43 @@ def f_gas(pp, pn, ps, pa):
     return 3.5 * pp**2 + 3.5 * pn**2 + 2.0 * ps**2 + 0.1 * pa**2
 
 
+# Taylor polynomial of x ln x at x = 1/2 to 4th order (Sec. 5):
+# derivatives of x ln x at 1/2: value -ln2/2, then 1 - ln 2, 1/x = 2,
+# -1/x^2 = -4, 2/x^3 = 16, divided by k!.
+TAYLOR_XLNX = (-0.5 * np.log(2.0), 1.0 - np.log(2.0), 1.0, -2.0 / 3.0, 2.0 / 3.0)
+
+
+def taylor_xlnx(x):
+    d = x - 0.5
+    c = TAYLOR_XLNX
+    return c[0] + d * (c[1] + d * (c[2] + d * (c[3] + d * c[4])))
+
+
+def dtaylor_xlnx(x):
+    d = x - 0.5
+    c = TAYLOR_XLNX
+    return c[1] + d * (2.0 * c[2] + d * (3.0 * c[3] + d * 4.0 * c[4]))
+
+
+def fh_liquid(ps, pa, prm):
+    return taylor_xlnx(ps) / prm["n_s"] + taylor_xlnx(pa) / prm["n_a"] + prm["chi_sa"] * ps * pa
+
+
+def fh_gas(ps, pa, prm):
+    return (taylor_xlnx(ps) - ps * np.log(prm["phi_sat_s"]) + taylor_xlnx(pa) - pa * np.log(prm["phi_sat_a"]))
+
+
+def fh_partials(ps, pa, Phi, prm):
+    """(df/dphi_s, df/dphi_a, df/dPhi_v) of the solvent-air density."""
+    q = interp_p(Phi)
+    dq = dinterp_p(Phi)
+    gs, ga = dtaylor_xlnx(ps), dtaylor_xlnx(pa)
+    d_s = (1 - q) * (gs / prm["n_s"] + prm["chi_sa"] * pa) + q * (gs - np.log(prm["phi_sat_s"]))
+    d_a = (1 - q) * (ga / prm["n_a"] + prm["chi_sa"] * ps) + q * (ga - np.log(prm["phi_sat_a"]))
+    d_v = dq * (fh_gas(ps, pa, prm) - fh_liquid(ps, pa, prm))
+    return d_s, d_a, d_v
+
+
 def potential(pp, pn, ps, pa, Phi):
     """f of eqn:appPotential."""
     q = interp_p(Phi)
@@ -61,17 +105,25 @@ def potential_partials(pp, pn, ps, pa, Phi):
     return d_p, d_n, d_s, d_a, d_v
 
 
-def potential_loads(mesh: Mesh, phi, Phi):
+def potential_loads(mesh: Mesh, phi, Phi, params=None):
     """Load vectors int df/dphi_i psi_m (i = p, N, s, a) and int df/dPhi psi_m
-    with phi_a = 1 - sum phi (Sec. 5).  Integrand degree 7 in P1 fields."""
+    with phi_a = 1 - sum phi (Sec. 5).  Integrand degree 7 in P1 fields.
+    Solvent-air model: the polymer and NFA loads are zero."""
+    solvent_air = params is not None and params.get("model", 0) == 1
     out = []
     for k in range(5):
+        if solvent_air and k < 2:
+            out.append(np.zeros(mesh.N1))
+            continue
+
         def integrand(lam, k=k):
             pp = fem.p1_field_at(mesh, phi[0], lam)
             pn = fem.p1_field_at(mesh, phi[1], lam)
             ps = fem.p1_field_at(mesh, phi[2], lam)
             pa = 1.0 - pp - pn - ps
             Ph = fem.p1_field_at(mesh, Phi, lam)
+            if solvent_air:
+                return fh_partials(ps, pa, Ph, params)[k - 2]
             return potential_partials(pp, pn, ps, pa, Ph)[k]
         out.append(fem.load_p1(mesh, integrand, 7))
     return out
@@ -88,7 +140,7 @@ def ch_rhs_loads(mesh: Mesh, state, params, loads=None, top=None):
     """f_i^k (i = p, N, s, a) of eqn:airdisc: int df/dphi_i w - beta_i int_Gt
     (d phi_i/dn) w, with d phi_s/dn = j_out and d phi_a/dn = -j_out (eqn:bc)."""
     if loads is None:
-        loads = potential_loads(mesh, state["phi"], state["Phi_v"])
+        loads = potential_loads(mesh, state["phi"], state["Phi_v"], params)
     if top is None:
         top = fem.top_load_p1(mesh)
     j = evaporation_flux(mesh, state["phi"][2], params)

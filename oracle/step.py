@@ -12,6 +12,12 @@ Order of work (Sec. 3 time scheme, Sec. 4 systems, Sec. 5 air recovery):
   5. Oseen system eqn:linearnav, FGMRES with diag(MG(A), M_p^{-1} A_p K_p^{-1})
      (pressure convection-diffusion); pressure shifted to zero mean.
 All matrices use coefficients at t_k, so 2, 3 and 5 are independent.
+
+Solvent-air sub-model (params["model"] = 1, Sec. 5.1): no polymer or NFA
+(their fields stay zero and their CH systems are not solved), the
+Taylor-expanded Flory-Huggins density of oracle.model, and the truncation
+eqn:truncateCH of the new solvent fraction to [0, 1] before phi_a^{k+1} is
+formed.
 """
 from __future__ import annotations
 
@@ -206,12 +212,20 @@ class Oracle:
         mesh = self.mesh
         lstates = self.level_states(state)
         convs = [fem.convection_p1(f.mesh, st["v"]) for f, st in zip(self.forms, lstates)]
-        loads = potential_loads(mesh, state["phi"], state["Phi_v"])
+        loads = potential_loads(mesh, state["phi"], state["Phi_v"], p)
         f, f_v, j_out = ch_rhs_loads(mesh, state, p, loads, self.forms[0].top)
         new = {"phi": np.empty_like(state["phi"]), "mu": np.empty_like(state["mu"])}
         info, systems = {}, {}
+        solvent_air = p.get("model", 0) == 1
         for i, name in enumerate(("ch_p", "ch_N", "ch_s")):
+            if solvent_air and i < 2:
+                new["phi"][i] = 0.0
+                new["mu"][i] = 0.0
+                info[name] = {"iters": 0, "rel_residual": 0.0, "converged": True}
+                continue
             new["phi"][i], new["mu"][i], info[name], systems[name] = self.solve_ch(state, i, f[i], lstates, convs)
+        if solvent_air:
+            new["phi"][2] = np.clip(new["phi"][2], 0.0, 1.0)      # eqn:truncateCH
         new["Phi_v"], info["ac"], systems["ac"] = self.solve_ac(state, f_v, j_out, convs)
         new["mu"][3], info["mu_a"] = self.solve_mu_a(f[3], new["phi"])
         new["v"], new["p"], info["ns"], systems["ns"] = self.solve_ns(state, lstates)

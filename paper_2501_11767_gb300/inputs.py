@@ -117,7 +117,45 @@ def default_params() -> dict:
         "atol": 0.0,
         "restart": 30,
         "maxit": 600,
+        # solvent-air sub-model (model = 1) only: Flory-Huggins constants
+        "model": 0,
+        "chi_sa": 0.0,
+        "n_s": 1.0,
+        "n_a": 1.0,
+        "phi_sat_s": 1e-6,
+        "phi_sat_a": 1.0,
     }
+
+
+FIELD_SOLVENT = 2
+
+
+def initial_state_solvent_air(n: int, seed: int = 0, amp: float = 0.01) -> dict:
+    """Solvent-air start of Sec. 5.1 (initial condition figure with a = 0,
+    b = 1): liquid solvent phi_s = 1 + U[-amp, amp) below y = 1/2 (Phi_v = 0),
+    air with Phi_v = 1 above; no polymer or NFA; flat interface."""
+    n1, n2 = p1_count(n), p2_count(n)
+    j = np.arange(n1) // (n + 1)
+    liquid = j <= n // 2
+    phi = np.zeros((3, n1))
+    phi[2] = np.where(liquid, 1.0 + uniform_noise(seed, FIELD_SOLVENT, n1, amp), 0.0)
+    return {
+        "phi": phi,
+        "mu": np.zeros((4, n1)),
+        "Phi_v": np.where(liquid, 0.0, 1.0),
+        "v": np.zeros(2 * n2),
+        "p": np.zeros(n1),
+    }
+
+
+def solvent_air_params() -> dict:
+    """Parameters of the paper's solvent-air runs (Sec. 5.1 figure captions):
+    beta_s = beta_a = 0.1, beta_v = 1, gamma = 1, delta_v = 1, alpha = 1e-8,
+    N_s = N_a = 1, chi_sa = 0, tau = 1e-4; evaporation rate and Krylov
+    tolerance as in the default set."""
+    p = default_params()
+    p.update(model=1, tau=1e-4, beta=[0.1, 0.1, 0.1, 0.1], chi_sa=0.0, n_s=1.0, n_a=1.0)
+    return p
 
 
 def workload(name: str) -> dict:
@@ -134,6 +172,10 @@ def workload(name: str) -> dict:
     if name == "film512_mixed":      # the same parameters on 512 x 512 (profiling captures)
         p.update(beta=film_betas(0.005), tau=5e-4, precision=1)
         return {"n": 512, "params": p, "steps": 10}
+    if name == "solvent_air1024_mixed":   # Sec. 5.1 sub-model on the bench mesh
+        p = solvent_air_params()
+        p.update(precision=1)
+        return {"n": 1024, "params": p, "steps": 10, "init": "solvent_air"}
     raise KeyError(name)
 
 
