@@ -60,7 +60,8 @@ def cpu_sample(n: int, workload: str, steps: int = 1) -> dict:
     w = inputs.workload(workload)
     params = dict(w["params"], precision=0)
     o = Oracle(n, params)
-    st = inputs.initial_state(n, seed=0)
+    init = inputs.initial_state_solvent_air if w.get("init") == "solvent_air" else inputs.initial_state
+    st = init(n, seed=0)
     times = []
     for _ in range(steps):
         t0 = time.perf_counter()
@@ -167,7 +168,8 @@ def run_gpu(args):
     mesh = chnss.Mesh(n)
     N1, N2 = mesh.N1, mesh.N2
     stream = torch.cuda.current_stream()
-    st0 = chnss.state_to_device(inputs.initial_state(n, seed=rank))
+    init = inputs.initial_state_solvent_air if w.get("init") == "solvent_air" else inputs.initial_state
+    st0 = chnss.state_to_device(init(n, seed=rank))
 
     def timed_run(prm, warmup, steps, profile, concurrent=True):
         ctx = chnss.Context(mesh, prm, stream)

@@ -77,6 +77,15 @@ typedef struct {
                             on every level (FP32 vectors, Jacobi diagonals and accumulation) */
   double rtol, atol;     /* stopping rule ||b - A x|| <= max(rtol ||b||, atol) (Sec. 5) */
   int restart, maxit;    /* FGMRES restart length (<= 64) and total iteration cap */
+  int model;             /* 0: polymer, NFA, solvent, air with eqn:appPotential;
+                            1: solvent-air sub-model (Sec. 5.1): no polymer / NFA (their
+                            fields stay zero and are not solved for), the Flory-Huggins
+                            density with every phi ln phi replaced by its degree-4 Taylor
+                            polynomial at 1/2 (Sec. 5), RT/V0 = 1, and the new solvent
+                            fraction truncated to [0, 1] (eqn:truncateCH) */
+  double chi_sa;         /* model 1: Flory-Huggins interaction solvent-air */
+  double n_s, n_a;       /* model 1: molar sizes N_s, N_a (> 0) */
+  double phi_sat_s, phi_sat_a;  /* model 1: saturated vapour fractions (> 0) */
 } chnss_params;
 
 /* Fields of one time level (DEVICE pointers, caller-owned, FP64). */

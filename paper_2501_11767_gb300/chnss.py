@@ -28,7 +28,9 @@ class Params(ctypes.Structure):
                 ("alpha", ctypes.c_double * 4), ("beta_v", ctypes.c_double), ("gamma_v", ctypes.c_double),
                 ("delta_v", ctypes.c_double), ("evap_rate", ctypes.c_double), ("phi_s_inf", ctypes.c_double),
                 ("ac_top_flux", ctypes.c_int), ("precision", ctypes.c_int), ("rtol", ctypes.c_double),
-                ("atol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int)]
+                ("atol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
+                ("model", ctypes.c_int), ("chi_sa", ctypes.c_double), ("n_s", ctypes.c_double),
+                ("n_a", ctypes.c_double), ("phi_sat_s", ctypes.c_double), ("phi_sat_a", ctypes.c_double)]
 
 
 class State(ctypes.Structure):
@@ -139,10 +141,14 @@ def _check(status, ctx=None):
         raise ChnssError(status, msg.decode() if msg else "")
 
 
+# fields of the solvent-air sub-model, defaulted when a parameter set omits them
+_OPTIONAL = {"model": 0, "chi_sa": 0.0, "n_s": 1.0, "n_a": 1.0, "phi_sat_s": 1e-6, "phi_sat_a": 1.0}
+
+
 def make_params(d: dict) -> Params:
     p = Params()
     for name, _ in Params._fields_:
-        val = d[name]
+        val = d[name] if name in d or name not in _OPTIONAL else _OPTIONAL[name]
         if isinstance(val, (list, tuple)):
             arr = getattr(p, name)
             for i, x in enumerate(val):

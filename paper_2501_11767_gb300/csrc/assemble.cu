@@ -248,10 +248,25 @@ __global__ void k_bdiv(Geo g, double *buf) {
       }
 }
 
-// Potential loads of eqn:appPotential: int df/dphi_i lambda_a (i = p, NFA,
-// s, a with phi_a = 1 - sum) and int df/dPhi_v lambda_a, layout [f][e][a].
+// x ln x replaced by its Taylor polynomial of degree 4 at 1/2 (Sec. 5); with
+// d = x - 1/2 the coefficients are the derivatives of x ln x at 1/2 over k!:
+// -ln2/2, 1 - ln2, 2/2!, -4/3!, 16/4!.  Returns the derivative.
+__device__ __forceinline__ double taylor_xlnx(double x, double *deriv) {
+  const double ln2 = 0.69314718055994530942;
+  const double c0 = -0.5 * ln2, c1 = 1.0 - ln2, c2 = 1.0, c3 = -2.0 / 3.0, c4 = 2.0 / 3.0;
+  const double d = x - 0.5;
+  *deriv = c1 + d * (2.0 * c2 + d * (3.0 * c3 + d * 4.0 * c4));
+  return c0 + d * (c1 + d * (c2 + d * (c3 + d * c4)));
+}
+
+// Potential loads: int df/dphi_i lambda_a (i = p, NFA, s, a with phi_a = 1 -
+// sum) and int df/dPhi_v lambda_a, layout [f][e][a].  Model 0: eqn:appPotential;
+// model 1 (solvent-air, Sec. 5.1): f_liq = g(s)/N_s + g(a)/N_a + chi s a,
+// f_gas = g(s) - s ln phi_sat(s) + g(a) - a ln phi_sat(a), g = Taylor(x ln x),
+// the polymer / NFA loads are zero.
 __global__ void k_loads(Geo g, const double *__restrict__ pp, const double *__restrict__ pn,
-                        const double *__restrict__ ps, const double *__restrict__ Ph, double *buf) {
+                        const double *__restrict__ ps, const double *__restrict__ Ph, PotentialCoef pc,
+                        double *buf) {
   const int E = 2 * g.n * g.n;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
@@ -275,14 +290,26 @@ __global__ void k_loads(Geo g, const double *__restrict__ pp, const double *__re
     const double V = l0 * fv[0] + l1 * fv[1] + l2 * fv[2];
     const double a = 1.0 - p - nn - s;
     const double ip = V * V * (3.0 - 2.0 * V), dip = 6.0 * V * (1.0 - V);
-    const double liq = 3.5 * p * p * nn * nn + 0.3 * s * s + 0.3 * a * a - 10.0 * s * a;
-    const double gas = 3.5 * p * p + 3.5 * nn * nn + 2.0 * s * s + 0.1 * a * a;
     double d[5];
-    d[0] = (1.0 - ip) * 7.0 * p * nn * nn + ip * 7.0 * p;
-    d[1] = (1.0 - ip) * 7.0 * p * p * nn + ip * 7.0 * nn;
-    d[2] = (1.0 - ip) * (0.6 * s - 10.0 * a) + ip * 4.0 * s;
-    d[3] = (1.0 - ip) * (0.6 * a - 10.0 * s) + ip * 0.2 * a;
-    d[4] = dip * (gas - liq);
+    if (pc.model == 0) {
+      const double liq = 3.5 * p * p * nn * nn + 0.3 * s * s + 0.3 * a * a - 10.0 * s * a;
+      const double gas = 3.5 * p * p + 3.5 * nn * nn + 2.0 * s * s + 0.1 * a * a;
+      d[0] = (1.0 - ip) * 7.0 * p * nn * nn + ip * 7.0 * p;
+      d[1] = (1.0 - ip) * 7.0 * p * p * nn + ip * 7.0 * nn;
+      d[2] = (1.0 - ip) * (0.6 * s - 10.0 * a) + ip * 4.0 * s;
+      d[3] = (1.0 - ip) * (0.6 * a - 10.0 * s) + ip * 0.2 * a;
+      d[4] = dip * (gas - liq);
+    } else {
+      double gs1, ga1;
+      const double gs = taylor_xlnx(s, &gs1), ga = taylor_xlnx(a, &ga1);
+      const double liq = gs * pc.inv_ns + ga * pc.inv_na + pc.chi_sa * s * a;
+      const double gas = gs - s * pc.ln_sat_s + ga - a * pc.ln_sat_a;
+      d[0] = 0.0;
+      d[1] = 0.0;
+      d[2] = (1.0 - ip) * (gs1 * pc.inv_ns + pc.chi_sa * a) + ip * (gs1 - pc.ln_sat_s);
+      d[3] = (1.0 - ip) * (ga1 * pc.inv_na + pc.chi_sa * s) + ip * (ga1 - pc.ln_sat_a);
+      d[4] = dip * (gas - liq);
+    }
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
       const double wd = w * d[f];
@@ -433,8 +460,8 @@ void launch_elem_bdiv(Geo g, double *buf, cudaStream_t s) {
   CHNSS_LAUNCH_CK();
 }
 void launch_elem_loads(Geo g, const double *pp, const double *pn, const double *ps, const double *Ph,
-                       double *buf, cudaStream_t s) {
-  k_loads<<<blocks_for(2L * g.n * g.n), TPB, 0, s>>>(g, pp, pn, ps, Ph, buf);
+                       PotentialCoef pc, double *buf, cudaStream_t s) {
+  k_loads<<<blocks_for(2L * g.n * g.n), TPB, 0, s>>>(g, pp, pn, ps, Ph, pc, buf);
   CHNSS_LAUNCH_CK();
 }
 void launch_elem_korteweg(Geo g, const double *pp, const double *pn, const double *ps, const double *Ph,

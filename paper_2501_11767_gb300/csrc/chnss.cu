@@ -468,7 +468,7 @@ void init_precset(chnss_ctx *c, PrecSet<T> &P) {
     h->prof = &c->prof;
   P.Kp.setup(c->s);
   for (int sp = 0; sp < 3; ++sp) P.X1[sp].setup(c->s);
-  if (c->p.mobility_kind == 0) {
+  if (c->p.mobility_kind == 0 && c->p.model == 0) {
     // species with equal (gamma, beta) have bitwise equal X1 = tau gamma K + sqrt(tau gamma / beta) M
     P.LB.init(ar, &P.L, 3);
     for (int sp = 0; sp < 3; ++sp) {
@@ -693,7 +693,14 @@ void assemble(chnss_ctx *c, const chnss_state *st) {
   launch_elem_p1_conv(g0, st->v, mu[0].data(), p.alpha, c->ebuf, s);
   launch_gather(F.g_p1, 1, c->ebuf, 1.0, c->Apb, 1.0, c->Ap, s);
   // potential loads (eqn:appPotential) and Korteweg term
-  launch_elem_loads(g0, st->phi[0], st->phi[1], st->phi[2], st->Phi_v, c->lbuf, s);
+  PotentialCoef pc;
+  pc.model = p.model;
+  pc.inv_ns = 1.0 / p.n_s;
+  pc.inv_na = 1.0 / p.n_a;
+  pc.chi_sa = p.chi_sa;
+  pc.ln_sat_s = std::log(p.phi_sat_s);
+  pc.ln_sat_a = std::log(p.phi_sat_a);
+  launch_elem_loads(g0, st->phi[0], st->phi[1], st->phi[2], st->Phi_v, pc, c->lbuf, s);
   for (int f = 0; f < 5; ++f)
     launch_gather(m.g_l1, 1, c->lbuf + (long)f * c->E * 3, 1.0, nullptr, 0.0, c->loads + (long)f * c->N1, s);
   KortewegCoef kc;
@@ -803,7 +810,20 @@ chnss_status step_ch(chnss_ctx *c, chnss_state *out, chnss_solve_info *inf, cuda
   const int N1 = c->N1;
   chnss_status worst = CHNSS_OK;
   auto keep = [&](chnss_status st) { if (worst == CHNSS_OK) worst = st; };
-  if (c->ch_batch) {
+  if (c->p.model == 1) {
+    // solvent-air sub-model (Sec. 5.1): no polymer / NFA; the new solvent
+    // fraction is truncated to [0, 1] (eqn:truncateCH)
+    for (int sp = 0; sp < 2; ++sp) {
+      vec_fill(2L * N1, 0.0, c->xsol[sp], s);
+      inf[sp].iters = 0;
+      inf[sp].converged = 1;
+      inf[sp].rel_residual = 0.0;
+      inf[sp].seconds = 0.0;
+    }
+    keep(solve_on(c, 2, nullptr, c->xsol[2], &inf[2], s, c->kwc0, c->tmp));
+    vec_clip01(N1, c->xsol[2], s);
+    c->ch_done[0] = c->ch_done[1] = true;
+  } else if (c->ch_batch) {
     // one batched preconditioner per Krylov tick
     CHOp o0(c, 0), o1(c, 1), o2(c, 2);
     LinearOperator *ops[3] = {&o0, &o1, &o2};
@@ -888,6 +908,9 @@ void check_params(const chnss_params *p) {
   if (p->restart < 1 || p->restart > 64) throw Error{CHNSS_ERR_ARG, "restart must be in [1, 64]"};
   if (p->maxit < 1) throw Error{CHNSS_ERR_ARG, "maxit must be >= 1"};
   if (p->precision < 0 || p->precision > 2) throw Error{CHNSS_ERR_ARG, "precision must be 0, 1 or 2"};
+  if (p->model != 0 && p->model != 1) throw Error{CHNSS_ERR_ARG, "model must be 0 or 1"};
+  if (p->model == 1 && !(p->n_s > 0 && p->n_a > 0 && p->phi_sat_s > 0 && p->phi_sat_a > 0))
+    throw Error{CHNSS_ERR_ARG, "model 1 needs n_s, n_a, phi_sat_s, phi_sat_a > 0"};
   if (p->mobility_kind != 0 && p->mobility_kind != 1) throw Error{CHNSS_ERR_ARG, "mobility_kind must be 0 or 1"};
   if (!(p->rtol >= 0) || !(p->atol >= 0)) throw Error{CHNSS_ERR_ARG, "tolerances must be >= 0"};
 }
@@ -1495,6 +1518,7 @@ extern "C" chnss_status chnss_adjoint_step(chnss_ctx_t ctx, const chnss_state *s
                                            const chnss_state *adj_k1, chnss_state *adj_k, double *grad_params,
                                            chnss_solve_info *info) {
   if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
+  if (ctx->p.model != 0) return fail(ctx, CHNSS_ERR_ARG, "the adjoint step covers model 0 only");
   ABI_TRY
   check_state(state_k);
   check_state(state_k1);

@@ -187,8 +187,15 @@ void launch_elem_p2_conv(Geo g, const double *v, const double *const *mu, const 
                          double *buf, cudaStream_t s);
 void launch_elem_ksym(Geo g, double eta, double *buf, cudaStream_t s);
 void launch_elem_bdiv(Geo g, double *buf, cudaStream_t s);
+// constants of the potential: model 0 eqn:appPotential; model 1 the
+// solvent-air Flory-Huggins density with Taylor-expanded phi ln phi
+struct PotentialCoef {
+  int model = 0;
+  double inv_ns = 1.0, inv_na = 1.0, chi_sa = 0.0;
+  double ln_sat_s = 0.0, ln_sat_a = 0.0;
+};
 void launch_elem_loads(Geo g, const double *phi_p, const double *phi_n, const double *phi_s,
-                       const double *Phi, double *buf, cudaStream_t s);
+                       const double *Phi, PotentialCoef pc, double *buf, cudaStream_t s);
 struct KortewegCoef {
   double beta[4];
   double beta_v;

@@ -144,6 +144,7 @@ void set_ptr_slots(void **slots, const void *a, const void *b, cudaStream_t s);
 void set_ptr_slots_n(void **slots, int n, const void *const *ptrs, cudaStream_t s);   // slots[0] = a, slots[1] = b
 void vec_axpby(long n, double a, const double *x, double b, double *y, cudaStream_t s);      // y = a x + b y
 void vec_copy(long n, const double *x, double *y, cudaStream_t s);
+void vec_clip01(long n, double *x, cudaStream_t s);   // x = min(max(x, 0), 1)
 void vec_fill(long n, double v, double *y, cudaStream_t s);
 void vec_scale_by_inv(long n, const double *src, const double *hn, double *dst, cudaStream_t s);  // dst = src / *hn
 template <typename T>

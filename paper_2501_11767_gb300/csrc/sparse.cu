@@ -1350,6 +1350,16 @@ void set_ptr_slots(void **slots, const void *a, const void *b, cudaStream_t s) {
   CHNSS_LAUNCH_CK();
 }
 
+__global__ void k_clip01(long n, double *x) {
+  const long i = (long)blockIdx.x * TPB + threadIdx.x;
+  if (i < n) x[i] = fmin(fmax(x[i], 0.0), 1.0);
+}
+void vec_clip01(long n, double *x, cudaStream_t s) {
+  if (n == 0) return;
+  k_clip01<<<nblocks(n, TPB), TPB, 0, s>>>(n, x);
+  CHNSS_LAUNCH_CK();
+}
+
 void vec_axpby(long n, double a, const double *x, double b, double *y, cudaStream_t s) {
   k_axpby<<<nblocks(n, TPB), TPB, 0, s>>>(n, a, x, b, y);
   CHNSS_LAUNCH_CK();

@@ -130,19 +130,23 @@ def default_params() -> dict:
 FIELD_SOLVENT = 2
 
 
-def initial_state_solvent_air(n: int, seed: int = 0, amp: float = 0.01) -> dict:
+def initial_state_solvent_air(n: int, seed: int = 0, amp: float = 0.01, width: float = 0.05) -> dict:
     """Solvent-air start of Sec. 5.1 (initial condition figure with a = 0,
-    b = 1): liquid solvent phi_s = 1 + U[-amp, amp) below y = 1/2 (Phi_v = 0),
-    air with Phi_v = 1 above; no polymer or NFA; flat interface."""
+    b = 1): liquid solvent (phi_s = 1 + U[-amp, amp), Phi_v = 0) below a
+    wavy interface y = 1/2 + 0.05 sin(2 pi x), air (phi_s = 0, Phi_v = 1)
+    above, joined by a tanh profile of the given width so that the initial
+    gradients do not grow with the resolution; no polymer or NFA."""
     n1, n2 = p1_count(n), p2_count(n)
+    i = np.arange(n1) % (n + 1)
     j = np.arange(n1) // (n + 1)
-    liquid = j <= n // 2
+    x, y = i / n, j / n
+    liquid = 0.5 * (1.0 - np.tanh((y - 0.5 - 0.05 * np.sin(2.0 * np.pi * x)) / width))
     phi = np.zeros((3, n1))
-    phi[2] = np.where(liquid, 1.0 + uniform_noise(seed, FIELD_SOLVENT, n1, amp), 0.0)
+    phi[2] = liquid * (1.0 + uniform_noise(seed, FIELD_SOLVENT, n1, amp))
     return {
         "phi": phi,
         "mu": np.zeros((4, n1)),
-        "Phi_v": np.where(liquid, 0.0, 1.0),
+        "Phi_v": 1.0 - liquid,
         "v": np.zeros(2 * n2),
         "p": np.zeros(n1),
     }
