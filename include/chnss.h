@@ -166,7 +166,8 @@ chnss_status chnss_set_step_concurrency(chnss_ctx_t ctx, int on);
 chnss_status chnss_step_host(chnss_ctx_t ctx, const chnss_state *host_in, chnss_state *host_out,
                              chnss_solve_info *info);
 
-/* Adjoint of one step (discrete adjoint of chnss_step; constant mobility).
+/* Adjoint of one step (discrete adjoint of chnss_step; constant mobility,
+ * model 0 only: CHNSS_ERR_ARG for the solvent-air model).
  * Every solve x = A(u)^-1 b(u) of the step contributes, with
  * y = A^-T xbar (FGMRES on the transposed operator to a relative residual of
  * 1e-12, preconditioned by the forward block preconditioner),
