@@ -220,6 +220,18 @@ def velocity_dirichlet(A, bnd_nodes_mask):
     return out
 
 
+def p1_dirichlet(A, nodes_mask):
+    """Homogeneous Dirichlet rows / columns on P1 nodes: identity rows, zero
+    coupling in both directions (the outflow condition of the pressure
+    convection-diffusion operators, Elman-Silvester-Wathen, cited in Sec. 4)."""
+    Dint = sp.diags((~nodes_mask).astype(float))
+    Db = sp.diags(nodes_mask.astype(float))
+    out = (Dint @ A @ Dint + Db).tocsr()
+    out.eliminate_zeros()
+    out.sort_indices()
+    return out
+
+
 def zero_velocity_columns(B, bnd_nodes_mask):
     mask = np.repeat(bnd_nodes_mask, 2)
     out = (B @ sp.diags((~mask).astype(float))).tocsr()

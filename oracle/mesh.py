@@ -20,9 +20,14 @@ import numpy as np
 
 
 class Mesh:
-    def __init__(self, n: int, lx: float = 1.0, ly: float = 1.0):
+    """top_free: the velocity is not prescribed on the top edge (do-nothing
+    condition there, no-slip on the other three sides); default: no-slip on
+    the whole boundary (eqn:bc)."""
+
+    def __init__(self, n: int, lx: float = 1.0, ly: float = 1.0, top_free: bool = False):
         if n < 1:
             raise ValueError("n must be >= 1")
+        self.top_free = bool(top_free)
         self.n, self.lx, self.ly = n, float(lx), float(ly)
         self.hx, self.hy = self.lx / n, self.ly / n
         self.N1 = (n + 1) ** 2
@@ -54,10 +59,13 @@ class Mesh:
 
     # ------------------------------------------------------------------
     def p2_boundary(self) -> np.ndarray:
-        """Boolean mask of P2 nodes on the boundary (velocity no-slip, eqn:bc)."""
+        """Boolean mask of P2 nodes with prescribed (zero) velocity: the whole
+        boundary (eqn:bc), or all but the open top edge when top_free (its two
+        corners stay on the side walls)."""
         m = 2 * self.n
         I, J = self.lat2[:, 0], self.lat2[:, 1]
-        return (I == 0) | (I == m) | (J == 0) | (J == m)
+        top = (J == m) & (not self.top_free)
+        return (I == 0) | (I == m) | (J == 0) | top
 
     def p1_top(self) -> np.ndarray:
         """Boolean mask of P1 nodes on Gamma_t (y = Ly)."""

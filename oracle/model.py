@@ -243,7 +243,10 @@ def korteweg_tensor(mesh: Mesh, state, params):
 
 def ns_system(forms: Forms, state, params):
     """Blocks and right-hand side of eqn:linearnav with rho = 1 (equal pure
-    densities), no-slip velocity on the whole boundary (eqn:bc)."""
+    densities), no-slip velocity on the whole boundary (eqn:bc) or, on a
+    top_free mesh, on the bottom and side walls with the do-nothing
+    condition (2 eta eps(v) - p I) n = 0 on the top (natural in the weak
+    form)."""
     mesh = forms.mesh
     vf = forms.velocity_forms()
     tau = params["tau"]
@@ -256,4 +259,6 @@ def ns_system(forms: Forms, state, params):
     rhs_v[np.repeat(vf["bnd"], 2)] = 0.0
     B = vf["B"]
     Ap = (forms.M / tau + params["eta"] * forms.K + fem.convection_p1(mesh, state["v"], shift)).tocsr()
+    if mesh.top_free:
+        Ap = fem.p1_dirichlet(Ap, mesh.p1_top())       # PCD outflow condition on the open top
     return A, B, rhs_v, Ap, shift

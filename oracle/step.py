@@ -57,7 +57,8 @@ class Oracle:
         self.exact = exact
         self.params = dict(params)
         self.sizes = level_sizes(n)
-        self.meshes = [Mesh(s, lx, ly) for s in self.sizes]
+        self.top_free = self.params.get("top_bc", 0) == 1
+        self.meshes = [Mesh(s, lx, ly, self.top_free) for s in self.sizes]
         self.forms = [Forms(m, self.params) for m in self.meshes]
         self.P1 = [prolongation_p1(self.meshes[l + 1]) for l in range(len(self.sizes) - 1)]
         self._Pv = None
@@ -170,7 +171,10 @@ class Oracle:
             mats.append(fem.velocity_dirichlet(Al.tocsr(), vf["bnd"]))
         mgA = MG(mats, self.Pv(), degree=VEL_SMOOTH_DEGREE, ratio=VEL_LO_RATIO)
         if self._Kp is None:
-            self._Kp = MG([f.K for f in self.forms], self.P1, singular=True)
+            if self.top_free:        # outflow: K_p with Dirichlet rows on the open top, non-singular
+                self._Kp = MG([fem.p1_dirichlet(f.K, f.mesh.p1_top()) for f in self.forms], self.P1)
+            else:
+                self._Kp = MG([f.K for f in self.forms], self.P1, singular=True)
         mgK = self._Kp
         Mp = self.forms[0].M
         mdinv = 1.0 / Mp.diagonal()
@@ -190,7 +194,9 @@ class Oracle:
         A, B, rhs_v, Ap, _ = ns_system(self.forms[0], state, p)
         nv = A.shape[0]
         rhs = np.concatenate([rhs_v, np.zeros(self.mesh.N1)])
-        if self.exact:
+        if self.exact and self.top_free:
+            x, info = _direct(sp.bmat([[A, B.T], [B, None]], format="csc"), rhs)
+        elif self.exact:
             m = self.forms[0].M @ np.ones(self.mesh.N1)
             K = sp.bmat([[A, B.T, None], [B, None, sp.csr_matrix(m[:, None])],
                          [None, sp.csr_matrix(m[None, :]), None]], format="csc")
@@ -200,9 +206,10 @@ class Oracle:
             prec = self.ns_preconditioner(A, Ap, lstates)
             x, info = fgmres(self.ns_operator(A, B), prec, rhs, p["rtol"], p["atol"], p["restart"], p["maxit"])
         v, pr = x[:nv], x[nv:]
-        Mp = self.forms[0].M
-        one = np.ones(self.mesh.N1)
-        pr = pr - (one @ (Mp @ pr)) / (one @ (Mp @ one))
+        if not self.top_free:       # enclosed flow: pressure in L^2_0
+            Mp = self.forms[0].M
+            one = np.ones(self.mesh.N1)
+            pr = pr - (one @ (Mp @ pr)) / (one @ (Mp @ one))
         return v, pr, info, (A, B, rhs)
 
     # ------------------------------------------------------------------
