@@ -165,7 +165,7 @@ def run_gpu(args):
 
     w = inputs.workload(args.workload)
     n, params = w["n"], w["params"]
-    mesh = chnss.Mesh(n)
+    mesh = chnss.Mesh(n, top_bc=params.get("top_bc", 0))
     N1, N2 = mesh.N1, mesh.N2
     stream = torch.cuda.current_stream()
     init = inputs.initial_state_solvent_air if w.get("init") == "solvent_air" else inputs.initial_state

@@ -110,6 +110,17 @@ typedef struct {
  * the transfer operators (host), and uploads them.  Returns CHNSS_ERR_ARG
  * for bad sizes, CHNSS_ERR_OOM / CHNSS_ERR_CUDA on device failures. */
 chnss_status chnss_mesh_create(int nx, int ny, double lx, double ly, chnss_mesh_t *out);
+/* The same with a choice of velocity condition on the top edge:
+ * top_bc = 0: no-slip on the whole boundary (eqn:bc), pressure with zero
+ * mean (as chnss_mesh_create); top_bc = 1: open top, i.e. no-slip on the
+ * bottom and side walls and the do-nothing condition (2 eta eps(v) - p I) n = 0
+ * on the top edge (its corners stay on the walls).  With an open top the
+ * pressure is not shifted, and the pressure convection-diffusion
+ * preconditioner puts homogeneous Dirichlet rows on the top pressure nodes
+ * of A_p and K_p (outflow condition; K_p is then non-singular).  The
+ * adjoint step returns CHNSS_ERR_ARG on such meshes.  CHNSS_ERR_ARG for
+ * other top_bc values. */
+chnss_status chnss_mesh_create_ex(int nx, int ny, double lx, double ly, int top_bc, chnss_mesh_t *out);
 chnss_status chnss_mesh_destroy(chnss_mesh_t mesh);
 /* Sizes: N1 P1 nodes, N2 P2 nodes, E triangles, number of multigrid levels. */
 chnss_status chnss_mesh_sizes(chnss_mesh_t mesh, int *N1, int *N2, int *E, int *levels);
@@ -167,7 +178,8 @@ chnss_status chnss_step_host(chnss_ctx_t ctx, const chnss_state *host_in, chnss_
                              chnss_solve_info *info);
 
 /* Adjoint of one step (discrete adjoint of chnss_step; constant mobility,
- * model 0 only: CHNSS_ERR_ARG for the solvent-air model).
+ * model 0, enclosed flow: CHNSS_ERR_ARG for the solvent-air model and for
+ * meshes with an open top).
  * Every solve x = A(u)^-1 b(u) of the step contributes, with
  * y = A^-T xbar (FGMRES on the transposed operator to a relative residual of
  * 1e-12, preconditioned by the forward block preconditioner),

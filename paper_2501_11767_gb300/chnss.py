@@ -80,6 +80,8 @@ _LIB = None
 EXPORTS = {
     "chnss_mesh_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "chnss_mesh_create_ex": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "chnss_mesh_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "chnss_mesh_sizes": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 4),
     "chnss_ctx_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Params), ctypes.c_void_p,
@@ -188,12 +190,12 @@ class Mesh:
     """Structured n x n triangulation of [0, lx] x [0, ly] with its multigrid
     hierarchy (chnss_mesh_create)."""
 
-    def __init__(self, n: int, lx: float = 1.0, ly: float = 1.0):
+    def __init__(self, n: int, lx: float = 1.0, ly: float = 1.0, top_bc: int = 0):
         lib = load()
         h = ctypes.c_void_p()
-        _check(lib.chnss_mesh_create(n, n, lx, ly, ctypes.byref(h)))
+        _check(lib.chnss_mesh_create_ex(n, n, lx, ly, top_bc, ctypes.byref(h)))
         self._h = h
-        self.n, self.lx, self.ly = n, lx, ly
+        self.n, self.lx, self.ly, self.top_bc = n, lx, ly, top_bc
         v = [ctypes.c_int() for _ in range(4)]
         _check(lib.chnss_mesh_sizes(h, *[ctypes.byref(x) for x in v]))
         self.N1, self.N2, self.E, self.levels = (x.value for x in v)

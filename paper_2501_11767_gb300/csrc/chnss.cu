@@ -77,6 +77,21 @@ __global__ void k_aconst_finish(int N2, const int *rowptr, const double *m2, con
     d[0] = 1.0; d[1] = 0.0; d[2] = 0.0; d[3] = 1.0;
   }
 }
+// Homogeneous Dirichlet rows / columns on the top P1 nodes (j = n) of a P1
+// CSR matrix: identity rows, zero coupling (outflow condition of the
+// pressure convection-diffusion operators on an open top).
+__global__ void k_p1_top_dirichlet(int n, const int *rowptr, const int *col, double *val) {
+  const int N1 = (n + 1) * (n + 1);
+  const int r = blockIdx.x * TPB + threadIdx.x;
+  if (r >= N1) return;
+  const bool rtop = r / (n + 1) == n;
+  for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+    const int c = col[k];
+    if (rtop) val[k] = c == r ? 1.0 : 0.0;
+    else if (c / (n + 1) == n) val[k] = 0.0;
+  }
+}
+
 __global__ void k_inv_diag(int n, const double *val, const int *diag, double *out) {
   const int i = blockIdx.x * TPB + threadIdx.x;
   if (i < n) out[i] = 1.0 / val[diag[i]];
@@ -148,6 +163,7 @@ struct chnss_ctx {
   bool concurrent = true;                   // chnss_set_step_concurrency
   cudaEvent_t ev_asm = nullptr, ev_done[3] = {nullptr, nullptr, nullptr};
   double *tmp_ns = nullptr;
+  std::vector<double *> Kpd;                // open top: K_p with Dirichlet top rows, per level
   Profiler prof;
   bool assembled = false;
   bool ch_done[3] = {false, false, false};
@@ -440,7 +456,10 @@ void init_precset(chnss_ctx *c, PrecSet<T> &P) {
   P.A.init(ar, 1, false, p2s, d2s, vals(c->A), tvs, c->partial);
   P.A.degree = 4;        // velocity smoothing: degree 4 on [hi / 16, hi]
   P.A.ratio = 16.0;
-  P.Kp.init(ar, 0, true, p1s, d1s, vals(c->K1), t1s, c->partial);
+  if (c->mesh->m.top_bc == 1)   // open top: Dirichlet outflow rows, non-singular
+    P.Kp.init(ar, 0, false, p1s, d1s, vals(c->Kpd), t1s, c->partial);
+  else
+    P.Kp.init(ar, 0, true, p1s, d1s, vals(c->K1), t1s, c->partial);
   for (int sp = 0; sp < 3; ++sp) {
     std::vector<const double *> x1, x2;
     for (int l = 0; l < nl; ++l) {
@@ -527,6 +546,13 @@ void create_context(chnss_ctx *c) {
     launch_gather(L.g_p1, 1, c->ebuf, 1.0, nullptr, 0.0, c->M1[l], s);
     launch_elem_p1_stiff(g, c->ebuf, s);
     launch_gather(L.g_p1, 1, c->ebuf, 1.0, nullptr, 0.0, c->K1[l], s);
+    if (m.top_bc == 1) {
+      if (l == 0) c->Kpd.assign(nl, nullptr);
+      c->Kpd[l] = ar.alloc<double>(nnz1);
+      vec_copy(nnz1, c->K1[l], c->Kpd[l], s);
+      k_p1_top_dirichlet<<<nb(L.N1), TPB, 0, s>>>(L.n, L.p1.rowptr, L.p1.col, c->Kpd[l]);
+      CHNSS_LAUNCH_CK();
+    }
     // M + tau delta_v K
     vec_copy(nnz1, c->M1[l], c->ACb[l], s);
     vec_axpby(nnz1, p.tau * p.delta_v, c->K1[l], 1.0, c->ACb[l], s);
@@ -692,6 +718,10 @@ void assemble(chnss_ctx *c, const chnss_state *st) {
   // A_p = M / tau + eta K + J_p(w)
   launch_elem_p1_conv(g0, st->v, mu[0].data(), p.alpha, c->ebuf, s);
   launch_gather(F.g_p1, 1, c->ebuf, 1.0, c->Apb, 1.0, c->Ap, s);
+  if (m.top_bc == 1) {
+    k_p1_top_dirichlet<<<nb(F.N1), TPB, 0, s>>>(F.n, F.p1.rowptr, F.p1.col, c->Ap);
+    CHNSS_LAUNCH_CK();
+  }
   // potential loads (eqn:appPotential) and Korteweg term
   PotentialCoef pc;
   pc.model = p.model;
@@ -786,14 +816,17 @@ chnss_status solve_on(chnss_ctx *c, int sys, const double *rhs_or_null, double *
   } else if (sys == CHNSS_SYS_NS) {
     NSOp op(c);
     st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[5], x, p.rtol, p.atol, p.maxit, kwk, info, s, &c->prof);
-    // zero-mean pressure: p -= (1^T M p) / (1^T M 1)
-    const long nv = 2L * c->N2;
-    SpmvArgs none;
-    spmv_csr<double>(c->lv(0).p1, c->M1[0], 1, x + nv, tmp, SPMV_PLAIN, none, s);
-    vsum<double>(N1, tmp, c->sum, c->partial, s);   // c->sum, c->partial: NS only during a step
+    // enclosed flow: zero-mean pressure, p -= (1^T M p) / (1^T M 1); an open
+    // top fixes the pressure level itself
     const Mesh &m = c->mesh->m;
-    k_shift<<<nb(N1), TPB, 0, s>>>(N1, x + nv, c->sum, m.lx * m.ly);
-    CHNSS_LAUNCH_CK();
+    if (m.top_bc == 0) {
+      const long nv = 2L * c->N2;
+      SpmvArgs none;
+      spmv_csr<double>(c->lv(0).p1, c->M1[0], 1, x + nv, tmp, SPMV_PLAIN, none, s);
+      vsum<double>(N1, tmp, c->sum, c->partial, s);   // c->sum, c->partial: NS only during a step
+      k_shift<<<nb(N1), TPB, 0, s>>>(N1, x + nv, c->sum, m.lx * m.ly);
+      CHNSS_LAUNCH_CK();
+    }
   } else {
     throw Error{CHNSS_ERR_ARG, "unknown system"};
   }
@@ -933,14 +966,19 @@ chnss_status fail(chnss_ctx *c, chnss_status st, const std::string &msg) {
 extern "C" {
 
 chnss_status chnss_mesh_create(int nx, int ny, double lx, double ly, chnss_mesh_t *out) {
+  return chnss_mesh_create_ex(nx, ny, lx, ly, 0, out);
+}
+
+chnss_status chnss_mesh_create_ex(int nx, int ny, double lx, double ly, int top_bc, chnss_mesh_t *out) {
   ABI_TRY
   if (!out) throw Error{CHNSS_ERR_ARG, "null output pointer"};
+  if (top_bc != 0 && top_bc != 1) throw Error{CHNSS_ERR_ARG, "top_bc must be 0 or 1"};
   *out = nullptr;
   if (nx != ny) throw Error{CHNSS_ERR_ARG, "nx must equal ny"};
   if (nx < 2 || nx % 2 != 0 || nx > 8192) throw Error{CHNSS_ERR_ARG, "n must be even and in [2, 8192]"};
   if (!(lx > 0) || !(ly > 0)) throw Error{CHNSS_ERR_ARG, "domain lengths must be > 0"};
   std::unique_ptr<chnss_mesh> m(new chnss_mesh());
-  build_mesh(m->m, nx, lx, ly);
+  build_mesh(m->m, nx, lx, ly, top_bc);
   *out = m.release();
   return CHNSS_OK;
   ABI_CATCH(nullptr)
@@ -1519,6 +1557,7 @@ extern "C" chnss_status chnss_adjoint_step(chnss_ctx_t ctx, const chnss_state *s
                                            chnss_solve_info *info) {
   if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
   if (ctx->p.model != 0) return fail(ctx, CHNSS_ERR_ARG, "the adjoint step covers model 0 only");
+  if (ctx->mesh->m.top_bc != 0) return fail(ctx, CHNSS_ERR_ARG, "the adjoint step covers the enclosed flow only");
   ABI_TRY
   check_state(state_k);
   check_state(state_k1);

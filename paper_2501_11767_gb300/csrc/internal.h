@@ -137,6 +137,7 @@ struct Level {
 struct Mesh {
   double lx = 1, ly = 1;
   int n = 0;
+  int top_bc = 0;              // 0: no-slip on the whole boundary; 1: open (do-nothing) top
   std::vector<Level> lv;
   Pattern pb, pbt;             // fine B (P1 rows x P2 node cols) and B^T
   Gather g_b, g_bt;            // <- element [E][3][6][2] (2 comps)
@@ -164,7 +165,7 @@ const RefTensors &reference_tensors();
 
 // ---------------------------------------------------------------------------
 // host builders (setup.cu)
-void build_mesh(Mesh &m, int n, double lx, double ly);
+void build_mesh(Mesh &m, int n, double lx, double ly, int top_bc);
 void destroy_mesh(Mesh &m);
 
 // ---------------------------------------------------------------------------

@@ -273,19 +273,23 @@ void build_p1_transfer(Arena &ar, int nc, Transfer &t) {
 }
 
 // Quadratic interpolation of coarse P2 functions at the fine P2 nodes, on
-// interior (non-Dirichlet) nodes of both levels.
-void build_vel_transfer(Arena &ar, int nc, Transfer &t) {
+// the nodes without prescribed velocity of both levels (open top: the top
+// edge except its corners is free).
+void build_vel_transfer(Arena &ar, int nc, int top_bc, Transfer &t) {
   const int mf = 4 * nc + 1, mc = 2 * nc + 1;
   Pattern &P = t.P;
   P.nrows = mf * mf;
   P.ncols = mc * mc;
   P.h_rowptr.assign(P.nrows + 1, 0);
   std::vector<double> pv;
-  auto cbnd = [&](int id) { int I = id % mc, J = id / mc; return I == 0 || J == 0 || I == mc - 1 || J == mc - 1; };
+  auto cbnd = [&](int id) {
+    int I = id % mc, J = id / mc;
+    return I == 0 || J == 0 || I == mc - 1 || (top_bc == 0 && J == mc - 1);
+  };
   for (int J = 0; J < mf; ++J)
     for (int I = 0; I < mf; ++I) {
       const int r = J * mf + I;
-      const bool fb = I == 0 || J == 0 || I == mf - 1 || J == mf - 1;
+      const bool fb = I == 0 || J == 0 || I == mf - 1 || (top_bc == 0 && J == mf - 1);
       if (!fb) {
         const int i = std::min(I / 4, nc - 1), j = std::min(J / 4, nc - 1);
         const double xi = I / 4.0 - i, eta = J / 4.0 - j;   // exact quarters
@@ -317,9 +321,10 @@ std::vector<int> diag_positions(const Pattern &P) {
 
 }  // namespace
 
-void build_mesh(Mesh &m, int n, double lx, double ly) {
+void build_mesh(Mesh &m, int n, double lx, double ly, int top_bc) {
   Arena &ar = m.arena;
   m.n = n;
+  m.top_bc = top_bc;
   m.lx = lx;
   m.ly = ly;
   std::vector<int> sizes{n};
@@ -339,7 +344,7 @@ void build_mesh(Mesh &m, int n, double lx, double ly) {
     std::vector<int> bnd(L.N2);
     for (int id = 0; id < L.N2; ++id) {
       int I = id % m2, J = id / m2;
-      bnd[id] = (I == 0 || J == 0 || I == m2 - 1 || J == m2 - 1) ? 1 : 0;
+      bnd[id] = (I == 0 || J == 0 || I == m2 - 1 || (top_bc == 0 && J == m2 - 1)) ? 1 : 0;
     }
     auto p1pair = [&](int e, int *r, int *c) { int v2[6]; element_nodes(nl, e, r, v2); std::memcpy(c, r, 3 * sizeof(int)); };
     auto p2pair = [&](int e, int *r, int *c) { int v1[3]; element_nodes(nl, e, v1, r); std::memcpy(c, r, 6 * sizeof(int)); };
@@ -385,7 +390,7 @@ void build_mesh(Mesh &m, int n, double lx, double ly) {
   }
   for (size_t l = 0; l + 1 < sizes.size(); ++l) {
     build_p1_transfer(ar, sizes[l + 1], m.lv[l].t1);
-    build_vel_transfer(ar, sizes[l + 1], m.lv[l].tv);
+    build_vel_transfer(ar, sizes[l + 1], top_bc, m.lv[l].tv);
   }
 }
 

@@ -117,6 +117,9 @@ def default_params() -> dict:
         "atol": 0.0,
         "restart": 30,
         "maxit": 600,
+        # velocity on the top edge: 0 no-slip (eqn:bc), 1 open (a mesh property on
+        # the GPU: chnss_mesh_create_ex; read by the oracle from here)
+        "top_bc": 0,
         # solvent-air sub-model (model = 1) only: Flory-Huggins constants
         "model": 0,
         "chi_sa": 0.0,
@@ -176,6 +179,9 @@ def workload(name: str) -> dict:
     if name == "film512_mixed":      # the same parameters on 512 x 512 (profiling captures)
         p.update(beta=film_betas(0.005), tau=5e-4, precision=1)
         return {"n": 512, "params": p, "steps": 10}
+    if name == "film1024_open_mixed":     # the bench set with an open (do-nothing) top
+        p.update(beta=film_betas(0.005), tau=5e-4, precision=1, top_bc=1)
+        return {"n": 1024, "params": p, "steps": 10}
     if name == "solvent_air1024_mixed":   # Sec. 5.1 sub-model on the bench mesh
         p = solvent_air_params()
         p.update(precision=1)

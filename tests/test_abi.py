@@ -48,6 +48,7 @@ def test_argument_errors_need_no_device(lib):
     assert lib.chnss_mesh_create(8, 16, 1.0, 1.0, ctypes.byref(h)) == 1     # nx != ny
     assert lib.chnss_mesh_create(8, 8, -1.0, 1.0, ctypes.byref(h)) == 1     # bad length
     assert lib.chnss_mesh_create(8, 8, 1.0, 1.0, None) == 1
+    assert lib.chnss_mesh_create_ex(8, 8, 1.0, 1.0, 2, ctypes.byref(h)) == 1   # unknown top condition
     assert lib.chnss_ctx_create(None, None, None, ctypes.byref(h)) == 1
     assert lib.chnss_step(None, None, None, None) == 1
     assert lib.chnss_system_size(None, 0) == -1
