@@ -179,9 +179,9 @@ def workload(name: str) -> dict:
     if name == "film512_mixed":      # the same parameters on 512 x 512 (profiling captures)
         p.update(beta=film_betas(0.005), tau=5e-4, precision=1)
         return {"n": 512, "params": p, "steps": 10}
-    if name == "film1024_open_mixed":     # the bench set with an open (do-nothing) top
+    if name == "film512_open_mixed":      # the bench set with an open (do-nothing) top, 512 x 512
         p.update(beta=film_betas(0.005), tau=5e-4, precision=1, top_bc=1)
-        return {"n": 1024, "params": p, "steps": 10}
+        return {"n": 512, "params": p, "steps": 10}
     if name == "solvent_air1024_mixed":   # Sec. 5.1 sub-model on the bench mesh
         p = solvent_air_params()
         p.update(precision=1)
