@@ -150,6 +150,11 @@ struct chnss_ctx {
   // captured preconditioner graphs (0..2 CH species, 3 AC, 4 NS)
   double **slots = nullptr;   // device [2 * kNumPrec] input / output pointers
   cudaStream_t cap = nullptr; // private stream used for capture only
+  // side branches of the preconditioner graphs (independent parts of one
+  // preconditioner run as parallel graph branches): streams and the
+  // fork / join events
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
   PrecGraph pg[kNumPrec];
   bool ch_batch = false;                    // step() solves the CH species together
   KrylovWork kwb[2];                        // Krylov work of the 2nd and 3rd CH species
@@ -185,6 +190,11 @@ struct chnss_ctx {
       }
     }
     if (cap) cudaStreamDestroy(cap);
+    for (cudaStream_t q : side)
+      if (q) cudaStreamDestroy(q);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    for (cudaEvent_t e : ev_join)
+      if (e) cudaEventDestroy(e);
     for (cudaStream_t q : sx)
       if (q) cudaStreamDestroy(q);
     if (ev_asm) cudaEventDestroy(ev_asm);
@@ -200,6 +210,17 @@ namespace {
 // and written through a device pointer slot (slot[0] = r, slot[1] = z), so
 // the whole launch sequence is captured once into a CUDA graph and replayed
 // for any pair of Krylov vectors.
+// Fork side stream k off s (its work becomes a parallel branch when s is
+// capturing) and join it back.
+void fork_side(chnss_ctx *c, cudaStream_t s, int k) {
+  CHNSS_CK(cudaEventRecord(c->ev_fork, s));
+  CHNSS_CK(cudaStreamWaitEvent(c->side[k], c->ev_fork, 0));
+}
+void join_side(chnss_ctx *c, cudaStream_t s, int k) {
+  CHNSS_CK(cudaEventRecord(c->ev_join[k], c->side[k]));
+  CHNSS_CK(cudaStreamWaitEvent(s, c->ev_join[k], 0));
+}
+
 template <typename T>
 void ch_precond(chnss_ctx *c, PrecSet<T> &P, int sp, double **slot, cudaStream_t s) {
   const int N1 = c->N1;
@@ -227,20 +248,25 @@ void ch_precond_batched(chnss_ctx *c, PrecSet<T> &P, cudaStream_t s) {
   const int N1 = c->N1;
   double **slot = c->slots + kBatchSlot;
   const double *const *in = const_cast<const double *const *>(slot);
+  const Pattern &p1 = c->lv(0).p1;
+  // the Schur parts of the species groups are independent of MG(L) and of
+  // each other: one side branch per group
+  for (int g = 0; g < P.ngroups; ++g) {
+    fork_side(c, s, g);
+    cudaStream_t q = c->side[g];
+    MGBatch<T> &X = P.XB[g];
+    for (int j = 0; j < P.gsize[g]; ++j) vec_convert_from_slot<double, T>(N1, in + 2 * P.gmem[g][j], N1, X.input(j), q);
+    X.apply(q);
+    MultiArgs<T> none;
+    spmv_sell_multi<T>(p1, P.Mv, P.gsize[g], X.x[0], X.b[0], SPMV_PLAIN, none, q);   // X2 = X1 (constant mobility)
+    X.apply(q);
+    for (int j = 0; j < P.gsize[g]; ++j)
+      vec_convert_to_slot<T, double>(N1, X.output(j), slot + 2 * P.gmem[g][j] + 1, N1, q);
+  }
   for (int k = 0; k < 3; ++k) vec_convert_from_slot<double, T>(N1, in + 2 * k, 0, P.LB.input(k), s);
   P.LB.apply(s);
   for (int k = 0; k < 3; ++k) vec_convert_to_slot<T, double>(N1, P.LB.output(k), slot + 2 * k + 1, 0, s);
-  const Pattern &p1 = c->lv(0).p1;
-  for (int g = 0; g < P.ngroups; ++g) {
-    MGBatch<T> &X = P.XB[g];
-    for (int j = 0; j < P.gsize[g]; ++j) vec_convert_from_slot<double, T>(N1, in + 2 * P.gmem[g][j], N1, X.input(j), s);
-    X.apply(s);
-    MultiArgs<T> none;
-    spmv_sell_multi<T>(p1, P.Mv, P.gsize[g], X.x[0], X.b[0], SPMV_PLAIN, none, s);   // X2 = X1 (constant mobility)
-    X.apply(s);
-    for (int j = 0; j < P.gsize[g]; ++j)
-      vec_convert_to_slot<T, double>(N1, X.output(j), slot + 2 * P.gmem[g][j] + 1, N1, s);
-  }
+  for (int g = 0; g < P.ngroups; ++g) join_side(c, s, g);
 }
 
 template <typename T>
@@ -256,17 +282,17 @@ void ns_precond(chnss_ctx *c, PrecSet<T> &P, double **slot, cudaStream_t s) {
   const int N1 = c->N1;
   const double *const *in = const_cast<const double *const *>(slot);
   double *const *out = slot + 1;
-  vec_convert_from_slot<double, T>(nv, in, 0, P.A.input(), s);
-  P.A.apply(s);
-  vec_convert_to_slot<T, double>(nv, P.A.output(), out, 0, s);
+  // the pressure block is independent of the velocity block: a side branch
+  fork_side(c, s, 0);
+  cudaStream_t q = c->side[0];
   // pressure convection-diffusion: M_p^-1 A_p K_p^-1
-  vec_convert_from_slot<double, T>(N1, in, nv, P.Kp.input(), s);
-  P.Kp.apply(s);
+  vec_convert_from_slot<double, T>(N1, in, nv, P.Kp.input(), q);
+  P.Kp.apply(q);
   SpmvArgs none;
   const Pattern &p1 = c->lv(0).p1;
-  spmv_sell<T>(p1, P.Apv, 1, P.Kp.output(), P.mb, SPMV_PLAIN, none, s);
+  spmv_sell<T>(p1, P.Apv, 1, P.Kp.output(), P.mb, SPMV_PLAIN, none, q);
   // M_p^-1 by Chebyshev iteration of degree 5 on D^-1 M, spectrum [1/2, 2]
-  vec_scale_dinv<T>(N1, c->massc, P.mdinv, P.mb, P.mx, s);
+  vec_scale_dinv<T>(N1, c->massc, P.mdinv, P.mb, P.mx, q);
   SpmvArgs a;
   a.b = P.mb;
   a.dinv = P.mdinv;
@@ -274,10 +300,15 @@ void ns_precond(chnss_ctx *c, PrecSet<T> &P, double **slot, cudaStream_t s) {
   for (int k = 1; k <= 4; ++k) {
     a.coef = c->massc + 1 + 3 * (k - 1);
     a.w = k == 1 ? nullptr : other;
-    spmv_sell<T>(p1, P.Mv, 1, cur, other, SPMV_CHEB, a, s);
+    spmv_sell<T>(p1, P.Mv, 1, cur, other, SPMV_CHEB, a, q);
     std::swap(cur, other);
   }
-  vec_convert_to_slot<T, double>(N1, cur, out, nv, s);
+  vec_convert_to_slot<T, double>(N1, cur, out, nv, q);
+  // velocity block on s
+  vec_convert_from_slot<double, T>(nv, in, 0, P.A.input(), s);
+  P.A.apply(s);
+  vec_convert_to_slot<T, double>(nv, P.A.output(), out, 0, s);
+  join_side(c, s, 0);
 }
 
 // preconditioner g: 0..2 CH species, 3 AC, 4 NS
@@ -645,6 +676,9 @@ void create_context(chnss_ctx *c) {
   c->kwa.init(ar, p.restart, c->N1, c->pinned + 28);
   c->tmp_ns = ar.alloc<double>(c->N1);
   for (cudaStream_t &q : c->sx) CHNSS_CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+  for (cudaStream_t &q : c->side) CHNSS_CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+  CHNSS_CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  for (cudaEvent_t &e : c->ev_join) CHNSS_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   CHNSS_CK(cudaEventCreateWithFlags(&c->ev_asm, cudaEventDisableTiming));
   for (cudaEvent_t &e : c->ev_done) CHNSS_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   if (p.mobility_kind == 0) {
