@@ -168,7 +168,11 @@ chnss_status chnss_solve(chnss_ctx_t ctx, chnss_system sys, const double *rhs_or
  * potential, NS. */
 chnss_status chnss_step(chnss_ctx_t ctx, const chnss_state *in, chnss_state *out, chnss_solve_info *info);
 /* on = 0: chnss_step runs the three solve groups one after the other on the
- * context stream's host thread (same results); on != 0 (default): concurrently. */
+ * context stream's host thread, and the preconditioner graphs launch one
+ * kernel at a time (same results; used to time kernels alone); on != 0
+ * (default): the solve groups run concurrently and the independent parts of
+ * a preconditioner (Oseen pressure block, CH Schur groups) are parallel
+ * graph branches.  Changing the setting re-captures the context's graphs. */
 chnss_status chnss_set_step_concurrency(chnss_ctx_t ctx, int on);
 
 /* Same step with HOST arrays (same layout as chnss_state): copies the input

@@ -212,11 +212,15 @@ namespace {
 // for any pair of Krylov vectors.
 // Fork side stream k off s (its work becomes a parallel branch when s is
 // capturing) and join it back.
-void fork_side(chnss_ctx *c, cudaStream_t s, int k) {
+// Without concurrency (chnss_set_step_concurrency 0) the "side" is s itself.
+cudaStream_t fork_side(chnss_ctx *c, cudaStream_t s, int k) {
+  if (!c->concurrent) return s;
   CHNSS_CK(cudaEventRecord(c->ev_fork, s));
   CHNSS_CK(cudaStreamWaitEvent(c->side[k], c->ev_fork, 0));
+  return c->side[k];
 }
 void join_side(chnss_ctx *c, cudaStream_t s, int k) {
+  if (!c->concurrent) return;
   CHNSS_CK(cudaEventRecord(c->ev_join[k], c->side[k]));
   CHNSS_CK(cudaStreamWaitEvent(s, c->ev_join[k], 0));
 }
@@ -252,8 +256,7 @@ void ch_precond_batched(chnss_ctx *c, PrecSet<T> &P, cudaStream_t s) {
   // the Schur parts of the species groups are independent of MG(L) and of
   // each other: one side branch per group
   for (int g = 0; g < P.ngroups; ++g) {
-    fork_side(c, s, g);
-    cudaStream_t q = c->side[g];
+    cudaStream_t q = fork_side(c, s, g);
     MGBatch<T> &X = P.XB[g];
     for (int j = 0; j < P.gsize[g]; ++j) vec_convert_from_slot<double, T>(N1, in + 2 * P.gmem[g][j], N1, X.input(j), q);
     X.apply(q);
@@ -283,8 +286,7 @@ void ns_precond(chnss_ctx *c, PrecSet<T> &P, double **slot, cudaStream_t s) {
   const double *const *in = const_cast<const double *const *>(slot);
   double *const *out = slot + 1;
   // the pressure block is independent of the velocity block: a side branch
-  fork_side(c, s, 0);
-  cudaStream_t q = c->side[0];
+  cudaStream_t q = fork_side(c, s, 0);
   // pressure convection-diffusion: M_p^-1 A_p K_p^-1
   vec_convert_from_slot<double, T>(N1, in, nv, P.Kp.input(), q);
   P.Kp.apply(q);
@@ -1739,8 +1741,15 @@ extern "C" chnss_status chnss_set_spmv_block(chnss_ctx_t ctx, int block_p1, int 
 
 extern "C" chnss_status chnss_set_step_concurrency(chnss_ctx_t ctx, int on) {
   if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
-  ctx->concurrent = on != 0;
+  ABI_TRY
+  if (ctx->concurrent != (on != 0)) {
+    CHNSS_CK(cudaStreamSynchronize(ctx->s));
+    ctx->concurrent = on != 0;
+    destroy_graphs(ctx);     // the graphs' branch structure follows the setting
+    capture_graphs(ctx);
+  }
   return CHNSS_OK;
+  ABI_CATCH(ctx)
 }
 
 extern "C" chnss_status chnss_step_batched(int n_inst, chnss_ctx_t *ctxs, const chnss_state *in, chnss_state *out,
