@@ -424,6 +424,9 @@ def run_sweep(args):
         tuning[n] = c.autotune()
         del c
     ctxs = [chnss.Context(meshes[i["n"]], i["params"], stream=torch.cuda.Stream()) for i in inst]
+    if not args.sweep_concurrent_steps:  # instances overlap already: serial steps measured faster
+        for c in ctxs:
+            c.set_step_concurrency(False)
     a = [chnss.state_to_device(inputs.initial_state(i["n"], seed=i["seed"])) for i in inst]
     b = [c.new_state() for c in ctxs]
     threads = args.sweep_threads or min(16, os.cpu_count() or 1)
@@ -474,7 +477,8 @@ def run_sweep(args):
                    "total_p1_nodes": sum((i["n"] + 1) ** 2 for i in all_inst),
                    "evap_rate": [round(min(i["params"]["evap_rate"] for i in all_inst), 4),
                                  round(max(i["params"]["evap_rate"] for i in all_inst), 4)],
-                   "host_threads": threads, "l2": "inputs larger than L2 (tens of GB resident)",
+                   "host_threads": threads, "serial_steps": not args.sweep_concurrent_steps,
+                   "l2": "inputs larger than L2 (tens of GB resident)",
                    "timing": "wall clock around chnss_step_batched (it returns after every stream is synchronised)"},
         "tuning": {str(n): {"block_p1": t["block_p1"], "block_p2": t["block_p2"],
                             "ms_p1": [round(x, 4) for x in t["ms_p1"]], "ms_p2": [round(x, 4) for x in t["ms_p2"]]}
@@ -536,6 +540,7 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="batched 64-instance parameter sweep instead")
     ap.add_argument("--sweep-count", type=int, default=64)
     ap.add_argument("--sweep-threads", type=int, default=0)
+    ap.add_argument("--sweep-concurrent-steps", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-steps", type=int, default=1, help=argparse.SUPPRESS)
     args = ap.parse_args()
