@@ -14,6 +14,7 @@ advances from step to step.  One JSON line on rank 0.
   python bench.py [--steps K] [--warmup W] [--gpus N]
   python bench.py --impl reference     # the CPU oracle on the same metric
   python bench.py --sweep              # 64 independent instances, chnss_step_batched
+  python bench.py --adjoint            # gradient through 40 FP64 steps on 256 x 256
 """
 from __future__ import annotations
 
@@ -389,6 +390,55 @@ def shard(items: list, rank: int, world: int) -> list:
     return [x for i, x in enumerate(items) if i % world == rank]
 
 
+ADJOINT_METRIC = "gradients/s of J = int |grad phi_p(t_40)|^2 on 256x256 (40 FP64 steps, checkpoints every 8)"
+
+
+def run_adjoint(args):
+    """The adjoint workload: one full gradient of the final-morphology
+    functional with respect to (evaporation rate, mobility scale, initial
+    polymer field) through 40 FP64 steps on 256 x 256, with a checkpoint
+    every 8 steps (forward sweep, segment recomputation, adjoint steps).
+    A timed unit is one whole gradient."""
+    import torch
+
+    from paper_2501_11767_gb300 import adjoint, chnss, inputs
+
+    torch.cuda.set_device(0)
+    n, steps, every = 256, 40, 8
+    p = inputs.workload("film256_mobility")["params"]
+    p = dict(p, mobility_kind=0)      # the adjoint covers constant mobility
+    mesh = chnss.Mesh(n)
+    ctx = chnss.Context(mesh, p)
+    st0 = chnss.state_to_device(inputs.initial_state(n, seed=0))
+    for _ in range(args.warmup):
+        adjoint.trajectory_gradient(ctx, st0, 2, checkpoint_every=1)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(_device_uuid(torch, 0))
+    sampler.start()
+    t0 = time.perf_counter()
+    g = None
+    for _ in range(args.steps):
+        g = adjoint.trajectory_gradient(ctx, st0, steps, checkpoint_every=every)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    clocks = sampler.stop()
+    # forward steps per gradient: the sweep plus the recomputed segments
+    fwd = steps + sum(min(every, steps - k) for k in range(0, steps, every))
+    out = {
+        "metric": ADJOINT_METRIC, "value": round(args.steps / sec, 4), "unit": "gradients/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec / args.steps * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded SplitMix64 noise on phi_p, phi_NFA)",
+        "config": {"workload": "adjoint256", "n": n, "time_steps": steps, "checkpoint_every": every,
+                   "forward_steps_per_gradient": fwd, "adjoint_steps_per_gradient": steps,
+                   "adjoint_rtol": 1e-12, "forward_rtol": p["rtol"], "beta": p["beta"]},
+        "J": g["J"], "dJ_devap": g["evap"], "dJ_dgamma": g["gamma"],
+        "timing": "wall clock around trajectory_gradient (forward sweep, checkpoints, recomputation, adjoint steps)",
+        "clocks": clocks,
+    }
+    print(json.dumps(out))
+
+
 def run_sweep(args):
     """Batched parameter sweep: independent instances of uneven mesh size
     and evaporation rate, one context (and stream) each, advanced together
@@ -538,6 +588,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="batched 64-instance parameter sweep instead")
+    ap.add_argument("--adjoint", action="store_true", help="40-step gradient on 256x256 instead")
     ap.add_argument("--sweep-count", type=int, default=64)
     ap.add_argument("--sweep-threads", type=int, default=0)
     ap.add_argument("--sweep-concurrent-steps", action="store_true")
@@ -554,6 +605,9 @@ def main():
         return
     if args.sweep:
         run_sweep(args)
+        return
+    if args.adjoint:
+        run_adjoint(args)
         return
     run_gpu(args)
 
