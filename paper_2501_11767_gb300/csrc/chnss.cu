@@ -261,10 +261,21 @@ void ch_precond_batched(chnss_ctx *c, PrecSet<T> &P, cudaStream_t s) {
     for (int j = 0; j < P.gsize[g]; ++j) vec_convert_from_slot<double, T>(N1, in + 2 * P.gmem[g][j], N1, X.input(j), q);
     X.apply(q);
     MultiArgs<T> none;
-    spmv_sell_multi<T>(p1, P.Mv, P.gsize[g], X.x[0], X.b[0], SPMV_PLAIN, none, q);   // X2 = X1 (constant mobility)
-    X.apply(q);
-    for (int j = 0; j < P.gsize[g]; ++j)
-      vec_convert_to_slot<T, double>(N1, X.output(j), slot + 2 * P.gmem[g][j] + 1, N1, q);
+    if (c->p.mobility_kind == 0) {   // X2 = X1: a second batched V-cycle
+      spmv_sell_multi<T>(p1, P.Mv, P.gsize[g], X.x[0], X.b[0], SPMV_PLAIN, none, q);
+      X.apply(q);
+      for (int j = 0; j < P.gsize[g]; ++j)
+        vec_convert_to_slot<T, double>(N1, X.output(j), slot + 2 * P.gmem[g][j] + 1, N1, q);
+    } else {                         // X2 per species (tau K_kappa + a M at t_k)
+      MultiPtr<T> x2in;
+      for (int j = 0; j < P.gsize[g]; ++j) x2in.p[j] = P.X2[P.gmem[g][j]].input();
+      spmv_sell_multi<T>(p1, P.Mv, P.gsize[g], X.x[0], x2in, SPMV_PLAIN, none, q);
+      for (int j = 0; j < P.gsize[g]; ++j) {
+        MGHier<T> &X2 = P.X2[P.gmem[g][j]];
+        X2.apply(q);
+        vec_convert_to_slot<T, double>(N1, X2.output(), slot + 2 * P.gmem[g][j] + 1, N1, q);
+      }
+    }
   }
   for (int k = 0; k < 3; ++k) vec_convert_from_slot<double, T>(N1, in + 2 * k, 0, P.LB.input(k), s);
   P.LB.apply(s);
@@ -520,8 +531,9 @@ void init_precset(chnss_ctx *c, PrecSet<T> &P) {
     h->prof = &c->prof;
   P.Kp.setup(c->s);
   for (int sp = 0; sp < 3; ++sp) P.X1[sp].setup(c->s);
-  if (c->p.mobility_kind == 0 && c->p.model == 0) {
+  if (c->p.model == 0) {
     // species with equal (gamma, beta) have bitwise equal X1 = tau gamma K + sqrt(tau gamma / beta) M
+    // (the variable-mobility factors X2 stay per species)
     P.LB.init(ar, &P.L, 3);
     for (int sp = 0; sp < 3; ++sp) {
       int g = 0;
@@ -683,7 +695,7 @@ void create_context(chnss_ctx *c) {
   for (cudaEvent_t &e : c->ev_join) CHNSS_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   CHNSS_CK(cudaEventCreateWithFlags(&c->ev_asm, cudaEventDisableTiming));
   for (cudaEvent_t &e : c->ev_done) CHNSS_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-  if (p.mobility_kind == 0) {
+  if (p.model == 0) {   // idle members of the batched CH solves
     c->dummy_in = ar.alloc<double>(2L * c->N1);
     c->dummy_out = ar.alloc<double>(2L * c->N1);
     vec_fill(2L * c->N1, 0.0, c->dummy_in, s);

@@ -191,15 +191,16 @@ def test_mixed_precision_step(torch, precision):
         st = ref
 
 
-@pytest.mark.parametrize("precision,beta", [(0, None), (1, None), (1, [0.02, 0.03, 0.1, 1.0]),
-                                            (0, [0.05, 0.05, 0.05, 1.0])])
-def test_batched_ch_solves_equal_single_solves(torch, precision, beta):
+@pytest.mark.parametrize("precision,beta,mobility", [(0, None, 0), (1, None, 0), (1, [0.02, 0.03, 0.1, 1.0], 0),
+                                                     (0, [0.05, 0.05, 0.05, 1.0], 0), (0, None, 1), (1, None, 1)])
+def test_batched_ch_solves_equal_single_solves(torch, precision, beta, mobility):
     """chnss_step solves the three CH systems together (one batched
     preconditioner per Krylov tick, shared matrix sweeps); each species must
     come out bitwise as its own chnss_solve, for 1, 2 and 3 groups of equal
-    Schur factors."""
+    Schur factors, and with the per-species factors X2 of the variable
+    mobility."""
     n = 32
-    p = dict(inputs.default_params(), precision=precision)
+    p = dict(inputs.default_params(), precision=precision, mobility_kind=mobility)
     if beta:
         p["beta"] = beta
     mesh = chnss.Mesh(n)
