@@ -197,7 +197,11 @@ chnss_status chnss_step_host(chnss_ctx_t ctx, const chnss_state *host_in, chnss_
  * velocity adjoints are zero on the no-slip boundary, the pressure adjoint
  * is zero because p^k does not enter the step).  grad_params (HOST, 2
  * doubles, accumulated): d/d(evap_rate) and d/d(gamma) where gamma scales
- * all three mobilities.  info[6] (optional): the transposed solves. */
+ * all three mobilities.  info[6] (optional): the transposed solves.
+ * Like chnss_step, the three independent groups (Oseen; Allen-Cahn; air
+ * potential then Cahn-Hilliard) run concurrently on library streams unless
+ * chnss_set_step_concurrency(ctx, 0); the result is bitwise the same either
+ * way.  Synchronises the context stream before returning. */
 chnss_status chnss_adjoint_step(chnss_ctx_t ctx, const chnss_state *state_k, const chnss_state *state_k1,
                                 const chnss_state *adj_k1, chnss_state *adj_k, double *grad_params,
                                 chnss_solve_info *info);

@@ -178,6 +178,9 @@ struct chnss_ctx {
   double *topv = nullptr, *mvec = nullptr;  // int_Gt psi, M 1
   double *arhs = nullptr, *ay = nullptr, *alam = nullptr, *az = nullptr, *atmp = nullptr, *atv = nullptr;
   double *alw[5] = {};
+  // per-group work and accumulators of the concurrent adjoint step (AC, CH)
+  double *ay_ac = nullptr, *aPhi = nullptr, *v_ac = nullptr;
+  double *arhs_ch = nullptr, *ay_ch = nullptr, *atmp_ch = nullptr, *aphi = nullptr, *v_ch = nullptr;
   double *adots = nullptr;                  // device scalars of the parameter gradients
   const Level &lv(int l) const { return mesh->m.lv[l]; }
   ~chnss_ctx() {
@@ -1456,6 +1459,14 @@ void adjoint_alloc(chnss_ctx *c) {
   c->atmp = ar.alloc<double>(N1);
   c->atv = ar.alloc<double>(2L * c->N2);
   for (double *&w : c->alw) w = ar.alloc<double>(N1);
+  c->ay_ac = ar.alloc<double>(N1);
+  c->aPhi = ar.alloc<double>(N1);
+  c->v_ac = ar.alloc<double>(2L * c->N2);
+  c->arhs_ch = ar.alloc<double>(2L * N1);
+  c->ay_ch = ar.alloc<double>(2L * N1);
+  c->atmp_ch = ar.alloc<double>(N1);
+  c->aphi = ar.alloc<double>(3L * N1);
+  c->v_ch = ar.alloc<double>(2L * c->N2);
   c->adots = ar.alloc<double>(32);
   k_top_load_vec<<<nb(N1), TPB, 0, c->s>>>((int)N1, F.n, F.hx, c->topv);
   CHNSS_LAUNCH_CK();
@@ -1465,8 +1476,8 @@ void adjoint_alloc(chnss_ctx *c) {
 }
 
 // out += alpha * (per-element P1 contributions gathered to nodes)
-void gather_p1_add(chnss_ctx *c, const double *buf, double alpha, double *out) {
-  launch_gather(c->mesh->m.g_l1, 1, buf, alpha, out, 1.0, out, c->s);
+void gather_p1_add(chnss_ctx *c, const double *buf, double alpha, double *out, cudaStream_t s) {
+  launch_gather(c->mesh->m.g_l1, 1, buf, alpha, out, 1.0, out, s);
 }
 
 chnss_status adjoint_step(chnss_ctx *c, const chnss_state *stk, const chnss_state *st1, const chnss_state *lam,
@@ -1484,8 +1495,6 @@ chnss_status adjoint_step(chnss_ctx *c, const chnss_state *stk, const chnss_stat
   const double tau = p.tau;
   chnss_solve_info loc[6];
   chnss_solve_info *inf = info ? info : loc;
-  chnss_status worst = CHNSS_OK;
-  auto keep = [&](chnss_status st) { if (worst == CHNSS_OK) worst = st; };
   SpmvArgs none;
   // transposed fine operators
   sell_gather_transposed(F.p1.sell, 1, c->L[0], c->LsT, s);
@@ -1498,81 +1507,132 @@ chnss_status adjoint_step(chnss_ctx *c, const chnss_state *stk, const chnss_stat
   vec_fill(N1, 0.0, out->p, s);
   vec_fill(32, 0.0, c->adots, s);
   double *D = c->adots;
-  // ---- Navier-Stokes -------------------------------------------------------
-  k_mask_velocity<<<nb(c->N2), TPB, 0, s>>>(c->N2, lam->v, F.bnd2, c->arhs);
-  CHNSS_LAUNCH_CK();
-  vsum<double>(N1, lam->p, c->sum, c->partial, s);
-  k_mean_shift_T<<<nb(N1), TPB, 0, s>>>(N1, lam->p, c->mvec, c->sum, m.lx * m.ly, c->arhs + nv);
-  CHNSS_LAUNCH_CK();
-  {
+  CHNSS_CK(cudaEventRecord(c->ev_asm, s));
+  // Three independent groups, as in the forward step: Navier-Stokes, Allen-
+  // Cahn, air potential -> Cahn-Hilliard.  Each has its own Krylov work,
+  // scratch, slice of ebuf and accumulators; the groups' contributions to
+  // the shared adjoints are summed on s after the join in a fixed order, so
+  // the result does not depend on whether the groups overlap.
+  auto group_ns = [&](cudaStream_t q) -> chnss_status {
+    KrylovWork &kw = c->kw;
+    k_mask_velocity<<<nb(c->N2), TPB, 0, q>>>(c->N2, lam->v, F.bnd2, c->arhs);
+    CHNSS_LAUNCH_CK();
+    vsum<double>(N1, lam->p, c->sum, kw.partial, q);
+    k_mean_shift_T<<<nb(N1), TPB, 0, q>>>(N1, lam->p, c->mvec, c->sum, m.lx * m.ly, c->arhs + nv);
+    CHNSS_LAUNCH_CK();
     NSOpT op(c);
-    keep(fgmres(op, c->arhs, c->ay, kAdjointRtol, 0.0, p.maxit, c->kw, &inf[5], s, &c->prof));
-  }
-  const double *yv = c->ay;
-  spmv_csr<double>(F.p2, c->M2v[0], 2, yv, c->atv, SPMV_PLAIN, none, s);
-  vec_axpby(nv, 1.0 / tau, c->atv, 1.0, out->v, s);                       // (M_v / tau)^T y_v
-  KortewegCoef kc;
-  for (int f = 0; f < 4; ++f) kc.beta[f] = p.beta[f];
-  kc.beta_v = p.beta_v;
-  launch_adj_korteweg(g0, stk->phi[0], stk->phi[1], stk->phi[2], stk->Phi_v, yv, kc, c->lbuf, s);
-  for (int f = 0; f < 3; ++f) gather_p1_add(c, c->lbuf + (long)f * E * 3, 1.0, out->phi[f]);
-  gather_p1_add(c, c->lbuf + 3L * E * 3, 1.0, out->Phi_v);
-  launch_adj_conv_p2(g0, st1->v, yv, c->ebuf, c->ebuf + 12L * E, s);
-  launch_gather(m.g_l2, 2, c->ebuf, -1.0, out->v, 1.0, out->v, s);       // - (dJ(w)x/dv)^T y
-  launch_gather(m.g_l1, 1, c->ebuf + 12L * E, 1.0, nullptr, 0.0, c->atmp, s);
-  for (int i = 0; i < 4; ++i) vec_axpby(N1, -p.alpha[i], c->atmp, 1.0, out->mu[i], s);
-  // ---- air potential -------------------------------------------------------
-  keep(pcg(F.p1, c->M1[0], c->dinvM, lam->mu[3], c->az, kAdjointRtol, 1000, c->kw, &inf[4], s));
-  spmv_csr<double>(F.p1, c->K1[0], 1, c->az, c->atmp, SPMV_PLAIN, none, s);
-  for (int i = 0; i < 3; ++i) {
-    vec_copy(N1, lam->phi[i], c->alam + (long)i * N1, s);
-    vec_axpby(N1, -p.beta[3], c->atmp, 1.0, c->alam + (long)i * N1, s);
-  }
-  vec_copy(N1, c->az, c->alw[3], s);
-  dot<double>(N1, c->topv, c->az, D + 0, c->partial, s);
-  // ---- Allen-Cahn ----------------------------------------------------------
-  {
+    const chnss_status st = fgmres(op, c->arhs, c->ay, kAdjointRtol, 0.0, p.maxit, kw, &inf[5], q, &c->prof);
+    const double *yv = c->ay;
+    spmv_csr<double>(F.p2, c->M2v[0], 2, yv, c->atv, SPMV_PLAIN, none, q);
+    vec_axpby(nv, 1.0 / tau, c->atv, 1.0, out->v, q);                       // (M_v / tau)^T y_v
+    KortewegCoef kc;
+    for (int f = 0; f < 4; ++f) kc.beta[f] = p.beta[f];
+    kc.beta_v = p.beta_v;
+    launch_adj_korteweg(g0, stk->phi[0], stk->phi[1], stk->phi[2], stk->Phi_v, yv, kc, c->lbuf, q);
+    for (int f = 0; f < 3; ++f) gather_p1_add(c, c->lbuf + (long)f * E * 3, 1.0, out->phi[f], q);
+    gather_p1_add(c, c->lbuf + 3L * E * 3, 1.0, out->Phi_v, q);
+    launch_adj_conv_p2(g0, st1->v, yv, c->ebuf, c->ebuf + 12L * E, q);
+    launch_gather(m.g_l2, 2, c->ebuf, -1.0, out->v, 1.0, out->v, q);       // - (dJ(w)x/dv)^T y
+    launch_gather(m.g_l1, 1, c->ebuf + 12L * E, 1.0, nullptr, 0.0, c->atmp, q);
+    for (int i = 0; i < 4; ++i) vec_axpby(N1, -p.alpha[i], c->atmp, 1.0, out->mu[i], q);
+    return st;
+  };
+  auto group_ac = [&](cudaStream_t q) -> chnss_status {
+    double *eb = c->ebuf + 16L * E;
     ACOpT op(c);
-    keep(fgmres(op, lam->Phi_v, c->ay, kAdjointRtol, 0.0, p.maxit, c->kw, &inf[3], s, &c->prof));
-  }
-  spmv_csr<double>(F.p1, c->M1[0], 1, c->ay, c->atmp, SPMV_PLAIN, none, s);
-  vec_axpby(N1, 1.0, c->atmp, 1.0, out->Phi_v, s);
-  vec_fill(N1, 0.0, c->alw[4], s);
-  vec_axpby(N1, -tau * p.gamma_v, c->ay, 0.0, c->alw[4], s);
-  launch_adj_conv_p1(g0, st1->Phi_v, c->ay, c->ebuf, s);
-  launch_gather(m.g_l2, 2, c->ebuf, -tau, out->v, 1.0, out->v, s);
-  dot<double>(N1, c->topv, c->ay, D + 1, c->partial, s);
-  // ---- Cahn-Hilliard -------------------------------------------------------
-  for (int i = 0; i < 3; ++i) {
-    vec_copy(N1, c->alam + (long)i * N1, c->arhs, s);
-    vec_copy(N1, lam->mu[i], c->arhs + N1, s);
-    {
-      CHOpT op(c, i);
-      keep(fgmres(op, c->arhs, c->ay, kAdjointRtol, 0.0, p.maxit, c->kw, &inf[i], s, &c->prof));
+    const chnss_status st = fgmres(op, lam->Phi_v, c->ay_ac, kAdjointRtol, 0.0, p.maxit, c->kwa, &inf[3], q, &c->prof);
+    spmv_csr<double>(F.p1, c->M1[0], 1, c->ay_ac, c->aPhi, SPMV_PLAIN, none, q);
+    vec_fill(N1, 0.0, c->alw[4], q);
+    vec_axpby(N1, -tau * p.gamma_v, c->ay_ac, 0.0, c->alw[4], q);
+    launch_adj_conv_p1(g0, st1->Phi_v, c->ay_ac, eb, q);
+    launch_gather(m.g_l2, 2, eb, -tau, nullptr, 0.0, c->v_ac, q);
+    dot<double>(N1, c->topv, c->ay_ac, D + 1, c->kwa.partial, q);
+    return st;
+  };
+  auto group_ch = [&](cudaStream_t q, chnss_status *st_mu) -> chnss_status {
+    double *eb = c->ebuf + 32L * E;
+    double *tmp = c->atmp_ch;
+    // air potential
+    *st_mu = pcg(F.p1, c->M1[0], c->dinvM, lam->mu[3], c->az, kAdjointRtol, 1000, c->kwb[0], &inf[4], q);
+    spmv_csr<double>(F.p1, c->K1[0], 1, c->az, tmp, SPMV_PLAIN, none, q);
+    for (int i = 0; i < 3; ++i) {
+      vec_copy(N1, lam->phi[i], c->alam + (long)i * N1, q);
+      vec_axpby(N1, -p.beta[3], tmp, 1.0, c->alam + (long)i * N1, q);
     }
-    const double *y1 = c->ay, *y2 = c->ay + N1;
-    const double cc = tau * p.gamma[i] / p.beta[i];
-    spmv_csr<double>(F.p1, c->M1[0], 1, y1, c->atmp, SPMV_PLAIN, none, s);
-    vec_axpby(N1, 1.0, c->atmp, 1.0, out->phi[i], s);
-    vec_fill(N1, 0.0, c->alw[i], s);
-    vec_axpby(N1, -cc, y2, 0.0, c->alw[i], s);
-    launch_adj_conv_p1(g0, st1->phi[i], y1, c->ebuf, s);
-    launch_gather(m.g_l2, 2, c->ebuf, -tau, out->v, 1.0, out->v, s);
-    double *d = D + 4 + 5 * i;
-    dot<double>(N1, c->loads + (long)i * N1, y2, d + 0, c->partial, s);    // F_i . y2
-    dot<double>(N1, c->topv, y2, d + 1, c->partial, s);                     // t . y2
-    spmv_csr<double>(F.p1, c->K1[0], 1, st1->mu[i], c->atmp, SPMV_PLAIN, none, s);
-    dot<double>(N1, y1, c->atmp, d + 2, c->partial, s);                     // y1 . K mu'
-    spmv_csr<double>(F.p1, c->K1[0], 1, st1->phi[i], c->atmp, SPMV_PLAIN, none, s);
-    dot<double>(N1, y2, c->atmp, d + 3, c->partial, s);                     // y2 . K phi'
-    spmv_csr<double>(F.p1, c->M1[0], 1, st1->mu[i], c->atmp, SPMV_PLAIN, none, s);
-    dot<double>(N1, y2, c->atmp, d + 4, c->partial, s);                     // y2 . M mu'
+    vec_copy(N1, c->az, c->alw[3], q);
+    dot<double>(N1, c->topv, c->az, D + 0, c->kwb[0].partial, q);
+    // Cahn-Hilliard
+    chnss_status worst = CHNSS_OK;
+    vec_fill(nv, 0.0, c->v_ch, q);
+    KrylovWork &kw = c->kwc0;
+    for (int i = 0; i < 3; ++i) {
+      vec_copy(N1, c->alam + (long)i * N1, c->arhs_ch, q);
+      vec_copy(N1, lam->mu[i], c->arhs_ch + N1, q);
+      {
+        CHOpT op(c, i);
+        const chnss_status st = fgmres(op, c->arhs_ch, c->ay_ch, kAdjointRtol, 0.0, p.maxit, kw, &inf[i], q, &c->prof);
+        if (worst == CHNSS_OK) worst = st;
+      }
+      const double *y1 = c->ay_ch, *y2 = c->ay_ch + N1;
+      const double cc = tau * p.gamma[i] / p.beta[i];
+      spmv_csr<double>(F.p1, c->M1[0], 1, y1, c->aphi + (long)i * N1, SPMV_PLAIN, none, q);
+      vec_fill(N1, 0.0, c->alw[i], q);
+      vec_axpby(N1, -cc, y2, 0.0, c->alw[i], q);
+      launch_adj_conv_p1(g0, st1->phi[i], y1, eb, q);
+      launch_gather(m.g_l2, 2, eb, -tau, c->v_ch, 1.0, c->v_ch, q);
+      double *d = D + 4 + 5 * i;
+      dot<double>(N1, c->loads + (long)i * N1, y2, d + 0, kw.partial, q);    // F_i . y2
+      dot<double>(N1, c->topv, y2, d + 1, kw.partial, q);                     // t . y2
+      spmv_csr<double>(F.p1, c->K1[0], 1, st1->mu[i], tmp, SPMV_PLAIN, none, q);
+      dot<double>(N1, y1, tmp, d + 2, kw.partial, q);                         // y1 . K mu'
+      spmv_csr<double>(F.p1, c->K1[0], 1, st1->phi[i], tmp, SPMV_PLAIN, none, q);
+      dot<double>(N1, y2, tmp, d + 3, kw.partial, q);                         // y2 . K phi'
+      spmv_csr<double>(F.p1, c->M1[0], 1, st1->mu[i], tmp, SPMV_PLAIN, none, q);
+      dot<double>(N1, y2, tmp, d + 4, kw.partial, q);                         // y2 . M mu'
+    }
+    return worst;
+  };
+  chnss_status st[4] = {CHNSS_OK, CHNSS_OK, CHNSS_OK, CHNSS_OK};   // CH, AC, NS, air potential
+  std::exception_ptr err[3];
+  int dev = 0;
+  CHNSS_CK(cudaGetDevice(&dev));
+  auto run = [&](int w) {
+    try {
+      CHNSS_CK(cudaSetDevice(dev));
+      cudaStream_t q = c->sx[w];
+      CHNSS_CK(cudaStreamWaitEvent(q, c->ev_asm, 0));
+      if (w == 0) st[0] = group_ch(q, &st[3]);
+      else if (w == 1) st[1] = group_ac(q);
+      else st[2] = group_ns(q);
+      CHNSS_CK(cudaEventRecord(c->ev_done[w], q));
+    } catch (...) {
+      err[w] = std::current_exception();
+    }
+  };
+  if (c->concurrent) {
+    std::thread t_ac(run, 1), t_ns(run, 2);
+    run(0);
+    t_ac.join();
+    t_ns.join();
+  } else {
+    for (int w = 0; w < 3; ++w) run(w);
   }
+  for (std::exception_ptr &e : err)
+    if (e) std::rethrow_exception(e);
+  for (cudaEvent_t e : c->ev_done) CHNSS_CK(cudaStreamWaitEvent(s, e, 0));
+  chnss_status worst = CHNSS_OK;
+  for (chnss_status x : {st[2], st[3], st[1], st[0]})   // the order of the sequential adjoint: NS, mu_a, AC, CH
+    if (worst == CHNSS_OK) worst = x;
+  // ---- the groups' contributions to the shared adjoints ---------------------
+  vec_axpby(nv, 1.0, c->v_ac, 1.0, out->v, s);
+  vec_axpby(nv, 1.0, c->v_ch, 1.0, out->v, s);
+  vec_axpby(N1, 1.0, c->aPhi, 1.0, out->Phi_v, s);
+  for (int i = 0; i < 3; ++i) vec_axpby(N1, 1.0, c->aphi + (long)i * N1, 1.0, out->phi[i], s);
   // ---- potential loads ------------------------------------------------------
   const double *lw[5] = {c->alw[0], c->alw[1], c->alw[2], c->alw[3], c->alw[4]};
   launch_adj_loads(g0, stk->phi[0], stk->phi[1], stk->phi[2], stk->Phi_v, lw, c->lbuf, s);
-  for (int f = 0; f < 3; ++f) gather_p1_add(c, c->lbuf + (long)f * E * 3, 1.0, out->phi[f]);
-  gather_p1_add(c, c->lbuf + 3L * E * 3, 1.0, out->Phi_v);
+  for (int f = 0; f < 3; ++f) gather_p1_add(c, c->lbuf + (long)f * E * 3, 1.0, out->phi[f], s);
+  gather_p1_add(c, c->lbuf + 3L * E * 3, 1.0, out->Phi_v, s);
   // ---- parameter gradients --------------------------------------------------
   double h[24], phis_ref = 0.0;
   CHNSS_CK(cudaMemcpyAsync(h, D, 24 * sizeof(double), cudaMemcpyDeviceToHost, s));

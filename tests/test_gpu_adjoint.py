@@ -52,6 +52,33 @@ def test_adjoint_step_matches_oracle(torch):
     assert grad[1] == pytest.approx(th["gamma"], rel=1e-8)
 
 
+def test_concurrent_adjoint_equals_serial(torch):
+    """The three adjoint groups (NS, AC, air potential -> CH) overlap on their
+    own streams; their contributions are summed in a fixed order, so the
+    result is bitwise the one of the serial setting."""
+    n = 24
+    p = _params()
+    o = Oracle(n, p)
+    s0 = inputs.initial_state(n, seed=9)
+    sk = o.step(s0)[0]
+    sk1 = o.step(sk)[0]
+    rng = np.random.default_rng(3)
+    lam = {k: rng.standard_normal(v.shape) for k, v in sk.items()}
+    lam["v"][np.repeat(o.mesh.p2_boundary(), 2)] = 0.0
+    res = []
+    for conc in (1, 0):
+        ctx = chnss.Context(chnss.Mesh(n), p)
+        ctx.set_step_concurrency(conc)
+        out, grad, info, st = ctx.adjoint_step(*(chnss.state_to_device(x) for x in (sk, sk1, lam)))
+        assert st == 0
+        res.append((chnss.state_to_numpy(out), list(grad), [v["iters"] for v in info.values()]))
+    (a, ga, ia), (b, gb, ib) = res
+    assert ia == ib
+    assert ga == gb
+    for key in ("phi", "mu", "Phi_v", "v", "p"):
+        assert np.array_equal(np.asarray(a[key]), np.asarray(b[key])), key
+
+
 @pytest.fixture(scope="module")
 def trajectory(torch):
     n, steps = 16, 4
