@@ -152,3 +152,32 @@ class MG:
             x = self.vcycle(b)
             return x - x.mean()
         return self.vcycle(b)
+
+    def solve(self, b, rtol, maxit):
+        """Multigrid as an inner solver with a tolerance (Sec. 5: the AMG
+        preconditioners are applied to a relative tolerance): the stationary
+        iteration x <- x + V(b - A x) from x = 0, stopped once
+        ||b - A x|| <= rtol ||b|| or after maxit V-cycles.  Returns (x, cycles).
+        For the singular pressure Laplacian b is first projected to mean
+        zero, and every V-cycle projects its input and output."""
+        A = self.mats[0]
+        if self.singular:
+            b = b - b.mean()
+        nb = float(np.linalg.norm(b))
+        x = self(b)
+        r = b - A @ x
+        cycles = 1
+        while float(np.linalg.norm(r)) > rtol * nb and cycles < maxit:
+            x = x + self(r)
+            r = b - A @ x
+            cycles += 1
+        return x, cycles
+
+    def inner(self, params):
+        """The block inverse a preconditioner applies: one V-cycle
+        (params["inner_rtol"] = 0) or solve() to inner_rtol."""
+        rtol = params.get("inner_rtol", 0.0)
+        if not rtol:
+            return self
+        maxit = params.get("inner_maxit", 20)
+        return lambda b: self.solve(b, rtol, maxit)[0]

@@ -12,6 +12,10 @@ Order of work (Sec. 3 time scheme, Sec. 4 systems, Sec. 5 air recovery):
   5. Oseen system eqn:linearnav, FGMRES with diag(MG(A), M_p^{-1} A_p K_p^{-1})
      (pressure convection-diffusion); pressure shifted to zero mean.
 All matrices use coefficients at t_k, so 2, 3 and 5 are independent.
+Every MG(.) above is one V-cycle, or with params["inner_rtol"] > 0 the
+V-cycle iteration MG.solve to that relative tolerance (Sec. 5 applies its
+AMG preconditioners with a tolerance of 1e-4); M_p^{-1} stays the fixed
+Chebyshev iteration.
 
 Solvent-air sub-model (params["model"] = 1, Sec. 5.1): no polymer or NFA
 (their fields stay zero and their CH systems are not solved), the
@@ -107,11 +111,12 @@ class Oracle:
             mgX2 = MG(X2, self.P1)
         M = self.forms[0].M
         N = self.mesh.N1
+        iL, iX1, iX2 = mgL.inner(p), mgX1.inner(p), mgX2.inner(p)
 
         def apply(r):
             z = np.empty_like(r)
-            z[:N] = mgL(r[:N])
-            z[N:] = mgX2(M @ mgX1(r[N:]))
+            z[:N] = iL(r[:N])
+            z[N:] = iX2(M @ iX1(r[N:]))
             return z
         return apply
 
@@ -135,7 +140,7 @@ class Oracle:
             return x, info, (A, rhs)
         mats = [(f.M + tau * p["delta_v"] * f.K + tau * C).tocsr() for f, C in zip(self.forms, convs)]
         mg = MG(mats, self.P1)
-        x, info = fgmres(lambda y: A @ y, mg, rhs, p["rtol"], p["atol"], p["restart"], p["maxit"])
+        x, info = fgmres(lambda y: A @ y, mg.inner(p), rhs, p["rtol"], p["atol"], p["restart"], p["maxit"])
         return x, info, (A, rhs)
 
     def solve_mu_a(self, f_a, phi_new):
@@ -176,6 +181,7 @@ class Oracle:
             else:
                 self._Kp = MG([f.K for f in self.forms], self.P1, singular=True)
         mgK = self._Kp
+        iA, iK = mgA.inner(p), mgK.inner(p)
         Mp = self.forms[0].M
         mdinv = 1.0 / Mp.diagonal()
         lo, hi = MASS_CHEB_BOUNDS
@@ -183,8 +189,8 @@ class Oracle:
 
         def apply(r):
             z = np.empty_like(r)
-            z[:nv] = mgA(r[:nv])
-            t = Ap @ mgK(r[nv:])
+            z[:nv] = iA(r[:nv])
+            t = Ap @ iK(r[nv:])
             z[nv:] = chebyshev(lambda y: Mp @ y, mdinv, t, None, lo, hi, MASS_CHEB_DEGREE)
             return z
         return apply
