@@ -208,6 +208,13 @@ def run_gpu(args):
     ctx, ms, infos, _, launches, clocks = timed_run(params, args.warmup, args.steps, False)
     launches_before_timed = timed_run.launches_before
     state_after = timed_run.last_state
+    inner = None
+    if params.get("inner_rtol", 0.0) > 0:
+        inner = {"inner_rtol": params["inner_rtol"], "inner_maxit": params["inner_maxit"],
+                 "over": "warm-up and timed steps",
+                 "blocks": {b: {"solves": v["solves"], "vcycles_per_solve": round(v["cycles"] / v["solves"], 2)}
+                            for b, v in ctx.inner_stats().items() if v["solves"]},
+                 "gpu_launches_note": "a WHILE-node body counts once per graph launch, not once per V-cycle"}
     ms_t = torch.tensor([ms], device=dev)
     if world > 1:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
@@ -247,8 +254,10 @@ def run_gpu(args):
     # roofline region: the same workload with every solve alone on the stream
     # (serial step) and CUDA-event probes around the instrumented kernels, so
     # that each family's duration is not shared with concurrent solves
-    ctxr, ms_r, _, prof, _, _ = timed_run(params, args.warmup, args.roofline_steps, True, concurrent=False)
-    del ctxr
+    ms_r, prof = 0.0, {"kinds": {}}
+    if args.roofline_steps > 0:
+        ctxr, ms_r, _, prof, _, _ = timed_run(params, args.warmup, args.roofline_steps, True, concurrent=False)
+        del ctxr
 
     bf16 = None
     if args.bf16_steps > 0:
@@ -299,8 +308,7 @@ def run_gpu(args):
                 "bytes_per_launch": d["bytes"] / d["launches"], "ms_per_launch": ms_l,
                 "launches": d["launches"], "traffic": _traffic(name, d["bytes"] / d["launches"])}
 
-    dom = max(kinds, key=lambda k: kinds[k]["ms"])
-    roofline = family_roofline(dom)
+    roofline = family_roofline(max(kinds, key=lambda k: kinds[k]["ms"])) if kinds else None
     rooflines = {k: family_roofline(k) for k in kinds}
     families = {k: {"ms_total": round(v["ms"], 3), "launches": v["launches"],
                     "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 and v["bytes"] > 0 else None,
@@ -339,8 +347,10 @@ def run_gpu(args):
         "fp64": fp64,
         "speedup_mixed_vs_fp64": round(value / fp64["value"], 3) if fp64 else None,
         "bf16_preconditioner": bf16,
+        "inner_multigrid": inner,
         "roofline": roofline,
-        "roofline_region": {"steps": args.roofline_steps, "warmup": args.warmup, "ms_per_step": round(ms_r / args.roofline_steps, 3),
+        "roofline_region": {"steps": args.roofline_steps, "warmup": args.warmup,
+                            "ms_per_step": round(ms_r / args.roofline_steps, 3) if args.roofline_steps else None,
                             "how": "separate timed region, solves one after the other (chnss_set_step_concurrency 0), "
                                    "CUDA events around each instrumented launch on its stream; the headline value "
                                    "comes from the concurrent region without probes"},

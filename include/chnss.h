@@ -86,6 +86,13 @@ typedef struct {
   double chi_sa;         /* model 1: Flory-Huggins interaction solvent-air */
   double n_s, n_a;       /* model 1: molar sizes N_s, N_a (> 0) */
   double phi_sat_s, phi_sat_a;  /* model 1: saturated vapour fractions (> 0) */
+  double inner_rtol;     /* 0: every multigrid block of the preconditioners is one V-cycle;
+                            > 0 (< 1): each is the V-cycle iteration x <- x + V(b - A x) from
+                            x = 0 to ||b - A x|| <= inner_rtol ||b|| (Sec. 5 applies its AMG
+                            preconditioners to a tolerance of 1e-4): MG(M + tau C), the
+                            matching factors X, MG of the AC matrix, the velocity block and
+                            K_p; the CH species are then solved one after the other */
+  int inner_maxit;       /* cap on the V-cycles of one inner solve (1..1000, inner_rtol > 0) */
 } chnss_params;
 
 /* Fields of one time level (DEVICE pointers, caller-owned, FP64). */
@@ -240,6 +247,21 @@ typedef struct {
 chnss_status chnss_profile_enable(chnss_ctx_t ctx, int on);
 /* Read the counters (synchronises the stream). */
 chnss_status chnss_profile_read(chnss_ctx_t ctx, chnss_profile *out);
+
+/* Inner multigrid solves (inner_rtol > 0), per preconditioner block in the
+ * order MG(M + tau C), MG(M + tau delta_v K + tau C), velocity MG(A),
+ * MG(K_p), X1 of polymer / NFA / solvent, X2 of polymer / NFA / solvent
+ * (CHNSS_INNER_BLOCKS): inner solves and V-cycles since the last reset, and
+ * ||b - A x|| / ||b|| at the end of the last solve.  Blocks without inner
+ * solves (inner_rtol = 0, X2 with constant mobility) report zeros.
+ * reset != 0 clears the counts after reading.  Synchronises the stream. */
+#define CHNSS_INNER_BLOCKS 10
+typedef struct {
+  long long solves[CHNSS_INNER_BLOCKS];
+  long long cycles[CHNSS_INNER_BLOCKS];
+  double last_rel_residual[CHNSS_INNER_BLOCKS];
+} chnss_inner_stats;
+chnss_status chnss_inner_stats_read(chnss_ctx_t ctx, int reset, chnss_inner_stats *out);
 
 /* Mass-matrix solve that allocates nothing.  The paper has no counterpart:
  * this is a service entry point of the library.  It solves M x = rhs for the

@@ -30,7 +30,8 @@ class Params(ctypes.Structure):
                 ("ac_top_flux", ctypes.c_int), ("precision", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("atol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("model", ctypes.c_int), ("chi_sa", ctypes.c_double), ("n_s", ctypes.c_double),
-                ("n_a", ctypes.c_double), ("phi_sat_s", ctypes.c_double), ("phi_sat_a", ctypes.c_double)]
+                ("n_a", ctypes.c_double), ("phi_sat_s", ctypes.c_double), ("phi_sat_a", ctypes.c_double),
+                ("inner_rtol", ctypes.c_double), ("inner_maxit", ctypes.c_int)]
 
 
 class State(ctypes.Structure):
@@ -45,6 +46,18 @@ class SolveInfo(ctypes.Structure):
     def as_dict(self):
         return {"iters": self.iters, "converged": bool(self.converged), "rel_residual": self.rel_residual,
                 "seconds": self.seconds}
+
+
+INNER_BLOCKS = ("L", "AC", "A", "Kp", "X1_p", "X1_N", "X1_s", "X2_p", "X2_N", "X2_s")
+
+
+class InnerStats(ctypes.Structure):
+    _fields_ = [("solves", ctypes.c_longlong * 10), ("cycles", ctypes.c_longlong * 10),
+                ("last_rel_residual", ctypes.c_double * 10)]
+
+    def as_dict(self):
+        return {name: {"solves": self.solves[i], "cycles": self.cycles[i],
+                       "last_rel_residual": self.last_rel_residual[i]} for i, name in enumerate(INNER_BLOCKS)}
 
 
 class Profile(ctypes.Structure):
@@ -108,6 +121,7 @@ EXPORTS = {
                                        ctypes.c_void_p]),
     "chnss_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
+    "chnss_inner_stats_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(InnerStats)]),
     "chnss_step_batched": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(State),
                                           ctypes.POINTER(State), ctypes.POINTER(SolveInfo), ctypes.c_int]),
     "chnss_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Tuning)]),
@@ -144,7 +158,8 @@ def _check(status, ctx=None):
 
 
 # fields of the solvent-air sub-model, defaulted when a parameter set omits them
-_OPTIONAL = {"model": 0, "chi_sa": 0.0, "n_s": 1.0, "n_a": 1.0, "phi_sat_s": 1e-6, "phi_sat_a": 1.0}
+_OPTIONAL = {"model": 0, "chi_sa": 0.0, "n_s": 1.0, "n_a": 1.0, "phi_sat_s": 1e-6, "phi_sat_a": 1.0,
+             "inner_rtol": 0.0, "inner_maxit": 20}
 
 
 def make_params(d: dict) -> Params:
@@ -349,6 +364,13 @@ class Context:
         p = Profile()
         _check(load().chnss_profile_read(self._h, ctypes.byref(p)), self._h)
         return p.as_dict()
+
+    def inner_stats(self, reset: bool = False) -> dict:
+        """Per multigrid block of the preconditioners: inner solves, V-cycles
+        and the last relative residual (inner_rtol > 0)."""
+        st = InnerStats()
+        _check(load().chnss_inner_stats_read(self._h, 1 if reset else 0, ctypes.byref(st)), self._h)
+        return st.as_dict()
 
     def export_rhs(self, sys: int):
         out = np.zeros(self.system_size(sys), dtype=np.float64)

@@ -150,6 +150,7 @@ struct chnss_ctx {
   // captured preconditioner graphs (0..2 CH species, 3 AC, 4 NS)
   double **slots = nullptr;   // device [2 * kNumPrec] input / output pointers
   cudaStream_t cap = nullptr; // private stream used for capture only
+  cudaStream_t bodyq = nullptr;  // captures the bodies of the inner multigrid loops
   // side branches of the preconditioner graphs (independent parts of one
   // preconditioner run as parallel graph branches): streams and the
   // fork / join events
@@ -193,6 +194,7 @@ struct chnss_ctx {
       }
     }
     if (cap) cudaStreamDestroy(cap);
+    if (bodyq) cudaStreamDestroy(bodyq);
     for (cudaStream_t q : side)
       if (q) cudaStreamDestroy(q);
     if (ev_fork) cudaEventDestroy(ev_fork);
@@ -235,7 +237,7 @@ void ch_precond(chnss_ctx *c, PrecSet<T> &P, int sp, double **slot, cudaStream_t
   double *const *out = slot + 1;
   vec_convert_from_slot<double, T>(N1, in, 0, P.L.input(), s);
   P.L.apply(s);
-  vec_convert_to_slot<T, double>(N1, P.L.output(), out, 0, s);
+  P.L.write_output(out, 0, s);
   // S~^-1 = X2^-1 M X1^-1 (matching factors of eqn::schurCH)
   MGHier<T> &X1 = P.X1[sp];
   MGHier<T> &X2 = c->p.mobility_kind == 0 ? P.X1[sp] : P.X2[sp];
@@ -244,7 +246,7 @@ void ch_precond(chnss_ctx *c, PrecSet<T> &P, int sp, double **slot, cudaStream_t
   SpmvArgs none;
   spmv_sell<T>(c->lv(0).p1, P.Mv, 1, X1.output(), X2.input(), SPMV_PLAIN, none, s);
   X2.apply(s);
-  vec_convert_to_slot<T, double>(N1, X2.output(), out, N1, s);
+  X2.write_output(out, N1, s);
 }
 
 // The three species' preconditioners in one pass (slots kBatchSlot..+5):
@@ -290,7 +292,7 @@ template <typename T>
 void ac_precond(chnss_ctx *c, PrecSet<T> &P, double **slot, cudaStream_t s) {
   vec_convert_from_slot<double, T>(c->N1, const_cast<const double *const *>(slot), 0, P.AC.input(), s);
   P.AC.apply(s);
-  vec_convert_to_slot<T, double>(c->N1, P.AC.output(), slot + 1, 0, s);
+  P.AC.write_output(slot + 1, 0, s);
 }
 
 template <typename T>
@@ -323,7 +325,7 @@ void ns_precond(chnss_ctx *c, PrecSet<T> &P, double **slot, cudaStream_t s) {
   // velocity block on s
   vec_convert_from_slot<double, T>(nv, in, 0, P.A.input(), s);
   P.A.apply(s);
-  vec_convert_to_slot<T, double>(nv, P.A.output(), out, 0, s);
+  P.A.write_output(out, 0, s);
   join_side(c, s, 0);
 }
 
@@ -532,9 +534,17 @@ void init_precset(chnss_ctx *c, PrecSet<T> &P) {
   P.mb = ar.alloc<T>(N1);
   for (MGHier<T> *h : {&P.L, &P.AC, &P.A, &P.Kp, &P.X1[0], &P.X1[1], &P.X1[2], &P.X2[0], &P.X2[1], &P.X2[2]})
     h->prof = &c->prof;
+  // inner multigrid solves to a tolerance (Sec. 5) in every block that the
+  // paper gives to AMG; M_p^-1 stays the fixed Chebyshev iteration
+  if (c->p.inner_rtol > 0.0) {
+    for (MGHier<T> *h : {&P.L, &P.AC, &P.A, &P.Kp, &P.X1[0], &P.X1[1], &P.X1[2]})
+      h->enable_inner(ar, c->p.inner_rtol, c->p.inner_maxit, c->bodyq);
+    if (c->p.mobility_kind != 0)
+      for (int sp = 0; sp < 3; ++sp) P.X2[sp].enable_inner(ar, c->p.inner_rtol, c->p.inner_maxit, c->bodyq);
+  }
   P.Kp.setup(c->s);
   for (int sp = 0; sp < 3; ++sp) P.X1[sp].setup(c->s);
-  if (c->p.model == 0) {
+  if (c->p.model == 0 && c->p.inner_rtol == 0.0) {
     // species with equal (gamma, beta) have bitwise equal X1 = tau gamma K + sqrt(tau gamma / beta) M
     // (the variable-mobility factors X2 stay per species)
     P.LB.init(ar, &P.L, 3);
@@ -694,6 +704,7 @@ void create_context(chnss_ctx *c) {
   c->tmp_ns = ar.alloc<double>(c->N1);
   for (cudaStream_t &q : c->sx) CHNSS_CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
   for (cudaStream_t &q : c->side) CHNSS_CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+  CHNSS_CK(cudaStreamCreateWithFlags(&c->bodyq, cudaStreamNonBlocking));
   CHNSS_CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   for (cudaEvent_t &e : c->ev_join) CHNSS_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   CHNSS_CK(cudaEventCreateWithFlags(&c->ev_asm, cudaEventDisableTiming));
@@ -996,6 +1007,9 @@ void check_params(const chnss_params *p) {
   if (p->model == 1 && !(p->n_s > 0 && p->n_a > 0 && p->phi_sat_s > 0 && p->phi_sat_a > 0))
     throw Error{CHNSS_ERR_ARG, "model 1 needs n_s, n_a, phi_sat_s, phi_sat_a > 0"};
   if (p->mobility_kind != 0 && p->mobility_kind != 1) throw Error{CHNSS_ERR_ARG, "mobility_kind must be 0 or 1"};
+  if (!(p->inner_rtol >= 0.0 && p->inner_rtol < 1.0)) throw Error{CHNSS_ERR_ARG, "inner_rtol must be in [0, 1)"};
+  if (p->inner_rtol > 0.0 && (p->inner_maxit < 1 || p->inner_maxit > 1000))
+    throw Error{CHNSS_ERR_ARG, "inner_maxit must be in [1, 1000]"};
   if (!(p->rtol >= 0) || !(p->atol >= 0)) throw Error{CHNSS_ERR_ARG, "tolerances must be >= 0"};
 }
 
@@ -1251,6 +1265,22 @@ chnss_status chnss_profile_read(chnss_ctx_t ctx, chnss_profile *out) {
     out->kind_bytes[k] = ctx->prof.rec[k].bytes;
     out->kind_flops[k] = ctx->prof.rec[k].flops;
   }
+  return CHNSS_OK;
+  ABI_CATCH(ctx)
+}
+
+chnss_status chnss_inner_stats_read(chnss_ctx_t ctx, int reset, chnss_inner_stats *out) {
+  if (!ctx || !out) return fail(ctx, CHNSS_ERR_ARG, "null argument");
+  ABI_TRY
+  std::memset(out, 0, sizeof(*out));
+  auto read = [&](auto &P) {
+    using H = std::remove_reference_t<decltype(P.L)>;
+    H *hs[CHNSS_INNER_BLOCKS] = {&P.L, &P.AC, &P.A, &P.Kp, &P.X1[0], &P.X1[1], &P.X1[2], &P.X2[0], &P.X2[1], &P.X2[2]};
+    for (int i = 0; i < CHNSS_INNER_BLOCKS; ++i)
+      hs[i]->inner_stats(reset != 0, &out->solves[i], &out->cycles[i], &out->last_rel_residual[i], ctx->s);
+  };
+  if (ctx->p32) read(*ctx->p32);
+  else read(*ctx->p64);
   return CHNSS_OK;
   ABI_CATCH(ctx)
 }

@@ -232,6 +232,7 @@ void MGHier<T>::setup(cudaStream_t s) {
   for (int l = 0; l < nl; ++l) {
     if (bf16) sell_gather<__nv_bfloat16>(pat[l]->sell, kind == 0 ? 1 : 4, val64[l], val16[l], s);
     else sell_gather<T>(pat[l]->sell, kind == 0 ? 1 : 4, val64[l], val[l], s);
+    if (l == 0 && val0_64) sell_gather<double>(pat[0]->sell, kind == 0 ? 1 : 4, val64[0], val0_64, s);
     if (l == nl - 1) break;
     if (kind == 0)
       jacobi_csr<T>(*pat[l], val64[l], diag[l], dinv[l], hi[l], partial, s);
@@ -333,16 +334,188 @@ void MGHier<T>::vcycle(int l, cudaStream_t s) {
 }
 
 template <typename T>
-void MGHier<T>::apply(cudaStream_t s) {
+void MGHier<T>::cycle(cudaStream_t s) {
+  double *pb = ipartial ? ipartial : partial;
   if (singular) {
-    vsum<T>(n[0], b[0], sum, partial, s);
+    vsum<T>(n[0], b[0], sum, pb, s);
     vec_sub_mean<T>((int)n[0], b[0], sum, s);
   }
   vcycle(0, s);
   if (singular) {
-    vsum<T>(n[0], x[0], sum, partial, s);
+    vsum<T>(n[0], x[0], sum, pb, s);
     vec_sub_mean<T>((int)n[0], x[0], sum, s);
   }
+}
+
+template <typename T>
+void MGHier<T>::apply(cudaStream_t s) {
+  if (inner_rtol > 0.0) solve(s);
+  else cycle(s);
+}
+
+namespace {
+
+constexpr int kAccTPB = 256;
+
+template <typename T>
+__global__ void k_acc(long n, const T *x, double *y) {
+  const long i = (long)blockIdx.x * kAccTPB + threadIdx.x;
+  if (i < n) y[i] += (double)x[i];
+}
+
+// continue while ||r||^2 > rtol^2 ||b||^2 (and finite) and fewer than maxit
+// V-cycles have run; first = 1 after the first V-cycle (sets the count)
+__global__ void k_inner_check(cudaGraphConditionalHandle h, double *ctl, int *it, double rtol2, int maxit,
+                              int first) {
+  const int k = first ? 1 : *it + 1;
+  *it = k;
+  ctl[2] = (double)k;
+  const double nr2 = ctl[1];
+  const bool more = isfinite(nr2) && nr2 > rtol2 * ctl[0] && k < maxit;
+  if (!more) {
+    ctl[3] += (double)k;
+    ctl[4] += 1.0;
+  }
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+__global__ void k_inner_tally(double *ctl, int k) {
+  ctl[2] = (double)k;
+  ctl[3] += (double)k;
+  ctl[4] += 1.0;
+}
+
+}  // namespace
+
+template <typename T>
+void MGHier<T>::enable_inner(Arena &ar, double rtol, int maxit, cudaStream_t body_stream) {
+  if (!(rtol > 0.0)) return;
+  inner_rtol = rtol;
+  inner_maxit = maxit;
+  bodyq = body_stream;
+  bsave = ar.alloc<double>(n[0]);
+  acc = ar.alloc<double>(n[0]);
+  if (!std::is_same<T, double>::value) {
+    r64 = ar.alloc<double>(n[0]);
+    val0_64 = ar.alloc<double>((kind == 0 ? 1L : 4L) * pat[0]->sell.nent);
+  }
+  ictl = ar.alloc<double>(8);
+  iit = ar.alloc<int>(1);
+  ipartial = ar.alloc<double>(64L * 1216);
+  CHNSS_CK(cudaMemset(ictl, 0, 8 * sizeof(double)));
+  CHNSS_CK(cudaMemset(iit, 0, sizeof(int)));
+}
+
+template <typename T>
+void MGHier<T>::write_output(double *const *slot, long off, cudaStream_t s) {
+  if (inner_rtol > 0.0) vec_convert_to_slot<double, double>(n[0], acc, slot, off, s);
+  else vec_convert_to_slot<T, double>(n[0], x[0], slot, off, s);
+}
+
+template <typename T>
+void MGHier<T>::inner_stats(bool reset, long long *solves, long long *cycles, double *last_rel, cudaStream_t s) {
+  *solves = 0;
+  *cycles = 0;
+  *last_rel = 0.0;
+  if (!ictl) return;
+  double h[5];
+  CHNSS_CK(cudaMemcpyAsync(h, ictl, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CHNSS_CK(cudaStreamSynchronize(s));
+  *solves = (long long)h[4];
+  *cycles = (long long)h[3];
+  *last_rel = h[0] > 0.0 ? std::sqrt(h[1] / h[0]) : 0.0;
+  if (reset) {
+    CHNSS_CK(cudaMemsetAsync(ictl + 3, 0, 2 * sizeof(double), s));
+    CHNSS_CK(cudaStreamSynchronize(s));
+  }
+}
+
+template <typename T>
+void MGHier<T>::inner_residual(cudaStream_t s) {
+  SpmvArgs a;
+  a.b = bsave;
+  if constexpr (std::is_same<T, double>::value) {
+    op(0, acc, b[0], SPMV_RES, a, s);
+    dot<double>(n[0], b[0], b[0], ictl + 1, ipartial, s);
+  } else {
+    if (kind == 0) spmv_sell<double>(*pat[0], val0_64, 1, acc, r64, SPMV_RES, a, s);
+    else spmv_sell_bsr2<double>(*pat[0], val0_64, acc, r64, SPMV_RES, a, s);
+    dot<double>(n[0], r64, r64, ictl + 1, ipartial, s);
+    vec_convert<double, T>(n[0], r64, b[0], s);
+  }
+}
+
+template <typename T>
+void MGHier<T>::solve(cudaStream_t s) {
+  const long n0 = n[0];
+  if (singular) {
+    vsum<T>(n0, b[0], sum, ipartial, s);
+    vec_sub_mean<T>((int)n0, b[0], sum, s);
+  }
+  vec_convert<T, double>(n0, b[0], bsave, s);
+  dot<double>(n0, bsave, bsave, ictl, ipartial, s);
+  cycle(s);
+  vec_convert<T, double>(n0, x[0], acc, s);
+  inner_residual(s);
+  const double rtol2 = inner_rtol * inner_rtol;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CHNSS_CK(cudaStreamIsCapturing(s, &cs));
+  if (cs == cudaStreamCaptureStatusActive) {
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edata = nullptr;
+    size_t nd = 0;
+    CHNSS_CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    cudaGraphConditionalHandle h;
+    CHNSS_CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    k_inner_check<<<1, 1, 0, s>>>(h, ictl, iit, rtol2, inner_maxit, 1);
+    CHNSS_LAUNCH_CK();
+    CHNSS_CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edata, &nd));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    CHNSS_CK(cudaGraphAddNode(&node, g, deps, edata, nd, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CHNSS_CK(cudaStreamBeginCaptureToGraph(bodyq, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    Profiler *pf = prof;
+    prof = nullptr;   // event-record nodes are not allowed in a conditional body
+    try {
+      cycle(bodyq);
+      k_acc<T><<<(unsigned)((n0 + kAccTPB - 1) / kAccTPB), kAccTPB, 0, bodyq>>>(n0, x[0], acc);
+      CHNSS_LAUNCH_CK();
+      inner_residual(bodyq);
+      k_inner_check<<<1, 1, 0, bodyq>>>(h, ictl, iit, rtol2, inner_maxit, 0);
+      CHNSS_LAUNCH_CK();
+    } catch (...) {
+      prof = pf;
+      cudaGraph_t tmp = nullptr;
+      cudaStreamEndCapture(bodyq, &tmp);
+      throw;
+    }
+    prof = pf;
+    cudaGraph_t tmp = nullptr;
+    CHNSS_CK(cudaStreamEndCapture(bodyq, &tmp));
+    CHNSS_CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  } else {
+    double h2[2];
+    int k = 1;
+    for (;;) {
+      CHNSS_CK(cudaMemcpyAsync(h2, ictl, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CHNSS_CK(cudaStreamSynchronize(s));
+      if (!(std::isfinite(h2[1]) && h2[1] > rtol2 * h2[0] && k < inner_maxit)) break;
+      cycle(s);
+      k_acc<T><<<(unsigned)((n0 + kAccTPB - 1) / kAccTPB), kAccTPB, 0, s>>>(n0, x[0], acc);
+      CHNSS_LAUNCH_CK();
+      inner_residual(s);
+      ++k;
+    }
+    k_inner_tally<<<1, 1, 0, s>>>(ictl, k);
+    CHNSS_LAUNCH_CK();
+  }
+  vec_convert<double, T>(n0, acc, x[0], s);
 }
 
 template struct MGHier<double>;

@@ -90,7 +90,30 @@ struct MGHier {
   void setup(cudaStream_t s);
   T *input() { return b[0]; }
   T *output() { return x[0]; }
-  void apply(cudaStream_t s);   // x[0] = V-cycle(b[0])
+  // x[0] = V-cycle(b[0]); with inner_rtol > 0, x[0] = solve(b[0]) instead
+  void apply(cudaStream_t s);
+  // Multigrid as an inner solver with a tolerance (Sec. 5 applies its AMG
+  // preconditioners to a relative tolerance): x <- x + V(b - A x) from x = 0
+  // until ||b - A x|| <= inner_rtol ||b|| or inner_maxit V-cycles.  The
+  // iterate, the right-hand side and the residual are FP64 whatever T is
+  // (FP64 level-0 values): an FP32 residual of smooth iterates cancels down
+  // to a floor of ~1e-4 relative on 1024^2 meshes, so the FP32 / BF16
+  // hierarchies do mixed-precision iterative refinement (V-cycles in T,
+  // residuals in FP64).  Under stream capture the loop is a conditional
+  // WHILE node whose condition a one-thread kernel sets from the device
+  // residual norm, so the captured preconditioner graph needs no host
+  // synchronisation; otherwise the host reads the norms.  b[0] is
+  // overwritten (it ends as the last residual).
+  double inner_rtol = 0.0;
+  int inner_maxit = 1;
+  void enable_inner(Arena &ar, double rtol, int maxit, cudaStream_t body_stream);
+  // the result as FP64 into *slot + off: the FP64 iterate of an inner
+  // solve (an FP32 rounding of it would cap the preconditioner's accuracy),
+  // else x[0] converted
+  void write_output(double *const *slot, long off, cudaStream_t s);
+  // inner solves and V-cycles since the last reset, residual ratio of the
+  // last solve (stream-ordered read on s, then a synchronisation)
+  void inner_stats(bool reset, long long *solves, long long *cycles, double *last_rel, cudaStream_t s);
   // descriptor of levels tail_l0.. with the given vectors (device copy)
   TailDesc<T> *make_tail(Arena &ar, const std::vector<MultiPtr<T>> &X, const std::vector<MultiPtr<T>> &Tt,
                          const std::vector<MultiPtr<T>> &Rr, const std::vector<MultiPtr<T>> &B) const;
@@ -98,8 +121,17 @@ struct MGHier {
   void spmv_level(int l, const T *u, T *out, SpmvMode mode, const SpmvArgs &a, cudaStream_t s);
 
  private:
+  double *bsave = nullptr, *acc = nullptr;   // inner solve: right-hand side, iterate (FP64)
+  double *r64 = nullptr, *val0_64 = nullptr;  // T != double: FP64 residual, level-0 FP64 SELL values
+  // [0] ||b||^2 [1] ||r||^2 [2] V-cycles of the last solve [3] V-cycles [4] solves since reset
+  double *ictl = nullptr, *ipartial = nullptr;
+  int *iit = nullptr;
+  cudaStream_t bodyq = nullptr;               // captures the WHILE body
   void op(int l, const T *u, T *out, SpmvMode mode, const SpmvArgs &a, cudaStream_t s);
   void vcycle(int l, cudaStream_t s);
+  void cycle(cudaStream_t s);                 // one V-cycle with the singular projections
+  void inner_residual(cudaStream_t s);        // b[0] = bsave - A acc (FP64); ictl[1] = ||b - A acc||^2
+  void solve(cudaStream_t s);
 };
 
 // The same V-cycle as MGHier<T> (kind 0: scalar P1 operators, non-singular)
