@@ -702,7 +702,14 @@ void create_context(chnss_ctx *c) {
   c->kwc0.init(ar, p.restart, 2L * c->N1, c->pinned + 24);
   c->kwa.init(ar, p.restart, c->N1, c->pinned + 28);
   c->tmp_ns = ar.alloc<double>(c->N1);
-  for (cudaStream_t &q : c->sx) CHNSS_CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+  // The Oseen group is the step's critical path (about three quarters of
+  // the serial step's solve time); its stream gets the highest priority so
+  // that the CH and AC groups fill the gaps it leaves (latency-bound coarse
+  // levels, FP64-ALU-bound orthogonalisation, host round trips).
+  int prio_low = 0, prio_high = 0;
+  CHNSS_CK(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+  for (int w = 0; w < 3; ++w)
+    CHNSS_CK(cudaStreamCreateWithPriority(&c->sx[w], cudaStreamNonBlocking, w == 2 ? prio_high : prio_low));
   for (cudaStream_t &q : c->side) CHNSS_CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
   CHNSS_CK(cudaStreamCreateWithFlags(&c->bodyq, cudaStreamNonBlocking));
   CHNSS_CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));

@@ -95,6 +95,14 @@ struct Sell {
   int *col = nullptr;            // [nent] column (padding: a valid column, value 0)
   int *map = nullptr;            // [nent] CSR position, -1 = padding
   int *mapT = nullptr;           // [nent] CSR position of the transposed entry (square symmetric patterns)
+  // Stencil layout (P1 patterns of the structured meshes): rows in natural
+  // order, every slice 7 wide, slot j of row i holds column i + soff[j]
+  // (ascending, so the CSR order) or a zero where that neighbour is not
+  // coupled; kernels that know the layout compute the columns instead of
+  // loading col / rowid.  The explicit arrays above stay valid for every
+  // other SELL kernel.
+  int stencil = 0;
+  int soff[7] = {0, 0, 0, 0, 0, 0, 0};
 };
 
 struct Pattern {

@@ -194,6 +194,55 @@ void build_sell(Arena &ar, Pattern &P, std::vector<int> *hmap = nullptr) {
   if (hmap) *hmap = std::move(map);
 }
 
+// Stencil layout of a P1 pattern on an nx-by-nx node lattice (nx = n + 1)
+// whose triangles are split along the lower-left -> upper-right diagonal:
+// row i couples at most to i + {-nx-1, -nx, -1, 0, 1, nx, nx+1}.  Returns
+// false (building nothing) if some row has another column.
+bool build_sell_stencil(Arena &ar, Pattern &P, int nx) {
+  const int C = Sell::C, W = 7, n = P.nrows;
+  const int off[W] = {-nx - 1, -nx, -1, 0, 1, nx, nx + 1};
+  if (P.ncols != n || (long)nx * nx != n) return false;
+  auto find = [&](int row, int c) -> int {
+    if (c < 0 || c >= n) return -1;
+    const int *b = P.h_col.data() + P.h_rowptr[row], *e = P.h_col.data() + P.h_rowptr[row + 1];
+    const int *it = std::lower_bound(b, e, c);
+    return (it != e && *it == c) ? (int)(it - P.h_col.data()) : -1;
+  };
+  for (int row = 0; row < n; ++row) {
+    int hit = 0;
+    for (int j = 0; j < W; ++j) hit += find(row, row + off[j]) >= 0 ? 1 : 0;
+    if (hit != P.h_rowptr[row + 1] - P.h_rowptr[row]) return false;
+  }
+  Sell &s = P.sell;
+  s.nslices = (n + C - 1) / C;
+  s.wmax = W;
+  s.nent = (long)s.nslices * W * C;
+  std::vector<int> sp(s.nslices + 1), rowid((size_t)s.nslices * C, -1), col(s.nent), map(s.nent), mapT(s.nent, -1);
+  for (int k = 0; k <= s.nslices; ++k) sp[k] = k * W * C;
+  for (int k = 0; k < s.nslices; ++k)
+    for (int r = 0; r < C; ++r) {
+      const int row = k * C + r;
+      if (row < n) rowid[(size_t)k * C + r] = row;
+      for (int j = 0; j < W; ++j) {
+        const long e = sp[k] + (long)j * C + r;
+        const int q = row < n ? find(row, row + off[j]) : -1;
+        col[e] = q >= 0 ? row + off[j] : (row < n ? row : 0);   // missing: own diagonal, value 0
+        map[e] = q;
+        if (q >= 0) mapT[e] = find(row + off[j], row);
+      }
+    }
+  for (long e = 0; e < s.nent; ++e)
+    if (map[e] >= 0 && mapT[e] < 0) throw Error{CHNSS_ERR_ARG, "stencil layout: unsymmetric P1 pattern"};
+  s.slice_ptr = ar.upload(sp);
+  s.rowid = ar.upload(rowid);
+  s.col = ar.upload(col);
+  s.map = ar.upload(map);
+  s.mapT = ar.upload(mapT);
+  s.stencil = 1;
+  for (int j = 0; j < W; ++j) s.soff[j] = off[j];
+  return true;
+}
+
 void upload_pattern(Arena &ar, Pattern &P, std::vector<int> *hmap = nullptr) {
   P.rowptr = ar.upload(P.h_rowptr);
   P.col = ar.upload(P.h_col);
@@ -350,7 +399,9 @@ void build_mesh(Mesh &m, int n, double lx, double ly, int top_bc) {
     auto p2pair = [&](int e, int *r, int *c) { int v1[3]; element_nodes(nl, e, v1, r); std::memcpy(c, r, 6 * sizeof(int)); };
     pattern_from_elements(L.N1, L.N1, L.E, 3, 3, p1pair, L.p1);
     pattern_from_elements(L.N2, L.N2, L.E, 6, 6, p2pair, L.p2);
-    upload_pattern(ar, L.p1);
+    L.p1.rowptr = ar.upload(L.p1.h_rowptr);
+    L.p1.col = ar.upload(L.p1.h_col);
+    if (!build_sell_stencil(ar, L.p1, nl + 1)) build_sell(ar, L.p1);
     upload_pattern(ar, L.p2);
     gather_from_elements(L.p1, L.E, 3, 3, p1pair, [](int e, int a, int b) { return e * 9 + a * 3 + b; },
                          [](int, int, int, int, int) { return true; }, L.g_p1, hptr, hidx);

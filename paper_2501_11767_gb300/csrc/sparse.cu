@@ -311,6 +311,49 @@ __global__ void __launch_bounds__(kSellMaxBlock) k_sell_w8(int nslices, const in
   out[row] = r;
 }
 
+struct StencilOff {
+  int o[7];
+};
+
+// P1 rows in the stencil layout (Sell::stencil): the same slots, values and
+// per-row summation order as k_sell_w8 on that layout, with the columns
+// computed from the row instead of loaded (no col / rowid traffic, one
+// dependent memory round trip instead of two).  Missing neighbours hold a
+// zero value; their column is clamped into range.
+template <typename T, typename VT>
+__global__ void __launch_bounds__(kSellMaxBlock) k_stencil7(int nrows, StencilOff so, const VT *__restrict__ val,
+                                                   const T *__restrict__ u, T *out, int mode, SpmvArgs a) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nrows) return;
+  const long base = (long)(row >> 5) * (7 * 32) + (row & 31);
+  const T *wv = static_cast<const T *>(a.w);
+  T bi = 0, di = 0, ui = 0, wi = 0, oi = 0;
+  if (mode == SPMV_RES || mode == SPMV_CHEB) bi = static_cast<const T *>(a.b)[row];
+  if (mode == SPMV_CHEB) {
+    di = static_cast<const T *>(a.dinv)[row];
+    ui = u[row];
+    if (wv) wi = wv[row];
+  }
+  if (mode == SPMV_ADD) oi = out[row];
+  T v[7];
+  int c[7];
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    v[j] = ldv(val + base + j * 32);
+    const int cj = row + so.o[j];
+    c[j] = cj < 0 ? 0 : (cj >= nrows ? nrows - 1 : cj);
+  }
+  T acc = 0;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) acc += v[j] * u[c[j]];
+  T r;
+  if (mode == SPMV_PLAIN) r = acc;
+  else if (mode == SPMV_RES) r = bi - acc;
+  else if (mode == SPMV_ADD) r = oi + acc;
+  else r = cheb_row<T>(a.coef, ui, di, bi, acc, wv != nullptr, wi);
+  out[row] = r;
+}
+
 template <typename T, typename VT, bool VEC>
 __global__ void __launch_bounds__(kSellMaxBlock) k_sell_bsr2(int nslices, const int *__restrict__ sp,
                                                    const int *__restrict__ rowid, const int *__restrict__ col,
@@ -867,6 +910,54 @@ __device__ __forceinline__ void sell_w8m_slice(int slice, int lane, const int *s
   }
 }
 
+// Multi-vector form of k_stencil7: per vector the same expressions as
+// sell_w8m_slice on the stencil layout.
+template <typename T, int NR>
+__global__ void __launch_bounds__(kSellMaxBlock) k_stencil7m(int nrows, StencilOff so, const T *__restrict__ val,
+                                                    MultiPtr<T> u, MultiPtr<T> out, int mode, MultiArgs<T> a) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nrows) return;
+  const long base = (long)(row >> 5) * (7 * 32) + (row & 31);
+  T bi[NR], ui[NR], wi[NR], oi[NR];
+  T di = 0;
+#pragma unroll
+  for (int k = 0; k < NR; ++k) bi[k] = ui[k] = wi[k] = oi[k] = 0;
+  if (mode == SPMV_CHEB) di = a.dinv[row];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    if (mode == SPMV_RES || mode == SPMV_CHEB) bi[k] = a.b.p[k][row];
+    if (mode == SPMV_CHEB) {
+      ui[k] = u.p[k][row];
+      if (a.w.p[k]) wi[k] = a.w.p[k][row];
+    }
+    if (mode == SPMV_ADD) oi[k] = out.p[k][row];
+  }
+  T v[7];
+  int c[7];
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    v[j] = val[base + j * 32];
+    const int cj = row + so.o[j];
+    c[j] = cj < 0 ? 0 : (cj >= nrows ? nrows - 1 : cj);
+  }
+  T acc[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    acc[k] = 0;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) acc[k] += v[j] * u.p[k][c[j]];
+  }
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    T r;
+    if (mode == SPMV_PLAIN) r = acc[k];
+    else if (mode == SPMV_RES) r = bi[k] - acc[k];
+    else if (mode == SPMV_ADD) r = oi[k] + acc[k];
+    else r = cheb_row<T>(a.coef, ui[k], di, bi[k], acc[k], a.w.p[k] != nullptr, wi[k]);
+    out.p[k][row] = r;
+  }
+}
+
 template <typename T, int NR>
 __global__ void __launch_bounds__(kSellMaxBlock) k_sell_w8m(int nslices, const int *__restrict__ sp,
                                                    const int *__restrict__ rowid, const int *__restrict__ col,
@@ -1164,7 +1255,11 @@ void spmv_sell_impl(const Pattern &P, const VT *sval, int ncomp, const T *u, T *
   const Sell &S = P.sell;
   if (S.nslices == 0) return;
   const int nb = nblocks((long)S.nslices * 32, S.block);
-  if (ncomp == 1 && S.wmax <= 8)
+  if (ncomp == 1 && S.stencil) {
+    StencilOff so;
+    for (int j = 0; j < 7; ++j) so.o[j] = S.soff[j];
+    k_stencil7<T, VT><<<nblocks(P.nrows, S.block), S.block, 0, s>>>(P.nrows, so, sval, u, out, mode, a);
+  } else if (ncomp == 1 && S.wmax <= 8)
     k_sell_w8<T, VT><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
   else if (ncomp == 1)
     k_sell<T, VT, 1, false><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
@@ -1574,6 +1669,19 @@ void spmv_sell_multi(const Pattern &P, const T *sval, int nr, const MultiPtr<T> 
   if (S.nslices == 0) return;
   if (S.wmax > 8) throw Error{CHNSS_ERR_ARG, "multi-vector SpMV needs rows of at most 8 entries"};
   const int nb = nblocks((long)S.nslices * 32, S.block);
+  if (S.stencil) {
+    StencilOff so;
+    for (int j = 0; j < 7; ++j) so.o[j] = S.soff[j];
+    const int nbs = nblocks(P.nrows, S.block);
+    switch (nr) {
+      case 1: k_stencil7m<T, 1><<<nbs, S.block, 0, s>>>(P.nrows, so, sval, u, out, mode, a); break;
+      case 2: k_stencil7m<T, 2><<<nbs, S.block, 0, s>>>(P.nrows, so, sval, u, out, mode, a); break;
+      case 3: k_stencil7m<T, 3><<<nbs, S.block, 0, s>>>(P.nrows, so, sval, u, out, mode, a); break;
+      default: throw Error{CHNSS_ERR_ARG, "multi-vector SpMV: 1 to 3 vectors"};
+    }
+    CHNSS_LAUNCH_CK();
+    return;
+  }
   switch (nr) {
     case 1: k_sell_w8m<T, 1><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a); break;
     case 2: k_sell_w8m<T, 2><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a); break;
