@@ -107,13 +107,17 @@ namespace {
 // algorithmic bytes of one SpMV launch: values + column indices + row
 // pointers + one read of u, one write of out, plus the extra vector streams
 // of the epilogue (b for RES, b + dinv (+ w) for CHEB, out read for ADD)
+// Algorithmic bytes of one sweep: every stored nonzero once (value, plus a
+// 4-byte column and the row pointers unless the stencil layout implies
+// them), the input and output vectors once, and the epilogue's vectors.
 double spmv_bytes(long nrows, long nnz, int vals_per_entry, long vec_len, size_t sv, size_t s, SpmvMode mode,
-                  bool has_w) {
+                  bool has_w, bool implicit_index) {
   double extra = 0.0;
   if (mode == SPMV_RES) extra = 1.0;
   if (mode == SPMV_ADD) extra = 1.0;
   if (mode == SPMV_CHEB) extra = has_w ? 3.0 : 2.0;
-  return (double)nnz * (vals_per_entry * (double)sv + 4.0) + 4.0 * (nrows + 1) + (2.0 + extra) * vec_len * s;
+  const double index = implicit_index ? 0.0 : (double)nnz * 4.0 + 4.0 * (nrows + 1);
+  return (double)nnz * vals_per_entry * (double)sv + index + (2.0 + extra) * vec_len * s;
 }
 }  // namespace
 
@@ -256,7 +260,7 @@ void MGHier<T>::op(int l, const T *u, T *out, SpmvMode mode, const SpmvArgs &a, 
   spmv_level(l, u, out, mode, a, s);
   if (timed)
     prof->stop(k, tk, s, spmv_bytes(pat[l]->nrows, pat[l]->nnz, kind == 0 ? 1 : 4, n[l], bf16 ? 2 : sizeof(T), sizeof(T),
-                                mode, a.w != nullptr));
+                                mode, a.w != nullptr, pat[l]->sell.stencil != 0));
 }
 
 template <typename T>
