@@ -93,6 +93,9 @@ typedef struct {
                             matching factors X, MG of the AC matrix, the velocity block and
                             K_p; the CH species are then solved one after the other */
   int inner_maxit;       /* cap on the V-cycles of one inner solve (1..1000, inner_rtol > 0) */
+  double ns_rtol, ns_atol;  /* ns_rtol > 0: stopping rule of the Oseen solve alone (Sec. 5 uses
+                               rtol 1e-4, atol 1e-8 for it and 1e-6, 1e-8 for CH and AC);
+                               0: the Oseen solve uses rtol, atol */
 } chnss_params;
 
 /* Fields of one time level (DEVICE pointers, caller-owned, FP64). */

@@ -210,7 +210,9 @@ class Oracle:
             x = x[:-1]
         else:
             prec = self.ns_preconditioner(A, Ap, lstates)
-            x, info = fgmres(self.ns_operator(A, B), prec, rhs, p["rtol"], p["atol"], p["restart"], p["maxit"])
+            # Sec. 5 stops the Oseen solve at tolerances of its own (ns_rtol > 0)
+            rt, at = (p["ns_rtol"], p["ns_atol"]) if p.get("ns_rtol", 0.0) > 0 else (p["rtol"], p["atol"])
+            x, info = fgmres(self.ns_operator(A, B), prec, rhs, rt, at, p["restart"], p["maxit"])
         v, pr = x[:nv], x[nv:]
         if not self.top_free:       # enclosed flow: pressure in L^2_0
             Mp = self.forms[0].M

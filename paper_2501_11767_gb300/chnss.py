@@ -31,7 +31,8 @@ class Params(ctypes.Structure):
                 ("atol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("model", ctypes.c_int), ("chi_sa", ctypes.c_double), ("n_s", ctypes.c_double),
                 ("n_a", ctypes.c_double), ("phi_sat_s", ctypes.c_double), ("phi_sat_a", ctypes.c_double),
-                ("inner_rtol", ctypes.c_double), ("inner_maxit", ctypes.c_int)]
+                ("inner_rtol", ctypes.c_double), ("inner_maxit", ctypes.c_int),
+                ("ns_rtol", ctypes.c_double), ("ns_atol", ctypes.c_double)]
 
 
 class State(ctypes.Structure):
@@ -159,7 +160,7 @@ def _check(status, ctx=None):
 
 # fields of the solvent-air sub-model, defaulted when a parameter set omits them
 _OPTIONAL = {"model": 0, "chi_sa": 0.0, "n_s": 1.0, "n_a": 1.0, "phi_sat_s": 1e-6, "phi_sat_a": 1.0,
-             "inner_rtol": 0.0, "inner_maxit": 20}
+             "inner_rtol": 0.0, "inner_maxit": 20, "ns_rtol": 0.0, "ns_atol": 0.0}
 
 
 def make_params(d: dict) -> Params:

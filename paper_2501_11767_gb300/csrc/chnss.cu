@@ -884,7 +884,10 @@ chnss_status solve_on(chnss_ctx *c, int sys, const double *rhs_or_null, double *
     st = pcg(c->lv(0).p1, c->M1[0], c->dinvM, b, x, 1e-12, 1000, kwk, info, s);
   } else if (sys == CHNSS_SYS_NS) {
     NSOp op(c);
-    st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[5], x, p.rtol, p.atol, p.maxit, kwk, info, s, &c->prof);
+    // the Oseen solve may have tolerances of its own (Sec. 5 stops it at a
+    // looser relative residual than the phase-field solves)
+    const double rt = p.ns_rtol > 0.0 ? p.ns_rtol : p.rtol, at = p.ns_rtol > 0.0 ? p.ns_atol : p.atol;
+    st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[5], x, rt, at, p.maxit, kwk, info, s, &c->prof);
     // enclosed flow: zero-mean pressure, p -= (1^T M p) / (1^T M 1); an open
     // top fixes the pressure level itself
     const Mesh &m = c->mesh->m;
@@ -1015,6 +1018,8 @@ void check_params(const chnss_params *p) {
     throw Error{CHNSS_ERR_ARG, "model 1 needs n_s, n_a, phi_sat_s, phi_sat_a > 0"};
   if (p->mobility_kind != 0 && p->mobility_kind != 1) throw Error{CHNSS_ERR_ARG, "mobility_kind must be 0 or 1"};
   if (!(p->inner_rtol >= 0.0 && p->inner_rtol < 1.0)) throw Error{CHNSS_ERR_ARG, "inner_rtol must be in [0, 1)"};
+  if (!(p->ns_rtol >= 0.0 && p->ns_rtol < 1.0) || !(p->ns_atol >= 0.0))
+    throw Error{CHNSS_ERR_ARG, "ns_rtol must be in [0, 1) and ns_atol >= 0"};
   if (p->inner_rtol > 0.0 && (p->inner_maxit < 1 || p->inner_maxit > 1000))
     throw Error{CHNSS_ERR_ARG, "inner_maxit must be in [1, 1000]"};
   if (!(p->rtol >= 0) || !(p->atol >= 0)) throw Error{CHNSS_ERR_ARG, "tolerances must be >= 0"};

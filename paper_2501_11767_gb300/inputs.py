@@ -131,6 +131,9 @@ def default_params() -> dict:
         # tolerance, at most inner_maxit (Sec. 5 uses 1e-4 for its AMG)
         "inner_rtol": 0.0,
         "inner_maxit": 20,
+        # Oseen stopping rule of its own when ns_rtol > 0 (0: rtol, atol)
+        "ns_rtol": 0.0,
+        "ns_atol": 0.0,
     }
 
 
@@ -185,6 +188,10 @@ def workload(name: str) -> dict:
         return {"n": 512, "params": p, "steps": 10}
     if name == "film1024_mixed_inner":   # the bench set with every MG block solved to 1e-4 (Sec. 5)
         p.update(beta=film_betas(0.005), tau=5e-4, precision=1, inner_rtol=1e-4, inner_maxit=20)
+        return {"n": 1024, "params": p, "steps": 10}
+    if name == "film1024_paper_solver":   # the bench film with the solver settings of Sec. 5
+        p.update(beta=film_betas(0.005), tau=5e-4, precision=1, rtol=1e-6, atol=1e-8, ns_rtol=1e-4, ns_atol=1e-8,
+                 inner_rtol=1e-4, inner_maxit=20)
         return {"n": 1024, "params": p, "steps": 10}
     if name == "film512_open_mixed":      # the bench set with an open (do-nothing) top, 512 x 512
         p.update(beta=film_betas(0.005), tau=5e-4, precision=1, top_bc=1)

@@ -165,3 +165,12 @@ def test_inner_adjoint_matches_oracle(torch):
 def test_inner_parameter_errors(torch, bad):
     with pytest.raises(chnss.ChnssError):
         chnss.Context(chnss.Mesh(8), _params(**bad))
+
+
+def test_paper_solver_settings_match_oracle(torch):
+    """Sec. 5's settings: CH / AC to rtol 1e-6 (atol 1e-8), the Oseen solve to
+    its own rtol 1e-4 (atol 1e-8), inner multigrid to 1e-4."""
+    p = _params(rtol=1e-6, atol=1e-8, ns_rtol=1e-4, ns_atol=1e-8)
+    ctx = _compare(torch, 32, p, seed=6)
+    with pytest.raises(chnss.ChnssError):
+        chnss.Context(chnss.Mesh(8), _params(ns_rtol=1.5))

@@ -149,3 +149,26 @@ def test_step_with_inner_tolerance():
     assert {"ch_p", "ac", "ns"} <= set(solves)
     for name in solves:
         assert info2[name]["iters"] <= info1[name]["iters"], name
+
+
+def test_paper_solver_settings():
+    """Sec. 5's settings: CH / AC to rtol 1e-6 (atol 1e-8), the Oseen solve to
+    rtol 1e-4 (atol 1e-8), AMG tolerance 1e-4.  Each solve stops at the first
+    iterate meeting its own rule."""
+    n = 16
+    p = inputs.default_params()
+    p.update(rtol=1e-6, atol=1e-8, ns_rtol=1e-4, ns_atol=1e-8, inner_rtol=1e-4, inner_maxit=20)
+    o = Oracle(n, p)
+    s0 = inputs.initial_state(n, seed=3)
+    s1, info = o.step(s0)
+    _, info2 = o.step(s1, keep_systems=True)[:2]
+    tight = Oracle(n, dict(p, ns_rtol=0.0, rtol=1e-8, atol=0.0))
+    _, info_t = tight.step(s1)[:2]
+    systems = info2["systems"]
+    for name, rt in (("ch_p", 1e-6), ("ch_N", 1e-6), ("ch_s", 1e-6), ("ac", 1e-6), ("ns", 1e-4)):
+        b = systems[name][-1]
+        nb = float(np.linalg.norm(b))
+        assert info2[name]["converged"], name
+        # ||b - A x|| <= max(rtol ||b||, atol), atol = 1e-8
+        assert info2[name]["rel_residual"] * nb <= max(rt * nb, 1e-8) * (1 + 1e-9), name
+    assert info2["ns"]["iters"] < info_t["ns"]["iters"]
