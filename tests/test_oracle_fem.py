@@ -317,3 +317,27 @@ def test_prolongation_reproduces_polynomials():
     assert np.allclose(inject_p1(fine.x1[:, 0], 8), coarse.x1[:, 0])
     v = np.stack([xf, yf], 1).ravel()
     assert np.allclose(inject_velocity(v, 8), np.stack([xc, yc], 1).ravel())
+
+
+@pytest.mark.parametrize("n", [2, 4, 6, 16])
+def test_p1_operators_are_seven_point_stencils(n):
+    """Every P1 operator of the step (mass, stiffness, convection with a P2
+    velocity, weighted stiffness) couples node i = j (n+1) + k only to
+    i + {-(n+2), -(n+1), -1, 0, 1, n+1, n+2} (the lower-left -> upper-right
+    diagonals of the mesh), and interior rows couple to all seven: the
+    precondition of the library's stencil layout for the P1 sweeps."""
+    m = Mesh(n)
+    nx = n + 1
+    off = {-nx - 1, -nx, -1, 0, 1, nx, nx + 1}
+    rng = np.random.default_rng(n)
+    v = rng.standard_normal(2 * m.N2)
+    kappa = lambda lam: 1.0 + np.outer(np.arange(m.E) % 3, lam[:, 0])   # (E, Q), positive
+    A = (fem.mass_p1(m) + fem.stiffness_p1(m) + fem.convection_p1(m, v)
+         + fem.weighted_stiffness_p1(m, kappa)).tocsr()
+    A.sort_indices()
+    for i in range(m.N1):
+        cols = A.indices[A.indptr[i]:A.indptr[i + 1]]
+        assert set((cols - i).tolist()) <= off, i
+        k, j = i % nx, i // nx
+        if 0 < k < n and 0 < j < n:
+            assert len(cols) == 7, i
