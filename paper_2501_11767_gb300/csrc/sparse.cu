@@ -201,6 +201,9 @@ __device__ __forceinline__ void load_blk(const double *p, double b[4]) {
   b[0] = v0.x; b[1] = v0.y; b[2] = v1.x; b[3] = v1.y;
 }
 
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
 template <typename T> __device__ __forceinline__ T from_double(double x) { return (T)x; }
 template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double x) {
   return __double2bfloat16(x);   // round to nearest even
@@ -380,8 +383,10 @@ __global__ void __launch_bounds__(kSellMaxBlock) k_sell_bsr2(int nslices, const 
       x0 = u[2L * c];
       x1 = u[2L * c + 1];
     }
-    acc0 += b[0] * x0 + b[1] * x1;
-    acc1 += b[2] * x0 + b[3] * x1;
+    // two FMAs per component (not a multiply, an FMA and an add): the FP64
+    // form of this kernel is bound by the FP64 pipe
+    acc0 = fma_t(b[1], x1, fma_t(b[0], x0, acc0));
+    acc1 = fma_t(b[3], x1, fma_t(b[2], x0, acc1));
   }
   if (row < 0) return;
   epilogue<T>(mode, 2L * row, acc0, u, out, a, a.coef);
@@ -433,9 +438,9 @@ __global__ void __launch_bounds__(kSellMaxBlock) k_sell_b(int nslices, const int
     const int c = col[e];
     if (VEC) {
       const double2 x = v2[c];
-      acc += b.x * x.x + b.y * x.y;
+      acc = fma(b.y, x.y, fma(b.x, x.x, acc));
     } else {
-      acc += b.x * v[2L * c] + b.y * v[2L * c + 1];
+      acc = fma(b.y, v[2L * c + 1], fma(b.x, v[2L * c], acc));
     }
   }
   if (row >= 0) y[row] = acc;
