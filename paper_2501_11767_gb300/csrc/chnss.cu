@@ -8,6 +8,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <future>
 #include <thread>
 
 #include "solver.h"
@@ -142,6 +143,7 @@ struct chnss_ctx {
   double *Kks[3] = {nullptr, nullptr, nullptr};
   double *Kk[3] = {nullptr, nullptr, nullptr};
   double *loads = nullptr, *G = nullptr, *fa = nullptr, *tmp = nullptr, *sum = nullptr, *partial = nullptr;
+  double *partial_ch = nullptr;             // reductions of the CH / AC hierarchies' setup (own stream)
   double *rhs[6] = {};
   double *xsol[6] = {};
   double *massc = nullptr;
@@ -168,6 +170,7 @@ struct chnss_ctx {
   cudaStream_t sx[3] = {nullptr, nullptr, nullptr};
   bool concurrent = true;                   // chnss_set_step_concurrency
   cudaEvent_t ev_asm = nullptr, ev_done[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_chac = nullptr;            // CH / AC assembly done (concurrent step)
   double *tmp_ns = nullptr;
   std::vector<double *> Kpd;                // open top: K_p with Dirichlet top rows, per level
   Profiler prof;
@@ -203,6 +206,7 @@ struct chnss_ctx {
     for (cudaStream_t q : sx)
       if (q) cudaStreamDestroy(q);
     if (ev_asm) cudaEventDestroy(ev_asm);
+    if (ev_chac) cudaEventDestroy(ev_chac);
     for (cudaEvent_t e : ev_done)
       if (e) cudaEventDestroy(e);
   }
@@ -500,8 +504,10 @@ void init_precset(chnss_ctx *c, PrecSet<T> &P) {
   // dominant SpMV stream by 40 %.  (The P1 hierarchies save only 25 % per
   // entry and cost more CH iterations than they save: 39 -> 48 at 1024^2.)
   P.A.bf16 = c->p.precision == 2;
-  P.L.init(ar, 0, false, p1s, d1s, vals(c->L), t1s, c->partial);
-  P.AC.init(ar, 0, false, p1s, d1s, vals(c->AC), t1s, c->partial);
+  // the CH / AC hierarchies reduce into partial_ch, the Oseen ones into
+  // partial: the two groups assemble and solve on different streams
+  P.L.init(ar, 0, false, p1s, d1s, vals(c->L), t1s, c->partial_ch);
+  P.AC.init(ar, 0, false, p1s, d1s, vals(c->AC), t1s, c->partial_ch);
   P.A.init(ar, 1, false, p2s, d2s, vals(c->A), tvs, c->partial);
   P.A.degree = 4;        // velocity smoothing: degree 4 on [hi / 16, hi]
   P.A.ratio = 16.0;
@@ -515,8 +521,8 @@ void init_precset(chnss_ctx *c, PrecSet<T> &P) {
       x1.push_back(c->X1[l][sp]);
       x2.push_back(c->X2[l][sp]);
     }
-    P.X1[sp].init(ar, 0, false, p1s, d1s, x1, t1s, c->partial);
-    if (c->p.mobility_kind != 0) P.X2[sp].init(ar, 0, false, p1s, d1s, x2, t1s, c->partial);
+    P.X1[sp].init(ar, 0, false, p1s, d1s, x1, t1s, c->partial_ch);
+    if (c->p.mobility_kind != 0) P.X2[sp].init(ar, 0, false, p1s, d1s, x2, t1s, c->partial_ch);
   }
   const int N1 = c->N1, nnz1 = c->lv(0).p1.nnz;
   const long nent1 = c->lv(0).p1.sell.nent;
@@ -560,13 +566,17 @@ void init_precset(chnss_ctx *c, PrecSet<T> &P) {
 }
 
 template <typename T>
-void setup_step_precset(chnss_ctx *c, PrecSet<T> &P) {
-  P.L.setup(c->s);
-  P.AC.setup(c->s);
-  P.A.setup(c->s);
+void setup_step_precset_chac(chnss_ctx *c, PrecSet<T> &P, cudaStream_t s) {
+  P.L.setup(s);
+  P.AC.setup(s);
   if (c->p.mobility_kind != 0)
-    for (int sp = 0; sp < 3; ++sp) P.X2[sp].setup(c->s);
-  sell_gather<T>(c->lv(0).p1.sell, 1, c->Ap, P.Apv, c->s);
+    for (int sp = 0; sp < 3; ++sp) P.X2[sp].setup(s);
+}
+
+template <typename T>
+void setup_step_precset_ns(chnss_ctx *c, PrecSet<T> &P, cudaStream_t s) {
+  P.A.setup(s);
+  sell_gather<T>(c->lv(0).p1.sell, 1, c->Ap, P.Apv, s);
 }
 
 void create_context(chnss_ctx *c) {
@@ -583,6 +593,7 @@ void create_context(chnss_ctx *c) {
   c->ebuf = ar.alloc<double>(144L * c->E);
   c->lbuf = ar.alloc<double>(15L * c->E);
   c->partial = ar.alloc<double>(64L * 1216);
+  c->partial_ch = ar.alloc<double>(64L * 1216);
   c->sum = ar.alloc<double>(4);
   const int nl = c->nlev;
   c->M1.resize(nl); c->K1.resize(nl); c->ACb.resize(nl); c->M2v.resize(nl); c->Aconst.resize(nl);
@@ -715,6 +726,7 @@ void create_context(chnss_ctx *c) {
   CHNSS_CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   for (cudaEvent_t &e : c->ev_join) CHNSS_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   CHNSS_CK(cudaEventCreateWithFlags(&c->ev_asm, cudaEventDisableTiming));
+  CHNSS_CK(cudaEventCreateWithFlags(&c->ev_chac, cudaEventDisableTiming));
   for (cudaEvent_t &e : c->ev_done) CHNSS_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   if (p.model == 0) {   // idle members of the batched CH solves
     c->dummy_in = ar.alloc<double>(2L * c->N1);
@@ -734,64 +746,68 @@ void create_context(chnss_ctx *c) {
   CHNSS_CK(cudaStreamSynchronize(s));
 }
 
-void assemble(chnss_ctx *c, const chnss_state *st) {
+// Coefficient fields on every level (injection), filled by assemble_prefix.
+struct AsmLevels {
+  std::vector<const double *> v;
+  std::vector<std::array<const double *, 4>> mu;
+  std::vector<std::array<const double *, 3>> ph;
+};
+
+void assemble_prefix(chnss_ctx *c, const chnss_state *st, AsmLevels &lv, cudaStream_t s) {
   const Mesh &m = c->mesh->m;
   const auto &p = c->p;
-  cudaStream_t s = c->s;
-  const int tka = c->prof.start(Profiler::ASSEMBLY, s);
   const int nl = c->nlev;
-  // coefficients on every level by injection
-  std::vector<const double *> v(nl);
-  std::vector<std::array<const double *, 4>> mu(nl);
-  std::vector<std::array<const double *, 3>> ph(nl);
-  v[0] = st->v;
-  for (int f = 0; f < 4; ++f) mu[0][f] = st->mu[f];
-  for (int f = 0; f < 3; ++f) ph[0][f] = st->phi[f];
+  lv.v.assign(nl, nullptr);
+  lv.mu.assign(nl, {});
+  lv.ph.assign(nl, {});
+  lv.v[0] = st->v;
+  for (int f = 0; f < 4; ++f) lv.mu[0][f] = st->mu[f];
+  for (int f = 0; f < 3; ++f) lv.ph[0][f] = st->phi[f];
   for (int l = 1; l < nl; ++l) {
     const Level &L = m.lv[l];
     const int nf = m.lv[l - 1].n;
-    launch_inject_vel(nf, v[l - 1], c->vl[l], s);
-    v[l] = c->vl[l];
+    launch_inject_vel(nf, lv.v[l - 1], c->vl[l], s);
+    lv.v[l] = c->vl[l];
     for (int f = 0; f < 4; ++f) {
       double *dst = c->mul[l] + (long)f * L.N1;
-      launch_inject_p1(nf, mu[l - 1][f], dst, s);
-      mu[l][f] = dst;
+      launch_inject_p1(nf, lv.mu[l - 1][f], dst, s);
+      lv.mu[l][f] = dst;
     }
     if (p.mobility_kind != 0)
       for (int f = 0; f < 3; ++f) {
         double *dst = c->phil[l] + (long)f * L.N1;
-        launch_inject_p1(nf, ph[l - 1][f], dst, s);
-        ph[l][f] = dst;
+        launch_inject_p1(nf, lv.ph[l - 1][f], dst, s);
+        lv.ph[l][f] = dst;
       }
   }
+}
+
+// Cahn-Hilliard / Allen-Cahn / air-potential part: C(v) on P1, the
+// matching factors of the variable mobility, potential loads, right-hand
+// sides, SELL copies and the P1 hierarchies' setup.  Element scratch:
+// ebuf[0, 9E) and lbuf.
+void assemble_chac(chnss_ctx *c, const chnss_state *st, const AsmLevels &lv, cudaStream_t s) {
+  const Mesh &m = c->mesh->m;
+  const auto &p = c->p;
+  const int nl = c->nlev;
   for (int l = 0; l < nl; ++l) {
     const Level &L = m.lv[l];
     const Geo g = geo(L);
     // C(v) on P1: L = M + tau C, AC = M + tau delta_v K + tau C
-    launch_elem_p1_conv(g, v[l], nullptr, nullptr, c->ebuf, s);
+    launch_elem_p1_conv(g, lv.v[l], nullptr, nullptr, c->ebuf, s);
     launch_gather(L.g_p1, 1, c->ebuf, p.tau, c->M1[l], 1.0, c->L[l], s);
     launch_gather(L.g_p1, 1, c->ebuf, p.tau, c->ACb[l], 1.0, c->AC[l], s);
-    // J(w) on P2 velocity blocks: A = M / tau + K_sym + J
-    launch_elem_p2_conv(g, v[l], mu[l].data(), p.alpha, c->ebuf, s);
-    launch_gather_diag2(L.g_p2v, c->ebuf, 1.0, c->Aconst[l], c->A[l], s);
     if (p.mobility_kind != 0)
       for (int sp = 0; sp < 3; ++sp) {
         const double a = std::sqrt(p.tau * p.gamma[sp] / p.beta[sp]);
-        launch_elem_p1_wstiff(g, ph[l][sp], p.gamma[sp], p.mobility_m0, c->ebuf, s);
+        launch_elem_p1_wstiff(g, lv.ph[l][sp], p.gamma[sp], p.mobility_m0, c->ebuf, s);
         launch_gather(L.g_p1, 1, c->ebuf, p.tau, c->M1[l], a, c->X2[l][sp], s);   // tau K_kappa + a M
         if (l == 0) launch_gather(L.g_p1, 1, c->ebuf, 1.0, nullptr, 0.0, c->Kk[sp], s);
       }
   }
   const Level &F = m.lv[0];
   const Geo g0 = geo(F);
-  // A_p = M / tau + eta K + J_p(w)
-  launch_elem_p1_conv(g0, st->v, mu[0].data(), p.alpha, c->ebuf, s);
-  launch_gather(F.g_p1, 1, c->ebuf, 1.0, c->Apb, 1.0, c->Ap, s);
-  if (m.top_bc == 1) {
-    k_p1_top_dirichlet<<<nb(F.N1), TPB, 0, s>>>(F.n, F.p1.rowptr, F.p1.col, c->Ap);
-    CHNSS_LAUNCH_CK();
-  }
-  // potential loads (eqn:appPotential) and Korteweg term
+  // potential loads (eqn:appPotential)
   PotentialCoef pc;
   pc.model = p.model;
   pc.inv_ns = 1.0 / p.n_s;
@@ -802,11 +818,6 @@ void assemble(chnss_ctx *c, const chnss_state *st) {
   launch_elem_loads(g0, st->phi[0], st->phi[1], st->phi[2], st->Phi_v, pc, c->lbuf, s);
   for (int f = 0; f < 5; ++f)
     launch_gather(m.g_l1, 1, c->lbuf + (long)f * c->E * 3, 1.0, nullptr, 0.0, c->loads + (long)f * c->N1, s);
-  KortewegCoef kc;
-  for (int f = 0; f < 4; ++f) kc.beta[f] = p.beta[f];
-  kc.beta_v = p.beta_v;
-  launch_elem_korteweg(g0, st->phi[0], st->phi[1], st->phi[2], st->Phi_v, kc, c->lbuf, s);
-  launch_gather(m.g_l2, 2, c->lbuf, 1.0, nullptr, 0.0, c->G, s);
   // right-hand sides
   const int N1 = c->N1, n = F.n, ref = m.ref_node;
   SpmvArgs none;
@@ -827,18 +838,65 @@ void assemble(chnss_ctx *c, const chnss_state *st) {
   k_ch_rhs_mu<<<nb(N1), TPB, 0, s>>>(N1, n, F.hx, c->loads + 3L * N1, st->phi[2], ref, p.evap_rate, p.phi_s_inf,
                                     p.beta[3], -1.0, c->fa);
   CHNSS_LAUNCH_CK();
-  const long nv = 2L * c->N2;
-  spmv_csr<double>(F.p2, c->M2v[0], 2, st->v, c->rhs[5], SPMV_PLAIN, none, s);
-  vec_axpby(nv, 1.0, c->G, 1.0 / p.tau, c->rhs[5], s);
-  vec_fill(N1, 0.0, c->rhs[5] + nv, s);
   // SELL copies of the fine operators applied by FGMRES
   sell_gather<double>(F.p1.sell, 1, c->L[0], c->Ls, s);
   sell_gather<double>(F.p1.sell, 1, c->AC[0], c->ACs, s);
-  sell_gather<double>(F.p2.sell, 4, c->A[0], c->As, s);
   if (p.mobility_kind != 0)
     for (int sp = 0; sp < 3; ++sp) sell_gather<double>(F.p1.sell, 1, c->Kk[sp], c->Kks[sp], s);
-  if (c->p32) setup_step_precset(c, *c->p32);
-  else setup_step_precset(c, *c->p64);
+  if (c->p32) setup_step_precset_chac(c, *c->p32, s);
+  else setup_step_precset_chac(c, *c->p64, s);
+}
+
+// Oseen part: J(w) on the P2 velocity blocks of every level, A_p, the
+// Korteweg load, the right-hand side, the SELL copy of A and the velocity
+// hierarchy's setup.  Element scratch: ebuf[16E, 64E).
+void assemble_ns(chnss_ctx *c, const chnss_state *st, const AsmLevels &lv, cudaStream_t s) {
+  const Mesh &m = c->mesh->m;
+  const auto &p = c->p;
+  const int nl = c->nlev;
+  double *eb = c->ebuf + 16L * c->E;
+  for (int l = 0; l < nl; ++l) {
+    const Level &L = m.lv[l];
+    const Geo g = geo(L);
+    // J(w) on P2 velocity blocks: A = M / tau + K_sym + J
+    launch_elem_p2_conv(g, lv.v[l], lv.mu[l].data(), p.alpha, eb, s);
+    launch_gather_diag2(L.g_p2v, eb, 1.0, c->Aconst[l], c->A[l], s);
+  }
+  const Level &F = m.lv[0];
+  const Geo g0 = geo(F);
+  // A_p = M / tau + eta K + J_p(w)
+  launch_elem_p1_conv(g0, st->v, lv.mu[0].data(), p.alpha, eb, s);
+  launch_gather(F.g_p1, 1, eb, 1.0, c->Apb, 1.0, c->Ap, s);
+  if (m.top_bc == 1) {
+    k_p1_top_dirichlet<<<nb(F.N1), TPB, 0, s>>>(F.n, F.p1.rowptr, F.p1.col, c->Ap);
+    CHNSS_LAUNCH_CK();
+  }
+  // Korteweg term
+  KortewegCoef kc;
+  for (int f = 0; f < 4; ++f) kc.beta[f] = p.beta[f];
+  kc.beta_v = p.beta_v;
+  launch_elem_korteweg(g0, st->phi[0], st->phi[1], st->phi[2], st->Phi_v, kc, eb, s);
+  launch_gather(m.g_l2, 2, eb, 1.0, nullptr, 0.0, c->G, s);
+  // right-hand side
+  const int N1 = c->N1;
+  const long nv = 2L * c->N2;
+  SpmvArgs none;
+  spmv_csr<double>(F.p2, c->M2v[0], 2, st->v, c->rhs[5], SPMV_PLAIN, none, s);
+  vec_axpby(nv, 1.0, c->G, 1.0 / p.tau, c->rhs[5], s);
+  vec_fill(N1, 0.0, c->rhs[5] + nv, s);
+  sell_gather<double>(F.p2.sell, 4, c->A[0], c->As, s);
+  if (c->p32) setup_step_precset_ns(c, *c->p32, s);
+  else setup_step_precset_ns(c, *c->p64, s);
+}
+
+// The whole per-step assembly on the context stream.
+void assemble(chnss_ctx *c, const chnss_state *st) {
+  cudaStream_t s = c->s;
+  const int tka = c->prof.start(Profiler::ASSEMBLY, s);
+  AsmLevels lv;
+  assemble_prefix(c, st, lv, s);
+  assemble_chac(c, st, lv, s);
+  assemble_ns(c, st, lv, s);
   c->prof.stop(Profiler::ASSEMBLY, tka, s, 0.0);
   c->assembled = true;
   for (bool &d : c->ch_done) d = false;
@@ -952,25 +1010,50 @@ chnss_status step_ch(chnss_ctx *c, chnss_state *out, chnss_solve_info *inf, cuda
 chnss_status step(chnss_ctx *c, const chnss_state *in, chnss_state *out, chnss_solve_info *info) {
   chnss_solve_info loc[6];
   chnss_solve_info *inf = info ? info : loc;
-  assemble(c, in);
   cudaStream_t s = c->s;
   const int N1 = c->N1;
   const long nv = 2L * c->N2;
+  // Concurrent: after the injections on s, each group assembles its own
+  // systems on its stream (the Oseen part is the longest and leads straight
+  // into the Oseen solve); the AC solve waits for the CH / AC assembly.
+  // Serial: the whole assembly on s first.
+  AsmLevels lv;
+  if (c->concurrent) {
+    assemble_prefix(c, in, lv, s);
+    c->assembled = true;
+    for (bool &d : c->ch_done) d = false;
+  } else {
+    assemble(c, in);
+  }
   CHNSS_CK(cudaEventRecord(c->ev_asm, s));
   chnss_status st[4] = {CHNSS_OK, CHNSS_OK, CHNSS_OK, CHNSS_OK};   // CH, AC, NS, air potential
   std::exception_ptr err[3];
+  std::promise<void> chac_ready;
+  std::shared_future<void> chac_done = chac_ready.get_future().share();
   int dev = 0;
   CHNSS_CK(cudaGetDevice(&dev));
   auto run = [&](int w) {
+    bool handed_over = false;
     try {
       CHNSS_CK(cudaSetDevice(dev));
       cudaStream_t q = c->sx[w];
       CHNSS_CK(cudaStreamWaitEvent(q, c->ev_asm, 0));
       if (w == 0) {
+        if (c->concurrent) {
+          assemble_chac(c, in, lv, q);
+          CHNSS_CK(cudaEventRecord(c->ev_chac, q));
+          handed_over = true;
+          chac_ready.set_value();
+        }
         st[0] = step_ch(c, out, inf, q, &st[3]);
       } else if (w == 1) {
+        if (c->concurrent) {
+          chac_done.get();   // ev_chac is recorded before this returns
+          CHNSS_CK(cudaStreamWaitEvent(q, c->ev_chac, 0));
+        }
         st[1] = solve_on(c, CHNSS_SYS_AC, nullptr, out->Phi_v, &inf[3], q, c->kwa, nullptr);
       } else {
+        if (c->concurrent) assemble_ns(c, in, lv, q);
         st[2] = solve_on(c, CHNSS_SYS_NS, nullptr, c->xsol[5], &inf[5], q, c->kw, c->tmp_ns);
         vec_copy(nv, c->xsol[5], out->v, q);
         vec_copy(N1, c->xsol[5] + nv, out->p, q);
@@ -978,6 +1061,7 @@ chnss_status step(chnss_ctx *c, const chnss_state *in, chnss_state *out, chnss_s
       CHNSS_CK(cudaEventRecord(c->ev_done[w], q));
     } catch (...) {
       err[w] = std::current_exception();
+      if (w == 0 && c->concurrent && !handed_over) chac_ready.set_exception(std::current_exception());
     }
   };
   if (c->concurrent) {
