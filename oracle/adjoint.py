@@ -10,7 +10,9 @@ products of the u-dependent pieces are written out here:
   convection C(v) on P1 and J(w) on P2 (w = v - sum alpha_i grad mu_i),
   the potential loads int df/dphi_i psi (Hessian of eqn:appPotential),
   the Korteweg load int G : grad u (G = sum beta_i grad phi_i (x) grad phi_i),
-  the evaporation flux j_out = evap (phi_s^vap - phi_s^inf).
+  the evaporation flux j_out = evap (phi_s^vap - phi_s^inf),
+  the concentration-dependent mobility K_kappa(phi_i^k) of the first CH row
+  (kappa = gamma_i (phi_i (1 - phi_i) + m0), Sec. 2.3 extension, lagged).
 Objective of the adjoint check: J = int |grad phi_p|^2 = phi_p^T K phi_p at
 the final time.  The pressure p^k does not enter the next step, and the
 velocity is zero on the boundary, so those adjoint entries are zero.
@@ -147,6 +149,22 @@ def korteweg_vjp(mesh: Mesh, phi, Phi, y, params):
     return phibar, Phibar
 
 
+def wstiff_vjp(mesh: Mesh, phi_i, gamma, x, y):
+    """d/d phi_i of y^T K_kappa(phi_i) x, kappa = gamma (phi (1 - phi) + m0):
+    entry c = int gamma (1 - 2 phi_h) psi_c grad x_h . grad y_h (degree-2
+    rule, exact: the integrand is quadratic on each triangle)."""
+    lam, w = triangle_rule(2)
+    _, area, g = mesh.element_geometry()
+    ph = fem.p1_field_at(mesh, phi_i, lam)                        # (E,Q)
+    gx = np.einsum("ea,ead->ed", x[mesh.tri], g)
+    gy = np.einsum("ea,ead->ed", y[mesh.tri], g)
+    dot = np.sum(gx * gy, axis=1)                                 # (E,)
+    loc = area[:, None] * dot[:, None] * np.einsum("eq,q,qc->ec", gamma * (1.0 - 2.0 * ph), w, lam)
+    out = np.zeros(mesh.N1)
+    np.add.at(out, mesh.tri.ravel(), loc.ravel())
+    return out
+
+
 def _solve_T(A, rhs):
     return spla.spsolve(A.T.tocsc(), rhs)
 
@@ -214,7 +232,7 @@ def adjoint_step(o: Oracle, st, new, lam):
         jbar += tau * p["delta_v"] * (top @ y)
     # --- Cahn-Hilliard ------------------------------------------------------
     for i in range(3):
-        Ach, _, _, _ = model.ch_system(F, st, p, i, f[i], C)
+        Ach, _, _, Kk = model.ch_system(F, st, p, i, f[i], C)
         y = _solve_T(Ach, np.concatenate([lam_phi_new[i], lam["mu"][i]]))
         y1, y2 = y[:N1], y[N1:]
         g_i, b_i = p["gamma"][i], p["beta"][i]
@@ -225,10 +243,15 @@ def adjoint_step(o: Oracle, st, new, lam):
             jbar += c * b_i * (top @ y2)               # f_s = F_s - beta_s j t
         out["v"] -= tau * conv_p1_vjp(mesh, new["phi"][i], y1)
         mu_new = new["mu"][i]
-        # d/dgamma_i of (b - A x), gamma_i = gamma (one mobility scale)
+        # d/dgamma_i of (b - A x), gamma_i = gamma (one mobility scale); the
+        # first row's tau K_kappa is gamma_i times a gamma-free matrix in both
+        # mobility laws
         db = -(tau / b_i) * f[i] @ y2
-        dAx = y1 @ (tau * (F.K @ mu_new)) + y2 @ (tau * (F.K @ new["phi"][i]) - (tau / b_i) * (F.M @ mu_new))
+        dAx = (y1 @ (tau * (Kk @ mu_new)) / g_i
+               + y2 @ (tau * (F.K @ new["phi"][i]) - (tau / b_i) * (F.M @ mu_new)))
         gbar += db - dAx
+        if p["mobility_kind"] != 0:                    # K_kappa depends on phi_i^k
+            out["phi"][i] -= tau * wstiff_vjp(mesh, st["phi"][i], g_i, mu_new, y1)
     # --- potential loads and evaporation flux ------------------------------
     lp_phi, lp_Phi = loads_vjp(mesh, st["phi"], st["Phi_v"], lw)
     out["phi"] += lp_phi

@@ -92,6 +92,20 @@ def test_korteweg_vjp(fields):
     assert np.sum(pb * dphi) + Pb @ dPhi == pytest.approx(fd, rel=1e-6)
 
 
+def test_wstiff_vjp(fields):
+    mesh, st, rng = fields
+    params = dict(inputs.default_params(), mobility_kind=1)
+    x, y = rng.standard_normal(mesh.N1), rng.standard_normal(mesh.N1)
+
+    def yKx(phi):
+        K = fem.weighted_stiffness_p1(mesh, model.mobility_at(mesh, phi, params, 1))
+        return y @ (K @ x)
+    d = rng.standard_normal(mesh.N1)
+    fd = _fd(lambda t: yKx(st["phi"][1] + t * d), 0.0, 1.0)
+    g = adjoint.wstiff_vjp(mesh, st["phi"][1], params["gamma"][1], x, y)
+    assert g @ d == pytest.approx(fd, rel=1e-7)
+
+
 def _J(n, params, st0, steps):
     from oracle.step import Oracle
     o = Oracle(n, params, exact=True)
@@ -101,11 +115,11 @@ def _J(n, params, st0, steps):
     return adjoint.objective(o, st)
 
 
-@pytest.fixture(scope="module")
-def gradient_case():
+@pytest.fixture(scope="module", params=[0, 1], ids=["constant_mobility", "variable_mobility"])
+def gradient_case(request):
     n, steps = 8, 3
     params = inputs.default_params()
-    params.update(alpha=[1e-2] * 4, evap_rate=0.5)     # make every coupling visible
+    params.update(alpha=[1e-2] * 4, evap_rate=0.5, mobility_kind=request.param)   # every coupling visible
     st0 = inputs.initial_state(n, seed=11)
     J, g = adjoint.trajectory_gradient(n, params, st0, steps)
     return n, steps, params, st0, J, g
