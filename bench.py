@@ -429,8 +429,7 @@ def run_adjoint(args):
 
     torch.cuda.set_device(0)
     n, steps, every = 256, 40, 8
-    p = inputs.workload("film256_mobility")["params"]
-    p = dict(p, mobility_kind=0)      # the adjoint covers constant mobility
+    p = inputs.workload("film256_mobility")["params"]   # concentration-dependent mobility
     mesh = chnss.Mesh(n)
     ctx = chnss.Context(mesh, p)
     st0 = chnss.state_to_device(inputs.initial_state(n, seed=0))
@@ -455,7 +454,8 @@ def run_adjoint(args):
         "data": "synthetic (seeded SplitMix64 noise on phi_p, phi_NFA)",
         "config": {"workload": "adjoint256", "n": n, "time_steps": steps, "checkpoint_every": every,
                    "forward_steps_per_gradient": fwd, "adjoint_steps_per_gradient": steps,
-                   "adjoint_rtol": 1e-12, "forward_rtol": p["rtol"], "beta": p["beta"]},
+                   "adjoint_rtol": 1e-12, "forward_rtol": p["rtol"], "beta": p["beta"],
+                   "mobility": "gamma (phi (1 - phi) + m0)" if p["mobility_kind"] else "constant"},
         "J": g["J"], "dJ_devap": g["evap"], "dJ_dgamma": g["gamma"],
         "timing": "wall clock around trajectory_gradient (forward sweep, checkpoints, recomputation, adjoint steps)",
         "clocks": clocks,

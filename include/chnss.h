@@ -191,16 +191,17 @@ chnss_status chnss_set_step_concurrency(chnss_ctx_t ctx, int on);
 chnss_status chnss_step_host(chnss_ctx_t ctx, const chnss_state *host_in, chnss_state *host_out,
                              chnss_solve_info *info);
 
-/* Adjoint of one step (discrete adjoint of chnss_step; constant mobility,
- * model 0, enclosed flow: CHNSS_ERR_ARG for the solvent-air model and for
- * meshes with an open top).
+/* Adjoint of one step (discrete adjoint of chnss_step; model 0, enclosed
+ * flow: CHNSS_ERR_ARG for the solvent-air model and for meshes with an open
+ * top; constant or concentration-dependent mobility).
  * Every solve x = A(u)^-1 b(u) of the step contributes, with
  * y = A^-T xbar (FGMRES on the transposed operator to a relative residual of
  * 1e-12, preconditioned by the forward block preconditioner),
  * ubar += (db/du)^T y - (d(A(u) x)/du)^T y: the transposed convection
  * derivatives of C(v) (CH, AC) and J(w) (Oseen, w = v - sum alpha_i grad
  * mu_i), the Hessian of eqn:appPotential in the potential loads, the
- * Korteweg load, and the evaporation flux j_out.
+ * Korteweg load, the evaporation flux j_out, and with mobility_kind 1 the
+ * derivative of K_kappa(phi_i^k) in the first CH row.
  * state_k: fields at t_k; state_k1: the step's output at t_{k+1};
  * adj_k1: adjoint of the state at t_{k+1}; adj_k (out, overwritten):
  * adjoint of the state at t_k (all DEVICE arrays, chnss_state layout;

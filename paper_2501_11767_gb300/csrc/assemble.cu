@@ -522,6 +522,31 @@ __global__ void k_adj_conv_p1(Geo g, const double *__restrict__ x, const double 
   }
 }
 
+// d/dphi of y^T K_kappa(phi) x, kappa = gamma (phi (1 - phi) + m0):
+// entry c of an element = int gamma (1 - 2 phi_h) psi_c grad x_h . grad y_h
+// = |T| gamma (grad x . grad y) (1/3 - (sum_d phi_d + phi_c) / 6)  [E][3]
+__global__ void k_adj_wstiff(Geo g, const double *__restrict__ phi, double gamma, const double *__restrict__ x,
+                             const double *__restrict__ y, double *buf) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * g.n * g.n) return;
+  Elem el;
+  element(g, e, el);
+  double gx[2] = {0.0, 0.0}, gy[2] = {0.0, 0.0}, ph[3], psum = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double xv = x[el.v1[k]], yv = y[el.v1[k]];
+    gx[0] += xv * el.gl[k][0];
+    gx[1] += xv * el.gl[k][1];
+    gy[0] += yv * el.gl[k][0];
+    gy[1] += yv * el.gl[k][1];
+    ph[k] = phi[el.v1[k]];
+    psum += ph[k];
+  }
+  const double s = el.area * gamma * (gx[0] * gy[0] + gx[1] * gy[1]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) buf[(long)e * 3 + c] = s * (1.0 / 3.0 - (psum + ph[c]) / 6.0);
+}
+
 // d/dw of y^T J(w) x (velocities): nodal part int zeta_k sum_c (d_d x_c) y_c
 // -> bufv [E][6][2]; shift part (w = v - s, s per element) projected on the
 // P1 gradients: (ds-gradient) . grad psi_m -> bufm [E][3]
@@ -689,6 +714,11 @@ __global__ void k_adj_korteweg(Geo g, const double *__restrict__ pp, const doubl
 
 void launch_adj_conv_p1(Geo g, const double *x, const double *y, double *buf, cudaStream_t s) {
   k_adj_conv_p1<<<blocks_for(2L * g.n * g.n), TPB, 0, s>>>(g, x, y, buf);
+  CHNSS_LAUNCH_CK();
+}
+void launch_adj_wstiff(Geo g, const double *phi, double gamma, const double *x, const double *y, double *buf,
+                       cudaStream_t s) {
+  k_adj_wstiff<<<blocks_for(2L * g.n * g.n), TPB, 0, s>>>(g, phi, gamma, x, y, buf);
   CHNSS_LAUNCH_CK();
 }
 void launch_adj_conv_p2(Geo g, const double *x, const double *y, double *bufv, double *bufm, cudaStream_t s) {

@@ -1532,10 +1532,12 @@ struct CHOpT : LinearOperator {   // [[L^T, a21 K], [a12 K12, a22 M]]
   void apply(const double *x, double *y, cudaStream_t s) override {
     const auto &p = c->p;
     const double tau = p.tau, g = p.gamma[sp], b = p.beta[sp];
-    const bool var = p.mobility_kind != 0;
     // y1 = L^T x1 + tau g K x2 ; y2 = (var ? tau K_kappa : tau g K) x1 - (tau g / b) M x2
-    spmv_sell_ch(c->lv(0).p1, c->LsT, c->Ks, nullptr, c->Ms, tau * g, tau * g, -tau * g / b, x, y, s);
-    if (var) throw Error{CHNSS_ERR_ARG, "the adjoint step supports constant mobility only"};
+    // (K, K_kappa symmetric: the transposed blocks are the forward ones swapped)
+    if (p.mobility_kind != 0)
+      spmv_sell_ch(c->lv(0).p1, c->LsT, c->Kks[sp], c->Ks, c->Ms, tau * g, tau, -tau * g / b, x, y, s);
+    else
+      spmv_sell_ch(c->lv(0).p1, c->LsT, c->Ks, nullptr, c->Ms, tau * g, tau * g, -tau * g / b, x, y, s);
   }
   void precond(const double *r, double *z, cudaStream_t s) override { run_prec(c, sp, r, z, s); }
   void after_sync() override { harvest_probes(c, sp); }
@@ -1609,7 +1611,7 @@ void gather_p1_add(chnss_ctx *c, const double *buf, double alpha, double *out, c
 chnss_status adjoint_step(chnss_ctx *c, const chnss_state *stk, const chnss_state *st1, const chnss_state *lam,
                           chnss_state *out, double *grad, chnss_solve_info *info) {
   const auto &p = c->p;
-  if (p.mobility_kind != 0) throw Error{CHNSS_ERR_ARG, "the adjoint step supports constant mobility only"};
+  const bool var = p.mobility_kind != 0;
   adjoint_alloc(c);
   assemble(c, stk);
   cudaStream_t s = c->s;
@@ -1702,6 +1704,10 @@ chnss_status adjoint_step(chnss_ctx *c, const chnss_state *stk, const chnss_stat
       const double *y1 = c->ay_ch, *y2 = c->ay_ch + N1;
       const double cc = tau * p.gamma[i] / p.beta[i];
       spmv_csr<double>(F.p1, c->M1[0], 1, y1, c->aphi + (long)i * N1, SPMV_PLAIN, none, q);
+      if (var) {   // - tau (d K_kappa(phi_i^k) / d phi_i)^T (y1, mu_i')
+        launch_adj_wstiff(g0, stk->phi[i], p.gamma[i], st1->mu[i], y1, eb, q);
+        launch_gather(m.g_l1, 1, eb, -tau, c->aphi + (long)i * N1, 1.0, c->aphi + (long)i * N1, q);
+      }
       vec_fill(N1, 0.0, c->alw[i], q);
       vec_axpby(N1, -cc, y2, 0.0, c->alw[i], q);
       launch_adj_conv_p1(g0, st1->phi[i], y1, eb, q);
@@ -1709,8 +1715,9 @@ chnss_status adjoint_step(chnss_ctx *c, const chnss_state *stk, const chnss_stat
       double *d = D + 4 + 5 * i;
       dot<double>(N1, c->loads + (long)i * N1, y2, d + 0, kw.partial, q);    // F_i . y2
       dot<double>(N1, c->topv, y2, d + 1, kw.partial, q);                     // t . y2
-      spmv_csr<double>(F.p1, c->K1[0], 1, st1->mu[i], tmp, SPMV_PLAIN, none, q);
-      dot<double>(N1, y1, tmp, d + 2, kw.partial, q);                         // y1 . K mu'
+      // y1 . K mu' (constant mobility) or y1 . K_kappa mu' (divided by gamma_i on the host)
+      spmv_csr<double>(F.p1, var ? c->Kk[i] : c->K1[0], 1, st1->mu[i], tmp, SPMV_PLAIN, none, q);
+      dot<double>(N1, y1, tmp, d + 2, kw.partial, q);
       spmv_csr<double>(F.p1, c->K1[0], 1, st1->phi[i], tmp, SPMV_PLAIN, none, q);
       dot<double>(N1, y2, tmp, d + 3, kw.partial, q);                         // y2 . K phi'
       spmv_csr<double>(F.p1, c->M1[0], 1, st1->mu[i], tmp, SPMV_PLAIN, none, q);
@@ -1773,7 +1780,8 @@ chnss_status adjoint_step(chnss_ctx *c, const chnss_state *stk, const chnss_stat
     const double cc = tau * p.gamma[i] / b_i;
     if (i == 2) jbar += cc * b_i * d[1];                                      // f_s = F_s - beta_s j t
     const double fy = d[0] - (i == 2 ? b_i * j_out * d[1] : 0.0);
-    gbar += -(tau / b_i) * fy - tau * d[2] - (tau * d[3] - (tau / b_i) * d[4]);
+    const double k2 = var ? d[2] / p.gamma[i] : d[2];   // tau K_kappa = gamma_i x (gamma-free matrix)
+    gbar += -(tau / b_i) * fy - tau * k2 - (tau * d[3] - (tau / b_i) * d[4]);
   }
   k_add_at<<<1, 1, 0, s>>>(out->phi[2], m.ref_node, jbar * p.evap_rate);
   CHNSS_LAUNCH_CK();

@@ -221,6 +221,9 @@ void launch_gather_diag2(const Gather &g, const double *buf, double alpha, const
 
 // adjoint (transposed Jacobian) element kernels
 void launch_adj_conv_p1(Geo g, const double *x, const double *y, double *buf, cudaStream_t s);   // [E][6][2]
+// d/dphi of y^T K_kappa(phi) x for kappa = gamma (phi (1 - phi) + m0)  [E][3]
+void launch_adj_wstiff(Geo g, const double *phi, double gamma, const double *x, const double *y, double *buf,
+                       cudaStream_t s);
 void launch_adj_conv_p2(Geo g, const double *x, const double *y, double *bufv, double *bufm,
                         cudaStream_t s);                                                        // [E][6][2], [E][3]
 void launch_adj_loads(Geo g, const double *pp, const double *pn, const double *ps, const double *Ph,
