@@ -196,10 +196,14 @@ def adjoint_step(o: Oracle, st, new, lam):
     nv = Amat.shape[0]
     m = F.M @ np.ones(N1)
     lv = np.where(bnd, 0.0, lam["v"])
-    lp = lam["p"] - m * lam["p"].sum() / m.sum()     # transpose of the zero-mean shift
-    Kaug = sp.bmat([[Amat.T, B.T, None], [B, None, sp.csr_matrix(m[:, None])],
-                    [None, sp.csr_matrix(m[None, :]), None]], format="csc")
-    y = spla.spsolve(Kaug, np.concatenate([lv, lp, [0.0]]))
+    if o.top_free:     # open top: non-singular saddle point, no pressure shift
+        Kt = sp.bmat([[Amat.T, B.T], [B, None]], format="csc")
+        y = spla.spsolve(Kt, np.concatenate([lv, lam["p"]]))
+    else:
+        lp = lam["p"] - m * lam["p"].sum() / m.sum()     # transpose of the zero-mean shift
+        Kaug = sp.bmat([[Amat.T, B.T, None], [B, None, sp.csr_matrix(m[:, None])],
+                        [None, sp.csr_matrix(m[None, :]), None]], format="csc")
+        y = spla.spsolve(Kaug, np.concatenate([lv, lp, [0.0]]))
     yv = y[:nv]
     vf = F.velocity_forms()
     out["v"] += vf["Mv"] @ yv / tau

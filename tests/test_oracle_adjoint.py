@@ -115,11 +115,14 @@ def _J(n, params, st0, steps):
     return adjoint.objective(o, st)
 
 
-@pytest.fixture(scope="module", params=[0, 1], ids=["constant_mobility", "variable_mobility"])
+@pytest.fixture(scope="module", params=[(0, 0), (1, 0), (0, 1)],
+                ids=["constant_mobility", "variable_mobility", "open_top"])
 def gradient_case(request):
     n, steps = 8, 3
+    mobility, top = request.param
     params = inputs.default_params()
-    params.update(alpha=[1e-2] * 4, evap_rate=0.5, mobility_kind=request.param)   # every coupling visible
+    # every coupling visible
+    params.update(alpha=[1e-2] * 4, evap_rate=0.5, mobility_kind=mobility, top_bc=top)
     st0 = inputs.initial_state(n, seed=11)
     J, g = adjoint.trajectory_gradient(n, params, st0, steps)
     return n, steps, params, st0, J, g
