@@ -191,9 +191,9 @@ chnss_status chnss_set_step_concurrency(chnss_ctx_t ctx, int on);
 chnss_status chnss_step_host(chnss_ctx_t ctx, const chnss_state *host_in, chnss_state *host_out,
                              chnss_solve_info *info);
 
-/* Adjoint of one step (discrete adjoint of chnss_step; model 0, enclosed
- * flow: CHNSS_ERR_ARG for the solvent-air model and for meshes with an open
- * top; constant or concentration-dependent mobility).
+/* Adjoint of one step (discrete adjoint of chnss_step; model 0:
+ * CHNSS_ERR_ARG for the solvent-air model; enclosed or open top, constant or
+ * concentration-dependent mobility).
  * Every solve x = A(u)^-1 b(u) of the step contributes, with
  * y = A^-T xbar (FGMRES on the transposed operator to a relative residual of
  * 1e-12, preconditioned by the forward block preconditioner),

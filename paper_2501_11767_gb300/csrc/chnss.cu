@@ -1645,9 +1645,13 @@ chnss_status adjoint_step(chnss_ctx *c, const chnss_state *stk, const chnss_stat
     KrylovWork &kw = c->kw;
     k_mask_velocity<<<nb(c->N2), TPB, 0, q>>>(c->N2, lam->v, F.bnd2, c->arhs);
     CHNSS_LAUNCH_CK();
-    vsum<double>(N1, lam->p, c->sum, kw.partial, q);
-    k_mean_shift_T<<<nb(N1), TPB, 0, q>>>(N1, lam->p, c->mvec, c->sum, m.lx * m.ly, c->arhs + nv);
-    CHNSS_LAUNCH_CK();
+    if (m.top_bc == 0) {   // transpose of the zero-mean pressure shift
+      vsum<double>(N1, lam->p, c->sum, kw.partial, q);
+      k_mean_shift_T<<<nb(N1), TPB, 0, q>>>(N1, lam->p, c->mvec, c->sum, m.lx * m.ly, c->arhs + nv);
+      CHNSS_LAUNCH_CK();
+    } else {               // open top: the pressure level is fixed by the outflow, no shift
+      vec_copy(N1, lam->p, c->arhs + nv, q);
+    }
     NSOpT op(c);
     const chnss_status st = fgmres(op, c->arhs, c->ay, kAdjointRtol, 0.0, p.maxit, kw, &inf[5], q, &c->prof);
     const double *yv = c->ay;
@@ -1799,7 +1803,6 @@ extern "C" chnss_status chnss_adjoint_step(chnss_ctx_t ctx, const chnss_state *s
                                            chnss_solve_info *info) {
   if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
   if (ctx->p.model != 0) return fail(ctx, CHNSS_ERR_ARG, "the adjoint step covers model 0 only");
-  if (ctx->mesh->m.top_bc != 0) return fail(ctx, CHNSS_ERR_ARG, "the adjoint step covers the enclosed flow only");
   ABI_TRY
   check_state(state_k);
   check_state(state_k1);

@@ -176,3 +176,25 @@ def test_adjoint_step_variable_mobility(torch):
     assert gg["J"] == pytest.approx(J, rel=1e-8)
     assert gg["evap"] == pytest.approx(g["evap"], rel=1e-6)
     assert gg["gamma"] == pytest.approx(g["gamma"], rel=1e-6)
+
+
+def test_adjoint_step_open_top(torch):
+    """Open (do-nothing) top: the transposed saddle point without the
+    pressure shift, free top velocities, against the oracle's adjoint."""
+    n = 8
+    p = dict(_params(), top_bc=1)
+    o = Oracle(n, p, exact=True)
+    sk = o.step(inputs.initial_state(n, seed=4))[0]
+    sk1 = o.step(sk)[0]
+    rng = np.random.default_rng(5)
+    lam = {k: rng.standard_normal(v.shape) for k, v in sk.items()}
+    lam["v"][np.repeat(o.mesh.p2_boundary(), 2)] = 0.0
+    ref, th = oadj.adjoint_step(o, sk, sk1, lam)
+    ctx = chnss.Context(chnss.Mesh(n, top_bc=1), p)
+    out, grad, info, st = ctx.adjoint_step(*(chnss.state_to_device(x) for x in (sk, sk1, lam)))
+    assert st == 0
+    got = chnss.state_to_numpy(out)
+    for key in ("phi", "mu", "Phi_v", "v"):
+        assert rel(got[key], ref[key]) < 1e-8, key
+    assert grad[0] == pytest.approx(th["evap"], rel=1e-8)
+    assert grad[1] == pytest.approx(th["gamma"], rel=1e-8)
