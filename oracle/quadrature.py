@@ -36,3 +36,23 @@ def edge_rule(degree: int):
     k = degree // 2 + 1
     x, w = np.polynomial.legendre.leggauss(k)
     return 0.5 * (x + 1.0), 0.5 * w
+
+
+def tetra_rule(degree: int):
+    """Barycentric points (Q,4) and weights (Q,) with sum(w) = 1, so that
+    integral_T g = |T| * sum_q w_q g(lambda_q) on a tetrahedron for
+    polynomials g of total degree <= ``degree``.  Collapsed map (s, t, u) in
+    [0,1]^3 to xi = s, eta = t (1 - s), zeta = u (1 - s)(1 - t), Jacobian
+    (1 - s)^2 (1 - t): Gauss-Legendre in each variable, exact to the raised
+    degrees degree + 2 (s), degree + 1 (t), degree (u)."""
+    ks, kt, ku = (degree + 4) // 2, (degree + 3) // 2, (degree + 2) // 2
+    rules = [np.polynomial.legendre.leggauss(k) for k in (ks, kt, ku)]
+    (xs, ws), (xt, wt), (xu, wu) = [(0.5 * (x + 1.0), 0.5 * w) for x, w in rules]
+    S, T, U = np.meshgrid(xs, xt, xu, indexing="ij")
+    W = np.einsum("i,j,k->ijk", ws, wt, wu) * (1.0 - S) ** 2 * (1.0 - T)
+    xi = S.ravel()
+    eta = (T * (1.0 - S)).ravel()
+    zeta = (U * (1.0 - S) * (1.0 - T)).ravel()
+    lam = np.stack([1.0 - xi - eta - zeta, xi, eta, zeta], axis=1)
+    return lam, 6.0 * W.ravel()         # reference volume 1/6
+

@@ -74,6 +74,19 @@ def initial_state(n: int, seed: int = 0, a: float = 0.3, b: float = 0.4, amp: fl
     }
 
 
+def initial_state_3d(n: int, seed: int = 0, a: float = 0.3, b: float = 0.4, amp: float = 0.01) -> dict:
+    """The same start on an n x n x n box mesh: P1 nodes (n+1)^3 (node
+    (i, j, k) has id (k (n+1) + j)(n+1) + i), velocity (3 (2n+1)^3,)
+    interleaved (x, y, z) per P2 node of the doubled lattice; the noise keyed
+    like the 2D fields."""
+    n1, n2 = (n + 1) ** 3, (2 * n + 1) ** 3
+    phi = np.empty((3, n1))
+    phi[0] = a + uniform_noise(seed, FIELD_POLYMER, n1, amp)
+    phi[1] = a + uniform_noise(seed, FIELD_NFA, n1, amp)
+    phi[2] = b
+    return {"phi": phi, "mu": np.zeros((4, n1)), "Phi_v": np.zeros(n1), "v": np.zeros(3 * n2), "p": np.zeros(n1)}
+
+
 def film_betas(eps: float) -> list:
     """Gradient-energy coefficients (beta_p, beta_NFA, beta_s, beta_a).
 
