@@ -267,6 +267,39 @@ typedef struct {
 } chnss_inner_stats;
 chnss_status chnss_inner_stats_read(chnss_ctx_t ctx, int reset, chnss_inner_stats *out);
 
+/* Tetrahedral (3D) discretisation, host side.  The box [0,1]^3 in n^3 cubes,
+ * each split into the six Kuhn tetrahedra along its main diagonal (the 3D
+ * form of the 2D diagonal split; the paper's 3D runs use uniform
+ * tetrahedral meshes of a cube, Sec. 5).  P1 node (a, b, c) has id
+ * (c (n+1) + b)(n+1) + a; velocity interleaved (x, y, z) per P2 node of the
+ * doubled lattice, node (A, B, C) id (C m + B) m + A, m = 2n + 1.
+ * chnss3_host_operator builds one operator on the HOST (no device use) with
+ * the element operators the 3D device step uses, in CSR (duplicates summed in
+ * element order) or, for the load vectors, as a dense vector:
+ *   CHNSS3_OP_M1       P1 mass (N1 x N1)
+ *   CHNSS3_OP_K1       P1 stiffness
+ *   CHNSS3_OP_C1       P1 convection int (v . grad psi_b) psi_a by the P2 velocity state->v
+ *   CHNSS3_OP_CP       the same with v - sum_i alpha_i grad mu_i (A_p of the PCD)
+ *   CHNSS3_OP_M2       scalar P2 mass (N2 x N2)
+ *   CHNSS3_OP_J2       scalar P2 convection by w = v - sum_i alpha_i grad mu_i
+ *   CHNSS3_OP_KSYM     eta-weighted symmetric-gradient form on the velocity (3 N2 x 3 N2, no boundary rows)
+ *   CHNSS3_OP_B        - int psi_q div zeta (N1 x 3 N2, no boundary columns)
+ *   CHNSS3_OP_P1PROL   P1 prolongation from the n/2 mesh (n even)
+ *   CHNSS3_OP_VPROL    velocity prolongation from the n/2 mesh, interior nodes of both meshes
+ *   CHNSS3_OP_LOADS    the five potential loads of eqn:appPotential, concatenated (5 N1)
+ *   CHNSS3_OP_KORTEWEG the Korteweg load (3 N2; beta_i, beta_v from params)
+ *   CHNSS3_OP_TOP      int over the top face of each P1 hat (N1)
+ * state (HOST arrays, 3D sizes) supplies v, mu, phi, Phi_v where needed
+ * (may be NULL otherwise).  Call with val == NULL to get nrows, ncols and nnz
+ * (the vector length for the loads); then with rowptr (nrows + 1), col and
+ * val (nnz) allocated (vectors: val only).  1 <= n <= 64. */
+enum {
+  CHNSS3_OP_M1 = 0, CHNSS3_OP_K1, CHNSS3_OP_C1, CHNSS3_OP_CP, CHNSS3_OP_M2, CHNSS3_OP_J2, CHNSS3_OP_KSYM,
+  CHNSS3_OP_B, CHNSS3_OP_P1PROL, CHNSS3_OP_VPROL, CHNSS3_OP_LOADS, CHNSS3_OP_KORTEWEG, CHNSS3_OP_TOP
+};
+chnss_status chnss3_host_operator(int n, int which, const chnss_params *params, const chnss_state *state,
+                                  int *nrows, int *ncols, long long *nnz, int *rowptr, int *col, double *val);
+
 /* Mass-matrix solve that allocates nothing.  The paper has no counterpart:
  * this is a service entry point of the library.  It solves M x = rhs for the
  * P1 mass matrix of ctx's mesh with the same Jacobi-preconditioned conjugate

@@ -123,6 +123,10 @@ EXPORTS = {
     "chnss_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
     "chnss_inner_stats_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(InnerStats)]),
+    "chnss3_host_operator": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params), ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_longlong), ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p]),
     "chnss_step_batched": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(State),
                                           ctypes.POINTER(State), ctypes.POINTER(SolveInfo), ctypes.c_int]),
     "chnss_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Tuning)]),
@@ -377,6 +381,35 @@ class Context:
         out = np.zeros(self.system_size(sys), dtype=np.float64)
         _check(load().chnss_export_rhs(self._h, sys, out.ctypes.data), self._h)
         return out
+
+
+OPS3 = ("M1", "K1", "C1", "CP", "M2", "J2", "KSYM", "B", "P1PROL", "VPROL", "LOADS", "KORTEWEG", "TOP")
+
+
+def host_operator3(n: int, which: str, params: dict, state: dict = None):
+    """One operator of the 3D (Kuhn tetrahedra) discretisation built on the
+    host by the library (chnss3_host_operator): a scipy CSR matrix, or a
+    numpy vector for LOADS, KORTEWEG and TOP.  state: host float64 arrays
+    of the 3D sizes (phi (3, N1), mu (4, N1), Phi_v, v (3 N2), p)."""
+    import scipy.sparse as sp
+    lib = load()
+    op = OPS3.index(which)
+    prm = make_params(params)
+    st = make_state(state) if state is not None else None
+    sptr = ctypes.byref(st) if st is not None else None
+    nr, nc, nnz = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+    _check(lib.chnss3_host_operator(n, op, ctypes.byref(prm), sptr, ctypes.byref(nr), ctypes.byref(nc),
+                                    ctypes.byref(nnz), None, None, None))
+    val = np.zeros(nnz.value)
+    if which in ("LOADS", "KORTEWEG", "TOP"):
+        _check(lib.chnss3_host_operator(n, op, ctypes.byref(prm), sptr, ctypes.byref(nr), ctypes.byref(nc),
+                                        ctypes.byref(nnz), None, None, val.ctypes.data))
+        return val
+    rowptr = np.zeros(nr.value + 1, dtype=np.int32)
+    col = np.zeros(nnz.value, dtype=np.int32)
+    _check(lib.chnss3_host_operator(n, op, ctypes.byref(prm), sptr, ctypes.byref(nr), ctypes.byref(nc),
+                                    ctypes.byref(nnz), rowptr.ctypes.data, col.ctypes.data, val.ctypes.data))
+    return sp.csr_matrix((val, col, rowptr), shape=(nr.value, nc.value))
 
 
 def step_batched(ctxs, states_in, states_out=None, max_threads: int = 0, check: bool = True):

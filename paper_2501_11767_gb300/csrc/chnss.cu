@@ -23,6 +23,13 @@ namespace {
 
 thread_local std::string g_last_error;
 
+}  // namespace
+
+// the last error of calls without a context (chnss_last_error(NULL))
+void chnss::set_global_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
+
 // ---------------------------------------------------------------------------
 // small kernels of the step
 constexpr int TPB = 256;

@@ -39,6 +39,9 @@ struct Error {
 // kernels launched by the library in this process (gpu_launches of the bench)
 extern std::atomic<long long> g_launch_count;
 
+// the last error of calls without a context (chnss_last_error(NULL))
+void set_global_error(const std::string &msg);
+
 #define CHNSS_LAUNCH_CK()                                                \
   do {                                                                   \
     ::chnss::g_launch_count.fetch_add(1, std::memory_order_relaxed);     \
