@@ -15,7 +15,7 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(chnss_[a-z_0-9]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(chnss3?_[a-z_0-9]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
