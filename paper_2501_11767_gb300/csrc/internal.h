@@ -116,6 +116,20 @@ struct Pattern {
   Sell sell;
 };
 
+// Host setup helpers (setup.cu): SELL view of an uploaded pattern (hmap:
+// host map SELL entry -> CSR position), pattern upload with its SELL view,
+// gather-list upload, transpose of a host CSR, transfer operator finishing
+// (R = P^T, SELL and FP32 copies), CSR positions of the diagonal.
+struct Pattern;
+struct Gather;
+struct Transfer;
+void build_sell(Arena &ar, Pattern &P, std::vector<int> *hmap = nullptr);
+void upload_pattern(Arena &ar, Pattern &P, std::vector<int> *hmap = nullptr);
+void upload_gather(Arena &ar, Gather &G, const std::vector<int> &ptr, const std::vector<int> &idx);
+void transpose(const Pattern &A, const std::vector<double> &av, Pattern &T, std::vector<double> &tv);
+void finish_transfer(Arena &ar, Transfer &t, const std::vector<double> &pv);
+std::vector<int> diag_positions(const Pattern &P);
+
 // out entry k sums buf[idx[j] + c] for j in [ptr[k], ptr[k+1]), c < ncomp.
 struct Gather {
   int nout = 0;

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <numeric>
 
+#include "gather.h"
 #include "internal.h"
 
 namespace chnss {
@@ -33,95 +34,11 @@ void element_nodes(int n, int e, int v1[3], int v2[6]) {
 }
 
 // Sorted-unique CSR pattern from per-element (row, col) node pairs.
-template <class PairFn>
-void pattern_from_elements(int nrows, int ncols, int E, int nr, int nc, PairFn nodes, Pattern &P) {
-  std::vector<int> cnt(nrows + 1, 0);
-  std::vector<int> rn(nr), cn(nc);
-  for (int e = 0; e < E; ++e) {
-    nodes(e, rn.data(), cn.data());
-    for (int a = 0; a < nr; ++a) cnt[rn[a] + 1] += nc;
-  }
-  for (int r = 0; r < nrows; ++r) cnt[r + 1] += cnt[r];
-  std::vector<int> cand(cnt[nrows]);
-  std::vector<int> fill(cnt.begin(), cnt.end() - 1);
-  for (int e = 0; e < E; ++e) {
-    nodes(e, rn.data(), cn.data());
-    for (int a = 0; a < nr; ++a)
-      for (int b = 0; b < nc; ++b) cand[fill[rn[a]]++] = cn[b];
-  }
-  P.nrows = nrows;
-  P.ncols = ncols;
-  P.h_rowptr.assign(nrows + 1, 0);
-  P.h_col.clear();
-  P.h_col.reserve(cand.size() / 3);
-  for (int r = 0; r < nrows; ++r) {
-    int *b = cand.data() + cnt[r], *e = cand.data() + cnt[r + 1];
-    std::sort(b, e);
-    int *u = std::unique(b, e);
-    P.h_col.insert(P.h_col.end(), b, u);
-    P.h_rowptr[r + 1] = (int)P.h_col.size();
-  }
-  P.nnz = (int)P.h_col.size();
-}
-
-inline int find_col(const Pattern &P, int row, int col) {
-  const int *b = P.h_col.data() + P.h_rowptr[row], *e = P.h_col.data() + P.h_rowptr[row + 1];
-  const int *it = std::lower_bound(b, e, col);
-  return (int)(it - P.h_col.data());
-}
-
-// Gather list: contribution j of element e, local (a, b) -> entry (row, col),
-// element-buffer offset off(e, a, b); keep(e, a, b) masks entries out.
-template <class PairFn, class OffFn, class KeepFn>
-void gather_from_elements(const Pattern &P, int E, int nr, int nc, PairFn nodes, OffFn off, KeepFn keep,
-                          Gather &G, std::vector<int> &hptr, std::vector<int> &hidx) {
-  hptr.assign(P.nnz + 1, 0);
-  std::vector<int> rn(nr), cn(nc);
-  for (int e = 0; e < E; ++e) {
-    nodes(e, rn.data(), cn.data());
-    for (int a = 0; a < nr; ++a)
-      for (int b = 0; b < nc; ++b)
-        if (keep(e, a, b, rn[a], cn[b])) hptr[find_col(P, rn[a], cn[b]) + 1]++;
-  }
-  for (int k = 0; k < P.nnz; ++k) hptr[k + 1] += hptr[k];
-  hidx.assign(hptr[P.nnz], 0);
-  std::vector<int> fill(hptr.begin(), hptr.end() - 1);
-  for (int e = 0; e < E; ++e) {   // element order: fixed summation order
-    nodes(e, rn.data(), cn.data());
-    for (int a = 0; a < nr; ++a)
-      for (int b = 0; b < nc; ++b)
-        if (keep(e, a, b, rn[a], cn[b])) hidx[fill[find_col(P, rn[a], cn[b])]++] = off(e, a, b);
-  }
-  G.nout = P.nnz;
-  G.ncontrib = (int)hidx.size();
-}
-
-// node <- (element, local) gather for load vectors
-template <class NodeFn, class OffFn, class KeepFn>
-void node_gather(int nnodes, int E, int nl, NodeFn nodes, OffFn off, KeepFn keep, std::vector<int> &hptr,
-                 std::vector<int> &hidx, Gather &G) {
-  hptr.assign(nnodes + 1, 0);
-  std::vector<int> nd(nl);
-  for (int e = 0; e < E; ++e) {
-    nodes(e, nd.data());
-    for (int a = 0; a < nl; ++a)
-      if (keep(nd[a])) hptr[nd[a] + 1]++;
-  }
-  for (int k = 0; k < nnodes; ++k) hptr[k + 1] += hptr[k];
-  hidx.assign(hptr[nnodes], 0);
-  std::vector<int> fill(hptr.begin(), hptr.end() - 1);
-  for (int e = 0; e < E; ++e) {
-    nodes(e, nd.data());
-    for (int a = 0; a < nl; ++a)
-      if (keep(nd[a])) hidx[fill[nd[a]]++] = off(e, a);
-  }
-  G.nout = nnodes;
-  G.ncontrib = (int)hidx.size();
-}
+}  // namespace
 
 // SELL-C-sigma view of P (see internal.h); also returns the host map from
 // SELL entries to CSR positions when hmap is given.
-void build_sell(Arena &ar, Pattern &P, std::vector<int> *hmap = nullptr) {
+void build_sell(Arena &ar, Pattern &P, std::vector<int> *hmap) {
   const int C = Sell::C, S = Sell::SIGMA, n = P.nrows;
   std::vector<int> perm(n);
   std::iota(perm.begin(), perm.end(), 0);
@@ -243,7 +160,7 @@ bool build_sell_stencil(Arena &ar, Pattern &P, int nx) {
   return true;
 }
 
-void upload_pattern(Arena &ar, Pattern &P, std::vector<int> *hmap = nullptr) {
+void upload_pattern(Arena &ar, Pattern &P, std::vector<int> *hmap) {
   P.rowptr = ar.upload(P.h_rowptr);
   P.col = ar.upload(P.h_col);
   build_sell(ar, P, hmap);
@@ -291,6 +208,14 @@ void finish_transfer(Arena &ar, Transfer &t, const std::vector<double> &pv) {
   t.Ps32 = ar.upload(std::vector<float>(ps.begin(), ps.end()));
   t.Rs32 = ar.upload(std::vector<float>(rs.begin(), rs.end()));
 }
+
+std::vector<int> diag_positions(const Pattern &P) {
+  std::vector<int> d(P.nrows);
+  for (int r = 0; r < P.nrows; ++r) d[r] = find_col(P, r, r);
+  return d;
+}
+
+namespace {
 
 // Linear interpolation of coarse P1 functions at the fine P1 nodes.
 void build_p1_transfer(Arena &ar, int nc, Transfer &t) {
@@ -360,12 +285,6 @@ void build_vel_transfer(Arena &ar, int nc, int top_bc, Transfer &t) {
     }
   P.nnz = (int)P.h_col.size();
   finish_transfer(ar, t, pv);
-}
-
-std::vector<int> diag_positions(const Pattern &P) {
-  std::vector<int> d(P.nrows);
-  for (int r = 0; r < P.nrows; ++r) d[r] = find_col(P, r, r);
-  return d;
 }
 
 }  // namespace

@@ -1,4 +1,5 @@
 // Multigrid V-cycle and Krylov drivers.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <type_traits>
@@ -173,7 +174,10 @@ void MGHier<T>::init(Arena &ar, int kind_, bool singular_, const std::vector<con
         tail_l0 = l;
         break;
       }
-    if (tail_l0 > 0 && nl - tail_l0 <= kMaxTailLevels) {
+    // the one-block tail sweeps rows of at most 8 entries (sell_w8m_slice)
+    bool narrow = true;
+    for (int l = std::max(tail_l0, 0); l < nl; ++l) narrow = narrow && pat[l]->sell.wmax <= 8;
+    if (tail_l0 > 0 && nl - tail_l0 <= kMaxTailLevels && narrow) {
       std::vector<MultiPtr<T>> X(nl), Tt(nl), Rr(nl), B(nl);
       for (int l = 0; l < nl; ++l) {
         X[l].p[0] = x[l];
