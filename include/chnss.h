@@ -300,6 +300,27 @@ enum {
 chnss_status chnss3_host_operator(int n, int which, const chnss_params *params, const chnss_state *state,
                                   int *nrows, int *ncols, long long *nnz, int *rowptr, int *col, double *val);
 
+/* One semi-implicit step on the 3D Kuhn mesh of n^3 cubes of the unit box
+ * (n even, 2 <= n <= 96), on the device: the 2D step's systems and solvers
+ * (CH for three species with diag(MG(M + tau C), X^-1 M X^-1), AC with MG,
+ * the air potential by Jacobi-PCG, Oseen with diag(MG(A), M_p^-1 A_p K_p^-1),
+ * FGMRES(restart) with CGS2, geometric multigrid on the nested Kuhn meshes)
+ * with no-slip on every face and evaporation through the top face z = 1
+ * (reference point (1/2, 1/2, 1)).  Covers model 0, constant mobility, FP64
+ * (precision 0) and one V-cycle per block (inner_rtol 0); other parameter
+ * sets get CHNSS_ERR_ARG.  The solves run one after the other on the
+ * context's stream (cuda_stream, or a library stream when NULL).
+ * States: chnss_state with DEVICE arrays of the 3D sizes (chnss3_sizes):
+ * phi[3], mu[4], Phi_v, p of N1 = (n+1)^3, v of 3 N2 = 3 (2n+1)^3.
+ * info[6] (optional): the six solves as in chnss_step.  chnss3_step
+ * synchronises the stream before returning. */
+typedef struct chnss3_ctx *chnss3_ctx_t;
+chnss_status chnss3_ctx_create(int n, const chnss_params *params, void *cuda_stream, chnss3_ctx_t *out);
+chnss_status chnss3_ctx_destroy(chnss3_ctx_t ctx);
+chnss_status chnss3_sizes(chnss3_ctx_t ctx, int *N1, int *N2);
+chnss_status chnss3_step(chnss3_ctx_t ctx, const chnss_state *in, chnss_state *out, chnss_solve_info *info);
+const char *chnss3_last_error(chnss3_ctx_t ctx);
+
 /* Mass-matrix solve that allocates nothing.  The paper has no counterpart:
  * this is a service entry point of the library.  It solves M x = rhs for the
  * P1 mass matrix of ctx's mesh with the same Jacobi-preconditioned conjugate

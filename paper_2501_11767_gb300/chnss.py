@@ -123,6 +123,13 @@ EXPORTS = {
     "chnss_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
     "chnss_inner_stats_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(InnerStats)]),
+    "chnss3_ctx_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Params), ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "chnss3_ctx_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "chnss3_sizes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "chnss3_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.POINTER(State),
+                                   ctypes.POINTER(SolveInfo)]),
+    "chnss3_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "chnss3_host_operator": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params), ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_longlong), ctypes.c_void_p, ctypes.c_void_p,
@@ -381,6 +388,45 @@ class Context:
         out = np.zeros(self.system_size(sys), dtype=np.float64)
         _check(load().chnss_export_rhs(self._h, sys, out.ctypes.data), self._h)
         return out
+
+
+class Context3:
+    """The 3D step on the Kuhn mesh of n^3 cubes of the unit box
+    (chnss3_ctx_create / chnss3_step): device states with phi (3, N1),
+    mu (4, N1), Phi_v, p (N1) and v (3 N2)."""
+
+    def __init__(self, n: int, params: dict, stream=None):
+        lib = load()
+        self._p = make_params(params)
+        h = ctypes.c_void_p()
+        sptr = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        _check(lib.chnss3_ctx_create(n, ctypes.byref(self._p), sptr, ctypes.byref(h)))
+        self._h = h
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib.chnss3_sizes(h, ctypes.byref(a), ctypes.byref(b)))
+        self.n, self.N1, self.N2 = n, a.value, b.value
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            load().chnss3_ctx_destroy(self._h)
+            self._h = None
+
+    def new_state(self):
+        import torch
+        z = lambda k: torch.zeros(k, dtype=torch.float64, device="cuda")   # noqa: E731
+        return {"phi": z((3, self.N1)), "mu": z((4, self.N1)), "Phi_v": z(self.N1), "v": z(3 * self.N2),
+                "p": z(self.N1)}
+
+    def step(self, state_in: dict, state_out: dict = None, check: bool = True):
+        if state_out is None:
+            state_out = self.new_state()
+        a, b = make_state(state_in), make_state(state_out)
+        infos = (SolveInfo * 6)()
+        st = load().chnss3_step(self._h, ctypes.byref(a), ctypes.byref(b), infos)
+        if check and st != 0:
+            msg = load().chnss3_last_error(self._h)
+            raise ChnssError(st, msg.decode() if msg else "")
+        return state_out, {SYSTEM_NAMES[i]: infos[i].as_dict() for i in range(6)}, st
 
 
 OPS3 = ("M1", "K1", "C1", "CP", "M2", "J2", "KSYM", "B", "P1PROL", "VPROL", "LOADS", "KORTEWEG", "TOP")

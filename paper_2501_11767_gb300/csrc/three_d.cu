@@ -496,3 +496,714 @@ extern "C" chnss_status chnss3_host_operator(int n, int which, const chnss_param
     return CHNSS_ERR_ARG;
   }
 }
+
+// ---------------------------------------------------------------------------
+// The 3D step on the device: the 2D step's systems and solvers (Sec. 4) on a
+// Kuhn mesh.  Per-step assembly: one thread per tetrahedron evaluates an
+// element operator of three_d.h into an element buffer, a gather kernel sums
+// every CSR entry's contributions in element order (no atomics).  The
+// velocity operator is a scalar CSR on the interleaved 3 N2 dofs; all
+// hierarchies are scalar (FP64) multigrid; the solves run one after the
+// other on the context's stream.
+#include "gather.h"
+#include "solver.h"
+
+namespace chnss {
+namespace {
+
+__constant__ Tet3Ref c3;
+
+struct Geo3 {
+  int n;
+  double h[3];
+};
+
+struct Fields3 {
+  const double *phi[3];
+  const double *mu[4];
+  const double *Phi;
+  const double *v;
+  double alpha[4], beta[4], beta_v;
+};
+
+constexpr int kTPB3 = 128;
+inline int nb3(long n, int t = kTPB3) { return (int)((n + t - 1) / t); }
+
+__device__ inline void tet_nodes(const Geo3 &g, long e, double x[4][3], int v1[4], int v2[10]) {
+  // kPerm3 and kEdge3 of three_d.h, as device-side tables
+  const int kPerm3[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  const int kEdge3[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+  const int n = g.n, p = (int)(e % 6);
+  const long c = e / 6;
+  int lat[4][3];
+  int v[3] = {(int)(c % n), (int)((c / n) % n), (int)(c / ((long)n * n))};
+  for (int d = 0; d < 3; ++d) lat[0][d] = v[d];
+  for (int s = 0; s < 3; ++s) {
+    v[kPerm3[p][s]] += 1;
+    for (int d = 0; d < 3; ++d) lat[s + 1][d] = v[d];
+  }
+  const int n1 = n + 1, m = 2 * n + 1;
+  for (int a = 0; a < 4; ++a) {
+    for (int d = 0; d < 3; ++d) x[a][d] = lat[a][d] * g.h[d];
+    v1[a] = (lat[a][2] * n1 + lat[a][1]) * n1 + lat[a][0];
+    v2[a] = (2 * lat[a][2] * m + 2 * lat[a][1]) * m + 2 * lat[a][0];
+  }
+  for (int q = 0; q < 6; ++q) {
+    const int a = kEdge3[q][0], b = kEdge3[q][1];
+    v2[4 + q] = ((lat[a][2] + lat[b][2]) * m + lat[a][1] + lat[b][1]) * m + lat[a][0] + lat[b][0];
+  }
+}
+
+__device__ inline void elem_shift(const Fields3 &f, const int v1[4], const double gr[4][3], double s[3]) {
+  s[0] = s[1] = s[2] = 0.0;
+  for (int i = 0; i < 4; ++i)
+    for (int a = 0; a < 4; ++a) {
+      const double mv = f.mu[i][v1[a]];
+      for (int d = 0; d < 3; ++d) s[d] += f.alpha[i] * mv * gr[a][d];
+    }
+}
+
+// mode 0: P1 convection (shift if `shift`), buf [E][16];  mode 1: P2
+// convection with the shift, buf [E][100]
+__global__ void k3_conv(Geo3 g, Fields3 f, int mode, int shift, double *buf) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 6L * g.n * g.n * g.n) return;
+  double x[4][3], gr[4][3], vk[10][3], s[3];
+  int v1[4], v2[10];
+  tet_nodes(g, e, x, v1, v2);
+  const double vol = tet_geometry(x, gr);
+  for (int k = 0; k < 10; ++k)
+    for (int d = 0; d < 3; ++d) vk[k][d] = f.v[3L * v2[k] + d];
+  if (shift) elem_shift(f, v1, gr, s);
+  if (mode == 0) tet_p1_conv(c3, vol, gr, vk, shift ? s : nullptr, buf + e * 16);
+  else tet_p2_conv(c3, vol, gr, vk, s, buf + e * 100);
+}
+
+// potential loads [E][20] and Korteweg load [E][30]
+__global__ void k3_loads(Geo3 g, Fields3 f, double *lbuf, double *kbuf) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 6L * g.n * g.n * g.n) return;
+  double x[4][3], gr[4][3], fl[4][4];
+  int v1[4], v2[10];
+  tet_nodes(g, e, x, v1, v2);
+  const double vol = tet_geometry(x, gr);
+  for (int a = 0; a < 4; ++a) {
+    for (int i = 0; i < 3; ++i) fl[i][a] = f.phi[i][v1[a]];
+    fl[3][a] = f.Phi[v1[a]];
+  }
+  tet_loads(c3, vol, fl, lbuf + e * 20);
+  double grd[5][3] = {};
+  for (int a = 0; a < 4; ++a)
+    for (int d = 0; d < 3; ++d) {
+      for (int i = 0; i < 3; ++i) grd[i][d] += fl[i][a] * gr[a][d];
+      grd[4][d] += fl[3][a] * gr[a][d];
+    }
+  for (int d = 0; d < 3; ++d) grd[3][d] = -(grd[0][d] + grd[1][d] + grd[2][d]);
+  double G[3][3];
+  for (int c = 0; c < 3; ++c)
+    for (int d = 0; d < 3; ++d) {
+      double s = 0.0;
+      for (int i = 0; i < 4; ++i) s += f.beta[i] * grd[i][c] * grd[i][d];
+      G[c][d] = s + f.beta_v * grd[4][c] * grd[4][d];
+    }
+  tet_korteweg(c3, vol, gr, G, kbuf + e * 30);
+}
+
+// coarse P1 node (a, b, c) <- fine (2a, 2b, 2c); coarse P2 node (A, B, C) <-
+// fine P2 node (2A, 2B, 2C), three components
+__global__ void k3_inject(int nf, int vel, const double *fine, double *coarse) {
+  const int nc = nf / 2;
+  const int mc = vel ? 2 * nc + 1 : nc + 1, mf = vel ? 2 * nf + 1 : nf + 1;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)mc * mc * mc) return;
+  const int a = (int)(i % mc), b = (int)((i / mc) % mc), c = (int)(i / ((long)mc * mc));
+  const long src = ((long)(2 * c) * mf + 2 * b) * mf + 2 * a;
+  if (vel)
+    for (int d = 0; d < 3; ++d) coarse[3 * i + d] = fine[3 * src + d];
+  else
+    coarse[i] = fine[src];
+}
+
+__global__ void k3_mask(long n, const int *bnd, double *x) {   // zero the boundary velocity dofs
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && bnd[i / 3]) x[i] = 0.0;
+}
+
+// out = -cc (load + sb j t), j = evap (phi_s[ref] - phi_inf)
+__global__ void k3_flux_rhs(int N1, const double *load, const double *top, const double *phi_s, int ref, double evap,
+                            double phi_inf, double sb, double cc, double *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N1) return;
+  const double j = evap * (phi_s[ref] - phi_inf);
+  out[i] = -cc * (load[i] + sb * j * top[i]);
+}
+
+// rhs += -tau gamma_v load_v + flux j t
+__global__ void k3_ac_rhs(int N1, const double *load, const double *top, const double *phi_s, int ref, double evap,
+                          double phi_inf, double tg, double flux, double *rhs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N1) return;
+  const double j = evap * (phi_s[ref] - phi_inf);
+  rhs[i] += -tg * load[i] + flux * j * top[i];
+}
+
+__global__ void k3_air(int N1, const double *p0, const double *p1, const double *p2, double *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N1) out[i] = 1.0 - p0[i] - p1[i] - p2[i];
+}
+
+__global__ void k3_shift(int N1, double *p, const double *sum, double vol) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N1) p[i] -= *sum / vol;
+}
+
+// one level of the 3D hierarchy on the device
+struct Level3 {
+  int n = 0;
+  long N1 = 0, N2 = 0, E = 0;
+  Geo3 geo{};
+  Pattern p1, pv;
+  int *diag1 = nullptr, *diagv = nullptr;
+  Transfer t1, tv;                 // from the next coarser level
+  Gather g1, gj;                   // element buffers -> P1 CSR, P2 convection -> velocity CSR
+  double *M1 = nullptr, *K1 = nullptr, *ACb = nullptr, *Aconst = nullptr;
+  double *L = nullptr, *AC = nullptr, *A = nullptr, *X[3] = {nullptr, nullptr, nullptr};
+  double *vl = nullptr, *mul = nullptr;   // injected v (3 N2) and mu (4 N1), levels >= 1
+};
+
+}  // namespace
+}  // namespace chnss
+
+struct chnss3_ctx {
+  chnss::Arena ar;
+  chnss_params p{};
+  cudaStream_t s = nullptr;
+  bool own_stream = false;
+  std::vector<chnss::Level3> lv;
+  chnss::Pattern pb, pbt;                       // B (N1 x 3 N2), B^T
+  chnss::Gather gl, gk;                         // loads -> P1 nodes, Korteweg -> velocity dofs
+  int *bnd = nullptr;                           // fine P2 boundary mask
+  int ref = 0;
+  double *Bs = nullptr, *Bts = nullptr, *Mv = nullptr, *Apb = nullptr, *Ap = nullptr, *top = nullptr;
+  double *Ls = nullptr, *Ks = nullptr, *Ms = nullptr, *ACs = nullptr, *As = nullptr, *Aps = nullptr;
+  double *ebuf = nullptr, *kbuf = nullptr, *loads = nullptr, *G = nullptr, *dinvM = nullptr, *massc = nullptr;
+  double *rhs[6] = {}, *xsol[6] = {}, *mb = nullptr, *mx = nullptr, *mt = nullptr, *phia = nullptr;
+  double *partial = nullptr, *sum = nullptr, *pinned = nullptr;
+  chnss::MGHier<double> hL, hAC, hX[3], hKp, hA;
+  chnss::KrylovWork kw;
+  std::string err;
+  ~chnss3_ctx() {
+    if (pinned) cudaFreeHost(pinned);
+    if (own_stream && s) cudaStreamDestroy(s);
+  }
+};
+
+namespace chnss {
+namespace {
+
+constexpr double kMassLo3 = 0.5, kMassHi3 = 2.5;   // spectrum of D^-1 M for P1 tetrahedra (Wathen)
+
+std::vector<double> on_pattern(const Pattern &P, const HostCSR &A) {
+  std::vector<double> v(P.nnz, 0.0);
+  for (int r = 0; r < A.nrows; ++r)
+    for (int k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k) v[find_col(P, r, A.col[k])] = A.val[k];
+  return v;
+}
+
+void pattern_from_csr(const HostCSR &A, Pattern &P) {
+  P.nrows = A.nrows;
+  P.ncols = A.ncols;
+  P.h_rowptr = A.rowptr;
+  P.h_col = A.col;
+  P.nnz = (int)A.col.size();
+}
+
+void make_transfer(Arena &ar, const HostCSR &A, Transfer &t) {
+  pattern_from_csr(A, t.P);
+  finish_transfer(ar, t, A.val);
+}
+
+void build_level3(chnss3_ctx *c, Level3 &L, int n, bool fine, const Mesh3Host *coarse) {
+  Arena &ar = c->ar;
+  const auto &p = c->p;
+  const double box[3] = {1.0, 1.0, 1.0};
+  const Mesh3Host M = make_mesh3(n, box);
+  L.n = n;
+  L.N1 = M.N1;
+  L.N2 = M.N2;
+  L.E = M.E;
+  L.geo.n = n;
+  for (int d = 0; d < 3; ++d) L.geo.h[d] = M.h[d];
+  const int E = (int)M.E, N1 = (int)M.N1, N2 = (int)M.N2;
+  auto p1n = [&](int e, int *r, int *cc) {
+    for (int a = 0; a < 4; ++a) r[a] = cc[a] = M.tet[(long)e * 4 + a];
+  };
+  auto vdn = [&](int e, int *r, int *cc) {
+    for (int a = 0; a < 10; ++a)
+      for (int d = 0; d < 3; ++d) r[a * 3 + d] = cc[a * 3 + d] = 3 * M.tet2[(long)e * 10 + a] + d;
+  };
+  pattern_from_elements(N1, N1, E, 4, 4, p1n, L.p1);
+  pattern_from_elements(3 * N2, 3 * N2, E, 30, 30, vdn, L.pv);
+  upload_pattern(ar, L.p1);
+  upload_pattern(ar, L.pv);
+  L.diag1 = ar.upload(diag_positions(L.p1));
+  L.diagv = ar.upload(diag_positions(L.pv));
+  std::vector<int> hptr, hidx;
+  gather_from_elements(L.p1, E, 4, 4, p1n, [](int e, int a, int b) { return e * 16 + a * 4 + b; },
+                       [](int, int, int, int, int) { return true; }, L.g1, hptr, hidx);
+  upload_gather(ar, L.g1, hptr, hidx);
+  auto vkeep = [&](int, int i, int j, int r, int cc) {
+    return i % 3 == j % 3 && !M.p2_boundary(r / 3) && !M.p2_boundary(cc / 3);
+  };
+  gather_from_elements(L.pv, E, 30, 30, vdn, [](int e, int i, int j) { return e * 100 + (i / 3) * 10 + j / 3; },
+                       vkeep, L.gj, hptr, hidx);
+  upload_gather(ar, L.gj, hptr, hidx);
+  // constant operators
+  chnss_params none = p;
+  const HostCSR hM = host_operator3(n, OP3_M1, none, nullptr), hK = host_operator3(n, OP3_K1, none, nullptr);
+  std::vector<double> m1 = on_pattern(L.p1, hM), k1 = on_pattern(L.p1, hK);
+  L.M1 = ar.upload(m1);
+  L.K1 = ar.upload(k1);
+  std::vector<double> acb(m1.size());
+  for (size_t k = 0; k < m1.size(); ++k) acb[k] = m1[k] + p.tau * p.delta_v * k1[k];
+  L.ACb = ar.upload(acb);
+  for (int sp = 0; sp < 3; ++sp) {
+    const double a = std::sqrt(p.tau * p.gamma[sp] / p.beta[sp]);
+    std::vector<double> x(m1.size());
+    for (size_t k = 0; k < m1.size(); ++k) x[k] = p.tau * p.gamma[sp] * k1[k] + a * m1[k];
+    L.X[sp] = ar.upload(x);
+  }
+  // A const = M_v / tau + K_sym with identity rows / zero columns on the no-slip dofs
+  const HostCSR hM2 = host_operator3(n, OP3_M2, none, nullptr), hKs = host_operator3(n, OP3_KSYM, none, nullptr);
+  std::vector<double> av = on_pattern(L.pv, hKs), mv(L.pv.nnz, 0.0);
+  for (int r = 0; r < hM2.nrows; ++r)
+    for (int k = hM2.rowptr[r]; k < hM2.rowptr[r + 1]; ++k)
+      for (int d = 0; d < 3; ++d) mv[find_col(L.pv, 3 * r + d, 3 * hM2.col[k] + d)] = hM2.val[k];
+  for (int r = 0; r < 3 * N2; ++r)
+    for (int k = L.pv.h_rowptr[r]; k < L.pv.h_rowptr[r + 1]; ++k) {
+      const int cc = L.pv.h_col[k];
+      av[k] += mv[k] / p.tau;
+      if (M.p2_boundary(r / 3) || M.p2_boundary(cc / 3)) av[k] = r == cc ? 1.0 : 0.0;
+    }
+  L.Aconst = ar.upload(av);
+  L.L = ar.alloc<double>(L.p1.nnz);
+  L.AC = ar.alloc<double>(L.p1.nnz);
+  L.A = ar.alloc<double>(L.pv.nnz);
+  if (!fine) {
+    L.vl = ar.alloc<double>(3L * N2);
+    L.mul = ar.alloc<double>(4L * N1);
+  }
+  if (coarse) {
+    make_transfer(ar, p1_prolongation3(*coarse), L.t1);
+    make_transfer(ar, velocity_prolongation3(*coarse, M), L.tv);
+  }
+  if (!fine) return;
+  // fine-level only: velocity mass, B and B^T (zero no-slip columns), A_p's constant part, loads
+  c->Mv = ar.upload(mv);
+  const HostCSR hB = host_operator3(n, OP3_B, none, nullptr);
+  HostCSR hBz = hB;
+  for (size_t k = 0; k < hBz.col.size(); ++k)
+    if (M.p2_boundary(hBz.col[k] / 3)) hBz.val[k] = 0.0;
+  pattern_from_csr(hBz, c->pb);
+  std::vector<double> btv;
+  transpose(c->pb, hBz.val, c->pbt, btv);
+  std::vector<int> map_b, map_bt;
+  upload_pattern(ar, c->pb, &map_b);
+  upload_pattern(ar, c->pbt, &map_bt);
+  auto sell_of = [](const std::vector<int> &map, const std::vector<double> &v) {
+    std::vector<double> out(map.size());
+    for (size_t e = 0; e < map.size(); ++e) out[e] = map[e] >= 0 ? v[map[e]] : 0.0;
+    return out;
+  };
+  c->Bs = ar.upload(sell_of(map_b, hBz.val));
+  c->Bts = ar.upload(sell_of(map_bt, btv));
+  std::vector<double> apb(m1.size());
+  for (size_t k = 0; k < m1.size(); ++k) apb[k] = m1[k] / p.tau + p.eta * k1[k];
+  c->Apb = ar.upload(apb);
+  const HostCSR hT = host_operator3(n, OP3_TOP, none, nullptr);
+  c->top = ar.upload(hT.val);
+  node_gather(N1, E, 4, [&](int e, int *nd) { for (int a = 0; a < 4; ++a) nd[a] = M.tet[(long)e * 4 + a]; },
+              [](int e, int a) { return e * 20 + a; }, [](int) { return true; }, hptr, hidx, c->gl);
+  upload_gather(ar, c->gl, hptr, hidx);
+  node_gather(N2, E, 10, [&](int e, int *nd) { for (int a = 0; a < 10; ++a) nd[a] = M.tet2[(long)e * 10 + a]; },
+              [](int e, int a) { return e * 30 + a * 3; }, [&](int nd) { return !M.p2_boundary(nd); }, hptr, hidx,
+              c->gk);
+  upload_gather(ar, c->gk, hptr, hidx);
+  std::vector<int> bnd(N2);
+  for (int i = 0; i < N2; ++i) bnd[i] = M.p2_boundary(i) ? 1 : 0;
+  c->bnd = ar.upload(bnd);
+  c->ref = M.id1(n / 2, n / 2, n);
+  std::vector<double> dinv(N1);
+  const std::vector<int> dpos = diag_positions(L.p1);
+  for (int r = 0; r < N1; ++r) dinv[r] = 1.0 / m1[dpos[r]];
+  c->dinvM = ar.upload(dinv);
+}
+
+void create3(chnss3_ctx *c, int n) {
+  Arena &ar = c->ar;
+  const auto &p = c->p;
+  std::vector<int> sizes{n};
+  while (sizes.back() % 2 == 0 && sizes.back() >= 4) sizes.push_back(sizes.back() / 2);
+  const int nl = (int)sizes.size();
+  c->lv.resize(nl);
+  const double box[3] = {1.0, 1.0, 1.0};
+  for (int l = 0; l < nl; ++l) {
+    const Mesh3Host coarse = l + 1 < nl ? make_mesh3(sizes[l + 1], box) : Mesh3Host{};
+    build_level3(c, c->lv[l], sizes[l], l == 0, l + 1 < nl ? &coarse : nullptr);
+  }
+  const Level3 &F = c->lv[0];
+  const long N1 = F.N1, nv = 3 * F.N2, E = F.E;
+  CHNSS_CK(cudaMemcpyToSymbolAsync(c3, &reference3(), sizeof(Tet3Ref), 0, cudaMemcpyHostToDevice, c->s));
+  c->ebuf = ar.alloc<double>(100 * E);
+  c->kbuf = ar.alloc<double>(30 * E);
+  c->loads = ar.alloc<double>(5 * N1);
+  c->G = ar.alloc<double>(nv);
+  c->Ap = ar.alloc<double>(F.p1.nnz);
+  const long nent1 = F.p1.sell.nent, nentv = F.pv.sell.nent;
+  c->Ls = ar.alloc<double>(nent1);
+  c->Ks = ar.alloc<double>(nent1);
+  c->Ms = ar.alloc<double>(nent1);
+  c->ACs = ar.alloc<double>(nent1);
+  c->Aps = ar.alloc<double>(nent1);
+  c->As = ar.alloc<double>(nentv);
+  sell_gather<double>(F.p1.sell, 1, F.K1, c->Ks, c->s);
+  sell_gather<double>(F.p1.sell, 1, F.M1, c->Ms, c->s);
+  for (int k = 0; k < 3; ++k) {
+    c->rhs[k] = ar.alloc<double>(2 * N1);
+    c->xsol[k] = ar.alloc<double>(2 * N1);
+  }
+  c->rhs[3] = ar.alloc<double>(N1);
+  c->rhs[4] = ar.alloc<double>(N1);
+  c->rhs[5] = ar.alloc<double>(nv + N1);
+  c->xsol[5] = ar.alloc<double>(nv + N1);
+  c->mb = ar.alloc<double>(N1);
+  c->mx = ar.alloc<double>(N1);
+  c->mt = ar.alloc<double>(N1);
+  c->phia = ar.alloc<double>(N1);
+  c->partial = ar.alloc<double>(64L * 1216);
+  c->sum = ar.alloc<double>(4);
+  CHNSS_CK(cudaHostAlloc(&c->pinned, 8 * sizeof(double), cudaHostAllocDefault));
+  c->kw.init(ar, p.restart, std::max(2 * N1, nv + N1), c->pinned);
+  // Chebyshev coefficients of M_p^-1 (degree 5 on D^-1 M over [1/2, 5/2])
+  {
+    const double theta = 0.5 * (kMassHi3 + kMassLo3), delta = 0.5 * (kMassHi3 - kMassLo3), sigma = theta / delta;
+    std::vector<double> mc(13);
+    mc[0] = 1.0 / theta;
+    double rho = 1.0 / sigma;
+    for (int k = 1; k <= 4; ++k) {
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      mc[1 + 3 * (k - 1)] = 1.0 + rn * rho;
+      mc[2 + 3 * (k - 1)] = -rn * rho;
+      mc[3 + 3 * (k - 1)] = 2.0 * rn / delta;
+      rho = rn;
+    }
+    c->massc = ar.upload(mc);
+  }
+  // hierarchies: P1 (L, AC, X per species, K_p singular) and the velocity operator (scalar)
+  std::vector<const Pattern *> p1s, pvs;
+  std::vector<const int *> d1s, dvs;
+  std::vector<const Transfer *> t1s, tvs;
+  std::vector<const double *> Ls, ACs, K1s, As, Xs[3];
+  for (int l = 0; l < nl; ++l) {
+    const Level3 &L = c->lv[l];
+    p1s.push_back(&L.p1);
+    pvs.push_back(&L.pv);
+    d1s.push_back(L.diag1);
+    dvs.push_back(L.diagv);
+    t1s.push_back(&L.t1);
+    tvs.push_back(&L.tv);
+    Ls.push_back(L.L);
+    ACs.push_back(L.AC);
+    K1s.push_back(L.K1);
+    As.push_back(L.A);
+    for (int sp = 0; sp < 3; ++sp) Xs[sp].push_back(L.X[sp]);
+  }
+  c->hL.init(ar, 0, false, p1s, d1s, Ls, t1s, c->partial);
+  c->hAC.init(ar, 0, false, p1s, d1s, ACs, t1s, c->partial);
+  for (int sp = 0; sp < 3; ++sp) {
+    c->hX[sp].init(ar, 0, false, p1s, d1s, Xs[sp], t1s, c->partial);
+    c->hX[sp].setup(c->s);
+  }
+  c->hKp.init(ar, 0, true, p1s, d1s, K1s, t1s, c->partial);
+  c->hKp.setup(c->s);
+  c->hA.degree = 4;      // as the 2D velocity operator: degree 4 on [hi / 16, hi]
+  c->hA.ratio = 16.0;
+  c->hA.init(ar, 0, false, pvs, dvs, As, tvs, c->partial);
+  CHNSS_CK(cudaStreamSynchronize(c->s));
+}
+
+void assemble3(chnss3_ctx *c, const chnss_state *st) {
+  cudaStream_t s = c->s;
+  const auto &p = c->p;
+  const int nl = (int)c->lv.size();
+  Fields3 f{};
+  for (int i = 0; i < 4; ++i) {
+    f.alpha[i] = p.alpha[i];
+    f.beta[i] = p.beta[i];
+  }
+  f.beta_v = p.beta_v;
+  for (int l = 0; l < nl; ++l) {
+    Level3 &L = c->lv[l];
+    if (l > 0) {
+      const Level3 &Fn = c->lv[l - 1];
+      const double *vf = l == 1 ? st->v : Fn.vl;
+      k3_inject<<<nb3(3L * L.N2), kTPB3, 0, s>>>(Fn.n, 1, vf, L.vl);
+      CHNSS_LAUNCH_CK();
+      for (int i = 0; i < 4; ++i) {
+        const double *mf = l == 1 ? st->mu[i] : Fn.mul + (long)i * Fn.N1;
+        k3_inject<<<nb3(L.N1), kTPB3, 0, s>>>(Fn.n, 0, mf, L.mul + (long)i * L.N1);
+        CHNSS_LAUNCH_CK();
+      }
+    }
+    f.v = l == 0 ? st->v : L.vl;
+    for (int i = 0; i < 4; ++i) f.mu[i] = l == 0 ? st->mu[i] : L.mul + (long)i * L.N1;
+    k3_conv<<<nb3(L.E), kTPB3, 0, s>>>(L.geo, f, 0, 0, c->ebuf);
+    CHNSS_LAUNCH_CK();
+    launch_gather(L.g1, 1, c->ebuf, p.tau, L.M1, 1.0, L.L, s);
+    launch_gather(L.g1, 1, c->ebuf, p.tau, L.ACb, 1.0, L.AC, s);
+    k3_conv<<<nb3(L.E), kTPB3, 0, s>>>(L.geo, f, 1, 1, c->ebuf);
+    CHNSS_LAUNCH_CK();
+    launch_gather(L.gj, 1, c->ebuf, 1.0, L.Aconst, 1.0, L.A, s);
+  }
+  const Level3 &F = c->lv[0];
+  const int N1 = (int)F.N1;
+  const long nv = 3 * F.N2;
+  f.v = st->v;
+  for (int i = 0; i < 4; ++i) f.mu[i] = st->mu[i];
+  for (int i = 0; i < 3; ++i) f.phi[i] = st->phi[i];
+  f.Phi = st->Phi_v;
+  // A_p = M / tau + eta K + C(w)
+  k3_conv<<<nb3(F.E), kTPB3, 0, s>>>(F.geo, f, 0, 1, c->ebuf);
+  CHNSS_LAUNCH_CK();
+  launch_gather(F.g1, 1, c->ebuf, 1.0, c->Apb, 1.0, c->Ap, s);
+  // potential and Korteweg loads
+  k3_loads<<<nb3(F.E), kTPB3, 0, s>>>(F.geo, f, c->ebuf, c->kbuf);
+  CHNSS_LAUNCH_CK();
+  for (int k = 0; k < 5; ++k) launch_gather(c->gl, 1, c->ebuf + 4 * k, 1.0, nullptr, 0.0, c->loads + (long)k * N1, s);
+  launch_gather(c->gk, 3, c->kbuf, 1.0, nullptr, 0.0, c->G, s);
+  // right-hand sides
+  SpmvArgs none;
+  for (int sp = 0; sp < 3; ++sp) {
+    spmv_csr<double>(F.p1, F.M1, 1, st->phi[sp], c->rhs[sp], SPMV_PLAIN, none, s);
+    const double cc = p.tau * p.gamma[sp] / p.beta[sp], sb = sp == 2 ? -p.beta[2] : 0.0;
+    k3_flux_rhs<<<nb3(N1), kTPB3, 0, s>>>(N1, c->loads + (long)sp * N1, c->top, st->phi[2], c->ref, p.evap_rate,
+                                         p.phi_s_inf, sb, cc, c->rhs[sp] + N1);
+    CHNSS_LAUNCH_CK();
+  }
+  spmv_csr<double>(F.p1, F.M1, 1, st->Phi_v, c->rhs[3], SPMV_PLAIN, none, s);
+  k3_ac_rhs<<<nb3(N1), kTPB3, 0, s>>>(N1, c->loads + 4L * N1, c->top, st->phi[2], c->ref, p.evap_rate, p.phi_s_inf,
+                                     p.tau * p.gamma_v, p.ac_top_flux ? p.tau * p.delta_v : 0.0, c->rhs[3]);
+  CHNSS_LAUNCH_CK();
+  spmv_csr<double>(F.pv, c->Mv, 1, st->v, c->rhs[5], SPMV_PLAIN, none, s);
+  vec_axpby(nv, 1.0, c->G, 1.0 / p.tau, c->rhs[5], s);
+  k3_mask<<<nb3(nv), kTPB3, 0, s>>>(nv, c->bnd, c->rhs[5]);
+  CHNSS_LAUNCH_CK();
+  vec_fill(N1, 0.0, c->rhs[5] + nv, s);
+  // SELL copies of the operators FGMRES applies, multigrid setup
+  sell_gather<double>(F.p1.sell, 1, F.L, c->Ls, s);
+  sell_gather<double>(F.p1.sell, 1, F.AC, c->ACs, s);
+  sell_gather<double>(F.p1.sell, 1, c->Ap, c->Aps, s);
+  sell_gather<double>(F.pv.sell, 1, F.A, c->As, s);
+  c->hL.setup(s);
+  c->hAC.setup(s);
+  c->hA.setup(s);
+}
+
+void mg_apply(MGHier<double> &h, long n, const double *r, double *z, cudaStream_t s) {
+  vec_copy(n, r, h.input(), s);
+  h.apply(s);
+  vec_copy(n, h.output(), z, s);
+}
+
+struct CH3Op : LinearOperator {
+  chnss3_ctx *c;
+  int sp;
+  CH3Op(chnss3_ctx *c_, int sp_) : c(c_), sp(sp_) {}
+  long size() const override { return 2 * c->lv[0].N1; }
+  void apply(const double *x, double *y, cudaStream_t s) override {
+    const auto &p = c->p;
+    const double tau = p.tau, g = p.gamma[sp], b = p.beta[sp];
+    spmv_sell_ch(c->lv[0].p1, c->Ls, c->Ks, nullptr, c->Ms, tau * g, tau * g, -tau * g / b, x, y, s);
+  }
+  void precond(const double *r, double *z, cudaStream_t s) override {
+    const long N1 = c->lv[0].N1;
+    mg_apply(c->hL, N1, r, z, s);
+    // S~^-1 = X^-1 M X^-1 (matching factors of eqn::schurCH)
+    MGHier<double> &X = c->hX[sp];
+    vec_copy(N1, r + N1, X.input(), s);
+    X.apply(s);
+    SpmvArgs none;
+    spmv_sell<double>(c->lv[0].p1, c->Ms, 1, X.output(), X.input(), SPMV_PLAIN, none, s);
+    X.apply(s);
+    vec_copy(N1, X.output(), z + N1, s);
+  }
+};
+
+struct AC3Op : LinearOperator {
+  chnss3_ctx *c;
+  explicit AC3Op(chnss3_ctx *c_) : c(c_) {}
+  long size() const override { return c->lv[0].N1; }
+  void apply(const double *x, double *y, cudaStream_t s) override {
+    SpmvArgs none;
+    spmv_sell<double>(c->lv[0].p1, c->ACs, 1, x, y, SPMV_PLAIN, none, s);
+  }
+  void precond(const double *r, double *z, cudaStream_t s) override { mg_apply(c->hAC, c->lv[0].N1, r, z, s); }
+};
+
+struct NS3Op : LinearOperator {
+  chnss3_ctx *c;
+  explicit NS3Op(chnss3_ctx *c_) : c(c_) {}
+  long size() const override { return 3 * c->lv[0].N2 + c->lv[0].N1; }
+  void apply(const double *x, double *y, cudaStream_t s) override {
+    const long nv = 3 * c->lv[0].N2;
+    SpmvArgs none;
+    spmv_sell<double>(c->lv[0].pv, c->As, 1, x, y, SPMV_PLAIN, none, s);
+    spmv_sell<double>(c->pbt, c->Bts, 1, x + nv, y, SPMV_ADD, none, s);
+    spmv_sell<double>(c->pb, c->Bs, 1, x, y + nv, SPMV_PLAIN, none, s);
+  }
+  void precond(const double *r, double *z, cudaStream_t s) override {
+    const Level3 &F = c->lv[0];
+    const long nv = 3 * F.N2, N1 = F.N1;
+    mg_apply(c->hA, nv, r, z, s);
+    // pressure convection-diffusion: M_p^-1 A_p K_p^-1
+    mg_apply(c->hKp, N1, r + nv, c->mt, s);
+    SpmvArgs none;
+    spmv_sell<double>(F.p1, c->Aps, 1, c->mt, c->mb, SPMV_PLAIN, none, s);
+    vec_scale_dinv<double>((int)N1, c->massc, c->dinvM, c->mb, c->mx, s);
+    SpmvArgs a;
+    a.b = c->mb;
+    a.dinv = c->dinvM;
+    double *cur = c->mx, *other = c->mt;
+    for (int k = 1; k <= 4; ++k) {
+      a.coef = c->massc + 1 + 3 * (k - 1);
+      a.w = k == 1 ? nullptr : other;
+      spmv_sell<double>(F.p1, c->Ms, 1, cur, other, SPMV_CHEB, a, s);
+      std::swap(cur, other);
+    }
+    vec_copy(N1, cur, z + nv, s);
+  }
+};
+
+chnss_status step3(chnss3_ctx *c, const chnss_state *in, chnss_state *out, chnss_solve_info *inf) {
+  const auto &p = c->p;
+  cudaStream_t s = c->s;
+  assemble3(c, in);
+  const Level3 &F = c->lv[0];
+  const int N1 = (int)F.N1;
+  const long nv = 3 * F.N2;
+  chnss_status worst = CHNSS_OK;
+  auto keep = [&](chnss_status st) { if (worst == CHNSS_OK) worst = st; };
+  for (int sp = 0; sp < 3; ++sp) {
+    CH3Op op(c, sp);
+    keep(fgmres(op, c->rhs[sp], c->xsol[sp], p.rtol, p.atol, p.maxit, c->kw, &inf[sp], s));
+    vec_copy(N1, c->xsol[sp], out->phi[sp], s);
+    vec_copy(N1, c->xsol[sp] + N1, out->mu[sp], s);
+  }
+  {
+    AC3Op op(c);
+    keep(fgmres(op, c->rhs[3], out->Phi_v, p.rtol, p.atol, p.maxit, c->kw, &inf[3], s));
+  }
+  // air potential: M mu_a = f_a + beta_a K phi_a^{k+1}
+  k3_air<<<nb3(N1), kTPB3, 0, s>>>(N1, out->phi[0], out->phi[1], out->phi[2], c->phia);
+  CHNSS_LAUNCH_CK();
+  k3_flux_rhs<<<nb3(N1), kTPB3, 0, s>>>(N1, c->loads + 3L * N1, c->top, in->phi[2], c->ref, p.evap_rate, p.phi_s_inf,
+                                       p.beta[3], -1.0, c->rhs[4]);
+  CHNSS_LAUNCH_CK();
+  SpmvArgs none;
+  spmv_csr<double>(F.p1, F.K1, 1, c->phia, c->mt, SPMV_PLAIN, none, s);
+  vec_axpby(N1, p.beta[3], c->mt, 1.0, c->rhs[4], s);
+  keep(pcg(F.p1, F.M1, c->dinvM, c->rhs[4], out->mu[3], 1e-12, 1000, c->kw, &inf[4], s));
+  {
+    NS3Op op(c);
+    const double rt = p.ns_rtol > 0.0 ? p.ns_rtol : p.rtol, at = p.ns_rtol > 0.0 ? p.ns_atol : p.atol;
+    keep(fgmres(op, c->rhs[5], c->xsol[5], rt, at, p.maxit, c->kw, &inf[5], s));
+  }
+  vec_copy(nv, c->xsol[5], out->v, s);
+  vec_copy(N1, c->xsol[5] + nv, out->p, s);
+  // zero-mean pressure: p -= (1^T M p) / (1^T M 1), 1^T M 1 = |box| = 1
+  spmv_csr<double>(F.p1, F.M1, 1, out->p, c->mt, SPMV_PLAIN, none, s);
+  vsum<double>(N1, c->mt, c->sum, c->partial, s);
+  k3_shift<<<nb3(N1), kTPB3, 0, s>>>(N1, out->p, c->sum, 1.0);
+  CHNSS_LAUNCH_CK();
+  CHNSS_CK(cudaStreamSynchronize(s));
+  return worst;
+}
+
+}  // namespace
+}  // namespace chnss
+
+extern "C" chnss_status chnss3_ctx_create(int n, const chnss_params *params, void *cuda_stream, chnss3_ctx_t *out) {
+  using namespace chnss;
+  chnss3_ctx *c = nullptr;
+  try {
+    if (!params || !out) throw Error{CHNSS_ERR_ARG, "null argument"};
+    if (n < 2 || n % 2 || n > 96) throw Error{CHNSS_ERR_ARG, "3D meshes: n even, 2 <= n <= 96"};
+    const chnss_params &p = *params;
+    if (p.model != 0 || p.mobility_kind != 0 || p.precision != 0 || p.inner_rtol != 0.0)
+      throw Error{CHNSS_ERR_ARG, "the 3D step covers model 0, constant mobility, FP64, one V-cycle per block"};
+    if (!(p.tau > 0) || !(p.eta > 0) || p.restart < 1 || p.restart > 64 || p.maxit < 1)
+      throw Error{CHNSS_ERR_ARG, "invalid parameters"};
+    for (int i = 0; i < 3; ++i)
+      if (!(p.beta[i] > 0) || !(p.gamma[i] > 0)) throw Error{CHNSS_ERR_ARG, "beta_i, gamma_i must be > 0"};
+    c = new chnss3_ctx;
+    c->p = p;
+    if (cuda_stream) {
+      c->s = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+      CHNSS_CK(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    create3(c, n);
+    *out = c;
+    return CHNSS_OK;
+  } catch (const Error &e) {
+    delete c;
+    set_global_error(e.msg);
+    return e.status;
+  } catch (const std::exception &e) {
+    delete c;
+    set_global_error(e.what());
+    return CHNSS_ERR_ARG;
+  }
+}
+
+extern "C" chnss_status chnss3_ctx_destroy(chnss3_ctx_t ctx) {
+  delete ctx;
+  return CHNSS_OK;
+}
+
+extern "C" chnss_status chnss3_sizes(chnss3_ctx_t ctx, int *N1, int *N2) {
+  if (!ctx || !N1 || !N2) {
+    chnss::set_global_error("null argument");
+    return CHNSS_ERR_ARG;
+  }
+  *N1 = (int)ctx->lv[0].N1;
+  *N2 = (int)ctx->lv[0].N2;
+  return CHNSS_OK;
+}
+
+extern "C" chnss_status chnss3_step(chnss3_ctx_t ctx, const chnss_state *in, chnss_state *out,
+                                   chnss_solve_info *info) {
+  using namespace chnss;
+  if (!ctx) {
+    set_global_error("null context");
+    return CHNSS_ERR_ARG;
+  }
+  try {
+    const chnss_state *states[2] = {in, out};
+    for (const chnss_state *st : states) {
+      if (!st || !st->Phi_v || !st->v || !st->p) throw Error{CHNSS_ERR_ARG, "null state"};
+      for (int k = 0; k < 3; ++k) if (!st->phi[k]) throw Error{CHNSS_ERR_ARG, "null phi pointer"};
+      for (int k = 0; k < 4; ++k) if (!st->mu[k]) throw Error{CHNSS_ERR_ARG, "null mu pointer"};
+    }
+    chnss_solve_info loc[6];
+    const chnss_status st = step3(ctx, in, out, info ? info : loc);
+    if (st != CHNSS_OK) ctx->err = "a solve of the 3D step did not converge cleanly";
+    return st;
+  } catch (const Error &e) {
+    ctx->err = e.msg;
+    return e.status;
+  }
+}
+
+extern "C" const char *chnss3_last_error(chnss3_ctx_t ctx) { return ctx ? ctx->err.c_str() : ""; }

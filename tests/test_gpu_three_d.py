@@ -1,0 +1,84 @@
+"""The 3D step on the GPU (chnss3_step, Kuhn tetrahedra) against the 3D
+oracle: every solve of a step (relative L2 <= 1e-9 when the Krylov iteration
+counts agree, counts within +-1), two steps (the second with flow), a finer
+mesh, determinism and the parameter checks."""
+import numpy as np
+import pytest
+
+from oracle import three_d as t3
+from paper_2501_11767_gb300 import chnss, inputs
+
+pytestmark = pytest.mark.gpu
+
+SOLVE_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    return torch
+
+
+def rel(a, b):
+    a, b = np.ravel(a), np.ravel(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _params(**kw):
+    p = inputs.default_params()
+    p.update(alpha=[1e-2] * 4)
+    p.update(kw)
+    return p
+
+
+def _compare(torch, n, params, seed, steps=2):
+    o = t3.Oracle3D(n, params)
+    ctx = chnss.Context3(n, params)
+    st = inputs.initial_state_3d(n, seed=seed)
+    for k in range(steps):
+        ref, rinfo = o.step(st)
+        out, info, status = ctx.step(chnss.state_to_device(st))
+        torch.cuda.synchronize()
+        assert status == 0
+        got = chnss.state_to_numpy(out)
+        groups = [(name, (("phi", i), ("mu", i))) for i, name in enumerate(("ch_p", "ch_N", "ch_s"))]
+        groups += [("ac", (("Phi_v", None),)), ("ns", (("v", None), ("p", None)))]
+        for name, keys in groups:
+            assert info[name]["converged"], (name, info[name])
+            assert abs(info[name]["iters"] - rinfo[name]["iters"]) <= 1, (k, name, info[name], rinfo[name])
+            if info[name]["iters"] == rinfo[name]["iters"]:
+                g = np.concatenate([np.ravel(got[a] if i is None else got[a][i]) for a, i in keys])
+                r = np.concatenate([np.ravel(ref[a] if i is None else ref[a][i]) for a, i in keys])
+                assert rel(g, r) <= SOLVE_TOL, (k, name, rel(g, r))
+        assert rel(got["mu"][3], ref["mu"][3]) <= SOLVE_TOL
+        st = ref
+    return ctx
+
+
+def test_step_3d_matches_oracle(torch):
+    _compare(torch, 4, _params(), seed=1)
+
+
+def test_step_3d_finer_mesh(torch):
+    """8^3 cubes: three multigrid levels (8, 4, 2)."""
+    _compare(torch, 8, _params(), seed=2, steps=1)
+
+
+def test_step_3d_is_deterministic(torch):
+    n = 4
+    ctx = chnss.Context3(n, _params())
+    st = chnss.state_to_device(inputs.initial_state_3d(n, seed=5))
+    a = chnss.state_to_numpy(ctx.step(st)[0])
+    b = chnss.state_to_numpy(ctx.step(st)[0])
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("bad", [dict(mobility_kind=1), dict(precision=1), dict(model=1)])
+def test_step_3d_parameter_errors(torch, bad):
+    with pytest.raises(chnss.ChnssError):
+        chnss.Context3(4, _params(**bad))
+    with pytest.raises(chnss.ChnssError):
+        chnss.Context3(3, _params())            # n must be even
