@@ -463,6 +463,58 @@ def run_adjoint(args):
     print(json.dumps(out))
 
 
+THREE_D_METRIC = "time steps/s of the 3D step on the Kuhn mesh of {n}^3 cubes (FP64, FGMRES to 1e-8)"
+
+
+def run_three_d(args):
+    """The 3D workload (the paper's 3D runs, Sec. 5, on a Kuhn tetrahedral
+    mesh): the film parameter set with the 3D step (chnss3_step), FP64,
+    solves one after the other; CUDA events around the timed steps, inputs
+    resident on the device."""
+    import torch
+
+    from paper_2501_11767_gb300 import chnss, inputs
+
+    torch.cuda.set_device(0)
+    n = args.three_d_n
+    p = inputs.default_params()
+    p.update(tau=1e-4)                 # the 3D figures' time step (Sec. 5)
+    stream = torch.cuda.current_stream()
+    ctx = chnss.Context3(n, p, stream)
+    a = chnss.state_to_device(inputs.initial_state_3d(n, seed=0))
+    b = ctx.new_state()
+    for _ in range(args.warmup):
+        ctx.step(a, b)
+        a, b = b, a
+    torch.cuda.synchronize()
+    sampler = ClockSampler(_device_uuid(torch, 0))
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        _, info, _ = ctx.step(a, b)
+        infos.append(info)
+        a, b = b, a
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    out = {
+        "metric": THREE_D_METRIC.format(n=n), "value": round(args.steps / (ms / 1e3), 4), "unit": "steps/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded SplitMix64 noise on phi_p, phi_NFA)",
+        "config": {"workload": f"film3d{n}_fp64", "n": n, "p1_nodes": ctx.N1, "p2_nodes": ctx.N2,
+                   "velocity_dofs": 3 * ctx.N2, "tau": p["tau"], "rtol": p["rtol"], "parallelism": "single GPU",
+                   "l2": "inputs larger than L2" if 3 * ctx.N2 * 8 * 100 > 129e6 else "working set near L2"},
+        "iters_mean": {k: round(sum(i[k]["iters"] for i in infos) / len(infos), 2) for k in infos[-1]},
+        "converged": all(i[k]["converged"] for i in infos for k in i),
+        "clocks": clocks,
+    }
+    print(json.dumps(out))
+
+
 def run_sweep(args):
     """Batched parameter sweep: independent instances of uneven mesh size
     and evaporation rate, one context (and stream) each, advanced together
@@ -613,6 +665,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="batched 64-instance parameter sweep instead")
     ap.add_argument("--adjoint", action="store_true", help="40-step gradient on 256x256 instead")
+    ap.add_argument("--three-d", action="store_true", help="the 3D step on a Kuhn mesh instead")
+    ap.add_argument("--three-d-n", type=int, default=32)
     ap.add_argument("--sweep-count", type=int, default=64)
     ap.add_argument("--sweep-threads", type=int, default=0)
     ap.add_argument("--sweep-concurrent-steps", action="store_true")
@@ -632,6 +686,9 @@ def main():
         return
     if args.adjoint:
         run_adjoint(args)
+        return
+    if args.three_d:
+        run_three_d(args)
         return
     run_gpu(args)
 
