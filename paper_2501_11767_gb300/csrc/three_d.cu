@@ -7,6 +7,7 @@
 // step use the same code.
 #include <algorithm>
 #include <array>
+#include <memory>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -671,6 +672,15 @@ struct Level3 {
   double *vl = nullptr, *mul = nullptr;   // injected v (3 N2) and mu (4 N1), levels >= 1
 };
 
+// The block preconditioners' hierarchies and scratch in the arithmetic of
+// precision 0 (T = double) or 1 / 2 (T = float; 2: the velocity hierarchy's
+// values stored in BF16)
+template <typename T>
+struct Prec3 {
+  MGHier<T> L, AC, X[3], Kp, A;
+  T *Ms = nullptr, *Aps = nullptr, *mdinv = nullptr, *mb = nullptr, *mx = nullptr, *mt = nullptr;
+};
+
 }  // namespace
 }  // namespace chnss
 
@@ -685,11 +695,12 @@ struct chnss3_ctx {
   int *bnd = nullptr;                           // fine P2 boundary mask
   int ref = 0;
   double *Bs = nullptr, *Bts = nullptr, *Mv = nullptr, *Apb = nullptr, *Ap = nullptr, *top = nullptr;
-  double *Ls = nullptr, *Ks = nullptr, *Ms = nullptr, *ACs = nullptr, *As = nullptr, *Aps = nullptr;
+  double *Ls = nullptr, *Ks = nullptr, *Ms = nullptr, *ACs = nullptr, *As = nullptr;
   double *ebuf = nullptr, *kbuf = nullptr, *loads = nullptr, *G = nullptr, *dinvM = nullptr, *massc = nullptr;
-  double *rhs[6] = {}, *xsol[6] = {}, *mb = nullptr, *mx = nullptr, *mt = nullptr, *phia = nullptr;
+  double *rhs[6] = {}, *xsol[6] = {}, *mt = nullptr, *phia = nullptr;
   double *partial = nullptr, *sum = nullptr, *pinned = nullptr;
-  chnss::MGHier<double> hL, hAC, hX[3], hKp, hA;
+  std::unique_ptr<chnss::Prec3<double>> p64;
+  std::unique_ptr<chnss::Prec3<float>> p32;
   chnss::KrylovWork kw;
   std::string err;
   ~chnss3_ctx() {
@@ -839,6 +850,37 @@ void build_level3(chnss3_ctx *c, Level3 &L, int n, bool fine, const Mesh3Host *c
   c->dinvM = ar.upload(dinv);
 }
 
+template <typename T>
+void init_prec3(chnss3_ctx *c, Prec3<T> &P, const std::vector<const Pattern *> &p1s,
+                const std::vector<const int *> &d1s, const std::vector<const Transfer *> &t1s,
+                const std::vector<const Pattern *> &pvs, const std::vector<const int *> &dvs,
+                const std::vector<const Transfer *> &tvs, const std::vector<const double *> &Ls,
+                const std::vector<const double *> &ACs, const std::vector<const double *> &K1s,
+                const std::vector<const double *> &As, const std::vector<const double *> *Xs) {
+  Arena &ar = c->ar;
+  const Level3 &F = c->lv[0];
+  P.L.init(ar, 0, false, p1s, d1s, Ls, t1s, c->partial);
+  P.AC.init(ar, 0, false, p1s, d1s, ACs, t1s, c->partial);
+  for (int sp = 0; sp < 3; ++sp) {
+    P.X[sp].init(ar, 0, false, p1s, d1s, Xs[sp], t1s, c->partial);
+    P.X[sp].setup(c->s);
+  }
+  P.Kp.init(ar, 0, true, p1s, d1s, K1s, t1s, c->partial);
+  P.Kp.setup(c->s);
+  P.A.degree = 4;      // as the 2D velocity operator: degree 4 on [hi / 16, hi]
+  P.A.ratio = 16.0;
+  P.A.init(ar, 0, false, pvs, dvs, As, tvs, c->partial);
+  const long N1 = F.N1, nent1 = F.p1.sell.nent;
+  P.Ms = ar.alloc<T>(nent1);
+  P.Aps = ar.alloc<T>(nent1);
+  sell_gather<T>(F.p1.sell, 1, F.M1, P.Ms, c->s);
+  P.mdinv = ar.alloc<T>(N1);
+  vec_convert<double, T>(N1, c->dinvM, P.mdinv, c->s);
+  P.mb = ar.alloc<T>(N1);
+  P.mx = ar.alloc<T>(N1);
+  P.mt = ar.alloc<T>(N1);
+}
+
 void create3(chnss3_ctx *c, int n) {
   Arena &ar = c->ar;
   const auto &p = c->p;
@@ -864,7 +906,6 @@ void create3(chnss3_ctx *c, int n) {
   c->Ks = ar.alloc<double>(nent1);
   c->Ms = ar.alloc<double>(nent1);
   c->ACs = ar.alloc<double>(nent1);
-  c->Aps = ar.alloc<double>(nent1);
   c->As = ar.alloc<double>(nentv);
   sell_gather<double>(F.p1.sell, 1, F.K1, c->Ks, c->s);
   sell_gather<double>(F.p1.sell, 1, F.M1, c->Ms, c->s);
@@ -876,8 +917,6 @@ void create3(chnss3_ctx *c, int n) {
   c->rhs[4] = ar.alloc<double>(N1);
   c->rhs[5] = ar.alloc<double>(nv + N1);
   c->xsol[5] = ar.alloc<double>(nv + N1);
-  c->mb = ar.alloc<double>(N1);
-  c->mx = ar.alloc<double>(N1);
   c->mt = ar.alloc<double>(N1);
   c->phia = ar.alloc<double>(N1);
   c->partial = ar.alloc<double>(64L * 1216);
@@ -918,18 +957,23 @@ void create3(chnss3_ctx *c, int n) {
     As.push_back(L.A);
     for (int sp = 0; sp < 3; ++sp) Xs[sp].push_back(L.X[sp]);
   }
-  c->hL.init(ar, 0, false, p1s, d1s, Ls, t1s, c->partial);
-  c->hAC.init(ar, 0, false, p1s, d1s, ACs, t1s, c->partial);
-  for (int sp = 0; sp < 3; ++sp) {
-    c->hX[sp].init(ar, 0, false, p1s, d1s, Xs[sp], t1s, c->partial);
-    c->hX[sp].setup(c->s);
+  if (p.precision == 0) {
+    c->p64.reset(new Prec3<double>);
+    init_prec3(c, *c->p64, p1s, d1s, t1s, pvs, dvs, tvs, Ls, ACs, K1s, As, Xs);
+  } else {
+    c->p32.reset(new Prec3<float>);
+    c->p32->A.bf16 = p.precision == 2;
+    init_prec3(c, *c->p32, p1s, d1s, t1s, pvs, dvs, tvs, Ls, ACs, K1s, As, Xs);
   }
-  c->hKp.init(ar, 0, true, p1s, d1s, K1s, t1s, c->partial);
-  c->hKp.setup(c->s);
-  c->hA.degree = 4;      // as the 2D velocity operator: degree 4 on [hi / 16, hi]
-  c->hA.ratio = 16.0;
-  c->hA.init(ar, 0, false, pvs, dvs, As, tvs, c->partial);
   CHNSS_CK(cudaStreamSynchronize(c->s));
+}
+
+template <typename T>
+void setup_prec3(chnss3_ctx *c, Prec3<T> &P, cudaStream_t s) {
+  P.L.setup(s);
+  P.AC.setup(s);
+  P.A.setup(s);
+  sell_gather<T>(c->lv[0].p1.sell, 1, c->Ap, P.Aps, s);
 }
 
 void assemble3(chnss3_ctx *c, const chnss_state *st) {
@@ -1002,17 +1046,54 @@ void assemble3(chnss3_ctx *c, const chnss_state *st) {
   // SELL copies of the operators FGMRES applies, multigrid setup
   sell_gather<double>(F.p1.sell, 1, F.L, c->Ls, s);
   sell_gather<double>(F.p1.sell, 1, F.AC, c->ACs, s);
-  sell_gather<double>(F.p1.sell, 1, c->Ap, c->Aps, s);
   sell_gather<double>(F.pv.sell, 1, F.A, c->As, s);
-  c->hL.setup(s);
-  c->hAC.setup(s);
-  c->hA.setup(s);
+  if (c->p32) setup_prec3(c, *c->p32, s);
+  else setup_prec3(c, *c->p64, s);
 }
 
-void mg_apply(MGHier<double> &h, long n, const double *r, double *z, cudaStream_t s) {
-  vec_copy(n, r, h.input(), s);
+template <typename T>
+void mg_apply(MGHier<T> &h, long n, const double *r, double *z, cudaStream_t s) {
+  vec_convert<double, T>(n, r, h.input(), s);
   h.apply(s);
-  vec_copy(n, h.output(), z, s);
+  vec_convert<T, double>(n, h.output(), z, s);
+}
+
+template <typename T>
+void prec_ch3(chnss3_ctx *c, Prec3<T> &P, int sp, const double *r, double *z, cudaStream_t s) {
+  const long N1 = c->lv[0].N1;
+  mg_apply(P.L, N1, r, z, s);
+  // S~^-1 = X^-1 M X^-1 (matching factors of eqn::schurCH)
+  MGHier<T> &X = P.X[sp];
+  vec_convert<double, T>(N1, r + N1, X.input(), s);
+  X.apply(s);
+  SpmvArgs none;
+  spmv_sell<T>(c->lv[0].p1, P.Ms, 1, X.output(), X.input(), SPMV_PLAIN, none, s);
+  X.apply(s);
+  vec_convert<T, double>(N1, X.output(), z + N1, s);
+}
+
+template <typename T>
+void prec_ns3(chnss3_ctx *c, Prec3<T> &P, const double *r, double *z, cudaStream_t s) {
+  const Level3 &F = c->lv[0];
+  const long nv = 3 * F.N2, N1 = F.N1;
+  mg_apply(P.A, nv, r, z, s);
+  // pressure convection-diffusion: M_p^-1 A_p K_p^-1
+  vec_convert<double, T>(N1, r + nv, P.Kp.input(), s);
+  P.Kp.apply(s);
+  SpmvArgs none;
+  spmv_sell<T>(F.p1, P.Aps, 1, P.Kp.output(), P.mb, SPMV_PLAIN, none, s);
+  vec_scale_dinv<T>((int)N1, c->massc, P.mdinv, P.mb, P.mx, s);
+  SpmvArgs a;
+  a.b = P.mb;
+  a.dinv = P.mdinv;
+  T *cur = P.mx, *other = P.mt;
+  for (int k = 1; k <= 4; ++k) {
+    a.coef = c->massc + 1 + 3 * (k - 1);
+    a.w = k == 1 ? nullptr : other;
+    spmv_sell<T>(F.p1, P.Ms, 1, cur, other, SPMV_CHEB, a, s);
+    std::swap(cur, other);
+  }
+  vec_convert<T, double>(N1, cur, z + nv, s);
 }
 
 struct CH3Op : LinearOperator {
@@ -1026,16 +1107,8 @@ struct CH3Op : LinearOperator {
     spmv_sell_ch(c->lv[0].p1, c->Ls, c->Ks, nullptr, c->Ms, tau * g, tau * g, -tau * g / b, x, y, s);
   }
   void precond(const double *r, double *z, cudaStream_t s) override {
-    const long N1 = c->lv[0].N1;
-    mg_apply(c->hL, N1, r, z, s);
-    // S~^-1 = X^-1 M X^-1 (matching factors of eqn::schurCH)
-    MGHier<double> &X = c->hX[sp];
-    vec_copy(N1, r + N1, X.input(), s);
-    X.apply(s);
-    SpmvArgs none;
-    spmv_sell<double>(c->lv[0].p1, c->Ms, 1, X.output(), X.input(), SPMV_PLAIN, none, s);
-    X.apply(s);
-    vec_copy(N1, X.output(), z + N1, s);
+    if (c->p32) prec_ch3(c, *c->p32, sp, r, z, s);
+    else prec_ch3(c, *c->p64, sp, r, z, s);
   }
 };
 
@@ -1047,7 +1120,10 @@ struct AC3Op : LinearOperator {
     SpmvArgs none;
     spmv_sell<double>(c->lv[0].p1, c->ACs, 1, x, y, SPMV_PLAIN, none, s);
   }
-  void precond(const double *r, double *z, cudaStream_t s) override { mg_apply(c->hAC, c->lv[0].N1, r, z, s); }
+  void precond(const double *r, double *z, cudaStream_t s) override {
+    if (c->p32) mg_apply(c->p32->AC, c->lv[0].N1, r, z, s);
+    else mg_apply(c->p64->AC, c->lv[0].N1, r, z, s);
+  }
 };
 
 struct NS3Op : LinearOperator {
@@ -1062,25 +1138,8 @@ struct NS3Op : LinearOperator {
     spmv_sell<double>(c->pb, c->Bs, 1, x, y + nv, SPMV_PLAIN, none, s);
   }
   void precond(const double *r, double *z, cudaStream_t s) override {
-    const Level3 &F = c->lv[0];
-    const long nv = 3 * F.N2, N1 = F.N1;
-    mg_apply(c->hA, nv, r, z, s);
-    // pressure convection-diffusion: M_p^-1 A_p K_p^-1
-    mg_apply(c->hKp, N1, r + nv, c->mt, s);
-    SpmvArgs none;
-    spmv_sell<double>(F.p1, c->Aps, 1, c->mt, c->mb, SPMV_PLAIN, none, s);
-    vec_scale_dinv<double>((int)N1, c->massc, c->dinvM, c->mb, c->mx, s);
-    SpmvArgs a;
-    a.b = c->mb;
-    a.dinv = c->dinvM;
-    double *cur = c->mx, *other = c->mt;
-    for (int k = 1; k <= 4; ++k) {
-      a.coef = c->massc + 1 + 3 * (k - 1);
-      a.w = k == 1 ? nullptr : other;
-      spmv_sell<double>(F.p1, c->Ms, 1, cur, other, SPMV_CHEB, a, s);
-      std::swap(cur, other);
-    }
-    vec_copy(N1, cur, z + nv, s);
+    if (c->p32) prec_ns3(c, *c->p32, r, z, s);
+    else prec_ns3(c, *c->p64, r, z, s);
   }
 };
 
@@ -1139,8 +1198,8 @@ extern "C" chnss_status chnss3_ctx_create(int n, const chnss_params *params, voi
     if (!params || !out) throw Error{CHNSS_ERR_ARG, "null argument"};
     if (n < 2 || n % 2 || n > 96) throw Error{CHNSS_ERR_ARG, "3D meshes: n even, 2 <= n <= 96"};
     const chnss_params &p = *params;
-    if (p.model != 0 || p.mobility_kind != 0 || p.precision != 0 || p.inner_rtol != 0.0)
-      throw Error{CHNSS_ERR_ARG, "the 3D step covers model 0, constant mobility, FP64, one V-cycle per block"};
+    if (p.model != 0 || p.mobility_kind != 0 || p.inner_rtol != 0.0 || p.precision < 0 || p.precision > 2)
+      throw Error{CHNSS_ERR_ARG, "the 3D step covers model 0, constant mobility, one V-cycle per block"};
     if (!(p.tau > 0) || !(p.eta > 0) || p.restart < 1 || p.restart > 64 || p.maxit < 1)
       throw Error{CHNSS_ERR_ARG, "invalid parameters"};
     for (int i = 0; i < 3; ++i)

@@ -76,9 +76,35 @@ def test_step_3d_is_deterministic(torch):
         assert np.array_equal(a[k], b[k]), k
 
 
-@pytest.mark.parametrize("bad", [dict(mobility_kind=1), dict(precision=1), dict(model=1)])
+@pytest.mark.parametrize("bad", [dict(mobility_kind=1), dict(precision=3), dict(model=1)])
 def test_step_3d_parameter_errors(torch, bad):
     with pytest.raises(chnss.ChnssError):
         chnss.Context3(4, _params(**bad))
     with pytest.raises(chnss.ChnssError):
         chnss.Context3(3, _params())            # n must be even
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_step_3d_mixed_precision(torch, precision):
+    """FP32 multigrid (precision 2: velocity hierarchy values in BF16) inside
+    FP64 FGMRES: the 1e-8 residual is reached, and at an outer tolerance of
+    1e-10 the step stays within 1e-6 of the oracle solved to 1e-12."""
+    n = 8
+    p = _params()
+    o = t3.Oracle3D(n, dict(p, rtol=1e-12))
+    ctx8 = chnss.Context3(n, dict(p, precision=precision))
+    ctx10 = chnss.Context3(n, dict(p, precision=precision, rtol=1e-10))
+    st = inputs.initial_state_3d(n, seed=7)
+    for _ in range(2):
+        ref, _ = o.step(st)
+        dev = chnss.state_to_device(st)
+        _, info8, status8 = ctx8.step(dev)
+        out10, _, status10 = ctx10.step(dev)
+        assert status8 == 0 and status10 == 0
+        for name, i in info8.items():
+            if name != "mu_a":
+                assert i["converged"] and i["rel_residual"] <= 1e-8, (name, i)
+        got = chnss.state_to_numpy(out10)
+        for key in ("phi", "mu", "Phi_v", "v", "p"):
+            assert rel(got[key], ref[key]) <= 1e-6, key
+        st = ref
