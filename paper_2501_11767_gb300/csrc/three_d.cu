@@ -702,8 +702,16 @@ struct chnss3_ctx {
   std::unique_ptr<chnss::Prec3<double>> p64;
   std::unique_ptr<chnss::Prec3<float>> p32;
   chnss::KrylovWork kw;
+  // captured preconditioners (0..2 CH species, 3 AC, 4 Oseen) replayed on s
+  // from fixed staging vectors; captured on a private stream
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double *pin[5] = {}, *pout[5] = {};
   std::string err;
   ~chnss3_ctx() {
+    for (cudaGraphExec_t g : gexec)
+      if (g) cudaGraphExecDestroy(g);
+    if (cap) cudaStreamDestroy(cap);
     if (pinned) cudaFreeHost(pinned);
     if (own_stream && s) cudaStreamDestroy(s);
   }
@@ -918,6 +926,12 @@ void create3(chnss3_ctx *c, int n) {
   c->rhs[5] = ar.alloc<double>(nv + N1);
   c->xsol[5] = ar.alloc<double>(nv + N1);
   c->mt = ar.alloc<double>(N1);
+  for (int g = 0; g < 5; ++g) {
+    const long len = g < 3 ? 2 * N1 : g == 3 ? N1 : nv + N1;
+    c->pin[g] = ar.alloc<double>(len);
+    c->pout[g] = ar.alloc<double>(len);
+  }
+  CHNSS_CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   c->phia = ar.alloc<double>(N1);
   c->partial = ar.alloc<double>(64L * 1216);
   c->sum = ar.alloc<double>(4);
@@ -1096,6 +1110,42 @@ void prec_ns3(chnss3_ctx *c, Prec3<T> &P, const double *r, double *z, cudaStream
   vec_convert<T, double>(N1, cur, z + nv, s);
 }
 
+void prec_body3(chnss3_ctx *c, int g, const double *r, double *z, cudaStream_t s) {
+  if (g < 3) {
+    if (c->p32) prec_ch3(c, *c->p32, g, r, z, s);
+    else prec_ch3(c, *c->p64, g, r, z, s);
+  } else if (g == 3) {
+    if (c->p32) mg_apply(c->p32->AC, c->lv[0].N1, r, z, s);
+    else mg_apply(c->p64->AC, c->lv[0].N1, r, z, s);
+  } else {
+    if (c->p32) prec_ns3(c, *c->p32, r, z, s);
+    else prec_ns3(c, *c->p64, r, z, s);
+  }
+}
+
+// z = P_g r through the captured graph of preconditioner g (captured at the
+// first application; the hierarchies' values change in place between steps)
+void run_prec3(chnss3_ctx *c, int g, long n, const double *r, double *z, cudaStream_t s) {
+  vec_copy(n, r, c->pin[g], s);
+  if (!c->gexec[g]) {
+    cudaGraph_t graph = nullptr;
+    CHNSS_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    try {
+      prec_body3(c, g, c->pin[g], c->pout[g], c->cap);
+    } catch (...) {
+      cudaStreamEndCapture(c->cap, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    CHNSS_CK(cudaStreamEndCapture(c->cap, &graph));
+    const cudaError_t e = cudaGraphInstantiate(&c->gexec[g], graph, 0);
+    cudaGraphDestroy(graph);
+    CHNSS_CK(e);
+  }
+  CHNSS_CK(cudaGraphLaunch(c->gexec[g], s));
+  vec_copy(n, c->pout[g], z, s);
+}
+
 struct CH3Op : LinearOperator {
   chnss3_ctx *c;
   int sp;
@@ -1106,10 +1156,7 @@ struct CH3Op : LinearOperator {
     const double tau = p.tau, g = p.gamma[sp], b = p.beta[sp];
     spmv_sell_ch(c->lv[0].p1, c->Ls, c->Ks, nullptr, c->Ms, tau * g, tau * g, -tau * g / b, x, y, s);
   }
-  void precond(const double *r, double *z, cudaStream_t s) override {
-    if (c->p32) prec_ch3(c, *c->p32, sp, r, z, s);
-    else prec_ch3(c, *c->p64, sp, r, z, s);
-  }
+  void precond(const double *r, double *z, cudaStream_t s) override { run_prec3(c, sp, 2 * c->lv[0].N1, r, z, s); }
 };
 
 struct AC3Op : LinearOperator {
@@ -1120,10 +1167,7 @@ struct AC3Op : LinearOperator {
     SpmvArgs none;
     spmv_sell<double>(c->lv[0].p1, c->ACs, 1, x, y, SPMV_PLAIN, none, s);
   }
-  void precond(const double *r, double *z, cudaStream_t s) override {
-    if (c->p32) mg_apply(c->p32->AC, c->lv[0].N1, r, z, s);
-    else mg_apply(c->p64->AC, c->lv[0].N1, r, z, s);
-  }
+  void precond(const double *r, double *z, cudaStream_t s) override { run_prec3(c, 3, c->lv[0].N1, r, z, s); }
 };
 
 struct NS3Op : LinearOperator {
@@ -1138,8 +1182,7 @@ struct NS3Op : LinearOperator {
     spmv_sell<double>(c->pb, c->Bs, 1, x, y + nv, SPMV_PLAIN, none, s);
   }
   void precond(const double *r, double *z, cudaStream_t s) override {
-    if (c->p32) prec_ns3(c, *c->p32, r, z, s);
-    else prec_ns3(c, *c->p64, r, z, s);
+    run_prec3(c, 4, 3 * c->lv[0].N2 + c->lv[0].N1, r, z, s);
   }
 };
 
