@@ -306,10 +306,11 @@ chnss_status chnss3_host_operator(int n, int which, const chnss_params *params, 
  * the air potential by Jacobi-PCG, Oseen with diag(MG(A), M_p^-1 A_p K_p^-1),
  * FGMRES(restart) with CGS2, geometric multigrid on the nested Kuhn meshes)
  * with no-slip on every face and evaporation through the top face z = 1
- * (reference point (1/2, 1/2, 1)).  Covers model 0, constant mobility, FP64
- * (precision 0) and one V-cycle per block (inner_rtol 0); other parameter
- * sets get CHNSS_ERR_ARG.  The solves run one after the other on the
- * context's stream (cuda_stream, or a library stream when NULL).
+ * (reference point (1/2, 1/2, 1)).  Covers model 0, constant mobility,
+ * precision 0, 1 or 2 and one V-cycle per block (inner_rtol 0); other parameter
+ * sets get CHNSS_ERR_ARG.  Assembly runs on the context's stream
+ * (cuda_stream, or a library stream when NULL), the solve groups on library
+ * streams after it (chnss3_set_step_concurrency).
  * States: chnss_state with DEVICE arrays of the 3D sizes (chnss3_sizes):
  * phi[3], mu[4], Phi_v, p of N1 = (n+1)^3, v of 3 N2 = 3 (2n+1)^3.
  * info[6] (optional): the six solves as in chnss_step.  chnss3_step
@@ -319,6 +320,10 @@ chnss_status chnss3_ctx_create(int n, const chnss_params *params, void *cuda_str
 chnss_status chnss3_ctx_destroy(chnss3_ctx_t ctx);
 chnss_status chnss3_sizes(chnss3_ctx_t ctx, int *N1, int *N2);
 chnss_status chnss3_step(chnss3_ctx_t ctx, const chnss_state *in, chnss_state *out, chnss_solve_info *info);
+/* on != 0 (default): the three solve groups (CH species then the air
+ * potential; AC; Oseen) of chnss3_step run concurrently on library streams;
+ * 0: one after the other.  Results are bitwise the same. */
+chnss_status chnss3_set_step_concurrency(chnss3_ctx_t ctx, int on);
 const char *chnss3_last_error(chnss3_ctx_t ctx);
 
 /* Mass-matrix solve that allocates nothing.  The paper has no counterpart:

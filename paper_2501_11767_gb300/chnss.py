@@ -130,6 +130,7 @@ EXPORTS = {
     "chnss3_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.POINTER(State),
                                    ctypes.POINTER(SolveInfo)]),
     "chnss3_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "chnss3_set_step_concurrency": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss3_host_operator": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params), ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_longlong), ctypes.c_void_p, ctypes.c_void_p,
@@ -410,6 +411,9 @@ class Context3:
         if getattr(self, "_h", None):
             load().chnss3_ctx_destroy(self._h)
             self._h = None
+
+    def set_step_concurrency(self, on: bool):
+        _check(load().chnss3_set_step_concurrency(self._h, 1 if on else 0))
 
     def new_state(self):
         import torch

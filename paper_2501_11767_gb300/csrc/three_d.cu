@@ -7,7 +7,9 @@
 // step use the same code.
 #include <algorithm>
 #include <array>
+#include <exception>
 #include <memory>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -701,17 +703,28 @@ struct chnss3_ctx {
   double *partial = nullptr, *sum = nullptr, *pinned = nullptr;
   std::unique_ptr<chnss::Prec3<double>> p64;
   std::unique_ptr<chnss::Prec3<float>> p32;
-  chnss::KrylovWork kw;
-  // captured preconditioners (0..2 CH species, 3 AC, 4 Oseen) replayed on s
-  // from fixed staging vectors; captured on a private stream
-  cudaStream_t cap = nullptr;
+  chnss::KrylovWork kw, kwc, kwa;               // Oseen; CH and air potential; AC
+  double *mt0 = nullptr;                        // air-potential scratch (CH group)
+  // solve groups (CH + air potential, AC, Oseen) on their own streams, host threads
+  bool concurrent = true;
+  cudaStream_t sx[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_asm = nullptr, ev_done[3] = {nullptr, nullptr, nullptr};
+  // captured preconditioners (0..2 CH species, 3 AC, 4 Oseen) replayed from
+  // fixed staging vectors; each captured on a private stream of its own
+  cudaStream_t cap[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaGraphExec_t gexec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double *pin[5] = {}, *pout[5] = {};
   std::string err;
   ~chnss3_ctx() {
     for (cudaGraphExec_t g : gexec)
       if (g) cudaGraphExecDestroy(g);
-    if (cap) cudaStreamDestroy(cap);
+    for (cudaStream_t q : cap)
+      if (q) cudaStreamDestroy(q);
+    for (cudaStream_t q : sx)
+      if (q) cudaStreamDestroy(q);
+    if (ev_asm) cudaEventDestroy(ev_asm);
+    for (cudaEvent_t e : ev_done)
+      if (e) cudaEventDestroy(e);
     if (pinned) cudaFreeHost(pinned);
     if (own_stream && s) cudaStreamDestroy(s);
   }
@@ -931,12 +944,21 @@ void create3(chnss3_ctx *c, int n) {
     c->pin[g] = ar.alloc<double>(len);
     c->pout[g] = ar.alloc<double>(len);
   }
-  CHNSS_CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  for (cudaStream_t &q : c->cap) CHNSS_CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+  int prio_low = 0, prio_high = 0;   // the Oseen group is the longest: highest priority
+  CHNSS_CK(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+  for (int w = 0; w < 3; ++w)
+    CHNSS_CK(cudaStreamCreateWithPriority(&c->sx[w], cudaStreamNonBlocking, w == 2 ? prio_high : prio_low));
+  CHNSS_CK(cudaEventCreateWithFlags(&c->ev_asm, cudaEventDisableTiming));
+  for (cudaEvent_t &e : c->ev_done) CHNSS_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  c->mt0 = ar.alloc<double>(N1);
   c->phia = ar.alloc<double>(N1);
   c->partial = ar.alloc<double>(64L * 1216);
   c->sum = ar.alloc<double>(4);
-  CHNSS_CK(cudaHostAlloc(&c->pinned, 8 * sizeof(double), cudaHostAllocDefault));
-  c->kw.init(ar, p.restart, std::max(2 * N1, nv + N1), c->pinned);
+  CHNSS_CK(cudaHostAlloc(&c->pinned, 32 * sizeof(double), cudaHostAllocDefault));
+  c->kw.init(ar, p.restart, nv + N1, c->pinned);
+  c->kwc.init(ar, p.restart, 2 * N1, c->pinned + 8);
+  c->kwa.init(ar, p.restart, N1, c->pinned + 16);
   // Chebyshev coefficients of M_p^-1 (degree 5 on D^-1 M over [1/2, 5/2])
   {
     const double theta = 0.5 * (kMassHi3 + kMassLo3), delta = 0.5 * (kMassHi3 - kMassLo3), sigma = theta / delta;
@@ -1129,15 +1151,15 @@ void run_prec3(chnss3_ctx *c, int g, long n, const double *r, double *z, cudaStr
   vec_copy(n, r, c->pin[g], s);
   if (!c->gexec[g]) {
     cudaGraph_t graph = nullptr;
-    CHNSS_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    CHNSS_CK(cudaStreamBeginCapture(c->cap[g], cudaStreamCaptureModeThreadLocal));
     try {
-      prec_body3(c, g, c->pin[g], c->pout[g], c->cap);
+      prec_body3(c, g, c->pin[g], c->pout[g], c->cap[g]);
     } catch (...) {
-      cudaStreamEndCapture(c->cap, &graph);
+      cudaStreamEndCapture(c->cap[g], &graph);
       if (graph) cudaGraphDestroy(graph);
       throw;
     }
-    CHNSS_CK(cudaStreamEndCapture(c->cap, &graph));
+    CHNSS_CK(cudaStreamEndCapture(c->cap[g], &graph));
     const cudaError_t e = cudaGraphInstantiate(&c->gexec[g], graph, 0);
     cudaGraphDestroy(graph);
     CHNSS_CK(e);
@@ -1186,49 +1208,97 @@ struct NS3Op : LinearOperator {
   }
 };
 
-chnss_status step3(chnss3_ctx *c, const chnss_state *in, chnss_state *out, chnss_solve_info *inf) {
+// The Cahn-Hilliard species and then the air potential (which needs the
+// new phase fields), on stream q.
+chnss_status group_ch3(chnss3_ctx *c, const chnss_state *in, chnss_state *out, chnss_solve_info *inf,
+                       cudaStream_t q) {
   const auto &p = c->p;
-  cudaStream_t s = c->s;
-  assemble3(c, in);
   const Level3 &F = c->lv[0];
   const int N1 = (int)F.N1;
-  const long nv = 3 * F.N2;
   chnss_status worst = CHNSS_OK;
   auto keep = [&](chnss_status st) { if (worst == CHNSS_OK) worst = st; };
   for (int sp = 0; sp < 3; ++sp) {
     CH3Op op(c, sp);
-    keep(fgmres(op, c->rhs[sp], c->xsol[sp], p.rtol, p.atol, p.maxit, c->kw, &inf[sp], s));
-    vec_copy(N1, c->xsol[sp], out->phi[sp], s);
-    vec_copy(N1, c->xsol[sp] + N1, out->mu[sp], s);
-  }
-  {
-    AC3Op op(c);
-    keep(fgmres(op, c->rhs[3], out->Phi_v, p.rtol, p.atol, p.maxit, c->kw, &inf[3], s));
+    keep(fgmres(op, c->rhs[sp], c->xsol[sp], p.rtol, p.atol, p.maxit, c->kwc, &inf[sp], q));
+    vec_copy(N1, c->xsol[sp], out->phi[sp], q);
+    vec_copy(N1, c->xsol[sp] + N1, out->mu[sp], q);
   }
   // air potential: M mu_a = f_a + beta_a K phi_a^{k+1}
-  k3_air<<<nb3(N1), kTPB3, 0, s>>>(N1, out->phi[0], out->phi[1], out->phi[2], c->phia);
+  k3_air<<<nb3(N1), kTPB3, 0, q>>>(N1, out->phi[0], out->phi[1], out->phi[2], c->phia);
   CHNSS_LAUNCH_CK();
-  k3_flux_rhs<<<nb3(N1), kTPB3, 0, s>>>(N1, c->loads + 3L * N1, c->top, in->phi[2], c->ref, p.evap_rate, p.phi_s_inf,
-                                       p.beta[3], -1.0, c->rhs[4]);
+  k3_flux_rhs<<<nb3(N1), kTPB3, 0, q>>>(N1, c->loads + 3L * N1, c->top, in->phi[2], c->ref, p.evap_rate,
+                                       p.phi_s_inf, p.beta[3], -1.0, c->rhs[4]);
   CHNSS_LAUNCH_CK();
   SpmvArgs none;
-  spmv_csr<double>(F.p1, F.K1, 1, c->phia, c->mt, SPMV_PLAIN, none, s);
-  vec_axpby(N1, p.beta[3], c->mt, 1.0, c->rhs[4], s);
-  keep(pcg(F.p1, F.M1, c->dinvM, c->rhs[4], out->mu[3], 1e-12, 1000, c->kw, &inf[4], s));
-  {
-    NS3Op op(c);
-    const double rt = p.ns_rtol > 0.0 ? p.ns_rtol : p.rtol, at = p.ns_rtol > 0.0 ? p.ns_atol : p.atol;
-    keep(fgmres(op, c->rhs[5], c->xsol[5], rt, at, p.maxit, c->kw, &inf[5], s));
-  }
-  vec_copy(nv, c->xsol[5], out->v, s);
-  vec_copy(N1, c->xsol[5] + nv, out->p, s);
-  // zero-mean pressure: p -= (1^T M p) / (1^T M 1), 1^T M 1 = |box| = 1
-  spmv_csr<double>(F.p1, F.M1, 1, out->p, c->mt, SPMV_PLAIN, none, s);
-  vsum<double>(N1, c->mt, c->sum, c->partial, s);
-  k3_shift<<<nb3(N1), kTPB3, 0, s>>>(N1, out->p, c->sum, 1.0);
-  CHNSS_LAUNCH_CK();
-  CHNSS_CK(cudaStreamSynchronize(s));
+  spmv_csr<double>(F.p1, F.K1, 1, c->phia, c->mt0, SPMV_PLAIN, none, q);
+  vec_axpby(N1, p.beta[3], c->mt0, 1.0, c->rhs[4], q);
+  keep(pcg(F.p1, F.M1, c->dinvM, c->rhs[4], out->mu[3], 1e-12, 1000, c->kwc, &inf[4], q));
   return worst;
+}
+
+chnss_status group_ns3(chnss3_ctx *c, chnss_state *out, chnss_solve_info *inf, cudaStream_t q) {
+  const auto &p = c->p;
+  const Level3 &F = c->lv[0];
+  const int N1 = (int)F.N1;
+  const long nv = 3 * F.N2;
+  NS3Op op(c);
+  const double rt = p.ns_rtol > 0.0 ? p.ns_rtol : p.rtol, at = p.ns_rtol > 0.0 ? p.ns_atol : p.atol;
+  const chnss_status st = fgmres(op, c->rhs[5], c->xsol[5], rt, at, p.maxit, c->kw, &inf[5], q);
+  vec_copy(nv, c->xsol[5], out->v, q);
+  vec_copy(N1, c->xsol[5] + nv, out->p, q);
+  // zero-mean pressure: p -= (1^T M p) / (1^T M 1), 1^T M 1 = |box| = 1
+  SpmvArgs none;
+  spmv_csr<double>(F.p1, F.M1, 1, out->p, c->mt, SPMV_PLAIN, none, q);
+  vsum<double>(N1, c->mt, c->sum, c->partial, q);
+  k3_shift<<<nb3(N1), kTPB3, 0, q>>>(N1, out->p, c->sum, 1.0);
+  CHNSS_LAUNCH_CK();
+  return st;
+}
+
+// Assembly on the context stream, then the three independent solve groups
+// (all coefficients at t_k): concurrently on their streams by three host
+// threads, or one after the other; the results are the same either way.
+chnss_status step3(chnss3_ctx *c, const chnss_state *in, chnss_state *out, chnss_solve_info *inf) {
+  cudaStream_t s = c->s;
+  assemble3(c, in);
+  CHNSS_CK(cudaEventRecord(c->ev_asm, s));
+  chnss_status st[3] = {CHNSS_OK, CHNSS_OK, CHNSS_OK};
+  std::exception_ptr err[3];
+  int dev = 0;
+  CHNSS_CK(cudaGetDevice(&dev));
+  auto run = [&](int w) {
+    try {
+      CHNSS_CK(cudaSetDevice(dev));
+      cudaStream_t q = c->sx[w];
+      CHNSS_CK(cudaStreamWaitEvent(q, c->ev_asm, 0));
+      if (w == 0) {
+        st[0] = group_ch3(c, in, out, inf, q);
+      } else if (w == 1) {
+        AC3Op op(c);
+        st[1] = fgmres(op, c->rhs[3], out->Phi_v, c->p.rtol, c->p.atol, c->p.maxit, c->kwa, &inf[3], q);
+      } else {
+        st[2] = group_ns3(c, out, inf, q);
+      }
+      CHNSS_CK(cudaEventRecord(c->ev_done[w], q));
+    } catch (...) {
+      err[w] = std::current_exception();
+    }
+  };
+  if (c->concurrent) {
+    std::thread t_ac(run, 1), t_ns(run, 2);
+    run(0);
+    t_ac.join();
+    t_ns.join();
+  } else {
+    for (int w = 0; w < 3; ++w) run(w);
+  }
+  for (std::exception_ptr &e : err)
+    if (e) std::rethrow_exception(e);
+  for (cudaEvent_t e : c->ev_done) CHNSS_CK(cudaStreamWaitEvent(s, e, 0));
+  CHNSS_CK(cudaStreamSynchronize(s));
+  for (chnss_status x : st)
+    if (x != CHNSS_OK) return x;
+  return CHNSS_OK;
 }
 
 }  // namespace
@@ -1306,6 +1376,15 @@ extern "C" chnss_status chnss3_step(chnss3_ctx_t ctx, const chnss_state *in, chn
     ctx->err = e.msg;
     return e.status;
   }
+}
+
+extern "C" chnss_status chnss3_set_step_concurrency(chnss3_ctx_t ctx, int on) {
+  if (!ctx) {
+    chnss::set_global_error("null context");
+    return CHNSS_ERR_ARG;
+  }
+  ctx->concurrent = on != 0;
+  return CHNSS_OK;
 }
 
 extern "C" const char *chnss3_last_error(chnss3_ctx_t ctx) { return ctx ? ctx->err.c_str() : ""; }
