@@ -137,7 +137,6 @@ void MGHier<T>::init(Arena &ar, int kind_, bool singular_, const std::vector<con
   n.resize(nl);
   val.resize(nl);
   val16.assign(nl, nullptr);
-  csr.assign(nl, 0);
   dinv.resize(nl);
   x.resize(nl);
   t.resize(nl);
@@ -149,12 +148,11 @@ void MGHier<T>::init(Arena &ar, int kind_, bool singular_, const std::vector<con
     const long nu = (kind == 0 ? 1L : 2L) * pat[l]->nrows;
     n[l] = nu;
     const long nv = (kind == 0 ? 1L : 4L) * pat[l]->sell.nent;   // SELL order
-    csr[l] = kind == 0 && !bf16 && pat[l]->nnz > 24L * pat[l]->nrows;
     if (bf16) {
       val[l] = nullptr;
       val16[l] = ar.alloc<__nv_bfloat16>(nv);
     } else {
-      val[l] = ar.alloc<T>(csr[l] ? std::max<long>(nv, pat[l]->nnz) : nv);
+      val[l] = ar.alloc<T>(nv);
     }
     dinv[l] = ar.alloc<T>(nu);
     x[l] = ar.alloc<T>(nu);
@@ -241,7 +239,6 @@ template <typename T>
 void MGHier<T>::setup(cudaStream_t s) {
   for (int l = 0; l < nl; ++l) {
     if (bf16) sell_gather<__nv_bfloat16>(pat[l]->sell, kind == 0 ? 1 : 4, val64[l], val16[l], s);
-    else if (csr[l]) vec_convert<double, T>(pat[l]->nnz, val64[l], val[l], s);
     else sell_gather<T>(pat[l]->sell, kind == 0 ? 1 : 4, val64[l], val[l], s);
     if (l == 0 && val0_64) sell_gather<double>(pat[0]->sell, kind == 0 ? 1 : 4, val64[0], val0_64, s);
     if (l == nl - 1) break;
@@ -279,9 +276,7 @@ void MGHier<T>::spmv_level(int l, const T *u, T *out, SpmvMode mode, const SpmvA
       return;
     }
   }
-  if (kind == 0 && csr[l])
-    spmv_csr<T>(*pat[l], val[l], 1, u, out, mode, a, s);
-  else if (kind == 0)
+  if (kind == 0)
     spmv_sell<T>(*pat[l], val[l], 1, u, out, mode, a, s);
   else
     spmv_sell_bsr2<T>(*pat[l], val[l], u, out, mode, a, s);

@@ -64,9 +64,6 @@ struct MGHier {
   std::vector<const double *> val64;
   std::vector<T *> val;
   std::vector<T *> dinv, x, t, r, b;
-  // levels whose rows are long (more than 24 entries on average: the 3D
-  // velocity operator) keep their values in CSR order and sweep a warp per row
-  std::vector<char> csr;
   std::vector<double *> hi, coef;
   std::vector<const Transfer *> tr;
   std::vector<long> n;

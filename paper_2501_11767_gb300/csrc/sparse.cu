@@ -1213,9 +1213,6 @@ void spmv_csr(const Pattern &P, const T *val, int ncomp, const T *u, T *out, Spm
   if (avg <= 4.5) {
     k_spmv_csr<4, T><<<nblocks((long)P.nrows * 4, TPB), TPB, 0, s>>>(P.nrows, ncomp, P.rowptr, P.col, val, u, out,
                                                                     mode, a);
-  } else if (avg > 24.0) {   // long rows (3D velocity, divergence): a warp per row
-    k_spmv_csr<32, T><<<nblocks((long)P.nrows * 32, TPB), TPB, 0, s>>>(P.nrows, ncomp, P.rowptr, P.col, val, u, out,
-                                                                      mode, a);
   } else {
     k_spmv_csr<8, T><<<nblocks((long)P.nrows * 8, TPB), TPB, 0, s>>>(P.nrows, ncomp, P.rowptr, P.col, val, u, out,
                                                                     mode, a);

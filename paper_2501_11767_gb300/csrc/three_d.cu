@@ -696,8 +696,8 @@ struct chnss3_ctx {
   chnss::Gather gl, gk;                         // loads -> P1 nodes, Korteweg -> velocity dofs
   int *bnd = nullptr;                           // fine P2 boundary mask
   int ref = 0;
-  double *Bv = nullptr, *Bts = nullptr, *Mv = nullptr, *Apb = nullptr, *Ap = nullptr, *top = nullptr;
-  double *Ls = nullptr, *Ks = nullptr, *Ms = nullptr, *ACs = nullptr;
+  double *Bs = nullptr, *Bts = nullptr, *Mv = nullptr, *Apb = nullptr, *Ap = nullptr, *top = nullptr;
+  double *Ls = nullptr, *Ks = nullptr, *Ms = nullptr, *ACs = nullptr, *As = nullptr;
   double *ebuf = nullptr, *kbuf = nullptr, *loads = nullptr, *G = nullptr, *dinvM = nullptr, *massc = nullptr;
   double *rhs[6] = {}, *xsol[6] = {}, *mt = nullptr, *phia = nullptr;
   double *partial = nullptr, *sum = nullptr, *pinned = nullptr;
@@ -847,7 +847,7 @@ void build_level3(chnss3_ctx *c, Level3 &L, int n, bool fine, const Mesh3Host *c
     for (size_t e = 0; e < map.size(); ++e) out[e] = map[e] >= 0 ? v[map[e]] : 0.0;
     return out;
   };
-  c->Bv = ar.upload(hBz.val);
+  c->Bs = ar.upload(sell_of(map_b, hBz.val));
   c->Bts = ar.upload(sell_of(map_bt, btv));
   std::vector<double> apb(m1.size());
   for (size_t k = 0; k < m1.size(); ++k) apb[k] = m1[k] / p.tau + p.eta * k1[k];
@@ -922,11 +922,12 @@ void create3(chnss3_ctx *c, int n) {
   c->loads = ar.alloc<double>(5 * N1);
   c->G = ar.alloc<double>(nv);
   c->Ap = ar.alloc<double>(F.p1.nnz);
-  const long nent1 = F.p1.sell.nent;
+  const long nent1 = F.p1.sell.nent, nentv = F.pv.sell.nent;
   c->Ls = ar.alloc<double>(nent1);
   c->Ks = ar.alloc<double>(nent1);
   c->Ms = ar.alloc<double>(nent1);
   c->ACs = ar.alloc<double>(nent1);
+  c->As = ar.alloc<double>(nentv);
   sell_gather<double>(F.p1.sell, 1, F.K1, c->Ks, c->s);
   sell_gather<double>(F.p1.sell, 1, F.M1, c->Ms, c->s);
   for (int k = 0; k < 3; ++k) {
@@ -1081,6 +1082,7 @@ void assemble3(chnss3_ctx *c, const chnss_state *st) {
   // SELL copies of the operators FGMRES applies, multigrid setup
   sell_gather<double>(F.p1.sell, 1, F.L, c->Ls, s);
   sell_gather<double>(F.p1.sell, 1, F.AC, c->ACs, s);
+  sell_gather<double>(F.pv.sell, 1, F.A, c->As, s);
   if (c->p32) setup_prec3(c, *c->p32, s);
   else setup_prec3(c, *c->p64, s);
 }
@@ -1197,10 +1199,9 @@ struct NS3Op : LinearOperator {
   void apply(const double *x, double *y, cudaStream_t s) override {
     const long nv = 3 * c->lv[0].N2;
     SpmvArgs none;
-    // long rows (velocity operator, divergence): CSR with a warp per row
-    spmv_csr<double>(c->lv[0].pv, c->lv[0].A, 1, x, y, SPMV_PLAIN, none, s);
+    spmv_sell<double>(c->lv[0].pv, c->As, 1, x, y, SPMV_PLAIN, none, s);
     spmv_sell<double>(c->pbt, c->Bts, 1, x + nv, y, SPMV_ADD, none, s);
-    spmv_csr<double>(c->pb, c->Bv, 1, x, y + nv, SPMV_PLAIN, none, s);
+    spmv_sell<double>(c->pb, c->Bs, 1, x, y + nv, SPMV_PLAIN, none, s);
   }
   void precond(const double *r, double *z, cudaStream_t s) override {
     run_prec3(c, 4, 3 * c->lv[0].N2 + c->lv[0].N1, r, z, s);
