@@ -289,13 +289,17 @@ chnss_status chnss_inner_stats_read(chnss_ctx_t ctx, int reset, chnss_inner_stat
  *   CHNSS3_OP_LOADS    the five potential loads of eqn:appPotential, concatenated (5 N1)
  *   CHNSS3_OP_KORTEWEG the Korteweg load (3 N2; beta_i, beta_v from params)
  *   CHNSS3_OP_TOP      int over the top face of each P1 hat (N1)
+ *   CHNSS3_OP_KK0..2   weighted stiffness int kappa grad psi_a . grad psi_b of species 0..2 with the
+ *                      concentration-dependent mobility kappa = gamma_i (phi_i (1 - phi_i) + mobility_m0)
+ *                      (state->phi[i]; any mobility_kind)
  * state (HOST arrays, 3D sizes) supplies v, mu, phi, Phi_v where needed
  * (may be NULL otherwise).  Call with val == NULL to get nrows, ncols and nnz
  * (the vector length for the loads); then with rowptr (nrows + 1), col and
  * val (nnz) allocated (vectors: val only).  1 <= n <= 64. */
 enum {
   CHNSS3_OP_M1 = 0, CHNSS3_OP_K1, CHNSS3_OP_C1, CHNSS3_OP_CP, CHNSS3_OP_M2, CHNSS3_OP_J2, CHNSS3_OP_KSYM,
-  CHNSS3_OP_B, CHNSS3_OP_P1PROL, CHNSS3_OP_VPROL, CHNSS3_OP_LOADS, CHNSS3_OP_KORTEWEG, CHNSS3_OP_TOP
+  CHNSS3_OP_B, CHNSS3_OP_P1PROL, CHNSS3_OP_VPROL, CHNSS3_OP_LOADS, CHNSS3_OP_KORTEWEG, CHNSS3_OP_TOP,
+  CHNSS3_OP_KK0, CHNSS3_OP_KK1, CHNSS3_OP_KK2
 };
 chnss_status chnss3_host_operator(int n, int which, const chnss_params *params, const chnss_state *state,
                                   int *nrows, int *ncols, long long *nnz, int *rowptr, int *col, double *val);
@@ -306,9 +310,11 @@ chnss_status chnss3_host_operator(int n, int which, const chnss_params *params, 
  * the air potential by Jacobi-PCG, Oseen with diag(MG(A), M_p^-1 A_p K_p^-1),
  * FGMRES(restart) with CGS2, geometric multigrid on the nested Kuhn meshes)
  * with no-slip on every face and evaporation through the top face z = 1
- * (reference point (1/2, 1/2, 1)).  Covers model 0, constant mobility,
- * precision 0, 1 or 2 and one V-cycle per block (inner_rtol 0); other parameter
- * sets get CHNSS_ERR_ARG.  Assembly runs on the context's stream
+ * (reference point (1/2, 1/2, 1)).  Covers model 0, constant or
+ * concentration-dependent mobility (mobility_kind 0 or 1: then the first
+ * row's tau K_kappa and the Schur factor X2 = tau K_kappa + a M as in 2D),
+ * precision 0, 1 or 2 and one V-cycle per block (inner_rtol 0); other
+ * parameter sets get CHNSS_ERR_ARG.  Assembly runs on the context's stream
  * (cuda_stream, or a library stream when NULL), the solve groups on library
  * streams after it (chnss3_set_step_concurrency).
  * States: chnss_state with DEVICE arrays of the 3D sizes (chnss3_sizes):

@@ -433,7 +433,8 @@ class Context3:
         return state_out, {SYSTEM_NAMES[i]: infos[i].as_dict() for i in range(6)}, st
 
 
-OPS3 = ("M1", "K1", "C1", "CP", "M2", "J2", "KSYM", "B", "P1PROL", "VPROL", "LOADS", "KORTEWEG", "TOP")
+OPS3 = ("M1", "K1", "C1", "CP", "M2", "J2", "KSYM", "B", "P1PROL", "VPROL", "LOADS", "KORTEWEG", "TOP",
+        "KK0", "KK1", "KK2")
 
 
 def host_operator3(n: int, which: str, params: dict, state: dict = None):

@@ -304,7 +304,7 @@ HostCSR velocity_prolongation3(const Mesh3Host &c, const Mesh3Host &f) {
 
 enum Op3 {
   OP3_M1 = 0, OP3_K1, OP3_C1, OP3_CP, OP3_M2, OP3_J2, OP3_KSYM, OP3_B, OP3_P1PROL, OP3_VPROL,
-  OP3_LOADS, OP3_KORTEWEG, OP3_TOP, OP3_COUNT
+  OP3_LOADS, OP3_KORTEWEG, OP3_TOP, OP3_KK0, OP3_KK1, OP3_KK2, OP3_COUNT
 };
 
 void element_fields(const Mesh3Host &M, long e, const double *v, double vk[10][3]) {
@@ -332,6 +332,22 @@ HostCSR host_operator3(int n, int which, const chnss_params &p, const chnss_stat
     if (!ok) throw Error{CHNSS_ERR_ARG, "this 3D operator needs the state fields"};
   };
   switch (which) {
+    case OP3_KK0:
+    case OP3_KK1:
+    case OP3_KK2: {
+      const int sp = which - OP3_KK0;
+      need(st && st->phi[sp]);
+      return assemble_host(N1, N1, M.E, 4, 4, [&](long e, int *r, int *c, double *b) {
+        double x[4][3], g[4][3], f[4];
+        M.coords(e, x);
+        const double vol = tet_geometry(x, g);
+        for (int a = 0; a < 4; ++a) {
+          r[a] = c[a] = M.tet[e * 4 + a];
+          f[a] = st->phi[sp][M.tet[e * 4 + a]];
+        }
+        tet_wstiff(vol, g, f, p.gamma[sp], p.mobility_m0, b);
+      });
+    }
     case OP3_M1:
     case OP3_K1:
     case OP3_C1:
@@ -506,8 +522,9 @@ extern "C" chnss_status chnss3_host_operator(int n, int which, const chnss_param
 // element operator of three_d.h into an element buffer, a gather kernel sums
 // every CSR entry's contributions in element order (no atomics).  The
 // velocity operator is a scalar CSR on the interleaved 3 N2 dofs; all
-// hierarchies are scalar (FP64) multigrid; the solves run one after the
-// other on the context's stream.
+// hierarchies are scalar multigrid (FP64, or FP32 / BF16-stored values
+// inside the FP64 Krylov solvers); the three solve groups run on library
+// streams after the assembly.
 #include "gather.h"
 #include "solver.h"
 
@@ -580,6 +597,19 @@ __global__ void k3_conv(Geo3 g, Fields3 f, int mode, int shift, double *buf) {
   if (shift) elem_shift(f, v1, gr, s);
   if (mode == 0) tet_p1_conv(c3, vol, gr, vk, shift ? s : nullptr, buf + e * 16);
   else tet_p2_conv(c3, vol, gr, vk, s, buf + e * 100);
+}
+
+// weighted stiffness of the concentration-dependent mobility
+// gamma (phi (1 - phi) + m0), buf [E][16]
+__global__ void k3_wstiff(Geo3 g, const double *phi, double gamma, double m0, double *buf) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 6L * g.n * g.n * g.n) return;
+  double x[4][3], gr[4][3], f[4];
+  int v1[4], v2[10];
+  tet_nodes(g, e, x, v1, v2);
+  const double vol = tet_geometry(x, gr);
+  for (int a = 0; a < 4; ++a) f[a] = phi[v1[a]];
+  tet_wstiff(vol, gr, f, gamma, m0, buf + e * 16);
 }
 
 // potential loads [E][20] and Korteweg load [E][30]
@@ -672,6 +702,9 @@ struct Level3 {
   double *M1 = nullptr, *K1 = nullptr, *ACb = nullptr, *Aconst = nullptr;
   double *L = nullptr, *AC = nullptr, *A = nullptr, *X[3] = {nullptr, nullptr, nullptr};
   double *vl = nullptr, *mul = nullptr;   // injected v (3 N2) and mu (4 N1), levels >= 1
+  // concentration-dependent mobility: X2 = tau K_kappa + a M per species,
+  // K_kappa itself (fine level), injected phi (3 N1, levels >= 1)
+  double *X2[3] = {nullptr, nullptr, nullptr}, *Kk[3] = {nullptr, nullptr, nullptr}, *phil = nullptr;
 };
 
 // The block preconditioners' hierarchies and scratch in the arithmetic of
@@ -679,7 +712,7 @@ struct Level3 {
 // values stored in BF16)
 template <typename T>
 struct Prec3 {
-  MGHier<T> L, AC, X[3], Kp, A;
+  MGHier<T> L, AC, X[3], X2[3], Kp, A;   // X2: concentration-dependent mobility only
   T *Ms = nullptr, *Aps = nullptr, *mdinv = nullptr, *mb = nullptr, *mx = nullptr, *mt = nullptr;
 };
 
@@ -698,6 +731,7 @@ struct chnss3_ctx {
   int ref = 0;
   double *Bs = nullptr, *Bts = nullptr, *Mv = nullptr, *Apb = nullptr, *Ap = nullptr, *top = nullptr;
   double *Ls = nullptr, *Ks = nullptr, *Ms = nullptr, *ACs = nullptr, *As = nullptr;
+  double *Kks[3] = {nullptr, nullptr, nullptr};   // SELL copies of K_kappa (mobility_kind 1)
   double *ebuf = nullptr, *kbuf = nullptr, *loads = nullptr, *G = nullptr, *dinvM = nullptr, *massc = nullptr;
   double *rhs[6] = {}, *xsol[6] = {}, *mt = nullptr, *phia = nullptr;
   double *partial = nullptr, *sum = nullptr, *pinned = nullptr;
@@ -804,7 +838,12 @@ void build_level3(chnss3_ctx *c, Level3 &L, int n, bool fine, const Mesh3Host *c
     std::vector<double> x(m1.size());
     for (size_t k = 0; k < m1.size(); ++k) x[k] = p.tau * p.gamma[sp] * k1[k] + a * m1[k];
     L.X[sp] = ar.upload(x);
+    if (p.mobility_kind != 0) {
+      L.X2[sp] = ar.alloc<double>(L.p1.nnz);
+      if (fine) L.Kk[sp] = ar.alloc<double>(L.p1.nnz);
+    }
   }
+  if (p.mobility_kind != 0 && !fine) L.phil = ar.alloc<double>(3L * N1);
   // A const = M_v / tau + K_sym with identity rows / zero columns on the no-slip dofs
   const HostCSR hM2 = host_operator3(n, OP3_M2, none, nullptr), hKs = host_operator3(n, OP3_KSYM, none, nullptr);
   std::vector<double> av = on_pattern(L.pv, hKs), mv(L.pv.nnz, 0.0);
@@ -877,7 +916,8 @@ void init_prec3(chnss3_ctx *c, Prec3<T> &P, const std::vector<const Pattern *> &
                 const std::vector<const Pattern *> &pvs, const std::vector<const int *> &dvs,
                 const std::vector<const Transfer *> &tvs, const std::vector<const double *> &Ls,
                 const std::vector<const double *> &ACs, const std::vector<const double *> &K1s,
-                const std::vector<const double *> &As, const std::vector<const double *> *Xs) {
+                const std::vector<const double *> &As, const std::vector<const double *> *Xs,
+                const std::vector<const double *> *X2s) {
   Arena &ar = c->ar;
   const Level3 &F = c->lv[0];
   P.L.init(ar, 0, false, p1s, d1s, Ls, t1s, c->partial);
@@ -885,6 +925,7 @@ void init_prec3(chnss3_ctx *c, Prec3<T> &P, const std::vector<const Pattern *> &
   for (int sp = 0; sp < 3; ++sp) {
     P.X[sp].init(ar, 0, false, p1s, d1s, Xs[sp], t1s, c->partial);
     P.X[sp].setup(c->s);
+    if (X2s) P.X2[sp].init(ar, 0, false, p1s, d1s, X2s[sp], t1s, c->partial);   // set up every step
   }
   P.Kp.init(ar, 0, true, p1s, d1s, K1s, t1s, c->partial);
   P.Kp.setup(c->s);
@@ -978,7 +1019,7 @@ void create3(chnss3_ctx *c, int n) {
   std::vector<const Pattern *> p1s, pvs;
   std::vector<const int *> d1s, dvs;
   std::vector<const Transfer *> t1s, tvs;
-  std::vector<const double *> Ls, ACs, K1s, As, Xs[3];
+  std::vector<const double *> Ls, ACs, K1s, As, Xs[3], X2s[3];
   for (int l = 0; l < nl; ++l) {
     const Level3 &L = c->lv[l];
     p1s.push_back(&L.p1);
@@ -991,15 +1032,21 @@ void create3(chnss3_ctx *c, int n) {
     ACs.push_back(L.AC);
     K1s.push_back(L.K1);
     As.push_back(L.A);
-    for (int sp = 0; sp < 3; ++sp) Xs[sp].push_back(L.X[sp]);
+    for (int sp = 0; sp < 3; ++sp) {
+      Xs[sp].push_back(L.X[sp]);
+      X2s[sp].push_back(L.X2[sp]);
+    }
   }
+  const std::vector<const double *> *x2 = p.mobility_kind != 0 ? X2s : nullptr;
+  if (p.mobility_kind != 0)
+    for (int sp = 0; sp < 3; ++sp) c->Kks[sp] = ar.alloc<double>(nent1);
   if (p.precision == 0) {
     c->p64.reset(new Prec3<double>);
-    init_prec3(c, *c->p64, p1s, d1s, t1s, pvs, dvs, tvs, Ls, ACs, K1s, As, Xs);
+    init_prec3(c, *c->p64, p1s, d1s, t1s, pvs, dvs, tvs, Ls, ACs, K1s, As, Xs, x2);
   } else {
     c->p32.reset(new Prec3<float>);
     c->p32->A.bf16 = p.precision == 2;
-    init_prec3(c, *c->p32, p1s, d1s, t1s, pvs, dvs, tvs, Ls, ACs, K1s, As, Xs);
+    init_prec3(c, *c->p32, p1s, d1s, t1s, pvs, dvs, tvs, Ls, ACs, K1s, As, Xs, x2);
   }
   CHNSS_CK(cudaStreamSynchronize(c->s));
 }
@@ -1009,6 +1056,8 @@ void setup_prec3(chnss3_ctx *c, Prec3<T> &P, cudaStream_t s) {
   P.L.setup(s);
   P.AC.setup(s);
   P.A.setup(s);
+  if (c->p.mobility_kind != 0)
+    for (int sp = 0; sp < 3; ++sp) P.X2[sp].setup(s);
   sell_gather<T>(c->lv[0].p1.sell, 1, c->Ap, P.Aps, s);
 }
 
@@ -1044,6 +1093,22 @@ void assemble3(chnss3_ctx *c, const chnss_state *st) {
     k3_conv<<<nb3(L.E), kTPB3, 0, s>>>(L.geo, f, 1, 1, c->ebuf);
     CHNSS_LAUNCH_CK();
     launch_gather(L.gj, 1, c->ebuf, 1.0, L.Aconst, 1.0, L.A, s);
+    if (p.mobility_kind != 0) {   // X2 = tau K_kappa(phi^k) + a M, phi injected on the coarse levels
+      for (int sp = 0; sp < 3; ++sp) {
+        if (l > 0) {
+          const Level3 &Fn = c->lv[l - 1];
+          const double *pf = l == 1 ? st->phi[sp] : Fn.phil + (long)sp * Fn.N1;
+          k3_inject<<<nb3(L.N1), kTPB3, 0, s>>>(Fn.n, 0, pf, L.phil + (long)sp * L.N1);
+          CHNSS_LAUNCH_CK();
+        }
+        const double *ph = l == 0 ? st->phi[sp] : L.phil + (long)sp * L.N1;
+        const double a = std::sqrt(p.tau * p.gamma[sp] / p.beta[sp]);
+        k3_wstiff<<<nb3(L.E), kTPB3, 0, s>>>(L.geo, ph, p.gamma[sp], p.mobility_m0, c->ebuf);
+        CHNSS_LAUNCH_CK();
+        launch_gather(L.g1, 1, c->ebuf, p.tau, L.M1, a, L.X2[sp], s);
+        if (l == 0) launch_gather(L.g1, 1, c->ebuf, 1.0, nullptr, 0.0, L.Kk[sp], s);
+      }
+    }
   }
   const Level3 &F = c->lv[0];
   const int N1 = (int)F.N1;
@@ -1083,6 +1148,8 @@ void assemble3(chnss3_ctx *c, const chnss_state *st) {
   sell_gather<double>(F.p1.sell, 1, F.L, c->Ls, s);
   sell_gather<double>(F.p1.sell, 1, F.AC, c->ACs, s);
   sell_gather<double>(F.pv.sell, 1, F.A, c->As, s);
+  if (p.mobility_kind != 0)
+    for (int sp = 0; sp < 3; ++sp) sell_gather<double>(F.p1.sell, 1, F.Kk[sp], c->Kks[sp], s);
   if (c->p32) setup_prec3(c, *c->p32, s);
   else setup_prec3(c, *c->p64, s);
 }
@@ -1098,14 +1165,15 @@ template <typename T>
 void prec_ch3(chnss3_ctx *c, Prec3<T> &P, int sp, const double *r, double *z, cudaStream_t s) {
   const long N1 = c->lv[0].N1;
   mg_apply(P.L, N1, r, z, s);
-  // S~^-1 = X^-1 M X^-1 (matching factors of eqn::schurCH)
-  MGHier<T> &X = P.X[sp];
-  vec_convert<double, T>(N1, r + N1, X.input(), s);
-  X.apply(s);
+  // S~^-1 = X2^-1 M X1^-1 (matching factors of eqn::schurCH; X2 = X1 with
+  // constant mobility)
+  MGHier<T> &X1 = P.X[sp], &X2 = c->p.mobility_kind != 0 ? P.X2[sp] : P.X[sp];
+  vec_convert<double, T>(N1, r + N1, X1.input(), s);
+  X1.apply(s);
   SpmvArgs none;
-  spmv_sell<T>(c->lv[0].p1, P.Ms, 1, X.output(), X.input(), SPMV_PLAIN, none, s);
-  X.apply(s);
-  vec_convert<T, double>(N1, X.output(), z + N1, s);
+  spmv_sell<T>(c->lv[0].p1, P.Ms, 1, X1.output(), X2.input(), SPMV_PLAIN, none, s);
+  X2.apply(s);
+  vec_convert<T, double>(N1, X2.output(), z + N1, s);
 }
 
 template <typename T>
@@ -1176,7 +1244,12 @@ struct CH3Op : LinearOperator {
   void apply(const double *x, double *y, cudaStream_t s) override {
     const auto &p = c->p;
     const double tau = p.tau, g = p.gamma[sp], b = p.beta[sp];
-    spmv_sell_ch(c->lv[0].p1, c->Ls, c->Ks, nullptr, c->Ms, tau * g, tau * g, -tau * g / b, x, y, s);
+    // [[M + tau C, tau K_kappa], [tau gamma K, -(tau gamma / beta) M]] (K_kappa = gamma K
+    // with constant mobility)
+    if (p.mobility_kind != 0)
+      spmv_sell_ch(c->lv[0].p1, c->Ls, c->Ks, c->Kks[sp], c->Ms, tau, tau * g, -tau * g / b, x, y, s);
+    else
+      spmv_sell_ch(c->lv[0].p1, c->Ls, c->Ks, nullptr, c->Ms, tau * g, tau * g, -tau * g / b, x, y, s);
   }
   void precond(const double *r, double *z, cudaStream_t s) override { run_prec3(c, sp, 2 * c->lv[0].N1, r, z, s); }
 };
@@ -1311,8 +1384,9 @@ extern "C" chnss_status chnss3_ctx_create(int n, const chnss_params *params, voi
     if (!params || !out) throw Error{CHNSS_ERR_ARG, "null argument"};
     if (n < 2 || n % 2 || n > 96) throw Error{CHNSS_ERR_ARG, "3D meshes: n even, 2 <= n <= 96"};
     const chnss_params &p = *params;
-    if (p.model != 0 || p.mobility_kind != 0 || p.inner_rtol != 0.0 || p.precision < 0 || p.precision > 2)
-      throw Error{CHNSS_ERR_ARG, "the 3D step covers model 0, constant mobility, one V-cycle per block"};
+    if (p.model != 0 || p.inner_rtol != 0.0 || p.precision < 0 || p.precision > 2)
+      throw Error{CHNSS_ERR_ARG, "the 3D step covers model 0, one V-cycle per block, precision 0-2"};
+    if (p.mobility_kind != 0 && p.mobility_kind != 1) throw Error{CHNSS_ERR_ARG, "mobility_kind must be 0 or 1"};
     if (!(p.tau > 0) || !(p.eta > 0) || p.restart < 1 || p.restart > 64 || p.maxit < 1)
       throw Error{CHNSS_ERR_ARG, "invalid parameters"};
     for (int i = 0; i < 3; ++i)

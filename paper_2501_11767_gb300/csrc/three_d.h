@@ -77,6 +77,20 @@ __host__ __device__ inline void tet_p1_conv(const Tet3Ref &R, double vol, const 
   }
 }
 
+// Weighted stiffness K_kappa,ab = int kappa grad psi_a . grad psi_b with the
+// concentration-dependent mobility kappa = gamma (phi (1 - phi) + m0) of a P1
+// field phi (nodal values f[4]).  The gradients are constant on the element,
+// so only int kappa is needed, and it is exact: int phi = vol sum f / 4,
+// int phi^2 = vol ((sum f)^2 + sum f^2) / 20.  out[a * 4 + b]
+__host__ __device__ inline void tet_wstiff(double vol, const double g[4][3], const double f[4], double gamma,
+                                           double m0, double out[16]) {
+  const double s1 = f[0] + f[1] + f[2] + f[3];
+  const double s2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3];
+  const double kint = vol * gamma * (0.25 * s1 - (s1 * s1 + s2) / 20.0 + m0);
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) out[a * 4 + b] = kint * (g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2]);
+}
+
 // J_ab = int ((v - s) . grad N_b) N_a on the P2 nodes: out[a * 10 + b]
 __host__ __device__ inline void tet_p2_conv(const Tet3Ref &R, double vol, const double g[4][3],
                                             const double vk[10][3], const double *s, double out[100]) {

@@ -1,7 +1,8 @@
 """The 3D step on the GPU (chnss3_step, Kuhn tetrahedra) against the 3D
 oracle: every solve of a step (relative L2 <= 1e-9 when the Krylov iteration
 counts agree, counts within +-1), two steps (the second with flow), a finer
-mesh, determinism and the parameter checks."""
+mesh, concentration-dependent mobility, mixed precision, concurrency,
+determinism and the parameter checks."""
 import numpy as np
 import pytest
 
@@ -66,6 +67,18 @@ def test_step_3d_finer_mesh(torch):
     _compare(torch, 8, _params(), seed=2, steps=1)
 
 
+def test_step_3d_variable_mobility(torch):
+    """Concentration-dependent mobility gamma_i (phi_i (1 - phi_i) + m0): the
+    first row's tau K_kappa and the Schur factor X2 = tau K_kappa + a M on
+    every level (phi injected), two steps."""
+    _compare(torch, 4, _params(mobility_kind=1, gamma=[1.0, 0.8, 1.2]), seed=3)
+
+
+def test_step_3d_variable_mobility_finer_mesh(torch):
+    """8^3 cubes: phi injected through two coarse levels."""
+    _compare(torch, 8, _params(mobility_kind=1), seed=4, steps=1)
+
+
 def test_step_3d_is_deterministic(torch):
     n = 4
     ctx = chnss.Context3(n, _params())
@@ -76,7 +89,7 @@ def test_step_3d_is_deterministic(torch):
         assert np.array_equal(a[k], b[k]), k
 
 
-@pytest.mark.parametrize("bad", [dict(mobility_kind=1), dict(precision=3), dict(model=1)])
+@pytest.mark.parametrize("bad", [dict(mobility_kind=2), dict(precision=3), dict(model=1), dict(inner_rtol=1e-4)])
 def test_step_3d_parameter_errors(torch, bad):
     with pytest.raises(chnss.ChnssError):
         chnss.Context3(4, _params(**bad))
@@ -84,13 +97,13 @@ def test_step_3d_parameter_errors(torch, bad):
         chnss.Context3(3, _params())            # n must be even
 
 
-@pytest.mark.parametrize("precision", [1, 2])
-def test_step_3d_mixed_precision(torch, precision):
+@pytest.mark.parametrize("precision,mobility", [(1, 0), (2, 0), (1, 1)])
+def test_step_3d_mixed_precision(torch, precision, mobility):
     """FP32 multigrid (precision 2: velocity hierarchy values in BF16) inside
     FP64 FGMRES: the 1e-8 residual is reached, and at an outer tolerance of
     1e-10 the step stays within 1e-6 of the oracle solved to 1e-12."""
     n = 8
-    p = _params()
+    p = _params(mobility_kind=mobility)
     o = t3.Oracle3D(n, dict(p, rtol=1e-12))
     ctx8 = chnss.Context3(n, dict(p, precision=precision))
     ctx10 = chnss.Context3(n, dict(p, precision=precision, rtol=1e-10))

@@ -213,3 +213,41 @@ def test_preconditioned_iterations_are_mesh_robust():
         assert b["ch_p"] <= a["ch_p"] + 5 and b["ac"] <= a["ac"] + 2
     d1, d2 = its[1]["ns"] - its[0]["ns"], its[2]["ns"] - its[1]["ns"]
     assert d2 <= d1 and its[2]["ns"] <= 80
+
+
+def test_weighted_stiffness_closed_forms():
+    """K_kappa of the concentration-dependent mobility gamma (phi (1 - phi) + m0):
+    symmetric, rows summing to zero (so CH mass stays conserved), gamma (c (1 - c)
+    + m0) K for a constant phi = c, and for phi = x (exact in P1) the energy of
+    u = x is int gamma (x (1 - x) + m0) dx = gamma (1/6 + m0) over the unit cube."""
+    mesh = t3.Mesh3D(4)
+    g, m0 = 1.3, 1e-3
+    p = dict(inputs.default_params(), mobility_kind=1, mobility_m0=m0, gamma=[g, g, g])
+    x = mesh.x1[:, 0]
+    Kk = t3.weighted_stiffness_p1(mesh, t3.mobility_at(mesh, x, p, 0))
+    assert abs(Kk - Kk.T).max() < 1e-14
+    assert np.abs(Kk @ np.ones(mesh.N1)).max() < 1e-13
+    assert x @ (Kk @ x) == pytest.approx(g * (1.0 / 6.0 + m0), rel=1e-13)
+    c = 0.3
+    Kc = t3.weighted_stiffness_p1(mesh, t3.mobility_at(mesh, np.full(mesh.N1, c), p, 0))
+    assert abs(Kc - g * (c * (1 - c) + m0) * t3.stiffness_p1(mesh)).max() < 1e-13
+
+
+def test_variable_mobility_step_matches_sparse_lu():
+    """With the concentration-dependent mobility the first row's tau K_kappa and
+    the Schur factor X2 = tau K_kappa + a M change; the preconditioned step still
+    reaches the sparse-LU step, and polymer and NFA mass stay conserved."""
+    n = 4
+    p = inputs.default_params()
+    p.update(rtol=1e-11, alpha=[1e-2] * 4, mobility_kind=1, gamma=[1.0, 0.8, 1.2])
+    o, ox = t3.Oracle3D(n, p), t3.Oracle3D(n, p, exact=True)
+    s0 = inputs.initial_state_3d(n, seed=3)
+    s1, info = o.step(s0)
+    x1 = ox.step(s0)[0]
+    assert all(v["converged"] for v in info.values())
+    for key in ("phi", "mu", "Phi_v", "v", "p"):
+        a, b = np.ravel(s1[key]), np.ravel(x1[key])
+        assert np.linalg.norm(a - b) <= 1e-7 * max(np.linalg.norm(b), 1e-30), key
+    d0, d1 = o.diagnostics(s0), o.diagnostics(s1)
+    for i in range(2):
+        assert d1["mass"][i] == pytest.approx(d0["mass"][i], rel=1e-9)

@@ -4,7 +4,8 @@ P1 and P2 convection with the PCD shift, the symmetric-gradient form, the
 divergence, the potential and Korteweg loads, the top-face load) and the
 nested transfers, entry by entry.  No device is needed: the operators are
 built by chnss3_host_operator from the same __host__ __device__ element
-functions as the device kernels (CPU)."""
+functions as the device kernels (CPU).  Also the weighted stiffness of the
+concentration-dependent mobility."""
 import numpy as np
 import pytest
 
@@ -73,6 +74,19 @@ def test_loads(case):
     ref = t3.korteweg(mesh, t3.korteweg_tensor(mesh, st, p))
     assert np.allclose(got, ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())
     assert np.allclose(chnss.host_operator3(N, "TOP", p), t3.top_load_p1(mesh), rtol=1e-14, atol=1e-16)
+
+
+def test_weighted_stiffness(case):
+    """K_kappa of the concentration-dependent mobility gamma_i (phi_i (1 - phi_i)
+    + m0), exact on each tetrahedron, against the oracle's degree-2 rule."""
+    mesh, st, p = case
+    pv = dict(p, mobility_kind=1, mobility_m0=1e-3, gamma=[1.0, 0.7, 1.3])
+    for sp in range(3):
+        ref = t3.weighted_stiffness_p1(mesh, t3.mobility_at(mesh, st["phi"][sp], pv, sp))
+        _same(chnss.host_operator3(N, f"KK{sp}", pv, st), ref)
+    # phi = 0 everywhere: gamma m0 K
+    zero = dict(st, phi=np.zeros_like(st["phi"]))
+    _same(chnss.host_operator3(N, "KK1", pv, zero), 0.7e-3 * t3.stiffness_p1(mesh))
 
 
 def test_argument_errors():
