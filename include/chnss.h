@@ -313,8 +313,9 @@ chnss_status chnss3_host_operator(int n, int which, const chnss_params *params, 
  * (reference point (1/2, 1/2, 1)).  Covers model 0, constant or
  * concentration-dependent mobility (mobility_kind 0 or 1: then the first
  * row's tau K_kappa and the Schur factor X2 = tau K_kappa + a M as in 2D),
- * precision 0, 1 or 2 and one V-cycle per block (inner_rtol 0); other
- * parameter sets get CHNSS_ERR_ARG.  Assembly runs on the context's stream
+ * precision 0, 1 or 2, and one V-cycle per multigrid block or (inner_rtol
+ * > 0) V-cycles to inner_rtol as in 2D; other parameter sets get
+ * CHNSS_ERR_ARG.  Assembly runs on the context's stream
  * (cuda_stream, or a library stream when NULL), the solve groups on library
  * streams after it (chnss3_set_step_concurrency).
  * States: chnss_state with DEVICE arrays of the 3D sizes (chnss3_sizes):

@@ -111,6 +111,8 @@ struct MGHier {
   // solve (an FP32 rounding of it would cap the preconditioner's accuracy),
   // else x[0] converted
   void write_output(double *const *slot, long off, cudaStream_t s);
+  // the FP64 iterate of the last inner solve (null unless enable_inner)
+  const double *iterate64() const { return acc; }
   // inner solves and V-cycles since the last reset, residual ratio of the
   // last solve (stream-ordered read on s, then a synchronisation)
   void inner_stats(bool reset, long long *solves, long long *cycles, double *last_rel, cudaStream_t s);

@@ -746,6 +746,8 @@ struct chnss3_ctx {
   // captured preconditioners (0..2 CH species, 3 AC, 4 Oseen) replayed from
   // fixed staging vectors; each captured on a private stream of its own
   cudaStream_t cap[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // bodies of the inner multigrid loops (inner_rtol > 0), one stream per solve group
+  cudaStream_t bodyq[3] = {nullptr, nullptr, nullptr};
   cudaGraphExec_t gexec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double *pin[5] = {}, *pout[5] = {};
   std::string err;
@@ -753,6 +755,8 @@ struct chnss3_ctx {
     for (cudaGraphExec_t g : gexec)
       if (g) cudaGraphExecDestroy(g);
     for (cudaStream_t q : cap)
+      if (q) cudaStreamDestroy(q);
+    for (cudaStream_t q : bodyq)
       if (q) cudaStreamDestroy(q);
     for (cudaStream_t q : sx)
       if (q) cudaStreamDestroy(q);
@@ -924,14 +928,29 @@ void init_prec3(chnss3_ctx *c, Prec3<T> &P, const std::vector<const Pattern *> &
   P.AC.init(ar, 0, false, p1s, d1s, ACs, t1s, c->partial);
   for (int sp = 0; sp < 3; ++sp) {
     P.X[sp].init(ar, 0, false, p1s, d1s, Xs[sp], t1s, c->partial);
-    P.X[sp].setup(c->s);
     if (X2s) P.X2[sp].init(ar, 0, false, p1s, d1s, X2s[sp], t1s, c->partial);   // set up every step
   }
   P.Kp.init(ar, 0, true, p1s, d1s, K1s, t1s, c->partial);
-  P.Kp.setup(c->s);
   P.A.degree = 4;      // as the 2D velocity operator: degree 4 on [hi / 16, hi]
   P.A.ratio = 16.0;
   P.A.init(ar, 0, false, pvs, dvs, As, tvs, c->partial);
+  // inner multigrid solves to a tolerance (Sec. 5) in every block that the
+  // paper gives to AMG; M_p^-1 stays the fixed Chebyshev iteration.  Each
+  // solve group captures its loop bodies on a stream of its own.
+  const double irt = c->p.inner_rtol;
+  if (irt > 0.0) {
+    const int imax = c->p.inner_maxit;
+    P.L.enable_inner(ar, irt, imax, c->bodyq[0]);
+    for (int sp = 0; sp < 3; ++sp) {
+      P.X[sp].enable_inner(ar, irt, imax, c->bodyq[0]);
+      if (X2s) P.X2[sp].enable_inner(ar, irt, imax, c->bodyq[0]);
+    }
+    P.AC.enable_inner(ar, irt, imax, c->bodyq[1]);
+    P.A.enable_inner(ar, irt, imax, c->bodyq[2]);
+    P.Kp.enable_inner(ar, irt, imax, c->bodyq[2]);
+  }
+  for (int sp = 0; sp < 3; ++sp) P.X[sp].setup(c->s);
+  P.Kp.setup(c->s);
   const long N1 = F.N1, nent1 = F.p1.sell.nent;
   P.Ms = ar.alloc<T>(nent1);
   P.Aps = ar.alloc<T>(nent1);
@@ -1038,6 +1057,8 @@ void create3(chnss3_ctx *c, int n) {
     }
   }
   const std::vector<const double *> *x2 = p.mobility_kind != 0 ? X2s : nullptr;
+  if (p.inner_rtol > 0.0)
+    for (cudaStream_t &q : c->bodyq) CHNSS_CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
   if (p.mobility_kind != 0)
     for (int sp = 0; sp < 3; ++sp) c->Kks[sp] = ar.alloc<double>(nent1);
   if (p.precision == 0) {
@@ -1154,11 +1175,19 @@ void assemble3(chnss3_ctx *c, const chnss_state *st) {
   else setup_prec3(c, *c->p64, s);
 }
 
+// z = the hierarchy's result in FP64: the FP64 iterate of an inner solve
+// (an FP32 rounding would cap the preconditioner's accuracy), else x[0]
+template <typename T>
+void mg_output(MGHier<T> &h, long n, double *z, cudaStream_t s) {
+  if (h.inner_rtol > 0.0) vec_copy(n, h.iterate64(), z, s);
+  else vec_convert<T, double>(n, h.output(), z, s);
+}
+
 template <typename T>
 void mg_apply(MGHier<T> &h, long n, const double *r, double *z, cudaStream_t s) {
   vec_convert<double, T>(n, r, h.input(), s);
   h.apply(s);
-  vec_convert<T, double>(n, h.output(), z, s);
+  mg_output(h, n, z, s);
 }
 
 template <typename T>
@@ -1173,7 +1202,7 @@ void prec_ch3(chnss3_ctx *c, Prec3<T> &P, int sp, const double *r, double *z, cu
   SpmvArgs none;
   spmv_sell<T>(c->lv[0].p1, P.Ms, 1, X1.output(), X2.input(), SPMV_PLAIN, none, s);
   X2.apply(s);
-  vec_convert<T, double>(N1, X2.output(), z + N1, s);
+  mg_output(X2, N1, z + N1, s);
 }
 
 template <typename T>
@@ -1384,8 +1413,11 @@ extern "C" chnss_status chnss3_ctx_create(int n, const chnss_params *params, voi
     if (!params || !out) throw Error{CHNSS_ERR_ARG, "null argument"};
     if (n < 2 || n % 2 || n > 96) throw Error{CHNSS_ERR_ARG, "3D meshes: n even, 2 <= n <= 96"};
     const chnss_params &p = *params;
-    if (p.model != 0 || p.inner_rtol != 0.0 || p.precision < 0 || p.precision > 2)
-      throw Error{CHNSS_ERR_ARG, "the 3D step covers model 0, one V-cycle per block, precision 0-2"};
+    if (p.model != 0 || p.precision < 0 || p.precision > 2)
+      throw Error{CHNSS_ERR_ARG, "the 3D step covers model 0, precision 0-2"};
+    if (!(p.inner_rtol >= 0.0 && p.inner_rtol < 1.0)) throw Error{CHNSS_ERR_ARG, "inner_rtol must be in [0, 1)"};
+    if (p.inner_rtol > 0.0 && (p.inner_maxit < 1 || p.inner_maxit > 1000))
+      throw Error{CHNSS_ERR_ARG, "inner_maxit must be in [1, 1000]"};
     if (p.mobility_kind != 0 && p.mobility_kind != 1) throw Error{CHNSS_ERR_ARG, "mobility_kind must be 0 or 1"};
     if (!(p.tau > 0) || !(p.eta > 0) || p.restart < 1 || p.restart > 64 || p.maxit < 1)
       throw Error{CHNSS_ERR_ARG, "invalid parameters"};

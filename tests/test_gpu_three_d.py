@@ -1,7 +1,8 @@
 """The 3D step on the GPU (chnss3_step, Kuhn tetrahedra) against the 3D
 oracle: every solve of a step (relative L2 <= 1e-9 when the Krylov iteration
 counts agree, counts within +-1), two steps (the second with flow), a finer
-mesh, concentration-dependent mobility, mixed precision, concurrency,
+mesh, concentration-dependent mobility, inner multigrid solves to a
+tolerance, mixed precision, concurrency,
 determinism and the parameter checks."""
 import numpy as np
 import pytest
@@ -79,6 +80,13 @@ def test_step_3d_variable_mobility_finer_mesh(torch):
     _compare(torch, 8, _params(mobility_kind=1), seed=4, steps=1)
 
 
+def test_step_3d_inner_multigrid(torch):
+    """Every multigrid block solved to inner_rtol = 1e-4 (Sec. 5's AMG
+    tolerance; conditional loops inside the captured preconditioners), two
+    steps."""
+    _compare(torch, 4, _params(inner_rtol=1e-4, inner_maxit=20), seed=5)
+
+
 def test_step_3d_is_deterministic(torch):
     n = 4
     ctx = chnss.Context3(n, _params())
@@ -89,7 +97,8 @@ def test_step_3d_is_deterministic(torch):
         assert np.array_equal(a[k], b[k]), k
 
 
-@pytest.mark.parametrize("bad", [dict(mobility_kind=2), dict(precision=3), dict(model=1), dict(inner_rtol=1e-4)])
+@pytest.mark.parametrize("bad", [dict(mobility_kind=2), dict(precision=3), dict(model=1), dict(inner_rtol=1.5),
+                                 dict(inner_rtol=1e-4, inner_maxit=0)])
 def test_step_3d_parameter_errors(torch, bad):
     with pytest.raises(chnss.ChnssError):
         chnss.Context3(4, _params(**bad))
@@ -97,13 +106,13 @@ def test_step_3d_parameter_errors(torch, bad):
         chnss.Context3(3, _params())            # n must be even
 
 
-@pytest.mark.parametrize("precision,mobility", [(1, 0), (2, 0), (1, 1)])
-def test_step_3d_mixed_precision(torch, precision, mobility):
+@pytest.mark.parametrize("precision,mobility,inner", [(1, 0, 0.0), (2, 0, 0.0), (1, 1, 0.0), (1, 0, 1e-4)])
+def test_step_3d_mixed_precision(torch, precision, mobility, inner):
     """FP32 multigrid (precision 2: velocity hierarchy values in BF16) inside
     FP64 FGMRES: the 1e-8 residual is reached, and at an outer tolerance of
     1e-10 the step stays within 1e-6 of the oracle solved to 1e-12."""
     n = 8
-    p = _params(mobility_kind=mobility)
+    p = _params(mobility_kind=mobility, inner_rtol=inner, inner_maxit=20)
     o = t3.Oracle3D(n, dict(p, rtol=1e-12))
     ctx8 = chnss.Context3(n, dict(p, precision=precision))
     ctx10 = chnss.Context3(n, dict(p, precision=precision, rtol=1e-10))

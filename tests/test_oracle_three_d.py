@@ -251,3 +251,22 @@ def test_variable_mobility_step_matches_sparse_lu():
     d0, d1 = o.diagnostics(s0), o.diagnostics(s1)
     for i in range(2):
         assert d1["mass"][i] == pytest.approx(d0["mass"][i], rel=1e-9)
+
+
+def test_inner_multigrid_step_matches_sparse_lu():
+    """With every multigrid block iterated to inner_rtol = 1e-4 (Sec. 5's AMG
+    tolerance) the preconditioners change but the step still reaches the
+    sparse-LU step; the inner solves cut the AC iterations (4 -> 2 or 3)."""
+    n = 4
+    p = inputs.default_params()
+    p.update(rtol=1e-11, alpha=[1e-2] * 4)
+    s0 = inputs.initial_state_3d(n, seed=5)
+    plain = t3.Oracle3D(n, p).step(s0)[1]
+    o = t3.Oracle3D(n, dict(p, inner_rtol=1e-4, inner_maxit=20))
+    s1, info = o.step(s0)
+    x1 = t3.Oracle3D(n, p, exact=True).step(s0)[0]
+    assert all(v["converged"] for v in info.values())
+    assert info["ac"]["iters"] < plain["ac"]["iters"]
+    for key in ("phi", "mu", "Phi_v", "v", "p"):
+        a, b = np.ravel(s1[key]), np.ravel(x1[key])
+        assert np.linalg.norm(a - b) <= 1e-7 * max(np.linalg.norm(b), 1e-30), key
