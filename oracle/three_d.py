@@ -14,8 +14,12 @@ oracle/step.py with every form integrated exactly on tetrahedra: CH for
 three species with diag(MG(M + tau C), X^{-1} M X^{-1}), AC with MG, the air
 potential by Jacobi-PCG, Oseen with diag(MG(A), M_p^{-1} A_p K_p^{-1}),
 FGMRES(30) with CGS2, geometric multigrid with rediscretised coarse
-operators and injected coefficients.  Enclosed flow (no-slip on every face);
-evaporation through the top face z = lz, reference point (lx/2, ly/2, lz).
+operators and injected coefficients.  Enclosed flow (no-slip on every face),
+or with top_bc = 1 the open top of oracle/step.py: no-slip on the bottom and
+the side walls, the do-nothing condition on the top face (natural in the weak
+form), Dirichlet outflow rows of A_p and K_p on the top face in the PCD and
+no pressure normalisation; evaporation through the top face z = lz,
+reference point (lx/2, ly/2, lz).
 
 Conventions.  Cube (i, j, k) has id (k n + j) n + i; its tetrahedron p
 (p = index of the axis order sigma in PERMS) has vertices v0 = (i, j, k),
@@ -32,6 +36,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
+from .fem import p1_dirichlet
 from .krylov import chebyshev, fgmres, pcg
 from .mg import MG
 from .model import potential_partials
@@ -46,10 +51,11 @@ MASS_CHEB_BOUNDS = (0.5, 2.5)               # spectrum of D^{-1} M for P1 tetrah
 
 # ----------------------------------------------------------------------------
 class Mesh3D:
-    def __init__(self, n: int, lx: float = 1.0, ly: float = 1.0, lz: float = 1.0):
+    def __init__(self, n: int, lx: float = 1.0, ly: float = 1.0, lz: float = 1.0, top_free: bool = False):
         if n < 1:
             raise ValueError("n must be >= 1")
         self.n = n
+        self.top_free = top_free
         self.L = np.array([lx, ly, lz], dtype=float)
         self.h = self.L / n
         self.N1 = (n + 1) ** 3
@@ -90,9 +96,13 @@ class Mesh3D:
         return (lat[..., 2] * m + lat[..., 1]) * m + lat[..., 0]
 
     def p2_boundary(self):
-        """P2 nodes on the boundary (no-slip on every face, eqn:bc)."""
+        """P2 nodes with prescribed (zero) velocity: every face (eqn:bc), or,
+        on a top_free mesh, all but the open top face (its edges stay on the
+        side walls)."""
         m = 2 * self.n
-        return np.any((self.lat2 == 0) | (self.lat2 == m), axis=1)
+        side = np.any((self.lat2[:, :2] == 0) | (self.lat2[:, :2] == m), axis=1)
+        top = (self.lat2[:, 2] == m) & (not self.top_free)
+        return side | (self.lat2[:, 2] == 0) | top
 
     def p1_top(self):
         return self.lat1[:, 2] == self.n
@@ -445,6 +455,8 @@ def ns_system(forms, state, params):
     rhs_v = vf["Mv"] @ state["v"] / tau + korteweg(mesh, korteweg_tensor(mesh, state, params))
     rhs_v[np.repeat(vf["bnd"], 3)] = 0.0
     Ap = (forms.M / tau + params["eta"] * forms.K + convection_p1(mesh, state["v"], shift)).tocsr()
+    if mesh.top_free:
+        Ap = p1_dirichlet(Ap, mesh.p1_top())       # PCD outflow condition on the open top
     return A, vf["B"], rhs_v, Ap, shift
 
 
@@ -462,7 +474,8 @@ class Oracle3D:
         self.params = dict(params)
         self.exact = exact
         self.sizes = level_sizes(n)
-        self.meshes = [Mesh3D(s) for s in self.sizes]
+        self.top_free = self.params.get("top_bc", 0) == 1
+        self.meshes = [Mesh3D(s, top_free=self.top_free) for s in self.sizes]
         self.forms = [Forms3D(m, self.params) for m in self.meshes]
         self.P1 = [prolongation_p1(self.meshes[l + 1]) for l in range(len(self.sizes) - 1)]
         self.Pv = [prolongation_velocity(self.meshes[l + 1], self.meshes[l]) for l in range(len(self.sizes) - 1)]
@@ -545,7 +558,9 @@ class Oracle3D:
         nv = A.shape[0]
         rhs = np.concatenate([rhs_v, np.zeros(N1)])
         m = F.M @ np.ones(N1)
-        if self.exact:
+        if self.exact and self.top_free:
+            x, info["ns"] = _direct(sp.bmat([[A, B.T], [B, None]], format="csc"), rhs)
+        elif self.exact:
             K = sp.bmat([[A, B.T, None], [B, None, sp.csr_matrix(m[:, None])],
                          [None, sp.csr_matrix(m[None, :]), None]], format="csc")
             x, info["ns"] = _direct(K, np.concatenate([rhs, [0.0]]))
@@ -559,7 +574,10 @@ class Oracle3D:
                 mats.append(velocity_dirichlet((vf["Mv"] / tau + sp.kron(J2, sp.eye(3)) + vf["Ksym"]).tocsr(), vf["bnd"]))
             mgA = self._mg(mats, self.Pv, degree=VEL_SMOOTH_DEGREE, ratio=VEL_LO_RATIO)
             if self._Kp is None:
-                self._Kp = MG([fm.K for fm in self.forms], self.P1, singular=True)
+                if self.top_free:   # outflow: K_p with Dirichlet rows on the open top, non-singular
+                    self._Kp = MG([p1_dirichlet(fm.K, fm.mesh.p1_top()) for fm in self.forms], self.P1)
+                else:
+                    self._Kp = MG([fm.K for fm in self.forms], self.P1, singular=True)
             kp = self._Kp if not p.get("inner_rtol", 0.0) else (
                 lambda b: self._Kp.solve(b, p["inner_rtol"], p.get("inner_maxit", 20))[0])
             mdinv = 1.0 / F.M.diagonal()
@@ -574,7 +592,8 @@ class Oracle3D:
             rt, at = (p["ns_rtol"], p["ns_atol"]) if p.get("ns_rtol", 0.0) > 0 else (p["rtol"], p["atol"])
             x, info["ns"] = fgmres(op, prec, rhs, rt, at, p["restart"], p["maxit"])
         pr = x[nv:]
-        new["v"], new["p"] = x[:nv], pr - (m @ pr) / m.sum()
+        # enclosed flow: pressure in L^2_0 (Sec. 3); open top: fixed by the do-nothing condition
+        new["v"], new["p"] = x[:nv], pr if self.top_free else pr - (m @ pr) / m.sum()
         return new, info
 
     def diagnostics(self, state):

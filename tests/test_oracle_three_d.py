@@ -270,3 +270,61 @@ def test_inner_multigrid_step_matches_sparse_lu():
     for key in ("phi", "mu", "Phi_v", "v", "p"):
         a, b = np.ravel(s1[key]), np.ravel(x1[key])
         assert np.linalg.norm(a - b) <= 1e-7 * max(np.linalg.norm(b), 1e-30), key
+
+
+def test_open_top_masks():
+    """Open top: the prescribed-velocity P2 nodes are every face but the
+    interior of the top face ((2n - 1)^2 nodes fewer, its edges stay on the
+    side walls); K_p with Dirichlet rows on the (n + 1)^2 top nodes is
+    non-singular."""
+    n = 4
+    closed, open_ = t3.Mesh3D(n), t3.Mesh3D(n, top_free=True)
+    a, b = closed.p2_boundary(), open_.p2_boundary()
+    assert np.all(b <= a) and a.sum() - b.sum() == (2 * n - 1) ** 2
+    freed = a & ~b
+    assert np.all(open_.lat2[freed, 2] == 2 * n)
+    assert np.all((open_.lat2[freed, :2] > 0) & (open_.lat2[freed, :2] < 2 * n))
+    assert open_.p1_top().sum() == (n + 1) ** 2
+    Kd = p1_dirichlet_dense(t3.stiffness_p1(open_), open_.p1_top())
+    assert np.linalg.matrix_rank(Kd) == open_.N1
+
+
+def p1_dirichlet_dense(K, mask):
+    D = K.toarray()
+    D[mask, :] = 0.0
+    D[:, mask] = 0.0
+    D[mask, mask] = 1.0
+    return D
+
+
+@pytest.fixture(scope="module")
+def open_steps():
+    n = 4
+    p = inputs.default_params()
+    p.update(rtol=1e-11, alpha=[1e-2] * 4, top_bc=1)
+    o, ox = t3.Oracle3D(n, p), t3.Oracle3D(n, p, exact=True)
+    s0 = inputs.initial_state_3d(n, seed=6)
+    s1, i1 = o.step(s0)
+    s2, i2 = o.step(s1)
+    return o, (s1, s2), (i1, i2), (ox.step(s0)[0], ox.step(s1)[0])
+
+
+def test_open_top_step_matches_sparse_lu(open_steps):
+    o, steps, infos, exact = open_steps
+    for info in infos:
+        assert all(v["converged"] for v in info.values())
+    for got, ref in zip(steps, exact):
+        for key in ("phi", "mu", "Phi_v", "v", "p"):
+            a, b = np.ravel(got[key]), np.ravel(ref[key])
+            assert np.linalg.norm(a - b) <= 1e-7 * max(np.linalg.norm(b), 1e-30), key
+
+
+def test_open_top_flow_leaves_through_the_top(open_steps):
+    """The do-nothing top lets the velocity through the top face (zero there
+    for enclosed flow); the velocity stays discretely divergence-free."""
+    o, (s1, s2), _, _ = open_steps
+    mesh = o.mesh
+    top = (mesh.lat2[:, 2] == 2 * mesh.n) & ~mesh.p2_boundary()
+    assert np.abs(s2["v"].reshape(-1, 3)[top]).max() > 1e-5
+    assert np.abs(s2["v"].reshape(-1, 3)[mesh.p2_boundary()]).max() == 0.0
+    assert o.diagnostics(s2)["div"] < 1e-9
