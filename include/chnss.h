@@ -292,6 +292,8 @@ chnss_status chnss_inner_stats_read(chnss_ctx_t ctx, int reset, chnss_inner_stat
  *   CHNSS3_OP_KK0..2   weighted stiffness int kappa grad psi_a . grad psi_b of species 0..2 with the
  *                      concentration-dependent mobility kappa = gamma_i (phi_i (1 - phi_i) + mobility_m0)
  *                      (state->phi[i]; any mobility_kind)
+ *   CHNSS3_OP_VPROL_OPEN  CHNSS3_OP_VPROL on meshes with an open top (the top face's interior nodes
+ *                      are unknowns)
  * state (HOST arrays, 3D sizes) supplies v, mu, phi, Phi_v where needed
  * (may be NULL otherwise).  Call with val == NULL to get nrows, ncols and nnz
  * (the vector length for the loads); then with rowptr (nrows + 1), col and
@@ -299,7 +301,7 @@ chnss_status chnss_inner_stats_read(chnss_ctx_t ctx, int reset, chnss_inner_stat
 enum {
   CHNSS3_OP_M1 = 0, CHNSS3_OP_K1, CHNSS3_OP_C1, CHNSS3_OP_CP, CHNSS3_OP_M2, CHNSS3_OP_J2, CHNSS3_OP_KSYM,
   CHNSS3_OP_B, CHNSS3_OP_P1PROL, CHNSS3_OP_VPROL, CHNSS3_OP_LOADS, CHNSS3_OP_KORTEWEG, CHNSS3_OP_TOP,
-  CHNSS3_OP_KK0, CHNSS3_OP_KK1, CHNSS3_OP_KK2
+  CHNSS3_OP_KK0, CHNSS3_OP_KK1, CHNSS3_OP_KK2, CHNSS3_OP_VPROL_OPEN
 };
 chnss_status chnss3_host_operator(int n, int which, const chnss_params *params, const chnss_state *state,
                                   int *nrows, int *ncols, long long *nnz, int *rowptr, int *col, double *val);
@@ -324,6 +326,15 @@ chnss_status chnss3_host_operator(int n, int which, const chnss_params *params, 
  * synchronises the stream before returning. */
 typedef struct chnss3_ctx *chnss3_ctx_t;
 chnss_status chnss3_ctx_create(int n, const chnss_params *params, void *cuda_stream, chnss3_ctx_t *out);
+/* As chnss3_ctx_create with the velocity condition on the top face z = 1:
+ * top_bc 0: no-slip on every face (eqn:bc; the pressure normalised to zero
+ * mean after the Oseen solve); 1: open top as chnss_mesh_create_ex's
+ * top_bc = 1 in 2D: no-slip on the bottom and the side walls, the
+ * do-nothing condition on the top face, Dirichlet outflow rows of A_p and
+ * K_p on its nodes in the PCD, the pressure left as solved.  Other values:
+ * CHNSS_ERR_ARG. */
+chnss_status chnss3_ctx_create_ex(int n, int top_bc, const chnss_params *params, void *cuda_stream,
+                                  chnss3_ctx_t *out);
 chnss_status chnss3_ctx_destroy(chnss3_ctx_t ctx);
 chnss_status chnss3_sizes(chnss3_ctx_t ctx, int *N1, int *N2);
 chnss_status chnss3_step(chnss3_ctx_t ctx, const chnss_state *in, chnss_state *out, chnss_solve_info *info);

@@ -125,6 +125,8 @@ EXPORTS = {
     "chnss_inner_stats_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(InnerStats)]),
     "chnss3_ctx_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Params), ctypes.c_void_p,
                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "chnss3_ctx_create_ex": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params), ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_void_p)]),
     "chnss3_ctx_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "chnss3_sizes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "chnss3_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.POINTER(State),
@@ -393,15 +395,17 @@ class Context:
 
 class Context3:
     """The 3D step on the Kuhn mesh of n^3 cubes of the unit box
-    (chnss3_ctx_create / chnss3_step): device states with phi (3, N1),
-    mu (4, N1), Phi_v, p (N1) and v (3 N2)."""
+    (chnss3_ctx_create_ex / chnss3_step): device states with phi (3, N1),
+    mu (4, N1), Phi_v, p (N1) and v (3 N2).  params["top_bc"] = 1 opens
+    the top face (do-nothing condition); default 0, no-slip everywhere."""
 
     def __init__(self, n: int, params: dict, stream=None):
         lib = load()
         self._p = make_params(params)
         h = ctypes.c_void_p()
         sptr = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
-        _check(lib.chnss3_ctx_create(n, ctypes.byref(self._p), sptr, ctypes.byref(h)))
+        _check(lib.chnss3_ctx_create_ex(n, int(params.get("top_bc", 0)), ctypes.byref(self._p), sptr,
+                                        ctypes.byref(h)))
         self._h = h
         a, b = ctypes.c_int(), ctypes.c_int()
         _check(lib.chnss3_sizes(h, ctypes.byref(a), ctypes.byref(b)))
@@ -434,7 +438,7 @@ class Context3:
 
 
 OPS3 = ("M1", "K1", "C1", "CP", "M2", "J2", "KSYM", "B", "P1PROL", "VPROL", "LOADS", "KORTEWEG", "TOP",
-        "KK0", "KK1", "KK2")
+        "KK0", "KK1", "KK2", "VPROL_OPEN")
 
 
 def host_operator3(n: int, which: str, params: dict, state: dict = None):

@@ -141,15 +141,20 @@ struct Mesh3Host {
     for (int v = 0; v < 4; ++v)
       for (int d = 0; d < 3; ++d) x[v][d] = lat[(e * 4 + v) * 3 + d] * h[d];
   }
+  bool top_free = false;   // open (do-nothing) top face
+  // P2 nodes with prescribed (zero) velocity: every face, or all but the
+  // open top face (its edges stay on the side walls)
   bool p2_boundary(int id) const {
     const int m = 2 * n + 1, A = id % m, B = (id / m) % m, C = id / (m * m);
-    return A == 0 || B == 0 || C == 0 || A == m - 1 || B == m - 1 || C == m - 1;
+    return A == 0 || B == 0 || C == 0 || A == m - 1 || B == m - 1 || (C == m - 1 && !top_free);
   }
+  bool p1_top(int id) const { return id / ((n + 1) * (n + 1)) == n; }
 };
 
-Mesh3Host make_mesh3(int n, const double L[3]) {
+Mesh3Host make_mesh3(int n, const double L[3], bool top_free = false) {
   Mesh3Host M;
   M.n = n;
+  M.top_free = top_free;
   M.N1 = (long)(n + 1) * (n + 1) * (n + 1);
   M.N2 = (long)(2 * n + 1) * (2 * n + 1) * (2 * n + 1);
   M.E = 6L * n * n * n;
@@ -304,7 +309,7 @@ HostCSR velocity_prolongation3(const Mesh3Host &c, const Mesh3Host &f) {
 
 enum Op3 {
   OP3_M1 = 0, OP3_K1, OP3_C1, OP3_CP, OP3_M2, OP3_J2, OP3_KSYM, OP3_B, OP3_P1PROL, OP3_VPROL,
-  OP3_LOADS, OP3_KORTEWEG, OP3_TOP, OP3_KK0, OP3_KK1, OP3_KK2, OP3_COUNT
+  OP3_LOADS, OP3_KORTEWEG, OP3_TOP, OP3_KK0, OP3_KK1, OP3_KK2, OP3_VPROL_OPEN, OP3_COUNT
 };
 
 void element_fields(const Mesh3Host &M, long e, const double *v, double vk[10][3]) {
@@ -412,10 +417,13 @@ HostCSR host_operator3(int n, int which, const chnss_params &p, const chnss_stat
         tet_div(R, vol, g, b);
       });
     case OP3_P1PROL:
-    case OP3_VPROL: {
+    case OP3_VPROL:
+    case OP3_VPROL_OPEN: {
       if (n % 2) throw Error{CHNSS_ERR_ARG, "transfers need an even n (coarse mesh n / 2)"};
-      const Mesh3Host C = make_mesh3(n / 2, L);
-      return which == OP3_P1PROL ? p1_prolongation3(C) : velocity_prolongation3(C, M);
+      const bool open = which == OP3_VPROL_OPEN;
+      const Mesh3Host C = make_mesh3(n / 2, L, open);
+      if (which == OP3_P1PROL) return p1_prolongation3(C);
+      return velocity_prolongation3(C, open ? make_mesh3(n, L, true) : M);
     }
     case OP3_LOADS:
     case OP3_KORTEWEG:
@@ -680,6 +688,13 @@ __global__ void k3_ac_rhs(int N1, const double *load, const double *top, const d
   rhs[i] += -tg * load[i] + flux * j * top[i];
 }
 
+// vals[idx[k]] = value: the Dirichlet outflow rows and columns of A_p on the
+// open top (zeros, then ones on the diagonal)
+__global__ void k3_set_entries(int n, const int *idx, double value, double *vals) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) vals[idx[k]] = value;
+}
+
 __global__ void k3_air(int N1, const double *p0, const double *p1, const double *p2, double *out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < N1) out[i] = 1.0 - p0[i] - p1[i] - p2[i];
@@ -700,6 +715,7 @@ struct Level3 {
   Transfer t1, tv;                 // from the next coarser level
   Gather g1, gj;                   // element buffers -> P1 CSR, P2 convection -> velocity CSR
   double *M1 = nullptr, *K1 = nullptr, *ACb = nullptr, *Aconst = nullptr;
+  double *Kp = nullptr;            // K_p of the PCD: K1, or with Dirichlet rows on an open top
   double *L = nullptr, *AC = nullptr, *A = nullptr, *X[3] = {nullptr, nullptr, nullptr};
   double *vl = nullptr, *mul = nullptr;   // injected v (3 N2) and mu (4 N1), levels >= 1
   // concentration-dependent mobility: X2 = tau K_kappa + a M per species,
@@ -729,6 +745,9 @@ struct chnss3_ctx {
   chnss::Gather gl, gk;                         // loads -> P1 nodes, Korteweg -> velocity dofs
   int *bnd = nullptr;                           // fine P2 boundary mask
   int ref = 0;
+  int top_bc = 0;                               // 1: open (do-nothing) top face
+  int *apz = nullptr, *apd = nullptr;           // open top: A_p entries set to 0, diagonal set to 1
+  int napz = 0, napd = 0;
   double *Bs = nullptr, *Bts = nullptr, *Mv = nullptr, *Apb = nullptr, *Ap = nullptr, *top = nullptr;
   double *Ls = nullptr, *Ks = nullptr, *Ms = nullptr, *ACs = nullptr, *As = nullptr;
   double *Kks[3] = {nullptr, nullptr, nullptr};   // SELL copies of K_kappa (mobility_kind 1)
@@ -797,7 +816,7 @@ void build_level3(chnss3_ctx *c, Level3 &L, int n, bool fine, const Mesh3Host *c
   Arena &ar = c->ar;
   const auto &p = c->p;
   const double box[3] = {1.0, 1.0, 1.0};
-  const Mesh3Host M = make_mesh3(n, box);
+  const Mesh3Host M = make_mesh3(n, box, c->top_bc == 1);
   L.n = n;
   L.N1 = M.N1;
   L.N2 = M.N2;
@@ -834,6 +853,19 @@ void build_level3(chnss3_ctx *c, Level3 &L, int n, bool fine, const Mesh3Host *c
   std::vector<double> m1 = on_pattern(L.p1, hM), k1 = on_pattern(L.p1, hK);
   L.M1 = ar.upload(m1);
   L.K1 = ar.upload(k1);
+  L.Kp = L.K1;
+  std::vector<int> zero_pos, diag_pos;   // open top: Dirichlet rows and columns on the top nodes
+  if (M.top_free) {
+    std::vector<double> kp = k1;
+    for (int r = 0; r < N1; ++r)
+      for (int k = L.p1.h_rowptr[r]; k < L.p1.h_rowptr[r + 1]; ++k) {
+        const int cc = L.p1.h_col[k];
+        if (!M.p1_top(r) && !M.p1_top(cc)) continue;
+        kp[k] = r == cc ? 1.0 : 0.0;
+        (r == cc ? diag_pos : zero_pos).push_back(k);
+      }
+    L.Kp = ar.upload(kp);
+  }
   std::vector<double> acb(m1.size());
   for (size_t k = 0; k < m1.size(); ++k) acb[k] = m1[k] + p.tau * p.delta_v * k1[k];
   L.ACb = ar.upload(acb);
@@ -908,6 +940,12 @@ void build_level3(chnss3_ctx *c, Level3 &L, int n, bool fine, const Mesh3Host *c
   for (int i = 0; i < N2; ++i) bnd[i] = M.p2_boundary(i) ? 1 : 0;
   c->bnd = ar.upload(bnd);
   c->ref = M.id1(n / 2, n / 2, n);
+  if (M.top_free) {
+    c->apz = ar.upload(zero_pos);
+    c->apd = ar.upload(diag_pos);
+    c->napz = (int)zero_pos.size();
+    c->napd = (int)diag_pos.size();
+  }
   std::vector<double> dinv(N1);
   const std::vector<int> dpos = diag_positions(L.p1);
   for (int r = 0; r < N1; ++r) dinv[r] = 1.0 / m1[dpos[r]];
@@ -930,7 +968,7 @@ void init_prec3(chnss3_ctx *c, Prec3<T> &P, const std::vector<const Pattern *> &
     P.X[sp].init(ar, 0, false, p1s, d1s, Xs[sp], t1s, c->partial);
     if (X2s) P.X2[sp].init(ar, 0, false, p1s, d1s, X2s[sp], t1s, c->partial);   // set up every step
   }
-  P.Kp.init(ar, 0, true, p1s, d1s, K1s, t1s, c->partial);
+  P.Kp.init(ar, 0, c->top_bc != 1, p1s, d1s, K1s, t1s, c->partial);   // singular for enclosed flow
   P.A.degree = 4;      // as the 2D velocity operator: degree 4 on [hi / 16, hi]
   P.A.ratio = 16.0;
   P.A.init(ar, 0, false, pvs, dvs, As, tvs, c->partial);
@@ -971,7 +1009,7 @@ void create3(chnss3_ctx *c, int n) {
   c->lv.resize(nl);
   const double box[3] = {1.0, 1.0, 1.0};
   for (int l = 0; l < nl; ++l) {
-    const Mesh3Host coarse = l + 1 < nl ? make_mesh3(sizes[l + 1], box) : Mesh3Host{};
+    const Mesh3Host coarse = l + 1 < nl ? make_mesh3(sizes[l + 1], box, c->top_bc == 1) : Mesh3Host{};
     build_level3(c, c->lv[l], sizes[l], l == 0, l + 1 < nl ? &coarse : nullptr);
   }
   const Level3 &F = c->lv[0];
@@ -1049,7 +1087,7 @@ void create3(chnss3_ctx *c, int n) {
     tvs.push_back(&L.tv);
     Ls.push_back(L.L);
     ACs.push_back(L.AC);
-    K1s.push_back(L.K1);
+    K1s.push_back(L.Kp);
     As.push_back(L.A);
     for (int sp = 0; sp < 3; ++sp) {
       Xs[sp].push_back(L.X[sp]);
@@ -1142,6 +1180,12 @@ void assemble3(chnss3_ctx *c, const chnss_state *st) {
   k3_conv<<<nb3(F.E), kTPB3, 0, s>>>(F.geo, f, 0, 1, c->ebuf);
   CHNSS_LAUNCH_CK();
   launch_gather(F.g1, 1, c->ebuf, 1.0, c->Apb, 1.0, c->Ap, s);
+  if (c->napz > 0) {   // PCD outflow condition on the open top
+    k3_set_entries<<<nb3(c->napz), kTPB3, 0, s>>>(c->napz, c->apz, 0.0, c->Ap);
+    CHNSS_LAUNCH_CK();
+    k3_set_entries<<<nb3(c->napd), kTPB3, 0, s>>>(c->napd, c->apd, 1.0, c->Ap);
+    CHNSS_LAUNCH_CK();
+  }
   // potential and Korteweg loads
   k3_loads<<<nb3(F.E), kTPB3, 0, s>>>(F.geo, f, c->ebuf, c->kbuf);
   CHNSS_LAUNCH_CK();
@@ -1348,6 +1392,7 @@ chnss_status group_ns3(chnss3_ctx *c, chnss_state *out, chnss_solve_info *inf, c
   const chnss_status st = fgmres(op, c->rhs[5], c->xsol[5], rt, at, p.maxit, c->kw, &inf[5], q);
   vec_copy(nv, c->xsol[5], out->v, q);
   vec_copy(N1, c->xsol[5] + nv, out->p, q);
+  if (c->top_bc == 1) return st;   // the do-nothing top fixes the pressure
   // zero-mean pressure: p -= (1^T M p) / (1^T M 1), 1^T M 1 = |box| = 1
   SpmvArgs none;
   spmv_csr<double>(F.p1, F.M1, 1, out->p, c->mt, SPMV_PLAIN, none, q);
@@ -1406,11 +1451,13 @@ chnss_status step3(chnss3_ctx *c, const chnss_state *in, chnss_state *out, chnss
 }  // namespace
 }  // namespace chnss
 
-extern "C" chnss_status chnss3_ctx_create(int n, const chnss_params *params, void *cuda_stream, chnss3_ctx_t *out) {
+extern "C" chnss_status chnss3_ctx_create_ex(int n, int top_bc, const chnss_params *params, void *cuda_stream,
+                                            chnss3_ctx_t *out) {
   using namespace chnss;
   chnss3_ctx *c = nullptr;
   try {
     if (!params || !out) throw Error{CHNSS_ERR_ARG, "null argument"};
+    if (top_bc != 0 && top_bc != 1) throw Error{CHNSS_ERR_ARG, "top_bc must be 0 (no-slip) or 1 (open top)"};
     if (n < 2 || n % 2 || n > 96) throw Error{CHNSS_ERR_ARG, "3D meshes: n even, 2 <= n <= 96"};
     const chnss_params &p = *params;
     if (p.model != 0 || p.precision < 0 || p.precision > 2)
@@ -1425,6 +1472,7 @@ extern "C" chnss_status chnss3_ctx_create(int n, const chnss_params *params, voi
       if (!(p.beta[i] > 0) || !(p.gamma[i] > 0)) throw Error{CHNSS_ERR_ARG, "beta_i, gamma_i must be > 0"};
     c = new chnss3_ctx;
     c->p = p;
+    c->top_bc = top_bc;
     if (cuda_stream) {
       c->s = static_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -1443,6 +1491,10 @@ extern "C" chnss_status chnss3_ctx_create(int n, const chnss_params *params, voi
     set_global_error(e.what());
     return CHNSS_ERR_ARG;
   }
+}
+
+extern "C" chnss_status chnss3_ctx_create(int n, const chnss_params *params, void *cuda_stream, chnss3_ctx_t *out) {
+  return chnss3_ctx_create_ex(n, 0, params, cuda_stream, out);
 }
 
 extern "C" chnss_status chnss3_ctx_destroy(chnss3_ctx_t ctx) {

@@ -2,7 +2,7 @@
 oracle: every solve of a step (relative L2 <= 1e-9 when the Krylov iteration
 counts agree, counts within +-1), two steps (the second with flow), a finer
 mesh, concentration-dependent mobility, inner multigrid solves to a
-tolerance, mixed precision, concurrency,
+tolerance, the open top face, mixed precision, concurrency,
 determinism and the parameter checks."""
 import numpy as np
 import pytest
@@ -87,6 +87,17 @@ def test_step_3d_inner_multigrid(torch):
     _compare(torch, 4, _params(inner_rtol=1e-4, inner_maxit=20), seed=5)
 
 
+def test_step_3d_open_top(torch):
+    """Open (do-nothing) top face: no-slip on the bottom and the side walls,
+    Dirichlet outflow rows of A_p and K_p in the PCD, no pressure
+    normalisation; two steps."""
+    _compare(torch, 4, _params(top_bc=1), seed=6)
+
+
+def test_step_3d_open_top_finer_mesh(torch):
+    _compare(torch, 8, _params(top_bc=1, mobility_kind=1), seed=8, steps=1)
+
+
 def test_step_3d_is_deterministic(torch):
     n = 4
     ctx = chnss.Context3(n, _params())
@@ -104,6 +115,8 @@ def test_step_3d_parameter_errors(torch, bad):
         chnss.Context3(4, _params(**bad))
     with pytest.raises(chnss.ChnssError):
         chnss.Context3(3, _params())            # n must be even
+    with pytest.raises(chnss.ChnssError):
+        chnss.Context3(4, _params(top_bc=2))    # top_bc is 0 or 1
 
 
 @pytest.mark.parametrize("precision,mobility,inner", [(1, 0, 0.0), (2, 0, 0.0), (1, 1, 0.0), (1, 0, 1e-4)])

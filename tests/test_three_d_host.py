@@ -64,6 +64,16 @@ def test_transfers(case):
     _same(chnss.host_operator3(N, "VPROL", p), t3.prolongation_velocity(coarse, mesh), rel=1e-15)
 
 
+def test_open_top_transfer(case):
+    """Velocity prolongation between meshes with an open top face: the top
+    face's interior nodes are unknowns on both meshes."""
+    mesh, _, p = case
+    coarse, fine = t3.Mesh3D(N // 2, top_free=True), t3.Mesh3D(N, top_free=True)
+    P = chnss.host_operator3(N, "VPROL_OPEN", p)
+    _same(P, t3.prolongation_velocity(coarse, fine), rel=1e-15)
+    assert P.nnz > chnss.host_operator3(N, "VPROL", p).nnz
+
+
 def test_loads(case):
     mesh, st, p = case
     got = chnss.host_operator3(N, "LOADS", p, st).reshape(5, mesh.N1)
