@@ -79,3 +79,30 @@ def test_params_struct_matches_header():
         for nm in rest.split(","):
             fields.append(re.sub(r"\[.*\]", "", nm).strip())
     assert fields == [f for f, _ in chnss.Params._fields_]
+
+
+def test_three_d_argument_errors_need_no_device(lib):
+    """chnss3_ctx_create / _create_ex reject bad meshes and parameter sets on
+    the host, before any device call."""
+    from paper_2501_11767_gb300 import inputs
+    h = ctypes.c_void_p()
+
+    def create(n, top_bc=0, **kw):
+        p = chnss.make_params(dict(inputs.default_params(), **kw))
+        return lib.chnss3_ctx_create_ex(n, top_bc, ctypes.byref(p), None, ctypes.byref(h))
+
+    assert create(3) == 1                                    # odd n
+    assert create(98) == 1                                   # above the 3D size limit
+    assert create(4, top_bc=2) == 1                          # unknown top condition
+    assert b"top_bc" in lib.chnss_last_error(None)
+    assert create(4, mobility_kind=2) == 1
+    assert create(4, inner_rtol=1.5) == 1
+    assert create(4, inner_rtol=1e-4, inner_maxit=0) == 1
+    assert create(4, model=1) == 1                           # solvent-air sub-model is 2D only
+    assert create(4, precision=3) == 1
+    assert create(4, tau=0.0) == 1
+    assert lib.chnss3_ctx_create(4, None, None, ctypes.byref(h)) == 1
+    assert lib.chnss3_step(None, None, None, None) == 1
+    assert lib.chnss3_sizes(None, None, None) == 1
+    assert lib.chnss3_set_step_concurrency(None, 1) == 1
+    assert lib.chnss3_ctx_destroy(None) == 0
