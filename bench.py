@@ -35,7 +35,6 @@ REF_SAMPLE_N = 128          # --impl reference: one oracle step on 128 x 128 per
 METRIC = "time steps/s at 1M nodes (1024x1024 P1 mesh, FGMRES to 1e-8 relative residual)"
 # FP64 pipe of this GB300: 152 SMs x 2 FP64 FMA per clock x 2 FLOP x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-FP64_BALANCE_FLOP_PER_BYTE = FP64_PEAK_TFLOPS * 1e12 / 6764.7e9   # ~0.19 FLOP/B
 
 
 def peaks():
@@ -295,7 +294,8 @@ def run_gpu(args):
         d = kinds[name]
         ms_l = d["ms"] / d["launches"]
         gbps = d["bytes"] / (d["ms"] * 1e-3) / 1e9
-        if d.get("flops", 0.0) > 0 and d["flops"] / d["bytes"] > FP64_BALANCE_FLOP_PER_BYTE:
+        # FP64 balance point, FLOP per byte of the measured HBM bandwidth (~0.19)
+        if d.get("flops", 0.0) > 0 and d["flops"] / d["bytes"] > FP64_PEAK_TFLOPS * 1e12 / (peak * 1e9):
             tf = d["flops"] / (d["ms"] * 1e-3) / 1e12
             return {"kernel": name, "bound": "alu", "achieved": round(tf, 4), "peak": FP64_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": round(tf / FP64_PEAK_TFLOPS, 4),
