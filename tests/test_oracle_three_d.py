@@ -1,9 +1,12 @@
 """Pins of the 3D oracle (Kuhn tetrahedra, oracle/three_d.py): quadrature
 exactness, mesh geometry, closed forms of the P1 matrices (the Kuhn P1
 stiffness is the 7-point finite-difference Laplacian), Taylor-Hood
-identities, nested transfers, manufactured-solution rates, and properties
-of whole steps: the Krylov step against sparse LU, mass conservation,
-discretely divergence-free velocity (CPU only)."""
+identities, nested transfers, manufactured-solution rates, closed forms of
+the potential and Korteweg loads, the weighted stiffness of the
+concentration-dependent mobility, the open top's masks, and properties of
+whole steps: the Krylov step against sparse LU (also with the variable
+mobility, inner solves and the open top), mass conservation, discretely
+divergence-free velocity (CPU only)."""
 import math
 
 import numpy as np
@@ -328,3 +331,54 @@ def test_open_top_flow_leaves_through_the_top(open_steps):
     assert np.abs(s2["v"].reshape(-1, 3)[top]).max() > 1e-5
     assert np.abs(s2["v"].reshape(-1, 3)[mesh.p2_boundary()]).max() == 0.0
     assert o.diagnostics(s2)["div"] < 1e-9
+
+
+def _linear_state(mesh):
+    x, y, z = mesh.x1.T
+    return {"phi": np.stack([0.3 + 0.05 * (x + 2 * y + 3 * z), 0.25 + 0.04 * (x - y), np.full(mesh.N1, 0.4)]),
+            "Phi_v": 0.2 * z, "mu": np.zeros((4, mesh.N1)), "v": np.zeros(3 * mesh.N2)}
+
+
+def test_korteweg_load_of_linear_fields():
+    """Linear fields give a constant Korteweg tensor G, and then int G grad zeta_a
+    is the boundary integral of zeta_a G n: zero at interior P2 nodes, and at a
+    node inside the top face G e_z times int_top zeta_a, which is h^2 / 3 for an
+    edge midpoint (two triangles of area h^2 / 2, a third each) and 0 for a
+    vertex."""
+    n = 4
+    mesh = t3.Mesh3D(n)
+    p = dict(inputs.default_params(), beta=[0.01, 0.02, 0.1, 1.0], beta_v=0.7)
+    st = _linear_state(mesh)
+    Gt = t3.korteweg_tensor(mesh, st, p)
+    G = Gt[0]
+    assert np.allclose(Gt, G[None], atol=1e-15) and np.abs(G).max() > 1e-3
+    L = t3.korteweg(mesh, Gt).reshape(-1, 3)
+    lat, m = mesh.lat2, 2 * n
+    inner = np.all((lat > 0) & (lat < m), axis=1)
+    assert np.abs(L[inner]).max() < 1e-15
+    top = (lat[:, 2] == m) & np.all((lat[:, :2] > 0) & (lat[:, :2] < m), axis=1)
+    mid = top & ((lat[:, 0] % 2 == 1) | (lat[:, 1] % 2 == 1))
+    h2 = mesh.h[0] * mesh.h[1]
+    assert np.allclose(L[mid], G[:, 2][None] * h2 / 3.0, rtol=1e-12, atol=1e-16)
+    assert np.abs(L[top & ~mid]).max() < 1e-15
+
+
+def test_potential_loads_constant_and_linear_fields():
+    """Constant fields: int df/dphi_k psi_a = df/dphi_k (M 1)_a (the partials are
+    pinned by finite differences in 2D).  Linear fields: the integrands are
+    polynomials of degree <= 7, so a degree-11 rule gives the same loads."""
+    mesh = t3.Mesh3D(3)
+    c = np.full(mesh.N1, 1.0)
+    loads = t3.potential_loads(mesh, np.stack([0.3 * c, 0.25 * c, 0.4 * c]), 0.2 * c)
+    d = t3.potential_partials(0.3, 0.25, 0.4, 0.05, 0.2)
+    m1 = t3.mass_p1(mesh) @ c
+    for k in range(5):
+        assert np.allclose(loads[k], d[k] * m1, rtol=1e-12, atol=1e-15)
+    st = _linear_state(mesh)
+    lin = t3.potential_loads(mesh, st["phi"], st["Phi_v"])
+    for k in range(5):
+        def integrand(lam, k=k):
+            pp, pn, ps = (t3.p1_field_at(mesh, st["phi"][i], lam) for i in range(3))
+            return t3.potential_partials(pp, pn, ps, 1.0 - pp - pn - ps, t3.p1_field_at(mesh, st["Phi_v"], lam))[k]
+        ref = t3.load_p1(mesh, integrand, 11)
+        assert np.allclose(lin[k], ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())
