@@ -110,6 +110,23 @@ def test_p2_identities():
     assert np.max(np.abs(fem.convection_p2(mesh, v) @ one)) < 1e-13
 
 
+def test_symmetric_gradient_form_on_quadratics():
+    """At interior P2 nodes K_sym u = -eta int div(2 sym grad u) zeta_a: (2, 0)
+    for u = (y^2, 0) and (4, 0) for u = (x^2, 0); the Laplacian form would give
+    2 for both, so this fixes the symmetric gradient and its factor 2 (the
+    Stokes MMS uses a divergence-free field, for which the two forms agree)."""
+    mesh = Mesh(6)
+    eta = 1.3
+    K = fem.ksym(mesh, eta)
+    x, y = mesh.x2[:, 0], mesh.x2[:, 1]
+    w = fem.mass_p2(mesh) @ np.ones(mesh.N2)
+    inner = np.all((mesh.lat2 > 0) & (mesh.lat2 < 2 * mesh.n), axis=1)
+    for ux, dx in ((y * y, 2.0), (x * x, 4.0)):
+        r = (K @ np.stack([ux, 0 * ux], 1).ravel()).reshape(-1, 2)
+        assert np.abs(r[inner, 0] + eta * dx * w[inner]).max() < 1e-11 * eta * dx * np.abs(w).max()
+        assert np.abs(r[inner, 1]).max() < 1e-14
+
+
 def test_convection_integration_by_parts():
     """C + C^T = int_{dOmega} (v.n) psi_a psi_b - int div(v) psi_a psi_b.
     For v = (y (1 - y), 0) (divergence-free, v.n = 0 on top and bottom) the

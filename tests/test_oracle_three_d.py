@@ -382,3 +382,45 @@ def test_potential_loads_constant_and_linear_fields():
             return t3.potential_partials(pp, pn, ps, 1.0 - pp - pn - ps, t3.p1_field_at(mesh, st["Phi_v"], lam))[k]
         ref = t3.load_p1(mesh, integrand, 11)
         assert np.allclose(lin[k], ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())
+
+
+def test_convection_of_polynomials():
+    """P1 and P2 convection by a quadratic velocity (exact in P2) with a
+    constant shift s: C(v, s) x = int (v_x - s_x) psi_a and
+    J(v, s) q = int ((v - s) . grad q) zeta_a for the quadratic q = x y + z^2,
+    computed from the analytic fields at the quadrature points."""
+    m = t3.Mesh3D(2)
+    X = m.x2
+    vfun = lambda x, y, z: (y * y, x * z, x + y)                                        # noqa: E731
+    v = np.stack(vfun(X[:, 0], X[:, 1], X[:, 2]), axis=1).ravel()
+    s = np.array([0.3, -0.2, 0.1])
+    shift = np.tile(s, (m.E, 1))
+    C = t3.convection_p1(m, v, shift)
+    ref = t3.load_p1(m, lambda lam: vfun(*np.moveaxis(t3.quad_points(m, lam), -1, 0))[0] - s[0], 3)
+    assert np.allclose(C @ m.x1[:, 0], ref, rtol=1e-12, atol=1e-15)
+    q = X[:, 0] * X[:, 1] + X[:, 2] ** 2
+    J = t3.convection_p2(m, v, shift)
+
+    def vgq(x, y, z):
+        vx, vy, vz = vfun(x, y, z)
+        val = (vx - s[0]) * y + (vy - s[1]) * x + (vz - s[2]) * 2 * z
+        return val, 0.0 * x, 0.0 * x
+    ref2 = t3.load_velocity(m, vgq, 5)[0::3]
+    assert np.allclose(J @ q, ref2, rtol=1e-12, atol=1e-15)
+
+
+def test_symmetric_gradient_form_on_quadratics():
+    """At interior P2 nodes K_sym u = -eta int div(2 sym grad u) zeta_a: for
+    u = (y^2, 0, 0) the divergence is (2, 0, 0), for u = (x^2, 0, 0) it is
+    (4, 0, 0) (the Laplacian form would give 2 for both)."""
+    m = t3.Mesh3D(4)
+    eta = 1.3
+    K = t3.ksym(m, eta)
+    X = m.x2
+    w = t3.mass_p2(m) @ np.ones(m.N2)
+    inner = np.all((m.lat2 > 0) & (m.lat2 < 2 * m.n), axis=1)
+    zero = np.zeros(m.N2)
+    for ux, dx in ((X[:, 1] ** 2, 2.0), (X[:, 0] ** 2, 4.0)):
+        r = (K @ np.stack([ux, zero, zero], axis=1).ravel()).reshape(-1, 3)
+        assert np.abs(r[inner, 0] + eta * dx * w[inner]).max() < 1e-11 * eta * dx * np.abs(w).max()
+        assert np.abs(r[inner, 1:]).max() < 1e-14
