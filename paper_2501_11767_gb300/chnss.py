@@ -190,29 +190,49 @@ def make_params(d: dict) -> Params:
     return p
 
 
-def _ptr(t):
+def _ptr(t, n=None, where=None):
+    """Address of a contiguous float64 array.  n: the number of elements the
+    call reads or writes (a shorter array is refused); where: "device" (a
+    CUDA tensor), "host" (a numpy array or CPU tensor) or None (unchecked).
+    The C ABI takes bare pointers, so these checks are the only guard against
+    out-of-bounds accesses from a wrongly sized or placed array."""
     if t is None:
         return None
     if hasattr(t, "data_ptr"):
         if not t.is_contiguous() or str(t.dtype) != "torch.float64":
             raise ValueError("chnss needs contiguous float64 tensors")
-        return t.data_ptr()
-    if isinstance(t, np.ndarray):
+        if where == "device" and not t.is_cuda:
+            raise ValueError("chnss needs CUDA tensors here (device pointers)")
+        if where == "host" and t.is_cuda:
+            raise ValueError("chnss needs host arrays here")
+        size = t.numel()
+        ptr = t.data_ptr()
+    elif isinstance(t, np.ndarray):
         if t.dtype != np.float64 or not t.flags["C_CONTIGUOUS"]:
             raise ValueError("chnss needs C-contiguous float64 arrays")
-        return t.ctypes.data
-    raise TypeError(type(t))
+        if where == "device":
+            raise ValueError("chnss needs CUDA tensors here (device pointers), not numpy arrays")
+        size = t.size
+        ptr = t.ctypes.data
+    else:
+        raise TypeError(type(t))
+    if n is not None and size < n:
+        raise ValueError(f"chnss: an array of {size} elements where {n} are needed")
+    return ptr
 
 
-def make_state(d: dict) -> State:
+def make_state(d: dict, N1: int = None, N2: int = None, dim: int = 2, where: str = None) -> State:
+    """chnss_state of the arrays of d; with N1, N2 (and the space dimension)
+    every field's length is checked, with where its placement (see _ptr)."""
+    nv = dim * N2 if N2 is not None else None
     s = State()
     for i in range(3):
-        s.phi[i] = _ptr(d["phi"][i])
+        s.phi[i] = _ptr(d["phi"][i], N1, where)
     for i in range(4):
-        s.mu[i] = _ptr(d["mu"][i])
-    s.Phi_v = _ptr(d["Phi_v"])
-    s.v = _ptr(d["v"])
-    s.p = _ptr(d["p"])
+        s.mu[i] = _ptr(d["mu"][i], N1, where)
+    s.Phi_v = _ptr(d["Phi_v"], N1, where)
+    s.v = _ptr(d["v"], nv, where)
+    s.p = _ptr(d["p"], N1, where)
     return s
 
 
@@ -279,8 +299,11 @@ class Context:
         z = lambda *s: torch.zeros(*s, dtype=torch.float64, device=device)  # noqa: E731
         return {"phi": z(3, N1), "mu": z(4, N1), "Phi_v": z(N1), "v": z(2 * N2), "p": z(N1)}
 
+    def _state(self, d: dict, where: str = "device") -> State:
+        return make_state(d, self.mesh.N1, self.mesh.N2, 2, where)
+
     def assemble(self, state: dict):
-        s = make_state(state)
+        s = self._state(state)
         _check(load().chnss_assemble(self._h, ctypes.byref(s)), self._h)
 
     def solve(self, sys: int, rhs=None, x=None, check: bool = True):
@@ -289,7 +312,7 @@ class Context:
         if x is None:
             x = torch.empty(n, dtype=torch.float64, device="cuda")
         info = SolveInfo()
-        st = load().chnss_solve(self._h, sys, _ptr(rhs), _ptr(x), ctypes.byref(info))
+        st = load().chnss_solve(self._h, sys, _ptr(rhs, n, "device"), _ptr(x, n, "device"), ctypes.byref(info))
         if check:
             _check(st, self._h)
         return x, info.as_dict(), st
@@ -297,7 +320,7 @@ class Context:
     def step(self, state_in: dict, state_out: dict = None, check: bool = True):
         if state_out is None:
             state_out = self.new_state()
-        a, b = make_state(state_in), make_state(state_out)
+        a, b = self._state(state_in), self._state(state_out)
         infos = (SolveInfo * 6)()
         st = load().chnss_step(self._h, ctypes.byref(a), ctypes.byref(b), infos)
         if check:
@@ -305,7 +328,7 @@ class Context:
         return state_out, {SYSTEM_NAMES[i]: infos[i].as_dict() for i in range(6)}, st
 
     def step_host(self, host_in: dict, host_out: dict, check: bool = True):
-        a, b = make_state(host_in), make_state(host_out)
+        a, b = self._state(host_in, "host"), self._state(host_out, "host")
         infos = (SolveInfo * 6)()
         st = load().chnss_step_host(self._h, ctypes.byref(a), ctypes.byref(b), infos)
         if check:
@@ -327,7 +350,7 @@ class Context:
         """Returns (adj_k, [d/d evap_rate, d/d gamma], infos, status)."""
         if adj_k is None:
             adj_k = self.new_state()
-        a, b, c, d = make_state(state_k), make_state(state_k1), make_state(adj_k1), make_state(adj_k)
+        a, b, c, d = (self._state(x) for x in (state_k, state_k1, adj_k1, adj_k))
         grad = (ctypes.c_double * 2)(0.0, 0.0)
         infos = (SolveInfo * 6)()
         st = load().chnss_adjoint_step(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d),
@@ -339,7 +362,9 @@ class Context:
     def objective(self, phi_p, grad=None):
         """J = int |grad phi_p|^2 and, if grad is a device array, 2 K phi_p."""
         J = ctypes.c_double()
-        _check(load().chnss_objective(self._h, _ptr(phi_p), ctypes.byref(J), _ptr(grad)), self._h)
+        N1 = self.mesh.N1
+        _check(load().chnss_objective(self._h, _ptr(phi_p, N1, "device"), ctypes.byref(J), _ptr(grad, N1, "device")),
+               self._h)
         return J.value
 
     def mass_solve_noalloc(self, rhs, x=None, check: bool = True):
@@ -349,7 +374,8 @@ class Context:
         if x is None:
             x = torch.empty(self.mesh.N1, dtype=torch.float64, device="cuda")
         info = SolveInfo()
-        st = load().chnss_mass_solve_noalloc(self._h, _ptr(rhs), _ptr(x), ctypes.byref(info))
+        N1 = self.mesh.N1
+        st = load().chnss_mass_solve_noalloc(self._h, _ptr(rhs, N1, "device"), _ptr(x, N1, "device"), ctypes.byref(info))
         if check:
             _check(st, self._h)
         return x, info.as_dict(), st
@@ -428,7 +454,7 @@ class Context3:
     def step(self, state_in: dict, state_out: dict = None, check: bool = True):
         if state_out is None:
             state_out = self.new_state()
-        a, b = make_state(state_in), make_state(state_out)
+        a, b = (make_state(x, self.N1, self.N2, 3, "device") for x in (state_in, state_out))
         infos = (SolveInfo * 6)()
         st = load().chnss3_step(self._h, ctypes.byref(a), ctypes.byref(b), infos)
         if check and st != 0:
@@ -450,7 +476,7 @@ def host_operator3(n: int, which: str, params: dict, state: dict = None):
     lib = load()
     op = OPS3.index(which)
     prm = make_params(params)
-    st = make_state(state) if state is not None else None
+    st = make_state(state, (n + 1) ** 3, (2 * n + 1) ** 3, 3, "host") if state is not None else None
     sptr = ctypes.byref(st) if st is not None else None
     nr, nc, nnz = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
     _check(lib.chnss3_host_operator(n, op, ctypes.byref(prm), sptr, ctypes.byref(nr), ctypes.byref(nc),
@@ -478,8 +504,8 @@ def step_batched(ctxs, states_in, states_out=None, max_threads: int = 0, check: 
     if states_out is None:
         states_out = [c.new_state() for c in ctxs]
     hs = (ctypes.c_void_p * n)(*[c._h.value for c in ctxs])
-    a = (State * n)(*[make_state(x) for x in states_in])
-    b = (State * n)(*[make_state(x) for x in states_out])
+    a = (State * n)(*[c._state(x) for c, x in zip(ctxs, states_in)])
+    b = (State * n)(*[c._state(x) for c, x in zip(ctxs, states_out)])
     infos = (SolveInfo * (6 * n))()
     st = load().chnss_step_batched(n, hs, a, b, infos, max_threads)
     if check:

@@ -106,3 +106,31 @@ def test_three_d_argument_errors_need_no_device(lib):
     assert lib.chnss3_sizes(None, None, None) == 1
     assert lib.chnss3_set_step_concurrency(None, 1) == 1
     assert lib.chnss3_ctx_destroy(None) == 0
+
+
+def test_binding_checks_array_sizes_and_placement():
+    """The C ABI takes bare pointers; the binding refuses arrays that are too
+    short or on the wrong side (host vs device) before any call."""
+    import numpy as np
+    import torch
+    from paper_2501_11767_gb300 import inputs
+    N1, N2 = 25, 81
+    host = {"phi": np.zeros((3, N1)), "mu": np.zeros((4, N1)), "Phi_v": np.zeros(N1), "v": np.zeros(2 * N2),
+            "p": np.zeros(N1)}
+    chnss.make_state(host, N1, N2, 2, "host")
+    with pytest.raises(ValueError):
+        chnss.make_state(host, N1, N2, 2, "device")              # numpy is never a device array
+    with pytest.raises(ValueError):
+        chnss.make_state(dict(host, v=np.zeros(2 * N2 - 1)), N1, N2, 2, "host")
+    with pytest.raises(ValueError):
+        chnss.make_state(host, N1, N2, 3, "host")                 # 3D velocity is longer
+    cpu = {k: torch.as_tensor(v) for k, v in host.items()}
+    chnss.make_state(cpu, N1, N2, 2, "host")
+    with pytest.raises(ValueError):
+        chnss.make_state(cpu, N1, N2, 2, "device")                # CPU tensor where a device pointer goes
+    with pytest.raises(ValueError):
+        chnss._ptr(torch.zeros(4, dtype=torch.float32))
+    n = 2
+    st3 = inputs.initial_state_3d(n, seed=0)
+    with pytest.raises(ValueError):
+        chnss.host_operator3(n, "C1", inputs.default_params(), dict(st3, v=st3["v"][:-3].copy()))
