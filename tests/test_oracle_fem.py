@@ -169,6 +169,29 @@ def test_potential_loads_constant_fields():
         assert np.allclose(loads[k], d[k] * m1, rtol=1e-12, atol=1e-15)
 
 
+@pytest.mark.parametrize("model_kind", [0, 1])
+def test_potential_loads_rule_degree_suffices(model_kind):
+    """For linear fields the load integrands are polynomials of degree <= 7
+    (eqn:appPotential; the solvent-air density with its degree-4 Taylor
+    polynomials of x ln x): the degree-7 rule equals a degree-13 one."""
+    from paper_2501_11767_gb300 import inputs
+    mesh = Mesh(4)
+    x, y = mesh.x1[:, 0], mesh.x1[:, 1]
+    phi = np.stack([0.3 + 0.05 * x, 0.25 - 0.04 * y, 0.4 + 0.1 * (x - y)])
+    Phi = 0.2 + 0.3 * y
+    params = inputs.solvent_air_params() if model_kind else None
+    loads = model.potential_loads(mesh, phi, Phi, params)
+    for k in range(5):
+        def integrand(lam, k=k):
+            pp, pn, ps = (fem.p1_field_at(mesh, phi[i], lam) for i in range(3))
+            pa, Ph = 1.0 - pp - pn - ps, fem.p1_field_at(mesh, Phi, lam)
+            if model_kind:
+                return model.fh_partials(ps, pa, Ph, params)[k - 2] if k >= 2 else 0.0 * pp
+            return model.potential_partials(pp, pn, ps, pa, Ph)[k]
+        ref = fem.load_p1(mesh, integrand, 13)
+        assert np.allclose(loads[k], ref, rtol=1e-12, atol=1e-14 * max(np.abs(ref).max(), 1e-300)), k
+
+
 def test_top_load_and_reference_node():
     mesh = Mesh(8, 2.0, 1.0)
     t = fem.top_load_p1(mesh)
