@@ -311,8 +311,8 @@ chnss_status chnss3_host_operator(int n, int which, const chnss_params *params, 
  * (CH for three species with diag(MG(M + tau C), X^-1 M X^-1), AC with MG,
  * the air potential by Jacobi-PCG, Oseen with diag(MG(A), M_p^-1 A_p K_p^-1),
  * FGMRES(restart) with CGS2, geometric multigrid on the nested Kuhn meshes)
- * with no-slip on every face and evaporation through the top face z = 1
- * (reference point (1/2, 1/2, 1)).  Covers model 0, constant or
+ * with no-slip on every face (or the open top of chnss3_ctx_create_ex) and
+ * evaporation through the top face z = 1 (reference point (1/2, 1/2, 1)).  Covers model 0, constant or
  * concentration-dependent mobility (mobility_kind 0 or 1: then the first
  * row's tau K_kappa and the Schur factor X2 = tau K_kappa + a M as in 2D),
  * precision 0, 1 or 2, and one V-cycle per multigrid block or (inner_rtol
@@ -323,7 +323,14 @@ chnss_status chnss3_host_operator(int n, int which, const chnss_params *params, 
  * States: chnss_state with DEVICE arrays of the 3D sizes (chnss3_sizes):
  * phi[3], mu[4], Phi_v, p of N1 = (n+1)^3, v of 3 N2 = 3 (2n+1)^3.
  * info[6] (optional): the six solves as in chnss_step.  chnss3_step
- * synchronises the stream before returning. */
+ * synchronises the stream before returning.  Ownership: the caller owns the
+ * state arrays (in and out must not overlap); the context owns its device
+ * workspace, streams and captured graphs, released by chnss3_ctx_destroy.
+ * Errors: CHNSS_ERR_ARG (bad size or parameters: nothing is allocated; the
+ * text is in chnss_last_error(NULL)), CHNSS_ERR_CUDA / CHNSS_ERR_OOM (the
+ * device failed), and from chnss3_step the first non-OK status of the six
+ * solves (CHNSS_ERR_NOCONV, CHNSS_ERR_BREAKDOWN, CHNSS_ERR_NAN), with the
+ * outputs holding the last iterates and the text in chnss3_last_error. */
 typedef struct chnss3_ctx *chnss3_ctx_t;
 chnss_status chnss3_ctx_create(int n, const chnss_params *params, void *cuda_stream, chnss3_ctx_t *out);
 /* As chnss3_ctx_create with the velocity condition on the top face z = 1:
