@@ -424,3 +424,19 @@ def test_symmetric_gradient_form_on_quadratics():
         r = (K @ np.stack([ux, zero, zero], axis=1).ravel()).reshape(-1, 3)
         assert np.abs(r[inner, 0] + eta * dx * w[inner]).max() < 1e-11 * eta * dx * np.abs(w).max()
         assert np.abs(r[inner, 1:]).max() < 1e-14
+
+
+def test_open_top_with_inner_solves_and_variable_mobility():
+    """The open top, the concentration-dependent mobility and inner solves to
+    1e-4 together (K_p with Dirichlet top rows as an inner solve, X2 per
+    species): the step still reaches the sparse-LU step."""
+    n = 4
+    p = inputs.default_params()
+    p.update(rtol=1e-11, alpha=[1e-2] * 4, top_bc=1, mobility_kind=1, inner_rtol=1e-4, inner_maxit=20)
+    s0 = inputs.initial_state_3d(n, seed=9)
+    s1, info = t3.Oracle3D(n, p).step(s0)
+    x1 = t3.Oracle3D(n, p, exact=True).step(s0)[0]
+    assert all(v["converged"] for v in info.values())
+    for key in ("phi", "mu", "Phi_v", "v", "p"):
+        a, b = np.ravel(s1[key]), np.ravel(x1[key])
+        assert np.linalg.norm(a - b) <= 1e-7 * max(np.linalg.norm(b), 1e-30), key
