@@ -114,7 +114,7 @@ typedef struct {
   double seconds;        /* host wall time of the solve */
 } chnss_solve_info;
 
-/* Mesh hierarchy for n x n squares on [0,lx] x [0,ly]: n even and >= 2,
+/* Mesh hierarchy for n x n squares on [0,lx] x [0,ly]: n even, 2 <= n <= 2048,
  * nx == ny required.  Multigrid levels n, n/2, ... while the size is even and
  * at least 4.  Builds the CSR patterns, the element -> CSR gather maps and
  * the transfer operators (host), and uploads them.  Returns CHNSS_ERR_ARG
@@ -307,7 +307,7 @@ chnss_status chnss3_host_operator(int n, int which, const chnss_params *params, 
                                   int *nrows, int *ncols, long long *nnz, int *rowptr, int *col, double *val);
 
 /* One semi-implicit step on the 3D Kuhn mesh of n^3 cubes of the unit box
- * (n even, 2 <= n <= 96), on the device: the 2D step's systems and solvers
+ * (n even, 2 <= n <= 64), on the device: the 2D step's systems and solvers
  * (CH for three species with diag(MG(M + tau C), X^-1 M X^-1), AC with MG,
  * the air potential by Jacobi-PCG, Oseen with diag(MG(A), M_p^-1 A_p K_p^-1),
  * FGMRES(restart) with CGS2, geometric multigrid on the nested Kuhn meshes)

@@ -1143,7 +1143,9 @@ chnss_status chnss_mesh_create_ex(int nx, int ny, double lx, double ly, int top_
   if (top_bc != 0 && top_bc != 1) throw Error{CHNSS_ERR_ARG, "top_bc must be 0 or 1"};
   *out = nullptr;
   if (nx != ny) throw Error{CHNSS_ERR_ARG, "nx must equal ny"};
-  if (nx < 2 || nx % 2 != 0 || nx > 8192) throw Error{CHNSS_ERR_ARG, "n must be even and in [2, 8192]"};
+  // element-buffer offsets and gather counts are int: 144 E = 288 n^2 stays
+  // below 2^31 up to n = 2730
+  if (nx < 2 || nx % 2 != 0 || nx > 2048) throw Error{CHNSS_ERR_ARG, "n must be even and in [2, 2048]"};
   if (!(lx > 0) || !(ly > 0)) throw Error{CHNSS_ERR_ARG, "domain lengths must be > 0"};
   std::unique_ptr<chnss_mesh> m(new chnss_mesh());
   build_mesh(m->m, nx, lx, ly, top_bc);

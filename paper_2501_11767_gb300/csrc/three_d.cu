@@ -1458,7 +1458,9 @@ extern "C" chnss_status chnss3_ctx_create_ex(int n, int top_bc, const chnss_para
   try {
     if (!params || !out) throw Error{CHNSS_ERR_ARG, "null argument"};
     if (top_bc != 0 && top_bc != 1) throw Error{CHNSS_ERR_ARG, "top_bc must be 0 (no-slip) or 1 (open top)"};
-    if (n < 2 || n % 2 || n > 96) throw Error{CHNSS_ERR_ARG, "3D meshes: n even, 2 <= n <= 96"};
+    // the host setup counts element contributions in int: 6 n^3 x 900 for the
+    // velocity pattern stays below 2^31 up to n = 72
+    if (n < 2 || n % 2 || n > 64) throw Error{CHNSS_ERR_ARG, "3D meshes: n even, 2 <= n <= 64"};
     const chnss_params &p = *params;
     if (p.model != 0 || p.precision < 0 || p.precision > 2)
       throw Error{CHNSS_ERR_ARG, "the 3D step covers model 0, precision 0-2"};

@@ -44,6 +44,7 @@ def test_library_is_built_for_sm_103a():
 def test_argument_errors_need_no_device(lib):
     h = ctypes.c_void_p()
     assert lib.chnss_mesh_create(7, 7, 1.0, 1.0, ctypes.byref(h)) == 1      # odd n
+    assert lib.chnss_mesh_create(2050, 2050, 1.0, 1.0, ctypes.byref(h)) == 1  # int32 element offsets
     assert b"even" in lib.chnss_last_error(None)
     assert lib.chnss_mesh_create(8, 16, 1.0, 1.0, ctypes.byref(h)) == 1     # nx != ny
     assert lib.chnss_mesh_create(8, 8, -1.0, 1.0, ctypes.byref(h)) == 1     # bad length
@@ -92,7 +93,7 @@ def test_three_d_argument_errors_need_no_device(lib):
         return lib.chnss3_ctx_create_ex(n, top_bc, ctypes.byref(p), None, ctypes.byref(h))
 
     assert create(3) == 1                                    # odd n
-    assert create(98) == 1                                   # above the 3D size limit
+    assert create(66) == 1                                   # above the 3D size limit (int32 host counts)
     assert create(4, top_bc=2) == 1                          # unknown top condition
     assert b"top_bc" in lib.chnss_last_error(None)
     assert create(4, mobility_kind=2) == 1
