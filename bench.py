@@ -483,6 +483,10 @@ def run_three_d(args):
     p.update(tau=1e-4)                 # the 3D figures' time step (Sec. 5)
     if args.three_d_mobility:          # gamma_i (phi_i (1 - phi_i) + m0), lagged
         p.update(mobility_kind=1)
+    if args.three_d_open:              # do-nothing top face
+        p.update(top_bc=1)
+    if args.three_d_inner > 0:         # multigrid blocks iterated to a tolerance (Sec. 5: 1e-4)
+        p.update(inner_rtol=args.three_d_inner, inner_maxit=20)
     stream = torch.cuda.current_stream()
 
     def timed(prm):
@@ -517,8 +521,11 @@ def run_three_d(args):
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 outer / f32 preconditioner",
         "data": "synthetic (seeded SplitMix64 noise on phi_p, phi_NFA)",
-        "config": {"workload": f"film3d{n}{'_mobility' if args.three_d_mobility else ''}_mixed", "n": n,
-                   "mobility": "phi (1 - phi) + m0" if args.three_d_mobility else "constant", "p1_nodes": ctx.N1, "p2_nodes": ctx.N2,
+        "config": {"workload": f"film3d{n}{'_mobility' if args.three_d_mobility else ''}"
+                               f"{'_open' if args.three_d_open else ''}{'_inner' if args.three_d_inner > 0 else ''}_mixed",
+                   "n": n, "mobility": "phi (1 - phi) + m0" if args.three_d_mobility else "constant",
+                   "top": "open (do-nothing)" if args.three_d_open else "no-slip",
+                   "inner_rtol": args.three_d_inner, "p1_nodes": ctx.N1, "p2_nodes": ctx.N2,
                    "velocity_dofs": 3 * ctx.N2, "tau": p["tau"], "rtol": p["rtol"], "parallelism": "single GPU",
                    "l2": "inputs larger than L2" if 3 * ctx.N2 * 8 * 100 > 129e6 else "working set near L2"},
         "iters_mean": iters(infos),
@@ -685,6 +692,9 @@ def main():
     ap.add_argument("--three-d-n", type=int, default=32)
     ap.add_argument("--three-d-mobility", type=int, default=0, choices=[0, 1],
                     help="3D workload with the concentration-dependent mobility")
+    ap.add_argument("--three-d-open", type=int, default=0, choices=[0, 1], help="3D workload with an open top")
+    ap.add_argument("--three-d-inner", type=float, default=0.0,
+                    help="3D workload with multigrid blocks iterated to this tolerance")
     ap.add_argument("--sweep-count", type=int, default=64)
     ap.add_argument("--sweep-threads", type=int, default=0)
     ap.add_argument("--sweep-concurrent-steps", action="store_true")
