@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <climits>
 #include <vector>
 
 #include "internal.h"
@@ -11,6 +12,8 @@ namespace chnss {
 
 template <class PairFn>
 inline void pattern_from_elements(int nrows, int ncols, int E, int nr, int nc, PairFn nodes, Pattern &P) {
+  // the candidate counts below are int: refuse sizes whose total would overflow
+  if ((long long)E * nr * nc > INT_MAX) throw Error{CHNSS_ERR_ARG, "mesh too large for int32 pattern counts"};
   std::vector<int> cnt(nrows + 1, 0);
   std::vector<int> rn(nr), cn(nc);
   for (int e = 0; e < E; ++e) {
@@ -51,6 +54,7 @@ inline int find_col(const Pattern &P, int row, int col) {
 template <class PairFn, class OffFn, class KeepFn>
 inline void gather_from_elements(const Pattern &P, int E, int nr, int nc, PairFn nodes, OffFn off, KeepFn keep,
                           Gather &G, std::vector<int> &hptr, std::vector<int> &hidx) {
+  if ((long long)E * nr * nc > INT_MAX) throw Error{CHNSS_ERR_ARG, "mesh too large for int32 gather lists"};
   hptr.assign(P.nnz + 1, 0);
   std::vector<int> rn(nr), cn(nc);
   for (int e = 0; e < E; ++e) {
