@@ -381,3 +381,43 @@ def test_p1_operators_are_seven_point_stencils(n):
         k, j = i % nx, i // nx
         if 0 < k < n and 0 < j < n:
             assert len(cols) == 7, i
+
+
+def test_mms_cahn_hilliard_and_allen_cahn_systems():
+    """The linear systems of one step (eqn:CH_linear, the AC system of Sec. 4)
+    against their PDEs with manufactured data, no flow: CH
+    (phi - phi_k) / tau = gamma lap mu, mu = -beta lap phi + f, with
+    phi = cos(pi x) cos(pi y) and f = cos(2 pi x) / 2 (Neumann data zero, so
+    phi_k follows by differentiation); AC (Phi - Phi_k) / tau = delta lap Phi
+    - gamma_v f_v with Phi = cos(pi x) cos(2 pi y).  The P1 solutions converge
+    at O(h^2) in L2: a wrong sign, a misplaced tau, gamma or beta, or a
+    transposed block breaks the rate."""
+    pi = math.pi
+    tau, g, beta, delta, gv = 0.01, 1.3, 0.05, 0.7, 0.9
+    phi = lambda x, y: np.cos(pi * x) * np.cos(pi * y)                                   # noqa: E731
+    fch = lambda x, y: 0.5 * np.cos(2 * pi * x)                                          # noqa: E731
+    mu = lambda x, y: 2 * pi * pi * beta * phi(x, y) + fch(x, y)                         # noqa: E731
+    lap_mu = lambda x, y: -4 * pi ** 4 * beta * phi(x, y) - 2 * pi * pi * np.cos(2 * pi * x)  # noqa: E731
+    phik = lambda x, y: phi(x, y) - tau * g * lap_mu(x, y)                               # noqa: E731
+    Phi = lambda x, y: np.cos(pi * x) * np.cos(2 * pi * y)                               # noqa: E731
+    fv = lambda x, y: np.cos(pi * y) ** 2                                                # noqa: E731
+    Phik = lambda x, y: Phi(x, y) + tau * delta * 5 * pi * pi * Phi(x, y) + tau * gv * fv(x, y)  # noqa: E731
+    params = dict(tau=tau, gamma=[g] * 3, beta=[beta] * 4, mobility_kind=0, delta_v=delta, gamma_v=gv,
+                  ac_top_flux=0)
+    e_phi, e_mu, e_Phi = [], [], []
+    for n in (8, 16, 32):
+        mesh = Mesh(n)
+        forms = model.Forms(mesh, params)
+        x, y = mesh.x1[:, 0], mesh.x1[:, 1]
+        X = lambda lam: fem.quad_points(mesh, lam)                                       # noqa: E731
+        load = lambda fn: fem.load_p1(mesh, lambda lam: fn(X(lam)[..., 0], X(lam)[..., 1]), 8)  # noqa: E731
+        st = {"phi": np.stack([phik(x, y)] * 3), "Phi_v": Phik(x, y)}
+        C = sp.csr_matrix((mesh.N1, mesh.N1))
+        A, rhs, _, _ = model.ch_system(forms, st, params, 0, load(fch), C)
+        sol = spla.spsolve(A.tocsc(), rhs)
+        e_phi.append(fem.l2_error_p1(mesh, sol[:mesh.N1], phi))
+        e_mu.append(fem.l2_error_p1(mesh, sol[mesh.N1:], mu))
+        Aac, rac = model.ac_system(forms, st, params, load(fv), C, 0.0)
+        e_Phi.append(fem.l2_error_p1(mesh, spla.spsolve(Aac.tocsc(), rac), Phi))
+    for errs in (e_phi, e_mu, e_Phi):
+        assert min(_rate(errs)) > 1.8, (errs, _rate(errs))
