@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -33,8 +34,23 @@ WORKLOAD = "film1024_mixed"
 CPU_SAMPLE_N = 256          # cpu_baseline: one oracle step on 256 x 256 (~10-30 s)
 REF_SAMPLE_N = 128          # --impl reference: one oracle step on 128 x 128 per timed step
 METRIC = "time steps/s at 1M nodes (1024x1024 P1 mesh, FGMRES to 1e-8 relative residual)"
-# FP64 pipe of this GB300: 152 SMs x 2 FP64 FMA per clock x 2 FLOP x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_FMA_PER_SM_CLK = 2     # FP64 FMA issue rate per multiprocessor per clock on this part
+
+
+def fp64_peak_tflops(sm_max_mhz=None):
+    """ALU roof of FP64 work: multiprocessors of the current device x FP64
+    FMAs per clock x 2 FLOP x the maximum SM clock (sampled by nvidia-smi
+    during the run, else the measured one, else 2070 MHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = sm_max_mhz
+    if not mhz:
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                mhz = float(json.load(f)["sm_max_mhz"])
+        except Exception:
+            mhz = 2070.0
+    return sms * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12, sms, mhz
 
 
 def peaks():
@@ -99,12 +115,11 @@ class ClockSampler:
 
     def __init__(self, device_id=None):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"chnss_clocks_{os.getpid()}_{id(self)}.csv")
         self.device_id = device_id
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
             if self.device_id:
                 cmd[1:1] = ["-i", self.device_id]
@@ -136,6 +151,10 @@ class ClockSampler:
             for nm, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
@@ -288,6 +307,7 @@ def run_gpu(args):
     # FP64 families that need more than one FMA per 11 bytes are bound by the
     # FP64 pipe of this part, not by HBM
     peak, peak_kind = peaks()
+    fp64_peak, n_sms, peak_mhz = fp64_peak_tflops(clocks["sm_max_mhz"] if clocks else None)
     kinds = {k: v for k, v in prof["kinds"].items() if v["launches"] > 0 and v["bytes"] > 0}
 
     def family_roofline(name):
@@ -295,11 +315,12 @@ def run_gpu(args):
         ms_l = d["ms"] / d["launches"]
         gbps = d["bytes"] / (d["ms"] * 1e-3) / 1e9
         # FP64 balance point, FLOP per byte of the measured HBM bandwidth (~0.19)
-        if d.get("flops", 0.0) > 0 and d["flops"] / d["bytes"] > FP64_PEAK_TFLOPS * 1e12 / (peak * 1e9):
+        if d.get("flops", 0.0) > 0 and d["flops"] / d["bytes"] > fp64_peak * 1e12 / (peak * 1e9):
             tf = d["flops"] / (d["ms"] * 1e-3) / 1e12
-            return {"kernel": name, "bound": "alu", "achieved": round(tf, 4), "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": round(tf / FP64_PEAK_TFLOPS, 4),
-                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz (FMA probe measured 1.20)",
+            return {"kernel": name, "bound": "alu", "achieved": round(tf, 4), "peak": round(fp64_peak, 4),
+                    "unit": "TFLOP/s", "frac": round(tf / fp64_peak, 4),
+                    "peak_source": f"derived: {n_sms} SMs x {FP64_FMA_PER_SM_CLK} FP64 FMA/clk x 2 FLOP x "
+                                   f"{peak_mhz:.0f} MHz",
                     "flops_per_launch": d["flops"] / d["launches"], "bytes_per_launch": d["bytes"] / d["launches"],
                     "ms_per_launch": ms_l, "launches": d["launches"], "hbm_GBps": round(gbps, 1),
                     "hbm_frac": round(gbps / peak, 4), "traffic": _traffic(name, d["bytes"] / d["launches"])}

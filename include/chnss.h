@@ -156,6 +156,10 @@ int chnss_system_size(chnss_ctx_t ctx, chnss_system sys);
  * system.  rhs_or_null: device right-hand side of chnss_system_size doubles,
  * or NULL for the assembled one (for MU_A: built from the last three CH
  * solutions).  x_out: device array of the same size, overwritten (x0 = 0).
+ * FGMRES reads the right-hand side again at every restart, so for CH, AC and
+ * NS rhs and x_out must not overlap; MU_A may solve in place (rhs == x_out)
+ * but not on partly overlapping arrays.  Overlap is refused with
+ * CHNSS_ERR_ARG before any work.
  * Preconditioners (Sec. 4): CH diag(MG(M + tau C), X2^-1 M X1^-1) with the
  * matching factor X = tau gamma K + sqrt(tau gamma / beta) M (eqn::schurCH);
  * AC MG(M + tau delta_v K + tau C); NS diag(MG(A), M_p^-1 A_p K_p^-1)
@@ -362,9 +366,11 @@ const char *chnss3_last_error(chnss3_ctx_t ctx);
  * reserved up front by their own pool (an allocation would fail or break
  * their accounting) and latency-critical loops that may not pay the implicit
  * synchronisation of cudaMalloc / cudaFree.
- * rhs, x_out: device arrays of N1 doubles, caller-owned.
+ * rhs, x_out: device arrays of N1 doubles, caller-owned.  rhs is read once,
+ * before x_out is written, so an in-place solve (rhs == x_out) is allowed;
+ * partly overlapping arrays return CHNSS_ERR_ARG.
  * Limit: N1 <= 66049 (meshes up to 256 x 256); larger meshes return
- * CHNSS_ERR_ARG with a message.  The array (about 2.1 MB) stays resident on
+ * CHNSS_ERR_ARG with a message.  The array (about 2.13 MB) stays resident on
  * every GPU that loads the library until the process exits.  The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.

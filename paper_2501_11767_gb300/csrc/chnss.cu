@@ -599,8 +599,8 @@ void create_context(chnss_ctx *c) {
   upload_reference_tensors(s);
   c->ebuf = ar.alloc<double>(144L * c->E);
   c->lbuf = ar.alloc<double>(15L * c->E);
-  c->partial = ar.alloc<double>(64L * 1216);
-  c->partial_ch = ar.alloc<double>(64L * 1216);
+  c->partial = ar.alloc<double>(64L * kReduceMaxBlocks);
+  c->partial_ch = ar.alloc<double>(64L * kReduceMaxBlocks);
   c->sum = ar.alloc<double>(4);
   const int nl = c->nlev;
   c->M1.resize(nl); c->K1.resize(nl); c->ACb.resize(nl); c->M2v.resize(nl); c->Aconst.resize(nl);
@@ -919,6 +919,13 @@ int system_size(chnss_ctx *c, int sys) {
 }
 
 // One system on stream s with Krylov work kw and an N1 scratch vector tmp.
+// [a, a + n) and [b, b + n) share at least one element
+bool ranges_overlap(const double *a, const double *b, long n) {
+  const auto x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  const uintptr_t len = (uintptr_t)n * sizeof(double);
+  return x < y + len && y < x + len;
+}
+
 chnss_status solve_on(chnss_ctx *c, int sys, const double *rhs_or_null, double *x, chnss_solve_info *info,
                       cudaStream_t s, KrylovWork &kwk, double *tmp) {
   if (!c->assembled) throw Error{CHNSS_ERR_STATE, "chnss_solve before chnss_assemble"};
@@ -1213,8 +1220,13 @@ chnss_status chnss_solve(chnss_ctx_t ctx, chnss_system sys, const double *rhs_or
                          chnss_solve_info *info) {
   if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
   ABI_TRY
-  if (system_size(ctx, sys) < 0) throw Error{CHNSS_ERR_ARG, "unknown system"};
+  const int nsys = system_size(ctx, sys);
+  if (nsys < 0) throw Error{CHNSS_ERR_ARG, "unknown system"};
   if (!x_out) throw Error{CHNSS_ERR_ARG, "null x_out"};
+  // FGMRES reads b again at every restart; PCG reads it once, before x is
+  // written, so only the mass solve may run in place
+  if (rhs_or_null && ranges_overlap(rhs_or_null, x_out, nsys) && !(sys == CHNSS_SYS_MU_A && rhs_or_null == x_out))
+    throw Error{CHNSS_ERR_ARG, "rhs and x_out overlap (only CHNSS_SYS_MU_A may solve in place, with rhs == x_out)"};
   const chnss_status st = solve(ctx, sys, rhs_or_null, x_out, info);
   if (st != CHNSS_OK) ctx->err = "solve did not converge cleanly (status " + std::to_string(st) + ")";
   return st;
@@ -1404,7 +1416,7 @@ const char *chnss_last_error(chnss_ctx_t ctx) { return ctx ? ctx->err.c_str() : 
 namespace {
 
 constexpr int kNoAllocMaxN1 = 257 * 257;             // P1 nodes of a 256 x 256 mesh
-constexpr long kNoAllocPartials = 1216;              // reduction blocks (reduce_blocks cap)
+constexpr long kNoAllocPartials = kReduceMaxBlocks;  // reduction blocks (reduce_blocks cap)
 constexpr long kNoAllocScalars = 16;
 constexpr long kNoAllocDoubles = 4L * kNoAllocMaxN1 + kNoAllocPartials + kNoAllocScalars;
 constexpr int kNoAllocMaxDevices = 64;
@@ -1429,68 +1441,21 @@ double *noalloc_scratch_address() {
   return g_noalloc_addr[dev];
 }
 
-// Jacobi PCG on M x = b with all work storage in the scratch array (same
-// kernels and stopping rule as the MU_A solve: rtol 1e-12, x0 = 0).
+// Jacobi PCG on M x = b (the MU_A solve's pcg(): rtol 1e-12, x0 = 0) with a
+// work view whose vectors, scalars and partials all point into the scratch
+// array, and the context's own pinned host slot for the scalar reads.
 chnss_status mass_solve_noalloc(chnss_ctx *c, const double *b, double *x, chnss_solve_info *info) {
-  const auto t0 = std::chrono::steady_clock::now();
   const Pattern &P = c->lv(0).p1;
   const long n = P.nrows;
-  cudaStream_t s = c->s;
   double *base = noalloc_scratch_address();
-  double *r = base, *z = base + n, *p = base + 2 * n, *q = base + 3 * n;
-  double *partial = base + 4L * kNoAllocMaxN1;
-  double *sc = partial + kNoAllocPartials;   // [0] bb [1] rz [2] rz_new [3] pq [4] alpha [5] rr
-  double *host = c->pinned + 12;             // pinned host slot owned by the context
-  auto read = [&](const double *d) {
-    CHNSS_CK(cudaMemcpyAsync(host, d, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CHNSS_CK(cudaStreamSynchronize(s));
-    return *host;
-  };
-  const double rtol = 1e-12;
-  const int maxit = 1000;
-  vec_fill(n, 0.0, x, s);
-  vec_copy(n, b, r, s);
-  dot<double>(n, b, b, sc, partial, s);
-  const double bnorm = std::sqrt(read(sc));
-  const double target = rtol * bnorm;
-  double rn = bnorm;
-  int it = 0;
-  bool converged = false;
-  chnss_status st = CHNSS_OK;
-  if (!std::isfinite(bnorm)) {
-    st = CHNSS_ERR_NAN;
-  } else if (bnorm <= target) {
-    converged = true;
-  } else {
-    vec_mul(n, c->dinvM, r, z, s);
-    vec_copy(n, z, p, s);
-    dot<double>(n, r, z, sc + 1, partial, s);
-    double *rz = sc + 1, *rzn = sc + 2;
-    SpmvArgs none;
-    while (it < maxit) {
-      spmv_csr<double>(P, c->M1[0], 1, p, q, SPMV_PLAIN, none, s);
-      dot<double>(n, p, q, sc + 3, partial, s);
-      pcg_alpha(rz, sc + 3, sc + 4, s);
-      pcg_update_xr(n, sc + 4, p, q, x, r, s);
-      ++it;
-      dot<double>(n, r, r, sc + 5, partial, s);
-      rn = std::sqrt(read(sc + 5));
-      if (!std::isfinite(rn)) { st = CHNSS_ERR_NAN; break; }
-      if (rn <= target) { converged = true; break; }
-      vec_mul(n, c->dinvM, r, z, s);
-      dot<double>(n, r, z, rzn, partial, s);
-      pcg_update_p(n, rzn, rz, z, p, s);
-      std::swap(rz, rzn);
-    }
-    if (!converged && st == CHNSS_OK) st = CHNSS_ERR_NOCONV;
-  }
-  if (info) {
-    info->iters = it;
-    info->converged = converged ? 1 : 0;
-    info->rel_residual = bnorm > 0 ? rn / bnorm : 0.0;
-    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  }
-  return st;
+  KrylovWork view;                       // no storage of its own
+  view.nmax = n;
+  view.w = base;                         // r
+  view.V = base + n;                     // z, p, q
+  view.partial = base + 4L * kNoAllocMaxN1;
+  view.sc = view.partial + kNoAllocPartials;
+  view.hstat = c->pinned + 12;
+  return pcg(P, c->M1[0], c->dinvM, b, x, 1e-12, 1000, view, info, c->s);
 }
 
 }  // namespace
@@ -1500,6 +1465,8 @@ extern "C" chnss_status chnss_mass_solve_noalloc(chnss_ctx_t ctx, const double *
   if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
   ABI_TRY
   if (!rhs || !x_out) throw Error{CHNSS_ERR_ARG, "null rhs or x_out"};
+  if (rhs != x_out && ranges_overlap(rhs, x_out, ctx->N1))
+    throw Error{CHNSS_ERR_ARG, "rhs and x_out overlap without being the same array"};
   if (ctx->N1 > kNoAllocMaxN1)
     throw Error{CHNSS_ERR_ARG, "chnss_mass_solve_noalloc supports at most " + std::to_string(kNoAllocMaxN1) +
                                    " P1 nodes (a 256 x 256 mesh); this mesh has " + std::to_string(ctx->N1)};

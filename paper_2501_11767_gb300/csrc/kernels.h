@@ -150,9 +150,14 @@ void vec_scale_by_inv(long n, const double *src, const double *hn, double *dst, 
 template <typename T>
 void vec_sub_mean(int n, T *x, const double *sum, cudaStream_t s);   // x -= sum / n
 
-// deterministic FP64 reductions: fixed grid of reduce_blocks(n) blocks,
-// partial sums in fixed order, then one block sums the partials.
+// deterministic FP64 reductions: fixed grid of reduce_blocks(n) blocks
+// (at most 8 per multiprocessor of the current device and never more than
+// kReduceMaxBlocks), partial sums in fixed order, then one block sums the
+// partials.  Partial buffers hold kReduceMaxBlocks doubles per reduced value.
+constexpr int kReduceMaxBlocks = 2048;
 int reduce_blocks(long n);
+// multiprocessors of the current device (queried once per device)
+int device_sm_count();
 template <typename T>
 void dot(long n, const T *x, const T *y, double *out, double *partial, cudaStream_t s);
 template <typename T>

@@ -409,7 +409,7 @@ void MGHier<T>::enable_inner(Arena &ar, double rtol, int maxit, cudaStream_t bod
   }
   ictl = ar.alloc<double>(8);
   iit = ar.alloc<int>(1);
-  ipartial = ar.alloc<double>(64L * 1216);
+  ipartial = ar.alloc<double>(64L * kReduceMaxBlocks);
   CHNSS_CK(cudaMemset(ictl, 0, 8 * sizeof(double)));
   CHNSS_CK(cudaMemset(iit, 0, sizeof(int)));
 }
@@ -647,7 +647,7 @@ void KrylovWork::init(Arena &ar, int m_, long nmax_, double *pinned) {
   h1 = ar.alloc<double>(m + 1);
   h2 = ar.alloc<double>(m + 1);
   sc = ar.alloc<double>(8);
-  partial = ar.alloc<double>(64L * 1216);
+  partial = ar.alloc<double>(64L * kReduceMaxBlocks);
   hstat = pinned;
 }
 
@@ -925,9 +925,10 @@ chnss_status pcg(const Pattern &P, const double *val, const double *dinv, const 
   const long n = P.nrows;
   double *r = ws.w, *z = ws.V, *p = ws.V + n, *q = ws.V + 2 * n;
   double *sc = ws.sc;   // [0] bb [1] rz [2] rz_new [3] pq [4] alpha [5] rr
-  vec_fill(n, 0.0, x, s);
+  // b is read only here, into r, before x is cleared: x may alias b
   vec_copy(n, b, r, s);
-  dot<double>(n, b, b, sc, ws.partial, s);
+  dot<double>(n, r, r, sc, ws.partial, s);
+  vec_fill(n, 0.0, x, s);
   const double bnorm = std::sqrt(read_scalar(sc, ws.hstat, s));
   const double target = rtol * bnorm;
   double rn = bnorm;

@@ -199,6 +199,9 @@ chnss_status fgmres_batch(int K, LinearOperator *const *A, const double *const *
                           cudaStream_t s, Profiler *prof = nullptr);
 
 // Jacobi PCG for an SPD CSR matrix (FP64), x0 = 0, recursive residual test.
+// Work storage: r = ws.w, z / p / q = ws.V + {0, 1, 2} n, scalars ws.sc[0..6),
+// reduction partials ws.partial, one pinned host double ws.hstat.  b is
+// read once, before x is written, so x may alias b.
 chnss_status pcg(const Pattern &P, const double *val, const double *dinv, const double *b, double *x, double rtol,
                  int maxit, KrylovWork &ws, chnss_solve_info *info, cudaStream_t s);
 

@@ -3,7 +3,9 @@
 // lanes of a group read consecutive entries of the row, so the value and
 // column streams are read coalesced; partial sums are combined with warp
 // shuffles.  Every reduction uses a grid size that depends only on the
-// vector length and sums in a fixed order, so results are bit-reproducible.
+// vector length and the device's multiprocessor count and sums in a fixed
+// order, so results are bit-reproducible on a given device.
+#include <atomic>
 #include <cmath>
 
 #include "kernels.h"
@@ -1091,7 +1093,7 @@ __global__ void k_copy_m(long n, int nr, MultiPtr<T> in, MultiPtr<T> out) {
 // the remaining steps fold the duplicate lanes; the warps' results are then
 // summed in fixed order through shared memory.  Bit-reproducible.
 constexpr int kCgsBlock = 256;
-constexpr int kCgsMaxBlocks = 304;   // 2 per SM
+constexpr int kCgsBlocksPerSm = 2;   // grid cap of the update passes
 constexpr int kCgsMaxK = 31;
 
 constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 * pow2_at_least((x + 1) / 2); }
@@ -1356,10 +1358,26 @@ void spmv_bt_add(const Pattern &P, const double *val, const double *p, double *y
   CHNSS_LAUNCH_CK();
 }
 
+int device_sm_count() {
+  constexpr int kDevs = 64;
+  static std::atomic<int> cache[kDevs];
+  int dev = 0;
+  CHNSS_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kDevs) throw Error{CHNSS_ERR_ARG, "device index out of range"};
+  int sms = cache[dev].load(std::memory_order_relaxed);
+  if (sms == 0) {
+    CHNSS_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (sms < 1) sms = 1;
+    cache[dev].store(sms, std::memory_order_relaxed);
+  }
+  return sms;
+}
+
 int reduce_blocks(long n) {
   long b = (n + 4L * TPB - 1) / (4L * TPB);
+  const long cap = std::min(8L * device_sm_count(), (long)kReduceMaxBlocks);   // 8 resident per SM
   if (b < 1) b = 1;
-  if (b > 1216) b = 1216;   // 8 per SM on 152 SMs
+  if (b > cap) b = cap;
   return (int)b;
 }
 
@@ -1559,20 +1577,21 @@ bool cgs2_fast(int k) { return k >= 1 && k <= kCgsMaxK; }
 namespace {
 int cgs_blocks(long n) {
   long b = (n + kCgsBlock - 1) / kCgsBlock;
-  return (int)std::max(1L, std::min(b, (long)kCgsMaxBlocks));
+  const long cap = std::min((long)kCgsBlocksPerSm * device_sm_count(), (long)kReduceMaxBlocks);
+  return (int)std::max(1L, std::min(b, cap));
 }
 // pass 1 reads KC + 1 streams per element with little FP64 work per load, so
 // it needs every resident block the registers allow (latency-bound at 2 per SM)
 template <int KC>
 int cgs_dots_blocks(long n) {
-  static const int cap = [] {
-    int dev = 0, sms = 0, occ = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgs_dots<KC>, kCgsBlock, 0);
+  static const int occ = [] {
+    int o = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cgs_dots<KC>, kCgsBlock, 0);
     cudaGetLastError();
-    return std::max(kCgsMaxBlocks, std::min(sms * occ, 1216));
+    return o;
   }();
+  const int sms = device_sm_count();
+  const int cap = std::max(kCgsBlocksPerSm * sms, std::min(sms * occ, std::min(8 * sms, kReduceMaxBlocks)));
   const long b = (n + kCgsBlock - 1) / kCgsBlock;
   return (int)std::max(1L, std::min(b, (long)cap));
 }

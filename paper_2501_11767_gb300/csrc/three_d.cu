@@ -1051,7 +1051,7 @@ void create3(chnss3_ctx *c, int n) {
   for (cudaEvent_t &e : c->ev_done) CHNSS_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   c->mt0 = ar.alloc<double>(N1);
   c->phia = ar.alloc<double>(N1);
-  c->partial = ar.alloc<double>(64L * 1216);
+  c->partial = ar.alloc<double>(64L * kReduceMaxBlocks);
   c->sum = ar.alloc<double>(4);
   CHNSS_CK(cudaHostAlloc(&c->pinned, 32 * sizeof(double), cudaHostAllocDefault));
   c->kw.init(ar, p.restart, nv + N1, c->pinned);

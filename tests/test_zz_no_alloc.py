@@ -27,8 +27,8 @@ def _rhs(torch, n1, seed):
     return torch.as_tensor(g.standard_normal(n1), dtype=torch.float64, device="cuda")
 
 
-def test_noalloc_mass_solve_matches_allocating_solve(torch):
-    n = 32
+@pytest.mark.parametrize("n", [32, 256])          # 256: N1 = 66049, the array's exact fit
+def test_noalloc_mass_solve_matches_allocating_solve(torch, n):
     ctx = chnss.Context(chnss.Mesh(n), inputs.default_params())
     ctx.assemble(chnss.state_to_device(inputs.initial_state(n)))
     for call, seed in enumerate((11, 12)):          # two calls in a row share the scratch array
@@ -43,8 +43,28 @@ def test_noalloc_mass_solve_matches_allocating_solve(torch):
         assert np.linalg.norm(g - r) <= 1e-12 * np.linalg.norm(r), call
 
 
-def test_noalloc_mass_solve_rejects_large_meshes(torch):
-    n = 512                                          # 263169 P1 nodes > 66049
+def test_noalloc_mass_solve_in_place(torch):
+    """rhs == x_out: the right-hand side is read before the iterate is
+    cleared, so an in-place solve gives the out-of-place result."""
+    n = 32
+    ctx = chnss.Context(chnss.Mesh(n), inputs.default_params())
+    ctx.assemble(chnss.state_to_device(inputs.initial_state(n)))
+    b = _rhs(torch, ctx.mesh.N1, 13)
+    ref, rinfo, _ = ctx.mass_solve_noalloc(b, torch.empty_like(b))
+    inplace = b.clone()
+    got, info, st = ctx.mass_solve_noalloc(inplace, inplace)
+    torch.cuda.synchronize()
+    assert st == 0 and info["converged"] and info["iters"] == rinfo["iters"]
+    assert torch.equal(got, ref)
+    # partly overlapping arrays are refused before any work
+    buf = torch.zeros(ctx.mesh.N1 + 8, dtype=torch.float64, device="cuda")
+    with pytest.raises(chnss.ChnssError) as e:
+        ctx.mass_solve_noalloc(buf[:ctx.mesh.N1], buf[8:])
+    assert e.value.status == 1 and "overlap" in str(e.value)
+
+
+@pytest.mark.parametrize("n", [258, 512])          # first even mesh past the limit, and a large one
+def test_noalloc_mass_solve_rejects_large_meshes(torch, n):
     ctx = chnss.Context(chnss.Mesh(n), inputs.default_params())
     b = torch.ones(ctx.mesh.N1, dtype=torch.float64, device="cuda")
     x = torch.zeros_like(b)
