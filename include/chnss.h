@@ -224,6 +224,36 @@ chnss_status chnss_adjoint_step(chnss_ctx_t ctx, const chnss_state *state_k, con
  * device polymer field; *J on the host; grad_phi_p (device, optional) = 2 K phi_p. */
 chnss_status chnss_objective(chnss_ctx_t ctx, const double *phi_p, double *J, double *grad_phi_p);
 
+/* Conservation and energy diagnostics of a device state, in FP64 with
+ * deterministic reductions (fixed grid and summation order: bit-reproducible
+ * on a given device).  The scheme conserves int phi_i exactly for enclosed
+ * flow (Sec. 3: the Cahn-Hilliard equations in divergence form with
+ * homogeneous fluxes, the discrete velocity divergence-free against the P1
+ * pressure space), keeps the pressure in L^2_0 (Sec. 3) and is driven by the
+ * free energy of Sec. 2.2.  Fields of the result:
+ *   mass[4]          int phi_i dx = 1^T M phi_i for i = p, NFA, s and the air
+ *                    fraction phi_a = 1 - sum phi_i (exact for P1 fields);
+ *   div_norm         ||B v||_2, the discrete divergence of the velocity;
+ *   p_mean           int p dx = 1^T M p;
+ *   energy_local     int f(phi, Phi_v) dx, f of eqn:appPotential (model 0) or
+ *                    the solvent-air density (model 1), a rule exact to degree 7;
+ *   energy_gradient  sum_i beta_i/2 int |grad phi_i|^2 + beta_v/2 int |grad Phi_v|^2
+ *                    (i over the four species, phi_a = 1 - sum phi_i);
+ *   energy_kinetic   1/2 int |v|^2 dx (rho = 1), the P2 mass form;
+ *   energy           the sum of the three parts.
+ * state: device arrays of ctx's mesh (chnss_state layout; mu is not read).
+ * Runs on ctx's stream and synchronises it once; needs no assembly.  Uses
+ * the context's scratch, so do not call it while a step of ctx is in flight
+ * on another thread.  Errors: CHNSS_ERR_ARG for null arguments. */
+typedef struct {
+  double mass[4];
+  double div_norm;
+  double p_mean;
+  double energy;
+  double energy_local, energy_gradient, energy_kinetic;
+} chnss_diag;
+chnss_status chnss_diagnostics(chnss_ctx_t ctx, const chnss_state *state, chnss_diag *out);
+
 /* Debug / test export of assembled fine-level objects to HOST memory.
  * which: 0 L = M + tau C, 1 AC matrix, 2 velocity block A (scalar CSR of the
  * interleaved dofs), 3 B (N1 x 2*N2), 4 A_p, 5 M, 6 K.  Call with null arrays

@@ -28,6 +28,7 @@ import scipy.sparse as sp
 
 from . import fem
 from .mesh import Mesh
+from .quadrature import triangle_rule
 
 SPECIES = ("p", "N", "s", "a")
 
@@ -90,6 +91,38 @@ def potential(pp, pn, ps, pa, Phi):
     """f of eqn:appPotential."""
     q = interp_p(Phi)
     return (1 - q) * f_liquid(pp, pn, ps, pa) + q * f_gas(pp, pn, ps, pa)
+
+
+def free_energy(forms: Forms, state, params):
+    """Parts of the discrete energy of a state (Sec. 2.2 free energy in its
+    dimensionless form, beta_i and beta_v in place of eps_i^2 and lambda^2,
+    plus the kinetic energy of the flow with rho = 1):
+      local:    int f(phi_h, Phi_h) dx, f of eqn:appPotential (or the
+                solvent-air density of Sec. 5.1), phi_a = 1 - sum phi;
+                degree-7 integrand, exact rule;
+      gradient: sum_i beta_i / 2 int |grad phi_i|^2 + beta_v / 2 int |grad Phi_v|^2
+                = sum_i beta_i / 2 phi_i^T K phi_i + beta_v / 2 Phi^T K Phi;
+      kinetic:  1/2 int |v_h|^2 dx = 1/2 v^T M_v v."""
+    mesh = forms.mesh
+    phi, Phi = state["phi"], state["Phi_v"]
+    lam, w = triangle_rule(7)
+    _, area, _ = mesh.element_geometry()
+    pp, pn, ps = (fem.p1_field_at(mesh, phi[i], lam) for i in range(3))
+    pa = 1.0 - pp - pn - ps
+    Ph = fem.p1_field_at(mesh, Phi, lam)
+    if params.get("model", 0) == 1:
+        q = interp_p(Ph)
+        fq = (1 - q) * fh_liquid(ps, pa, params) + q * fh_gas(ps, pa, params)
+    else:
+        fq = potential(pp, pn, ps, pa, Ph)
+    local = float(np.sum(area[:, None] * w[None] * fq))
+    K = forms.K
+    fields = [phi[0], phi[1], phi[2], 1.0 - phi[0] - phi[1] - phi[2]]
+    grad = sum(0.5 * params["beta"][i] * float(fields[i] @ (K @ fields[i])) for i in range(4))
+    grad += 0.5 * params["beta_v"] * float(Phi @ (K @ Phi))
+    v = state["v"]
+    kinetic = 0.5 * float(v @ (forms.velocity_forms()["Mv"] @ v))
+    return {"local": local, "gradient": grad, "kinetic": kinetic}
 
 
 def potential_partials(pp, pn, ps, pa, Phi):

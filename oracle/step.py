@@ -36,7 +36,7 @@ from .krylov import chebyshev, fgmres, pcg
 from .mesh import Mesh
 from .mg import (MG, VEL_LO_RATIO, VEL_SMOOTH_DEGREE, inject_p1, inject_velocity, level_sizes, prolongation_p1,
                  prolongation_velocity)
-from .model import (Forms, ac_system, ch_rhs_loads, ch_system, mobility_at, ns_shift, ns_system,
+from .model import (Forms, ac_system, ch_rhs_loads, ch_system, free_energy, mobility_at, ns_shift, ns_system,
                     potential_loads)
 
 MASS_CHEB_DEGREE = 5
@@ -251,12 +251,20 @@ class Oracle:
         return new, info
 
     def diagnostics(self, state):
-        """FP64 mass sums 1^T M phi_i, ||B v||, int p (Sec. 3, L^2_0 pressure)."""
+        """FP64 mass sums 1^T M phi_i (i = p, N, s, and the air fraction
+        phi_a = 1 - sum phi), ||B v|| (discrete divergence), int p (Sec. 3,
+        L^2_0 pressure) and the discrete energy (model.free_energy: local
+        and gradient parts of the Sec. 2.2 free energy, kinetic energy)."""
         F = self.forms[0]
         vf = F.velocity_forms()
         one = np.ones(self.mesh.N1)
+        phi_a = 1.0 - state["phi"][0] - state["phi"][1] - state["phi"][2]
+        e = free_energy(F, state, self.params)
         return {
             "mass": [float(one @ (F.M @ state["phi"][i])) for i in range(3)],
+            "mass_a": float(one @ (F.M @ phi_a)),
             "div": float(np.linalg.norm(vf["B"] @ state["v"])),
             "p_mean": float(one @ (F.M @ state["p"])),
+            "energy": e["local"] + e["gradient"] + e["kinetic"],
+            "energy_parts": e,
         }

@@ -83,6 +83,18 @@ class Tuning(ctypes.Structure):
                 "block_p1": self.block_p1, "block_p2": self.block_p2}
 
 
+class Diag(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double * 4), ("div_norm", ctypes.c_double), ("p_mean", ctypes.c_double),
+                ("energy", ctypes.c_double), ("energy_local", ctypes.c_double),
+                ("energy_gradient", ctypes.c_double), ("energy_kinetic", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"mass": list(self.mass[:3]), "mass_a": self.mass[3], "div": self.div_norm, "p_mean": self.p_mean,
+                "energy": self.energy,
+                "energy_parts": {"local": self.energy_local, "gradient": self.energy_gradient,
+                                 "kinetic": self.energy_kinetic}}
+
+
 class ChnssError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"chnss {STATUS.get(status, status)}: {msg}")
@@ -120,6 +132,7 @@ EXPORTS = {
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo)]),
     "chnss_objective": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                        ctypes.c_void_p]),
+    "chnss_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.POINTER(Diag)]),
     "chnss_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
     "chnss_inner_stats_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(InnerStats)]),
@@ -366,6 +379,14 @@ class Context:
         _check(load().chnss_objective(self._h, _ptr(phi_p, N1, "device"), ctypes.byref(J), _ptr(grad, N1, "device")),
                self._h)
         return J.value
+
+    def diagnostics(self, state: dict) -> dict:
+        """chnss_diagnostics: FP64 mass sums of the four species, ||B v||,
+        int p and the energy parts of a device state (keys as the oracle's
+        Oracle.diagnostics)."""
+        d = Diag()
+        _check(load().chnss_diagnostics(self._h, ctypes.byref(self._state(state)), ctypes.byref(d)), self._h)
+        return d.as_dict()
 
     def mass_solve_noalloc(self, rhs, x=None, check: bool = True):
         """M x = rhs through chnss_mass_solve_noalloc (no device allocation

@@ -8,7 +8,7 @@
 // bit-reproducible results.
 #include <cmath>
 
-#include "internal.h"
+#include "kernels.h"
 
 namespace chnss {
 
@@ -413,6 +413,120 @@ __global__ void k_inject_vel(int nf, const double *__restrict__ fine, double *__
   coarse[2 * id + 1] = fine[2 * f + 1];
 }
 
+// Free-energy density f at one point (model 0: eqn:appPotential; model 1:
+// the solvent-air density of Sec. 5.1 with the Taylor-expanded x ln x).
+__device__ __forceinline__ double potential_value(const PotentialCoef &pc, double p, double nn, double s, double a,
+                                                  double V) {
+  const double ip = V * V * (3.0 - 2.0 * V);
+  if (pc.model == 0) {
+    const double liq = 3.5 * p * p * nn * nn + 0.3 * s * s + 0.3 * a * a - 10.0 * s * a;
+    const double gas = 3.5 * p * p + 3.5 * nn * nn + 2.0 * s * s + 0.1 * a * a;
+    return (1.0 - ip) * liq + ip * gas;
+  }
+  double d;
+  const double gs = taylor_xlnx(s, &d), ga = taylor_xlnx(a, &d);
+  const double liq = gs * pc.inv_ns + ga * pc.inv_na + pc.chi_sa * s * a;
+  const double gas = gs - s * pc.ln_sat_s + ga - a * pc.ln_sat_a;
+  return (1.0 - ip) * liq + ip * gas;
+}
+
+// Diagnostics of a state, one pass over the elements (fixed grid, each
+// thread its elements in grid-stride order, then the block in a fixed
+// order: bit-reproducible).  Per element, exactly:
+//   q 0..3  int phi_i = |T|/3 sum of the vertex values (i = p, NFA, s, and
+//           phi_a = 1 - sum phi), the entries of 1^T M phi_i;
+//   q 4     int p, likewise;
+//   q 5     int f(phi, Phi_v), 20-point rule exact to degree 7;
+//   q 6     |T| (sum_i beta_i |grad phi_i|^2 + beta_v |grad Phi_v|^2) / 2;
+//   q 7     |T| / 2 sum_ab m2_ab (v_a . v_b), the P2 mass form of the velocity.
+// partial[q * gridDim.x + blockIdx.x] = block sum of quantity q.
+constexpr int kDiagBlock = 256;
+__global__ void __launch_bounds__(kDiagBlock) k_diag(Geo g, DiagArgs d, double *__restrict__ partial) {
+  const int E = 2 * g.n * g.n;
+  double acc[kDiagQuantities];
+#pragma unroll
+  for (int q = 0; q < kDiagQuantities; ++q) acc[q] = 0.0;
+  for (int e = blockIdx.x * kDiagBlock + threadIdx.x; e < E; e += gridDim.x * kDiagBlock) {
+    Elem el;
+    element(g, e, el);
+    double f[5][3];
+    const double *fld[5] = {d.pp, d.pn, d.ps, d.Ph, d.p};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) f[c][k] = fld[c][el.v1[k]];
+    const double a3 = el.area / 3.0;
+    double sa = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double sc = f[c][0] + f[c][1] + f[c][2];
+      acc[c] += a3 * sc;
+      sa += sc;
+    }
+    acc[3] += a3 * (3.0 - sa);
+    acc[4] += a3 * (f[4][0] + f[4][1] + f[4][2]);
+    double loc = 0.0;
+    for (int q = 0; q < 20; ++q) {
+      const double l0 = c_ref.qlam[q][0], l1 = c_ref.qlam[q][1], l2 = c_ref.qlam[q][2];
+      const double pp = l0 * f[0][0] + l1 * f[0][1] + l2 * f[0][2];
+      const double pn = l0 * f[1][0] + l1 * f[1][1] + l2 * f[1][2];
+      const double ps = l0 * f[2][0] + l1 * f[2][1] + l2 * f[2][2];
+      const double V = l0 * f[3][0] + l1 * f[3][1] + l2 * f[3][2];
+      loc += c_ref.qw[q] * potential_value(d.pc, pp, pn, ps, 1.0 - pp - pn - ps, V);
+    }
+    acc[5] += el.area * loc;
+    double ge = 0.0;
+    double ga[2] = {0.0, 0.0};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      double gx = 0.0, gy = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        gx += f[c][k] * el.gl[k][0];
+        gy += f[c][k] * el.gl[k][1];
+      }
+      if (c < 3) {
+        ge += d.beta[c] * (gx * gx + gy * gy);
+        ga[0] -= gx;
+        ga[1] -= gy;
+      } else {
+        ge += d.beta_v * (gx * gx + gy * gy);
+      }
+    }
+    ge += d.beta[3] * (ga[0] * ga[0] + ga[1] * ga[1]);   // grad phi_a = -sum grad phi_i
+    acc[6] += 0.5 * el.area * ge;
+    double vx[6], vy[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      vx[k] = d.v[2L * el.v2[k]];
+      vy[k] = d.v[2L * el.v2[k] + 1];
+    }
+    double ke = 0.0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int b = 0; b < 6; ++b) ke += c_ref.m2[a][b] * (vx[a] * vx[b] + vy[a] * vy[b]);
+    acc[7] += 0.5 * el.area * ke;
+  }
+  // block sums in a fixed order: warp butterflies, then the warps' results
+  __shared__ double red[kDiagBlock / 32][kDiagQuantities];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kDiagQuantities; ++q) {
+    double v = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kDiagQuantities) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kDiagBlock / 32; ++w) t += red[w][threadIdx.x];
+    partial[(long)threadIdx.x * gridDim.x + blockIdx.x] = t;
+  }
+}
+
 MuPtrs mu_ptrs(const double *const *mu, const double *alpha) {
   MuPtrs m{};
   m.has = mu != nullptr;
@@ -424,6 +538,14 @@ MuPtrs mu_ptrs(const double *const *mu, const double *alpha) {
 }
 
 }  // namespace
+
+int launch_diagnostics(Geo g, const DiagArgs &d, double *partial, cudaStream_t s) {
+  const long E = 2L * g.n * g.n;
+  const int nb = reduce_blocks(E);
+  k_diag<<<nb, kDiagBlock, 0, s>>>(g, d, partial);
+  CHNSS_LAUNCH_CK();
+  return nb;
+}
 
 void launch_elem_p1_mass(Geo g, double *buf, cudaStream_t s) {
   k_p1_mass<<<blocks_for(2L * g.n * g.n), TPB, 0, s>>>(g, buf);

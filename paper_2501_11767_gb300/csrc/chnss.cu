@@ -154,6 +154,7 @@ struct chnss_ctx {
   double *rhs[6] = {};
   double *xsol[6] = {};
   double *massc = nullptr;
+  double *diag = nullptr;                   // chnss_diagnostics: kDiagQuantities sums + ||B v||^2
   std::unique_ptr<PrecSet<double>> p64;
   std::unique_ptr<PrecSet<float>> p32;
   // captured preconditioner graphs (0..2 CH species, 3 AC, 4 NS)
@@ -602,6 +603,7 @@ void create_context(chnss_ctx *c) {
   c->partial = ar.alloc<double>(64L * kReduceMaxBlocks);
   c->partial_ch = ar.alloc<double>(64L * kReduceMaxBlocks);
   c->sum = ar.alloc<double>(4);
+  c->diag = ar.alloc<double>(kDiagQuantities + 1);
   const int nl = c->nlev;
   c->M1.resize(nl); c->K1.resize(nl); c->ACb.resize(nl); c->M2v.resize(nl); c->Aconst.resize(nl);
   c->L.resize(nl); c->AC.resize(nl); c->A.resize(nl); c->X1.resize(nl); c->X2.resize(nl);
@@ -1805,6 +1807,48 @@ extern "C" chnss_status chnss_objective(chnss_ctx_t ctx, const double *phi_p, do
   }
   CHNSS_CK(cudaMemcpyAsync(J, ctx->adots + 30, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
   CHNSS_CK(cudaStreamSynchronize(ctx->s));
+  return CHNSS_OK;
+  ABI_CATCH(ctx)
+}
+
+extern "C" chnss_status chnss_diagnostics(chnss_ctx_t ctx, const chnss_state *state, chnss_diag *out) {
+  if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
+  ABI_TRY
+  if (!out) throw Error{CHNSS_ERR_ARG, "null output"};
+  check_state(state);
+  const chnss_params &p = ctx->p;
+  const Mesh &m = ctx->mesh->m;
+  cudaStream_t s = ctx->s;
+  DiagArgs d;
+  d.pp = state->phi[0];
+  d.pn = state->phi[1];
+  d.ps = state->phi[2];
+  d.Ph = state->Phi_v;
+  d.p = state->p;
+  d.v = state->v;
+  for (int i = 0; i < 4; ++i) d.beta[i] = p.beta[i];
+  d.beta_v = p.beta_v;
+  d.pc.model = p.model;
+  d.pc.inv_ns = 1.0 / p.n_s;
+  d.pc.inv_na = 1.0 / p.n_a;
+  d.pc.chi_sa = p.chi_sa;
+  d.pc.ln_sat_s = std::log(p.phi_sat_s);
+  d.pc.ln_sat_a = std::log(p.phi_sat_a);
+  const int nb = launch_diagnostics(geo(ctx->lv(0)), d, ctx->partial, s);
+  sum_partials(nb, kDiagQuantities, ctx->partial, ctx->diag, s);
+  // ||B v||: B v into the P1 scratch vector, then its FP64 dot product
+  spmv_b(m.pb, ctx->Bv, state->v, ctx->tmp, s);
+  dot<double>(ctx->N1, ctx->tmp, ctx->tmp, ctx->diag + kDiagQuantities, ctx->partial, s);
+  double h[kDiagQuantities + 1];
+  CHNSS_CK(cudaMemcpyAsync(h, ctx->diag, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CHNSS_CK(cudaStreamSynchronize(s));
+  for (int i = 0; i < 4; ++i) out->mass[i] = h[i];
+  out->p_mean = h[4];
+  out->energy_local = h[5];
+  out->energy_gradient = h[6];
+  out->energy_kinetic = h[7];
+  out->energy = h[5] + h[6] + h[7];
+  out->div_norm = std::sqrt(h[kDiagQuantities]);
   return CHNSS_OK;
   ABI_CATCH(ctx)
 }

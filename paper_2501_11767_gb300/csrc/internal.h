@@ -222,6 +222,16 @@ struct PotentialCoef {
 };
 void launch_elem_loads(Geo g, const double *phi_p, const double *phi_n, const double *phi_s,
                        const double *Phi, PotentialCoef pc, double *buf, cudaStream_t s);
+// Conservation and energy sums of a state (chnss_diagnostics): quantities
+// int phi_p, int phi_NFA, int phi_s, int phi_a, int p, int f, gradient
+// energy, kinetic energy; partial[q * nb + b] for the nb blocks returned.
+constexpr int kDiagQuantities = 8;
+struct DiagArgs {
+  const double *pp, *pn, *ps, *Ph, *p, *v;
+  double beta[4], beta_v;
+  PotentialCoef pc;
+};
+int launch_diagnostics(Geo g, const DiagArgs &d, double *partial, cudaStream_t s);
 struct KortewegCoef {
   double beta[4];
   double beta_v;

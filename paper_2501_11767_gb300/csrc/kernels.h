@@ -158,6 +158,8 @@ constexpr int kReduceMaxBlocks = 2048;
 int reduce_blocks(long n);
 // multiprocessors of the current device (queried once per device)
 int device_sm_count();
+// out[v] = sum over b < nb of partial[v * nb + b], v < k (fixed order)
+void sum_partials(int nb, int k, const double *partial, double *out, cudaStream_t s);
 template <typename T>
 void dot(long n, const T *x, const T *y, double *out, double *partial, cudaStream_t s);
 template <typename T>

@@ -1506,6 +1506,11 @@ void vec_mul(long n, const double *a, const double *b, double *out, cudaStream_t
   CHNSS_LAUNCH_CK();
 }
 
+void sum_partials(int nb, int k, const double *partial, double *out, cudaStream_t s) {
+  k_sum_final<<<std::min(k, 64), TPB, 0, s>>>(nb, k, partial, out);
+  CHNSS_LAUNCH_CK();
+}
+
 template <typename T>
 void dot(long n, const T *x, const T *y, double *out, double *partial, cudaStream_t s) {
   const int nb = reduce_blocks(n);

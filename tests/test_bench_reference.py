@@ -1,6 +1,6 @@
 """bench.py's reference arm (--impl reference): the oracle timed on the host
 cores, one JSON line with the keys of the bench contract (CPU only; one
-128 x 128 oracle step)."""
+128 x 128 oracle step, scaled to the 1024 x 1024 metric by the node ratio)."""
 import json
 import os
 import subprocess
@@ -27,8 +27,10 @@ def test_reference_line_has_the_contract_keys():
         assert key in d, key
     assert d["value"] > 0 and d["unit"] == "steps/s" and d["higher_is_better"] is True
     assert d["steps"] == 1 and d["n_gpus"] == 1
-    assert abs(d["ms_per_step"] - 1e3 / d["value"]) < 1e-6 * d["ms_per_step"]
-    assert d["config"]["workload"] == "film1024_mixed"
+    # ms_per_step is the wall time of one sampled step; value scales its rate by the node ratio
+    ratio = (d["config"]["sampled_n"] + 1) ** 2 / (d["config"]["n"] + 1) ** 2
+    assert abs(d["value"] * d["ms_per_step"] * 1e-3 - ratio) < 1e-3 * ratio
+    assert d["config"]["workload"] == "film1024_mixed" and d["config"]["sampled_n"] < d["config"]["n"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

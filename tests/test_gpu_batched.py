@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 from oracle.step import Oracle
+from solve_compare import compare_solves
 from paper_2501_11767_gb300 import chnss, inputs
 
 pytestmark = pytest.mark.gpu
@@ -60,14 +61,7 @@ def test_batched_instance_matches_oracle(torch):
     out, recs, _ = chnss.step_batched(ctxs, [chnss.state_to_device(st0)])
     ref, oinfo = Oracle(n, p).step(st0)
     got = chnss.state_to_numpy(out[0])
-    keys = {"ch_p": ("phi", 0), "ch_N": ("phi", 1), "ch_s": ("phi", 2), "ac": ("Phi_v", None), "ns": ("v", None)}
-    for name, (key, i) in keys.items():
-        assert recs[0][name]["converged"]
-        assert abs(recs[0][name]["iters"] - oinfo[name]["iters"]) <= 1, name
-        if recs[0][name]["iters"] == oinfo[name]["iters"]:
-            a = np.ravel(got[key] if i is None else got[key][i])
-            b = np.ravel(ref[key] if i is None else ref[key][i])
-            assert np.linalg.norm(a - b) <= 1e-9 * max(np.linalg.norm(b), 1e-300), name
+    compare_solves(got, recs[0], ref, oinfo, st0, p, lambda q: Oracle(n, q))
 
 
 def test_batched_rejects_a_repeated_context(torch):

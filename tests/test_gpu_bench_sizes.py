@@ -1,0 +1,117 @@
+"""Parity at the sizes the benchmarks run.
+
+128^2 (enclosed and open top) and 256^2 (concentration-dependent mobility,
+eps = 0.01: the 256^2 FP64 workload) against the oracle, solve by solve.
+From 128^2 on the Oseen system has more unknowns (148,739 at 128^2, 592,387
+at 256^2) than the CGS2 update kernels cover in one grid pass (two blocks of
+256 threads per multiprocessor), so their grid-stride loops repeat; the
+smaller parity cases never reach that.
+
+At the full 1024^2 bench configuration (FP32 multigrid inside FP64 FGMRES)
+the oracle is too slow for a whole step, so the properties that hold at any
+size are checked instead: every FGMRES solve of the step meets its stopping
+rule ||b - A x|| <= 1e-8 ||b|| when the residual is recomputed in FP64 by
+scipy from the exported assembled operators (an implementation that shares
+nothing with the library's SpMV), and the CH operators the solves used equal
+their definition from the exported M, K and L blocks."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle.step import Oracle
+from solve_compare import compare_solves, rel
+from paper_2501_11767_gb300 import chnss, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    return torch
+
+
+def _steps(torch, n, params, seed, steps, top_bc=0):
+    o = Oracle(n, params)
+    ctx = chnss.Context(chnss.Mesh(n, top_bc=top_bc), params)
+    st = inputs.initial_state(n, seed=seed)
+    reruns = []
+    for k in range(steps):
+        ref, rinfo = o.step(st)
+        out, info, status = ctx.step(chnss.state_to_device(st))
+        torch.cuda.synchronize()
+        assert status == 0
+        got = chnss.state_to_numpy(out)
+        reruns += compare_solves(got, info, ref, rinfo, st, params, lambda q: Oracle(n, q), where=(n, k))
+        assert rel(got["mu"][3], ref["mu"][3]) <= 1e-9
+        st = ref
+    return reruns
+
+
+@pytest.mark.parametrize("top_bc", [0, 1])
+def test_steps_match_oracle_at_128(torch, top_bc):
+    """Two steps (the second with convection) on 128 x 128."""
+    p = dict(inputs.default_params(), top_bc=top_bc)
+    _steps(torch, 128, p, seed=128 + top_bc, steps=2, top_bc=top_bc)
+
+
+def test_step_matches_oracle_at_256_variable_mobility(torch):
+    """One FP64 step of the 256 x 256 workload: eps = 0.01, mobility
+    gamma_i (phi_i (1 - phi_i) + 1e-3)."""
+    w = inputs.workload("film256_mobility")
+    _steps(torch, w["n"], dict(w["params"], precision=0), seed=0, steps=1)
+
+
+def _csr(ctx, which, shape):
+    rp, col, val = ctx.export_csr(which)
+    return sp.csr_matrix((val, col, rp), shape=shape)
+
+
+def test_full_size_solves_meet_the_stopping_rule(torch):
+    """1024 x 1024, the bench parameter set (mixed precision), two steps from
+    the seeded start: residuals of the returned solutions recomputed in FP64
+    on the host."""
+    w = inputs.workload("film1024_mixed")
+    n, p = w["n"], w["params"]
+    mesh = chnss.Mesh(n)
+    ctx = chnss.Context(mesh, p)
+    N1, N2 = mesh.N1, mesh.N2
+    st = chnss.state_to_device(inputs.initial_state(n, seed=0))
+    for k in range(2):
+        out, info, status = ctx.step(st)
+        torch.cuda.synchronize()
+        assert status == 0
+        # the context holds the operators and right-hand sides of this step
+        M = _csr(ctx, chnss.MAT_M, (N1, N1))
+        K = _csr(ctx, chnss.MAT_K, (N1, N1))
+        L = _csr(ctx, chnss.MAT_L, (N1, N1))
+        got = chnss.state_to_numpy(out)
+        tau, rtol = p["tau"], p["rtol"]
+        for sp_, name in enumerate(("ch_p", "ch_N", "ch_s")):
+            g, b = p["gamma"][sp_], p["beta"][sp_]
+            A = sp.bmat([[L, tau * g * K], [tau * g * K, -(tau * g / b) * M]], format="csr")
+            rhs = ctx.export_rhs(sp_)
+            x = np.concatenate([got["phi"][sp_], got["mu"][sp_]])
+            r = np.linalg.norm(rhs - A @ x) / np.linalg.norm(rhs)
+            assert info[name]["converged"] and r <= rtol * (1 + 1e-6), (k, name, r, info[name])
+        Aac = _csr(ctx, chnss.MAT_AC, (N1, N1))
+        rhs = ctx.export_rhs(chnss.SYS_AC)
+        r = np.linalg.norm(rhs - Aac @ got["Phi_v"]) / np.linalg.norm(rhs)
+        assert info["ac"]["converged"] and r <= rtol * (1 + 1e-6), (k, r)
+        # AC operator = M + tau delta_v K + tau C with tau C = L - M
+        D = Aac - (M + tau * p["delta_v"] * K + (L - M))
+        assert abs(D).max() <= 1e-13 * abs(Aac).max()
+        del Aac, A, L
+        Av = _csr(ctx, chnss.MAT_A, (2 * N2, 2 * N2))
+        B = _csr(ctx, chnss.MAT_B, (N1, 2 * N2))
+        rhs = ctx.export_rhs(chnss.SYS_NS)
+        v, pr = got["v"], got["p"]
+        res = np.concatenate([rhs[:2 * N2] - Av @ v - B.T @ pr, rhs[2 * N2:] - B @ v])
+        r = np.linalg.norm(res) / np.linalg.norm(rhs)
+        assert info["ns"]["converged"] and r <= rtol * (1 + 1e-6), (k, r, info["ns"])
+        # enclosed flow: the returned pressure has zero mean
+        assert abs(M @ pr).sum() > 0 and abs((M @ pr).sum()) <= 1e-12 * abs(M @ pr).sum()
+        del Av, B
+        st = out

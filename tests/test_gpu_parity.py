@@ -9,6 +9,7 @@ import scipy.sparse as sp
 from oracle import fem, model
 from oracle.step import Oracle
 from paper_2501_11767_gb300 import chnss, inputs
+from solve_compare import compare_solves
 
 pytestmark = pytest.mark.gpu
 
@@ -92,19 +93,7 @@ def _compare_step(torch, n, params, seed, steps=2):
         out, info, status = ctx.step(dev)
         torch.cuda.synchronize()
         got = chnss.state_to_numpy(out)
-        N1 = o.mesh.N1
-        for i, name in enumerate(("ch_p", "ch_N", "ch_s")):
-            assert info[name]["converged"], (name, info[name])
-            assert abs(info[name]["iters"] - rinfo[name]["iters"]) <= 1, (k, name, info[name], rinfo[name])
-            if info[name]["iters"] == rinfo[name]["iters"]:
-                e = rel(np.concatenate([got["phi"][i], got["mu"][i]]), np.concatenate([ref["phi"][i], ref["mu"][i]]))
-                assert e <= SOLVE_TOL, (k, name, e)
-        for name, keys in (("ac", ("Phi_v",)), ("ns", ("v", "p"))):
-            assert info[name]["converged"], (name, info[name])
-            assert abs(info[name]["iters"] - rinfo[name]["iters"]) <= 1, (k, name, info[name], rinfo[name])
-            if info[name]["iters"] == rinfo[name]["iters"]:
-                e = rel(np.concatenate([got[x].ravel() for x in keys]), np.concatenate([ref[x].ravel() for x in keys]))
-                assert e <= SOLVE_TOL, (k, name, e)
+        compare_solves(got, info, ref, rinfo, st, params, lambda q: Oracle(n, q), where=k)
         assert rel(got["mu"][3], ref["mu"][3]) <= SOLVE_TOL
         assert status == 0
         st, dev = ref, chnss.state_to_device(ref)     # continue both from the oracle state

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from oracle.step import Oracle
+from solve_compare import compare_solves
 from paper_2501_11767_gb300 import chnss, inputs
 
 pytestmark = pytest.mark.gpu
@@ -38,13 +39,7 @@ def test_solvent_air_steps_match_oracle(torch, n):
         assert info["ch_p"]["iters"] == 0 and info["ch_N"]["iters"] == 0
         assert not np.any(got["phi"][:2]) and not np.any(got["mu"][:2])
         assert got["phi"][2].min() >= 0.0 and got["phi"][2].max() <= 1.0
-        for name, keys in (("ch_s", (("phi", 2), ("mu", 2))), ("ac", (("Phi_v", None),)),
-                           ("ns", (("v", None), ("p", None)))):
-            assert abs(info[name]["iters"] - rinfo[name]["iters"]) <= 1, (k, name, info[name], rinfo[name])
-            if info[name]["iters"] == rinfo[name]["iters"]:
-                a = np.concatenate([np.ravel(got[f] if i is None else got[f][i]) for f, i in keys])
-                b = np.concatenate([np.ravel(ref[f] if i is None else ref[f][i]) for f, i in keys])
-                assert rel(a, b) <= SOLVE_TOL, (k, name, rel(a, b))
+        compare_solves(got, info, ref, rinfo, st, p, lambda q: Oracle(n, q), names=("ch_s", "ac", "ns"), where=k)
         assert rel(got["mu"][3], ref["mu"][3]) <= SOLVE_TOL
         st = ref
 

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import three_d as t3
+from solve_compare import compare_solves
 from paper_2501_11767_gb300 import chnss, inputs
 
 pytestmark = pytest.mark.gpu
@@ -45,15 +46,7 @@ def _compare(torch, n, params, seed, steps=2):
         torch.cuda.synchronize()
         assert status == 0
         got = chnss.state_to_numpy(out)
-        groups = [(name, (("phi", i), ("mu", i))) for i, name in enumerate(("ch_p", "ch_N", "ch_s"))]
-        groups += [("ac", (("Phi_v", None),)), ("ns", (("v", None), ("p", None)))]
-        for name, keys in groups:
-            assert info[name]["converged"], (name, info[name])
-            assert abs(info[name]["iters"] - rinfo[name]["iters"]) <= 1, (k, name, info[name], rinfo[name])
-            if info[name]["iters"] == rinfo[name]["iters"]:
-                g = np.concatenate([np.ravel(got[a] if i is None else got[a][i]) for a, i in keys])
-                r = np.concatenate([np.ravel(ref[a] if i is None else ref[a][i]) for a, i in keys])
-                assert rel(g, r) <= SOLVE_TOL, (k, name, rel(g, r))
+        compare_solves(got, info, ref, rinfo, st, params, lambda q: t3.Oracle3D(n, q), where=k)
         assert rel(got["mu"][3], ref["mu"][3]) <= SOLVE_TOL
         st = ref
     return ctx

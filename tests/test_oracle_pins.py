@@ -237,3 +237,74 @@ def test_enclosed_pcd_oseen_iterations_stay_flat(n):
     st = o.step(inputs.initial_state(n, seed=1))[0]
     info = o.step(st)[1]
     assert info["ns"]["converged"] and info["ns"]["iters"] <= 60, info["ns"]
+
+
+# ---------------------------------------------------------------------------
+def _forms(n, params):
+    return model.Forms(Mesh(n), params)
+
+
+def test_free_energy_local_part_of_constant_fields():
+    """phi = (0.3, 0.3, 0.4), phi_a = 0: eqn:appPotential gives f_liq =
+    3.5 * 0.09 * 0.09 + 0.3 * 0.16 = 0.07635 and f_gas = 3.5 * 0.09 * 2 + 2 *
+    0.16 = 0.95; with p(Phi) = Phi^2 (3 - 2 Phi), p(1/2) = 1/2, so the
+    density at Phi = 1/2 is 0.513175.  Area 2 (a 2 x 1 box)."""
+    p = inputs.default_params()
+    mesh = Mesh(4, 2.0, 1.0)
+    forms = model.Forms(mesh, p)
+    for Phi, dens in ((0.0, 0.07635), (1.0, 0.95), (0.5, 0.513175)):
+        st = {"phi": np.stack([np.full(mesh.N1, 0.3), np.full(mesh.N1, 0.3), np.full(mesh.N1, 0.4)]),
+              "Phi_v": np.full(mesh.N1, Phi), "v": np.zeros(2 * mesh.N2)}
+        e = model.free_energy(forms, st, p)
+        assert e["local"] == pytest.approx(2.0 * dens, rel=1e-13), Phi
+        assert abs(e["gradient"]) < 1e-15 and e["kinetic"] == 0.0
+
+
+def test_free_energy_gradient_part_is_half_the_trace_of_the_korteweg_tensor():
+    """For linear fields the gradient energy density sum beta_i |grad
+    phi_i|^2 / 2 + beta_v |grad Phi_v|^2 / 2 is constant and equals tr(G) / 2
+    with G the Korteweg tensor of the golden file: (0.01312 + 0.00725) / 2 =
+    0.010185 on the unit square."""
+    g = _golden()
+    p = _params(g)
+    forms = _forms(4, p)
+    mesh = forms.mesh
+    x, y = mesh.x1[:, 0], mesh.x1[:, 1]
+    st = {"phi": np.stack([0.3 + 0.1 * x, 0.3 - 0.05 * y, 0.4 + 0.02 * x]), "Phi_v": 0.1 * y,
+          "v": np.zeros(2 * mesh.N2)}
+    e = model.free_energy(forms, st, p)
+    assert e["gradient"] == pytest.approx(0.010185, rel=1e-12)
+    assert e["gradient"] == pytest.approx(0.5 * (g["G2"][0] + g["G2"][3]), rel=1e-12)
+
+
+def test_free_energy_local_part_rule_is_exact_for_linear_fields():
+    """With linear fields the density is a polynomial of degree 7 (degree 4 in
+    phi times the cubic p(Phi)); the degree-7 rule must equal a degree-15 one."""
+    from oracle.quadrature import triangle_rule
+    p = inputs.default_params()
+    forms = _forms(4, p)
+    mesh = forms.mesh
+    x, y = mesh.x1[:, 0], mesh.x1[:, 1]
+    st = {"phi": np.stack([0.2 + 0.3 * x, 0.35 - 0.2 * y + 0.1 * x, 0.3 + 0.1 * y]), "Phi_v": 0.2 + 0.6 * x * 0 + 0.5 * y,
+          "v": np.zeros(2 * mesh.N2)}
+    e = model.free_energy(forms, st, p)
+    lam, w = triangle_rule(15)
+    _, area, _ = mesh.element_geometry()
+    pp, pn, ps = (fem.p1_field_at(mesh, st["phi"][i], lam) for i in range(3))
+    Ph = fem.p1_field_at(mesh, st["Phi_v"], lam)
+    ref = float(np.sum(area[:, None] * w[None] * model.potential(pp, pn, ps, 1 - pp - pn - ps, Ph)))
+    assert e["local"] == pytest.approx(ref, rel=1e-13)
+
+
+def test_free_energy_kinetic_part_of_quadratic_free_velocities():
+    """v = (1, 0): 1/2 int |v|^2 = 1/2; v = (x, y): 1/2 (1/3 + 1/3) = 1/3 on the
+    unit square (both exact in the P2 velocity space)."""
+    p = inputs.default_params()
+    forms = _forms(4, p)
+    mesh = forms.mesh
+    X, Y = mesh.x2[:, 0], mesh.x2[:, 1]
+    base = {"phi": np.zeros((3, mesh.N1)), "Phi_v": np.zeros(mesh.N1)}
+    e1 = model.free_energy(forms, dict(base, v=np.stack([np.ones_like(X), np.zeros_like(X)], 1).ravel()), p)
+    e2 = model.free_energy(forms, dict(base, v=np.stack([X, Y], 1).ravel()), p)
+    assert e1["kinetic"] == pytest.approx(0.5, rel=1e-13)
+    assert e2["kinetic"] == pytest.approx(1.0 / 3.0, rel=1e-13)
