@@ -116,7 +116,10 @@ typedef struct {
 
 /* Mesh hierarchy for n x n squares on [0,lx] x [0,ly]: n even, 2 <= n <= 2048,
  * nx == ny required.  Multigrid levels n, n/2, ... while the size is even and
- * at least 4.  Builds the CSR patterns, the element -> CSR gather maps and
+ * at least 4; the coarsest level (n = m 2^k with m odd or m = 2) must have
+ * m <= 9 cells per side, because it is solved by a dense inverse rebuilt
+ * every step by one thread block (2 (2m + 1)^2 velocity rows: 722 for
+ * m = 9); n = 50, 100 or 200 (m = 25) are refused.  Builds the CSR patterns, the element -> CSR gather maps and
  * the transfer operators (host), and uploads them.  Returns CHNSS_ERR_ARG
  * for bad sizes, CHNSS_ERR_OOM / CHNSS_ERR_CUDA on device failures. */
 chnss_status chnss_mesh_create(int nx, int ny, double lx, double ly, chnss_mesh_t *out);

@@ -921,6 +921,8 @@ int system_size(chnss_ctx *c, int sys) {
 }
 
 // One system on stream s with Krylov work kw and an N1 scratch vector tmp.
+constexpr int kMaxCoarseCells = 9;   // largest coarsest level of a 2D mesh hierarchy (cells per side)
+
 // [a, a + n) and [b, b + n) share at least one element
 bool ranges_overlap(const double *a, const double *b, long n) {
   const auto x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
@@ -1155,6 +1157,18 @@ chnss_status chnss_mesh_create_ex(int nx, int ny, double lx, double ly, int top_
   // element-buffer offsets and gather counts are int: 144 E = 288 n^2 stays
   // below 2^31 up to n = 2730
   if (nx < 2 || nx % 2 != 0 || nx > 2048) throw Error{CHNSS_ERR_ARG, "n must be even and in [2, 2048]"};
+  // the hierarchy halves n while it is even and >= 4; the coarsest level is
+  // solved by a dense inverse built by one thread block every step, whose
+  // velocity block has 2 (2 n_c + 1)^2 rows: its memory grows as n_c^4 and
+  // its cost as n_c^6 (n_c = 9: 722 rows, ~0.1 s per step; n_c = 129 would
+  // need 144 GB), so meshes must coarsen to at most 9 x 9 cells
+  int nc = nx;
+  while (nc % 2 == 0 && nc >= 4) nc /= 2;
+  if (nc > kMaxCoarseCells)
+    throw Error{CHNSS_ERR_ARG, "n = " + std::to_string(nx) + " coarsens to " + std::to_string(nc) + " x " +
+                                   std::to_string(nc) + " cells; the dense coarse-level solve supports at most " +
+                                   std::to_string(kMaxCoarseCells) + " x " + std::to_string(kMaxCoarseCells) +
+                                   ": choose n = m 2^k with m <= " + std::to_string(kMaxCoarseCells)};
   if (!(lx > 0) || !(ly > 0)) throw Error{CHNSS_ERR_ARG, "domain lengths must be > 0"};
   std::unique_ptr<chnss_mesh> m(new chnss_mesh());
   build_mesh(m->m, nx, lx, ly, top_bc);

@@ -46,6 +46,9 @@ def test_argument_errors_need_no_device(lib):
     assert lib.chnss_mesh_create(7, 7, 1.0, 1.0, ctypes.byref(h)) == 1      # odd n
     assert lib.chnss_mesh_create(2050, 2050, 1.0, 1.0, ctypes.byref(h)) == 1  # int32 element offsets
     assert b"even" in lib.chnss_last_error(None)
+    assert lib.chnss_mesh_create(258, 258, 1.0, 1.0, ctypes.byref(h)) == 1  # coarsens to 129 x 129
+    assert b"coarsens to 129 x 129" in lib.chnss_last_error(None)
+    assert lib.chnss_mesh_create(100, 100, 1.0, 1.0, ctypes.byref(h)) == 1  # coarsens to 25 x 25
     assert lib.chnss_mesh_create(8, 16, 1.0, 1.0, ctypes.byref(h)) == 1     # nx != ny
     assert lib.chnss_mesh_create(8, 8, -1.0, 1.0, ctypes.byref(h)) == 1     # bad length
     assert lib.chnss_mesh_create(8, 8, 1.0, 1.0, None) == 1
@@ -63,6 +66,7 @@ def test_argument_errors_need_no_device(lib):
     assert lib.chnss_autotune(None, None) == 1
     assert lib.chnss_set_spmv_block(None, 256, 256) == 1
     assert lib.chnss_set_step_concurrency(None, 1) == 1
+    assert lib.chnss_diagnostics(None, None, None) == 1
 
 
 def test_params_struct_matches_header():
