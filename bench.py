@@ -183,7 +183,9 @@ def run_gpu(args):
             dist.barrier()
 
     w = inputs.workload(args.workload)
-    n, params = w["n"], w["params"]
+    n, params = w["n"], dict(w["params"])
+    if args.ortho >= 0:
+        params["ortho"] = args.ortho
     mesh = chnss.Mesh(n, top_bc=params.get("top_bc", 0))
     N1, N2 = mesh.N1, mesh.N2
     stream = torch.cuda.current_stream()
@@ -294,7 +296,7 @@ def run_gpu(args):
 
     fp64 = None
     if not args.no_fp64:
-        p64 = dict(params, precision=0)
+        p64 = dict(params, precision=0, ortho=0)     # FP64 throughout, Gram-Schmidt included
         ctx64, ms64, infos64, _, _, _ = timed_run(p64, 1, args.fp64_steps, False)
         fp64 = {"value": args.fp64_steps / (ms64 / 1e3), "unit": "steps/s", "steps": args.fp64_steps,
                 "ms_per_step": ms64 / args.fp64_steps,
@@ -385,6 +387,7 @@ def run_gpu(args):
         "data": "synthetic (seeded SplitMix64 noise on phi_p, phi_NFA; paper-shaped thin film)",
         "config": {"workload": args.workload, "n": n, "p1_nodes": N1, "p2_nodes": N2,
                    "velocity_dofs": 2 * N2, "precision": "mixed" if params["precision"] == 1 else "fp64",
+                   "gram_schmidt": "double-FP32" if params.get("ortho", 0) == 1 else "FP64",
                    "rtol": params["rtol"], "restart": params["restart"], "tau": params["tau"],
                    "beta": params["beta"],
                    "l2": "inputs larger than L2 (per-step working set > 10 GB)",
@@ -772,6 +775,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--bf16-steps", type=int, default=5)
     ap.add_argument("--roofline-steps", type=int, default=3)
+    ap.add_argument("--ortho", type=int, default=-1, choices=[-1, 0, 1],
+                    help="Gram-Schmidt arithmetic of the headline leg: 0 FP64, 1 double-FP32 (-1: the workload's)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -96,6 +96,12 @@ typedef struct {
   double ns_rtol, ns_atol;  /* ns_rtol > 0: stopping rule of the Oseen solve alone (Sec. 5 uses
                                rtol 1e-4, atol 1e-8 for it and 1e-6, 1e-8 for CH and AC);
                                0: the Oseen solve uses rtol, atol */
+  int ortho;             /* arithmetic of the FGMRES Gram-Schmidt passes (CGS2): 0: FP64;
+                            1: double-FP32, every value a pair of FP32 numbers (about 48
+                            significant bits; Dekker's exact product, Knuth's two-sum) on the
+                            FP32 pipe, with the basis kept as pairs beside its FP64 copy (the
+                            outer residuals, the Hessenberg data, the solution update and the
+                            preconditioner input stay FP64); applies when restart <= 31 */
 } chnss_params;
 
 /* Fields of one time level (DEVICE pointers, caller-owned, FP64). */
@@ -264,6 +270,18 @@ chnss_status chnss_diagnostics(chnss_ctx_t ctx, const chnss_state *state, chnss_
  * val[nnz]. */
 chnss_status chnss_export_csr(chnss_ctx_t ctx, int which, int *nrows, int *nnz, int *rowptr, int *col,
                               double *val);
+/* Debug / test entry: one orthogonalisation step of FGMRES (Sec. 5 solves
+ * with GMRES; the build's Krylov method orthogonalises by classical
+ * Gram-Schmidt applied twice) of the device vector w against the k device
+ * vectors V (column j at V + j ld, 1 <= k <= 31, ld >= n and even), with the
+ * library's own kernels in FP64 (arith 0) or double-FP32 (arith 1, the
+ * ortho = 1 path).  h (host, 2k + 1 doubles): the pass-1 dots V^T w, the
+ * pass-2 dots V^T w' of w' = w - V h1, and ||w'||^2; vout (device, n): the
+ * next basis vector (w' - V h2) / hn with hn^2 = ||w'||^2 - ||h2||^2.  V and
+ * w are not modified.  Allocates its scratch with cudaMalloc on every call
+ * and synchronises; CHNSS_ERR_ARG for bad sizes or null pointers. */
+chnss_status chnss_debug_cgs2(int arith, long n, int k, const double *V, long ld, const double *w, double *h,
+                              double *vout);
 /* Assembled right-hand side of a system (host, chnss_system_size doubles). */
 chnss_status chnss_export_rhs(chnss_ctx_t ctx, chnss_system sys, double *host_out);
 

@@ -32,7 +32,7 @@ class Params(ctypes.Structure):
                 ("model", ctypes.c_int), ("chi_sa", ctypes.c_double), ("n_s", ctypes.c_double),
                 ("n_a", ctypes.c_double), ("phi_sat_s", ctypes.c_double), ("phi_sat_a", ctypes.c_double),
                 ("inner_rtol", ctypes.c_double), ("inner_maxit", ctypes.c_int),
-                ("ns_rtol", ctypes.c_double), ("ns_atol", ctypes.c_double)]
+                ("ns_rtol", ctypes.c_double), ("ns_atol", ctypes.c_double), ("ortho", ctypes.c_int)]
 
 
 class State(ctypes.Structure):
@@ -133,6 +133,8 @@ EXPORTS = {
     "chnss_objective": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                        ctypes.c_void_p]),
     "chnss_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.POINTER(Diag)]),
+    "chnss_debug_cgs2": (ctypes.c_int, [ctypes.c_int, ctypes.c_long, ctypes.c_int, ctypes.c_void_p, ctypes.c_long,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "chnss_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
     "chnss_inner_stats_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(InnerStats)]),
@@ -187,7 +189,8 @@ def _check(status, ctx=None):
 
 # fields of the solvent-air sub-model, defaulted when a parameter set omits them
 _OPTIONAL = {"model": 0, "chi_sa": 0.0, "n_s": 1.0, "n_a": 1.0, "phi_sat_s": 1e-6, "phi_sat_a": 1.0,
-             "inner_rtol": 0.0, "inner_maxit": 20, "ns_rtol": 0.0, "ns_atol": 0.0}
+             "inner_rtol": 0.0, "inner_maxit": 20, "ns_rtol": 0.0, "ns_atol": 0.0,
+             "ortho": 0}
 
 
 def make_params(d: dict) -> Params:
@@ -512,6 +515,23 @@ def host_operator3(n: int, which: str, params: dict, state: dict = None):
     _check(lib.chnss3_host_operator(n, op, ctypes.byref(prm), sptr, ctypes.byref(nr), ctypes.byref(nc),
                                     ctypes.byref(nnz), rowptr.ctypes.data, col.ctypes.data, val.ctypes.data))
     return sp.csr_matrix((val, col, rowptr), shape=(nr.value, nc.value))
+
+
+def debug_cgs2(V, w, arith: int):
+    """chnss_debug_cgs2: one CGS2 step of the CUDA device vector w against the
+    rows of the (k, ld) CUDA array V (FP64 or double-FP32 kernels).
+    Returns (h1, h2, ||w'||^2, vout)."""
+    import torch
+    k, ld = V.shape
+    n = w.numel()
+    if not (V.is_cuda and w.is_cuda) or V.dtype != torch.float64 or w.dtype != torch.float64:
+        raise ValueError("V and w must be CUDA float64 tensors")
+    if not V.is_contiguous() or not w.is_contiguous() or ld < n:
+        raise ValueError("V must be contiguous (k, ld) with ld >= n")
+    h = np.zeros(2 * k + 1)
+    vout = torch.empty(n, dtype=torch.float64, device=w.device)
+    _check(load().chnss_debug_cgs2(arith, n, k, V.data_ptr(), ld, w.data_ptr(), h.ctypes.data, vout.data_ptr()))
+    return h[:k], h[k:2 * k], h[2 * k], vout
 
 
 def step_batched(ctxs, states_in, states_out=None, max_threads: int = 0, check: bool = True):

@@ -716,11 +716,12 @@ void create_context(chnss_ctx *c) {
     }
     c->massc = ar.upload(mc);
   }
-  c->kw.init(ar, p.restart, 2L * c->N2 + c->N1, c->pinned + 8);
-  c->kwb[0].init(ar, p.restart, 2L * c->N1, c->pinned + 16);
-  c->kwb[1].init(ar, p.restart, 2L * c->N1, c->pinned + 20);
-  c->kwc0.init(ar, p.restart, 2L * c->N1, c->pinned + 24);
-  c->kwa.init(ar, p.restart, c->N1, c->pinned + 28);
+  const bool pairs = p.ortho == 1;
+  c->kw.init(ar, p.restart, 2L * c->N2 + c->N1, c->pinned + 8, pairs);
+  c->kwb[0].init(ar, p.restart, 2L * c->N1, c->pinned + 16, pairs);
+  c->kwb[1].init(ar, p.restart, 2L * c->N1, c->pinned + 20, pairs);
+  c->kwc0.init(ar, p.restart, 2L * c->N1, c->pinned + 24, pairs);
+  c->kwa.init(ar, p.restart, c->N1, c->pinned + 28, pairs);
   c->tmp_ns = ar.alloc<double>(c->N1);
   // The Oseen group is the step's critical path (about three quarters of
   // the serial step's solve time); its stream gets the highest priority so
@@ -923,6 +924,21 @@ int system_size(chnss_ctx *c, int sys) {
 // One system on stream s with Krylov work kw and an N1 scratch vector tmp.
 constexpr int kMaxCoarseCells = 9;   // largest coarsest level of a 2D mesh hierarchy (cells per side)
 
+// device allocations of a debug entry point, freed when it returns
+struct ScopedDeviceMem {
+  std::vector<void *> p;
+  template <typename T>
+  T *get(long count) {
+    void *q = nullptr;
+    CHNSS_CK(cudaMalloc(&q, std::max(count, 1L) * sizeof(T)));
+    p.push_back(q);
+    return static_cast<T *>(q);
+  }
+  ~ScopedDeviceMem() {
+    for (void *q : p) cudaFree(q);
+  }
+};
+
 // [a, a + n) and [b, b + n) share at least one element
 bool ranges_overlap(const double *a, const double *b, long n) {
   const auto x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
@@ -1122,6 +1138,7 @@ void check_params(const chnss_params *p) {
   if (!(p->inner_rtol >= 0.0 && p->inner_rtol < 1.0)) throw Error{CHNSS_ERR_ARG, "inner_rtol must be in [0, 1)"};
   if (!(p->ns_rtol >= 0.0 && p->ns_rtol < 1.0) || !(p->ns_atol >= 0.0))
     throw Error{CHNSS_ERR_ARG, "ns_rtol must be in [0, 1) and ns_atol >= 0"};
+  if (p->ortho != 0 && p->ortho != 1) throw Error{CHNSS_ERR_ARG, "ortho must be 0 (FP64) or 1 (double-FP32)"};
   if (p->inner_rtol > 0.0 && (p->inner_maxit < 1 || p->inner_maxit > 1000))
     throw Error{CHNSS_ERR_ARG, "inner_maxit must be in [1, 1000]"};
   if (!(p->rtol >= 0) || !(p->atol >= 0)) throw Error{CHNSS_ERR_ARG, "tolerances must be >= 0"};
@@ -1359,6 +1376,52 @@ chnss_status chnss_export_csr(chnss_ctx_t ctx, int which, int *nrows, int *nnz, 
   }
   return CHNSS_OK;
   ABI_CATCH(ctx)
+}
+
+chnss_status chnss_debug_cgs2(int arith, long n, int k, const double *V, long ld, const double *w, double *h,
+                              double *vout) {
+  ABI_TRY
+  if (arith != 0 && arith != 1) throw Error{CHNSS_ERR_ARG, "arith must be 0 (FP64) or 1 (double-FP32)"};
+  if (n < 1 || k < 1 || k > 31 || ld < n) throw Error{CHNSS_ERR_ARG, "need n >= 1, 1 <= k <= 31, ld >= n"};
+  if (!V || !w || !h || !vout) throw Error{CHNSS_ERR_ARG, "null argument"};
+  if (ld % 2 != 0) throw Error{CHNSS_ERR_ARG, "ld must be even (16-byte aligned basis vectors)"};
+  ScopedDeviceMem mem;
+  cudaStream_t s = nullptr;   // the legacy stream, synchronised before returning
+  double *wc = mem.get<double>(n), *h1 = mem.get<double>(k + 1), *h2 = mem.get<double>(k + 1);
+  double *partial = mem.get<double>(64L * kReduceMaxBlocks), *hn = mem.get<double>(1);
+  CHNSS_CK(cudaMemcpyAsync(wc, w, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  std::vector<double> hh(2 * k + 1);
+  auto finish_norm = [&]() {
+    CHNSS_CK(cudaMemcpyAsync(hh.data(), h1, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CHNSS_CK(cudaMemcpyAsync(hh.data() + k, h2, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CHNSS_CK(cudaStreamSynchronize(s));
+    double sq = hh[2 * k];
+    for (int j = 0; j < k; ++j) sq -= hh[k + j] * hh[k + j];
+    const double nrm = std::sqrt(std::max(sq, 0.0));
+    CHNSS_CK(cudaMemcpyAsync(hn, &nrm, sizeof(double), cudaMemcpyHostToDevice, s));
+    CHNSS_CK(cudaStreamSynchronize(s));
+  };
+  if (arith == 0) {
+    cgs2_dots(n, V, ld, k, wc, h1, partial, s);
+    cgs2_update_dots(n, V, ld, k, h1, wc, h2, partial, s);
+    finish_norm();
+    cgs2_update_scale(n, V, ld, k, h2, wc, hn, vout, s);
+  } else {
+    float2 *V2 = mem.get<float2>((long)k * ld), *v2 = mem.get<float2>(n);
+    double *one = mem.get<double>(1), *tmp = mem.get<double>(n);
+    const double o = 1.0;
+    CHNSS_CK(cudaMemcpyAsync(one, &o, sizeof(double), cudaMemcpyHostToDevice, s));
+    for (int j = 0; j < k; ++j) dfgs_first(n, V + (long)j * ld, one, V2 + (long)j * ld, tmp, s);
+    dfgs_dots(n, V2, ld, k, wc, h1, partial, s);
+    dfgs_update_dots(n, V2, ld, k, h1, wc, h2, partial, s);
+    finish_norm();
+    dfgs_update_scale(n, V2, ld, k, h2, wc, hn, v2, vout, s);
+  }
+  CHNSS_CK(cudaStreamSynchronize(s));
+  CHNSS_CK(cudaGetLastError());
+  std::copy(hh.begin(), hh.end(), h);
+  return CHNSS_OK;
+  ABI_CATCH(nullptr)
 }
 
 chnss_status chnss_export_rhs(chnss_ctx_t ctx, chnss_system sys, double *host_out) {

@@ -183,6 +183,20 @@ void cgs2_update_dots(long n, const double *V, long ld, int k, const double *h1,
 void cgs2_update_scale(long n, const double *V, long ld, int k, const double *h2, const double *w, const double *hn,
                        double *vout, cudaStream_t s);
 
+// The same three CGS2 passes in double-FP32 arithmetic (values as pairs of
+// FP32 numbers, about 48 significant bits), reading the basis from V2, its
+// pair copy; w enters pass 1 and 2 in FP64, pass 2 leaves it in place as
+// pairs, pass 3 reads those pairs and writes the next basis vector both as
+// pairs (vout2) and as their exact FP64 values (vout64).  k <= 31.
+void dfgs_dots(long n, const float2 *V2, long ld, int k, const double *w, double *h1, double *partial,
+               cudaStream_t s);
+void dfgs_update_dots(long n, const float2 *V2, long ld, int k, const double *h1, double *w, double *h2w,
+                      double *partial, cudaStream_t s);
+void dfgs_update_scale(long n, const float2 *V2, long ld, int k, const double *h2, const double *w,
+                       const double *hn, float2 *vout2, double *vout64, cudaStream_t s);
+// first basis vector w / *hn as pairs and as their FP64 values
+void dfgs_first(long n, const double *w, const double *hn, float2 *vout2, double *vout64, cudaStream_t s);
+
 // Arnoldi bookkeeping on one thread: H(:, j) = h1 + h2, H(j+1, j) = sqrt(nrm2),
 // previous Givens rotations, new rotation, g update.  Writes to status:
 // [0] |g_{j+1}|, [1] H(j+1, j).

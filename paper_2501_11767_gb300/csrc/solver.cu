@@ -632,11 +632,12 @@ template struct MGBatch<double>;
 template struct MGBatch<float>;
 
 // ---------------------------------------------------------------------------
-void KrylovWork::init(Arena &ar, int m_, long nmax_, double *pinned) {
+void KrylovWork::init(Arena &ar, int m_, long nmax_, double *pinned, bool pairs) {
   m = m_;
   nmax = nmax_;
   const long ldmax = (nmax + 31) / 32 * 32;   // basis stride: 256-byte aligned vectors
   V = ar.alloc<double>((long)(m + 1) * ldmax);
+  if (pairs && cgs2_fast(m)) V2 = ar.alloc<float2>((long)(m + 1) * ldmax);
   Z = ar.alloc<double>((long)m * ldmax);
   w = ar.alloc<double>(nmax);
   H = ar.alloc<double>((long)(m + 1) * m);
@@ -683,7 +684,10 @@ chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, 
     vec_copy(n, b, ws.w, s);
     set_scalar(sc + 2, sc, 1.0, true, s);   // sc[2] = ||r||
     while (true) {
-      vec_scale_by_inv(n, ws.w, sc + 2, ws.V, s);
+      if (ws.V2)
+        dfgs_first(n, ws.w, sc + 2, ws.V2, ws.V, s);
+      else
+        vec_scale_by_inv(n, ws.w, sc + 2, ws.V, s);
       vec_fill(m + 1, 0.0, ws.g, s);
       set_scalar(ws.g, sc + 2, 1.0, false, s);
       int k = 0;
@@ -696,7 +700,13 @@ chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, 
         const int kv = j + 1;
         const bool fast = cgs2_fast(kv);
         const int tko = prof ? prof->start(Profiler::ORTHO, s) : -1;
-        if (fast) {
+        if (ws.V2) {
+          // the same passes in double-FP32 arithmetic (same bytes, no FP64 FMAs)
+          dfgs_dots(n, ws.V2, ld, kv, ws.w, ws.h1, ws.partial, s);
+          dfgs_update_dots(n, ws.V2, ld, kv, ws.h1, ws.w, ws.h2, ws.partial, s);
+          if (prof) prof->stop(Profiler::ORTHO, tko, s, 8.0 * n * (2.0 * kv + 3.0), 0.0);
+          arnoldi_finish_pyth(j, ldh, ws.H, ws.h1, ws.h2, ws.cs, ws.sn, ws.g, sc + 4, s);
+        } else if (fast) {
           // CGS2 passes 1-2: h1 = V^T w; w -= V h1, h2 = V^T w and ||w||^2 in
           // one sweep (V read twice, w read twice and written once; 3k+1 FMAs
           // per element).  Pass 3 forms the next basis vector after the sync.
@@ -724,7 +734,13 @@ chnss_status fgmres(LinearOperator &A, const double *b, double *x, double rtol, 
           break;
         }
         breakdown = hn == 0.0;
-        if (!breakdown && fast) {
+        if (!breakdown && ws.V2) {
+          // pass 3 in pairs: V read once, w (pairs) read once, V_{j+1} written as pairs and FP64
+          const int tk3 = prof ? prof->start(Profiler::ORTHO, s) : -1;
+          dfgs_update_scale(n, ws.V2, ld, kv, ws.h2, ws.w, sc + 5, ws.V2 + (long)(j + 1) * ld,
+                            ws.V + (long)(j + 1) * ld, s);
+          if (prof) prof->stop(Profiler::ORTHO, tk3, s, 8.0 * n * (kv + 3.0), 0.0, 0);
+        } else if (!breakdown && fast) {
           // pass 3: V_{j+1} = (w - V h2) / hn (V read once, w read once, V_{j+1} written; k FMAs)
           const int tk3 = prof ? prof->start(Profiler::ORTHO, s) : -1;
           cgs2_update_scale(n, ws.V, ld, kv, ws.h2, ws.w, sc + 5, ws.V + (long)(j + 1) * ld, s);
@@ -811,7 +827,10 @@ chnss_status fgmres_batch(int K, LinearOperator *const *A, const double *const *
       zout[q] = nullptr;
       if (r.done) continue;
       if (r.cycle_start) {
-        vec_scale_by_inv(r.n, w.w, w.sc + 2, w.V, s);
+        if (w.V2)
+          dfgs_first(r.n, w.w, w.sc + 2, w.V2, w.V, s);
+        else
+          vec_scale_by_inv(r.n, w.w, w.sc + 2, w.V, s);
         vec_fill(r.m + 1, 0.0, w.g, s);
         set_scalar(w.g, w.sc + 2, 1.0, false, s);
         r.j = 0;
@@ -834,7 +853,12 @@ chnss_status fgmres_batch(int K, LinearOperator *const *A, const double *const *
       const int kv = r.j + 1;
       r.fast = cgs2_fast(kv);
       const int tko = prof ? prof->start(Profiler::ORTHO, s) : -1;
-      if (r.fast) {
+      if (w.V2) {
+        dfgs_dots(n, w.V2, ld, kv, w.w, w.h1, w.partial, s);
+        dfgs_update_dots(n, w.V2, ld, kv, w.h1, w.w, w.h2, w.partial, s);
+        if (prof) prof->stop(Profiler::ORTHO, tko, s, 8.0 * n * (2.0 * kv + 3.0), 0.0);
+        arnoldi_finish_pyth(r.j, r.ldh, w.H, w.h1, w.h2, w.cs, w.sn, w.g, sc + 4, s);
+      } else if (r.fast) {
         cgs2_dots(n, w.V, ld, kv, w.w, w.h1, w.partial, s);
         cgs2_update_dots(n, w.V, ld, kv, w.h1, w.w, w.h2, w.partial, s);
         if (prof) prof->stop(Profiler::ORTHO, tko, s, 8.0 * n * (2.0 * kv + 3.0), 2.0 * n * (3.0 * kv + 1.0));
@@ -866,7 +890,12 @@ chnss_status fgmres_batch(int K, LinearOperator *const *A, const double *const *
         continue;
       }
       r.breakdown = hn == 0.0;
-      if (!r.breakdown && r.fast) {
+      if (!r.breakdown && w.V2) {
+        const int tk3 = prof ? prof->start(Profiler::ORTHO, s) : -1;
+        dfgs_update_scale(r.n, w.V2, r.ld, r.k, w.h2, w.w, w.sc + 5, w.V2 + (long)(r.j + 1) * r.ld,
+                          w.V + (long)(r.j + 1) * r.ld, s);
+        if (prof) prof->stop(Profiler::ORTHO, tk3, s, 8.0 * r.n * (r.k + 3.0), 0.0, 0);
+      } else if (!r.breakdown && r.fast) {
         const int tk3 = prof ? prof->start(Profiler::ORTHO, s) : -1;
         cgs2_update_scale(r.n, w.V, r.ld, r.k, w.h2, w.w, w.sc + 5, w.V + (long)(r.j + 1) * r.ld, s);
         if (prof) prof->stop(Profiler::ORTHO, tk3, s, 8.0 * r.n * (r.k + 2.0), 2.0 * r.n * r.k, 0);

@@ -174,7 +174,11 @@ struct KrylovWork {
   double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
   double *h1 = nullptr, *h2 = nullptr, *sc = nullptr, *partial = nullptr;
   double *hstat = nullptr;   // pinned host, 4 doubles
-  void init(Arena &ar, int m, long nmax, double *pinned);
+  // double-FP32 Gram-Schmidt (params.ortho = 1, restart <= 31): the basis
+  // also as pairs of FP32 numbers, read by the Gram-Schmidt passes; V keeps
+  // each vector's exact FP64 value for the preconditioner
+  float2 *V2 = nullptr;
+  void init(Arena &ar, int m, long nmax, double *pinned, bool pairs = false);
 };
 
 // Right-preconditioned FGMRES(m), CGS2, Givens, x0 = 0; stop when the true

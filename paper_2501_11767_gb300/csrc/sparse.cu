@@ -1204,6 +1204,148 @@ __global__ void __launch_bounds__(kCgsBlock) k_cgs_update_scale(long n, const do
   out[i] = (w[i] - (s0 + s1)) * inv;
 }
 
+// ---------------------------------------------------------------------------
+// CGS2 in double-FP32 arithmetic.  A value is carried as the unevaluated sum
+// h + l of two FP32 numbers (h = the value rounded to FP32, l = the rest
+// rounded to FP32: about 48 significant bits).  The exact product of two
+// FP32 numbers is p + e with e = fma(a, b, -p) (Dekker's two-product,
+// "A floating-point technique for extending the available precision",
+// 1971); the exact sum is s + t with Knuth's two-sum (TAOCP vol. 2,
+// 4.2.2).  One FP64 multiply-add of the Gram-Schmidt passes becomes about
+// eleven FP32 operations, on a pipe 64 times wider than this part's FP64
+// pipe, so the passes are bound by their memory traffic instead of by FP64
+// arithmetic.  Every step of the error-free transformations uses the _rn
+// intrinsics, which the compiler never contracts into FMAs.
+__device__ __forceinline__ float2 df_split(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(__dsub_rn(x, (double)h)));
+}
+__device__ __forceinline__ double df_join(float2 a) { return __dadd_rn((double)a.x, (double)a.y); }
+// (s, t) with s + t = a + b exactly, |b| <= |a| not required
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return make_float2(s, t);
+}
+// (s, t) with s + t = a + b exactly when |a| >= |b|
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+// acc += a * b; acc is kept unnormalised (acc.x the running leading sum,
+// acc.y the collected rounding errors and low-order products; a.y * b.y,
+// of relative size 2^-48, is dropped)
+__device__ __forceinline__ void df_mac(float2 &acc, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float2 st = two_sum(acc.x, p);
+  acc.x = st.x;
+  acc.y = __fadd_rn(acc.y, __fadd_rn(st.y, e));
+}
+// normalised a - b
+__device__ __forceinline__ float2 df_sub(float2 a, float2 b) {
+  const float2 st = two_sum(a.x, -b.x);
+  return fast_two_sum(st.x, __fadd_rn(st.y, __fsub_rn(a.y, b.y)));
+}
+// normalised a * b
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  return fast_two_sum(p, e);
+}
+
+// pass 1: h = V^T w over KC vectors (partials); V in pairs, w in FP64
+template <int KC>
+__global__ void __launch_bounds__(kCgsBlock) k_dfgs_dots(long n, const float2 *__restrict__ V, long ld,
+                                                         const double *__restrict__ w,
+                                                         double *__restrict__ partial) {
+  float2 acc[KC];
+#pragma unroll
+  for (int j = 0; j < KC; ++j) acc[j] = make_float2(0.f, 0.f);
+  for (long i = (long)blockIdx.x * kCgsBlock + threadIdx.x; i < n; i += (long)gridDim.x * kCgsBlock) {
+    const float2 wi = df_split(w[i]);
+#pragma unroll
+    for (int j = 0; j < KC; ++j) df_mac(acc[j], V[(long)j * ld + i], wi);
+  }
+  double a[pow2_at_least(KC)];
+#pragma unroll
+  for (int j = 0; j < pow2_at_least(KC); ++j) a[j] = j < KC ? df_join(acc[j]) : 0.0;
+  cgs_block_reduce<KC>(a, partial);
+}
+
+// pass 2: w -= V h (w read in FP64, written back in place as pairs); then
+// partials of V^T w (KC values) and w^T w (one more)
+template <int KC>
+__global__ void __launch_bounds__(kCgsBlock) k_dfgs_update_dots(long n, const float2 *__restrict__ V, long ld,
+                                                                const double *__restrict__ h, double *w,
+                                                                double *__restrict__ partial) {
+  __shared__ float2 hs[KC];
+  if (threadIdx.x < KC) hs[threadIdx.x] = df_split(h[threadIdx.x]);
+  __syncthreads();
+  float2 acc[KC + 1];
+#pragma unroll
+  for (int j = 0; j <= KC; ++j) acc[j] = make_float2(0.f, 0.f);
+  float2 *w2 = reinterpret_cast<float2 *>(w);
+  for (long i = (long)blockIdx.x * kCgsBlock + threadIdx.x; i < n; i += (long)gridDim.x * kCgsBlock) {
+    float2 v[KC];
+#pragma unroll
+    for (int j = 0; j < KC; ++j) v[j] = V[(long)j * ld + i];
+    float2 sv = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < KC; ++j) df_mac(sv, v[j], hs[j]);
+    const float2 wi = df_sub(df_split(w[i]), sv);
+    w2[i] = wi;
+#pragma unroll
+    for (int j = 0; j < KC; ++j) df_mac(acc[j], v[j], wi);
+    df_mac(acc[KC], wi, wi);
+  }
+  double a[pow2_at_least(KC + 1)];
+#pragma unroll
+  for (int j = 0; j < pow2_at_least(KC + 1); ++j) a[j] = j <= KC ? df_join(acc[j]) : 0.0;
+  cgs_block_reduce<KC + 1>(a, partial);
+}
+
+// pass 3: the next basis vector (w - V h) / hn, from w in pairs; written in
+// pairs (for the Gram-Schmidt passes) and in FP64 (for the preconditioner),
+// the FP64 copy being the exact value of the pair
+template <int KC>
+__global__ void __launch_bounds__(kCgsBlock) k_dfgs_update_scale(long n, const float2 *__restrict__ V, long ld,
+                                                                 const double *__restrict__ h,
+                                                                 const float2 *__restrict__ w,
+                                                                 const double *__restrict__ hn,
+                                                                 float2 *__restrict__ out2,
+                                                                 double *__restrict__ out64) {
+  __shared__ float2 hs[KC];
+  __shared__ float2 inv;
+  if (threadIdx.x < KC) hs[threadIdx.x] = df_split(h[threadIdx.x]);
+  if (threadIdx.x == 0) inv = df_split(1.0 / *hn);
+  __syncthreads();
+  const long i = (long)blockIdx.x * kCgsBlock + threadIdx.x;
+  if (i >= n) return;
+  float2 sv = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < KC; ++j) df_mac(sv, V[(long)j * ld + i], hs[j]);
+  const float2 r = df_mul(df_sub(w[i], sv), inv);
+  out2[i] = r;
+  out64[i] = df_join(r);
+}
+
+// the first basis vector: x = w / hn in FP64, kept as its pair and as the
+// pair's exact FP64 value
+__global__ void k_df_first(long n, const double *__restrict__ w, const double *__restrict__ hn,
+                           float2 *__restrict__ out2, double *__restrict__ out64) {
+  const long i = (long)blockIdx.x * kCgsBlock + threadIdx.x;
+  if (i >= n) return;
+  const float2 r = df_split(w[i] / *hn);
+  out2[i] = r;
+  out64[i] = df_join(r);
+}
+
 }  // namespace
 
 // ============================================================================
@@ -1649,6 +1791,78 @@ void cgs2_update_scale(long n, const double *V, long ld, int k, const double *h2
                        double *vout, cudaStream_t s) {
   cgs_dispatch(k, 3, n, V, ld, h2, w, nullptr, hn, vout, nullptr, s);
 }
+namespace {
+// passes 1 and 2 stream KC + 1 vectors with few operations per load: every
+// block the registers allow stays resident (capped by the partial buffers)
+template <int KC, int PASS>
+int dfgs_blocks(long n) {
+  static const int occ = [] {
+    int o = 0;
+    const void *f = PASS == 1 ? (const void *)k_dfgs_dots<KC> : (const void *)k_dfgs_update_dots<KC>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, f, kCgsBlock, 0);
+    cudaGetLastError();
+    return o;
+  }();
+  const int sms = device_sm_count();
+  const int cap = std::max(kCgsBlocksPerSm * sms, std::min(sms * occ, std::min(8 * sms, kReduceMaxBlocks)));
+  const long b = (n + kCgsBlock - 1) / kCgsBlock;
+  return (int)std::max(1L, std::min(b, (long)cap));
+}
+
+template <int KC>
+void dfgs_pass(int pass, long n, const float2 *V, long ld, const double *h, double *w, const double *hn,
+               double *out, float2 *out2, double *partial, cudaStream_t s) {
+  if (pass == 1) {
+    const int nb = dfgs_blocks<KC, 1>(n);
+    k_dfgs_dots<KC><<<nb, kCgsBlock, 0, s>>>(n, V, ld, w, partial);
+    CHNSS_LAUNCH_CK();
+    k_sum_final<<<KC, TPB, 0, s>>>(nb, KC, partial, out);
+  } else if (pass == 2) {
+    const int nb = dfgs_blocks<KC, 2>(n);
+    k_dfgs_update_dots<KC><<<nb, kCgsBlock, 0, s>>>(n, V, ld, h, w, partial);
+    CHNSS_LAUNCH_CK();
+    k_sum_final<<<KC + 1, TPB, 0, s>>>(nb, KC + 1, partial, out);
+  } else {
+    k_dfgs_update_scale<KC><<<nblocks(n, kCgsBlock), kCgsBlock, 0, s>>>(
+        n, V, ld, h, reinterpret_cast<const float2 *>(w), hn, out2, out);
+  }
+  CHNSS_LAUNCH_CK();
+}
+void dfgs_dispatch(int k, int pass, long n, const float2 *V, long ld, const double *h, double *w, const double *hn,
+                   double *out, float2 *out2, double *partial, cudaStream_t s) {
+  switch (k) {
+#define CHNSS_DFGS_CASE(K) \
+  case K: dfgs_pass<K>(pass, n, V, ld, h, w, hn, out, out2, partial, s); break;
+    CHNSS_DFGS_CASE(1) CHNSS_DFGS_CASE(2) CHNSS_DFGS_CASE(3) CHNSS_DFGS_CASE(4) CHNSS_DFGS_CASE(5)
+    CHNSS_DFGS_CASE(6) CHNSS_DFGS_CASE(7) CHNSS_DFGS_CASE(8) CHNSS_DFGS_CASE(9) CHNSS_DFGS_CASE(10)
+    CHNSS_DFGS_CASE(11) CHNSS_DFGS_CASE(12) CHNSS_DFGS_CASE(13) CHNSS_DFGS_CASE(14) CHNSS_DFGS_CASE(15)
+    CHNSS_DFGS_CASE(16) CHNSS_DFGS_CASE(17) CHNSS_DFGS_CASE(18) CHNSS_DFGS_CASE(19) CHNSS_DFGS_CASE(20)
+    CHNSS_DFGS_CASE(21) CHNSS_DFGS_CASE(22) CHNSS_DFGS_CASE(23) CHNSS_DFGS_CASE(24) CHNSS_DFGS_CASE(25)
+    CHNSS_DFGS_CASE(26) CHNSS_DFGS_CASE(27) CHNSS_DFGS_CASE(28) CHNSS_DFGS_CASE(29) CHNSS_DFGS_CASE(30)
+    CHNSS_DFGS_CASE(31)
+#undef CHNSS_DFGS_CASE
+    default: throw Error{CHNSS_ERR_ARG, "double-FP32 Gram-Schmidt: k must be in [1, 31]"};
+  }
+}
+}  // namespace
+
+void dfgs_dots(long n, const float2 *V, long ld, int k, const double *w, double *h1, double *partial,
+               cudaStream_t s) {
+  dfgs_dispatch(k, 1, n, V, ld, nullptr, const_cast<double *>(w), nullptr, h1, nullptr, partial, s);
+}
+void dfgs_update_dots(long n, const float2 *V, long ld, int k, const double *h1, double *w, double *h2w,
+                      double *partial, cudaStream_t s) {
+  dfgs_dispatch(k, 2, n, V, ld, h1, w, nullptr, h2w, nullptr, partial, s);
+}
+void dfgs_update_scale(long n, const float2 *V, long ld, int k, const double *h2, const double *w,
+                       const double *hn, float2 *vout2, double *vout64, cudaStream_t s) {
+  dfgs_dispatch(k, 3, n, V, ld, h2, const_cast<double *>(w), hn, vout64, vout2, nullptr, s);
+}
+void dfgs_first(long n, const double *w, const double *hn, float2 *vout2, double *vout64, cudaStream_t s) {
+  k_df_first<<<nblocks(n, kCgsBlock), kCgsBlock, 0, s>>>(n, w, hn, vout2, vout64);
+  CHNSS_LAUNCH_CK();
+}
+
 void hessenberg_solve(int k, int ldh, const double *H, const double *g, double *y, cudaStream_t s) {
   k_hessenberg_solve<<<1, 1, 0, s>>>(k, ldh, H, g, y);
   CHNSS_LAUNCH_CK();

@@ -1054,9 +1054,9 @@ void create3(chnss3_ctx *c, int n) {
   c->partial = ar.alloc<double>(64L * kReduceMaxBlocks);
   c->sum = ar.alloc<double>(4);
   CHNSS_CK(cudaHostAlloc(&c->pinned, 32 * sizeof(double), cudaHostAllocDefault));
-  c->kw.init(ar, p.restart, nv + N1, c->pinned);
-  c->kwc.init(ar, p.restart, 2 * N1, c->pinned + 8);
-  c->kwa.init(ar, p.restart, N1, c->pinned + 16);
+  c->kw.init(ar, p.restart, nv + N1, c->pinned, p.ortho == 1);
+  c->kwc.init(ar, p.restart, 2 * N1, c->pinned + 8, p.ortho == 1);
+  c->kwa.init(ar, p.restart, N1, c->pinned + 16, p.ortho == 1);
   // Chebyshev coefficients of M_p^-1 (degree 5 on D^-1 M over [1/2, 5/2])
   {
     const double theta = 0.5 * (kMassHi3 + kMassLo3), delta = 0.5 * (kMassHi3 - kMassLo3), sigma = theta / delta;
@@ -1468,6 +1468,7 @@ extern "C" chnss_status chnss3_ctx_create_ex(int n, int top_bc, const chnss_para
     if (p.inner_rtol > 0.0 && (p.inner_maxit < 1 || p.inner_maxit > 1000))
       throw Error{CHNSS_ERR_ARG, "inner_maxit must be in [1, 1000]"};
     if (p.mobility_kind != 0 && p.mobility_kind != 1) throw Error{CHNSS_ERR_ARG, "mobility_kind must be 0 or 1"};
+    if (p.ortho != 0 && p.ortho != 1) throw Error{CHNSS_ERR_ARG, "ortho must be 0 (FP64) or 1 (double-FP32)"};
     if (!(p.tau > 0) || !(p.eta > 0) || p.restart < 1 || p.restart > 64 || p.maxit < 1)
       throw Error{CHNSS_ERR_ARG, "invalid parameters"};
     for (int i = 0; i < 3; ++i)

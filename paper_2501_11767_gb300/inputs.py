@@ -147,6 +147,8 @@ def default_params() -> dict:
         # Oseen stopping rule of its own when ns_rtol > 0 (0: rtol, atol)
         "ns_rtol": 0.0,
         "ns_atol": 0.0,
+        # Gram-Schmidt arithmetic of FGMRES: 0 FP64, 1 double-FP32 (pairs of FP32)
+        "ortho": 0,
     }
 
 
@@ -194,24 +196,24 @@ def workload(name: str) -> dict:
         p.update(beta=film_betas(0.01), mobility_kind=1)
         return {"n": 256, "params": p, "steps": 20}
     if name == "film1024_mixed":
-        p.update(beta=film_betas(0.005), tau=5e-4, precision=1)
+        p.update(beta=film_betas(0.005), tau=5e-4, precision=1, ortho=1)
         return {"n": 1024, "params": p, "steps": 10}
     if name == "film512_mixed":      # the same parameters on 512 x 512 (profiling captures)
-        p.update(beta=film_betas(0.005), tau=5e-4, precision=1)
+        p.update(beta=film_betas(0.005), tau=5e-4, precision=1, ortho=1)
         return {"n": 512, "params": p, "steps": 10}
     if name == "film1024_mixed_inner":   # the bench set with every MG block solved to 1e-4 (Sec. 5)
-        p.update(beta=film_betas(0.005), tau=5e-4, precision=1, inner_rtol=1e-4, inner_maxit=20)
+        p.update(beta=film_betas(0.005), tau=5e-4, precision=1, inner_rtol=1e-4, inner_maxit=20, ortho=1)
         return {"n": 1024, "params": p, "steps": 10}
     if name == "film1024_paper_solver":   # the bench film with the solver settings of Sec. 5
         p.update(beta=film_betas(0.005), tau=5e-4, precision=1, rtol=1e-6, atol=1e-8, ns_rtol=1e-4, ns_atol=1e-8,
-                 inner_rtol=1e-4, inner_maxit=20)
+                 inner_rtol=1e-4, inner_maxit=20, ortho=1)
         return {"n": 1024, "params": p, "steps": 10}
     if name == "film512_open_mixed":      # the bench set with an open (do-nothing) top, 512 x 512
-        p.update(beta=film_betas(0.005), tau=5e-4, precision=1, top_bc=1)
+        p.update(beta=film_betas(0.005), tau=5e-4, precision=1, top_bc=1, ortho=1)
         return {"n": 512, "params": p, "steps": 10}
     if name == "solvent_air1024_mixed":   # Sec. 5.1 sub-model on the bench mesh
         p = solvent_air_params()
-        p.update(precision=1)
+        p.update(precision=1, ortho=1)
         return {"n": 1024, "params": p, "steps": 10, "init": "solvent_air"}
     raise KeyError(name)
 
@@ -231,6 +233,6 @@ def sweep_instances(count: int = 64, seed: int = 0) -> list:
     for i in range(count):
         n = SWEEP_MESHES[min(int(u[2 * i] * len(SWEEP_MESHES)), len(SWEEP_MESHES) - 1)]
         p = default_params()
-        p.update(evap_rate=0.05 + 0.45 * float(u[2 * i + 1]), precision=1)
+        p.update(evap_rate=0.05 + 0.45 * float(u[2 * i + 1]), precision=1, ortho=1)
         out.append({"n": n, "params": p, "seed": 1000 + i})
     return out
