@@ -604,13 +604,17 @@ def run_three_d(args):
 
 
 def run_sweep(args):
-    """Batched parameter sweep: independent instances of uneven mesh size
-    and evaporation rate, one context (and stream) each, advanced together
-    by chnss_step_batched after the SpMV launch shapes of every mesh have
-    been autotuned.  Also times the same instances stepped one after the
-    other (one chnss_step at a time) for comparison.  Under torchrun the
-    instances are sharded round-robin over the ranks (weak scaling of the
-    per-rank batch is not kept: the sweep is fixed, so this is strong)."""
+    """Batched parameter sweep (the 64-instance workload): independent
+    instances of uneven mesh size and evaporation rate, one context (and
+    stream) each, FP32 preconditioners inside FP64 FGMRES with double-FP32
+    Gram-Schmidt.  Headline: every instance step one recorded CUDA graph
+    (chnss_set_step_mode 1), all instances launched by chnss_step_batched
+    from one thread, args.sweep_steps steps each.  Beside it: the same batch
+    host-driven (worker threads, one synchronisation per Krylov iteration),
+    and the instances' FP64 steps one instance at a time.  Under torchrun the
+    instances are sharded round-robin over the ranks (a fixed sweep: strong
+    scaling)."""
+    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -637,51 +641,82 @@ def run_sweep(args):
         c.step(chnss.state_to_device(inputs.initial_state(n, seed=0)))
         tuning[n] = c.autotune()
         del c
-    ctxs = [chnss.Context(meshes[i["n"]], i["params"], stream=torch.cuda.Stream()) for i in inst]
-    if not args.sweep_concurrent_steps:  # instances overlap already: serial steps measured faster
-        for c in ctxs:
-            c.set_step_concurrency(False)
-    a = [chnss.state_to_device(inputs.initial_state(i["n"], seed=i["seed"])) for i in inst]
-    b = [c.new_state() for c in ctxs]
     threads = args.sweep_threads or min(16, os.cpu_count() or 1)
-    for _ in range(args.warmup):
-        chnss.step_batched(ctxs, a, b, max_threads=threads)
-        a, b = b, a
-    torch.cuda.synchronize()
-    launches0 = ctxs[0].profile_read()["launches"]
-    sampler = ClockSampler(_device_uuid(torch, local))
-    barrier()
-    sampler.start()
-    t0 = time.perf_counter()
-    recs = None
-    for _ in range(args.steps):
-        _, recs, _ = chnss.step_batched(ctxs, a, b, max_threads=threads)
-        a, b = b, a
-    torch.cuda.synchronize()
-    sec = time.perf_counter() - t0
-    barrier()
-    clocks = sampler.stop()
-    launches = ctxs[0].profile_read()["launches"] - launches0
-    if world > 1:
-        t = torch.tensor([sec], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec = float(t.item())
-    value = len(all_inst) * args.steps / sec
 
-    # the same instances one at a time (one step each)
+    def make(mode, params_of=lambda i: i["params"]):
+        ctxs = [chnss.Context(meshes[i["n"]], params_of(i), stream=torch.cuda.Stream()) for i in inst]
+        for c in ctxs:
+            c.set_step_mode(mode)
+            if mode == 0 and not args.sweep_concurrent_steps:
+                c.set_step_concurrency(False)   # host-driven: the instances overlap already
+        a = [chnss.state_to_device(inputs.initial_state(i["n"], seed=i["seed"])) for i in inst]
+        b = [c.new_state() for c in ctxs]
+        return ctxs, a, b
+
+    def timed_sweep(mode, steps, warmup):
+        ctxs, a, b = make(mode)
+        t_rec = time.perf_counter()
+        for _ in range(warmup):                 # the first two steps record the ping-pong graphs
+            chnss.step_batched(ctxs, a, b, max_threads=threads)
+            a, b = b, a
+        torch.cuda.synchronize()
+        t_rec = time.perf_counter() - t_rec
+        launches0 = ctxs[0].profile_read()["launches"]
+        sampler = ClockSampler(_device_uuid(torch, local))
+        barrier()
+        sampler.start()
+        t0 = time.perf_counter()
+        recs, iters = None, []
+        for _ in range(steps):
+            _, recs, _ = chnss.step_batched(ctxs, a, b, max_threads=threads)
+            iters.append(recs)
+            a, b = b, a
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        barrier()
+        clocks = sampler.stop()
+        launches = ctxs[0].profile_read()["launches"] - launches0
+        if world > 1:
+            t = torch.tensor([sec], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            sec = float(t.item())
+        conv = all(r[k]["converged"] for rs in iters for r in rs for k in r)
+        mean = {k: round(sum(r[k]["iters"] for rs in iters for r in rs) / (len(iters) * len(rs)), 2) for k in recs[0]}
+        final = [chnss.state_to_numpy(x) for x in a]
+        del ctxs, a, b
+        return sec, clocks, launches, conv, mean, t_rec, final
+
+    sec_g, clocks, launches, conv_g, iters_g, rec_g, fin_g = timed_sweep(1, args.sweep_steps, args.warmup)
+    value = len(all_inst) * args.sweep_steps / sec_g
+    host = None
+    if args.sweep_host_steps > 0:
+        sec_h, _, _, conv_h, iters_h, _, fin_h = timed_sweep(0, args.sweep_host_steps, args.warmup)
+        host = {"value": round(len(all_inst) * args.sweep_host_steps / sec_h, 3), "unit": "instance steps/s",
+                "steps": args.sweep_host_steps, "converged": conv_h, "iters_mean": iters_h,
+                "how": "the same batch with host-driven Krylov loops: chnss_step_batched on "
+                       f"{threads} worker threads, serial solve groups inside each instance"}
+        if args.sweep_host_steps == args.sweep_steps:
+            host["equal_final_states"] = all(all(np.array_equal(x[k], y[k]) for k in x) for x, y in zip(fin_g, fin_h))
+
+    # the FP64 step of every instance, one instance at a time (host-driven)
+    ctx64, a64, b64 = make(0, lambda i: dict(i["params"], precision=0, ortho=0))
+    for c, x, y in zip(ctx64, a64, b64):       # one warm-up step each
+        c.step(x, y)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for c, x, y in zip(ctxs, a, b):
+    for c, x, y in zip(ctx64, b64, a64):
         c.step(x, y)
         c.stream.synchronize()
-    seq = len(inst) / (time.perf_counter() - t0)
+    seq64 = len(inst) / (time.perf_counter() - t0)
+    del ctx64, a64, b64
     if rank != 0:
-        dist.destroy_process_group()
+        if world > 1:
+            dist.destroy_process_group()
         return
 
     out = {
         "metric": SWEEP_METRIC, "value": round(value, 3), "unit": "instance steps/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec / args.steps * 1e3, 3),
+        "steps": args.sweep_steps, "warmup": args.warmup, "ms_per_step": round(sec_g / args.sweep_steps * 1e3, 3),
         "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
         "dtype": "f64 outer / f32 preconditioner", "data": "synthetic (seeded SplitMix64 draws)",
         "config": {"workload": f"sweep{len(all_inst)}", "instances": len(all_inst),
@@ -691,17 +726,21 @@ def run_sweep(args):
                    "total_p1_nodes": sum((i["n"] + 1) ** 2 for i in all_inst),
                    "evap_rate": [round(min(i["params"]["evap_rate"] for i in all_inst), 4),
                                  round(max(i["params"]["evap_rate"] for i in all_inst), 4)],
-                   "host_threads": threads, "serial_steps": not args.sweep_concurrent_steps,
+                   "step": "one recorded CUDA graph per instance step (Krylov loops as conditional nodes)",
+                   "gram_schmidt": "double-FP32",
                    "l2": "inputs larger than L2 (tens of GB resident)",
                    "timing": "wall clock around chnss_step_batched (it returns after every stream is synchronised)"},
+        "graph_recording_s": round(rec_g, 2),
         "tuning": {str(n): {"block_p1": t["block_p1"], "block_p2": t["block_p2"],
                             "ms_p1": [round(x, 4) for x in t["ms_p1"]], "ms_p2": [round(x, 4) for x in t["ms_p2"]]}
                    for n, t in tuning.items()},
-        "sequential": {"value": round(seq, 3), "unit": "instance steps/s",
-                       "how": "rank 0: one chnss_step per instance, one after the other, same contexts"},
-        "speedup_batched_vs_sequential": round(value / world / seq, 3),
-        "converged": all(r[k]["converged"] for r in recs for k in r),
-        "iters_mean": {k: round(sum(r[k]["iters"] for r in recs) / len(recs), 2) for k in recs[0]},
+        "host_driven_batch": host,
+        "fp64_one_at_a_time": {"value": round(seq64, 3), "unit": "instance steps/s",
+                               "how": "rank 0: the FP64 step (FP64 Gram-Schmidt) of each instance, one after the "
+                                      "other, host-driven"},
+        "speedup_vs_fp64_one_at_a_time": round(value / world / seq64, 3),
+        "converged": conv_g,
+        "iters_mean": iters_g,
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -792,6 +831,9 @@ def main():
     ap.add_argument("--sweep-count", type=int, default=64)
     ap.add_argument("--sweep-threads", type=int, default=0)
     ap.add_argument("--sweep-concurrent-steps", action="store_true")
+    ap.add_argument("--sweep-steps", type=int, default=50, help="steps of every instance in the timed sweep")
+    ap.add_argument("--sweep-host-steps", type=int, default=5,
+                    help="steps of the host-driven comparison batch (0: skip)")
     ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-steps", type=int, default=1, help=argparse.SUPPRESS)
     args = ap.parse_args()

@@ -449,6 +449,27 @@ chnss_status chnss_mass_solve_noalloc(chnss_ctx_t ctx, const double *rhs, double
 chnss_status chnss_step_batched(int n_inst, chnss_ctx_t *ctxs, const chnss_state *in, chnss_state *out,
                                 chnss_solve_info *info, int max_threads);
 
+/* How chnss_step (and chnss_step_host, chnss_step_batched) run a step.
+ * mode 0 (default): host-driven, the Krylov loops decide on the host after
+ * reading each iteration's residual estimate (one synchronisation per
+ * iteration).  mode 1: the whole step as one CUDA graph launch with no host
+ * synchronisation inside: every FGMRES restart cycle a conditional WHILE
+ * node, every Arnoldi step a conditional IF node, every stopping decision a
+ * one-thread kernel, the PCG iterations a WHILE node; the three solve groups
+ * (Sec. 3: all coefficients at t_k) run as parallel graph branches, the
+ * three CH species one after the other.  Same kernels, arithmetic and
+ * stopping rules as mode 0, so the states and iteration counts are equal.
+ * The graph is recorded on the first step with a given pair of state arrays
+ * (two pairs are kept, so a ping-pong of two states records twice) and
+ * replayed afterwards; it is recorded again after chnss_autotune,
+ * chnss_set_spmv_block or chnss_set_step_concurrency.  Solve records
+ * (iterations, convergence, residual, status) are returned as in mode 0
+ * once the graph has finished.  Needs restart <= 31 (CHNSS_ERR_ARG).  With
+ * every context of a chnss_step_batched call in mode 1, the batch is one
+ * graph launch per instance from the calling thread, then one
+ * synchronisation per instance stream (max_threads is ignored). */
+chnss_status chnss_set_step_mode(chnss_ctx_t ctx, int mode);
+
 /* Launch-shape autotuner.  Times the fine-level SpMV of the scalar (P1) and
  * of the velocity (2x2-block) multigrid operator of ctx for threads-per-block
  * 128, 256 and 512, keeps the fastest for each family (all levels and the

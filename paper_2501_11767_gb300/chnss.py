@@ -157,6 +157,7 @@ EXPORTS = {
     "chnss_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Tuning)]),
     "chnss_set_spmv_block": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "chnss_set_step_concurrency": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "chnss_set_step_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
 }
 
@@ -411,6 +412,11 @@ class Context:
         t = Tuning()
         _check(load().chnss_autotune(self._h, ctypes.byref(t)), self._h)
         return t.as_dict()
+
+    def set_step_mode(self, mode: int):
+        """chnss_set_step_mode: 0 host-driven Krylov loops (default), 1 the
+        whole step as one recorded CUDA graph launch."""
+        _check(load().chnss_set_step_mode(self._h, int(mode)), self._h)
 
     def set_step_concurrency(self, on: bool):
         """chnss_set_step_concurrency: solve CH, AC and NS of a step on three

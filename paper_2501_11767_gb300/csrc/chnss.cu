@@ -155,6 +155,19 @@ struct chnss_ctx {
   double *xsol[6] = {};
   double *massc = nullptr;
   double *diag = nullptr;                   // chnss_diagnostics: kDiagQuantities sums + ||B v||^2
+  // device-driven step (chnss_set_step_mode 1): a whole step captured as one
+  // CUDA graph per pair of state arrays (two pairs cached)
+  struct StepGraph {
+    std::array<const void *, 20> key{};
+    cudaGraphExec_t exec = nullptr;
+  };
+  int step_mode = 0;
+  bool recording = false;                   // preconditioners record their bodies inline
+  StepGraph sgr[2];
+  int sg_next = 0;
+  cudaStream_t rq0 = nullptr;                  // private stream the step is recorded on
+  cudaStream_t rq1 = nullptr, rq2 = nullptr;   // capture streams of the conditional bodies
+  double *srec = nullptr, *srec_h = nullptr;   // per solve [iterations, converged, rel. residual, status]
   std::unique_ptr<PrecSet<double>> p64;
   std::unique_ptr<PrecSet<float>> p32;
   // captured preconditioner graphs (0..2 CH species, 3 AC, 4 NS)
@@ -213,6 +226,12 @@ struct chnss_ctx {
       if (e) cudaEventDestroy(e);
     for (cudaStream_t q : sx)
       if (q) cudaStreamDestroy(q);
+    for (StepGraph &g : sgr)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (rq0) cudaStreamDestroy(rq0);
+    if (rq1) cudaStreamDestroy(rq1);
+    if (rq2) cudaStreamDestroy(rq2);
+    if (srec_h) cudaFreeHost(srec_h);
     if (ev_asm) cudaEventDestroy(ev_asm);
     if (ev_chac) cudaEventDestroy(ev_chac);
     for (cudaEvent_t e : ev_done)
@@ -358,7 +377,7 @@ void prec_body(chnss_ctx *c, int g, cudaStream_t s) {
 void run_prec(chnss_ctx *c, int g, const double *r, double *z, cudaStream_t s) {
   set_ptr_slots(reinterpret_cast<void **>(c->slots + 2 * g), r, z, s);
   PrecGraph &pg = c->pg[g];
-  if (!pg.plain) {
+  if (!pg.plain || c->recording) {
     prec_body(c, g, s);
     return;
   }
@@ -604,6 +623,7 @@ void create_context(chnss_ctx *c) {
   c->partial_ch = ar.alloc<double>(64L * kReduceMaxBlocks);
   c->sum = ar.alloc<double>(4);
   c->diag = ar.alloc<double>(kDiagQuantities + 1);
+  c->srec = ar.alloc<double>(24);
   const int nl = c->nlev;
   c->M1.resize(nl); c->K1.resize(nl); c->ACb.resize(nl); c->M2v.resize(nl); c->Aconst.resize(nl);
   c->L.resize(nl); c->AC.resize(nl); c->A.resize(nl); c->X1.resize(nl); c->X2.resize(nl);
@@ -946,6 +966,32 @@ bool ranges_overlap(const double *a, const double *b, long n) {
   return x < y + len && y < x + len;
 }
 
+// right-hand side of the air-potential mass solve into rhs[4]:
+// f_a + beta_a K phi_a^{k+1}, phi_a^{k+1} = 1 - sum of the new CH fractions
+void mu_a_rhs(chnss_ctx *c, double *tmp, cudaStream_t s) {
+  const int N1 = c->N1;
+  const Level &F = c->lv(0);
+  k_phi_a<<<nb(N1), TPB, 0, s>>>(N1, c->xsol[0], c->xsol[1], c->xsol[2], tmp);
+  CHNSS_LAUNCH_CK();
+  SpmvArgs none;
+  spmv_csr<double>(F.p1, c->K1[0], 1, tmp, c->rhs[4], SPMV_PLAIN, none, s);
+  vec_axpby(N1, 1.0, c->fa, c->p.beta[3], c->rhs[4], s);    // f_a + beta_a K phi_a^{k+1}
+}
+
+// enclosed flow: zero-mean pressure of the Oseen solution x = (v, p),
+// p -= (1^T M p) / (1^T M 1); an open top fixes the pressure level itself
+void ns_pressure_shift(chnss_ctx *c, double *x, double *tmp, cudaStream_t s) {
+  const Mesh &m = c->mesh->m;
+  if (m.top_bc != 0) return;
+  const int N1 = c->N1;
+  const long nv = 2L * c->N2;
+  SpmvArgs none;
+  spmv_csr<double>(c->lv(0).p1, c->M1[0], 1, x + nv, tmp, SPMV_PLAIN, none, s);
+  vsum<double>(N1, tmp, c->sum, c->partial, s);   // c->sum, c->partial: NS only during a step
+  k_shift<<<nb(N1), TPB, 0, s>>>(N1, x + nv, c->sum, m.lx * m.ly);
+  CHNSS_LAUNCH_CK();
+}
+
 chnss_status solve_on(chnss_ctx *c, int sys, const double *rhs_or_null, double *x, chnss_solve_info *info,
                       cudaStream_t s, KrylovWork &kwk, double *tmp) {
   if (!c->assembled) throw Error{CHNSS_ERR_STATE, "chnss_solve before chnss_assemble"};
@@ -965,12 +1011,7 @@ chnss_status solve_on(chnss_ctx *c, int sys, const double *rhs_or_null, double *
     if (!b) {
       if (!(c->ch_done[0] && c->ch_done[1] && c->ch_done[2]))
         throw Error{CHNSS_ERR_STATE, "MU_A needs the three CH solutions of this step"};
-      const Level &F = c->lv(0);
-      k_phi_a<<<nb(N1), TPB, 0, s>>>(N1, c->xsol[0], c->xsol[1], c->xsol[2], tmp);
-      CHNSS_LAUNCH_CK();
-      SpmvArgs none;
-      spmv_csr<double>(F.p1, c->K1[0], 1, tmp, c->rhs[4], SPMV_PLAIN, none, s);
-      vec_axpby(N1, 1.0, c->fa, p.beta[3], c->rhs[4], s);    // f_a + beta_a K phi_a^{k+1}
+      mu_a_rhs(c, tmp, s);
       b = c->rhs[4];
     }
     st = pcg(c->lv(0).p1, c->M1[0], c->dinvM, b, x, 1e-12, 1000, kwk, info, s);
@@ -980,17 +1021,7 @@ chnss_status solve_on(chnss_ctx *c, int sys, const double *rhs_or_null, double *
     // looser relative residual than the phase-field solves)
     const double rt = p.ns_rtol > 0.0 ? p.ns_rtol : p.rtol, at = p.ns_rtol > 0.0 ? p.ns_atol : p.atol;
     st = fgmres(op, rhs_or_null ? rhs_or_null : c->rhs[5], x, rt, at, p.maxit, kwk, info, s, &c->prof);
-    // enclosed flow: zero-mean pressure, p -= (1^T M p) / (1^T M 1); an open
-    // top fixes the pressure level itself
-    const Mesh &m = c->mesh->m;
-    if (m.top_bc == 0) {
-      const long nv = 2L * c->N2;
-      SpmvArgs none;
-      spmv_csr<double>(c->lv(0).p1, c->M1[0], 1, x + nv, tmp, SPMV_PLAIN, none, s);
-      vsum<double>(N1, tmp, c->sum, c->partial, s);   // c->sum, c->partial: NS only during a step
-      k_shift<<<nb(N1), TPB, 0, s>>>(N1, x + nv, c->sum, m.lx * m.ly);
-      CHNSS_LAUNCH_CK();
-    }
+    ns_pressure_shift(c, x, tmp, s);
   } else {
     throw Error{CHNSS_ERR_ARG, "unknown system"};
   }
@@ -1113,6 +1144,189 @@ chnss_status step(chnss_ctx *c, const chnss_state *in, chnss_state *out, chnss_s
   for (chnss_status x : {st[0], st[1], st[3], st[2]})
     if (x != CHNSS_OK) return x;
   return CHNSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device-driven step: the same work as step() recorded into one CUDA graph
+// (assembly, the three solve groups as parallel branches, every Krylov loop
+// a conditional node, the solve records copied to pinned memory at the end),
+// replayed with one launch.  The CH species are solved one after the other
+// (their preconditioners share the MG(M + tau C) hierarchy), each exactly as
+// its own chnss_solve, so the result equals step()'s bitwise.
+__global__ void k_rec_const(double *dst, double iters, double conv, double rel, double status) {
+  dst[0] = iters;
+  dst[1] = conv;
+  dst[2] = rel;
+  dst[3] = status;
+}
+
+std::array<const void *, 20> state_key(const chnss_state *in, const chnss_state *out) {
+  std::array<const void *, 20> k{};
+  int i = 0;
+  for (const chnss_state *st : {in, out}) {
+    for (int j = 0; j < 3; ++j) k[i++] = st->phi[j];
+    for (int j = 0; j < 4; ++j) k[i++] = st->mu[j];
+    k[i++] = st->Phi_v;
+    k[i++] = st->v;
+    k[i++] = st->p;
+  }
+  return k;
+}
+
+void record_step_body(chnss_ctx *c, const chnss_state *in, chnss_state *out) {
+  const auto &p = c->p;
+  cudaStream_t s = c->s;
+  const int N1 = c->N1;
+  const long nv = 2L * c->N2;
+  AsmLevels lv;
+  if (c->concurrent) {
+    assemble_prefix(c, in, lv, s);
+  } else {
+    assemble(c, in);
+  }
+  CHNSS_CK(cudaEventRecord(c->ev_asm, s));
+  for (cudaStream_t q : c->sx) CHNSS_CK(cudaStreamWaitEvent(q, c->ev_asm, 0));
+  // CH species and the air potential
+  {
+    cudaStream_t q = c->sx[0];
+    if (c->concurrent) {
+      assemble_chac(c, in, lv, q);
+      CHNSS_CK(cudaEventRecord(c->ev_chac, q));
+    }
+    for (int sp = 0; sp < 3; ++sp) {
+      if (p.model == 1 && sp < 2) {
+        vec_fill(2L * N1, 0.0, c->xsol[sp], q);
+        k_rec_const<<<1, 1, 0, q>>>(c->srec + 4 * sp, 0.0, 1.0, 0.0, 0.0);
+        CHNSS_LAUNCH_CK();
+        continue;
+      }
+      CHOp op(c, sp);
+      fgmres_record(op, c->rhs[sp], c->xsol[sp], p.rtol, p.atol, p.maxit, c->kwc0, q, c->rq1, c->rq2);
+      krylov_record(c->kwc0, c->srec + 4 * sp, q);
+    }
+    if (p.model == 1) vec_clip01(N1, c->xsol[2], q);      // eqn:truncateCH
+    for (int sp = 0; sp < 3; ++sp) {
+      vec_copy(N1, c->xsol[sp], out->phi[sp], q);
+      vec_copy(N1, c->xsol[sp] + N1, out->mu[sp], q);
+    }
+    mu_a_rhs(c, c->tmp, q);
+    pcg_record(c->lv(0).p1, c->M1[0], c->dinvM, c->rhs[4], out->mu[3], 1e-12, 1000, c->kwb[0], q, c->rq1);
+    krylov_record(c->kwb[0], c->srec + 16, q);
+    CHNSS_CK(cudaEventRecord(c->ev_done[0], q));
+  }
+  // Allen-Cahn
+  {
+    cudaStream_t q = c->sx[1];
+    if (c->concurrent) CHNSS_CK(cudaStreamWaitEvent(q, c->ev_chac, 0));
+    ACOp op(c);
+    fgmres_record(op, c->rhs[3], out->Phi_v, p.rtol, p.atol, p.maxit, c->kwa, q, c->rq1, c->rq2);
+    krylov_record(c->kwa, c->srec + 12, q);
+    CHNSS_CK(cudaEventRecord(c->ev_done[1], q));
+  }
+  // Navier-Stokes
+  {
+    cudaStream_t q = c->sx[2];
+    if (c->concurrent) assemble_ns(c, in, lv, q);
+    NSOp op(c);
+    const double rt = p.ns_rtol > 0.0 ? p.ns_rtol : p.rtol, at = p.ns_rtol > 0.0 ? p.ns_atol : p.atol;
+    fgmres_record(op, c->rhs[5], c->xsol[5], rt, at, p.maxit, c->kw, q, c->rq1, c->rq2);
+    krylov_record(c->kw, c->srec + 20, q);
+    ns_pressure_shift(c, c->xsol[5], c->tmp_ns, q);
+    vec_copy(nv, c->xsol[5], out->v, q);
+    vec_copy(N1, c->xsol[5] + nv, out->p, q);
+    CHNSS_CK(cudaEventRecord(c->ev_done[2], q));
+  }
+  for (cudaEvent_t e : c->ev_done) CHNSS_CK(cudaStreamWaitEvent(s, e, 0));
+  CHNSS_CK(cudaMemcpyAsync(c->srec_h, c->srec, 24 * sizeof(double), cudaMemcpyDeviceToHost, s));
+}
+
+cudaGraphExec_t step_graph_for(chnss_ctx *c, const chnss_state *in, chnss_state *out) {
+  const auto key = state_key(in, out);
+  for (auto &g : c->sgr)
+    if (g.exec && g.key == key) return g.exec;
+  if (!c->rq1) {
+    CHNSS_CK(cudaStreamCreateWithFlags(&c->rq0, cudaStreamNonBlocking));
+    CHNSS_CK(cudaStreamCreateWithFlags(&c->rq1, cudaStreamNonBlocking));
+    CHNSS_CK(cudaStreamCreateWithFlags(&c->rq2, cudaStreamNonBlocking));
+    CHNSS_CK(cudaHostAlloc(&c->srec_h, 24 * sizeof(double), cudaHostAllocDefault));
+  }
+  // record on the private stream (the context stream may be the legacy
+  // default stream, which cannot be captured); everything that uses the
+  // context stream follows it while recording
+  CHNSS_CK(cudaStreamSynchronize(c->s));
+  const bool prof_on = c->prof.on;
+  cudaStream_t user = c->s;
+  c->prof.on = false;          // no event nodes inside conditional bodies
+  c->recording = true;
+  c->s = c->rq0;
+  cudaGraph_t graph = nullptr;
+  auto restore = [&] {
+    c->s = user;
+    c->recording = false;
+    c->prof.on = prof_on;
+  };
+  try {
+    CHNSS_CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+  } catch (...) {
+    restore();
+    throw;
+  }
+  try {
+    record_step_body(c, in, out);
+  } catch (...) {
+    cudaGraph_t tmp = nullptr;
+    cudaStreamEndCapture(c->s, &tmp);
+    if (tmp) cudaGraphDestroy(tmp);
+    restore();
+    throw;
+  }
+  const cudaError_t ec = cudaStreamEndCapture(c->s, &graph);
+  restore();
+  if (ec != cudaSuccess) throw Error{CHNSS_ERR_CUDA, std::string("recording the step graph: ") + cudaGetErrorString(ec)};
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) throw Error{CHNSS_ERR_CUDA, std::string("instantiating the step graph: ") + cudaGetErrorString(e)};
+  auto &slot = c->sgr[c->sg_next];
+  c->sg_next ^= 1;
+  if (slot.exec) CHNSS_CK(cudaGraphExecDestroy(slot.exec));
+  slot.exec = exec;
+  slot.key = key;
+  return exec;
+}
+
+void step_graph_launch(chnss_ctx *c, const chnss_state *in, chnss_state *out) {
+  cudaGraphExec_t g = step_graph_for(c, in, out);
+  CHNSS_CK(cudaGraphLaunch(g, c->s));
+}
+
+// after the context stream has been synchronised: the solve records
+chnss_status step_graph_finish(chnss_ctx *c, chnss_solve_info *inf, double seconds) {
+  c->assembled = true;
+  for (bool &d : c->ch_done) d = true;
+  chnss_status st[6];
+  for (int i = 0; i < 6; ++i) {
+    const double *r = c->srec_h + 4 * i;
+    if (inf) {
+      inf[i].iters = (int)r[0];
+      inf[i].converged = r[1] != 0.0 ? 1 : 0;
+      inf[i].rel_residual = r[2];
+      inf[i].seconds = seconds;
+    }
+    st[i] = (chnss_status)(int)r[3];
+  }
+  // the first failure in the order of the sequential step: CH, AC, air potential, NS
+  for (int i : {0, 1, 2, 3, 4, 5})
+    if (st[i] != CHNSS_OK) return st[i];
+  return CHNSS_OK;
+}
+
+chnss_status step_graph(chnss_ctx *c, const chnss_state *in, chnss_state *out, chnss_solve_info *info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  step_graph_launch(c, in, out);
+  CHNSS_CK(cudaStreamSynchronize(c->s));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return step_graph_finish(c, info, secs);
 }
 
 void check_state(const chnss_state *st) {
@@ -1273,7 +1487,7 @@ chnss_status chnss_step(chnss_ctx_t ctx, const chnss_state *in, chnss_state *out
   check_state(out);
   if (in->v == out->v || in->p == out->p || in->Phi_v == out->Phi_v)
     throw Error{CHNSS_ERR_ARG, "in and out states must not alias"};
-  const chnss_status st = step(ctx, in, out, info);
+  const chnss_status st = ctx->step_mode ? step_graph(ctx, in, out, info) : step(ctx, in, out, info);
   if (st != CHNSS_OK) ctx->err = "a solve of the step did not converge cleanly (status " + std::to_string(st) + ")";
   return st;
   ABI_CATCH(ctx)
@@ -1312,7 +1526,7 @@ chnss_status chnss_step_host(chnss_ctx_t ctx, const chnss_state *hin, chnss_stat
   h2d(din.Phi_v, hin->Phi_v, N1);
   h2d(din.p, hin->p, N1);
   h2d(din.v, hin->v, nv);
-  const chnss_status st = step(ctx, &din, &dout, info);
+  const chnss_status st = ctx->step_mode ? step_graph(ctx, &din, &dout, info) : step(ctx, &din, &dout, info);
   for (int k = 0; k < 3; ++k) d2h(hout->phi[k], dout.phi[k], N1);
   for (int k = 0; k < 4; ++k) d2h(hout->mu[k], dout.mu[k], N1);
   d2h(hout->Phi_v, dout.Phi_v, N1);
@@ -1937,6 +2151,11 @@ namespace {
 constexpr int kTuneCandidates[3] = {128, 256, 512};
 
 void destroy_graphs(chnss_ctx *c) {
+  for (auto &g : c->sgr) {      // recorded steps hold copies of the preconditioner bodies
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    g.key = {};
+  }
   for (PrecGraph &g : c->pg) {
     if (g.plain) cudaGraphExecDestroy(g.plain);
     if (g.prof) cudaGraphExecDestroy(g.prof);
@@ -2045,6 +2264,16 @@ extern "C" chnss_status chnss_set_spmv_block(chnss_ctx_t ctx, int block_p1, int 
   ABI_CATCH(ctx)
 }
 
+extern "C" chnss_status chnss_set_step_mode(chnss_ctx_t ctx, int mode) {
+  if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
+  ABI_TRY
+  if (mode != 0 && mode != 1) throw Error{CHNSS_ERR_ARG, "step mode must be 0 (host-driven) or 1 (one graph)"};
+  if (mode == 1 && ctx->p.restart > 31) throw Error{CHNSS_ERR_ARG, "the one-graph step needs restart <= 31"};
+  ctx->step_mode = mode;
+  return CHNSS_OK;
+  ABI_CATCH(ctx)
+}
+
 extern "C" chnss_status chnss_set_step_concurrency(chnss_ctx_t ctx, int on) {
   if (!ctx) return fail(nullptr, CHNSS_ERR_ARG, "null context");
   ABI_TRY
@@ -2073,13 +2302,49 @@ extern "C" chnss_status chnss_step_batched(int n_inst, chnss_ctx_t *ctxs, const 
   int dev = 0;
   CHNSS_CK(cudaGetDevice(&dev));
   std::vector<chnss_status> st(n_inst, CHNSS_OK);
+  bool all_graphs = true;
+  for (int i = 0; i < n_inst; ++i) all_graphs = all_graphs && ctxs[i]->step_mode == 1;
+  if (all_graphs) {
+    // one graph launch per instance from this thread, every instance on its
+    // own stream; then one synchronisation per stream
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<bool> launched(n_inst, false);
+    for (int i = 0; i < n_inst; ++i) {
+      try {
+        step_graph_launch(ctxs[i], &in[i], &out[i]);
+        launched[i] = true;
+      } catch (const Error &e) {
+        ctxs[i]->err = e.msg;
+        st[i] = e.status;
+      }
+    }
+    for (int i = 0; i < n_inst; ++i) {
+      if (!launched[i]) continue;
+      const cudaError_t e = cudaStreamSynchronize(ctxs[i]->s);
+      if (e != cudaSuccess) {
+        ctxs[i]->err = cudaGetErrorString(e);
+        st[i] = CHNSS_ERR_CUDA;
+        continue;
+      }
+      const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      st[i] = step_graph_finish(ctxs[i], info ? info + 6L * i : nullptr, secs);
+    }
+    for (int i = 0; i < n_inst; ++i)
+      if (st[i] != CHNSS_OK) {
+        g_last_error = "instance " + std::to_string(i) + " failed with status " + std::to_string((int)st[i]) +
+                       (ctxs[i]->err.empty() ? std::string() : ": " + ctxs[i]->err);
+        return st[i];
+      }
+    return CHNSS_OK;
+  }
   std::atomic<int> next{0};
   auto worker = [&]() {
     cudaSetDevice(dev);
     for (int i = next++; i < n_inst; i = next++) {
       chnss_ctx *c = ctxs[i];
       try {
-        st[i] = step(c, &in[i], &out[i], info ? info + 6L * i : nullptr);
+        st[i] = c->step_mode ? step_graph(c, &in[i], &out[i], info ? info + 6L * i : nullptr)
+                             : step(c, &in[i], &out[i], info ? info + 6L * i : nullptr);
       } catch (const Error &e) {
         c->err = e.msg;
         st[i] = e.status;

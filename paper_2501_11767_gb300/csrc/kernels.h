@@ -206,6 +206,10 @@ void arnoldi_finish(int j, int ldh, double *H, const double *h1, const double *h
 void arnoldi_finish_pyth(int j, int ldh, double *H, const double *h1, const double *h2w, double *cs, double *sn,
                          double *g, double *status, cudaStream_t s);
 void hessenberg_solve(int k, int ldh, const double *H, const double *g, double *y, cudaStream_t s);
+// the same two steps with the column count k read from device memory
+void hessenberg_solve_dev(const int *k, int ldh, const double *H, const double *g, double *y, cudaStream_t s);
+void combine_columns_dev(long n, const double *Z, long ldz, const int *k, const double *y, double *x,
+                         cudaStream_t s);
 void set_scalar(double *dst, const double *src, double scale, bool sqrt_first, cudaStream_t s);
 // PCG scalars: alpha = rz / pq
 void pcg_alpha(const double *rz, const double *pq, double *alpha, cudaStream_t s);

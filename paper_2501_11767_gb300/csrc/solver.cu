@@ -650,6 +650,8 @@ void KrylovWork::init(Arena &ar, int m_, long nmax_, double *pinned, bool pairs)
   sc = ar.alloc<double>(8);
   partial = ar.alloc<double>(64L * kReduceMaxBlocks);
   hstat = pinned;
+  dv = ar.alloc<double>(8);
+  di = ar.alloc<int>(8);
 }
 
 namespace {
@@ -946,6 +948,258 @@ chnss_status fgmres_batch(int K, LinearOperator *const *A, const double *const *
     if (worst == CHNSS_OK) worst = r.st;
   }
   return worst;
+}
+
+// ---------------------------------------------------------------------------
+// Device-driven solves.
+namespace {
+constexpr int kMaxRecRestart = 31;
+
+// x = 0 was done; sc[0] = ||b||^2.  Decide whether any cycle runs.
+__global__ void k_fg_init(double *sc, double *dv, int *di, double rtol, double atol,
+                          cudaGraphConditionalHandle hw) {
+  const double bn = sqrt(sc[0]);
+  const double target = fmax(rtol * bn, atol);
+  dv[0] = bn;
+  dv[1] = target;
+  dv[2] = bn;
+  for (int i = 0; i < 8; ++i) di[i] = 0;
+  bool more = true;
+  if (!isfinite(bn)) {
+    di[2] = CHNSS_ERR_NAN;
+    more = false;
+  } else if (bn <= target) {
+    di[3] = 1;
+    more = false;
+  }
+  sc[2] = bn;                                         // ||r|| of the first cycle
+  cudaGraphSetConditional(hw, more ? 1u : 0u);
+}
+__global__ void k_fg_cycle_begin(int *di) {
+  di[1] = 0;
+  di[4] = 0;
+  di[6] = 1;                                          // Arnoldi step 0 runs
+}
+__global__ void k_fg_gate(cudaGraphConditionalHandle h, const int *di) { cudaGraphSetConditional(h, di[6] ? 1u : 0u); }
+// after Arnoldi step j: sc[4] = |g_{j+1}| (the residual estimate), sc[5] = H(j+1, j)
+__global__ void k_fg_step(int j, int m, const double *sc, const double *dv, int *di, int maxit) {
+  const int it = di[0] + 1;
+  di[0] = it;
+  di[1] = j + 1;
+  const double est = sc[4], hn = sc[5];
+  bool stop;
+  if (!isfinite(est) || !isfinite(hn)) {
+    di[5] = 1;
+    stop = true;
+  } else {
+    const bool breakdown = hn == 0.0;
+    di[4] = breakdown ? 1 : 0;
+    stop = est <= dv[1] || it >= maxit || breakdown;
+  }
+  di[6] = (!stop && j + 1 < m) ? 1 : 0;
+}
+// after the cycle's true residual: sc[1] = ||b - A x||^2
+__global__ void k_fg_cycle_end(const double *sc, double *dv, int *di, int maxit, cudaGraphConditionalHandle hw) {
+  bool more = false;
+  if (di[5]) {
+    di[2] = CHNSS_ERR_NAN;
+  } else {
+    const double rn = sqrt(sc[1]);
+    dv[2] = rn;
+    if (!isfinite(rn)) di[2] = CHNSS_ERR_NAN;
+    else if (rn <= dv[1]) di[3] = 1;
+    else if (di[0] >= maxit) di[2] = CHNSS_ERR_NOCONV;
+    else if (di[4]) di[2] = CHNSS_ERR_BREAKDOWN;
+    else more = true;
+  }
+  cudaGraphSetConditional(hw, more ? 1u : 0u);
+}
+// PCG: sc[0] = ||b||^2 (b copied to r)
+__global__ void k_pcg_init(const double *sc, double *dv, int *di, double rtol, cudaGraphConditionalHandle hw) {
+  const double bn = sqrt(sc[0]);
+  dv[0] = bn;
+  dv[1] = rtol * bn;
+  dv[2] = bn;
+  for (int i = 0; i < 8; ++i) di[i] = 0;
+  bool more = true;
+  if (!isfinite(bn)) {
+    di[2] = CHNSS_ERR_NAN;
+    more = false;
+  } else if (bn <= dv[1]) {
+    di[3] = 1;
+    more = false;
+  }
+  cudaGraphSetConditional(hw, more ? 1u : 0u);
+}
+// after an iteration: sc[5] = ||r||^2
+__global__ void k_pcg_decide(const double *sc, double *dv, int *di, int maxit, cudaGraphConditionalHandle hw) {
+  const int it = di[0] + 1;
+  di[0] = it;
+  const double rn = sqrt(sc[5]);
+  dv[2] = rn;
+  bool more = false;
+  if (!isfinite(rn)) di[2] = CHNSS_ERR_NAN;
+  else if (rn <= dv[1]) di[3] = 1;
+  else if (it >= maxit) di[2] = CHNSS_ERR_NOCONV;
+  else more = true;
+  cudaGraphSetConditional(hw, more ? 1u : 0u);
+}
+__global__ void k_copy_scalar(const double *src, double *dst) { *dst = *src; }
+__global__ void k_krylov_record(const double *dv, const int *di, double *dst) {
+  dst[0] = (double)di[0];
+  dst[1] = (double)di[3];
+  dst[2] = dv[0] > 0.0 ? dv[2] / dv[0] : 0.0;
+  dst[3] = (double)di[2];
+}
+
+// Add a conditional node of the given type after the capture position of s
+// (handle h, created on s's capture graph and set by an earlier node) and
+// start capturing its body on q.  end_body() finishes the body and makes
+// the node the capture position of s.
+cudaGraphNode_t begin_body(cudaStream_t s, cudaStream_t q, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  const cudaGraphEdgeData *edata = nullptr;
+  size_t nd = 0;
+  CHNSS_CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edata, &nd));
+  if (cs != cudaStreamCaptureStatusActive) throw Error{CHNSS_ERR_STATE, "device-driven solve outside a stream capture"};
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = type;
+  np.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  CHNSS_CK(cudaGraphAddNode(&node, g, deps, edata, nd, &np));
+  CHNSS_CK(cudaStreamBeginCaptureToGraph(q, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal));
+  return node;
+}
+void end_body(cudaStream_t s, cudaStream_t q, cudaGraphNode_t node) {
+  cudaGraph_t tmp = nullptr;
+  CHNSS_CK(cudaStreamEndCapture(q, &tmp));
+  CHNSS_CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+}
+cudaGraphConditionalHandle new_handle(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  CHNSS_CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+  if (cs != cudaStreamCaptureStatusActive) throw Error{CHNSS_ERR_STATE, "device-driven solve outside a stream capture"};
+  cudaGraphConditionalHandle h;
+  CHNSS_CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+  return h;
+}
+// a failed body capture must still end it, or the streams stay in capture mode
+template <typename F>
+void record_body(cudaStream_t s, cudaStream_t q, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                 F &&body) {
+  const cudaGraphNode_t node = begin_body(s, q, h, type);
+  try {
+    body();
+  } catch (...) {
+    cudaGraph_t tmp = nullptr;
+    cudaStreamEndCapture(q, &tmp);
+    throw;
+  }
+  end_body(s, q, node);
+}
+}  // namespace
+
+void fgmres_record(LinearOperator &A, const double *b, double *x, double rtol, double atol, int maxit,
+                   KrylovWork &ws, cudaStream_t s, cudaStream_t bq1, cudaStream_t bq2) {
+  const long n = A.size();
+  const long ld = (n + 31) / 32 * 32;
+  const int m = ws.m;
+  const int ldh = m + 1;
+  if (m > kMaxRecRestart) throw Error{CHNSS_ERR_ARG, "device-driven FGMRES needs restart <= 31"};
+  double *sc = ws.sc;
+  vec_fill(n, 0.0, x, s);
+  dot<double>(n, b, b, sc, ws.partial, s);
+  const cudaGraphConditionalHandle hw = new_handle(s);
+  k_fg_init<<<1, 1, 0, s>>>(sc, ws.dv, ws.di, rtol, atol, hw);
+  CHNSS_LAUNCH_CK();
+  vec_copy(n, b, ws.w, s);
+  record_body(s, bq1, hw, cudaGraphCondTypeWhile, [&] {
+    if (ws.V2)
+      dfgs_first(n, ws.w, sc + 2, ws.V2, ws.V, bq1);
+    else
+      vec_scale_by_inv(n, ws.w, sc + 2, ws.V, bq1);
+    vec_fill(m + 1, 0.0, ws.g, bq1);
+    set_scalar(ws.g, sc + 2, 1.0, false, bq1);
+    k_fg_cycle_begin<<<1, 1, 0, bq1>>>(ws.di);
+    CHNSS_LAUNCH_CK();
+    for (int j = 0; j < m; ++j) {
+      const cudaGraphConditionalHandle hj = new_handle(bq1);
+      k_fg_gate<<<1, 1, 0, bq1>>>(hj, ws.di);
+      CHNSS_LAUNCH_CK();
+      record_body(bq1, bq2, hj, cudaGraphCondTypeIf, [&] {
+        double *vj = ws.V + (long)j * ld;
+        double *zj = ws.Z + (long)j * ld;
+        A.precond(vj, zj, bq2);
+        A.apply(zj, ws.w, bq2);
+        const int kv = j + 1;
+        if (ws.V2) {
+          dfgs_dots(n, ws.V2, ld, kv, ws.w, ws.h1, ws.partial, bq2);
+          dfgs_update_dots(n, ws.V2, ld, kv, ws.h1, ws.w, ws.h2, ws.partial, bq2);
+          arnoldi_finish_pyth(j, ldh, ws.H, ws.h1, ws.h2, ws.cs, ws.sn, ws.g, sc + 4, bq2);
+          dfgs_update_scale(n, ws.V2, ld, kv, ws.h2, ws.w, sc + 5, ws.V2 + (long)(j + 1) * ld,
+                            ws.V + (long)(j + 1) * ld, bq2);
+        } else {
+          cgs2_dots(n, ws.V, ld, kv, ws.w, ws.h1, ws.partial, bq2);
+          cgs2_update_dots(n, ws.V, ld, kv, ws.h1, ws.w, ws.h2, ws.partial, bq2);
+          arnoldi_finish_pyth(j, ldh, ws.H, ws.h1, ws.h2, ws.cs, ws.sn, ws.g, sc + 4, bq2);
+          cgs2_update_scale(n, ws.V, ld, kv, ws.h2, ws.w, sc + 5, ws.V + (long)(j + 1) * ld, bq2);
+        }
+        k_fg_step<<<1, 1, 0, bq2>>>(j, m, sc, ws.dv, ws.di, maxit);
+        CHNSS_LAUNCH_CK();
+      });
+    }
+    hessenberg_solve_dev(ws.di + 1, ldh, ws.H, ws.g, ws.y, bq1);
+    combine_columns_dev(n, ws.Z, ld, ws.di + 1, ws.y, x, bq1);
+    A.apply(x, ws.w, bq1);
+    vec_axpby(n, 1.0, b, -1.0, ws.w, bq1);                 // w = b - A x
+    dot<double>(n, ws.w, ws.w, sc + 1, ws.partial, bq1);
+    set_scalar(sc + 2, sc + 1, 1.0, true, bq1);
+    k_fg_cycle_end<<<1, 1, 0, bq1>>>(sc, ws.dv, ws.di, maxit, hw);
+    CHNSS_LAUNCH_CK();
+  });
+}
+
+void pcg_record(const Pattern &P, const double *val, const double *dinv, const double *b, double *x, double rtol,
+                int maxit, KrylovWork &ws, cudaStream_t s, cudaStream_t bq1) {
+  const long n = P.nrows;
+  double *r = ws.w, *z = ws.V, *p = ws.V + n, *q = ws.V + 2 * n;
+  double *sc = ws.sc;   // [0] bb [1] rz [2] rz_new [3] pq [4] alpha [5] rr
+  vec_copy(n, b, r, s);
+  dot<double>(n, r, r, sc, ws.partial, s);
+  vec_fill(n, 0.0, x, s);
+  const cudaGraphConditionalHandle hw = new_handle(s);
+  k_pcg_init<<<1, 1, 0, s>>>(sc, ws.dv, ws.di, rtol, hw);
+  CHNSS_LAUNCH_CK();
+  vec_mul(n, dinv, r, z, s);
+  vec_copy(n, z, p, s);
+  dot<double>(n, r, z, sc + 1, ws.partial, s);
+  record_body(s, bq1, hw, cudaGraphCondTypeWhile, [&] {
+    SpmvArgs none;
+    spmv_csr<double>(P, val, 1, p, q, SPMV_PLAIN, none, bq1);
+    dot<double>(n, p, q, sc + 3, ws.partial, bq1);
+    pcg_alpha(sc + 1, sc + 3, sc + 4, bq1);
+    pcg_update_xr(n, sc + 4, p, q, x, r, bq1);
+    dot<double>(n, r, r, sc + 5, ws.partial, bq1);
+    k_pcg_decide<<<1, 1, 0, bq1>>>(sc, ws.dv, ws.di, maxit, hw);
+    CHNSS_LAUNCH_CK();
+    // the next direction (unused once the loop has stopped)
+    vec_mul(n, dinv, r, z, bq1);
+    dot<double>(n, r, z, sc + 2, ws.partial, bq1);
+    pcg_update_p(n, sc + 2, sc + 1, z, p, bq1);
+    k_copy_scalar<<<1, 1, 0, bq1>>>(sc + 2, sc + 1);
+    CHNSS_LAUNCH_CK();
+  });
+}
+
+void krylov_record(const KrylovWork &ws, double *dst, cudaStream_t s) {
+  k_krylov_record<<<1, 1, 0, s>>>(ws.dv, ws.di, dst);
+  CHNSS_LAUNCH_CK();
 }
 
 chnss_status pcg(const Pattern &P, const double *val, const double *dinv, const double *b, double *x, double rtol,

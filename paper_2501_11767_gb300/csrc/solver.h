@@ -178,8 +178,26 @@ struct KrylovWork {
   // also as pairs of FP32 numbers, read by the Gram-Schmidt passes; V keeps
   // each vector's exact FP64 value for the preconditioner
   float2 *V2 = nullptr;
+  // device-driven solves: [0] ||b|| [1] target [2] ||r||; [0] iterations
+  // [1] k [2] status [3] converged [4] breakdown [5] non-finite [6] go on
+  double *dv = nullptr;
+  int *di = nullptr;
   void init(Arena &ar, int m, long nmax, double *pinned, bool pairs = false);
 };
+
+// Device-driven solves, recorded into the CUDA graph that s is capturing
+// (no host synchronisation): the FGMRES restart cycles are a conditional
+// WHILE node, the m Arnoldi steps of a cycle conditional IF nodes, every
+// decision a one-thread kernel; the PCG iterations a WHILE node.  Bodies
+// are captured on bq1 (WHILE) and bq2 (IF).  Same kernels, order and
+// stopping rules as fgmres() / pcg(), so the results are bitwise theirs.
+// The outcome stays on the device: krylov_record() writes [iterations,
+// converged, relative residual, status] (doubles) to dst.
+void fgmres_record(LinearOperator &A, const double *b, double *x, double rtol, double atol, int maxit,
+                   KrylovWork &ws, cudaStream_t s, cudaStream_t bq1, cudaStream_t bq2);
+void pcg_record(const Pattern &P, const double *val, const double *dinv, const double *b, double *x, double rtol,
+                int maxit, KrylovWork &ws, cudaStream_t s, cudaStream_t bq1);
+void krylov_record(const KrylovWork &ws, double *dst, cudaStream_t s);
 
 // Right-preconditioned FGMRES(m), CGS2, Givens, x0 = 0; stop when the true
 // residual satisfies ||b - A x|| <= max(rtol ||b||, atol) (Sec. 5).

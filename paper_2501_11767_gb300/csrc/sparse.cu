@@ -693,9 +693,10 @@ __global__ void k_ortho_update(long n, const double *__restrict__ V, long ldv, i
   }
 }
 
-__global__ void k_combine(long n, const double *__restrict__ Z, long ldz, int k, const double *__restrict__ y,
-                          double *__restrict__ x) {
+__global__ void k_combine(long n, const double *__restrict__ Z, long ldz, int k0, const int *kd,
+                          const double *__restrict__ y, double *__restrict__ x) {
   __shared__ double ys[64];
+  const int k = kd ? *kd : k0;   // kd: the column count from device memory
   if (threadIdx.x < k) ys[threadIdx.x] = y[threadIdx.x];
   __syncthreads();
   const long i = (long)blockIdx.x * TPB + threadIdx.x;
@@ -734,7 +735,8 @@ __global__ void k_arnoldi_finish(int j, int ldh, double *H, const double *h1, co
   status[1] = hn;
 }
 
-__global__ void k_hessenberg_solve(int k, int ldh, const double *H, const double *g, double *y) {
+__global__ void k_hessenberg_solve(int k0, const int *kd, int ldh, const double *H, const double *g, double *y) {
+  const int k = kd ? *kd : k0;
   for (int i = k - 1; i >= 0; --i) {
     double s = g[i];
     for (int c = i + 1; c < k; ++c) s -= H[(long)c * ldh + i] * y[c];
@@ -1704,7 +1706,12 @@ void ortho_update_norm(long n, const double *V, long ldv, int k, const double *h
   CHNSS_LAUNCH_CK();
 }
 void combine_columns(long n, const double *Z, long ldz, int k, const double *y, double *x, cudaStream_t s) {
-  k_combine<<<nblocks(n, TPB), TPB, 0, s>>>(n, Z, ldz, k, y, x);
+  k_combine<<<nblocks(n, TPB), TPB, 0, s>>>(n, Z, ldz, k, nullptr, y, x);
+  CHNSS_LAUNCH_CK();
+}
+void combine_columns_dev(long n, const double *Z, long ldz, const int *k, const double *y, double *x,
+                         cudaStream_t s) {
+  k_combine<<<nblocks(n, TPB), TPB, 0, s>>>(n, Z, ldz, 0, k, y, x);
   CHNSS_LAUNCH_CK();
 }
 void arnoldi_finish(int j, int ldh, double *H, const double *h1, const double *h2, const double *nrm2, double *cs,
@@ -1864,7 +1871,11 @@ void dfgs_first(long n, const double *w, const double *hn, float2 *vout2, double
 }
 
 void hessenberg_solve(int k, int ldh, const double *H, const double *g, double *y, cudaStream_t s) {
-  k_hessenberg_solve<<<1, 1, 0, s>>>(k, ldh, H, g, y);
+  k_hessenberg_solve<<<1, 1, 0, s>>>(k, nullptr, ldh, H, g, y);
+  CHNSS_LAUNCH_CK();
+}
+void hessenberg_solve_dev(const int *k, int ldh, const double *H, const double *g, double *y, cudaStream_t s) {
+  k_hessenberg_solve<<<1, 1, 0, s>>>(0, k, ldh, H, g, y);
   CHNSS_LAUNCH_CK();
 }
 void set_scalar(double *dst, const double *src, double scale, bool sq, cudaStream_t s) {
