@@ -195,6 +195,8 @@ def run_gpu(args):
     def timed_run(prm, warmup, steps, profile, concurrent=True):
         ctx = chnss.Context(mesh, prm, stream)
         ctx.set_step_concurrency(concurrent)
+        if args.step_mode == 1 and not profile:
+            ctx.set_step_mode(1)
         a, b = {k: v.clone() for k, v in st0.items()}, ctx.new_state()
         for _ in range(warmup):
             ctx.step(a, b)
@@ -388,6 +390,7 @@ def run_gpu(args):
         "config": {"workload": args.workload, "n": n, "p1_nodes": N1, "p2_nodes": N2,
                    "velocity_dofs": 2 * N2, "precision": "mixed" if params["precision"] == 1 else "fp64",
                    "gram_schmidt": "double-FP32" if params.get("ortho", 0) == 1 else "FP64",
+                   "step_mode": "one graph" if args.step_mode == 1 else "host-driven Krylov loops",
                    "rtol": params["rtol"], "restart": params["restart"], "tau": params["tau"],
                    "beta": params["beta"],
                    "l2": "inputs larger than L2 (per-step working set > 10 GB)",
@@ -681,7 +684,7 @@ def run_sweep(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             sec = float(t.item())
         conv = all(r[k]["converged"] for rs in iters for r in rs for k in r)
-        mean = {k: round(sum(r[k]["iters"] for rs in iters for r in rs) / (len(iters) * len(rs)), 2) for k in recs[0]}
+        mean = {k: round(sum(r[k]["iters"] for rs in iters for r in rs) / (len(iters) * len(recs)), 2) for k in recs[0]}
         final = [chnss.state_to_numpy(x) for x in a]
         del ctxs, a, b
         return sec, clocks, launches, conv, mean, t_rec, final
@@ -816,6 +819,8 @@ def main():
     ap.add_argument("--roofline-steps", type=int, default=3)
     ap.add_argument("--ortho", type=int, default=-1, choices=[-1, 0, 1],
                     help="Gram-Schmidt arithmetic of the headline leg: 0 FP64, 1 double-FP32 (-1: the workload's)")
+    ap.add_argument("--step-mode", type=int, default=0, choices=[0, 1],
+                    help="0: host-driven Krylov loops; 1: every step one recorded CUDA graph")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
