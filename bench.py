@@ -396,6 +396,7 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (per-step working set > 10 GB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "iters_last_step": {k: v["iters"] for k, v in last.items()},
+        "solve_seconds_last_step": {k: round(v["seconds"], 4) for k, v in last.items()},
         "iters_mean": {k: round(sum(i[k]["iters"] for i in infos) / len(infos), 2) for k in last},
         "converged": all(i[k]["converged"] for i in infos for k in last),
         "fp64": fp64,
