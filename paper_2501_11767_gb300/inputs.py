@@ -208,6 +208,9 @@ def workload(name: str) -> dict:
         p.update(beta=film_betas(0.005), tau=5e-4, precision=1, rtol=1e-6, atol=1e-8, ns_rtol=1e-4, ns_atol=1e-8,
                  inner_rtol=1e-4, inner_maxit=20, ortho=1)
         return {"n": 1024, "params": p, "steps": 10}
+    if name == "film1024_open_mixed":     # open top on the bench mesh with the paper's time step 1e-4
+        p.update(beta=film_betas(0.005), tau=1e-4, precision=1, top_bc=1, ortho=1)
+        return {"n": 1024, "params": p, "steps": 10}
     if name == "film512_open_mixed":      # the bench set with an open (do-nothing) top, 512 x 512
         p.update(beta=film_betas(0.005), tau=5e-4, precision=1, top_bc=1, ortho=1)
         return {"n": 512, "params": p, "steps": 10}

@@ -69,13 +69,14 @@ def _csr(ctx, which, shape):
     return sp.csr_matrix((val, col, rp), shape=shape)
 
 
-def test_full_size_solves_meet_the_stopping_rule(torch):
-    """1024 x 1024, the bench parameter set (mixed precision), two steps from
-    the seeded start: residuals of the returned solutions recomputed in FP64
-    on the host."""
-    w = inputs.workload("film1024_mixed")
+@pytest.mark.parametrize("workload", ["film1024_mixed", "film1024_open_mixed"])
+def test_full_size_solves_meet_the_stopping_rule(torch, workload):
+    """1024 x 1024, the bench parameter set (mixed precision) and the open
+    top with the paper's time step, two steps from the seeded start:
+    residuals of the returned solutions recomputed in FP64 on the host."""
+    w = inputs.workload(workload)
     n, p = w["n"], w["params"]
-    mesh = chnss.Mesh(n)
+    mesh = chnss.Mesh(n, top_bc=p.get("top_bc", 0))
     ctx = chnss.Context(mesh, p)
     N1, N2 = mesh.N1, mesh.N2
     st = chnss.state_to_device(inputs.initial_state(n, seed=0))
@@ -111,7 +112,7 @@ def test_full_size_solves_meet_the_stopping_rule(torch):
         res = np.concatenate([rhs[:2 * N2] - Av @ v - B.T @ pr, rhs[2 * N2:] - B @ v])
         r = np.linalg.norm(res) / np.linalg.norm(rhs)
         assert info["ns"]["converged"] and r <= rtol * (1 + 1e-6), (k, r, info["ns"])
-        # enclosed flow: the returned pressure has zero mean
-        assert abs(M @ pr).sum() > 0 and abs((M @ pr).sum()) <= 1e-12 * abs(M @ pr).sum()
+        if p.get("top_bc", 0) == 0:      # enclosed flow: the returned pressure has zero mean
+            assert abs(M @ pr).sum() > 0 and abs((M @ pr).sum()) <= 1e-9 * abs(M @ pr).sum()
         del Av, B
         st = out
