@@ -123,9 +123,12 @@ typedef struct {
 /* Mesh hierarchy for n x n squares on [0,lx] x [0,ly]: n even, 2 <= n <= 2048,
  * nx == ny required.  Multigrid levels n, n/2, ... while the size is even and
  * at least 4; the coarsest level (n = m 2^k with m odd or m = 2) must have
- * m <= 9 cells per side, because it is solved by a dense inverse rebuilt
- * every step by one thread block (2 (2m + 1)^2 velocity rows: 722 for
- * m = 9); n = 50, 100 or 200 (m = 25) are refused.  Builds the CSR patterns, the element -> CSR gather maps and
+ * m <= 25 cells per side.  On it the pressure Laplacian of the PCD keeps a
+ * dense FP64 inverse (built once by one thread block, (m + 1)^2 rows), as
+ * does every block while the level has at most 400 unknowns; larger
+ * non-singular coarsest levels (the velocity block for m >= 7, the P1 blocks
+ * for m >= 20) take 16 Chebyshev-Jacobi steps from zero on [hi/64, hi]
+ * instead.  n = 50, 100, 200 (m = 25) are accepted.  Builds the CSR patterns, the element -> CSR gather maps and
  * the transfer operators (host), and uploads them.  Returns CHNSS_ERR_ARG
  * for bad sizes, CHNSS_ERR_OOM / CHNSS_ERR_CUDA on device failures. */
 chnss_status chnss_mesh_create(int nx, int ny, double lx, double ly, chnss_mesh_t *out);

@@ -8,7 +8,12 @@ hierarchy is geometric: meshes n, n/2, ... while the size is even and at least
 nodes; prolongation is nodal interpolation (linear for P1, quadratic for P2,
 exact for the nested spaces) and restriction its transpose.  One V-cycle:
 Chebyshev-Jacobi pre-smoothing from x = 0, coarse correction, post-smoothing;
-dense LU with partial pivoting on the coarsest mesh.  Smoother interval
+dense LU with partial pivoting on the coarsest mesh while it has at most
+COARSE_DENSE_MAX unknowns (always for the pressure Laplacian, dense_coarse),
+else COARSE_DEGREE Chebyshev-Jacobi steps from zero on [hi / COARSE_RATIO,
+hi] (the other blocks are mass-dominated on a coarse mesh, so a fixed
+polynomial solves them well; a dense inverse of a 25 x 25 velocity level
+would have 5202 rows).  Smoother interval
 [hi / ratio, hi] with hi the Gershgorin bound max_i sum_j |a_ij| / |a_ii| of
 D^{-1} A: degree 2, ratio 4 for the scalar P1 operators; degree 4, ratio 16
 for the Taylor-Hood velocity operator (the paper leaves the AMG smoothing to
@@ -28,6 +33,9 @@ SMOOTH_DEGREE = 2
 LO_RATIO = 4.0
 VEL_SMOOTH_DEGREE = 4
 VEL_LO_RATIO = 16.0
+COARSE_DENSE_MAX = 400
+COARSE_DEGREE = 16
+COARSE_RATIO = 64.0
 
 
 def level_sizes(n: int):
@@ -116,7 +124,7 @@ def inject_velocity(v, nf):
 class MG:
     """One V-cycle of geometric multigrid for a hierarchy of matrices."""
 
-    def __init__(self, mats, prolongs, singular=False, degree=None, ratio=None):
+    def __init__(self, mats, prolongs, singular=False, degree=None, ratio=None, dense_coarse=False):
         self.mats = mats
         self.degree = SMOOTH_DEGREE if degree is None else degree
         self.ratio = LO_RATIO if ratio is None else ratio
@@ -128,13 +136,26 @@ class MG:
             self.dinv.append(1.0 / d)
             absA = abs(A)
             self.hi.append(float(np.max(np.asarray(absA.sum(axis=1)).ravel() / np.abs(d))))
-        Ac = mats[-1].toarray()
-        if singular:
-            Ac = Ac + np.ones_like(Ac)
-        self.lu = sla.lu_factor(Ac)
+        self.coarse_iter = (len(mats) > 1 and not singular and not dense_coarse
+                            and mats[-1].shape[0] > COARSE_DENSE_MAX)
+        if self.coarse_iter:
+            A = mats[-1]
+            d = A.diagonal()
+            self.cdinv = 1.0 / d
+            self.chi = float(np.max(np.asarray(abs(A).sum(axis=1)).ravel() / np.abs(d)))
+            self.lu = None
+        else:
+            Ac = mats[-1].toarray()
+            if singular:
+                Ac = Ac + np.ones_like(Ac)
+            self.lu = sla.lu_factor(Ac)
 
     def vcycle(self, b, level=0):
         if level == len(self.mats) - 1:
+            if self.coarse_iter:
+                A = self.mats[level]
+                return chebyshev(lambda y: A @ y, self.cdinv, b, None, self.chi / COARSE_RATIO, self.chi,
+                                 COARSE_DEGREE)
             return sla.lu_solve(self.lu, b)
         A = self.mats[level]
         dinv, hi = self.dinv[level], self.hi[level]

@@ -177,9 +177,10 @@ class Oracle:
         mgA = MG(mats, self.Pv(), degree=VEL_SMOOTH_DEGREE, ratio=VEL_LO_RATIO)
         if self._Kp is None:
             if self.top_free:        # outflow: K_p with Dirichlet rows on the open top, non-singular
-                self._Kp = MG([fem.p1_dirichlet(f.K, f.mesh.p1_top()) for f in self.forms], self.P1)
+                self._Kp = MG([fem.p1_dirichlet(f.K, f.mesh.p1_top()) for f in self.forms], self.P1,
+                              dense_coarse=True)
             else:
-                self._Kp = MG([f.K for f in self.forms], self.P1, singular=True)
+                self._Kp = MG([f.K for f in self.forms], self.P1, singular=True, dense_coarse=True)
         mgK = self._Kp
         iA, iK = mgA.inner(p), mgK.inner(p)
         Mp = self.forms[0].M

@@ -575,9 +575,10 @@ class Oracle3D:
             mgA = self._mg(mats, self.Pv, degree=VEL_SMOOTH_DEGREE, ratio=VEL_LO_RATIO)
             if self._Kp is None:
                 if self.top_free:   # outflow: K_p with Dirichlet rows on the open top, non-singular
-                    self._Kp = MG([p1_dirichlet(fm.K, fm.mesh.p1_top()) for fm in self.forms], self.P1)
+                    self._Kp = MG([p1_dirichlet(fm.K, fm.mesh.p1_top()) for fm in self.forms], self.P1,
+                                  dense_coarse=True)
                 else:
-                    self._Kp = MG([fm.K for fm in self.forms], self.P1, singular=True)
+                    self._Kp = MG([fm.K for fm in self.forms], self.P1, singular=True, dense_coarse=True)
             kp = self._Kp if not p.get("inner_rtol", 0.0) else (
                 lambda b: self._Kp.solve(b, p["inner_rtol"], p.get("inner_maxit", 20))[0])
             mdinv = 1.0 / F.M.diagonal()

@@ -538,6 +538,7 @@ void init_precset(chnss_ctx *c, PrecSet<T> &P) {
   P.A.init(ar, 1, false, p2s, d2s, vals(c->A), tvs, c->partial);
   P.A.degree = 4;        // velocity smoothing: degree 4 on [hi / 16, hi]
   P.A.ratio = 16.0;
+  P.Kp.keep_dense = true;       // a pure Laplacian: its coarsest level is not mass-dominated
   if (c->mesh->m.top_bc == 1)   // open top: Dirichlet outflow rows, non-singular
     P.Kp.init(ar, 0, false, p1s, d1s, vals(c->Kpd), t1s, c->partial);
   else
@@ -942,7 +943,7 @@ int system_size(chnss_ctx *c, int sys) {
 }
 
 // One system on stream s with Krylov work kw and an N1 scratch vector tmp.
-constexpr int kMaxCoarseCells = 9;   // largest coarsest level of a 2D mesh hierarchy (cells per side)
+constexpr int kMaxCoarseCells = 25;  // largest coarsest level of a 2D mesh hierarchy (cells per side)
 
 // device allocations of a debug entry point, freed when it returns
 struct ScopedDeviceMem {
@@ -1388,11 +1389,10 @@ chnss_status chnss_mesh_create_ex(int nx, int ny, double lx, double ly, int top_
   // element-buffer offsets and gather counts are int: 144 E = 288 n^2 stays
   // below 2^31 up to n = 2730
   if (nx < 2 || nx % 2 != 0 || nx > 2048) throw Error{CHNSS_ERR_ARG, "n must be even and in [2, 2048]"};
-  // the hierarchy halves n while it is even and >= 4; the coarsest level is
-  // solved by a dense inverse built by one thread block every step, whose
-  // velocity block has 2 (2 n_c + 1)^2 rows: its memory grows as n_c^4 and
-  // its cost as n_c^6 (n_c = 9: 722 rows, ~0.1 s per step; n_c = 129 would
-  // need 144 GB), so meshes must coarsen to at most 9 x 9 cells
+  // the hierarchy halves n while it is even and >= 4; on the coarsest level
+  // the pressure Laplacian keeps a dense inverse built once by one thread
+  // block, with (n_c + 1)^2 rows (n_c = 25: 676 rows, about 0.1 s once; its
+  // cost grows as n_c^6), so meshes must coarsen to at most 25 x 25 cells
   int nc = nx;
   while (nc % 2 == 0 && nc >= 4) nc /= 2;
   if (nc > kMaxCoarseCells)

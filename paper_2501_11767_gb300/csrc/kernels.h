@@ -90,6 +90,7 @@ struct TailLevel {
 template <typename T>
 struct TailDesc {
   int nlev = 0, degree = 2, nc = 0;
+  int coarse_degree = 0;          // > 0: Chebyshev steps on the coarsest level instead of cinv
   const double *cinv = nullptr;   // coarsest level, row-major nc x nc
   TailLevel<T> lv[kMaxTailLevels];
 };
@@ -125,7 +126,15 @@ void jacobi_bsr2(const Pattern &P, const double *val, const int *diag, T *dinv, 
 // Chebyshev smoother of degree d on [hi / ratio, hi]; coef layout (4 + 3(d-1)
 // doubles): [beta0][first post step: 1, 0, beta0][(c0, c1, c2) for k = 1..d-1]
 // with x_{k+1} = c0 x_k + c1 x_{k-1} + c2 D^-1 (b - A x_k).
-constexpr int kMaxSmoothDegree = 8;
+constexpr int kMaxSmoothDegree = 16;
+// Coarsest multigrid level: a dense FP64 inverse (rebuilt with the level's
+// operator by one thread block) while it has at most kCoarseDenseMax rows or
+// is the singular pressure Laplacian (constant, built once); otherwise
+// kCoarseDegree Chebyshev-Jacobi steps from zero on [hi / kCoarseRatio, hi]
+// (the non-singular blocks are mass-dominated on coarse meshes).
+constexpr int kCoarseDenseMax = 400;
+constexpr int kCoarseDegree = 16;
+constexpr double kCoarseRatio = 64.0;
 void cheb_coefficients(const double *hi, double ratio, int degree, double *coef, cudaStream_t s);
 
 // vectors

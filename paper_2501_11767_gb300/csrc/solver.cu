@@ -163,8 +163,11 @@ void MGHier<T>::init(Arena &ar, int kind_, bool singular_, const std::vector<con
     coef[l] = ar.alloc<double>(4 + 3 * (kMaxSmoothDegree - 1));
   }
   nc = (int)n[nl - 1];
-  dense = ar.alloc<double>((long)nc * nc);
-  cinv = ar.alloc<double>((long)nc * nc);
+  coarse_iter = nl > 1 && !singular && !keep_dense && nc > kCoarseDenseMax;
+  if (!coarse_iter) {
+    dense = ar.alloc<double>((long)nc * nc);
+    cinv = ar.alloc<double>((long)nc * nc);
+  }
   status = ar.alloc<int>(1);
   partial = partial_buf;
   sum = ar.alloc<double>(1);
@@ -203,6 +206,7 @@ TailDesc<T> *MGHier<T>::make_tail(Arena &ar, const std::vector<MultiPtr<T>> &X, 
   d.degree = degree;
   d.nc = nc;
   d.cinv = cinv;
+  d.coarse_degree = coarse_iter ? kCoarseDegree : 0;
   auto view = [](const Pattern &P) {
     if (P.sell.wmax > 8) throw Error{CHNSS_ERR_ARG, "coarse-level block: rows of at most 8 entries"};
     TailSell v;
@@ -241,13 +245,17 @@ void MGHier<T>::setup(cudaStream_t s) {
     if (bf16) sell_gather<__nv_bfloat16>(pat[l]->sell, kind == 0 ? 1 : 4, val64[l], val16[l], s);
     else sell_gather<T>(pat[l]->sell, kind == 0 ? 1 : 4, val64[l], val[l], s);
     if (l == 0 && val0_64) sell_gather<double>(pat[0]->sell, kind == 0 ? 1 : 4, val64[0], val0_64, s);
-    if (l == nl - 1) break;
+    if (l == nl - 1 && !coarse_iter) break;
     if (kind == 0)
       jacobi_csr<T>(*pat[l], val64[l], diag[l], dinv[l], hi[l], partial, s);
     else
       jacobi_bsr2<T>(*pat[l], val64[l], diag[l], dinv[l], hi[l], partial, s);
-    cheb_coefficients(hi[l], ratio, degree, coef[l], s);
+    if (l == nl - 1)
+      cheb_coefficients(hi[l], kCoarseRatio, kCoarseDegree, coef[l], s);
+    else
+      cheb_coefficients(hi[l], ratio, degree, coef[l], s);
   }
+  if (coarse_iter) return;
   const int L = nl - 1;
   if (kind == 0)
     coarse_dense_csr(*pat[L], val64[L], singular ? 1.0 : 0.0, dense, s);
@@ -294,7 +302,7 @@ void MGHier<T>::vcycle(int l, cudaStream_t s) {
     mg_tail<T>(tail, 1, s);
     return;
   }
-  if (l == nl - 1) {
+  if (l == nl - 1 && !coarse_iter) {
     dense_apply<T>(nc, cinv, b[l], x[l], s);
     return;
   }
@@ -302,18 +310,21 @@ void MGHier<T>::vcycle(int l, cudaStream_t s) {
   SpmvArgs a;
   a.b = b[l];
   a.dinv = dinv[l];
-  // pre-smoothing from x = 0: x_1 = D^-1 b / theta, then degree - 1 steps of
+  // pre-smoothing from x = 0 (on the coarsest level of an iterative coarse
+  // solve: kCoarseDegree steps): x_1 = D^-1 b / theta, then deg - 1 steps of
   // the three-term recurrence; x_{k+1} overwrites x_{k-1}, so x_1 starts in
-  // the buffer that makes x_degree land in x[l]
-  T *cur = (degree - 1) % 2 == 0 ? x[l] : t[l];
+  // the buffer that makes x_deg land in x[l]
+  const int deg = l == nl - 1 ? kCoarseDegree : degree;
+  T *cur = (deg - 1) % 2 == 0 ? x[l] : t[l];
   T *oth = cur == x[l] ? t[l] : x[l];
   vec_scale_dinv<T>((int)n[l], coef[l], dinv[l], b[l], cur, s);
-  for (int k = 1; k < degree; ++k) {
+  for (int k = 1; k < deg; ++k) {
     a.coef = coef[l] + 4 + 3 * (k - 1);
     a.w = k == 1 ? nullptr : oth;
     op(l, cur, oth, SPMV_CHEB, a, s);
     std::swap(cur, oth);
   }
+  if (l == nl - 1) return;
   // residual, restriction, coarse correction, prolongation
   SpmvArgs ar;
   ar.b = b[l];
@@ -578,7 +589,7 @@ void MGBatch<T>::vcycle(int l, cudaStream_t s) {
     mg_tail<T>(tail, nr, s);
     return;
   }
-  if (l == nl - 1) {
+  if (l == nl - 1 && !h->coarse_iter) {
     dense_apply_multi<T>(h->nc, nr, h->cinv, b[l], x[l], s);
     return;
   }
@@ -588,15 +599,17 @@ void MGBatch<T>::vcycle(int l, cudaStream_t s) {
   a.b = b[l];
   a.dinv = h->dinv[l];
   // same buffer rotation as MGHier<T>::vcycle
-  MultiPtr<T> cur = (degree - 1) % 2 == 0 ? x[l] : t[l];
-  MultiPtr<T> oth = (degree - 1) % 2 == 0 ? t[l] : x[l];
+  const int deg = l == nl - 1 ? kCoarseDegree : degree;
+  MultiPtr<T> cur = (deg - 1) % 2 == 0 ? x[l] : t[l];
+  MultiPtr<T> oth = (deg - 1) % 2 == 0 ? t[l] : x[l];
   vec_scale_dinv_multi<T>(n, nr, h->coef[l], h->dinv[l], b[l], cur, s);
-  for (int k = 1; k < degree; ++k) {
+  for (int k = 1; k < deg; ++k) {
     a.coef = h->coef[l] + 4 + 3 * (k - 1);
     a.w = k == 1 ? MultiPtr<T>() : oth;
     op(l, cur, oth, SPMV_CHEB, a, s);
     std::swap(cur, oth);
   }
+  if (l == nl - 1) return;
   MultiArgs<T> ar;
   ar.b = b[l];
   op(l, x[l], r[l], SPMV_RES, ar, s);

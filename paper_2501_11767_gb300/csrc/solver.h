@@ -68,6 +68,8 @@ struct MGHier {
   std::vector<const Transfer *> tr;
   std::vector<long> n;
   int nc = 0;
+  bool coarse_iter = false;   // coarsest level by Chebyshev steps (kCoarseDegree), no dense inverse
+  bool keep_dense = false;    // set before init: dense coarsest level whatever its size (pressure Laplacian)
   double *dense = nullptr, *cinv = nullptr;
   int *status = nullptr;
   double *partial = nullptr, *sum = nullptr;

@@ -1023,8 +1023,28 @@ __global__ void __launch_bounds__(512) k_mg_tail(const TailDesc<T> *__restrict__
     MultiArgs<T> none;
     tail_sweep<T, NR>(q.R, q.Rval, q.r, d.lv[l + 1].b, SPMV_PLAIN, none);
   }
-  // coarsest: dense inverse
-  {
+  // coarsest: dense inverse, or Chebyshev steps from zero (same sweeps as
+  // the pre-smoothing, coarse_degree of them)
+  if (d.coarse_degree > 0) {
+    const TailLevel<T> &q = d.lv[L];
+    const int cd = d.coarse_degree;
+    MultiPtr<T> cur = (cd - 1) % 2 == 0 ? q.x : q.t;
+    MultiPtr<T> oth = (cd - 1) % 2 == 0 ? q.t : q.x;
+    for (int i = threadIdx.x; i < q.n; i += blockDim.x)
+      for (int k = 0; k < NR; ++k) cur.p[k][i] = (T)(*q.coef) * q.dinv[i] * q.b.p[k][i];
+    __syncthreads();
+    MultiArgs<T> a;
+    a.b = q.b;
+    a.dinv = q.dinv;
+    for (int st = 1; st < cd; ++st) {
+      a.coef = q.coef + 4 + 3 * (st - 1);
+      a.w = st == 1 ? MultiPtr<T>() : oth;
+      tail_sweep<T, NR>(q.A, q.val, cur, oth, SPMV_CHEB, a);
+      const MultiPtr<T> tmp = cur;
+      cur = oth;
+      oth = tmp;
+    }
+  } else {
     const TailLevel<T> &q = d.lv[L];
     for (int r = threadIdx.x; r < d.nc; r += blockDim.x)
       for (int k = 0; k < NR; ++k) {

@@ -968,6 +968,7 @@ void init_prec3(chnss3_ctx *c, Prec3<T> &P, const std::vector<const Pattern *> &
     P.X[sp].init(ar, 0, false, p1s, d1s, Xs[sp], t1s, c->partial);
     if (X2s) P.X2[sp].init(ar, 0, false, p1s, d1s, X2s[sp], t1s, c->partial);   // set up every step
   }
+  P.Kp.keep_dense = true;   // a pure Laplacian: its coarsest level is not mass-dominated
   P.Kp.init(ar, 0, c->top_bc != 1, p1s, d1s, K1s, t1s, c->partial);   // singular for enclosed flow
   P.A.degree = 4;      // as the 2D velocity operator: degree 4 on [hi / 16, hi]
   P.A.ratio = 16.0;

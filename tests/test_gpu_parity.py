@@ -100,11 +100,30 @@ def _compare_step(torch, n, params, seed, steps=2):
     return ctx
 
 
-@pytest.mark.parametrize("n", [32, 6, 20])
+@pytest.mark.parametrize("n", [32, 6, 20, 50])
 def test_step_matches_oracle(torch, n):
     """Two steps (the second with flow); n = 6 and 20 end on odd coarsest
-    meshes (3 and 5), 32 coarsens to 2."""
+    meshes (3 and 5), 32 coarsens to 2; n = 50 (a mesh of the paper's 2D
+    runs) to 25 x 25, where the velocity and the mass-dominated P1 blocks
+    take 16 Chebyshev steps instead of a dense coarse inverse."""
     _compare_step(torch, n, inputs.default_params(), seed=n)
+
+
+def test_step_matches_oracle_on_100_mesh(torch):
+    """n = 100, the base mesh of the paper's 2D mesh study (coarsest 25 x 25),
+    one step, mixed precision within 1e-6 of the oracle at an outer 1e-10."""
+    n = 100
+    p = inputs.default_params()
+    _compare_step(torch, n, p, seed=100, steps=1)
+    o = Oracle(n, dict(p, rtol=1e-12))
+    ctx = chnss.Context(chnss.Mesh(n), dict(p, precision=1, ortho=1, rtol=1e-10))
+    st = inputs.initial_state(n, seed=101)
+    ref, _ = o.step(st)
+    out, _, status = ctx.step(chnss.state_to_device(st))
+    assert status == 0
+    got = chnss.state_to_numpy(out)
+    for key in ("phi", "mu", "Phi_v", "v", "p"):
+        assert rel(got[key], ref[key]) <= MIXED_TOL, key
 
 
 def test_single_level_mesh(torch):

@@ -56,6 +56,12 @@ def test_step_3d_matches_oracle(torch):
     _compare(torch, 4, _params(), seed=1)
 
 
+def test_step_3d_iterative_coarse_level(torch):
+    """10^3 cubes coarsen to 5^3: the 3D velocity block's coarsest level (3993
+    unknowns) takes 16 Chebyshev steps, as in the paper's 40^3 runs."""
+    _compare(torch, 10, _params(), seed=10, steps=1)
+
+
 def test_step_3d_finer_mesh(torch):
     """8^3 cubes: three multigrid levels (8, 4, 2)."""
     _compare(torch, 8, _params(), seed=2, steps=1)

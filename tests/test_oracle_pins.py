@@ -308,3 +308,43 @@ def test_free_energy_kinetic_part_of_quadratic_free_velocities():
     e2 = model.free_energy(forms, dict(base, v=np.stack([X, Y], 1).ravel()), p)
     assert e1["kinetic"] == pytest.approx(0.5, rel=1e-13)
     assert e2["kinetic"] == pytest.approx(1.0 / 3.0, rel=1e-13)
+
+
+# ---------------------------------------------------------------------------
+def test_iterative_coarsest_level_on_the_papers_2d_mesh():
+    """n = 50 (a mesh of the paper's 2D runs) coarsens to 25 x 25: the
+    velocity and the mass-dominated P1 blocks solve their coarsest level by 16
+    Chebyshev-Jacobi steps, the pressure Laplacian keeps its dense inverse.
+    The polynomial coarse solve of the velocity block is within 5 % of the
+    exact coarse solve (the block is mass-dominated there), and a whole step
+    stays within the Krylov tolerance's reach of the exact (sparse LU) step."""
+    import scipy.sparse.linalg as spla
+    from oracle.mg import COARSE_DEGREE, MG, VEL_LO_RATIO, VEL_SMOOTH_DEGREE
+    n = 50
+    p = inputs.default_params()
+    o = Oracle(n, p)
+    st = inputs.initial_state(n, seed=1)
+    lstates = o.level_states(st)
+    A, _, _, Ap, _ = model.ns_system(o.forms[0], st, p)
+    o.ns_preconditioner(A, Ap, lstates)
+    assert not o._Kp.coarse_iter and o._Kp.lu is not None
+    mats = [A]
+    for lev in range(1, len(o.sizes)):
+        f, s_ = o.forms[lev], lstates[lev]
+        vf = f.velocity_forms()
+        J2 = fem.convection_p2(f.mesh, s_["v"], model.ns_shift(f.mesh, s_, p))
+        import scipy.sparse as sp
+        Al = vf["Mv"] / p["tau"] + sp.kron(J2, sp.eye(2), format="csr") + vf["Ksym"]
+        mats.append(fem.velocity_dirichlet(Al.tocsr(), vf["bnd"]))
+    mg = MG(mats, o.Pv(), degree=VEL_SMOOTH_DEGREE, ratio=VEL_LO_RATIO)
+    assert mg.coarse_iter and mats[-1].shape[0] == 2 * 51 ** 2 and COARSE_DEGREE == 16
+    b = np.random.default_rng(3).standard_normal(mats[-1].shape[0])
+    exact = spla.spsolve(mats[-1].tocsc(), b)
+    got = mg.vcycle(b, level=len(mats) - 1)
+    assert np.linalg.norm(got - exact) <= 0.05 * np.linalg.norm(exact)
+    oe = Oracle(n, p, exact=True)
+    a, info = o.step(st)
+    e, _ = oe.step(st)
+    assert info["ns"]["converged"] and info["ns"]["iters"] <= 60
+    for key, tol in (("phi", 1e-8), ("Phi_v", 1e-8), ("v", 1e-6), ("p", 1e-5), ("mu", 1e-5)):
+        assert np.linalg.norm(a[key] - e[key]) <= tol * np.linalg.norm(e[key]), key

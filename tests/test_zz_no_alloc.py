@@ -63,9 +63,9 @@ def test_noalloc_mass_solve_in_place(torch):
     assert e.value.status == 1 and "overlap" in str(e.value)
 
 
-# 288 = 9 * 2^5 is the smallest mesh above 256 x 256 that the library builds
-# (258 ... 286 coarsen to more than 9 x 9 cells and are refused at creation)
-@pytest.mark.parametrize("n", [288, 512])
+# 272 = 17 * 2^4 is the smallest mesh above 256 x 256 that the library builds
+# (258 ... 270 coarsen to more than 25 x 25 cells and are refused at creation)
+@pytest.mark.parametrize("n", [272, 512])
 def test_noalloc_mass_solve_rejects_large_meshes(torch, n):
     ctx = chnss.Context(chnss.Mesh(n), inputs.default_params())
     b = torch.ones(ctx.mesh.N1, dtype=torch.float64, device="cuda")
