@@ -31,8 +31,14 @@ def _params():
     return p
 
 
-def test_adjoint_step_matches_oracle(torch):
-    n = 8
+@pytest.mark.parametrize("n", [8, 32])
+def test_adjoint_step_matches_oracle(torch, n):
+    """One adjoint step against the oracle's discrete adjoint (32 x 32 is the
+    mesh of the adjoint workload's oracle check).  The oracle solves the
+    transposed systems exactly (sparse LU), the GPU by FGMRES to 1e-12; the
+    parameter gradients are sums of dot products that cancel, so at 32 x 32
+    that tolerance reaches them at ~1e-8 relative (bound 1e-7, still far
+    inside the 1e-5 of the finite-difference check)."""
     p = _params()
     o = Oracle(n, p, exact=True)
     s0 = inputs.initial_state(n, seed=4)
@@ -48,8 +54,9 @@ def test_adjoint_step_matches_oracle(torch):
     got = chnss.state_to_numpy(out)
     for key in ("phi", "mu", "Phi_v", "v"):
         assert rel(got[key], ref[key]) < 1e-8, key
-    assert grad[0] == pytest.approx(th["evap"], rel=1e-8)
-    assert grad[1] == pytest.approx(th["gamma"], rel=1e-8)
+    gtol = 1e-8 if n <= 8 else 1e-7
+    assert grad[0] == pytest.approx(th["evap"], rel=gtol)
+    assert grad[1] == pytest.approx(th["gamma"], rel=gtol)
 
 
 def test_concurrent_adjoint_equals_serial(torch):
@@ -91,6 +98,23 @@ def trajectory(torch):
 
 def test_trajectory_gradient_matches_oracle_adjoint(trajectory):
     n, steps, p, st0, ctx, g = trajectory
+    J, ref = oadj.trajectory_gradient(n, p, st0, steps)
+    assert g["J"] == pytest.approx(J, rel=1e-9)
+    assert g["evap"] == pytest.approx(ref["evap"], rel=1e-6)
+    assert g["gamma"] == pytest.approx(ref["gamma"], rel=1e-6)
+    assert rel(g["adj0"]["phi"][0].cpu().numpy(), ref["phi_p0"]) < 1e-6
+
+
+def test_trajectory_gradient_on_32_matches_oracle_adjoint(torch):
+    """The checkpointed trajectory gradient on 32 x 32 (three steps,
+    checkpoints every two) against the oracle's adjoint of the same
+    trajectory: J, both parameter gradients and the initial polymer field's
+    gradient."""
+    n, steps = 32, 3
+    p = _params()
+    st0 = inputs.initial_state(n, seed=32)
+    ctx = chnss.Context(chnss.Mesh(n), p)
+    g = gadj.trajectory_gradient(ctx, chnss.state_to_device(st0), steps, checkpoint_every=2)
     J, ref = oadj.trajectory_gradient(n, p, st0, steps)
     assert g["J"] == pytest.approx(J, rel=1e-9)
     assert g["evap"] == pytest.approx(ref["evap"], rel=1e-6)
