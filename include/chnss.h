@@ -125,9 +125,9 @@ typedef struct {
  * at least 4; the coarsest level (n = m 2^k with m odd or m = 2) must have
  * m <= 25 cells per side.  On it the pressure Laplacian of the PCD keeps a
  * dense FP64 inverse (built once by one thread block, (m + 1)^2 rows), as
- * does every block while the level has at most 400 unknowns; larger
+ * does every block while the level has at most 256 unknowns; larger
  * non-singular coarsest levels (the velocity block for m >= 7, the P1 blocks
- * for m >= 20) take 16 Chebyshev-Jacobi steps from zero on [hi/64, hi]
+ * for m >= 17) take 16 Chebyshev-Jacobi steps from zero on [hi/64, hi]
  * instead.  n = 50, 100, 200 (m = 25) are accepted.  Builds the CSR patterns, the element -> CSR gather maps and
  * the transfer operators (host), and uploads them.  Returns CHNSS_ERR_ARG
  * for bad sizes, CHNSS_ERR_OOM / CHNSS_ERR_CUDA on device failures. */

@@ -33,7 +33,7 @@ SMOOTH_DEGREE = 2
 LO_RATIO = 4.0
 VEL_SMOOTH_DEGREE = 4
 VEL_LO_RATIO = 16.0
-COARSE_DENSE_MAX = 400
+COARSE_DENSE_MAX = 256
 COARSE_DEGREE = 16
 COARSE_RATIO = 64.0
 

@@ -132,7 +132,7 @@ constexpr int kMaxSmoothDegree = 16;
 // is the singular pressure Laplacian (constant, built once); otherwise
 // kCoarseDegree Chebyshev-Jacobi steps from zero on [hi / kCoarseRatio, hi]
 // (the non-singular blocks are mass-dominated on coarse meshes).
-constexpr int kCoarseDenseMax = 400;
+constexpr int kCoarseDenseMax = 256;
 constexpr int kCoarseDegree = 16;
 constexpr double kCoarseRatio = 64.0;
 void cheb_coefficients(const double *hi, double ratio, int degree, double *coef, cudaStream_t s);
