@@ -408,6 +408,26 @@ chnss_status chnss3_step(chnss3_ctx_t ctx, const chnss_state *in, chnss_state *o
  * 0: one after the other.  Results are bitwise the same. */
 chnss_status chnss3_set_step_concurrency(chnss3_ctx_t ctx, int on);
 const char *chnss3_last_error(chnss3_ctx_t ctx);
+/* Adjoint of one 3D step: the discrete adjoint of chnss3_step, with the
+ * same contributions as chnss_adjoint_step (transposed solves by FGMRES to a
+ * relative residual of 1e-12 with the forward preconditioners; the
+ * transposed convection derivatives of C(v) and J(w), w = v - sum alpha_i
+ * grad mu_i, the potential Hessian at the degree-7 tetrahedral rule, the
+ * Korteweg load, the evaporation flux and, with mobility_kind 1, the
+ * derivative of K_kappa(phi_i^k)) on the tetrahedra; enclosed or open top.
+ * state_k, state_k1 (the step's output), adj_k1, adj_k (out, overwritten):
+ * DEVICE states of the 3D sizes; velocity adjoints are zero on the no-slip
+ * dofs, the pressure adjoint is zero.  grad_params (HOST, 2 doubles,
+ * accumulated): d/d(evap_rate), d/d(gamma) with gamma scaling the three
+ * mobilities.  info[6] (optional): the transposed solves.  The solves run one
+ * after the other on the context stream, which is synchronised before the
+ * return.  Errors as chnss3_step (text in chnss3_last_error). */
+chnss_status chnss3_adjoint_step(chnss3_ctx_t ctx, const chnss_state *state_k, const chnss_state *state_k1,
+                                 const chnss_state *adj_k1, chnss_state *adj_k, double *grad_params,
+                                 chnss_solve_info *info);
+/* J = int |grad phi_p|^2 = phi_p^T K phi_p of a device polymer field on the
+ * 3D mesh; *J on the host; grad_phi_p (device, optional) = 2 K phi_p. */
+chnss_status chnss3_objective(chnss3_ctx_t ctx, const double *phi_p, double *J, double *grad_phi_p);
 
 /* Mass-matrix solve that allocates nothing.  The paper has no counterpart:
  * this is a service entry point of the library.  It solves M x = rhs for the

@@ -148,6 +148,11 @@ EXPORTS = {
                                    ctypes.POINTER(SolveInfo)]),
     "chnss3_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "chnss3_set_step_concurrency": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "chnss3_adjoint_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.POINTER(State),
+                                           ctypes.POINTER(State), ctypes.POINTER(State),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo)]),
+    "chnss3_objective": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.c_void_p]),
     "chnss3_host_operator": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params), ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_longlong), ctypes.c_void_p, ctypes.c_void_p,
@@ -491,6 +496,31 @@ class Context3:
             msg = load().chnss3_last_error(self._h)
             raise ChnssError(st, msg.decode() if msg else "")
         return state_out, {SYSTEM_NAMES[i]: infos[i].as_dict() for i in range(6)}, st
+
+    def _check3(self, st):
+        if st != 0:
+            msg = load().chnss3_last_error(self._h)
+            raise ChnssError(st, msg.decode() if msg else "")
+
+    def adjoint_step(self, state_k: dict, state_k1: dict, adj_k1: dict, adj_k: dict = None, check: bool = True):
+        """chnss3_adjoint_step: returns (adj_k, [d/d evap_rate, d/d gamma], infos, status)."""
+        if adj_k is None:
+            adj_k = self.new_state()
+        a, b, c, d = (make_state(x, self.N1, self.N2, 3, "device") for x in (state_k, state_k1, adj_k1, adj_k))
+        grad = (ctypes.c_double * 2)(0.0, 0.0)
+        infos = (SolveInfo * 6)()
+        st = load().chnss3_adjoint_step(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d),
+                                        grad, infos)
+        if check:
+            self._check3(st)
+        return adj_k, [grad[0], grad[1]], {SYSTEM_NAMES[i]: infos[i].as_dict() for i in range(6)}, st
+
+    def objective(self, phi_p, grad=None):
+        """J = int |grad phi_p|^2 on the 3D mesh and, if grad is a device array, 2 K phi_p."""
+        J = ctypes.c_double()
+        self._check3(load().chnss3_objective(self._h, _ptr(phi_p, self.N1, "device"), ctypes.byref(J),
+                                             _ptr(grad, self.N1, "device")))
+        return J.value
 
 
 OPS3 = ("M1", "K1", "C1", "CP", "M2", "J2", "KSYM", "B", "P1PROL", "VPROL", "LOADS", "KORTEWEG", "TOP",

@@ -650,6 +650,192 @@ __global__ void k3_loads(Geo3 g, Fields3 f, double *lbuf, double *kbuf) {
   tet_korteweg(c3, vol, gr, G, kbuf + e * 30);
 }
 
+// ---- adjoint (transposed Jacobian) element kernels.  P1 results go to the
+// [E][20] layout of the potential loads (field f, node a at 4 f + a; gathered
+// by the load list), velocity results to the [E][30] Korteweg layout.
+
+// d/dv of y^T C(v) x (P1 x, y): int zeta_k (d_d x) y = (d_d x) vol sum_a y_a
+// r[k][a] -> buf [E][30]
+__global__ void k3_adj_conv_p1(Geo3 g, const double *__restrict__ x, const double *__restrict__ y, double *buf) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 6L * g.n * g.n * g.n) return;
+  double xc[4][3], gr[4][3], gx[3] = {0.0, 0.0, 0.0}, ya[4];
+  int v1[4], v2[10];
+  tet_nodes(g, e, xc, v1, v2);
+  const double vol = tet_geometry(xc, gr);
+  for (int a = 0; a < 4; ++a) {
+    const double xv = x[v1[a]];
+    for (int d = 0; d < 3; ++d) gx[d] += xv * gr[a][d];
+    ya[a] = y[v1[a]];
+  }
+  for (int k = 0; k < 10; ++k) {
+    const double s = vol * (ya[0] * c3.r[k][0] + ya[1] * c3.r[k][1] + ya[2] * c3.r[k][2] + ya[3] * c3.r[k][3]);
+    for (int d = 0; d < 3; ++d) buf[e * 30 + k * 3 + d] = s * gx[d];
+  }
+}
+
+// d/dphi of y^T K_kappa(phi) x, kappa = gamma (phi (1 - phi) + m0): node c of
+// an element gets int gamma (1 - 2 phi_h) psi_c grad x . grad y
+// = vol gamma (grad x . grad y) (1/4 - (sum_a phi_a + phi_c) / 10) -> buf [E][20], slot 0
+__global__ void k3_adj_wstiff(Geo3 g, const double *__restrict__ phi, double gamma, const double *__restrict__ x,
+                              const double *__restrict__ y, double *buf) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 6L * g.n * g.n * g.n) return;
+  double xc[4][3], gr[4][3], gx[3] = {0.0, 0.0, 0.0}, gy[3] = {0.0, 0.0, 0.0}, ph[4], psum = 0.0;
+  int v1[4], v2[10];
+  tet_nodes(g, e, xc, v1, v2);
+  const double vol = tet_geometry(xc, gr);
+  for (int a = 0; a < 4; ++a) {
+    const double xv = x[v1[a]], yv = y[v1[a]];
+    for (int d = 0; d < 3; ++d) {
+      gx[d] += xv * gr[a][d];
+      gy[d] += yv * gr[a][d];
+    }
+    ph[a] = phi[v1[a]];
+    psum += ph[a];
+  }
+  const double s = vol * gamma * (gx[0] * gy[0] + gx[1] * gy[1] + gx[2] * gy[2]);
+  for (int c = 0; c < 4; ++c) buf[e * 20 + c] = s * (0.25 - (psum + ph[c]) / 10.0);
+}
+
+// d/dw of y^T (J(w) (x) I) x (velocities x, y): nodal part int N_k
+// sum_c (d_d x_c) y_c -> bufv [E][30]; the part of the per-element shift
+// (w = v - s) projected on the P1 gradients, (d/ds) . grad psi_a -> bufm [E][20], slot 0
+__global__ void k3_adj_conv_p2(Geo3 g, const double *__restrict__ x, const double *__restrict__ y, double *bufv,
+                               double *bufm) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 6L * g.n * g.n * g.n) return;
+  double xc[4][3], gr[4][3], yk[10][3];
+  int v1[4], v2[10];
+  tet_nodes(g, e, xc, v1, v2);
+  const double vol = tet_geometry(xc, gr);
+  for (int a = 0; a < 10; ++a)
+    for (int c = 0; c < 3; ++c) yk[a][c] = y[3L * v2[a] + c];
+  // acc[k][l] = sum_(a,b) xy[b][a] t[k][l][b][a], accs[l] = sum xy[b][a] s[l][b][a],
+  // xy[b][a] = sum_c x_(b,c) y_(a,c)
+  double acc[10][4], accs[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < 10; ++k)
+#pragma unroll
+    for (int l = 0; l < 4; ++l) acc[k][l] = 0.0;
+  for (int b = 0; b < 10; ++b) {
+    const double x0 = x[3L * v2[b]], x1 = x[3L * v2[b] + 1], x2 = x[3L * v2[b] + 2];
+    for (int a = 0; a < 10; ++a) {
+      const double xy = x0 * yk[a][0] + x1 * yk[a][1] + x2 * yk[a][2];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        accs[l] += xy * c3.s[l][b][a];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) acc[k][l] += xy * c3.t[k][l][b][a];
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 10; ++k)
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      bufv[e * 30 + k * 3 + d] =
+          vol * (gr[0][d] * acc[k][0] + gr[1][d] * acc[k][1] + gr[2][d] * acc[k][2] + gr[3][d] * acc[k][3]);
+  double sb[3];
+  for (int d = 0; d < 3; ++d)
+    sb[d] = -vol * (gr[0][d] * accs[0] + gr[1][d] * accs[1] + gr[2][d] * accs[2] + gr[3][d] * accs[3]);
+  for (int a = 0; a < 4; ++a) bufm[e * 20 + a] = sb[0] * gr[a][0] + sb[1] * gr[a][1] + sb[2] * gr[a][2];
+}
+
+struct LoadWeights3 {
+  const double *z[5];   // adjoint weights of the loads of df/dphi_p, _N, _s, _a, df/dPhi (null: zero)
+};
+
+// gradient of sum_i z_i^T F_i with respect to (phi_p, phi_N, phi_s, Phi):
+// int (sum_i d g_i / d var) z_i psi_a with the Hessian at the degree-7 rule,
+// d/dphi_j = H_ij - H_ia (phi_a = 1 - sum phi) -> buf [E][20] (field f, node a)
+__global__ void k3_adj_loads(Geo3 g, Fields3 f, LoadWeights3 lw, double *buf) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 6L * g.n * g.n * g.n) return;
+  double xc[4][3], gr[4][3], fl[4][4], zz[5][4];
+  int v1[4], v2[10];
+  tet_nodes(g, e, xc, v1, v2);
+  const double vol = tet_geometry(xc, gr);
+  for (int a = 0; a < 4; ++a) {
+    for (int i = 0; i < 3; ++i) fl[i][a] = f.phi[i][v1[a]];
+    fl[3][a] = f.Phi[v1[a]];
+    for (int i = 0; i < 5; ++i) zz[i][a] = lw.z[i] ? lw.z[i][v1[a]] : 0.0;
+  }
+  double acc[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int a = 0; a < 4; ++a) acc[i][a] = 0.0;
+  for (int q = 0; q < kLoadPts3; ++q) {
+    const double *lq = c3.ql[q];
+    double v[4], z[5];
+    for (int i = 0; i < 4; ++i) v[i] = lq[0] * fl[i][0] + lq[1] * fl[i][1] + lq[2] * fl[i][2] + lq[3] * fl[i][3];
+    for (int i = 0; i < 5; ++i) z[i] = lq[0] * zz[i][0] + lq[1] * zz[i][1] + lq[2] * zz[i][2] + lq[3] * zz[i][3];
+    double H[5][5];
+    potential_hessian3(v[0], v[1], v[2], v[3], H);
+    double gj[4];
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int i = 0; i < 5; ++i) s += z[i] * (H[i][j] - H[i][3]);
+      gj[j] = s;
+    }
+    gj[3] = z[0] * H[0][4] + z[1] * H[1][4] + z[2] * H[2][4] + z[3] * H[3][4] + z[4] * H[4][4];
+    for (int i = 0; i < 4; ++i) {
+      const double wg = c3.qw[q] * gj[i];
+      for (int a = 0; a < 4; ++a) acc[i][a] += wg * lq[a];
+    }
+  }
+  for (int i = 0; i < 4; ++i)
+    for (int a = 0; a < 4; ++a) buf[e * 20 + i * 4 + a] = vol * acc[i][a];
+}
+
+// gradient of y^T G (Korteweg load) with respect to (phi_p, phi_N, phi_s,
+// Phi): grad psi_m . (Y + Y^T) u, u = beta_j grad phi_j - beta_a grad phi_a
+// (beta_v grad Phi for Phi), Y[c][b] = int d_b y_c -> buf [E][20]
+__global__ void k3_adj_korteweg(Geo3 g, Fields3 f, const double *__restrict__ y, double *buf) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 6L * g.n * g.n * g.n) return;
+  double xc[4][3], gr[4][3];
+  int v1[4], v2[10];
+  tet_nodes(g, e, xc, v1, v2);
+  const double vol = tet_geometry(xc, gr);
+  double Y[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int a = 0; a < 10; ++a) {
+    double da[3] = {0.0, 0.0, 0.0};   // int grad N_a / vol
+    for (int l = 0; l < 4; ++l)
+      for (int b = 0; b < 3; ++b) da[b] += c3.d[a][l] * gr[l][b];
+    for (int c = 0; c < 3; ++c) {
+      const double yc = y[3L * v2[a] + c];
+      for (int b = 0; b < 3; ++b) Y[c][b] += vol * yc * da[b];
+    }
+  }
+  double S[3][3];
+  for (int c = 0; c < 3; ++c)
+    for (int b = 0; b < 3; ++b) S[c][b] = Y[c][b] + Y[b][c];
+  double grd[5][3] = {};
+  for (int a = 0; a < 4; ++a)
+    for (int d = 0; d < 3; ++d) {
+      for (int i = 0; i < 3; ++i) grd[i][d] += f.phi[i][v1[a]] * gr[a][d];
+      grd[4][d] += f.Phi[v1[a]] * gr[a][d];
+    }
+  for (int d = 0; d < 3; ++d) grd[3][d] = -(grd[0][d] + grd[1][d] + grd[2][d]);
+  for (int fi = 0; fi < 4; ++fi) {
+    double u[3];
+    for (int d = 0; d < 3; ++d)
+      u[d] = fi < 3 ? f.beta[fi] * grd[fi][d] - f.beta[3] * grd[3][d] : f.beta_v * grd[4][d];
+    double su[3];
+    for (int c = 0; c < 3; ++c) su[c] = S[c][0] * u[0] + S[c][1] * u[1] + S[c][2] * u[2];
+    for (int m = 0; m < 4; ++m) buf[e * 20 + fi * 4 + m] = gr[m][0] * su[0] + gr[m][1] * su[1] + gr[m][2] * su[2];
+  }
+}
+
+__global__ void k3_add_at(double *x, int idx, double v) { x[idx] += v; }
+
+// out = lp - m sum(lp) / vol (transpose of the zero-mean pressure shift)
+__global__ void k3_mean_shift_T(int N1, const double *lp, const double *m, const double *sum, double vol,
+                                double *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N1) out[i] = lp[i] - m[i] * (*sum) / vol;
+}
+
 // coarse P1 node (a, b, c) <- fine (2a, 2b, 2c); coarse P2 node (A, B, C) <-
 // fine P2 node (2A, 2B, 2C), three components
 __global__ void k3_inject(int nf, int vel, const double *fine, double *coarse) {
@@ -769,6 +955,11 @@ struct chnss3_ctx {
   cudaStream_t bodyq[3] = {nullptr, nullptr, nullptr};
   cudaGraphExec_t gexec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double *pin[5] = {}, *pout[5] = {};
+  // adjoint step (allocated on first use): transposed fine operators, M 1, work
+  double *LsT = nullptr, *ACsT = nullptr, *AsT = nullptr, *mvec = nullptr;
+  double *arhs = nullptr, *ay = nullptr, *alam = nullptr, *az = nullptr, *atmp = nullptr, *atv = nullptr;
+  double *alw[5] = {};
+  double *adots = nullptr;                      // device scalars of the parameter gradients
   std::string err;
   ~chnss3_ctx() {
     for (cudaGraphExec_t g : gexec)
@@ -1449,6 +1640,233 @@ chnss_status step3(chnss3_ctx *c, const chnss_state *in, chnss_state *out, chnss
   return CHNSS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint of the 3D step: for each solve x = A(u)^-1 b(u), given the adjoint
+// xbar of its solution, y = A^-T xbar (FGMRES on the transposed operator,
+// preconditioned by the forward block preconditioner), then
+// ubar += (db/du)^T y - (d(A(u) x)/du)^T y (the k3_adj_* element kernels).
+// The solves run one after the other on the context stream.
+constexpr double kAdjointRtol3 = 1e-12;
+
+struct CH3OpT : LinearOperator {   // [[L^T, tau g K], [tau K_kappa, -(tau g / b) M]] (K, K_kappa symmetric)
+  chnss3_ctx *c;
+  int sp;
+  CH3OpT(chnss3_ctx *c_, int sp_) : c(c_), sp(sp_) {}
+  long size() const override { return 2 * c->lv[0].N1; }
+  void apply(const double *x, double *y, cudaStream_t s) override {
+    const auto &p = c->p;
+    const double tau = p.tau, g = p.gamma[sp], b = p.beta[sp];
+    if (p.mobility_kind != 0)
+      spmv_sell_ch(c->lv[0].p1, c->LsT, c->Kks[sp], c->Ks, c->Ms, tau * g, tau, -tau * g / b, x, y, s);
+    else
+      spmv_sell_ch(c->lv[0].p1, c->LsT, c->Ks, nullptr, c->Ms, tau * g, tau * g, -tau * g / b, x, y, s);
+  }
+  void precond(const double *r, double *z, cudaStream_t s) override { run_prec3(c, sp, 2 * c->lv[0].N1, r, z, s); }
+};
+
+struct AC3OpT : LinearOperator {
+  chnss3_ctx *c;
+  explicit AC3OpT(chnss3_ctx *c_) : c(c_) {}
+  long size() const override { return c->lv[0].N1; }
+  void apply(const double *x, double *y, cudaStream_t s) override {
+    SpmvArgs none;
+    spmv_sell<double>(c->lv[0].p1, c->ACsT, 1, x, y, SPMV_PLAIN, none, s);
+  }
+  void precond(const double *r, double *z, cudaStream_t s) override { run_prec3(c, 3, c->lv[0].N1, r, z, s); }
+};
+
+struct NS3OpT : LinearOperator {   // [[A^T, B^T], [B, 0]]
+  chnss3_ctx *c;
+  explicit NS3OpT(chnss3_ctx *c_) : c(c_) {}
+  long size() const override { return 3 * c->lv[0].N2 + c->lv[0].N1; }
+  void apply(const double *x, double *y, cudaStream_t s) override {
+    const long nv = 3 * c->lv[0].N2;
+    SpmvArgs none;
+    spmv_sell<double>(c->lv[0].pv, c->AsT, 1, x, y, SPMV_PLAIN, none, s);
+    spmv_sell<double>(c->pbt, c->Bts, 1, x + nv, y, SPMV_ADD, none, s);
+    spmv_sell<double>(c->pb, c->Bs, 1, x, y + nv, SPMV_PLAIN, none, s);
+  }
+  void precond(const double *r, double *z, cudaStream_t s) override {
+    run_prec3(c, 4, 3 * c->lv[0].N2 + c->lv[0].N1, r, z, s);
+  }
+};
+
+void adjoint_alloc3(chnss3_ctx *c) {
+  if (c->LsT) return;
+  Arena &ar = c->ar;
+  const Level3 &F = c->lv[0];
+  const long N1 = F.N1, nv = 3 * F.N2;
+  c->LsT = ar.alloc<double>(F.p1.sell.nent);
+  c->ACsT = ar.alloc<double>(F.p1.sell.nent);
+  c->AsT = ar.alloc<double>(F.pv.sell.nent);
+  c->mvec = ar.alloc<double>(N1);
+  c->arhs = ar.alloc<double>(nv + N1);
+  c->ay = ar.alloc<double>(nv + N1);
+  c->alam = ar.alloc<double>(3 * N1);
+  c->az = ar.alloc<double>(N1);
+  c->atmp = ar.alloc<double>(N1);
+  c->atv = ar.alloc<double>(nv);
+  for (double *&w : c->alw) w = ar.alloc<double>(N1);
+  c->adots = ar.alloc<double>(32);
+  vec_fill(N1, 1.0, c->atmp, c->s);
+  SpmvArgs none;
+  spmv_csr<double>(F.p1, F.M1, 1, c->atmp, c->mvec, SPMV_PLAIN, none, c->s);
+}
+
+chnss_status adjoint_step3(chnss3_ctx *c, const chnss_state *stk, const chnss_state *st1, const chnss_state *lam,
+                           chnss_state *out, double *grad, chnss_solve_info *inf) {
+  const auto &p = c->p;
+  const bool var = p.mobility_kind != 0;
+  adjoint_alloc3(c);
+  assemble3(c, stk);
+  cudaStream_t s = c->s;
+  const Level3 &F = c->lv[0];
+  const int N1 = (int)F.N1;
+  const long nv = 3 * F.N2, E = F.E;
+  const double tau = p.tau;
+  SpmvArgs none;
+  sell_gather_transposed(F.p1.sell, 1, F.L, c->LsT, s);
+  sell_gather_transposed(F.p1.sell, 1, F.AC, c->ACsT, s);
+  sell_gather_transposed(F.pv.sell, 1, F.A, c->AsT, s);
+  for (int k = 0; k < 3; ++k) vec_fill(N1, 0.0, out->phi[k], s);
+  for (int k = 0; k < 4; ++k) vec_fill(N1, 0.0, out->mu[k], s);
+  vec_fill(N1, 0.0, out->Phi_v, s);
+  vec_fill(nv, 0.0, out->v, s);
+  vec_fill(N1, 0.0, out->p, s);
+  vec_fill(32, 0.0, c->adots, s);
+  double *D = c->adots;
+  Fields3 fk{};
+  for (int i = 0; i < 3; ++i) fk.phi[i] = stk->phi[i];
+  fk.Phi = stk->Phi_v;
+  for (int i = 0; i < 4; ++i) fk.beta[i] = p.beta[i];
+  fk.beta_v = p.beta_v;
+  // element scratch (the assembly's buffer, free once assemble3 has run)
+  double *bufP = c->ebuf, *bufV = c->ebuf + 20 * E;
+  auto gather_fields = [&](const double *buf, double *const dst[4]) {   // [E][20] -> four P1 fields, added
+    for (int f = 0; f < 4; ++f) launch_gather(c->gl, 1, buf + 4 * f, 1.0, dst[f], 1.0, dst[f], s);
+  };
+  double *const phiPhi[4] = {out->phi[0], out->phi[1], out->phi[2], out->Phi_v};
+  chnss_status worst = CHNSS_OK;
+  auto keep = [&](chnss_status st) { if (worst == CHNSS_OK) worst = st; };
+  // ---- Oseen: [[A^T, B^T], [B, 0]] y = (masked lambda_v, lambda_p) ----------
+  vec_copy(nv, lam->v, c->arhs, s);
+  k3_mask<<<nb3(nv), kTPB3, 0, s>>>(nv, c->bnd, c->arhs);
+  CHNSS_LAUNCH_CK();
+  if (c->top_bc == 0) {   // transpose of the zero-mean pressure shift (|box| = 1)
+    vsum<double>(N1, lam->p, c->sum, c->partial, s);
+    k3_mean_shift_T<<<nb3(N1), kTPB3, 0, s>>>(N1, lam->p, c->mvec, c->sum, 1.0, c->arhs + nv);
+    CHNSS_LAUNCH_CK();
+  } else {                // open top: the outflow fixes the pressure level, no shift
+    vec_copy(N1, lam->p, c->arhs + nv, s);
+  }
+  {
+    NS3OpT op(c);
+    keep(fgmres(op, c->arhs, c->ay, kAdjointRtol3, 0.0, p.maxit, c->kw, &inf[5], s));
+  }
+  const double *yv = c->ay;
+  spmv_csr<double>(F.pv, c->Mv, 1, yv, c->atv, SPMV_PLAIN, none, s);
+  vec_axpby(nv, 1.0 / tau, c->atv, 1.0, out->v, s);                          // (M_v / tau)^T y_v
+  k3_adj_korteweg<<<nb3(E), kTPB3, 0, s>>>(F.geo, fk, yv, bufP);
+  CHNSS_LAUNCH_CK();
+  gather_fields(bufP, phiPhi);
+  vec_copy(nv, st1->v, c->atv, s);                                            // J(w) acts on v^(k+1), no-slip dofs zero
+  k3_mask<<<nb3(nv), kTPB3, 0, s>>>(nv, c->bnd, c->atv);
+  CHNSS_LAUNCH_CK();
+  k3_adj_conv_p2<<<nb3(E), kTPB3, 0, s>>>(F.geo, c->atv, yv, bufV, bufP);
+  CHNSS_LAUNCH_CK();
+  launch_gather(c->gk, 3, bufV, -1.0, out->v, 1.0, out->v, s);               // - (d J(w) x / dv)^T y
+  launch_gather(c->gl, 1, bufP, 1.0, nullptr, 0.0, c->atmp, s);
+  for (int i = 0; i < 4; ++i) vec_axpby(N1, -p.alpha[i], c->atmp, 1.0, out->mu[i], s);   // ds/dmu_i = alpha_i grad psi
+  // ---- air potential: M z = lambda_mu_a --------------------------------------
+  keep(pcg(F.p1, F.M1, c->dinvM, lam->mu[3], c->az, kAdjointRtol3, 1000, c->kwc, &inf[4], s));
+  spmv_csr<double>(F.p1, F.K1, 1, c->az, c->atmp, SPMV_PLAIN, none, s);
+  for (int i = 0; i < 3; ++i) {   // mu_a^(k+1) depends on phi^(k+1) through beta_a K (1 - sum phi)
+    vec_copy(N1, lam->phi[i], c->alam + (long)i * N1, s);
+    vec_axpby(N1, -p.beta[3], c->atmp, 1.0, c->alam + (long)i * N1, s);
+  }
+  vec_copy(N1, c->az, c->alw[3], s);
+  dot<double>(N1, c->top, c->az, D + 0, c->partial, s);
+  // ---- Allen-Cahn -------------------------------------------------------------
+  {
+    AC3OpT op(c);
+    keep(fgmres(op, lam->Phi_v, c->ay, kAdjointRtol3, 0.0, p.maxit, c->kwa, &inf[3], s));
+  }
+  spmv_csr<double>(F.p1, F.M1, 1, c->ay, c->atmp, SPMV_PLAIN, none, s);
+  vec_axpby(N1, 1.0, c->atmp, 1.0, out->Phi_v, s);
+  vec_fill(N1, 0.0, c->alw[4], s);
+  vec_axpby(N1, -tau * p.gamma_v, c->ay, 0.0, c->alw[4], s);
+  k3_adj_conv_p1<<<nb3(E), kTPB3, 0, s>>>(F.geo, st1->Phi_v, c->ay, bufV);
+  CHNSS_LAUNCH_CK();
+  launch_gather(c->gk, 3, bufV, -tau, out->v, 1.0, out->v, s);
+  dot<double>(N1, c->top, c->ay, D + 1, c->partial, s);
+  // ---- Cahn-Hilliard, three species ------------------------------------------
+  for (int i = 0; i < 3; ++i) {
+    vec_copy(N1, c->alam + (long)i * N1, c->arhs, s);
+    vec_copy(N1, lam->mu[i], c->arhs + N1, s);
+    {
+      CH3OpT op(c, i);
+      keep(fgmres(op, c->arhs, c->ay, kAdjointRtol3, 0.0, p.maxit, c->kwc, &inf[i], s));
+    }
+    const double *y1 = c->ay, *y2 = c->ay + N1;
+    const double cc = tau * p.gamma[i] / p.beta[i];
+    spmv_csr<double>(F.p1, F.M1, 1, y1, c->atmp, SPMV_PLAIN, none, s);
+    vec_axpby(N1, 1.0, c->atmp, 1.0, out->phi[i], s);
+    if (var) {   // - tau (d K_kappa(phi_i^k) / d phi_i)^T (y1, mu_i^(k+1))
+      k3_adj_wstiff<<<nb3(E), kTPB3, 0, s>>>(F.geo, stk->phi[i], p.gamma[i], st1->mu[i], y1, bufP);
+      CHNSS_LAUNCH_CK();
+      launch_gather(c->gl, 1, bufP, -tau, out->phi[i], 1.0, out->phi[i], s);
+    }
+    vec_fill(N1, 0.0, c->alw[i], s);
+    vec_axpby(N1, -cc, y2, 0.0, c->alw[i], s);
+    k3_adj_conv_p1<<<nb3(E), kTPB3, 0, s>>>(F.geo, st1->phi[i], y1, bufV);
+    CHNSS_LAUNCH_CK();
+    launch_gather(c->gk, 3, bufV, -tau, out->v, 1.0, out->v, s);
+    double *d = D + 4 + 5 * i;
+    dot<double>(N1, c->loads + (long)i * N1, y2, d + 0, c->partial, s);        // F_i . y2
+    dot<double>(N1, c->top, y2, d + 1, c->partial, s);                          // t . y2
+    // y1 . K mu' (constant mobility) or y1 . K_kappa mu' (divided by gamma_i on the host)
+    spmv_csr<double>(F.p1, var ? F.Kk[i] : F.K1, 1, st1->mu[i], c->atmp, SPMV_PLAIN, none, s);
+    dot<double>(N1, y1, c->atmp, d + 2, c->partial, s);
+    spmv_csr<double>(F.p1, F.K1, 1, st1->phi[i], c->atmp, SPMV_PLAIN, none, s);
+    dot<double>(N1, y2, c->atmp, d + 3, c->partial, s);                         // y2 . K phi'
+    spmv_csr<double>(F.p1, F.M1, 1, st1->mu[i], c->atmp, SPMV_PLAIN, none, s);
+    dot<double>(N1, y2, c->atmp, d + 4, c->partial, s);                         // y2 . M mu'
+  }
+  // ---- potential loads ---------------------------------------------------------
+  LoadWeights3 lw;
+  for (int i = 0; i < 5; ++i) lw.z[i] = c->alw[i];
+  k3_adj_loads<<<nb3(E), kTPB3, 0, s>>>(F.geo, fk, lw, bufP);
+  CHNSS_LAUNCH_CK();
+  gather_fields(bufP, phiPhi);
+  // ---- parameter gradients and the evaporation flux ------------------------------
+  double h[24], phis_ref = 0.0;
+  CHNSS_CK(cudaMemcpyAsync(h, D, 24 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CHNSS_CK(cudaMemcpyAsync(&phis_ref, stk->phi[2] + c->ref, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CHNSS_CK(cudaStreamSynchronize(s));
+  const double j_out = p.evap_rate * (phis_ref - p.phi_s_inf);
+  double jbar = p.beta[3] * h[0] + (p.ac_top_flux ? tau * p.delta_v * h[1] : 0.0);
+  double gbar = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    const double *d = h + 4 + 5 * i;
+    const double b_i = p.beta[i];
+    const double cc = tau * p.gamma[i] / b_i;
+    if (i == 2) jbar += cc * b_i * d[1];                                      // f_s = F_s - beta_s j t
+    const double fy = d[0] - (i == 2 ? b_i * j_out * d[1] : 0.0);
+    const double k2 = var ? d[2] / p.gamma[i] : d[2];   // tau K_kappa = gamma_i x (gamma-free matrix)
+    gbar += -(tau / b_i) * fy - tau * k2 - (tau * d[3] - (tau / b_i) * d[4]);
+  }
+  k3_add_at<<<1, 1, 0, s>>>(out->phi[2], c->ref, jbar * p.evap_rate);
+  CHNSS_LAUNCH_CK();
+  k3_mask<<<nb3(nv), kTPB3, 0, s>>>(nv, c->bnd, out->v);
+  CHNSS_LAUNCH_CK();
+  CHNSS_CK(cudaStreamSynchronize(s));
+  if (grad) {
+    grad[0] += jbar * (phis_ref - p.phi_s_inf);
+    grad[1] += gbar;
+  }
+  return worst;
+}
+
 }  // namespace
 }  // namespace chnss
 
@@ -1534,6 +1952,58 @@ extern "C" chnss_status chnss3_step(chnss3_ctx_t ctx, const chnss_state *in, chn
     const chnss_status st = step3(ctx, in, out, info ? info : loc);
     if (st != CHNSS_OK) ctx->err = "a solve of the 3D step did not converge cleanly";
     return st;
+  } catch (const Error &e) {
+    ctx->err = e.msg;
+    return e.status;
+  }
+}
+
+extern "C" chnss_status chnss3_adjoint_step(chnss3_ctx_t ctx, const chnss_state *state_k,
+                                            const chnss_state *state_k1, const chnss_state *adj_k1,
+                                            chnss_state *adj_k, double *grad_params, chnss_solve_info *info) {
+  using namespace chnss;
+  if (!ctx) {
+    set_global_error("null context");
+    return CHNSS_ERR_ARG;
+  }
+  try {
+    const chnss_state *states[4] = {state_k, state_k1, adj_k1, adj_k};
+    for (const chnss_state *st : states) {
+      if (!st || !st->Phi_v || !st->v || !st->p) throw Error{CHNSS_ERR_ARG, "null state"};
+      for (int k = 0; k < 3; ++k) if (!st->phi[k]) throw Error{CHNSS_ERR_ARG, "null phi pointer"};
+      for (int k = 0; k < 4; ++k) if (!st->mu[k]) throw Error{CHNSS_ERR_ARG, "null mu pointer"};
+    }
+    chnss_solve_info loc[6];
+    const chnss_status st = adjoint_step3(ctx, state_k, state_k1, adj_k1, adj_k, grad_params, info ? info : loc);
+    if (st != CHNSS_OK) ctx->err = "a transposed solve of the 3D adjoint step did not converge cleanly";
+    return st;
+  } catch (const Error &e) {
+    ctx->err = e.msg;
+    return e.status;
+  }
+}
+
+extern "C" chnss_status chnss3_objective(chnss3_ctx_t ctx, const double *phi_p, double *J, double *grad_phi_p) {
+  using namespace chnss;
+  if (!ctx) {
+    set_global_error("null context");
+    return CHNSS_ERR_ARG;
+  }
+  try {
+    if (!phi_p || !J) throw Error{CHNSS_ERR_ARG, "null phi_p or J"};
+    adjoint_alloc3(ctx);
+    const Level3 &F = ctx->lv[0];
+    const long N1 = F.N1;
+    SpmvArgs none;
+    spmv_csr<double>(F.p1, F.K1, 1, phi_p, ctx->atmp, SPMV_PLAIN, none, ctx->s);
+    dot<double>(N1, phi_p, ctx->atmp, ctx->adots + 30, ctx->partial, ctx->s);
+    if (grad_phi_p) {
+      vec_fill(N1, 0.0, grad_phi_p, ctx->s);
+      vec_axpby(N1, 2.0, ctx->atmp, 0.0, grad_phi_p, ctx->s);
+    }
+    CHNSS_CK(cudaMemcpyAsync(J, ctx->adots + 30, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    CHNSS_CK(cudaStreamSynchronize(ctx->s));
+    return CHNSS_OK;
   } catch (const Error &e) {
     ctx->err = e.msg;
     return e.status;

@@ -160,6 +160,29 @@ __host__ __device__ inline void potential_partials3(double p, double nn, double 
   out[4] = dip * (gas - liq);
 }
 
+// Second derivatives of the same free energy in (phi_p, phi_N, phi_s, phi_a,
+// Phi), un-reduced, at phi_a = 1 - sum phi: H[i][j] (symmetric)
+__host__ __device__ inline void potential_hessian3(double p, double nn, double s, double V, double H[5][5]) {
+  const double a = 1.0 - p - nn - s;
+  const double ip = V * V * (3.0 - 2.0 * V), dip = 6.0 * V * (1.0 - V), ddip = 6.0 - 12.0 * V;
+  const double liq = 3.5 * p * p * nn * nn + 0.3 * s * s + 0.3 * a * a - 10.0 * s * a;
+  const double gas = 3.5 * p * p + 3.5 * nn * nn + 2.0 * s * s + 0.1 * a * a;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) H[i][j] = 0.0;
+  H[0][0] = (1.0 - ip) * 7.0 * nn * nn + 7.0 * ip;
+  H[0][1] = H[1][0] = (1.0 - ip) * 14.0 * p * nn;
+  H[1][1] = (1.0 - ip) * 7.0 * p * p + 7.0 * ip;
+  H[2][2] = (1.0 - ip) * 0.6 + 4.0 * ip;
+  H[2][3] = H[3][2] = -(1.0 - ip) * 10.0;
+  H[3][3] = (1.0 - ip) * 0.6 + 0.2 * ip;
+  // d/dPhi of the first partials: dip (gas_i - liq_i)
+  H[0][4] = H[4][0] = dip * 7.0 * p * (1.0 - nn * nn);
+  H[1][4] = H[4][1] = dip * 7.0 * nn * (1.0 - p * p);
+  H[2][4] = H[4][2] = dip * (3.4 * s + 10.0 * a);
+  H[3][4] = H[4][3] = dip * (10.0 * s - 0.4 * a);
+  H[4][4] = ddip * (gas - liq);
+}
+
 // Potential loads int df/dfield psi_a of one element: fields[f][k] = nodal
 // values of phi_p, phi_N, phi_s, Phi; out[f * 4 + a] for the five partials
 __host__ __device__ inline void tet_loads(const Tet3Ref &R, double vol, const double fields[4][4], double out[20]) {
