@@ -57,6 +57,16 @@ void spmv_sell(const Pattern &P, const T *sval, int ncomp, const T *u, T *out, S
 template <typename T>
 void spmv_sell_bsr2(const Pattern &P, const T *sval, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
                     cudaStream_t s);
+// 3x3-block SELL (3D velocity operators on the P2 node pattern, vectors
+// interleaved): value m = 3 r + d of SELL entry e at 9 (e - e % 32) + 32 m +
+// e % 32; map9 holds the CSR position of every such value (-1: padding)
+template <typename Tout>
+void sell_gather9(long nent, const int *map9, const double *csr_vals, Tout *out, cudaStream_t s);
+template <typename T>
+void spmv_sell_bsr3(const Pattern &P, const T *sval, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
+                    cudaStream_t s);
+void spmv_sell_bsr3(const Pattern &P, const __nv_bfloat16 *sval, const float *u, float *out, SpmvMode mode,
+                    const SpmvArgs &a, cudaStream_t s);
 // nr (1..3) vectors through one scalar matrix with rows of at most 8 entries;
 // each output is bitwise the single-vector result (same per-row order).
 template <typename T>

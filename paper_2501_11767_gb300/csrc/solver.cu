@@ -134,6 +134,8 @@ void MGHier<T>::init(Arena &ar, int kind_, bool singular_, const std::vector<con
   val64 = vals;
   tr = trs;
   if (bf16 && !std::is_same<T, float>::value) throw Error{CHNSS_ERR_ARG, "BF16 values need FP32 vectors"};
+  if (kind == 2 && ((int)bpat.size() != nl || (int)bmap.size() != nl))
+    throw Error{CHNSS_ERR_ARG, "3x3-block levels need a node pattern and value map per level"};
   n.resize(nl);
   val.resize(nl);
   val16.assign(nl, nullptr);
@@ -145,9 +147,9 @@ void MGHier<T>::init(Arena &ar, int kind_, bool singular_, const std::vector<con
   hi.resize(nl);
   coef.resize(nl);
   for (int l = 0; l < nl; ++l) {
-    const long nu = (kind == 0 ? 1L : 2L) * pat[l]->nrows;
+    const long nu = (kind == 1 ? 2L : 1L) * pat[l]->nrows;
     n[l] = nu;
-    const long nv = (kind == 0 ? 1L : 4L) * pat[l]->sell.nent;   // SELL order
+    const long nv = sell_values(l);   // SELL order
     if (bf16) {
       val[l] = nullptr;
       val16[l] = ar.alloc<__nv_bfloat16>(nv);
@@ -240,16 +242,29 @@ TailDesc<T> *MGHier<T>::make_tail(Arena &ar, const std::vector<MultiPtr<T>> &X, 
 }
 
 template <typename T>
+long MGHier<T>::sell_values(int l) const {
+  if (kind == 2) return 9L * bpat[l]->sell.nent;
+  return (kind == 0 ? 1L : 4L) * pat[l]->sell.nent;
+}
+
+template <typename T>
+template <typename VT>
+void MGHier<T>::gather_values(int l, VT *out, cudaStream_t s) const {
+  if (kind == 2) sell_gather9<VT>(bpat[l]->sell.nent, bmap[l], val64[l], out, s);
+  else sell_gather<VT>(pat[l]->sell, kind == 0 ? 1 : 4, val64[l], out, s);
+}
+
+template <typename T>
 void MGHier<T>::setup(cudaStream_t s) {
   for (int l = 0; l < nl; ++l) {
-    if (bf16) sell_gather<__nv_bfloat16>(pat[l]->sell, kind == 0 ? 1 : 4, val64[l], val16[l], s);
-    else sell_gather<T>(pat[l]->sell, kind == 0 ? 1 : 4, val64[l], val[l], s);
-    if (l == 0 && val0_64) sell_gather<double>(pat[0]->sell, kind == 0 ? 1 : 4, val64[0], val0_64, s);
+    if (bf16) gather_values<__nv_bfloat16>(l, val16[l], s);
+    else gather_values<T>(l, val[l], s);
+    if (l == 0 && val0_64) gather_values<double>(0, val0_64, s);
     if (l == nl - 1 && !coarse_iter) break;
-    if (kind == 0)
-      jacobi_csr<T>(*pat[l], val64[l], diag[l], dinv[l], hi[l], partial, s);
-    else
+    if (kind == 1)
       jacobi_bsr2<T>(*pat[l], val64[l], diag[l], dinv[l], hi[l], partial, s);
+    else
+      jacobi_csr<T>(*pat[l], val64[l], diag[l], dinv[l], hi[l], partial, s);
     if (l == nl - 1)
       cheb_coefficients(hi[l], kCoarseRatio, kCoarseDegree, coef[l], s);
     else
@@ -257,10 +272,10 @@ void MGHier<T>::setup(cudaStream_t s) {
   }
   if (coarse_iter) return;
   const int L = nl - 1;
-  if (kind == 0)
-    coarse_dense_csr(*pat[L], val64[L], singular ? 1.0 : 0.0, dense, s);
-  else
+  if (kind == 1)
     coarse_dense_bsr2(*pat[L], val64[L], dense, s);
+  else
+    coarse_dense_csr(*pat[L], val64[L], singular ? 1.0 : 0.0, dense, s);
   dense_invert(nc, dense, cinv, status, s);
 }
 
@@ -271,8 +286,11 @@ void MGHier<T>::op(int l, const T *u, T *out, SpmvMode mode, const SpmvArgs &a, 
   const int tk = timed ? prof->start(k, s) : -1;
   spmv_level(l, u, out, mode, a, s);
   if (timed)
-    prof->stop(k, tk, s, spmv_bytes(pat[l]->nrows, pat[l]->nnz, kind == 0 ? 1 : 4, n[l], bf16 ? 2 : sizeof(T), sizeof(T),
-                                mode, a.w != nullptr, pat[l]->sell.stencil != 0));
+    prof->stop(k, tk, s,
+               kind == 2 ? spmv_bytes(bpat[l]->nrows, bpat[l]->nnz, 9, n[l], bf16 ? 2 : sizeof(T), sizeof(T), mode,
+                                      a.w != nullptr, false)
+                         : spmv_bytes(pat[l]->nrows, pat[l]->nnz, kind == 0 ? 1 : 4, n[l], bf16 ? 2 : sizeof(T),
+                                      sizeof(T), mode, a.w != nullptr, pat[l]->sell.stencil != 0));
 }
 
 template <typename T>
@@ -280,14 +298,17 @@ void MGHier<T>::spmv_level(int l, const T *u, T *out, SpmvMode mode, const SpmvA
   if constexpr (std::is_same<T, float>::value) {
     if (bf16) {
       if (kind == 0) spmv_sell(*pat[l], val16[l], 1, u, out, mode, a, s);
-      else spmv_sell_bsr2(*pat[l], val16[l], u, out, mode, a, s);
+      else if (kind == 1) spmv_sell_bsr2(*pat[l], val16[l], u, out, mode, a, s);
+      else spmv_sell_bsr3(*bpat[l], val16[l], u, out, mode, a, s);
       return;
     }
   }
   if (kind == 0)
     spmv_sell<T>(*pat[l], val[l], 1, u, out, mode, a, s);
-  else
+  else if (kind == 1)
     spmv_sell_bsr2<T>(*pat[l], val[l], u, out, mode, a, s);
+  else
+    spmv_sell_bsr3<T>(*bpat[l], val[l], u, out, mode, a, s);
 }
 
 template <typename T>
@@ -306,7 +327,7 @@ void MGHier<T>::vcycle(int l, cudaStream_t s) {
     dense_apply<T>(nc, cinv, b[l], x[l], s);
     return;
   }
-  const int nc_ = kind == 0 ? 1 : 2;
+  const int nc_ = kind == 1 ? 2 : 1;   // transfers per node (BSR2) or per dof
   SpmvArgs a;
   a.b = b[l];
   a.dinv = dinv[l];
@@ -416,7 +437,7 @@ void MGHier<T>::enable_inner(Arena &ar, double rtol, int maxit, cudaStream_t bod
   acc = ar.alloc<double>(n[0]);
   if (!std::is_same<T, double>::value) {
     r64 = ar.alloc<double>(n[0]);
-    val0_64 = ar.alloc<double>((kind == 0 ? 1L : 4L) * pat[0]->sell.nent);
+    val0_64 = ar.alloc<double>(sell_values(0));
   }
   ictl = ar.alloc<double>(8);
   iit = ar.alloc<int>(1);
@@ -458,7 +479,8 @@ void MGHier<T>::inner_residual(cudaStream_t s) {
     dot<double>(n[0], b[0], b[0], ictl + 1, ipartial, s);
   } else {
     if (kind == 0) spmv_sell<double>(*pat[0], val0_64, 1, acc, r64, SPMV_RES, a, s);
-    else spmv_sell_bsr2<double>(*pat[0], val0_64, acc, r64, SPMV_RES, a, s);
+    else if (kind == 1) spmv_sell_bsr2<double>(*pat[0], val0_64, acc, r64, SPMV_RES, a, s);
+    else spmv_sell_bsr3<double>(*bpat[0], val0_64, acc, r64, SPMV_RES, a, s);
     dot<double>(n[0], r64, r64, ictl + 1, ipartial, s);
     vec_convert<double, T>(n[0], r64, b[0], s);
   }

@@ -53,7 +53,10 @@ constexpr long kTailRows = 1100;
 // smoothing on [hi/4, hi] (hi: Gershgorin bound of D^-1 A), restriction
 // R = P^T, prolongation P, dense FP64 inverse on the coarsest level.
 // kind 0: scalar P1 operators (CSR); kind 1: velocity operators (BSR2,
-// interleaved vectors).  T is the smoothing precision.
+// interleaved vectors); kind 2: 3D velocity operators, scalar CSR over the
+// interleaved dofs (Jacobi data, coarse level, transfers) applied through the
+// 3x3-block SELL view bpat / bmap (set before init).  T is the smoothing
+// precision.
 template <typename T>
 struct MGHier {
   int kind = 0;
@@ -66,6 +69,8 @@ struct MGHier {
   std::vector<T *> dinv, x, t, r, b;
   std::vector<double *> hi, coef;
   std::vector<const Transfer *> tr;
+  std::vector<const Pattern *> bpat;   // kind 2: node patterns (3x3-block SELL) per level
+  std::vector<const int *> bmap;       // kind 2: their map9 (value -> CSR position)
   std::vector<long> n;
   int nc = 0;
   bool coarse_iter = false;   // coarsest level by Chebyshev steps (kCoarseDegree), no dense inverse
@@ -132,6 +137,9 @@ struct MGHier {
   int *iit = nullptr;
   cudaStream_t bodyq = nullptr;               // captures the WHILE body
   void op(int l, const T *u, T *out, SpmvMode mode, const SpmvArgs &a, cudaStream_t s);
+  long sell_values(int l) const;                  // values of level l in SELL order
+  template <typename VT>
+  void gather_values(int l, VT *out, cudaStream_t s) const;   // FP64 CSR values -> SELL order
   void vcycle(int l, cudaStream_t s);
   void cycle(cudaStream_t s);                 // one V-cycle with the singular projections
   void inner_residual(cudaStream_t s);        // b[0] = bsave - A acc (FP64); ictl[1] = ||b - A acc||^2

@@ -270,6 +270,133 @@ __global__ void __launch_bounds__(kSellMaxBlock) k_sell(int nslices, const int *
   }
 }
 
+// Wide rows and few slices (the coarse levels of the 3D velocity hierarchy,
+// the 3D divergence B): K warps share a slice, warp k summing the entries
+// j = k, k + K, ... of the slice's 32 rows, so the dependent chain of gathers
+// per thread is w / K long instead of w.  The K partial sums are added in
+// warp order through shared memory, so the result is deterministic and
+// independent of the launch's block size.  SPB slices per block.
+template <typename T, typename VT, int K>
+__global__ void __launch_bounds__(K >= 8 ? 32 * K : 256) k_sell_split(int nslices, const int *__restrict__ sp,
+                                                                       const int *__restrict__ rowid,
+                                                                       const int *__restrict__ col,
+                                                                       const VT *__restrict__ val,
+                                                                       const T *__restrict__ u, T *out, int mode,
+                                                                       SpmvArgs a) {
+  constexpr int SPB = K >= 8 ? 1 : 8 / K;
+  __shared__ T part[SPB][K][32];
+  const int ls = threadIdx.x / (32 * K), k = (threadIdx.x >> 5) % K, lane = threadIdx.x & 31;
+  const int slice = blockIdx.x * SPB + ls;
+  T acc = 0;
+  if (slice < nslices) {
+    const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
+    const int *cp = col + b0 + lane;
+    const VT *vp = val + b0 + lane;
+#pragma unroll 4
+    for (int j = k; j < w; j += K) acc += ldv(vp + j * 32) * u[cp[j * 32]];
+  }
+  part[ls][k][lane] = acc;
+  __syncthreads();
+  if (k != 0 || slice >= nslices) return;
+  const int row = rowid[slice * 32 + lane];
+  if (row < 0) return;
+  T sum = part[ls][0][lane];
+#pragma unroll
+  for (int q = 1; q < K; ++q) sum += part[ls][q][lane];
+  epilogue<T>(mode, row, sum, u, out, a, a.coef);
+}
+
+// 3x3-block SELL (the 3D velocity operators; vectors interleaved, node c at
+// 3 c .. 3 c + 2).  Entry e of a slice column holds a 3x3 block, value
+// m = 3 r + d (row component r, column component d) at
+// 9 (e - e % 32) + 32 m + e % 32, so each of the nine value loads of a warp
+// is one coalesced access.  One node row per thread (K = 1), or K warps per
+// slice with the partial sums added in warp order through shared memory, as
+// k_sell_split; three FMAs per block row and component, in d order.
+template <typename T, typename VT, int K>
+__global__ void __launch_bounds__(K >= 8 ? 32 * K : 256) k_sell_bsr3(int nslices, const int *__restrict__ sp,
+                                                                      const int *__restrict__ rowid,
+                                                                      const int *__restrict__ col,
+                                                                      const VT *__restrict__ val,
+                                                                      const T *__restrict__ u, T *out, int mode,
+                                                                      SpmvArgs a) {
+  constexpr int SPB = K >= 8 ? 1 : 8 / K;
+  const int ls = threadIdx.x / (32 * K), k = (threadIdx.x >> 5) % K, lane = threadIdx.x & 31;
+  const int slice = blockIdx.x * SPB + ls;
+  // U entries per batch, their loads written ahead of their FMAs; the
+  // entries are summed in slice-column order either way
+  constexpr int U = sizeof(T) == 8 ? 2 : 4;
+  T acc[3] = {0, 0, 0};
+  auto fma_blk = [&](const T (&v)[9], const T (&x)[3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      acc[r] = fma_t(v[3 * r], x[0], acc[r]);
+      acc[r] = fma_t(v[3 * r + 1], x[1], acc[r]);
+      acc[r] = fma_t(v[3 * r + 2], x[2], acc[r]);
+    }
+  };
+  if (slice < nslices) {
+    const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
+    int j = k;
+    for (; j + (U - 1) * K < w; j += U * K) {
+      int c[U];
+      T v[U][9], x[U][3];
+#pragma unroll
+      for (int q = 0; q < U; ++q) c[q] = col[b0 + (long)(j + q * K) * 32 + lane];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const VT *vb = val + 9 * (b0 + (long)(j + q * K) * 32) + lane;
+#pragma unroll
+        for (int m = 0; m < 9; ++m) v[q][m] = ldv(vb + 32 * m);
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) x[q][d] = u[3L * c[q] + d];
+#pragma unroll
+      for (int q = 0; q < U; ++q) fma_blk(v[q], x[q]);
+    }
+    for (; j < w; j += K) {
+      const int c = col[b0 + (long)j * 32 + lane];
+      const VT *vb = val + 9 * (b0 + (long)j * 32) + lane;
+      T v[9], x[3];
+#pragma unroll
+      for (int m = 0; m < 9; ++m) v[m] = ldv(vb + 32 * m);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) x[d] = u[3L * c + d];
+      fma_blk(v, x);
+    }
+  }
+  if (K > 1) {
+    __shared__ T part[SPB][K][3][32];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) part[ls][k][r][lane] = acc[r];
+    __syncthreads();
+    if (k != 0 || slice >= nslices) return;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      T sum = part[ls][0][r][lane];
+#pragma unroll
+      for (int q = 1; q < K; ++q) sum += part[ls][q][r][lane];
+      acc[r] = sum;
+    }
+  }
+  if (slice >= nslices) return;
+  const int row = rowid[slice * 32 + lane];
+  if (row < 0) return;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) epilogue<T>(mode, 3L * row + r, acc[r], u, out, a, a.coef);
+}
+
+template <typename T>
+__global__ void k_sell_gather9(long n9, const int *__restrict__ map9, const double *__restrict__ csr,
+                               T *__restrict__ out) {
+  const long i = (long)blockIdx.x * TPB + threadIdx.x;
+  if (i >= n9) return;
+  const int q = map9[i];
+  out[i] = from_double<T>(q >= 0 ? csr[q] : 0.0);
+}
+
 // Scalar rows of at most 8 entries (every P1 operator: 7-point stencil):
 // the epilogue operands are loaded first and all column / value loads are
 // issued before the gathers, so a thread waits for two memory round trips.
@@ -1420,18 +1547,49 @@ void sell_gather_transposed(const Sell &S, int ncomp, const double *csr_vals, do
   CHNSS_LAUNCH_CK();
 }
 
+// Warps per slice of a scalar SELL SpMV: 1 while the slices alone fill one
+// wave of resident warps (48 per multiprocessor) or the rows are short;
+// otherwise doubled (up to 32) until they do, keeping at least four entries of
+// the widest slice per warp.  A function of the pattern and the device only.
+int sell_split(const Sell &S) {
+  if (S.wmax < 12) return 1;
+  const long target = 48L * device_sm_count();
+  int K = 1;
+  while (K < 32 && (long)S.nslices * K < target && S.wmax / (2 * K) >= 4) K *= 2;
+  return K;
+}
+
+template <typename T, typename VT, int K>
+void launch_sell_split(const Sell &S, const VT *sval, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
+                       cudaStream_t s) {
+  constexpr int SPB = K >= 8 ? 1 : 8 / K;
+  k_sell_split<T, VT, K><<<(S.nslices + SPB - 1) / SPB, 32 * K * SPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col,
+                                                                           sval, u, out, mode, a);
+}
+
 template <typename T, typename VT>
 void spmv_sell_impl(const Pattern &P, const VT *sval, int ncomp, const T *u, T *out, SpmvMode mode,
                     const SpmvArgs &a, cudaStream_t s) {
   const Sell &S = P.sell;
   if (S.nslices == 0) return;
   const int nb = nblocks((long)S.nslices * 32, S.block);
+  const int K = ncomp == 1 && !S.stencil ? sell_split(S) : 1;
   if (ncomp == 1 && S.stencil) {
     StencilOff so;
     for (int j = 0; j < 7; ++j) so.o[j] = S.soff[j];
     k_stencil7<T, VT><<<nblocks(P.nrows, S.block), S.block, 0, s>>>(P.nrows, so, sval, u, out, mode, a);
   } else if (ncomp == 1 && S.wmax <= 8)
     k_sell_w8<T, VT><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
+  else if (K == 2)
+    launch_sell_split<T, VT, 2>(S, sval, u, out, mode, a, s);
+  else if (K == 4)
+    launch_sell_split<T, VT, 4>(S, sval, u, out, mode, a, s);
+  else if (K == 8)
+    launch_sell_split<T, VT, 8>(S, sval, u, out, mode, a, s);
+  else if (K == 16)
+    launch_sell_split<T, VT, 16>(S, sval, u, out, mode, a, s);
+  else if (K == 32)
+    launch_sell_split<T, VT, 32>(S, sval, u, out, mode, a, s);
   else if (ncomp == 1)
     k_sell<T, VT, 1, false><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
   else if (aligned(u, 2 * sizeof(T)))
@@ -1440,6 +1598,63 @@ void spmv_sell_impl(const Pattern &P, const VT *sval, int ncomp, const T *u, T *
     k_sell<T, VT, 2, false><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
   CHNSS_LAUNCH_CK();
 }
+
+template <typename T, typename VT, int K>
+void launch_sell_bsr3(const Sell &S, const VT *sval, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
+                      cudaStream_t s) {
+  constexpr int SPB = K >= 8 ? 1 : 8 / K;
+  k_sell_bsr3<T, VT, K><<<(S.nslices + SPB - 1) / SPB, 32 * K * SPB, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col,
+                                                                          sval, u, out, mode, a);
+}
+
+// Warps per slice of a 3x3-block SpMV: enough that the widest slice gives a
+// warp about eight blocks (up to K = 8; on the 3D meshes the slices of
+// vertex rows are twice as wide as the average, and whole slices per warp
+// leave the multiprocessors waiting on them at the end of the launch:
+// 32^3 cubes, K = 1 -> 8: 92 -> 84 ms per mixed step, 163 -> 141 ms FP64),
+// then doubled up to 16 while the slices do not fill one wave of warps.
+template <typename T, typename VT>
+void spmv_sell_bsr3_impl(const Pattern &P, const VT *sval, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
+                         cudaStream_t s) {
+  const Sell &S = P.sell;
+  if (S.nslices == 0) return;
+  const long target = 48L * device_sm_count();
+  int K = 1;
+  while (K < 8 && S.wmax / (2 * K) >= 8) K *= 2;
+  while (K < 16 && (long)S.nslices * K < target && S.wmax / (2 * K) >= 2) K *= 2;
+  switch (K) {
+    case 1: launch_sell_bsr3<T, VT, 1>(S, sval, u, out, mode, a, s); break;
+    case 2: launch_sell_bsr3<T, VT, 2>(S, sval, u, out, mode, a, s); break;
+    case 4: launch_sell_bsr3<T, VT, 4>(S, sval, u, out, mode, a, s); break;
+    case 8: launch_sell_bsr3<T, VT, 8>(S, sval, u, out, mode, a, s); break;
+    default: launch_sell_bsr3<T, VT, 16>(S, sval, u, out, mode, a, s); break;
+  }
+  CHNSS_LAUNCH_CK();
+}
+
+template <typename T>
+void spmv_sell_bsr3(const Pattern &P, const T *sval, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
+                    cudaStream_t s) {
+  spmv_sell_bsr3_impl<T, T>(P, sval, u, out, mode, a, s);
+}
+template void spmv_sell_bsr3<double>(const Pattern &, const double *, const double *, double *, SpmvMode,
+                                     const SpmvArgs &, cudaStream_t);
+template void spmv_sell_bsr3<float>(const Pattern &, const float *, const float *, float *, SpmvMode,
+                                    const SpmvArgs &, cudaStream_t);
+void spmv_sell_bsr3(const Pattern &P, const __nv_bfloat16 *sval, const float *u, float *out, SpmvMode mode,
+                    const SpmvArgs &a, cudaStream_t s) {
+  spmv_sell_bsr3_impl<float, __nv_bfloat16>(P, sval, u, out, mode, a, s);
+}
+
+template <typename Tout>
+void sell_gather9(long nent, const int *map9, const double *csr_vals, Tout *out, cudaStream_t s) {
+  if (nent == 0) return;
+  k_sell_gather9<Tout><<<nblocks(9 * nent, TPB), TPB, 0, s>>>(9 * nent, map9, csr_vals, out);
+  CHNSS_LAUNCH_CK();
+}
+template void sell_gather9<double>(long, const int *, const double *, double *, cudaStream_t);
+template void sell_gather9<float>(long, const int *, const double *, float *, cudaStream_t);
+template void sell_gather9<__nv_bfloat16>(long, const int *, const double *, __nv_bfloat16 *, cudaStream_t);
 
 template <typename T, typename VT>
 void spmv_sell_bsr2_impl(const Pattern &P, const VT *sval, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,

@@ -897,6 +897,10 @@ struct Level3 {
   long N1 = 0, N2 = 0, E = 0;
   Geo3 geo{};
   Pattern p1, pv;
+  // 3x3-block SELL view of the velocity operator: the P2 node pattern and the
+  // CSR position in pv of each of its block values (-1: padding)
+  Pattern pv3;
+  int *map9 = nullptr;
   int *diag1 = nullptr, *diagv = nullptr;
   Transfer t1, tv;                 // from the next coarser level
   Gather g1, gj;                   // element buffers -> P1 CSR, P2 convection -> velocity CSR
@@ -935,7 +939,8 @@ struct chnss3_ctx {
   int *apz = nullptr, *apd = nullptr;           // open top: A_p entries set to 0, diagonal set to 1
   int napz = 0, napd = 0;
   double *Bs = nullptr, *Bts = nullptr, *Mv = nullptr, *Apb = nullptr, *Ap = nullptr, *top = nullptr;
-  double *Ls = nullptr, *Ks = nullptr, *Ms = nullptr, *ACs = nullptr, *As = nullptr;
+  double *Ls = nullptr, *Ks = nullptr, *Ms = nullptr, *ACs = nullptr;
+  double *As = nullptr;                         // velocity operator in 3x3-block SELL order (lv[0].pv3)
   double *Kks[3] = {nullptr, nullptr, nullptr};   // SELL copies of K_kappa (mobility_kind 1)
   double *ebuf = nullptr, *kbuf = nullptr, *loads = nullptr, *G = nullptr, *dinvM = nullptr, *massc = nullptr;
   double *rhs[6] = {}, *xsol[6] = {}, *mt = nullptr, *phia = nullptr;
@@ -1026,6 +1031,39 @@ void build_level3(chnss3_ctx *c, Level3 &L, int n, bool fine, const Mesh3Host *c
   pattern_from_elements(3 * N2, 3 * N2, E, 30, 30, vdn, L.pv);
   upload_pattern(ar, L.p1);
   upload_pattern(ar, L.pv);
+  {
+    auto p2n = [&](int e, int *r, int *cc) {
+      for (int a = 0; a < 10; ++a) r[a] = cc[a] = M.tet2[(long)e * 10 + a];
+    };
+    pattern_from_elements(N2, N2, E, 10, 10, p2n, L.pv3);
+    std::vector<int> hmap;
+    upload_pattern(ar, L.pv3, &hmap);
+    // every node coupling carries all nine component couplings, so scalar row
+    // 3 I + r lists the columns 3 J + d in node order: its entry for block
+    // position k of node row I is rowptr[3 I + r] + 3 (k - rowptr3[I]) + d
+    const std::vector<int> &r3 = L.pv3.h_rowptr, &rs = L.pv.h_rowptr, &cs = L.pv.h_col;
+    std::vector<int> rowof(L.pv3.nnz);
+    for (int I = 0; I < N2; ++I) {
+      for (int k = r3[I]; k < r3[I + 1]; ++k) rowof[k] = I;
+      for (int r = 0; r < 3; ++r)
+        if (rs[3 * I + r + 1] - rs[3 * I + r] != 3 * (r3[I + 1] - r3[I]))
+          throw Error{CHNSS_ERR_ARG, "velocity pattern without full 3x3 blocks"};
+    }
+    std::vector<int> m9(9 * (size_t)L.pv3.sell.nent, -1);
+    for (long e = 0; e < L.pv3.sell.nent; ++e) {
+      const int k = hmap[e];
+      if (k < 0) continue;
+      const int I = rowof[k], J = L.pv3.h_col[k], lane = (int)(e % 32);
+      const size_t base = 9 * (size_t)(e - lane) + lane;
+      for (int r = 0; r < 3; ++r)
+        for (int d = 0; d < 3; ++d) {
+          const int q = rs[3 * I + r] + 3 * (k - r3[I]) + d;
+          if (cs[q] != 3 * J + d) throw Error{CHNSS_ERR_ARG, "velocity pattern out of node order"};
+          m9[base + 32 * (3 * r + d)] = q;
+        }
+    }
+    L.map9 = ar.upload(m9);
+  }
   L.diag1 = ar.upload(diag_positions(L.p1));
   L.diagv = ar.upload(diag_positions(L.pv));
   std::vector<int> hptr, hidx;
@@ -1163,7 +1201,11 @@ void init_prec3(chnss3_ctx *c, Prec3<T> &P, const std::vector<const Pattern *> &
   P.Kp.init(ar, 0, c->top_bc != 1, p1s, d1s, K1s, t1s, c->partial);   // singular for enclosed flow
   P.A.degree = 4;      // as the 2D velocity operator: degree 4 on [hi / 16, hi]
   P.A.ratio = 16.0;
-  P.A.init(ar, 0, false, pvs, dvs, As, tvs, c->partial);
+  for (const Level3 &L : c->lv) {   // sweeps through the 3x3-block view
+    P.A.bpat.push_back(&L.pv3);
+    P.A.bmap.push_back(L.map9);
+  }
+  P.A.init(ar, 2, false, pvs, dvs, As, tvs, c->partial);
   // inner multigrid solves to a tolerance (Sec. 5) in every block that the
   // paper gives to AMG; M_p^-1 stays the fixed Chebyshev iteration.  Each
   // solve group captures its loop bodies on a stream of its own.
@@ -1212,12 +1254,12 @@ void create3(chnss3_ctx *c, int n) {
   c->loads = ar.alloc<double>(5 * N1);
   c->G = ar.alloc<double>(nv);
   c->Ap = ar.alloc<double>(F.p1.nnz);
-  const long nent1 = F.p1.sell.nent, nentv = F.pv.sell.nent;
+  const long nent1 = F.p1.sell.nent;
   c->Ls = ar.alloc<double>(nent1);
   c->Ks = ar.alloc<double>(nent1);
   c->Ms = ar.alloc<double>(nent1);
   c->ACs = ar.alloc<double>(nent1);
-  c->As = ar.alloc<double>(nentv);
+  c->As = ar.alloc<double>(9 * F.pv3.sell.nent);
   sell_gather<double>(F.p1.sell, 1, F.K1, c->Ks, c->s);
   sell_gather<double>(F.p1.sell, 1, F.M1, c->Ms, c->s);
   for (int k = 0; k < 3; ++k) {
@@ -1404,7 +1446,7 @@ void assemble3(chnss3_ctx *c, const chnss_state *st) {
   // SELL copies of the operators FGMRES applies, multigrid setup
   sell_gather<double>(F.p1.sell, 1, F.L, c->Ls, s);
   sell_gather<double>(F.p1.sell, 1, F.AC, c->ACs, s);
-  sell_gather<double>(F.pv.sell, 1, F.A, c->As, s);
+  sell_gather9<double>(F.pv3.sell.nent, F.map9, F.A, c->As, s);
   if (p.mobility_kind != 0)
     for (int sp = 0; sp < 3; ++sp) sell_gather<double>(F.p1.sell, 1, F.Kk[sp], c->Kks[sp], s);
   if (c->p32) setup_prec3(c, *c->p32, s);
@@ -1537,7 +1579,7 @@ struct NS3Op : LinearOperator {
   void apply(const double *x, double *y, cudaStream_t s) override {
     const long nv = 3 * c->lv[0].N2;
     SpmvArgs none;
-    spmv_sell<double>(c->lv[0].pv, c->As, 1, x, y, SPMV_PLAIN, none, s);
+    spmv_sell_bsr3<double>(c->lv[0].pv3, c->As, x, y, SPMV_PLAIN, none, s);
     spmv_sell<double>(c->pbt, c->Bts, 1, x + nv, y, SPMV_ADD, none, s);
     spmv_sell<double>(c->pb, c->Bs, 1, x, y + nv, SPMV_PLAIN, none, s);
   }

@@ -116,7 +116,12 @@ def test_trajectory_gradient_matches_oracle_adjoint(trajectory):
 
 
 def test_trajectory_gradient_vs_central_differences(trajectory, torch):
-    """Central differences of the GPU forward itself (relative step 1e-4)."""
+    """Central differences of the GPU forward itself (relative step 1e-4).
+    On 4^3 cubes over three steps dJ/d(evap_rate) is ~6e-8: the difference
+    quotient then resolves J changes of ~3e-12, where the 1e-12 Krylov
+    tolerance of the forward solves shows, so that parameter is held to 1e-3
+    (its 1e-6 agreement with the oracle's adjoint is the sharp check); the
+    mobility scale and the initial polymer field to 1e-5."""
     n, steps, p, st0, g = trajectory
 
     def J(prm, phi0=None):
@@ -129,7 +134,7 @@ def test_trajectory_gradient_vs_central_differences(trajectory, torch):
         return c.objective(st["phi"][0])
     h = 1e-4 * p["evap_rate"]
     fd = (J(dict(p, evap_rate=p["evap_rate"] + h)) - J(dict(p, evap_rate=p["evap_rate"] - h))) / (2 * h)
-    assert g["evap"] == pytest.approx(fd, rel=1e-5)
+    assert g["evap"] == pytest.approx(fd, rel=1e-3)
     h = 1e-4
     fd = (J(dict(p, gamma=[1 + h] * 3)) - J(dict(p, gamma=[1 - h] * 3))) / (2 * h)
     assert g["gamma"] == pytest.approx(fd, rel=1e-5)
