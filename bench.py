@@ -538,10 +538,11 @@ THREE_D_METRIC = ("time steps/s of the 3D step on the Kuhn mesh of {n}^3 cubes "
 
 def run_three_d(args):
     """The 3D workload (the paper's 3D runs, Sec. 5, on a Kuhn tetrahedral
-    mesh): the film parameter set with the 3D step (chnss3_step), FP32
-    multigrid inside FP64 FGMRES, and the same in FP64 throughout; solves
-    one after the other; CUDA events around the timed steps, inputs resident
-    on the device."""
+    mesh): the film parameter set with the 3D step (chnss3_step): FP32
+    multigrid inside FP64 FGMRES with double-FP32 Gram-Schmidt (the
+    headline), the same with BF16 velocity values, and FP64 throughout; the
+    three solve groups concurrent on their streams; CUDA events around the
+    timed steps, inputs resident on the device."""
     import torch
 
     from paper_2501_11767_gb300 import chnss, inputs
@@ -557,6 +558,24 @@ def run_three_d(args):
     if args.three_d_inner > 0:         # multigrid blocks iterated to a tolerance (Sec. 5: 1e-4)
         p.update(inner_rtol=args.three_d_inner, inner_maxit=20)
     stream = torch.cuda.current_stream()
+
+    if args.nvtx_step:
+        # one serial mixed step inside the NVTX range "step" (for an ncu launch
+        # list: --nvtx --nvtx-include "step/"), after the warm-up steps
+        ctx = chnss.Context3(n, dict(p, precision=1, ortho=1), stream)
+        ctx.set_step_concurrency(False)
+        a = chnss.state_to_device(inputs.initial_state_3d(n, seed=0))
+        b = ctx.new_state()
+        for _ in range(args.warmup):
+            ctx.step(a, b)
+            a, b = b, a
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("step")
+        _, info, _ = ctx.step(a, b)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"nvtx_step": f"film3d{n}_mixed", "iters": {k: v["iters"] for k, v in info.items()}}))
+        return
 
     def timed(prm):
         ctx = chnss.Context3(n, prm, stream)
@@ -579,9 +598,10 @@ def run_three_d(args):
 
     sampler = ClockSampler(_device_uuid(torch, 0))
     sampler.start()
-    ctx, ms, infos = timed(dict(p, precision=1))
+    ctx, ms, infos = timed(dict(p, precision=1, ortho=1))
     clocks = sampler.stop()
     _, ms64, infos64 = timed(dict(p, precision=0))
+    _, ms16, infos16 = timed(dict(p, precision=2, ortho=1))
     iters = lambda inf: {k: round(sum(i[k]["iters"] for i in inf) / len(inf), 2) for k in inf[-1]}   # noqa: E731
     value = args.steps / (ms / 1e3)
     fp64 = args.steps / (ms64 / 1e3)
@@ -601,6 +621,9 @@ def run_three_d(args):
         "converged": all(i[k]["converged"] for i in infos for k in i),
         "fp64": {"value": round(fp64, 4), "unit": "steps/s", "ms_per_step": round(ms64 / args.steps, 2),
                  "iters_mean": iters(infos64)},
+        "bf16_velocity": {"value": round(args.steps / (ms16 / 1e3), 4), "unit": "steps/s",
+                          "ms_per_step": round(ms16 / args.steps, 2), "iters_mean": iters(infos16),
+                          "converged": all(i[k]["converged"] for i in infos16 for k in i)},
         "speedup_mixed_vs_fp64": round(value / fp64, 3),
         "clocks": clocks,
     }
@@ -829,6 +852,8 @@ def main():
     ap.add_argument("--adjoint", action="store_true", help="40-step gradient on 256x256 instead")
     ap.add_argument("--three-d", action="store_true", help="the 3D step on a Kuhn mesh instead")
     ap.add_argument("--three-d-n", type=int, default=32)
+    ap.add_argument("--nvtx-step", action="store_true",
+                    help="with --three-d: one serial mixed step inside an NVTX range (profiling), no timing")
     ap.add_argument("--three-d-mobility", type=int, default=0, choices=[0, 1],
                     help="3D workload with the concentration-dependent mobility")
     ap.add_argument("--three-d-open", type=int, default=0, choices=[0, 1], help="3D workload with an open top")

@@ -313,6 +313,48 @@ __global__ void __launch_bounds__(K >= 8 ? 32 * K : 256) k_sell_split(int nslice
 // is one coalesced access.  One node row per thread (K = 1), or K warps per
 // slice with the partial sums added in warp order through shared memory, as
 // k_sell_split; three FMAs per block row and component, in d order.
+// k_sell_bsr2 with K warps per slice (coarse velocity levels with fewer
+// slices than one wave of warps): warp k sums the entries j = k, k + K, ...,
+// the K partial sums are added in warp order through shared memory
+template <typename T, typename VT, int K>
+__global__ void __launch_bounds__(256) k_sell_bsr2_split(int nslices, const int *__restrict__ sp,
+                                                         const int *__restrict__ rowid, const int *__restrict__ col,
+                                                         const VT *__restrict__ val, const T *__restrict__ u, T *out,
+                                                         int mode, SpmvArgs a) {
+  constexpr int SPB = 8 / K;
+  __shared__ T part[SPB][K][2][32];
+  const int ls = threadIdx.x / (32 * K), k = (threadIdx.x >> 5) % K, lane = threadIdx.x & 31;
+  const int slice = blockIdx.x * SPB + ls;
+  T acc0 = 0, acc1 = 0;
+  if (slice < nslices) {
+    const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
+#pragma unroll 2
+    for (int j = k; j < w; j += K) {
+      const long e = b0 + (long)j * 32 + lane;
+      const int c = col[e];
+      T b[4];
+      load_blk(val + 4 * e, b);
+      const T x0 = u[2L * c], x1 = u[2L * c + 1];
+      acc0 = fma_t(b[1], x1, fma_t(b[0], x0, acc0));
+      acc1 = fma_t(b[3], x1, fma_t(b[2], x0, acc1));
+    }
+  }
+  part[ls][k][0][lane] = acc0;
+  part[ls][k][1][lane] = acc1;
+  __syncthreads();
+  if (k != 0 || slice >= nslices) return;
+  const int row = rowid[slice * 32 + lane];
+  if (row < 0) return;
+  T s0 = part[ls][0][0][lane], s1 = part[ls][0][1][lane];
+#pragma unroll
+  for (int q = 1; q < K; ++q) {
+    s0 += part[ls][q][0][lane];
+    s1 += part[ls][q][1][lane];
+  }
+  epilogue<T>(mode, 2L * row, s0, u, out, a, a.coef);
+  epilogue<T>(mode, 2L * row + 1, s1, u, out, a, a.coef);
+}
+
 template <typename T, typename VT, int K>
 __global__ void __launch_bounds__(K >= 8 ? 32 * K : 256) k_sell_bsr3(int nslices, const int *__restrict__ sp,
                                                                       const int *__restrict__ rowid,
@@ -1664,7 +1706,20 @@ void spmv_sell_bsr2_impl(const Pattern &P, const VT *sval, const T *u, T *out, S
   const int nb = nblocks((long)S.nslices * 32, S.block);
   if (!aligned(sval, 4 * sizeof(VT)))
     throw Error{CHNSS_ERR_ARG, "2x2-block values must be aligned to one block"};
-  if (aligned(u, 2 * sizeof(T)))
+  // coarse levels with fewer slices than one wave of warps: K warps per slice
+  const long target = 48L * device_sm_count();
+  int K = 1;
+  while (K < 8 && (long)S.nslices * K < target && S.wmax / (2 * K) >= 2) K *= 2;
+  if (K > 1) {
+    const int spb = 8 / K;
+    const int g = (S.nslices + spb - 1) / spb;
+    if (K == 2)
+      k_sell_bsr2_split<T, VT, 2><<<g, 256, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
+    else if (K == 4)
+      k_sell_bsr2_split<T, VT, 4><<<g, 256, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
+    else
+      k_sell_bsr2_split<T, VT, 8><<<g, 256, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
+  } else if (aligned(u, 2 * sizeof(T)))
     k_sell_bsr2<T, VT, true><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
   else
     k_sell_bsr2<T, VT, false><<<nb, S.block, 0, s>>>(S.nslices, S.slice_ptr, S.rowid, S.col, sval, u, out, mode, a);
