@@ -67,6 +67,13 @@ void spmv_sell_bsr3(const Pattern &P, const T *sval, const T *u, T *out, SpmvMod
                     cudaStream_t s);
 void spmv_sell_bsr3(const Pattern &P, const __nv_bfloat16 *sval, const float *u, float *out, SpmvMode mode,
                     const SpmvArgs &a, cudaStream_t s);
+// Coarsest level of a 3x3-block hierarchy: degree Chebyshev-Jacobi steps from
+// zero (coef layout of cheb_coefficients) in one block; the iterate ends in x
+// (t: scratch).  Levels of at most kChebBlockSlices SELL slices.
+constexpr int kChebBlockSlices = 8;
+template <typename T, typename VT>
+void cheb_block_bsr3(const Pattern &P, const VT *sval, const T *dinv, const T *b, T *x, T *t, const double *coef,
+                     int degree, cudaStream_t s);
 // nr (1..3) vectors through one scalar matrix with rows of at most 8 entries;
 // each output is bitwise the single-vector result (same per-row order).
 template <typename T>
@@ -85,7 +92,7 @@ void vec_copy_multi(long n, int nr, const MultiPtr<T> &in, const MultiPtr<T> &ou
 // one is the coarsest (dense inverse).  Level sizes must allow every sweep's
 // rows to be spread over the block; all pointers are device pointers.
 constexpr int kMaxTailLevels = 8;
-struct TailSell {                 // SELL view of one operator (rows of at most 8 entries)
+struct TailSell {                 // SELL view of one operator (rows of at most 16 entries)
   int nslices = 0;
   const int *sp = nullptr, *rowid = nullptr, *col = nullptr;
 };
@@ -104,8 +111,9 @@ struct TailDesc {
   const double *cinv = nullptr;   // coarsest level, row-major nc x nc
   TailLevel<T> lv[kMaxTailLevels];
 };
+// width: 8 or 16, the widest row of any tail operator or transfer (rounded up)
 template <typename T>
-void mg_tail(const TailDesc<T> *d_desc, int nr, cudaStream_t s);
+void mg_tail(const TailDesc<T> *d_desc, int nr, int width, cudaStream_t s);
 // BF16-stored values, FP32 vectors and accumulation (preconditioner variant)
 void spmv_sell(const Pattern &P, const __nv_bfloat16 *sval, int ncomp, const float *u, float *out, SpmvMode mode,
                const SpmvArgs &a, cudaStream_t s);

@@ -179,10 +179,15 @@ void MGHier<T>::init(Arena &ar, int kind_, bool singular_, const std::vector<con
         tail_l0 = l;
         break;
       }
-    // the one-block tail sweeps rows of at most 8 entries (sell_w8m_slice)
-    bool narrow = true;
-    for (int l = std::max(tail_l0, 0); l < nl; ++l) narrow = narrow && pat[l]->sell.wmax <= 8;
-    if (tail_l0 > 0 && nl - tail_l0 <= kMaxTailLevels && narrow) {
+    // the one-block tail sweeps rows of at most 16 entries (sell_w8m_slice;
+    // 8 on the triangle meshes, 15 on the tetrahedral P1 levels)
+    int wmax = 0;
+    for (int l = std::max(tail_l0, 0); l < nl; ++l) {
+      wmax = std::max(wmax, pat[l]->sell.wmax);
+      if (l < nl - 1) wmax = std::max({wmax, tr[l]->R.sell.wmax, tr[l]->P.sell.wmax});
+    }
+    tail_width = wmax <= 8 ? 8 : 16;
+    if (tail_l0 > 0 && nl - tail_l0 <= kMaxTailLevels && wmax <= 16) {
       std::vector<MultiPtr<T>> X(nl), Tt(nl), Rr(nl), B(nl);
       for (int l = 0; l < nl; ++l) {
         X[l].p[0] = x[l];
@@ -210,7 +215,7 @@ TailDesc<T> *MGHier<T>::make_tail(Arena &ar, const std::vector<MultiPtr<T>> &X, 
   d.cinv = cinv;
   d.coarse_degree = coarse_iter ? kCoarseDegree : 0;
   auto view = [](const Pattern &P) {
-    if (P.sell.wmax > 8) throw Error{CHNSS_ERR_ARG, "coarse-level block: rows of at most 8 entries"};
+    if (P.sell.wmax > 16) throw Error{CHNSS_ERR_ARG, "coarse-level block: rows of at most 16 entries"};
     TailSell v;
     v.nslices = P.sell.nslices;
     v.sp = P.sell.slice_ptr;
@@ -320,11 +325,22 @@ static inline const T *transfer_vals(const Transfer &t, bool restrict_) {
 template <typename T>
 void MGHier<T>::vcycle(int l, cudaStream_t s) {
   if (l == tail_l0) {
-    mg_tail<T>(tail, 1, s);
+    mg_tail<T>(tail, 1, tail_width, s);
     return;
   }
   if (l == nl - 1 && !coarse_iter) {
     dense_apply<T>(nc, cinv, b[l], x[l], s);
+    return;
+  }
+  if (l == nl - 1 && kind == 2 && bpat[l]->sell.nslices <= kChebBlockSlices) {
+    // small 3x3-block coarsest level: its Chebyshev steps in one launch
+    if constexpr (std::is_same<T, float>::value) {
+      if (bf16) {
+        cheb_block_bsr3<float, __nv_bfloat16>(*bpat[l], val16[l], dinv[l], b[l], x[l], t[l], coef[l], kCoarseDegree, s);
+        return;
+      }
+    }
+    cheb_block_bsr3<T, T>(*bpat[l], val[l], dinv[l], b[l], x[l], t[l], coef[l], kCoarseDegree, s);
     return;
   }
   const int nc_ = kind == 1 ? 2 : 1;   // transfers per node (BSR2) or per dof
@@ -608,7 +624,7 @@ template <typename T>
 void MGBatch<T>::vcycle(int l, cudaStream_t s) {
   const int nl = h->nl;
   if (l == h->tail_l0) {
-    mg_tail<T>(tail, nr, s);
+    mg_tail<T>(tail, nr, h->tail_width, s);
     return;
   }
   if (l == nl - 1 && !h->coarse_iter) {

@@ -85,6 +85,7 @@ struct MGHier {
   double ratio = 4.0;      // smoothing interval [hi / ratio, hi]
   // levels tail_l0.. (at most kTailRows rows each) run as one block launch
   int tail_l0 = -1;
+  int tail_width = 8;            // widest tail row (operators and transfers): 8 or 16
   TailDesc<T> *tail = nullptr;   // device
 
   // levels: per level pattern + FP64 value pointer (values may change

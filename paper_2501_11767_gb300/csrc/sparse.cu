@@ -430,6 +430,64 @@ __global__ void __launch_bounds__(K >= 8 ? 32 * K : 256) k_sell_bsr3(int nslices
   for (int r = 0; r < 3; ++r) epilogue<T>(mode, 3L * row + r, acc[r], u, out, a, a.coef);
 }
 
+// The coarsest level of a 3x3-block hierarchy solved by degree Chebyshev-
+// Jacobi steps from zero, all in one block of 32 warps (levels of at most
+// eight slices, 256 node rows): K = 32 / slices warps share a slice as in
+// k_sell_bsr3, a block barrier between steps.  The same expressions as the
+// per-launch form (k_scale_dinv, then SPMV_CHEB sweeps), so the iterate
+// lands in x after the last step.
+template <typename T, typename VT>
+__global__ void __launch_bounds__(1024) k_cheb_bsr3_block(int nslices, int K, const int *__restrict__ sp,
+                                                          const int *__restrict__ rowid, const int *__restrict__ col,
+                                                          const VT *__restrict__ val, const T *__restrict__ dinv,
+                                                          const T *__restrict__ b, T *x, T *t,
+                                                          const double *__restrict__ coef, int degree, int n) {
+  __shared__ T part[32][3][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int slice = warp / K, k = warp % K;
+  T *cur = (degree - 1) % 2 == 0 ? x : t;
+  T *oth = cur == x ? t : x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) cur[i] = (T)(*coef) * dinv[i] * b[i];
+  __syncthreads();
+  for (int st = 1; st < degree; ++st) {
+    T acc[3] = {0, 0, 0};
+    if (slice < nslices) {
+      const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
+      for (int j = k; j < w; j += K) {
+        const int c = col[b0 + j * 32 + lane];
+        const VT *vb = val + 9 * (b0 + j * 32) + lane;
+        const T x0 = cur[3 * c], x1 = cur[3 * c + 1], x2 = cur[3 * c + 2];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          acc[r] = fma_t(ldv(vb + 32 * (3 * r)), x0, acc[r]);
+          acc[r] = fma_t(ldv(vb + 32 * (3 * r + 1)), x1, acc[r]);
+          acc[r] = fma_t(ldv(vb + 32 * (3 * r + 2)), x2, acc[r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) part[warp][r][lane] = acc[r];
+    __syncthreads();
+    if (k == 0 && slice < nslices) {
+      const int row = rowid[slice * 32 + lane];
+      if (row >= 0) {
+        const double *cf = coef + 4 + 3 * (st - 1);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          T sum = part[warp][r][lane];
+          for (int q = 1; q < K; ++q) sum += part[warp + q][r][lane];
+          const int i = 3 * row + r;
+          oth[i] = cheb_row<T>(cf, cur[i], dinv[i], b[i], sum, st > 1, st > 1 ? oth[i] : (T)0);
+        }
+      }
+    }
+    __syncthreads();
+    T *tmp = cur;
+    cur = oth;
+    oth = tmp;
+  }
+}
+
 template <typename T>
 __global__ void k_sell_gather9(long n9, const int *__restrict__ map9, const double *__restrict__ csr,
                                T *__restrict__ out) {
@@ -1035,9 +1093,10 @@ __global__ void k_dense_apply(int n, const double *inv, const T *b, T *x) {
 // the matrix stream is read once, each right-hand side is summed in the same
 // order as by the single-vector kernels, so every output is bitwise the one
 // the single-vector kernel would give.
-// One slice (32 rows) of a multi-vector scalar SpMV with rows of at most 8
-// entries; shared by k_sell_w8m and the one-block coarse-level kernel.
-template <typename T, int NR>
+// One slice (32 rows) of a multi-vector scalar SpMV with rows of at most W
+// entries; shared by k_sell_w8m (W = 8) and the one-block coarse-level
+// kernel (W = 8, or 16 for the 15-entry rows of the tetrahedral P1 levels).
+template <typename T, int NR, int W = 8>
 __device__ __forceinline__ void sell_w8m_slice(int slice, int lane, const int *sp, const int *rowid, const int *col,
                                                const T *val, const MultiPtr<T> &u, const MultiPtr<T> &out, int mode,
                                                const MultiArgs<T> &a) {
@@ -1059,22 +1118,26 @@ __device__ __forceinline__ void sell_w8m_slice(int slice, int lane, const int *s
       if (mode == SPMV_ADD) oi[k] = out.p[k][row];
     }
   }
-  int c[8];
-  T v[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    if (j < w) {
-      c[j] = col[b0 + j * 32 + lane];
-      v[j] = val[b0 + j * 32 + lane];
-    }
-  }
   T acc[NR];
 #pragma unroll
-  for (int k = 0; k < NR; ++k) {
-    acc[k] = 0;
+  for (int k = 0; k < NR; ++k) acc[k] = 0;
+  // entries in chunks of 8 (all loads of a chunk first), summed in order
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-      if (j < w) acc[k] += v[j] * u.p[k][c[j]];
+  for (int j0 = 0; j0 < W; j0 += 8) {
+    int c[8];
+    T v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (j0 + j < w) {
+        c[j] = col[b0 + (j0 + j) * 32 + lane];
+        v[j] = val[b0 + (j0 + j) * 32 + lane];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k)
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (j0 + j < w) acc[k] += v[j] * u.p[k][c[j]];
   }
   if (row < 0) return;
 #pragma unroll
@@ -1153,16 +1216,16 @@ __global__ void __launch_bounds__(kSellMaxBlock) k_sell_w8m(int nslices, const i
 // Every row is computed by the same code as in the per-sweep kernels
 // (sell_w8m_slice, the same scale / copy / dense expressions), so the
 // result is bitwise the multi-launch V-cycle's.
-template <typename T, int NR>
+template <typename T, int NR, int W>
 __device__ void tail_sweep(const TailSell &S, const T *val, const MultiPtr<T> &u, const MultiPtr<T> &out, int mode,
                            const MultiArgs<T> &a) {
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int slice = threadIdx.x >> 5; slice < S.nslices; slice += nw)
-    sell_w8m_slice<T, NR>(slice, lane, S.sp, S.rowid, S.col, val, u, out, mode, a);
+    sell_w8m_slice<T, NR, W>(slice, lane, S.sp, S.rowid, S.col, val, u, out, mode, a);
   __syncthreads();
 }
 
-template <typename T, int NR>
+template <typename T, int NR, int W>
 __global__ void __launch_bounds__(512) k_mg_tail(const TailDesc<T> *__restrict__ dp) {
   const TailDesc<T> &d = *dp;
   const int L = d.nlev - 1;
@@ -1181,16 +1244,16 @@ __global__ void __launch_bounds__(512) k_mg_tail(const TailDesc<T> *__restrict__
     for (int s = 1; s < degree; ++s) {
       a.coef = q.coef + 4 + 3 * (s - 1);
       a.w = s == 1 ? MultiPtr<T>() : oth;
-      tail_sweep<T, NR>(q.A, q.val, cur, oth, SPMV_CHEB, a);
+      tail_sweep<T, NR, W>(q.A, q.val, cur, oth, SPMV_CHEB, a);
       const MultiPtr<T> tmp = cur;
       cur = oth;
       oth = tmp;
     }
     MultiArgs<T> ar;
     ar.b = q.b;
-    tail_sweep<T, NR>(q.A, q.val, q.x, q.r, SPMV_RES, ar);
+    tail_sweep<T, NR, W>(q.A, q.val, q.x, q.r, SPMV_RES, ar);
     MultiArgs<T> none;
-    tail_sweep<T, NR>(q.R, q.Rval, q.r, d.lv[l + 1].b, SPMV_PLAIN, none);
+    tail_sweep<T, NR, W>(q.R, q.Rval, q.r, d.lv[l + 1].b, SPMV_PLAIN, none);
   }
   // coarsest: dense inverse, or Chebyshev steps from zero (same sweeps as
   // the pre-smoothing, coarse_degree of them)
@@ -1208,7 +1271,7 @@ __global__ void __launch_bounds__(512) k_mg_tail(const TailDesc<T> *__restrict__
     for (int st = 1; st < cd; ++st) {
       a.coef = q.coef + 4 + 3 * (st - 1);
       a.w = st == 1 ? MultiPtr<T>() : oth;
-      tail_sweep<T, NR>(q.A, q.val, cur, oth, SPMV_CHEB, a);
+      tail_sweep<T, NR, W>(q.A, q.val, cur, oth, SPMV_CHEB, a);
       const MultiPtr<T> tmp = cur;
       cur = oth;
       oth = tmp;
@@ -1227,17 +1290,17 @@ __global__ void __launch_bounds__(512) k_mg_tail(const TailDesc<T> *__restrict__
   for (int l = L - 1; l >= 0; --l) {
     const TailLevel<T> &q = d.lv[l];
     MultiArgs<T> none;
-    tail_sweep<T, NR>(q.P, q.Pval, d.lv[l + 1].x, q.x, SPMV_ADD, none);
+    tail_sweep<T, NR, W>(q.P, q.Pval, d.lv[l + 1].x, q.x, SPMV_ADD, none);
     MultiArgs<T> a;
     a.b = q.b;
     a.dinv = q.dinv;
     a.coef = q.coef + 1;
-    tail_sweep<T, NR>(q.A, q.val, q.x, q.t, SPMV_CHEB, a);
+    tail_sweep<T, NR, W>(q.A, q.val, q.x, q.t, SPMV_CHEB, a);
     MultiPtr<T> cur = q.t, oth = q.x;
     for (int s = 1; s < degree; ++s) {
       a.coef = q.coef + 4 + 3 * (s - 1);
       a.w = oth;
-      tail_sweep<T, NR>(q.A, q.val, cur, oth, SPMV_CHEB, a);
+      tail_sweep<T, NR, W>(q.A, q.val, cur, oth, SPMV_CHEB, a);
       const MultiPtr<T> tmp = cur;
       cur = oth;
       oth = tmp;
@@ -1687,6 +1750,27 @@ void spmv_sell_bsr3(const Pattern &P, const __nv_bfloat16 *sval, const float *u,
                     const SpmvArgs &a, cudaStream_t s) {
   spmv_sell_bsr3_impl<float, __nv_bfloat16>(P, sval, u, out, mode, a, s);
 }
+
+template <typename T, typename VT>
+void cheb_block_bsr3(const Pattern &P, const VT *sval, const T *dinv, const T *b, T *x, T *t, const double *coef,
+                     int degree, cudaStream_t s) {
+  const Sell &S = P.sell;
+  if (S.nslices < 1 || S.nslices > kChebBlockSlices)
+    throw Error{CHNSS_ERR_ARG, "one-block Chebyshev: 1 to 8 slices of node rows"};
+  if (degree < 1 || degree > kMaxSmoothDegree + 1) throw Error{CHNSS_ERR_ARG, "one-block Chebyshev: bad degree"};
+  int ns = 1;
+  while (ns < S.nslices) ns *= 2;
+  k_cheb_bsr3_block<T, VT><<<1, 1024, 0, s>>>(S.nslices, 32 / ns, S.slice_ptr, S.rowid, S.col, sval, dinv, b, x, t,
+                                               coef, degree, 3 * P.nrows);
+  CHNSS_LAUNCH_CK();
+}
+template void cheb_block_bsr3<double, double>(const Pattern &, const double *, const double *, const double *,
+                                              double *, double *, const double *, int, cudaStream_t);
+template void cheb_block_bsr3<float, float>(const Pattern &, const float *, const float *, const float *, float *,
+                                            float *, const double *, int, cudaStream_t);
+template void cheb_block_bsr3<float, __nv_bfloat16>(const Pattern &, const __nv_bfloat16 *, const float *,
+                                                    const float *, float *, float *, const double *, int,
+                                                    cudaStream_t);
 
 template <typename Tout>
 void sell_gather9(long nent, const int *map9, const double *csr_vals, Tout *out, cudaStream_t s) {
@@ -2262,17 +2346,28 @@ template void dense_apply_multi<float>(int, int, const double *, const MultiPtr<
                                        cudaStream_t);
 
 template <typename T>
-void mg_tail(const TailDesc<T> *d_desc, int nr, cudaStream_t s) {
+void mg_tail(const TailDesc<T> *d_desc, int nr, int width, cudaStream_t s) {
+  if (width != 8 && width != 16) throw Error{CHNSS_ERR_ARG, "coarse-level block: rows of 8 or 16 entries"};
+  const bool w16 = width == 16;
   switch (nr) {
-    case 1: k_mg_tail<T, 1><<<1, 512, 0, s>>>(d_desc); break;
-    case 2: k_mg_tail<T, 2><<<1, 512, 0, s>>>(d_desc); break;
-    case 3: k_mg_tail<T, 3><<<1, 512, 0, s>>>(d_desc); break;
+    case 1:
+      if (w16) k_mg_tail<T, 1, 16><<<1, 512, 0, s>>>(d_desc);
+      else k_mg_tail<T, 1, 8><<<1, 512, 0, s>>>(d_desc);
+      break;
+    case 2:
+      if (w16) k_mg_tail<T, 2, 16><<<1, 512, 0, s>>>(d_desc);
+      else k_mg_tail<T, 2, 8><<<1, 512, 0, s>>>(d_desc);
+      break;
+    case 3:
+      if (w16) k_mg_tail<T, 3, 16><<<1, 512, 0, s>>>(d_desc);
+      else k_mg_tail<T, 3, 8><<<1, 512, 0, s>>>(d_desc);
+      break;
     default: throw Error{CHNSS_ERR_ARG, "coarse-level block: 1 to 3 vectors"};
   }
   CHNSS_LAUNCH_CK();
 }
-template void mg_tail<double>(const TailDesc<double> *, int, cudaStream_t);
-template void mg_tail<float>(const TailDesc<float> *, int, cudaStream_t);
+template void mg_tail<double>(const TailDesc<double> *, int, int, cudaStream_t);
+template void mg_tail<float>(const TailDesc<float> *, int, int, cudaStream_t);
 
 template <typename T>
 void vec_copy_multi(long n, int nr, const MultiPtr<T> &in, const MultiPtr<T> &out, cudaStream_t s) {
