@@ -37,6 +37,11 @@ METRIC = "time steps/s at 1M nodes (1024x1024 P1 mesh, FGMRES to 1e-8 relative r
 FP64_FMA_PER_SM_CLK = 2     # FP64 FMA issue rate per multiprocessor per clock on this part
 
 
+# GB300 HBM3e nominal bandwidth (8 stacks), reported beside the measured copy
+# bandwidth that the fractions are taken against
+HBM_NOMINAL_GBS = 7900.0
+
+
 def fp64_peak_tflops(sm_max_mhz=None):
     """ALU roof of FP64 work: multiprocessors of the current device x FP64
     FMAs per clock x 2 FLOP x the maximum SM clock (sampled by nvidia-smi
@@ -356,6 +361,7 @@ def run_gpu(args):
                     "hbm_frac": round(gbps / peak, 4), "traffic": _traffic(name, d["bytes"] / d["launches"])}
         return {"kernel": name, "bound": "hbm", "achieved": round(gbps, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(gbps / peak, 4), "peak_source": peak_kind,
+                "frac_of_nominal": round(gbps / HBM_NOMINAL_GBS, 4),
                 "bytes_per_launch": d["bytes"] / d["launches"], "ms_per_launch": ms_l,
                 "launches": d["launches"], "traffic": _traffic(name, d["bytes"] / d["launches"])}
 
