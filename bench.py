@@ -496,18 +496,26 @@ def run_adjoint(args):
     """The adjoint workload: one full gradient of the final-morphology
     functional with respect to (evaporation rate, mobility scale, initial
     polymer field) through 40 FP64 steps on 256 x 256, with a checkpoint
-    every 8 steps (forward sweep, segment recomputation, adjoint steps).
-    A timed unit is one whole gradient."""
+    every 8 steps (forward sweep, segment recomputation, adjoint steps);
+    with --three-d, 20 FP64 3D steps on the Kuhn mesh of --three-d-n cubes,
+    checkpoints every 4.  A timed unit is one whole gradient."""
     import torch
 
     from paper_2501_11767_gb300 import adjoint, chnss, inputs
 
     torch.cuda.set_device(0)
-    n, steps, every = 256, 40, 8
-    p = inputs.workload("film256_mobility")["params"]   # concentration-dependent mobility
-    mesh = chnss.Mesh(n)
-    ctx = chnss.Context(mesh, p)
-    st0 = chnss.state_to_device(inputs.initial_state(n, seed=0))
+    if args.three_d:   # the 3D adjoint (chnss3_adjoint_step) on the Kuhn mesh of n^3 cubes
+        n, steps, every = args.three_d_n, 20, 4
+        p = dict(inputs.default_params(), tau=1e-4, mobility_kind=1)
+        ctx = chnss.Context3(n, p)
+        st0 = chnss.state_to_device(inputs.initial_state_3d(n, seed=0))
+        workload = f"adjoint3d{n}"
+    else:
+        n, steps, every = 256, 40, 8
+        p = inputs.workload("film256_mobility")["params"]   # concentration-dependent mobility
+        ctx = chnss.Context(chnss.Mesh(n), p)
+        st0 = chnss.state_to_device(inputs.initial_state(n, seed=0))
+        workload = "adjoint256"
     for _ in range(args.warmup):
         adjoint.trajectory_gradient(ctx, st0, 2, checkpoint_every=1)
     torch.cuda.synchronize()
@@ -523,11 +531,12 @@ def run_adjoint(args):
     # forward steps per gradient: the sweep plus the recomputed segments
     fwd = steps + sum(min(every, steps - k) for k in range(0, steps, every))
     out = {
-        "metric": ADJOINT_METRIC, "value": round(args.steps / sec, 4), "unit": "gradients/s", "n_gpus": 1,
+        "metric": ADJOINT3_METRIC.format(n=n) if args.three_d else ADJOINT_METRIC,
+        "value": round(args.steps / sec, 4), "unit": "gradients/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec / args.steps * 1e3, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded SplitMix64 noise on phi_p, phi_NFA)",
-        "config": {"workload": "adjoint256", "n": n, "time_steps": steps, "checkpoint_every": every,
+        "config": {"workload": workload, "n": n, "time_steps": steps, "checkpoint_every": every,
                    "forward_steps_per_gradient": fwd, "adjoint_steps_per_gradient": steps,
                    "adjoint_rtol": 1e-12, "forward_rtol": p["rtol"], "beta": p["beta"],
                    "mobility": "gamma (phi (1 - phi) + m0)" if p["mobility_kind"] else "constant"},
@@ -538,6 +547,8 @@ def run_adjoint(args):
     print(json.dumps(out))
 
 
+ADJOINT3_METRIC = ("gradients/s of J = int |grad phi_p|^2 after 20 FP64 3D steps on the Kuhn mesh of {n}^3 "
+                   "cubes (discrete adjoint, checkpoints every 4)")
 THREE_D_METRIC = ("time steps/s of the 3D step on the Kuhn mesh of {n}^3 cubes "
                   "(FP32 multigrid inside FP64 FGMRES to 1e-8)")
 

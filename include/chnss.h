@@ -419,9 +419,13 @@ const char *chnss3_last_error(chnss3_ctx_t ctx);
  * DEVICE states of the 3D sizes; velocity adjoints are zero on the no-slip
  * dofs, the pressure adjoint is zero.  grad_params (HOST, 2 doubles,
  * accumulated): d/d(evap_rate), d/d(gamma) with gamma scaling the three
- * mobilities.  info[6] (optional): the transposed solves.  The solves run one
- * after the other on the context stream, which is synchronised before the
- * return.  Errors as chnss3_step (text in chnss3_last_error). */
+ * mobilities.  info[6] (optional): the transposed solves.  As in
+ * chnss3_step the three groups (Oseen; Allen-Cahn; air potential then
+ * Cahn-Hilliard) run concurrently on library streams unless
+ * chnss3_set_step_concurrency(ctx, 0); their contributions are summed in a
+ * fixed order, so the result is bitwise the same either way.  The context
+ * stream is synchronised before the return.  Errors as chnss3_step (text in
+ * chnss3_last_error). */
 chnss_status chnss3_adjoint_step(chnss3_ctx_t ctx, const chnss_state *state_k, const chnss_state *state_k1,
                                  const chnss_state *adj_k1, chnss_state *adj_k, double *grad_params,
                                  chnss_solve_info *info);

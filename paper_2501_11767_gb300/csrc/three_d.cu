@@ -965,6 +965,9 @@ struct chnss3_ctx {
   double *arhs = nullptr, *ay = nullptr, *alam = nullptr, *az = nullptr, *atmp = nullptr, *atv = nullptr;
   double *alw[5] = {};
   double *adots = nullptr;                      // device scalars of the parameter gradients
+  // per-group work and accumulators of the concurrent adjoint step (AC, CH)
+  double *ay_ac = nullptr, *aPhi = nullptr, *v_ac = nullptr;
+  double *arhs_ch = nullptr, *ay_ch = nullptr, *atmp_ch = nullptr, *aphi = nullptr, *v_ch = nullptr;
   std::string err;
   ~chnss3_ctx() {
     for (cudaGraphExec_t g : gexec)
@@ -1687,7 +1690,6 @@ chnss_status step3(chnss3_ctx *c, const chnss_state *in, chnss_state *out, chnss
 // xbar of its solution, y = A^-T xbar (FGMRES on the transposed operator,
 // preconditioned by the forward block preconditioner), then
 // ubar += (db/du)^T y - (d(A(u) x)/du)^T y (the k3_adj_* element kernels).
-// The solves run one after the other on the context stream.
 constexpr double kAdjointRtol3 = 1e-12;
 
 struct CH3OpT : LinearOperator {   // [[L^T, tau g K], [tau K_kappa, -(tau g / b) M]] (K, K_kappa symmetric)
@@ -1750,11 +1752,26 @@ void adjoint_alloc3(chnss3_ctx *c) {
   c->atv = ar.alloc<double>(nv);
   for (double *&w : c->alw) w = ar.alloc<double>(N1);
   c->adots = ar.alloc<double>(32);
+  c->ay_ac = ar.alloc<double>(N1);
+  c->aPhi = ar.alloc<double>(N1);
+  c->v_ac = ar.alloc<double>(nv);
+  c->arhs_ch = ar.alloc<double>(2 * N1);
+  c->ay_ch = ar.alloc<double>(2 * N1);
+  c->atmp_ch = ar.alloc<double>(N1);
+  c->aphi = ar.alloc<double>(3 * N1);
+  c->v_ch = ar.alloc<double>(nv);
   vec_fill(N1, 1.0, c->atmp, c->s);
   SpmvArgs none;
   spmv_csr<double>(F.p1, F.M1, 1, c->atmp, c->mvec, SPMV_PLAIN, none, c->s);
 }
 
+// The adjoint of step3: three independent groups as in the forward step
+// (Oseen; Allen-Cahn; air potential -> Cahn-Hilliard), each with its own
+// Krylov work, scratch vectors, slice of the element buffers and
+// accumulators.  The groups' contributions to the shared adjoints (v, phi,
+// Phi_v) are added on the context stream after the join in a fixed order,
+// then the potential-load adjoint and the parameter gradients, so the result
+// does not depend on whether the groups overlap.
 chnss_status adjoint_step3(chnss3_ctx *c, const chnss_state *stk, const chnss_state *st1, const chnss_state *lam,
                            chnss_state *out, double *grad, chnss_solve_info *inf) {
   const auto &p = c->p;
@@ -1782,104 +1799,160 @@ chnss_status adjoint_step3(chnss3_ctx *c, const chnss_state *stk, const chnss_st
   fk.Phi = stk->Phi_v;
   for (int i = 0; i < 4; ++i) fk.beta[i] = p.beta[i];
   fk.beta_v = p.beta_v;
-  // element scratch (the assembly's buffer, free once assemble3 has run)
-  double *bufP = c->ebuf, *bufV = c->ebuf + 20 * E;
-  auto gather_fields = [&](const double *buf, double *const dst[4]) {   // [E][20] -> four P1 fields, added
-    for (int f = 0; f < 4; ++f) launch_gather(c->gl, 1, buf + 4 * f, 1.0, dst[f], 1.0, dst[f], s);
-  };
-  double *const phiPhi[4] = {out->phi[0], out->phi[1], out->phi[2], out->Phi_v};
-  chnss_status worst = CHNSS_OK;
-  auto keep = [&](chnss_status st) { if (worst == CHNSS_OK) worst = st; };
+  CHNSS_CK(cudaEventRecord(c->ev_asm, s));
   // ---- Oseen: [[A^T, B^T], [B, 0]] y = (masked lambda_v, lambda_p) ----------
-  vec_copy(nv, lam->v, c->arhs, s);
-  k3_mask<<<nb3(nv), kTPB3, 0, s>>>(nv, c->bnd, c->arhs);
-  CHNSS_LAUNCH_CK();
-  if (c->top_bc == 0) {   // transpose of the zero-mean pressure shift (|box| = 1)
-    vsum<double>(N1, lam->p, c->sum, c->partial, s);
-    k3_mean_shift_T<<<nb3(N1), kTPB3, 0, s>>>(N1, lam->p, c->mvec, c->sum, 1.0, c->arhs + nv);
+  auto group_ns = [&](cudaStream_t q) -> chnss_status {
+    double *bufP = c->ebuf, *bufV = c->ebuf + 20 * E;   // element scratch [0, 50 E)
+    KrylovWork &kw = c->kw;
+    vec_copy(nv, lam->v, c->arhs, q);
+    k3_mask<<<nb3(nv), kTPB3, 0, q>>>(nv, c->bnd, c->arhs);
     CHNSS_LAUNCH_CK();
-  } else {                // open top: the outflow fixes the pressure level, no shift
-    vec_copy(N1, lam->p, c->arhs + nv, s);
-  }
-  {
-    NS3OpT op(c);
-    keep(fgmres(op, c->arhs, c->ay, kAdjointRtol3, 0.0, p.maxit, c->kw, &inf[5], s));
-  }
-  const double *yv = c->ay;
-  spmv_csr<double>(F.pv, c->Mv, 1, yv, c->atv, SPMV_PLAIN, none, s);
-  vec_axpby(nv, 1.0 / tau, c->atv, 1.0, out->v, s);                          // (M_v / tau)^T y_v
-  k3_adj_korteweg<<<nb3(E), kTPB3, 0, s>>>(F.geo, fk, yv, bufP);
-  CHNSS_LAUNCH_CK();
-  gather_fields(bufP, phiPhi);
-  vec_copy(nv, st1->v, c->atv, s);                                            // J(w) acts on v^(k+1), no-slip dofs zero
-  k3_mask<<<nb3(nv), kTPB3, 0, s>>>(nv, c->bnd, c->atv);
-  CHNSS_LAUNCH_CK();
-  k3_adj_conv_p2<<<nb3(E), kTPB3, 0, s>>>(F.geo, c->atv, yv, bufV, bufP);
-  CHNSS_LAUNCH_CK();
-  launch_gather(c->gk, 3, bufV, -1.0, out->v, 1.0, out->v, s);               // - (d J(w) x / dv)^T y
-  launch_gather(c->gl, 1, bufP, 1.0, nullptr, 0.0, c->atmp, s);
-  for (int i = 0; i < 4; ++i) vec_axpby(N1, -p.alpha[i], c->atmp, 1.0, out->mu[i], s);   // ds/dmu_i = alpha_i grad psi
-  // ---- air potential: M z = lambda_mu_a --------------------------------------
-  keep(pcg(F.p1, F.M1, c->dinvM, lam->mu[3], c->az, kAdjointRtol3, 1000, c->kwc, &inf[4], s));
-  spmv_csr<double>(F.p1, F.K1, 1, c->az, c->atmp, SPMV_PLAIN, none, s);
-  for (int i = 0; i < 3; ++i) {   // mu_a^(k+1) depends on phi^(k+1) through beta_a K (1 - sum phi)
-    vec_copy(N1, lam->phi[i], c->alam + (long)i * N1, s);
-    vec_axpby(N1, -p.beta[3], c->atmp, 1.0, c->alam + (long)i * N1, s);
-  }
-  vec_copy(N1, c->az, c->alw[3], s);
-  dot<double>(N1, c->top, c->az, D + 0, c->partial, s);
-  // ---- Allen-Cahn -------------------------------------------------------------
-  {
-    AC3OpT op(c);
-    keep(fgmres(op, lam->Phi_v, c->ay, kAdjointRtol3, 0.0, p.maxit, c->kwa, &inf[3], s));
-  }
-  spmv_csr<double>(F.p1, F.M1, 1, c->ay, c->atmp, SPMV_PLAIN, none, s);
-  vec_axpby(N1, 1.0, c->atmp, 1.0, out->Phi_v, s);
-  vec_fill(N1, 0.0, c->alw[4], s);
-  vec_axpby(N1, -tau * p.gamma_v, c->ay, 0.0, c->alw[4], s);
-  k3_adj_conv_p1<<<nb3(E), kTPB3, 0, s>>>(F.geo, st1->Phi_v, c->ay, bufV);
-  CHNSS_LAUNCH_CK();
-  launch_gather(c->gk, 3, bufV, -tau, out->v, 1.0, out->v, s);
-  dot<double>(N1, c->top, c->ay, D + 1, c->partial, s);
-  // ---- Cahn-Hilliard, three species ------------------------------------------
-  for (int i = 0; i < 3; ++i) {
-    vec_copy(N1, c->alam + (long)i * N1, c->arhs, s);
-    vec_copy(N1, lam->mu[i], c->arhs + N1, s);
-    {
-      CH3OpT op(c, i);
-      keep(fgmres(op, c->arhs, c->ay, kAdjointRtol3, 0.0, p.maxit, c->kwc, &inf[i], s));
-    }
-    const double *y1 = c->ay, *y2 = c->ay + N1;
-    const double cc = tau * p.gamma[i] / p.beta[i];
-    spmv_csr<double>(F.p1, F.M1, 1, y1, c->atmp, SPMV_PLAIN, none, s);
-    vec_axpby(N1, 1.0, c->atmp, 1.0, out->phi[i], s);
-    if (var) {   // - tau (d K_kappa(phi_i^k) / d phi_i)^T (y1, mu_i^(k+1))
-      k3_adj_wstiff<<<nb3(E), kTPB3, 0, s>>>(F.geo, stk->phi[i], p.gamma[i], st1->mu[i], y1, bufP);
+    if (c->top_bc == 0) {   // transpose of the zero-mean pressure shift (|box| = 1)
+      vsum<double>(N1, lam->p, c->sum, kw.partial, q);
+      k3_mean_shift_T<<<nb3(N1), kTPB3, 0, q>>>(N1, lam->p, c->mvec, c->sum, 1.0, c->arhs + nv);
       CHNSS_LAUNCH_CK();
-      launch_gather(c->gl, 1, bufP, -tau, out->phi[i], 1.0, out->phi[i], s);
+    } else {                // open top: the outflow fixes the pressure level, no shift
+      vec_copy(N1, lam->p, c->arhs + nv, q);
     }
-    vec_fill(N1, 0.0, c->alw[i], s);
-    vec_axpby(N1, -cc, y2, 0.0, c->alw[i], s);
-    k3_adj_conv_p1<<<nb3(E), kTPB3, 0, s>>>(F.geo, st1->phi[i], y1, bufV);
+    chnss_status st;
+    {
+      NS3OpT op(c);
+      st = fgmres(op, c->arhs, c->ay, kAdjointRtol3, 0.0, p.maxit, kw, &inf[5], q);
+    }
+    const double *yv = c->ay;
+    spmv_csr<double>(F.pv, c->Mv, 1, yv, c->atv, SPMV_PLAIN, none, q);
+    vec_axpby(nv, 1.0 / tau, c->atv, 1.0, out->v, q);                          // (M_v / tau)^T y_v
+    k3_adj_korteweg<<<nb3(E), kTPB3, 0, q>>>(F.geo, fk, yv, bufP);
     CHNSS_LAUNCH_CK();
-    launch_gather(c->gk, 3, bufV, -tau, out->v, 1.0, out->v, s);
-    double *d = D + 4 + 5 * i;
-    dot<double>(N1, c->loads + (long)i * N1, y2, d + 0, c->partial, s);        // F_i . y2
-    dot<double>(N1, c->top, y2, d + 1, c->partial, s);                          // t . y2
-    // y1 . K mu' (constant mobility) or y1 . K_kappa mu' (divided by gamma_i on the host)
-    spmv_csr<double>(F.p1, var ? F.Kk[i] : F.K1, 1, st1->mu[i], c->atmp, SPMV_PLAIN, none, s);
-    dot<double>(N1, y1, c->atmp, d + 2, c->partial, s);
-    spmv_csr<double>(F.p1, F.K1, 1, st1->phi[i], c->atmp, SPMV_PLAIN, none, s);
-    dot<double>(N1, y2, c->atmp, d + 3, c->partial, s);                         // y2 . K phi'
-    spmv_csr<double>(F.p1, F.M1, 1, st1->mu[i], c->atmp, SPMV_PLAIN, none, s);
-    dot<double>(N1, y2, c->atmp, d + 4, c->partial, s);                         // y2 . M mu'
+    for (int f = 0; f < 4; ++f) {
+      double *dst = f < 3 ? out->phi[f] : out->Phi_v;
+      launch_gather(c->gl, 1, bufP + 4 * f, 1.0, dst, 1.0, dst, q);
+    }
+    vec_copy(nv, st1->v, c->atv, q);                                            // J(w) acts on v^(k+1)
+    k3_mask<<<nb3(nv), kTPB3, 0, q>>>(nv, c->bnd, c->atv);
+    CHNSS_LAUNCH_CK();
+    k3_adj_conv_p2<<<nb3(E), kTPB3, 0, q>>>(F.geo, c->atv, yv, bufV, bufP);
+    CHNSS_LAUNCH_CK();
+    launch_gather(c->gk, 3, bufV, -1.0, out->v, 1.0, out->v, q);               // - (d J(w) x / dv)^T y
+    launch_gather(c->gl, 1, bufP, 1.0, nullptr, 0.0, c->atmp, q);
+    for (int i = 0; i < 4; ++i) vec_axpby(N1, -p.alpha[i], c->atmp, 1.0, out->mu[i], q);   // ds/dmu_i = alpha_i grad psi
+    return st;
+  };
+  // ---- Allen-Cahn -------------------------------------------------------------
+  auto group_ac = [&](cudaStream_t q) -> chnss_status {
+    double *bufV = c->ebuf + 50 * E;                    // element scratch [50 E, 80 E)
+    chnss_status st;
+    {
+      AC3OpT op(c);
+      st = fgmres(op, lam->Phi_v, c->ay_ac, kAdjointRtol3, 0.0, p.maxit, c->kwa, &inf[3], q);
+    }
+    spmv_csr<double>(F.p1, F.M1, 1, c->ay_ac, c->aPhi, SPMV_PLAIN, none, q);
+    vec_fill(N1, 0.0, c->alw[4], q);
+    vec_axpby(N1, -tau * p.gamma_v, c->ay_ac, 0.0, c->alw[4], q);
+    k3_adj_conv_p1<<<nb3(E), kTPB3, 0, q>>>(F.geo, st1->Phi_v, c->ay_ac, bufV);
+    CHNSS_LAUNCH_CK();
+    launch_gather(c->gk, 3, bufV, -tau, nullptr, 0.0, c->v_ac, q);
+    dot<double>(N1, c->top, c->ay_ac, D + 1, c->kwa.partial, q);
+    return st;
+  };
+  // ---- air potential (M z = lambda_mu_a), then Cahn-Hilliard, three species -----
+  auto group_ch = [&](cudaStream_t q, chnss_status *st_mu) -> chnss_status {
+    double *bufP = c->ebuf + 80 * E, *bufV = c->kbuf;   // element scratch [80 E, 100 E) and the Korteweg buffer
+    double *tmp = c->atmp_ch;
+    KrylovWork &kw = c->kwc;
+    *st_mu = pcg(F.p1, F.M1, c->dinvM, lam->mu[3], c->az, kAdjointRtol3, 1000, kw, &inf[4], q);
+    spmv_csr<double>(F.p1, F.K1, 1, c->az, tmp, SPMV_PLAIN, none, q);
+    for (int i = 0; i < 3; ++i) {   // mu_a^(k+1) depends on phi^(k+1) through beta_a K (1 - sum phi)
+      vec_copy(N1, lam->phi[i], c->alam + (long)i * N1, q);
+      vec_axpby(N1, -p.beta[3], tmp, 1.0, c->alam + (long)i * N1, q);
+    }
+    vec_copy(N1, c->az, c->alw[3], q);
+    dot<double>(N1, c->top, c->az, D + 0, kw.partial, q);
+    chnss_status worst = CHNSS_OK;
+    vec_fill(nv, 0.0, c->v_ch, q);
+    for (int i = 0; i < 3; ++i) {
+      vec_copy(N1, c->alam + (long)i * N1, c->arhs_ch, q);
+      vec_copy(N1, lam->mu[i], c->arhs_ch + N1, q);
+      {
+        CH3OpT op(c, i);
+        const chnss_status st = fgmres(op, c->arhs_ch, c->ay_ch, kAdjointRtol3, 0.0, p.maxit, kw, &inf[i], q);
+        if (worst == CHNSS_OK) worst = st;
+      }
+      const double *y1 = c->ay_ch, *y2 = c->ay_ch + N1;
+      double *aphi = c->aphi + (long)i * N1;
+      const double cc = tau * p.gamma[i] / p.beta[i];
+      spmv_csr<double>(F.p1, F.M1, 1, y1, aphi, SPMV_PLAIN, none, q);
+      if (var) {   // - tau (d K_kappa(phi_i^k) / d phi_i)^T (y1, mu_i^(k+1))
+        k3_adj_wstiff<<<nb3(E), kTPB3, 0, q>>>(F.geo, stk->phi[i], p.gamma[i], st1->mu[i], y1, bufP);
+        CHNSS_LAUNCH_CK();
+        launch_gather(c->gl, 1, bufP, -tau, aphi, 1.0, aphi, q);
+      }
+      vec_fill(N1, 0.0, c->alw[i], q);
+      vec_axpby(N1, -cc, y2, 0.0, c->alw[i], q);
+      k3_adj_conv_p1<<<nb3(E), kTPB3, 0, q>>>(F.geo, st1->phi[i], y1, bufV);
+      CHNSS_LAUNCH_CK();
+      launch_gather(c->gk, 3, bufV, -tau, c->v_ch, 1.0, c->v_ch, q);
+      double *d = D + 4 + 5 * i;
+      dot<double>(N1, c->loads + (long)i * N1, y2, d + 0, kw.partial, q);     // F_i . y2
+      dot<double>(N1, c->top, y2, d + 1, kw.partial, q);                       // t . y2
+      // y1 . K mu' (constant mobility) or y1 . K_kappa mu' (divided by gamma_i on the host)
+      spmv_csr<double>(F.p1, var ? F.Kk[i] : F.K1, 1, st1->mu[i], tmp, SPMV_PLAIN, none, q);
+      dot<double>(N1, y1, tmp, d + 2, kw.partial, q);
+      spmv_csr<double>(F.p1, F.K1, 1, st1->phi[i], tmp, SPMV_PLAIN, none, q);
+      dot<double>(N1, y2, tmp, d + 3, kw.partial, q);                          // y2 . K phi'
+      spmv_csr<double>(F.p1, F.M1, 1, st1->mu[i], tmp, SPMV_PLAIN, none, q);
+      dot<double>(N1, y2, tmp, d + 4, kw.partial, q);                          // y2 . M mu'
+    }
+    return worst;
+  };
+  chnss_status st[4] = {CHNSS_OK, CHNSS_OK, CHNSS_OK, CHNSS_OK};   // CH, AC, NS, air potential
+  std::exception_ptr err[3];
+  int dev = 0;
+  CHNSS_CK(cudaGetDevice(&dev));
+  auto run = [&](int w) {
+    try {
+      CHNSS_CK(cudaSetDevice(dev));
+      cudaStream_t q = c->sx[w];
+      CHNSS_CK(cudaStreamWaitEvent(q, c->ev_asm, 0));
+      if (w == 0) st[0] = group_ch(q, &st[3]);
+      else if (w == 1) st[1] = group_ac(q);
+      else st[2] = group_ns(q);
+      CHNSS_CK(cudaEventRecord(c->ev_done[w], q));
+    } catch (...) {
+      err[w] = std::current_exception();
+    }
+  };
+  if (c->concurrent) {
+    std::thread t_ac(run, 1), t_ns(run, 2);
+    run(0);
+    t_ac.join();
+    t_ns.join();
+  } else {
+    for (int w = 0; w < 3; ++w) run(w);
   }
+  for (std::exception_ptr &e : err)
+    if (e) std::rethrow_exception(e);
+  for (cudaEvent_t e : c->ev_done) CHNSS_CK(cudaStreamWaitEvent(s, e, 0));
+  chnss_status worst = CHNSS_OK;
+  for (chnss_status x : {st[2], st[3], st[1], st[0]})   // the order of the sequential adjoint: NS, mu_a, AC, CH
+    if (worst == CHNSS_OK) worst = x;
+  // ---- the groups' contributions to the shared adjoints --------------------------
+  vec_axpby(nv, 1.0, c->v_ac, 1.0, out->v, s);
+  vec_axpby(nv, 1.0, c->v_ch, 1.0, out->v, s);
+  vec_axpby(N1, 1.0, c->aPhi, 1.0, out->Phi_v, s);
+  for (int i = 0; i < 3; ++i) vec_axpby(N1, 1.0, c->aphi + (long)i * N1, 1.0, out->phi[i], s);
   // ---- potential loads ---------------------------------------------------------
-  LoadWeights3 lw;
-  for (int i = 0; i < 5; ++i) lw.z[i] = c->alw[i];
-  k3_adj_loads<<<nb3(E), kTPB3, 0, s>>>(F.geo, fk, lw, bufP);
-  CHNSS_LAUNCH_CK();
-  gather_fields(bufP, phiPhi);
+  {
+    double *bufP = c->ebuf;
+    LoadWeights3 lw;
+    for (int i = 0; i < 5; ++i) lw.z[i] = c->alw[i];
+    k3_adj_loads<<<nb3(E), kTPB3, 0, s>>>(F.geo, fk, lw, bufP);
+    CHNSS_LAUNCH_CK();
+    for (int f = 0; f < 4; ++f) {
+      double *dst = f < 3 ? out->phi[f] : out->Phi_v;
+      launch_gather(c->gl, 1, bufP + 4 * f, 1.0, dst, 1.0, dst, s);
+    }
+  }
   // ---- parameter gradients and the evaporation flux ------------------------------
   double h[24], phis_ref = 0.0;
   CHNSS_CK(cudaMemcpyAsync(h, D, 24 * sizeof(double), cudaMemcpyDeviceToHost, s));

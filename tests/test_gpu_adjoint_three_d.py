@@ -78,6 +78,31 @@ def test_adjoint_step_matches_oracle(torch, case):
     assert grad[1] == pytest.approx(th["gamma"], rel=1e-8)
 
 
+def test_concurrent_adjoint_equals_serial(torch):
+    """The three adjoint groups overlap on their own streams; their
+    contributions are summed in a fixed order, so the result is bitwise the
+    one of the serial setting."""
+    n = 8
+    p = _params(mobility_kind=1)
+    o = t3.Oracle3D(n, p)
+    sk = o.step(_moving_state(o, n, seed=9))[0]
+    sk1 = o.step(sk)[0]
+    rng = np.random.default_rng(3)
+    lam = {k: rng.standard_normal(np.shape(v)) for k, v in sk.items()}
+    lam["v"][np.repeat(o.mesh.p2_boundary(), 3)] = 0.0
+    res = []
+    for conc in (True, False):
+        ctx = chnss.Context3(n, p)
+        ctx.set_step_concurrency(conc)
+        out, grad, info, st = ctx.adjoint_step(*(chnss.state_to_device(x) for x in (sk, sk1, lam)))
+        assert st == 0
+        res.append((chnss.state_to_numpy(out), list(grad), [v["iters"] for v in info.values()]))
+    (a, ga, ia), (b, gb, ib) = res
+    assert ia == ib and ga == gb
+    for key in ("phi", "mu", "Phi_v", "v", "p"):
+        assert np.array_equal(a[key], b[key]), key
+
+
 def test_objective_matches_oracle(torch):
     n = 4
     p = _params()
