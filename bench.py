@@ -855,7 +855,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--bf16-steps", type=int, default=5)
     ap.add_argument("--roofline-steps", type=int, default=3)
     ap.add_argument("--ortho", type=int, default=-1, choices=[-1, 0, 1],
