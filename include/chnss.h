@@ -285,6 +285,23 @@ chnss_status chnss_export_csr(chnss_ctx_t ctx, int which, int *nrows, int *nnz, 
  * and synchronises; CHNSS_ERR_ARG for bad sizes or null pointers. */
 chnss_status chnss_debug_cgs2(int arith, long n, int k, const double *V, long ld, const double *w, double *h,
                               double *vout);
+/* Test entry: one sparse matrix-vector product through the library's
+ * SELL-C-sigma SpMV kernels, with the dispatch the solvers use (including the
+ * number of warps that share a slice).  layout 0: scalar rows; 1: 2x2 blocks;
+ * 2: 3x3 blocks (vectors interleaved per node, bs = 1, 2, 3).  precision 0:
+ * FP64 values and vectors; 1: FP32; 2: BF16 values, FP32 vectors and sums.
+ * mode 0: y = A x; 1: y = b - A x; 2: y += A x; 3 (square only):
+ * y = c0 x + c1 w + c2 dinv (b - A x) with (c0, c1, c2) = coef (w may be
+ * null: no c1 term).  HOST arrays: the (node) pattern in CSR with ascending
+ * columns per row (rowptr[nrows + 1], col[nnz]), val (nnz blocks of bs^2
+ * values, each block row-major), x (bs ncols), b, w, dinv (bs nrows),
+ * coef[3]; y (bs nrows; read by mode 2, then written).  *warps_per_slice
+ * (optional, out): the warps per SELL slice the dispatcher chose.  Allocates
+ * its device copies and synchronises; CHNSS_ERR_ARG for bad sizes, modes,
+ * columns or null pointers. */
+chnss_status chnss_debug_spmv(int layout, int precision, int mode, int nrows, int ncols, const int *rowptr,
+                              const int *col, const double *val, const double *x, const double *b, const double *w,
+                              const double *dinv, const double *coef, double *y, int *warps_per_slice);
 /* Assembled right-hand side of a system (host, chnss_system_size doubles). */
 chnss_status chnss_export_rhs(chnss_ctx_t ctx, chnss_system sys, double *host_out);
 

@@ -135,6 +135,10 @@ EXPORTS = {
     "chnss_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.POINTER(Diag)]),
     "chnss_debug_cgs2": (ctypes.c_int, [ctypes.c_int, ctypes.c_long, ctypes.c_int, ctypes.c_void_p, ctypes.c_long,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "chnss_debug_spmv": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "chnss_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
     "chnss_inner_stats_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(InnerStats)]),
@@ -551,6 +555,32 @@ def host_operator3(n: int, which: str, params: dict, state: dict = None):
     _check(lib.chnss3_host_operator(n, op, ctypes.byref(prm), sptr, ctypes.byref(nr), ctypes.byref(nc),
                                     ctypes.byref(nnz), rowptr.ctypes.data, col.ctypes.data, val.ctypes.data))
     return sp.csr_matrix((val, col, rowptr), shape=(nr.value, nc.value))
+
+
+def debug_spmv(layout: int, precision: int, mode: int, rowptr, col, val, x, b=None, w=None, dinv=None,
+               coef=None, y=None, ncols: int = None):
+    """chnss_debug_spmv: one SpMV through the library's SELL kernels on HOST
+    numpy data (layout 0 scalar, 1 2x2 blocks, 2 3x3 blocks; val (nnz, bs^2)).
+    Returns (y, warps per slice)."""
+    bs = (1, 2, 3)[layout] if 0 <= layout <= 2 else 1   # other layouts: refused by the library
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    nrows = len(rowptr) - 1
+    ncols = nrows if ncols is None else ncols
+    val = np.ascontiguousarray(val, dtype=np.float64).reshape(-1)
+    if val.size != len(col) * bs * bs:
+        raise ValueError("val must hold bs^2 values per entry")
+    arr = lambda a, n: None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(n)   # noqa: E731
+    x = arr(x, bs * ncols)
+    b, w, dinv = arr(b, bs * nrows), arr(w, bs * nrows), arr(dinv, bs * nrows)
+    coef = arr(coef, 3)
+    y = np.zeros(bs * nrows) if y is None else np.array(y, dtype=np.float64).reshape(bs * nrows)
+    ptr = lambda a: None if a is None else a.ctypes.data   # noqa: E731
+    k = ctypes.c_int()
+    _check(load().chnss_debug_spmv(layout, precision, mode, nrows, ncols, rowptr.ctypes.data, col.ctypes.data,
+                                   val.ctypes.data, x.ctypes.data, ptr(b), ptr(w), ptr(dinv), ptr(coef),
+                                   y.ctypes.data, ctypes.byref(k)))
+    return y, k.value
 
 
 def debug_cgs2(V, w, arith: int):

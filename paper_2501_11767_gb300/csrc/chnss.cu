@@ -1374,6 +1374,76 @@ chnss_status fail(chnss_ctx *c, chnss_status st, const std::string &msg) {
   catch (const std::bad_alloc &) { return fail(ctx, CHNSS_ERR_OOM, "host allocation failed"); } \
   catch (const std::exception &e) { return fail(ctx, CHNSS_ERR_CUDA, e.what()); }
 
+namespace chnss {
+namespace debug_spmv_detail {
+
+template <typename U>
+U from_host(double v) {
+  if constexpr (std::is_same<U, __nv_bfloat16>::value) return __float2bfloat16((float)v);
+  else return (U)v;
+}
+
+// One SpMV of chnss_debug_spmv in vector type T with values stored as VT.
+template <typename T, typename VT>
+void debug_spmv_run(int layout, int mode, Pattern &P, const std::vector<int> &hmap, const std::vector<double> &cval,
+                    long nx, long ny, const double *x, const double *b, const double *w, const double *dinv,
+                    const double *coef, double *y) {
+  ScopedDeviceMem mem;
+  cudaStream_t s = nullptr;
+  const int bs = layout == 0 ? 1 : layout + 1, nv = bs * bs;
+  const Sell &S = P.sell;
+  // values in the layout's SELL order, from the host CSR values (nv per entry)
+  std::vector<double> sv;
+  if (layout == 2) {
+    sv.assign(9 * (size_t)S.nent, 0.0);
+    for (long e = 0; e < S.nent; ++e) {
+      if (hmap[e] < 0) continue;
+      const long lane = e % 32, base = 9 * (e - lane) + lane;
+      for (int m = 0; m < 9; ++m) sv[base + 32 * m] = cval[(size_t)hmap[e] * 9 + m];
+    }
+  } else {
+    sv.assign((size_t)nv * S.nent, 0.0);
+    for (long e = 0; e < S.nent; ++e)
+      if (hmap[e] >= 0)
+        for (int m = 0; m < nv; ++m) sv[(size_t)e * nv + m] = cval[(size_t)hmap[e] * nv + m];
+  }
+  auto up = [&](const double *h, long n, auto *tag) {
+    using U = std::remove_pointer_t<decltype(tag)>;
+    std::vector<U> t(n);
+    for (long i = 0; i < n; ++i) t[i] = from_host<U>(h[i]);
+    U *d = mem.get<U>(n);
+    CHNSS_CK(cudaMemcpy(d, t.data(), n * sizeof(U), cudaMemcpyHostToDevice));
+    return d;
+  };
+  VT *dval = up(sv.data(), (long)sv.size(), (VT *)nullptr);
+  T *dx = up(x, nx, (T *)nullptr);
+  T *dy = up(y, ny, (T *)nullptr);
+  SpmvArgs a;
+  if (mode == SPMV_RES || mode == SPMV_CHEB) a.b = up(b, ny, (T *)nullptr);
+  if (mode == SPMV_CHEB) {
+    a.dinv = up(dinv, ny, (T *)nullptr);
+    if (w) a.w = up(w, ny, (T *)nullptr);
+    double *dc = mem.get<double>(3);
+    CHNSS_CK(cudaMemcpy(dc, coef, 3 * sizeof(double), cudaMemcpyHostToDevice));
+    a.coef = dc;
+  }
+  if constexpr (std::is_same<VT, __nv_bfloat16>::value) {
+    if (layout == 0) spmv_sell(P, dval, 1, dx, dy, (SpmvMode)mode, a, s);
+    else if (layout == 1) spmv_sell_bsr2(P, dval, dx, dy, (SpmvMode)mode, a, s);
+    else spmv_sell_bsr3(P, dval, dx, dy, (SpmvMode)mode, a, s);
+  } else {
+    if (layout == 0) spmv_sell<T>(P, dval, 1, dx, dy, (SpmvMode)mode, a, s);
+    else if (layout == 1) spmv_sell_bsr2<T>(P, dval, dx, dy, (SpmvMode)mode, a, s);
+    else spmv_sell_bsr3<T>(P, dval, dx, dy, (SpmvMode)mode, a, s);
+  }
+  std::vector<T> hy(ny);
+  CHNSS_CK(cudaMemcpy(hy.data(), dy, ny * sizeof(T), cudaMemcpyDeviceToHost));
+  for (long i = 0; i < ny; ++i) y[i] = (double)hy[i];
+}
+
+}  // namespace debug_spmv_detail
+}  // namespace chnss
+
 extern "C" {
 
 chnss_status chnss_mesh_create(int nx, int ny, double lx, double ly, chnss_mesh_t *out) {
@@ -1634,6 +1704,49 @@ chnss_status chnss_debug_cgs2(int arith, long n, int k, const double *V, long ld
   CHNSS_CK(cudaStreamSynchronize(s));
   CHNSS_CK(cudaGetLastError());
   std::copy(hh.begin(), hh.end(), h);
+  return CHNSS_OK;
+  ABI_CATCH(nullptr)
+}
+
+
+chnss_status chnss_debug_spmv(int layout, int precision, int mode, int nrows, int ncols, const int *rowptr,
+                              const int *col, const double *val, const double *x, const double *b, const double *w,
+                              const double *dinv, const double *coef, double *y, int *warps_per_slice) {
+  ABI_TRY
+  if (layout < 0 || layout > 2) throw Error{CHNSS_ERR_ARG, "layout must be 0 (scalar), 1 (2x2) or 2 (3x3)"};
+  if (precision < 0 || precision > 2) throw Error{CHNSS_ERR_ARG, "precision must be 0, 1 or 2"};
+  if (mode < 0 || mode > 3) throw Error{CHNSS_ERR_ARG, "mode must be 0 (plain), 1 (residual), 2 (add), 3 (Chebyshev)"};
+  if (nrows < 1 || ncols < 1 || !rowptr || !col || !val || !x || !y) throw Error{CHNSS_ERR_ARG, "bad size or null"};
+  if ((mode == 1 || mode == 3) && !b) throw Error{CHNSS_ERR_ARG, "modes 1 and 3 need b"};
+  if (mode == 3 && (!dinv || !coef)) throw Error{CHNSS_ERR_ARG, "mode 3 needs dinv and coef"};
+  if (mode == 3 && nrows != ncols) throw Error{CHNSS_ERR_ARG, "mode 3 needs a square matrix"};
+  if (layout > 0 && nrows != ncols) throw Error{CHNSS_ERR_ARG, "block layouts need a square node pattern"};
+  Pattern P;
+  P.nrows = nrows;
+  P.ncols = ncols;
+  P.h_rowptr.assign(rowptr, rowptr + nrows + 1);
+  if (P.h_rowptr[0] != 0) throw Error{CHNSS_ERR_ARG, "rowptr[0] must be 0"};
+  for (int r = 0; r < nrows; ++r)
+    if (P.h_rowptr[r + 1] < P.h_rowptr[r]) throw Error{CHNSS_ERR_ARG, "rowptr must be non-decreasing"};
+  P.nnz = P.h_rowptr[nrows];
+  P.h_col.assign(col, col + P.nnz);
+  for (int k = 0; k < P.nnz; ++k)
+    if (P.h_col[k] < 0 || P.h_col[k] >= ncols) throw Error{CHNSS_ERR_ARG, "column out of range"};
+  const int bs = layout == 0 ? 1 : layout + 1;
+  Arena ar;
+  std::vector<int> hmap;
+  upload_pattern(ar, P, &hmap);
+  std::vector<double> cval(val, val + (size_t)P.nnz * bs * bs);
+  const long nx = (long)bs * ncols, ny = (long)bs * nrows;
+  if (warps_per_slice)
+    *warps_per_slice = layout == 0 ? (P.sell.wmax <= 8 ? 1 : sell_split(P.sell))
+                                   : (layout == 1 ? sell_warps_bsr2(P.sell) : sell_warps_bsr3(P.sell));
+  using debug_spmv_detail::debug_spmv_run;
+  if (precision == 0) debug_spmv_run<double, double>(layout, mode, P, hmap, cval, nx, ny, x, b, w, dinv, coef, y);
+  else if (precision == 1) debug_spmv_run<float, float>(layout, mode, P, hmap, cval, nx, ny, x, b, w, dinv, coef, y);
+  else debug_spmv_run<float, __nv_bfloat16>(layout, mode, P, hmap, cval, nx, ny, x, b, w, dinv, coef, y);
+  CHNSS_CK(cudaDeviceSynchronize());
+  CHNSS_CK(cudaGetLastError());
   return CHNSS_OK;
   ABI_CATCH(nullptr)
 }

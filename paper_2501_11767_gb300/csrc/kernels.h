@@ -57,6 +57,12 @@ void spmv_sell(const Pattern &P, const T *sval, int ncomp, const T *u, T *out, S
 template <typename T>
 void spmv_sell_bsr2(const Pattern &P, const T *sval, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
                     cudaStream_t s);
+// Warps per slice the SpMV dispatchers use for a pattern (1: one thread per
+// row; a function of the pattern and the device only): scalar rows, 2x2
+// blocks, 3x3 blocks
+int sell_split(const Sell &S);
+int sell_warps_bsr2(const Sell &S);
+int sell_warps_bsr3(const Sell &S);
 // 3x3-block SELL (3D velocity operators on the P2 node pattern, vectors
 // interleaved): value m = 3 r + d of SELL entry e at 9 (e - e % 32) + 32 m +
 // e % 32; map9 holds the CSR position of every such value (-1: padding)

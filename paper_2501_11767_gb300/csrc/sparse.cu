@@ -1718,15 +1718,20 @@ void launch_sell_bsr3(const Sell &S, const VT *sval, const T *u, T *out, SpmvMod
 // leave the multiprocessors waiting on them at the end of the launch:
 // 32^3 cubes, K = 1 -> 8: 92 -> 84 ms per mixed step, 163 -> 141 ms FP64),
 // then doubled up to 16 while the slices do not fill one wave of warps.
+int sell_warps_bsr3(const Sell &S) {
+  const long target = 48L * device_sm_count();
+  int K = 1;
+  while (K < 8 && S.wmax / (2 * K) >= 8) K *= 2;
+  while (K < 16 && (long)S.nslices * K < target && S.wmax / (2 * K) >= 2) K *= 2;
+  return K;
+}
+
 template <typename T, typename VT>
 void spmv_sell_bsr3_impl(const Pattern &P, const VT *sval, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
                          cudaStream_t s) {
   const Sell &S = P.sell;
   if (S.nslices == 0) return;
-  const long target = 48L * device_sm_count();
-  int K = 1;
-  while (K < 8 && S.wmax / (2 * K) >= 8) K *= 2;
-  while (K < 16 && (long)S.nslices * K < target && S.wmax / (2 * K) >= 2) K *= 2;
+  const int K = sell_warps_bsr3(S);
   switch (K) {
     case 1: launch_sell_bsr3<T, VT, 1>(S, sval, u, out, mode, a, s); break;
     case 2: launch_sell_bsr3<T, VT, 2>(S, sval, u, out, mode, a, s); break;
@@ -1782,6 +1787,13 @@ template void sell_gather9<double>(long, const int *, const double *, double *, 
 template void sell_gather9<float>(long, const int *, const double *, float *, cudaStream_t);
 template void sell_gather9<__nv_bfloat16>(long, const int *, const double *, __nv_bfloat16 *, cudaStream_t);
 
+int sell_warps_bsr2(const Sell &S) {
+  const long target = 48L * device_sm_count();
+  int K = 1;
+  while (K < 8 && (long)S.nslices * K < target && S.wmax / (2 * K) >= 2) K *= 2;
+  return K;
+}
+
 template <typename T, typename VT>
 void spmv_sell_bsr2_impl(const Pattern &P, const VT *sval, const T *u, T *out, SpmvMode mode, const SpmvArgs &a,
                          cudaStream_t s) {
@@ -1791,9 +1803,7 @@ void spmv_sell_bsr2_impl(const Pattern &P, const VT *sval, const T *u, T *out, S
   if (!aligned(sval, 4 * sizeof(VT)))
     throw Error{CHNSS_ERR_ARG, "2x2-block values must be aligned to one block"};
   // coarse levels with fewer slices than one wave of warps: K warps per slice
-  const long target = 48L * device_sm_count();
-  int K = 1;
-  while (K < 8 && (long)S.nslices * K < target && S.wmax / (2 * K) >= 2) K *= 2;
+  const int K = sell_warps_bsr2(S);
   if (K > 1) {
     const int spb = 8 / K;
     const int g = (S.nslices + spb - 1) / spb;
