@@ -302,7 +302,7 @@ def run_gpu(args):
                 "iters_last_step": {k: v["iters"] for k, v in infosb[-1].items()}}
 
     fp64 = None
-    if not args.no_fp64:
+    if not args.no_fp64 and args.fp64_steps > 0:
         p64 = dict(params, precision=0, ortho=0)     # FP64 throughout, Gram-Schmidt included
         ctx64, ms64, infos64, _, _, _ = timed_run(p64, 1, args.fp64_steps, False)
         fp64 = {"value": args.fp64_steps / (ms64 / 1e3), "unit": "steps/s", "steps": args.fp64_steps,

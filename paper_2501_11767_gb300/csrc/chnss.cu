@@ -438,6 +438,25 @@ struct CHOp : LinearOperator {
   }
   void precond(const double *r, double *z, cudaStream_t s) override { run_prec(c, sp, r, z, s); }
   void after_sync() override { harvest_probes(c, sp); }
+  // with constant mobility the species share L, K and M: one pass over them
+  const void *batch_key() const override { return c->p.mobility_kind == 0 ? c : nullptr; }
+  void apply_batch(int n, LinearOperator *const *ops, const double *const *x, double *const *y,
+                   cudaStream_t s) override {
+    const auto &p = c->p;
+    ChCoef3 cf{};
+    MultiPtr<const double> xs;
+    MultiPtr<double> ys;
+    for (int i = 0; i < n; ++i) {
+      const int q = static_cast<const CHOp *>(ops[i])->sp;
+      const double g = p.gamma[q], b = p.beta[q];
+      cf.a12[i] = p.tau * g;
+      cf.a21[i] = p.tau * g;
+      cf.a22[i] = -p.tau * g / b;
+      xs.p[i] = x[i];
+      ys.p[i] = y[i];
+    }
+    spmv_sell_ch_multi(c->lv(0).p1, c->Ls, c->Ks, nullptr, c->Ms, n, cf, xs, ys, s);
+  }
 };
 
 struct ACOp : LinearOperator {

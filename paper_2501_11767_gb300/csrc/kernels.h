@@ -127,6 +127,14 @@ void spmv_sell_bsr2(const Pattern &P, const __nv_bfloat16 *sval, const float *u,
                     const SpmvArgs &a, cudaStream_t s);
 void spmv_sell_ch(const Pattern &P, const double *L, const double *K, const double *k12, const double *M, double a12,
                   double a21, double a22, const double *x, double *y, cudaStream_t s);
+// nr (1..kMaxRhs) CH systems that share L, K, K12 (K when null) and M, with
+// per-system coefficients: each output bitwise the spmv_sell_ch result
+struct ChCoef3 {
+  double a12[kMaxRhs], a21[kMaxRhs], a22[kMaxRhs];
+};
+void spmv_sell_ch_multi(const Pattern &P, const double *L, const double *K, const double *k12, const double *M, int nr,
+                        const ChCoef3 &cf, const MultiPtr<const double> &x, const MultiPtr<double> &y,
+                        cudaStream_t s);
 void spmv_sell_b(const Pattern &P, const double *sval2, const double *v, double *y, cudaStream_t s);
 void spmv_sell_bt_add(const Pattern &P, const double *sval2, const double *p, double *yv, cudaStream_t s);
 

@@ -896,13 +896,30 @@ chnss_status fgmres_batch(int K, LinearOperator *const *A, const double *const *
     }
     if (!any) break;
     P.apply(K, rin.data(), zout.data(), s);
+    {
+      // the active systems' operator applies, fused when their operators allow it
+      std::vector<LinearOperator *> ops;
+      std::vector<const double *> xin;
+      std::vector<double *> yout;
+      for (int q = 0; q < K; ++q)
+        if (rin[q]) {
+          ops.push_back(A[q]);
+          xin.push_back(zout[q]);
+          yout.push_back(ws[q]->w);
+        }
+      const void *key = ops[0]->batch_key();
+      bool same = key != nullptr && ops.size() > 1;
+      for (LinearOperator *o : ops) same = same && o->batch_key() == key;
+      if (same) ops[0]->apply_batch((int)ops.size(), ops.data(), xin.data(), yout.data(), s);
+      else
+        for (size_t i = 0; i < ops.size(); ++i) ops[i]->apply(xin[i], yout[i], s);
+    }
     for (int q = 0; q < K; ++q) {
       Run &r = R[q];
       if (!rin[q]) continue;
       KrylovWork &w = *ws[q];
       const long n = r.n, ld = r.ld;
       double *sc = w.sc;
-      A[q]->apply(zout[q], w.w, s);
       const int kv = r.j + 1;
       r.fast = cgs2_fast(kv);
       const int tko = prof ? prof->start(Profiler::ORTHO, s) : -1;

@@ -176,6 +176,14 @@ struct LinearOperator {
   virtual void precond(const double *r, double *z, cudaStream_t s) = 0;
   // called by the Krylov driver after each host synchronisation of the stream
   virtual void after_sync() {}
+  // Batched FGMRES: operators returning the same non-null key are applied
+  // together by apply_batch of the first one (x[i] -> y[i] for ops[i]), with
+  // results bitwise those of their own apply
+  virtual const void *batch_key() const { return nullptr; }
+  virtual void apply_batch(int n, LinearOperator *const *ops, const double *const *x, double *const *y,
+                           cudaStream_t s) {
+    for (int i = 0; i < n; ++i) ops[i]->apply(x[i], y[i], s);
+  }
 };
 
 struct KrylovWork {

@@ -649,6 +649,45 @@ __global__ void __launch_bounds__(kSellMaxBlock) k_sell_ch(int nslices, int nrow
   y[nrows + row] = a21 * s21 + a22 * s22;
 }
 
+// k_sell_ch for NR systems that share L, K, K12 and M (the CH species with
+// constant mobility): the matrix stream is read once; each system's sums are
+// the single-system kernel's expressions in the same order, so every output
+// is bitwise k_sell_ch's.
+template <int NR>
+__global__ void __launch_bounds__(kSellMaxBlock) k_sell_ch_multi(int nslices, int nrows, const int *__restrict__ sp,
+                                                      const int *__restrict__ rowid, const int *__restrict__ col,
+                                                      const double *__restrict__ L, const double *__restrict__ K,
+                                                      const double *__restrict__ K12, const double *__restrict__ M,
+                                                      ChCoef3 cf, MultiPtr<const double> x, MultiPtr<double> y) {
+  const int slice = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (slice >= nslices) return;
+  const int row = rowid[slice * 32 + lane];
+  const int b0 = sp[slice], w = (sp[slice + 1] - b0) >> 5;
+  double s11[NR], s12[NR], s21[NR], s22[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) s11[q] = s12[q] = s21[q] = s22[q] = 0;
+#pragma unroll 4
+  for (int j = 0; j < w; ++j) {
+    const int e = b0 + j * 32 + lane;
+    const int c = col[e];
+    const double lv = L[e], kv = K[e], k12 = K12 ? K12[e] : kv, mv = M[e];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      const double u1 = x.p[q][c], u2 = x.p[q][nrows + c];
+      s11[q] += lv * u1;
+      s12[q] += k12 * u2;
+      s21[q] += kv * u1;
+      s22[q] += mv * u2;
+    }
+  }
+  if (row < 0) return;
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    y.p[q][row] = s11[q] + cf.a12[q] * s12[q];
+    y.p[q][nrows + row] = cf.a21[q] * s21[q] + cf.a22[q] * s22[q];
+  }
+}
+
 template <bool VEC>
 __global__ void __launch_bounds__(kSellMaxBlock) k_sell_b(int nslices, const int *__restrict__ sp, const int *__restrict__ rowid,
                                                 const int *__restrict__ col, const double *__restrict__ val2,
@@ -1853,6 +1892,25 @@ void spmv_sell_ch(const Pattern &P, const double *L, const double *K, const doub
   const Sell &S = P.sell;
   k_sell_ch<<<nblocks((long)S.nslices * 32, S.block), S.block, 0, s>>>(S.nslices, P.nrows, S.slice_ptr, S.rowid, S.col, L, K,
                                                                k12, M, a12, a21, a22, x, y);
+  CHNSS_LAUNCH_CK();
+}
+void spmv_sell_ch_multi(const Pattern &P, const double *L, const double *K, const double *k12, const double *M, int nr,
+                        const ChCoef3 &cf, const MultiPtr<const double> &x, const MultiPtr<double> &y,
+                        cudaStream_t s) {
+  const Sell &S = P.sell;
+  const int nb = nblocks((long)S.nslices * 32, S.block);
+  switch (nr) {
+    case 1:
+      k_sell_ch_multi<1><<<nb, S.block, 0, s>>>(S.nslices, P.nrows, S.slice_ptr, S.rowid, S.col, L, K, k12, M, cf, x, y);
+      break;
+    case 2:
+      k_sell_ch_multi<2><<<nb, S.block, 0, s>>>(S.nslices, P.nrows, S.slice_ptr, S.rowid, S.col, L, K, k12, M, cf, x, y);
+      break;
+    case 3:
+      k_sell_ch_multi<3><<<nb, S.block, 0, s>>>(S.nslices, P.nrows, S.slice_ptr, S.rowid, S.col, L, K, k12, M, cf, x, y);
+      break;
+    default: throw Error{CHNSS_ERR_ARG, "CH operator: 1 to 3 systems"};
+  }
   CHNSS_LAUNCH_CK();
 }
 void spmv_sell_b(const Pattern &P, const double *sval2, const double *v, double *y, cudaStream_t s) {
