@@ -271,3 +271,16 @@ def l2_error_velocity(mesh: Mesh, vh, fn, degree: int = 8):
     fx, fy = fn(X[..., 0], X[..., 1])
     d = p2_field_at(mesh, vh, lam) - np.stack([fx, fy], axis=-1)
     return float(np.sqrt(np.sum(area[:, None] * w[None] * np.sum(d * d, axis=-1))))
+
+
+def convection_p1_wind(mesh: Mesh, wind):
+    """C_ab = int (w . grad psi_b) psi_a with w a P1 vector field given at
+    the vertices, (N1, 2) (the convection matrix C of Sec. 4 with a
+    prescribed velocity; also on oracle.mesh.TriMesh)."""
+    lam, w = triangle_rule(2)
+    _, area, g = mesh.element_geometry()
+    phi = p1_values(lam)                                    # (Q,3)
+    wq = np.einsum("qk,ekd->eqd", phi, np.asarray(wind)[mesh.tri])   # (E,Q,2)
+    vg = np.einsum("eqd,ebd->eqb", wq, g)                   # (E,Q,3)
+    loc = area[:, None, None] * np.einsum("q,qa,eqb->eab", w, phi, vg)
+    return _scatter(loc, mesh.tri, mesh.tri, (mesh.N1, mesh.N1))

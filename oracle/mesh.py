@@ -94,3 +94,18 @@ class Mesh:
         g[:, 2] = inv[:, 1, :]
         g[:, 0] = -g[:, 1] - g[:, 2]
         return X, 0.5 * np.abs(det), g
+
+
+class TriMesh(Mesh):
+    """A general triangulation given by its vertex coordinates x (N, 2) and
+    counter-clockwise triangles tri (E, 3): the P1 forms of oracle.fem that
+    need only x1, tri, N1, E and element_geometry work on it unchanged (the
+    P2 lattice of the structured mesh does not exist here)."""
+
+    def __init__(self, x, tri):
+        self.x1 = np.asarray(x, dtype=np.float64)
+        self.tri = np.asarray(tri, dtype=np.int64)
+        self.N1 = self.x1.shape[0]
+        self.E = self.tri.shape[0]
+        self.n = None
+        self.top_free = False

@@ -124,25 +124,29 @@ def inject_velocity(v, nf):
 class MG:
     """One V-cycle of geometric multigrid for a hierarchy of matrices."""
 
-    def __init__(self, mats, prolongs, singular=False, degree=None, ratio=None, dense_coarse=False):
+    def __init__(self, mats, prolongs, singular=False, degree=None, ratio=None, dense_coarse=False, his=None):
+        """his: per-level upper ends of the smoothing intervals in place of
+        the Gershgorin bounds (the algebraic hierarchies of oracle.amg)."""
         self.mats = mats
         self.degree = SMOOTH_DEGREE if degree is None else degree
         self.ratio = LO_RATIO if ratio is None else ratio
         self.P = prolongs                     # P[l]: level l+1 -> level l
         self.singular = singular
         self.dinv, self.hi = [], []
-        for A in mats[:-1]:
+        for l, A in enumerate(mats[:-1]):
             d = A.diagonal()
             self.dinv.append(1.0 / d)
             absA = abs(A)
-            self.hi.append(float(np.max(np.asarray(absA.sum(axis=1)).ravel() / np.abs(d))))
+            self.hi.append(float(np.max(np.asarray(absA.sum(axis=1)).ravel() / np.abs(d)))
+                           if his is None else float(his[l]))
         self.coarse_iter = (len(mats) > 1 and not singular and not dense_coarse
                             and mats[-1].shape[0] > COARSE_DENSE_MAX)
         if self.coarse_iter:
             A = mats[-1]
             d = A.diagonal()
             self.cdinv = 1.0 / d
-            self.chi = float(np.max(np.asarray(abs(A).sum(axis=1)).ravel() / np.abs(d)))
+            self.chi = (float(np.max(np.asarray(abs(A).sum(axis=1)).ravel() / np.abs(d)))
+                        if his is None else float(his[-1]))
             self.lu = None
         else:
             Ac = mats[-1].toarray()

@@ -239,3 +239,37 @@ def sweep_instances(count: int = 64, seed: int = 0) -> list:
         p.update(evap_rate=0.05 + 0.45 * float(u[2 * i + 1]), precision=1, ortho=1)
         out.append({"n": n, "params": p, "seed": 1000 + i})
     return out
+
+
+FIELD_MESH = 9           # key space of the unstructured-mesh draws
+
+
+def unstructured_square(n: int, seed: int = 0, jitter: float = 0.2):
+    """A seeded unstructured triangulation of the unit square: the (n+1)^2
+    lattice with every interior node moved by up to jitter * h in each
+    coordinate, and every square split along a diagonal drawn at random
+    (vertex degrees 3 to 8 instead of the structured mesh's 6).  Returns
+    (x (N, 2) float64, tri (E, 3) int64, counter-clockwise), the node (i, j)
+    at index j * (n + 1) + i."""
+    h = 1.0 / n
+    m = n + 1
+    N = m * m
+    u = uniform_noise(seed, FIELD_MESH, 2 * N + n * n, amp=1.0)       # U[-1, 1)
+    ii, jj = np.meshgrid(np.arange(m), np.arange(m), indexing="xy")
+    ii, jj = ii.ravel(), jj.ravel()
+    x = np.stack([ii * h, jj * h], axis=1).astype(np.float64)
+    inner = (ii > 0) & (ii < n) & (jj > 0) & (jj < n)
+    x[inner, 0] += jitter * h * u[0:N][inner]
+    x[inner, 1] += jitter * h * u[N:2 * N][inner]
+    si, sj = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    si, sj = si.ravel(), sj.ravel()
+    v = lambda a, b: b * m + a          # noqa: E731
+    flip = u[2 * N:] >= 0.0                                        # split along the other diagonal
+    tri = np.empty((2 * n * n, 3), dtype=np.int64)
+    lo = np.stack([v(si, sj), v(si + 1, sj), v(si + 1, sj + 1)], axis=1)
+    up = np.stack([v(si, sj), v(si + 1, sj + 1), v(si, sj + 1)], axis=1)
+    lo_f = np.stack([v(si, sj), v(si + 1, sj), v(si, sj + 1)], axis=1)
+    up_f = np.stack([v(si + 1, sj), v(si + 1, sj + 1), v(si, sj + 1)], axis=1)
+    tri[0::2] = np.where(flip[:, None], lo_f, lo)
+    tri[1::2] = np.where(flip[:, None], up_f, up)
+    return x, tri
