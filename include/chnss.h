@@ -541,6 +541,76 @@ chnss_status chnss_set_spmv_block(chnss_ctx_t ctx, int block_p1, int block_p2);
  * when ctx is NULL).  Valid until the next call on the same context. */
 const char *chnss_last_error(chnss_ctx_t ctx);
 
+/* ------------------------------------------------------------------------
+ * Smoothed-aggregation algebraic multigrid for a general sparse operator.
+ *
+ * Sec. 5 builds the block preconditioners with PyAMG's algebraic multigrid:
+ * smoothed aggregation (SA) for the nonsymmetric Cahn-Hilliard blocks
+ * M + tau C (Sec. 4) and for every Navier-Stokes block of the 3D runs, on
+ * meshes that need not be structured.  This handle runs the SA setup on the
+ * device for a square CSR matrix A with the constant near-null space:
+ *   strength graph: every stored off-diagonal entry (theta = 0);
+ *   aggregates: a maximal distance-2 independent set of that graph (synchronous
+ *     rounds on the keys (state, 30 leading bits of SplitMix64 output number
+ *     (level << 32) + i, i)), every neighbour of a root joining its adjacent
+ *     root of largest key, every remaining node its assigned neighbour of
+ *     largest key;
+ *   T[i, agg(i)] = 1 / sqrt(|agg(i)|);  P = T - (4 / (3 hi)) D^-1 (A T);
+ *   A_c = P^T (A P);  hi = min(Gershgorin bound, 1.1 x a 10-step power
+ *     estimate of rho(D^-1 A) from a +-1 start vector drawn with SplitMix64
+ *     outputs ((level + 64) << 32) + i),
+ * adding levels while a level has more than 256 rows (at most 12 levels).
+ * Its V-cycle: Chebyshev-Jacobi pre- and post-smoothing of degree 2 on
+ * [hi / 4, hi], restriction P^T, prolongation P, a dense FP64 inverse on a
+ * coarsest level of at most 256 rows (otherwise 16 Chebyshev steps).  P and
+ * A_c keep every structurally non-zero entry; every sum runs in a fixed
+ * order, so the hierarchy and every result are bit-reproducible.
+ *
+ * A must be square with n >= 1 rows, its columns sorted and unique within
+ * each row, a stored diagonal with non-zero values, and a structurally
+ * symmetric pattern (entry (j, i) stored whenever (i, j) is: every finite-
+ * element matrix); product rows of more than 512 entries are refused.
+ * Errors are returned as statuses, with the message in chnss_last_error(NULL).
+ * All pointers are DEVICE pointers unless the function says "host"; the
+ * calls run on the handle's own stream and synchronise it before returning.
+ */
+typedef struct chnss_amg *chnss_amg_t;
+
+/* Build the hierarchy of A (rowptr[n + 1], col[nnz], val[nnz]: device CSR,
+ * read during the call only; the handle keeps its own copy of the values).
+ * precision 0: the V-cycle in FP64; 1: level values, smoothing and
+ * transfers in FP32 (the setup is FP64 either way).  CHNSS_ERR_ARG for a
+ * matrix that breaks the rules above (nothing is kept), CHNSS_ERR_OOM /
+ * CHNSS_ERR_CUDA on device failures. */
+chnss_status chnss_amg_create(int n, int nnz, const int *rowptr, const int *col, const double *val, int precision,
+                              chnss_amg_t *out);
+/* New values of A on the same pattern (val: device, nnz doubles): the
+ * aggregates and every pattern are kept (they depend on the pattern only),
+ * the spectral bounds, prolongators, coarse operators and smoother data
+ * are recomputed, as a per-step re-setup of the paper's time loop needs. */
+chnss_status chnss_amg_update(chnss_amg_t h, const double *val);
+/* Level count and, per level l < *nlevels (host arrays of at least 12
+ * entries, each may be NULL): rows, nnz of A_l, nnz of P_l (0 on the
+ * coarsest level). */
+chnss_status chnss_amg_levels(chnss_amg_t h, int *nlevels, int *rows, int *nnz, int *pnnz);
+/* Copy level l to HOST arrays (each may be NULL): agg[rows] (aggregate of
+ * every node; level < nlevels - 1), hi (spectral bound), A_l as
+ * a_rowptr[rows + 1], a_col[nnz], a_val[nnz], and P_l (rows x rows of level
+ * l + 1) as p_rowptr[rows + 1], p_col[pnnz], p_val[pnnz]. */
+chnss_status chnss_amg_export_level(chnss_amg_t h, int level, int *agg, double *hi, int *a_rowptr, int *a_col,
+                                    double *a_val, int *p_rowptr, int *p_col, double *p_val);
+/* x = one V-cycle applied to b (device, n doubles each; may not overlap). */
+chnss_status chnss_amg_vcycle(chnss_amg_t h, const double *b, double *x);
+/* Solve A x = b by right-preconditioned FGMRES(30) with one V-cycle as the
+ * preconditioner, from x = 0, to ||b - A x|| <= max(rtol ||b||, atol) or
+ * maxit iterations (Sec. 5 solver setup; the operator applied in FP64).
+ * b and x: device, n doubles, may not overlap.  CHNSS_ERR_NOCONV at maxit
+ * (x holds the last iterate); info (host, may be NULL) as chnss_solve. */
+chnss_status chnss_amg_solve(chnss_amg_t h, const double *b, double *x, double rtol, double atol, int maxit,
+                             chnss_solve_info *info);
+/* Release everything the handle owns (NULL is ignored). */
+void chnss_amg_destroy(chnss_amg_t h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libchnss.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["setup.cu", "assemble.cu", "sparse.cu", "solver.cu", "chnss.cu", "three_d.cu"]
+SOURCES = ["setup.cu", "assemble.cu", "sparse.cu", "solver.cu", "chnss.cu", "three_d.cu", "amg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + INCLUDE]

@@ -168,6 +168,16 @@ EXPORTS = {
     "chnss_set_step_concurrency": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss_set_step_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "chnss_amg_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "chnss_amg_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "chnss_amg_levels": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "chnss_amg_export_level": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 8),
+    "chnss_amg_vcycle": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "chnss_amg_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
+    "chnss_amg_destroy": (None, [ctypes.c_void_p]),
 }
 
 
@@ -629,3 +639,83 @@ def state_to_device(state: dict, device="cuda") -> dict:
 
 def state_to_numpy(state: dict) -> dict:
     return {k: v.detach().cpu().numpy() for k, v in state.items()}
+
+
+def _int32_device(t, n):
+    """Address of a contiguous int32 CUDA tensor of at least n entries."""
+    if not hasattr(t, "data_ptr") or not t.is_cuda or str(t.dtype) != "torch.int32" or not t.is_contiguous():
+        raise ValueError("chnss needs contiguous int32 CUDA tensors here")
+    if t.numel() < n:
+        raise ValueError(f"chnss: an array of {t.numel()} elements where {n} are needed")
+    return t.data_ptr()
+
+
+class Amg:
+    """Smoothed-aggregation AMG hierarchy of a square CSR matrix on the device
+    (chnss_amg_*): rowptr / col int32 and val float64 CUDA tensors."""
+
+    def __init__(self, rowptr, col, val, precision: int = 0):
+        n = rowptr.numel() - 1
+        nnz = col.numel()
+        self.n, self.nnz = n, nnz
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.chnss_amg_create(n, nnz, _int32_device(rowptr, n + 1), _int32_device(col, nnz),
+                                    _ptr(val, nnz, "device"), int(precision), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().chnss_amg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, val):
+        _check(load().chnss_amg_update(self._h, _ptr(val, self.nnz, "device")))
+
+    def levels(self):
+        """[(rows, nnz of A_l, nnz of P_l)] per level."""
+        nl = ctypes.c_int()
+        rows, nnz, pnnz = (np.zeros(12, np.int32) for _ in range(3))
+        _check(load().chnss_amg_levels(self._h, ctypes.byref(nl), rows.ctypes.data, nnz.ctypes.data,
+                                       pnnz.ctypes.data))
+        return [(int(rows[l]), int(nnz[l]), int(pnnz[l])) for l in range(nl.value)]
+
+    def export_level(self, level: int) -> dict:
+        """Level l on the host: A (rowptr, col, val), hi, and unless it is the
+        coarsest, agg and P (rowptr, col, val)."""
+        lv = self.levels()
+        rows, nnz, pnnz = lv[level]
+        last = level == len(lv) - 1
+        out = {"hi": np.zeros(1), "a_rowptr": np.zeros(rows + 1, np.int32), "a_col": np.zeros(nnz, np.int32),
+               "a_val": np.zeros(nnz)}
+        if not last:
+            out.update(agg=np.zeros(rows, np.int32), p_rowptr=np.zeros(rows + 1, np.int32),
+                       p_col=np.zeros(pnnz, np.int32), p_val=np.zeros(pnnz))
+        g = lambda k: out[k].ctypes.data if k in out else None   # noqa: E731
+        _check(load().chnss_amg_export_level(self._h, level, g("agg"), g("hi"), g("a_rowptr"), g("a_col"),
+                                             g("a_val"), g("p_rowptr"), g("p_col"), g("p_val")))
+        out["hi"] = float(out["hi"][0])
+        return out
+
+    def vcycle(self, b, x=None):
+        import torch
+        x = torch.empty_like(b) if x is None else x
+        _check(load().chnss_amg_vcycle(self._h, _ptr(b, self.n, "device"), _ptr(x, self.n, "device")))
+        return x
+
+    def solve(self, b, x=None, rtol=1e-8, atol=0.0, maxit=500, check=True):
+        import torch
+        x = torch.empty_like(b) if x is None else x
+        info = SolveInfo()
+        st = load().chnss_amg_solve(self._h, _ptr(b, self.n, "device"), _ptr(x, self.n, "device"), rtol, atol,
+                                    maxit, ctypes.byref(info))
+        if check and st != 0:
+            _check(st)
+        return x, {"iters": info.iters, "converged": bool(info.converged), "rel_residual": info.rel_residual,
+                   "seconds": info.seconds}, st

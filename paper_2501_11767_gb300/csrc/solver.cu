@@ -270,6 +270,8 @@ void MGHier<T>::setup(cudaStream_t s) {
       jacobi_bsr2<T>(*pat[l], val64[l], diag[l], dinv[l], hi[l], partial, s);
     else
       jacobi_csr<T>(*pat[l], val64[l], diag[l], dinv[l], hi[l], partial, s);
+    if (!hi_ext.empty())
+      CHNSS_CK(cudaMemcpyAsync(hi[l], hi_ext[l], sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (l == nl - 1)
       cheb_coefficients(hi[l], kCoarseRatio, kCoarseDegree, coef[l], s);
     else

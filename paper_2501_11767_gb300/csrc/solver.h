@@ -81,6 +81,9 @@ struct MGHier {
   Profiler *prof = nullptr;
   bool bf16 = false;       // level values stored in BF16 (T = float only; set before init)
   std::vector<__nv_bfloat16 *> val16;
+  // set before setup: per-level smoothing bounds (device scalars) in place of
+  // the Gershgorin bounds (the algebraic hierarchies of amg.cu)
+  std::vector<const double *> hi_ext;
   int degree = 2;          // Chebyshev smoothing degree (pre and post)
   double ratio = 4.0;      // smoothing interval [hi / ratio, hi]
   // levels tail_l0.. (at most kTailRows rows each) run as one block launch

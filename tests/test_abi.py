@@ -139,3 +139,17 @@ def test_binding_checks_array_sizes_and_placement():
     st3 = inputs.initial_state_3d(n, seed=0)
     with pytest.raises(ValueError):
         chnss.host_operator3(n, "C1", inputs.default_params(), dict(st3, v=st3["v"][:-3].copy()))
+
+
+def test_amg_argument_errors_need_no_device(lib):
+    h = ctypes.c_void_p()
+    assert lib.chnss_amg_create(0, 0, None, None, None, 0, ctypes.byref(h)) == 1
+    assert lib.chnss_amg_create(4, 4, None, None, None, 0, ctypes.byref(h)) == 1
+    assert lib.chnss_amg_create(4, 4, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), 2,
+                                ctypes.byref(h)) == 1          # unknown precision
+    assert b"precision" in lib.chnss_last_error(None)
+    assert lib.chnss_amg_create(4, 4, None, None, None, 0, None) == 1
+    assert lib.chnss_amg_update(None, None) == 1
+    assert lib.chnss_amg_vcycle(None, None, None) == 1
+    assert lib.chnss_amg_solve(None, None, None, 1e-8, 0.0, 10, None) == 1
+    lib.chnss_amg_destroy(None)
