@@ -15,6 +15,7 @@ advances from step to step.  One JSON line on rank 0.
   python bench.py --impl reference     # the CPU oracle on the same metric
   python bench.py --sweep              # 64 independent instances, chnss_step_batched
   python bench.py --adjoint            # gradient through 40 FP64 steps on 256 x 256
+  python bench.py --amg                # smoothed-aggregation AMG on the CH block M + tau C(v)
 """
 from __future__ import annotations
 
@@ -647,6 +648,92 @@ def run_three_d(args):
     print(json.dumps(out))
 
 
+AMG_METRIC = ("SA-AMG re-setups + solves/s of the Cahn-Hilliard block M + tau C(v) at {n}x{n} "
+              "(numeric setup on the step's new values, then SA-preconditioned FGMRES to 1e-8)")
+
+
+def run_amg(args):
+    """The paper's per-step use of smoothed aggregation (Sec. 5: SA for the
+    nonsymmetric Cahn-Hilliard blocks): the block L = M + tau C(v) of the
+    1024^2 film workload, assembled by the library after args.warmup mixed
+    steps (so that C(v) carries the flow), is given to chnss_amg_create
+    (symbolic + numeric setup, timed once); a timed repetition is
+    chnss_amg_update on the current values (spectral bounds, prolongators,
+    Galerkin products, smoother data) followed by chnss_amg_solve of L x = b
+    (b: the polymer CH right-hand side's first block) in FP64 and FP32
+    hierarchies.  CUDA events on the handle's synchronised calls, inputs
+    resident on the device."""
+    import numpy as np
+    import torch
+
+    from paper_2501_11767_gb300 import chnss, inputs
+
+    torch.cuda.set_device(0)
+    w = inputs.workload(args.workload)
+    n, params = w["n"], dict(w["params"])
+    mesh = chnss.Mesh(n)
+    stream = torch.cuda.current_stream()
+    ctx = chnss.Context(mesh, params, stream)
+    a, b = chnss.state_to_device(inputs.initial_state(n, seed=0)), ctx.new_state()
+    for _ in range(args.warmup):
+        ctx.step(a, b)
+        a, b = b, a
+    ctx.assemble(a)
+    rp, col, val = ctx.export_csr(0)
+    rhs = ctx.export_rhs(0)[:mesh.N1]
+    torch.cuda.synchronize()
+    d = lambda x, t: torch.as_tensor(x, dtype=t, device="cuda")   # noqa: E731
+    rp_d, col_d, val_d, b_d = d(rp, torch.int32), d(col, torch.int32), d(val, torch.float64), d(rhs, torch.float64)
+    out = {}
+    sampler = ClockSampler(_device_uuid(torch, 0))
+    for prec, key in ((1, "fp32_hierarchy"), (0, "fp64_hierarchy")):
+        t0 = time.perf_counter()
+        h = chnss.Amg(rp_d, col_d, val_d, precision=prec)
+        create_s = time.perf_counter() - t0
+        for _ in range(2):                        # warm-up repetitions
+            h.update(val_d)
+            h.solve(b_d, rtol=1e-8)
+        torch.cuda.synchronize()
+        if prec == 1:
+            sampler.start()
+            torch.cuda.nvtx.range_push("amg")      # the timed FP32-hierarchy repetitions (ncu --nvtx-include)
+        t_upd, t_sol, iters = [], [], []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            h.update(val_d)
+            t1 = time.perf_counter()
+            x, info, _ = h.solve(b_d, rtol=1e-8)
+            t2 = time.perf_counter()
+            t_upd.append(t1 - t0)
+            t_sol.append(t2 - t1)
+            iters.append(info["iters"])
+        if prec == 1:
+            torch.cuda.nvtx.range_pop()
+            clocks = sampler.stop()
+        xr = x.cpu().numpy()
+        Lx = np.zeros(mesh.N1)
+        np.add.at(Lx, np.repeat(np.arange(mesh.N1), np.diff(rp)), val * xr[col])
+        res = float(np.linalg.norm(rhs - Lx) / np.linalg.norm(rhs))
+        out[key] = {"create_s": round(create_s, 3), "update_ms": round(1e3 * statistics.median(t_upd), 2),
+                    "solve_ms": round(1e3 * statistics.median(t_sol), 2), "iters": iters[-1],
+                    "rel_residual": res, "levels": h.levels(),
+                    "value": round(args.steps / (sum(t_upd) + sum(t_sol)), 3)}
+        h.close()
+    head = out["fp32_hierarchy"]
+    line = {
+        "metric": AMG_METRIC.format(n=n), "value": head["value"], "unit": "setups+solves/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(head["update_ms"] + head["solve_ms"], 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 outer / f32 hierarchy",
+        "data": "synthetic (the 1024^2 film state after the warm-up steps)",
+        "config": {"workload": f"amg_ch_block{n}", "n": n, "rows": mesh.N1, "nnz": int(len(col)),
+                   "tau": params["tau"], "rtol": 1e-8, "parallelism": "single GPU",
+                   "l2": "matrix and hierarchy larger than L2"},
+        "clocks": clocks, **out,
+    }
+    print(json.dumps(line))
+
+
 def run_sweep(args):
     """Batched parameter sweep (the 64-instance workload): independent
     instances of uneven mesh size and evaporation rate, one context (and
@@ -868,6 +955,7 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="batched 64-instance parameter sweep instead")
     ap.add_argument("--adjoint", action="store_true", help="40-step gradient on 256x256 instead")
     ap.add_argument("--three-d", action="store_true", help="the 3D step on a Kuhn mesh instead")
+    ap.add_argument("--amg", action="store_true", help="smoothed-aggregation AMG on the 1024^2 CH block instead")
     ap.add_argument("--three-d-n", type=int, default=32)
     ap.add_argument("--nvtx-step", action="store_true",
                     help="with --three-d: one serial mixed step inside an NVTX range (profiling), no timing")
@@ -901,6 +989,9 @@ def main():
         return
     if args.three_d:
         run_three_d(args)
+        return
+    if args.amg:
+        run_amg(args)
         return
     run_gpu(args)
 

@@ -709,11 +709,15 @@ chnss_status chnss_amg_create(int n, int nnz, const int *rowptr, const int *col,
       if (c < 0 || c >= n) throw Error{CHNSS_ERR_ARG, "column out of range"};
       if (k > hrp[i] && hcol[k - 1] >= c) throw Error{CHNSS_ERR_ARG, "columns must be sorted and unique in each row"};
       has_diag |= c == i;
-      const int *b = hcol.data() + hrp[c], *e = hcol.data() + hrp[c + 1];
-      if (!std::binary_search(b, e, i)) throw Error{CHNSS_ERR_ARG, "the pattern must be structurally symmetric"};
     }
     if (!has_diag) throw Error{CHNSS_ERR_ARG, "every row needs its diagonal entry"};
   }
+  for (int i = 0; i < n; ++i)   // (rows sorted: binary search)
+    for (int k = hrp[i]; k < hrp[i + 1]; ++k) {
+      const int c = hcol[k];
+      const int *b = hcol.data() + hrp[c], *e = hcol.data() + hrp[c + 1];
+      if (!std::binary_search(b, e, i)) throw Error{CHNSS_ERR_ARG, "the pattern must be structurally symmetric"};
+    }
   H = std::make_unique<chnss_amg>();
   AmgHandle &h = H->h;
   h.n = n;
