@@ -559,7 +559,7 @@ const char *chnss_last_error(chnss_ctx_t ctx);
  *   A_c = P^T (A P);  hi = min(Gershgorin bound, 1.1 x a 10-step power
  *     estimate of rho(D^-1 A) from a +-1 start vector drawn with SplitMix64
  *     outputs ((level + 64) << 32) + i),
- * adding levels while a level has more than 256 rows (at most 12 levels).
+ * adding levels while a level has more than 64 rows (at most 12 levels).
  * Its V-cycle: Chebyshev-Jacobi pre- and post-smoothing of degree 2 on
  * [hi / 4, hi], restriction P^T, prolongation P, a dense FP64 inverse on a
  * coarsest level of at most 256 rows (otherwise 16 Chebyshev steps).  P and

@@ -49,7 +49,7 @@ from paper_2501_11767_gb300.inputs import splitmix64
 
 from .mg import MG
 
-COARSE_ROWS = 256
+COARSE_ROWS = 64
 MAX_LEVELS = 12
 POWER_STEPS = 10
 POWER_SAFETY = 1.1

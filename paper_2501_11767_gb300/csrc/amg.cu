@@ -39,7 +39,7 @@ namespace {
 constexpr int TPB = 256;
 constexpr int kAmgMaxRow = 512;      // widest row of a product pattern
 constexpr int kAmgMaxLevels = 12;
-constexpr int kAmgCoarseRows = 256;  // levels are added while a level is larger
+constexpr int kAmgCoarseRows = 64;   // levels are added while a level is larger
 constexpr int kAmgPowerSteps = 10;
 constexpr double kAmgPowerSafety = 1.1;
 constexpr int kAmgMaxRounds = 100000;

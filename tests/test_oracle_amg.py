@@ -144,7 +144,7 @@ def _sa_iterations(n, seed=0, wind=None, tau=1.0):
 def test_sa_preconditioner_mesh_robust_on_unstructured_meshes():
     """M + K on unstructured meshes (stiffness-dominated: the condition
     number grows like h^-2): SA-preconditioned FGMRES iterations grow by a
-    few from 16^2 to 64^2 meshes (13, 14, 19: cheap degree-2 smoothing and
+    few from 16^2 to 64^2 meshes (13, 17, 19: cheap degree-2 smoothing and
     ~10:1 aggregates) while the hierarchy deepens; a dropped or sign-flipped
     prolongator smoothing (below) takes 57 or 122 at 64^2."""
     its, levels = [], []
