@@ -738,9 +738,9 @@ def run_sweep(args):
     """Batched parameter sweep (the 64-instance workload): independent
     instances of uneven mesh size and evaporation rate, one context (and
     stream) each, FP32 preconditioners inside FP64 FGMRES with double-FP32
-    Gram-Schmidt.  Headline: every instance step one recorded CUDA graph
-    (chnss_set_step_mode 1), all instances launched by chnss_step_batched
-    from one thread, args.sweep_steps steps each.  Beside it: the same batch
+    Gram-Schmidt.  Headline: every instance step recorded as a branch of
+    one CUDA graph (chnss_set_step_mode 1), launched once per batch step by
+    chnss_step_batched, args.sweep_steps steps each.  Beside it: the same batch
     host-driven (worker threads, one synchronisation per Krylov iteration),
     and the instances' FP64 steps one instance at a time.  Under torchrun the
     instances are sharded round-robin over the ranks (a fixed sweep: strong
@@ -793,6 +793,7 @@ def run_sweep(args):
         torch.cuda.synchronize()
         t_rec = time.perf_counter() - t_rec
         launches0 = ctxs[0].profile_read()["launches"]
+        stats0 = chnss.batch_stats()
         sampler = ClockSampler(_device_uuid(torch, local))
         barrier()
         sampler.start()
@@ -807,6 +808,8 @@ def run_sweep(args):
         barrier()
         clocks = sampler.stop()
         launches = ctxs[0].profile_read()["launches"] - launches0
+        stats1 = chnss.batch_stats()
+        batch_calls = {k: stats1[k] - stats0[k] for k in stats1}
         if world > 1:
             t = torch.tensor([sec], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -815,13 +818,13 @@ def run_sweep(args):
         mean = {k: round(sum(r[k]["iters"] for rs in iters for r in rs) / (len(iters) * len(recs)), 2) for k in recs[0]}
         final = [chnss.state_to_numpy(x) for x in a]
         del ctxs, a, b
-        return sec, clocks, launches, conv, mean, t_rec, final
+        return sec, clocks, launches, conv, mean, t_rec, final, batch_calls
 
-    sec_g, clocks, launches, conv_g, iters_g, rec_g, fin_g = timed_sweep(1, args.sweep_steps, args.warmup)
+    sec_g, clocks, launches, conv_g, iters_g, rec_g, fin_g, batch_g = timed_sweep(1, args.sweep_steps, args.warmup)
     value = len(all_inst) * args.sweep_steps / sec_g
     host = None
     if args.sweep_host_steps > 0:
-        sec_h, _, _, conv_h, iters_h, _, fin_h = timed_sweep(0, args.sweep_host_steps, args.warmup)
+        sec_h, _, _, conv_h, iters_h, _, fin_h, _ = timed_sweep(0, args.sweep_host_steps, args.warmup)
         host = {"value": round(len(all_inst) * args.sweep_host_steps / sec_h, 3), "unit": "instance steps/s",
                 "steps": args.sweep_host_steps, "converged": conv_h, "iters_mean": iters_h,
                 "how": "the same batch with host-driven Krylov loops: chnss_step_batched on "
@@ -857,7 +860,10 @@ def run_sweep(args):
                    "total_p1_nodes": sum((i["n"] + 1) ** 2 for i in all_inst),
                    "evap_rate": [round(min(i["params"]["evap_rate"] for i in all_inst), 4),
                                  round(max(i["params"]["evap_rate"] for i in all_inst), 4)],
-                   "step": "one recorded CUDA graph per instance step (Krylov loops as conditional nodes)",
+                   "step": ("every instance's step a branch of one recorded CUDA graph, one launch per batch "
+                            "step (Krylov loops as conditional nodes)" if batch_g["one_graph"] == args.sweep_steps
+                            else "one recorded CUDA graph per instance step (Krylov loops as conditional nodes)"),
+                   "batch_calls": batch_g,
                    "gram_schmidt": "double-FP32",
                    "l2": "inputs larger than L2 (tens of GB resident)",
                    "timing": "wall clock around chnss_step_batched (it returns after every stream is synchronised)"},

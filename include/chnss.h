@@ -509,10 +509,20 @@ chnss_status chnss_step_batched(int n_inst, chnss_ctx_t *ctxs, const chnss_state
  * chnss_set_spmv_block or chnss_set_step_concurrency.  Solve records
  * (iterations, convergence, residual, status) are returned as in mode 0
  * once the graph has finished.  Needs restart <= 31 (CHNSS_ERR_ARG).  With
- * every context of a chnss_step_batched call in mode 1, the batch is one
- * graph launch per instance from the calling thread, then one
- * synchronisation per instance stream (max_threads is ignored). */
+ * every context of a chnss_step_batched call in mode 1 (and at least two of
+ * them), the whole batch is ONE graph launch: every instance's step is
+ * recorded as a parallel branch of one graph (on the first call with a given
+ * list of contexts and states; the two most recent lists are kept, and a
+ * list is recorded again after one of its contexts re-records its graphs),
+ * launched on a library stream after each context's stream has drained,
+ * then one synchronisation (max_threads is ignored).  If that graph cannot
+ * be recorded, the batch falls back to one graph launch per instance on
+ * its own stream.  Destroying a context drops the batch graphs that hold it. */
 chnss_status chnss_set_step_mode(chnss_ctx_t ctx, int mode);
+/* Counters of chnss_step_batched calls in this process that ran as one
+ * batch graph launch (*one_graph) and as one graph launch per instance
+ * (*per_instance); either pointer may be NULL. */
+chnss_status chnss_batch_stats(long long *one_graph, long long *per_instance);
 
 /* Launch-shape autotuner.  Times the fine-level SpMV of the scalar (P1) and
  * of the velocity (2x2-block) multigrid operator of ctx for threads-per-block

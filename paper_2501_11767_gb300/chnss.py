@@ -168,6 +168,7 @@ EXPORTS = {
     "chnss_set_step_concurrency": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss_set_step_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "chnss_batch_stats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "chnss_amg_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "chnss_amg_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -629,6 +630,13 @@ def step_batched(ctxs, states_in, states_out=None, max_threads: int = 0, check: 
         _check(st, None)
     recs = [{SYSTEM_NAMES[k]: infos[6 * i + k].as_dict() for k in range(6)} for i in range(n)]
     return states_out, recs, st
+
+
+def batch_stats() -> dict:
+    """chnss_step_batched calls run as one batch graph / one graph per instance."""
+    a, b = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load().chnss_batch_stats(ctypes.byref(a), ctypes.byref(b)))
+    return {"one_graph": a.value, "per_instance": b.value}
 
 
 def state_to_device(state: dict, device="cuda") -> dict:

@@ -165,6 +165,7 @@ struct chnss_ctx {
   bool recording = false;                   // preconditioners record their bodies inline
   StepGraph sgr[2];
   int sg_next = 0;
+  unsigned long long sg_gen = 0;               // bumped whenever the recorded graphs are dropped
   cudaStream_t rq0 = nullptr;                  // private stream the step is recorded on
   cudaStream_t rq1 = nullptr, rq2 = nullptr;   // capture streams of the conditional bodies
   double *srec = nullptr, *srec_h = nullptr;   // per solve [iterations, converged, rel. residual, status]
@@ -1260,16 +1261,20 @@ void record_step_body(chnss_ctx *c, const chnss_state *in, chnss_state *out) {
   CHNSS_CK(cudaMemcpyAsync(c->srec_h, c->srec, 24 * sizeof(double), cudaMemcpyDeviceToHost, s));
 }
 
+// the private streams a step is recorded on, and the pinned solve records
+void ensure_record_streams(chnss_ctx *c) {
+  if (c->rq1) return;
+  CHNSS_CK(cudaStreamCreateWithFlags(&c->rq0, cudaStreamNonBlocking));
+  CHNSS_CK(cudaStreamCreateWithFlags(&c->rq1, cudaStreamNonBlocking));
+  CHNSS_CK(cudaStreamCreateWithFlags(&c->rq2, cudaStreamNonBlocking));
+  CHNSS_CK(cudaHostAlloc(&c->srec_h, 24 * sizeof(double), cudaHostAllocDefault));
+}
+
 cudaGraphExec_t step_graph_for(chnss_ctx *c, const chnss_state *in, chnss_state *out) {
   const auto key = state_key(in, out);
   for (auto &g : c->sgr)
     if (g.exec && g.key == key) return g.exec;
-  if (!c->rq1) {
-    CHNSS_CK(cudaStreamCreateWithFlags(&c->rq0, cudaStreamNonBlocking));
-    CHNSS_CK(cudaStreamCreateWithFlags(&c->rq1, cudaStreamNonBlocking));
-    CHNSS_CK(cudaStreamCreateWithFlags(&c->rq2, cudaStreamNonBlocking));
-    CHNSS_CK(cudaHostAlloc(&c->srec_h, 24 * sizeof(double), cudaHostAllocDefault));
-  }
+  ensure_record_streams(c);
   // record on the private stream (the context stream may be the legacy
   // default stream, which cannot be captured); everything that uses the
   // context stream follows it while recording
@@ -1533,9 +1538,14 @@ chnss_status chnss_ctx_create(chnss_mesh_t mesh, const chnss_params *params, voi
   ABI_CATCH(nullptr)
 }
 
+namespace chnss {
+void drop_batch_graphs(chnss_ctx *c);
+}
+
 chnss_status chnss_ctx_destroy(chnss_ctx_t ctx) {
   if (!ctx) return CHNSS_OK;
   cudaStreamSynchronize(ctx->s);
+  chnss::drop_batch_graphs(ctx);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   delete ctx;
   return CHNSS_OK;
@@ -2283,6 +2293,7 @@ namespace {
 constexpr int kTuneCandidates[3] = {128, 256, 512};
 
 void destroy_graphs(chnss_ctx *c) {
+  ++c->sg_gen;                  // batch graphs recorded from this context are stale now
   for (auto &g : c->sgr) {      // recorded steps hold copies of the preconditioner bodies
     if (g.exec) cudaGraphExecDestroy(g.exec);
     g.exec = nullptr;
@@ -2419,6 +2430,137 @@ extern "C" chnss_status chnss_set_step_concurrency(chnss_ctx_t ctx, int on) {
   ABI_CATCH(ctx)
 }
 
+// ---------------------------------------------------------------------------
+// One CUDA graph for a whole batch: every instance's step recorded as a
+// parallel branch of one capture (a fork from the batch stream into each
+// context's recording stream, a join back), launched once per call.  Kept
+// for the two most recent (contexts, states) sets, since a trajectory
+// alternates two state sets; dropped when a context is destroyed or its
+// recorded graphs are (its generation changes).
+namespace {
+struct BatchGraph {
+  std::vector<chnss_ctx *> ctx;
+  std::vector<std::array<const void *, 20>> key;
+  std::vector<unsigned long long> gen;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t s = nullptr;
+  void release() {
+    if (s) cudaStreamSynchronize(s);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (s) cudaStreamDestroy(s);
+    exec = nullptr;
+    s = nullptr;
+  }
+};
+std::mutex g_batch_mu;
+std::vector<BatchGraph> g_batch;
+std::atomic<long long> g_batch_one_graph{0}, g_batch_per_instance{0};
+
+BatchGraph record_batch(int n, chnss_ctx *const *ctxs, const chnss_state *in, chnss_state *out) {
+  BatchGraph b;
+  for (int i = 0; i < n; ++i) {
+    ensure_record_streams(ctxs[i]);
+    CHNSS_CK(cudaStreamSynchronize(ctxs[i]->s));
+    b.ctx.push_back(ctxs[i]);
+    b.key.push_back(state_key(&in[i], &out[i]));
+    b.gen.push_back(ctxs[i]->sg_gen);
+  }
+  CHNSS_CK(cudaStreamCreateWithFlags(&b.s, cudaStreamNonBlocking));
+  cudaEvent_t fork = nullptr, join = nullptr;
+  CHNSS_CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  CHNSS_CK(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+  cudaGraph_t graph = nullptr;
+  chnss_ctx *cur = nullptr;
+  cudaStream_t user = nullptr;
+  bool prof_on = false;
+  auto restore = [&] {
+    if (!cur) return;
+    cur->s = user;
+    cur->recording = false;
+    cur->prof.on = prof_on;
+    cur = nullptr;
+  };
+  try {
+    CHNSS_CK(cudaStreamBeginCapture(b.s, cudaStreamCaptureModeThreadLocal));
+    try {
+      for (int i = 0; i < n; ++i) {
+        cur = ctxs[i];
+        user = cur->s;
+        prof_on = cur->prof.on;
+        cur->prof.on = false;          // no event nodes inside conditional bodies
+        cur->recording = true;
+        cur->s = cur->rq0;
+        CHNSS_CK(cudaEventRecord(fork, b.s));
+        CHNSS_CK(cudaStreamWaitEvent(cur->rq0, fork, 0));
+        record_step_body(cur, &in[i], &out[i]);
+        CHNSS_CK(cudaEventRecord(join, cur->rq0));
+        CHNSS_CK(cudaStreamWaitEvent(b.s, join, 0));
+        restore();
+      }
+    } catch (...) {
+      restore();
+      cudaGraph_t tmp = nullptr;
+      cudaStreamEndCapture(b.s, &tmp);
+      if (tmp) cudaGraphDestroy(tmp);
+      throw;
+    }
+    const cudaError_t ec = cudaStreamEndCapture(b.s, &graph);
+    if (ec != cudaSuccess)
+      throw Error{CHNSS_ERR_CUDA, std::string("recording the batch graph: ") + cudaGetErrorString(ec)};
+    const cudaError_t ei = cudaGraphInstantiate(&b.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess)
+      throw Error{CHNSS_ERR_CUDA, std::string("instantiating the batch graph: ") + cudaGetErrorString(ei)};
+  } catch (...) {
+    cudaEventDestroy(fork);
+    cudaEventDestroy(join);
+    b.release();
+    throw;
+  }
+  cudaEventDestroy(fork);
+  cudaEventDestroy(join);
+  return b;
+}
+
+// the cached graph of this batch (recorded on a miss)
+BatchGraph &batch_graph_for(int n, chnss_ctx *const *ctxs, const chnss_state *in, chnss_state *out) {
+  for (BatchGraph &b : g_batch) {
+    if ((int)b.ctx.size() != n) continue;
+    bool same = true;
+    for (int i = 0; i < n && same; ++i)
+      same = b.ctx[i] == ctxs[i] && b.gen[i] == ctxs[i]->sg_gen && b.key[i] == state_key(&in[i], &out[i]);
+    if (same) return b;
+  }
+  BatchGraph b = record_batch(n, ctxs, in, out);
+  if (g_batch.size() >= 2) {
+    g_batch.front().release();
+    g_batch.erase(g_batch.begin());
+  }
+  g_batch.push_back(std::move(b));
+  return g_batch.back();
+}
+}  // namespace
+
+namespace chnss {
+void drop_batch_graphs(chnss_ctx *c) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (size_t i = 0; i < g_batch.size();) {
+    if (std::find(g_batch[i].ctx.begin(), g_batch[i].ctx.end(), c) != g_batch[i].ctx.end()) {
+      g_batch[i].release();
+      g_batch.erase(g_batch.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+}  // namespace chnss
+
+extern "C" chnss_status chnss_batch_stats(long long *one_graph, long long *per_instance) {
+  if (one_graph) *one_graph = g_batch_one_graph.load();
+  if (per_instance) *per_instance = g_batch_per_instance.load();
+  return CHNSS_OK;
+}
+
 extern "C" chnss_status chnss_step_batched(int n_inst, chnss_ctx_t *ctxs, const chnss_state *in, chnss_state *out,
                                            chnss_solve_info *info, int max_threads) {
   ABI_TRY
@@ -2436,9 +2578,40 @@ extern "C" chnss_status chnss_step_batched(int n_inst, chnss_ctx_t *ctxs, const 
   std::vector<chnss_status> st(n_inst, CHNSS_OK);
   bool all_graphs = true;
   for (int i = 0; i < n_inst; ++i) all_graphs = all_graphs && ctxs[i]->step_mode == 1;
+  if (all_graphs && n_inst > 1) {
+    // the whole batch as one graph launch; if it cannot be recorded, one
+    // graph launch per instance below
+    std::unique_lock<std::mutex> lk(g_batch_mu);
+    BatchGraph *bg = nullptr;
+    std::string why;
+    try {
+      bg = &batch_graph_for(n_inst, ctxs, in, out);
+    } catch (const Error &e) {
+      why = e.msg;
+    }
+    if (bg) {
+      const auto t0 = std::chrono::steady_clock::now();
+      for (int i = 0; i < n_inst; ++i) CHNSS_CK(cudaStreamSynchronize(ctxs[i]->s));
+      CHNSS_CK(cudaGraphLaunch(bg->exec, bg->s));
+      g_launch_count.fetch_add(1, std::memory_order_relaxed);
+      CHNSS_CK(cudaStreamSynchronize(bg->s));
+      lk.unlock();
+      ++g_batch_one_graph;
+      const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      for (int i = 0; i < n_inst; ++i) st[i] = step_graph_finish(ctxs[i], info ? info + 6L * i : nullptr, secs);
+      for (int i = 0; i < n_inst; ++i)
+        if (st[i] != CHNSS_OK) {
+          g_last_error = "instance " + std::to_string(i) + " failed with status " + std::to_string((int)st[i]);
+          return st[i];
+        }
+      return CHNSS_OK;
+    }
+    g_last_error = "batch graph not recorded (" + why + "); one graph per instance";
+  }
   if (all_graphs) {
     // one graph launch per instance from this thread, every instance on its
     // own stream; then one synchronisation per stream
+    ++g_batch_per_instance;
     const auto t0 = std::chrono::steady_clock::now();
     std::vector<bool> launched(n_inst, false);
     for (int i = 0; i < n_inst; ++i) {

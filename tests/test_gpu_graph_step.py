@@ -85,9 +85,12 @@ def test_graph_batched_steps_equal_single_steps(torch):
         c.set_step_mode(1)
         ctxs.append(c)
         cur.append(chnss.state_to_device(st0))
+    before = chnss.batch_stats()
     for _ in range(2):
         cur, recs, st = chnss.step_batched(ctxs, cur)
         assert st == 0
+    after = chnss.batch_stats()
+    assert after["one_graph"] == before["one_graph"] + 2, (before, after)   # one graph launch per call
     for (s_ref, i_ref), s_b, rec in zip(ref, cur, recs):
         assert _equal(s_b, s_ref)
         for k in rec:
