@@ -738,9 +738,10 @@ def run_sweep(args):
     """Batched parameter sweep (the 64-instance workload): independent
     instances of uneven mesh size and evaporation rate, one context (and
     stream) each, FP32 preconditioners inside FP64 FGMRES with double-FP32
-    Gram-Schmidt.  Headline: every instance step recorded as a branch of
-    one CUDA graph (chnss_set_step_mode 1), launched once per batch step by
-    chnss_step_batched, args.sweep_steps steps each.  Beside it: the same batch
+    Gram-Schmidt.  Headline: every instance step one recorded CUDA graph
+    (chnss_set_step_mode 1), all instances launched by chnss_step_batched
+    from one thread, args.sweep_steps steps each; beside it the whole batch
+    as one graph launch per batch step (chnss_set_batch_mode 1).  Beside it: the same batch
     host-driven (worker threads, one synchronisation per Krylov iteration),
     and the instances' FP64 steps one instance at a time.  Under torchrun the
     instances are sharded round-robin over the ranks (a fixed sweep: strong
@@ -784,7 +785,8 @@ def run_sweep(args):
         b = [c.new_state() for c in ctxs]
         return ctxs, a, b
 
-    def timed_sweep(mode, steps, warmup):
+    def timed_sweep(mode, steps, warmup, batch_mode=0):
+        chnss.set_batch_mode(batch_mode)
         ctxs, a, b = make(mode)
         t_rec = time.perf_counter()
         for _ in range(warmup):                 # the first two steps record the ping-pong graphs
@@ -818,10 +820,19 @@ def run_sweep(args):
         mean = {k: round(sum(r[k]["iters"] for rs in iters for r in rs) / (len(iters) * len(recs)), 2) for k in recs[0]}
         final = [chnss.state_to_numpy(x) for x in a]
         del ctxs, a, b
+        chnss.set_batch_mode(0)
         return sec, clocks, launches, conv, mean, t_rec, final, batch_calls
 
     sec_g, clocks, launches, conv_g, iters_g, rec_g, fin_g, batch_g = timed_sweep(1, args.sweep_steps, args.warmup)
     value = len(all_inst) * args.sweep_steps / sec_g
+    one_graph = None
+    if args.sweep_batch_graph_steps > 0:
+        sec_b, _, _, conv_b, _, rec_b, _, batch_b = timed_sweep(1, args.sweep_batch_graph_steps, args.warmup, 1)
+        one_graph = {"value": round(len(all_inst) * args.sweep_batch_graph_steps / sec_b, 3),
+                     "unit": "instance steps/s", "steps": args.sweep_batch_graph_steps, "converged": conv_b,
+                     "batch_calls": batch_b, "graph_recording_s": round(rec_b, 2),
+                     "how": "chnss_set_batch_mode(1): the whole batch recorded as one CUDA graph (every "
+                            "instance's step a parallel branch), one launch per batch step"}
     host = None
     if args.sweep_host_steps > 0:
         sec_h, _, _, conv_h, iters_h, _, fin_h, _ = timed_sweep(0, args.sweep_host_steps, args.warmup)
@@ -871,6 +882,7 @@ def run_sweep(args):
         "tuning": {str(n): {"block_p1": t["block_p1"], "block_p2": t["block_p2"],
                             "ms_p1": [round(x, 4) for x in t["ms_p1"]], "ms_p2": [round(x, 4) for x in t["ms_p2"]]}
                    for n, t in tuning.items()},
+        "one_graph_batch": one_graph,
         "host_driven_batch": host,
         "fp64_one_at_a_time": {"value": round(seq64, 3), "unit": "instance steps/s",
                                "how": "rank 0: the FP64 step (FP64 Gram-Schmidt) of each instance, one after the "
@@ -974,6 +986,8 @@ def main():
     ap.add_argument("--sweep-threads", type=int, default=0)
     ap.add_argument("--sweep-concurrent-steps", action="store_true")
     ap.add_argument("--sweep-steps", type=int, default=50, help="steps of every instance in the timed sweep")
+    ap.add_argument("--sweep-batch-graph-steps", type=int, default=10,
+                    help="steps of the same sweep as one graph launch per batch step (0: skip)")
     ap.add_argument("--sweep-host-steps", type=int, default=5,
                     help="steps of the host-driven comparison batch (0: skip)")
     ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)

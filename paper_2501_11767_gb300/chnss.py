@@ -168,6 +168,7 @@ EXPORTS = {
     "chnss_set_step_concurrency": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss_set_step_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "chnss_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "chnss_set_batch_mode": (ctypes.c_int, [ctypes.c_int]),
     "chnss_batch_stats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "chnss_amg_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
@@ -630,6 +631,11 @@ def step_batched(ctxs, states_in, states_out=None, max_threads: int = 0, check: 
         _check(st, None)
     recs = [{SYSTEM_NAMES[k]: infos[6 * i + k].as_dict() for k in range(6)} for i in range(n)]
     return states_out, recs, st
+
+
+def set_batch_mode(mode: int):
+    """chnss_set_batch_mode: 0 one graph launch per instance, 1 one graph per batch."""
+    _check(load().chnss_set_batch_mode(int(mode)))
 
 
 def batch_stats() -> dict:

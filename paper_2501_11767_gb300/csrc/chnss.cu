@@ -2454,6 +2454,7 @@ struct BatchGraph {
 };
 std::mutex g_batch_mu;
 std::vector<BatchGraph> g_batch;
+std::atomic<int> g_batch_mode{0};    // chnss_set_batch_mode
 std::atomic<long long> g_batch_one_graph{0}, g_batch_per_instance{0};
 
 BatchGraph record_batch(int n, chnss_ctx *const *ctxs, const chnss_state *in, chnss_state *out) {
@@ -2555,6 +2556,12 @@ void drop_batch_graphs(chnss_ctx *c) {
 }
 }  // namespace chnss
 
+extern "C" chnss_status chnss_set_batch_mode(int mode) {
+  if (mode != 0 && mode != 1) return fail(nullptr, CHNSS_ERR_ARG, "batch mode must be 0 (a graph per instance) or 1 (one graph)");
+  g_batch_mode = mode;
+  return CHNSS_OK;
+}
+
 extern "C" chnss_status chnss_batch_stats(long long *one_graph, long long *per_instance) {
   if (one_graph) *one_graph = g_batch_one_graph.load();
   if (per_instance) *per_instance = g_batch_per_instance.load();
@@ -2578,7 +2585,7 @@ extern "C" chnss_status chnss_step_batched(int n_inst, chnss_ctx_t *ctxs, const 
   std::vector<chnss_status> st(n_inst, CHNSS_OK);
   bool all_graphs = true;
   for (int i = 0; i < n_inst; ++i) all_graphs = all_graphs && ctxs[i]->step_mode == 1;
-  if (all_graphs && n_inst > 1) {
+  if (all_graphs && n_inst > 1 && g_batch_mode == 1) {
     // the whole batch as one graph launch; if it cannot be recorded, one
     // graph launch per instance below
     std::unique_lock<std::mutex> lk(g_batch_mu);

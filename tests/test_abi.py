@@ -153,3 +153,10 @@ def test_amg_argument_errors_need_no_device(lib):
     assert lib.chnss_amg_vcycle(None, None, None) == 1
     assert lib.chnss_amg_solve(None, None, None, 1e-8, 0.0, 10, None) == 1
     lib.chnss_amg_destroy(None)
+
+
+def test_batch_mode_argument_errors_need_no_device(lib):
+    assert lib.chnss_set_batch_mode(2) == 1
+    assert b"batch mode" in lib.chnss_last_error(None)
+    a, b = ctypes.c_longlong(-1), ctypes.c_longlong(-1)
+    assert lib.chnss_batch_stats(ctypes.byref(a), ctypes.byref(b)) == 0 and a.value >= 0 and b.value >= 0

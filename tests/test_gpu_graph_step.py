@@ -74,7 +74,10 @@ def test_graph_step_serial_branches(torch):
     assert _equal(host, graph)
 
 
-def test_graph_batched_steps_equal_single_steps(torch):
+@pytest.mark.parametrize("batch_mode", [0, 1])
+def test_graph_batched_steps_equal_single_steps(torch, batch_mode):
+    """Both batch modes (a graph launch per instance; one graph launch for
+    the whole batch) give every instance bitwise its single steps."""
     inst = [(16, 0.1), (20, 0.3), (32, 0.05)]
     ref, ctxs, cur = [], [], []
     for i, (n, evap) in enumerate(inst):
@@ -85,12 +88,17 @@ def test_graph_batched_steps_equal_single_steps(torch):
         c.set_step_mode(1)
         ctxs.append(c)
         cur.append(chnss.state_to_device(st0))
-    before = chnss.batch_stats()
-    for _ in range(2):
-        cur, recs, st = chnss.step_batched(ctxs, cur)
-        assert st == 0
-    after = chnss.batch_stats()
-    assert after["one_graph"] == before["one_graph"] + 2, (before, after)   # one graph launch per call
+    chnss.set_batch_mode(batch_mode)
+    try:
+        before = chnss.batch_stats()
+        for _ in range(2):
+            cur, recs, st = chnss.step_batched(ctxs, cur)
+            assert st == 0
+        after = chnss.batch_stats()
+    finally:
+        chnss.set_batch_mode(0)
+    key = "one_graph" if batch_mode == 1 else "per_instance"
+    assert after[key] == before[key] + 2, (before, after)   # the chosen path ran on both calls
     for (s_ref, i_ref), s_b, rec in zip(ref, cur, recs):
         assert _equal(s_b, s_ref)
         for k in rec:
