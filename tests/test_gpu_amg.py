@@ -185,3 +185,25 @@ def test_refuses_bad_patterns(torch):
     with pytest.raises(chnss.ChnssError) as e:
         chnss.Amg(rp, col2, val)
     assert e.value.status == 1 and "sorted" in str(e.value)
+
+
+def test_full_size_ch_block_matches_oracle(torch):
+    """The bench's size: the 1024^2 CH block M + tau C(v) (1 050 625 rows).
+    The oracle's own setup is cheap enough here (numpy rounds, one Python
+    pass per aggregation rule), so every level, one V-cycle and the
+    SA-preconditioned solve are compared at the tolerances of the small
+    cases."""
+    A = _step_block(1024)
+    H = amg.SAHierarchy(A)
+    h = chnss.Amg(*_device(torch, A))
+    _compare_hierarchy(h, H)
+    b = np.cos(np.arange(A.shape[0]) * 0.731) + 0.2
+    x = h.vcycle(torch.as_tensor(b, device="cuda")).cpu().numpy()
+    want = H(b)
+    assert np.linalg.norm(x - want) <= CYCLE_TOL * np.linalg.norm(want)
+    xs, info, st = h.solve(torch.as_tensor(b, device="cuda"), rtol=1e-8)
+    ref, rinfo = fgmres(lambda y: A @ y, H, b, rtol=1e-8, restart=30, maxit=500)
+    assert st == 0 and abs(info["iters"] - rinfo["iters"]) <= 1, (info, rinfo)
+    if info["iters"] != rinfo["iters"]:
+        ref, _ = fgmres(lambda y: A @ y, H, b, rtol=0.0, atol=0.0, restart=30, maxit=info["iters"])
+    assert np.linalg.norm(xs.cpu().numpy() - ref) <= SOLVE_TOL * np.linalg.norm(ref), info
