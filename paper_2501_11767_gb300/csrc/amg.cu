@@ -20,7 +20,9 @@
 //     hi_l      min(Gershgorin bound, 1.1 x 10 power steps on D^-1 A_l from a
 //               +-1 start drawn with SplitMix64 outputs ((l + 64) << 32) + i)
 //     P         T - (4 / (3 hi_l)) D^-1 (A T) on its pattern,
-//     A_{l+1}   R (A P): every product summed by one thread in CSR order.
+//     A_{l+1}   R (A P): every product row summed by one thread in CSR
+//               order, through term -> position maps built with the
+//               patterns (no searches in the numeric setup).
 // The V-cycle is MGHier<T> (kind 0) on these levels with hi_l as the
 // smoothing bounds.  No atomics touch a floating-point value, so every
 // result is bit-reproducible.
@@ -249,19 +251,28 @@ __global__ void k_product_fill(int n, const int *arp, const int *acol, const int
   for (int q = 0; q < m && c0 + q < crp[i + 1]; ++q) ccol[c0 + q] = buf[q];
 }
 
-// C = A B on C's (sorted) pattern: row i summed by one thread, in the CSR
-// order of A's row and then of B's rows
-__global__ void k_product_values(int n, const int *__restrict__ arp, const int *__restrict__ acol,
-                                 const double *__restrict__ aval, const int *__restrict__ brp,
-                                 const int *__restrict__ bcol, const double *__restrict__ bval,
-                                 const int *__restrict__ crp, const int *__restrict__ ccol, double *cval) {
+// products per row of A B (the length of its term list)
+__global__ void k_product_terms(int n, const int *__restrict__ arp, const int *__restrict__ acol,
+                                const int *__restrict__ brp, int *cnt) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i >= n) return;
+  int t = 0;
+  for (int ka = arp[i]; ka < arp[i + 1]; ++ka) t += brp[acol[ka] + 1] - brp[acol[ka]];
+  cnt[i] = t;
+}
+
+// position in C of every term of row i of A B, in the order the numeric
+// product sums them (A's CSR order, then B's)
+__global__ void k_product_positions(int n, const int *__restrict__ arp, const int *__restrict__ acol,
+                                    const int *__restrict__ brp, const int *__restrict__ bcol,
+                                    const int *__restrict__ crp, const int *__restrict__ ccol,
+                                    const int *__restrict__ tptr, int *tpos) {
   const int i = blockIdx.x * TPB + threadIdx.x;
   if (i >= n) return;
   const int c0 = crp[i], c1 = crp[i + 1];
-  for (int q = c0; q < c1; ++q) cval[q] = 0.0;
+  int t = tptr[i];
   for (int ka = arp[i]; ka < arp[i + 1]; ++ka) {
     const int k = acol[ka];
-    const double a = aval[ka];
     for (int kb = brp[k]; kb < brp[k + 1]; ++kb) {
       const int c = bcol[kb];
       int lo = c0, hi = c1;
@@ -270,7 +281,28 @@ __global__ void k_product_values(int n, const int *__restrict__ arp, const int *
         if (ccol[mid] < c) lo = mid + 1;
         else hi = mid;
       }
-      if (lo < c1 && ccol[lo] == c) cval[lo] += a * bval[kb];   // always found: C is the product's pattern
+      tpos[t++] = lo < c1 && ccol[lo] == c ? lo : -1;   // always found: C is the product's pattern
+    }
+  }
+}
+
+// C = A B on C's (sorted) pattern through the term positions: row i summed by
+// one thread, term by term in the CSR order of A's row and then of B's rows
+__global__ void k_product_values_mapped(int n, const int *__restrict__ arp, const int *__restrict__ acol,
+                                        const double *__restrict__ aval, const int *__restrict__ brp,
+                                        const double *__restrict__ bval, const int *__restrict__ crp,
+                                        const int *__restrict__ tptr, const int *__restrict__ tpos,
+                                        double *cval) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i >= n) return;
+  for (int q = crp[i]; q < crp[i + 1]; ++q) cval[q] = 0.0;
+  int t = tptr[i];
+  for (int ka = arp[i]; ka < arp[i + 1]; ++ka) {
+    const int k = acol[ka];
+    const double a = aval[ka];
+    for (int kb = brp[k]; kb < brp[k + 1]; ++kb) {
+      const int q = tpos[t++];
+      if (q >= 0) cval[q] += a * bval[kb];
     }
   }
 }
@@ -320,22 +352,40 @@ __global__ void k_diag_pos(int n, const int *rp, const int *col, int *diag, int 
   diag[i] = d;
 }
 
-__global__ void k_power_init(int n, int level, double *x) {
+// the +-1 start vector; *hn = its norm sqrt(n) (exact: the squares sum to n)
+__global__ void k_power_init(int n, int level, double *x, double *hn) {
   const int i = blockIdx.x * TPB + threadIdx.x;
   if (i >= n) return;
   const uint64_t z = splitmix64_out(((uint64_t)(level + 64) << 32) + (uint64_t)i);
   x[i] = (z >> 63) ? 1.0 : -1.0;
+  if (i == 0) *hn = sqrt((double)n);
 }
 
-// y = D^-1 (A x), the row sum in CSR order
-__global__ void k_dinv_spmv(int n, const int *__restrict__ rp, const int *__restrict__ col,
-                            const double *__restrict__ val, const double *__restrict__ dinv,
-                            const double *__restrict__ x, double *y) {
-  const int i = blockIdx.x * TPB + threadIdx.x;
-  if (i >= n) return;
-  double s = 0.0;
-  for (int k = rp[i]; k < rp[i + 1]; ++k) s += val[k] * x[col[k]];
-  y[i] = dinv[i] * s;
+// One power step: y = D^-1 (A x) / *hn, i.e. D^-1 A applied to the
+// normalised x with the normalisation folded into the row (equal up to
+// rounding; one FP64 division per thread instead of one per entry); the row
+// sum in CSR order; per-block partial sums of y_i^2 in a fixed tree order
+__global__ void k_power_step(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                             const double *__restrict__ val, const double *__restrict__ dinv,
+                             const double *__restrict__ x, const double *__restrict__ hn, double *y,
+                             double *partial) {
+  __shared__ double sm[TPB];
+  const double r = 1.0 / *hn;
+  double acc = 0.0;
+  for (int i = blockIdx.x * TPB + threadIdx.x; i < n; i += gridDim.x * TPB) {
+    double s = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) s += val[k] * x[col[k]];
+    const double yi = dinv[i] * s * r;
+    y[i] = yi;
+    acc += yi * yi;
+  }
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = TPB / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
 }
 
 __global__ void k_rho(const double *gersh, const double *nrm, double *rho) {
@@ -390,6 +440,10 @@ struct AmgLevel {
   Pattern AP;                   // pattern of A P (device only)
   double *apval = nullptr;
   double *atval = nullptr;      // A T on P's pattern
+  // term positions of the products A T (in P), A P (in AP) and R (A P) (in
+  // the next level's operator): row pointers and positions
+  int *at_ptr = nullptr, *at_pos = nullptr, *ap_ptr = nullptr, *ap_pos = nullptr;
+  int *rap_ptr = nullptr, *rap_pos = nullptr;
 };
 
 struct AmgHandle {
@@ -452,6 +506,19 @@ struct AmgHandle {
     C.nnz = scan(A.nrows, cnt, C.rowptr);
     C.col = ar.alloc<int>(C.nnz);
     k_product_fill<<<nblk(A.nrows) * 2, 128, 0, s>>>(A.nrows, A.rowptr, A.col, brp, bcol, C.rowptr, C.col);
+    CHNSS_LAUNCH_CK();
+  }
+
+  // term positions of A B in C (C: the pattern of A B)
+  void product_terms(const Pattern &A, const int *brp, const int *bcol, const Pattern &C, int **tptr, int **tpos) {
+    int *cnt = ar.alloc<int>(A.nrows);
+    k_product_terms<<<nblk(A.nrows), TPB, 0, s>>>(A.nrows, A.rowptr, A.col, brp, cnt);
+    CHNSS_LAUNCH_CK();
+    *tptr = ar.alloc<int>(A.nrows + 1);
+    const int terms = scan(A.nrows, cnt, *tptr);
+    *tpos = ar.alloc<int>(terms);
+    k_product_positions<<<nblk(A.nrows), TPB, 0, s>>>(A.nrows, A.rowptr, A.col, brp, bcol, C.rowptr, C.col, *tptr,
+                                                      *tpos);
     CHNSS_LAUNCH_CK();
   }
 
@@ -530,6 +597,10 @@ struct AmgHandle {
     product_pattern(L.A, P.rowptr, P.col, nagg, L.AP, "A P");
     auto next = std::make_unique<AmgLevel>();
     product_pattern(R, L.AP.rowptr, L.AP.col, nagg, next->A, "coarse operator");
+    // term positions of the three products (numeric setup without searches)
+    product_terms(L.A, L.iota, L.agg, P, &L.at_ptr, &L.at_pos);
+    product_terms(L.A, P.rowptr, P.col, L.AP, &L.ap_ptr, &L.ap_pos);
+    product_terms(R, L.AP.rowptr, L.AP.col, next->A, &L.rap_ptr, &L.rap_pos);
     // host copies and SELL views of the patterns the V-cycle sweeps
     download(P);
     download(R);
@@ -568,17 +639,17 @@ struct AmgHandle {
     AmgLevel &L = *lv[l];
     const int nl = L.A.nrows;
     jacobi_csr<double>(L.A, L.val, L.diag, L.dinv, L.gersh, partial, s);
-    k_power_init<<<nblk(nl), TPB, 0, s>>>(nl, l, px);
+    k_power_init<<<nblk(nl), TPB, 0, s>>>(nl, l, px, sc + 1);
     CHNSS_LAUNCH_CK();
-    dot<double>(nl, px, px, sc, partial, s);
-    set_scalar(sc + 1, sc, 1.0, true, s);
-    vec_scale_by_inv(nl, px, sc + 1, px, s);
+    const int nb = std::min(nblk(nl), kReduceMaxBlocks);
+    double *cur = px, *nxt = py;
     for (int k = 0; k < kAmgPowerSteps; ++k) {
-      k_dinv_spmv<<<nblk(nl), TPB, 0, s>>>(nl, L.A.rowptr, L.A.col, L.val, L.dinv, px, py);
+      // nxt = D^-1 A (cur / ||cur||); then ||nxt|| in sc[1] for the next step
+      k_power_step<<<nb, TPB, 0, s>>>(nl, L.A.rowptr, L.A.col, L.val, L.dinv, cur, sc + 1, nxt, partial);
       CHNSS_LAUNCH_CK();
-      dot<double>(nl, py, py, sc, partial, s);
+      sum_partials(nb, 1, partial, sc, s);
       set_scalar(sc + 1, sc, 1.0, true, s);
-      vec_scale_by_inv(nl, py, sc + 1, px, s);
+      std::swap(cur, nxt);
     }
     k_rho<<<1, 1, 0, s>>>(L.gersh, sc + 1, L.rho);
     CHNSS_LAUNCH_CK();
@@ -593,19 +664,19 @@ struct AmgHandle {
       AmgLevel &L = *lv[l], &N = *lv[l + 1];
       const int nl = L.A.nrows;
       const Pattern &P = L.tr.P, &R = L.tr.R;
-      k_product_values<<<nblk(nl), TPB, 0, s>>>(nl, L.A.rowptr, L.A.col, L.val, L.iota, L.agg, L.tval, P.rowptr,
-                                                P.col, L.atval);
+      k_product_values_mapped<<<nblk(nl), TPB, 0, s>>>(nl, L.A.rowptr, L.A.col, L.val, L.iota, L.tval, P.rowptr,
+                                                       L.at_ptr, L.at_pos, L.atval);
       CHNSS_LAUNCH_CK();
       k_smooth_prolongator<<<nblk(nl), TPB, 0, s>>>(nl, P.rowptr, P.col, L.atval, L.agg, L.tval, L.dinv, L.rho,
                                                     L.tr.Pv);
       CHNSS_LAUNCH_CK();
       k_gather_pos<<<nblk(R.nnz), TPB, 0, s>>>(R.nnz, L.rmap, L.tr.Pv, L.tr.Rv);
       CHNSS_LAUNCH_CK();
-      k_product_values<<<nblk(nl), TPB, 0, s>>>(nl, L.A.rowptr, L.A.col, L.val, P.rowptr, P.col, L.tr.Pv,
-                                                L.AP.rowptr, L.AP.col, L.apval);
+      k_product_values_mapped<<<nblk(nl), TPB, 0, s>>>(nl, L.A.rowptr, L.A.col, L.val, P.rowptr, L.tr.Pv,
+                                                       L.AP.rowptr, L.ap_ptr, L.ap_pos, L.apval);
       CHNSS_LAUNCH_CK();
-      k_product_values<<<nblk(R.nrows), TPB, 0, s>>>(R.nrows, R.rowptr, R.col, L.tr.Rv, L.AP.rowptr, L.AP.col,
-                                                     L.apval, N.A.rowptr, N.A.col, N.val);
+      k_product_values_mapped<<<nblk(R.nrows), TPB, 0, s>>>(R.nrows, R.rowptr, R.col, L.tr.Rv, L.AP.rowptr,
+                                                            L.apval, N.A.rowptr, L.rap_ptr, L.rap_pos, N.val);
       CHNSS_LAUNCH_CK();
       sell_gather<double>(P.sell, 1, L.tr.Pv, L.tr.Ps, s);
       sell_gather<double>(R.sell, 1, L.tr.Rv, L.tr.Rs, s);
