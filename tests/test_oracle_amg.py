@@ -194,3 +194,26 @@ def test_spectral_bound_against_eigenvalues():
     for l, Al in enumerate(H.mats):
         rho = np.abs(np.linalg.eigvals(Al.toarray() / Al.diagonal()[:, None])).max()
         assert rho / 1.05 <= H.his[l] <= min(amg.gershgorin(Al), 1.1 * rho) * (1 + 1e-12), (l, rho, H.his[l])
+
+
+@pytest.mark.parametrize("n,seed", [(8, 0), (33, 7), (64, 11)])
+def test_unstructured_mesh_generator_is_a_valid_triangulation(n, seed):
+    """The seeded unstructured meshes the SA tests run on: counter-clockwise
+    triangles of positive area tiling the unit square, boundary nodes on the
+    boundary, every interior edge shared by exactly two triangles."""
+    x, tri = inputs.unstructured_square(n, seed)
+    assert x.shape == ((n + 1) ** 2, 2) and tri.shape == (2 * n * n, 3)
+    X = x[tri]
+    area = 0.5 * ((X[:, 1, 0] - X[:, 0, 0]) * (X[:, 2, 1] - X[:, 0, 1])
+                  - (X[:, 2, 0] - X[:, 0, 0]) * (X[:, 1, 1] - X[:, 0, 1]))
+    assert area.min() > 0.0 and abs(area.sum() - 1.0) < 1e-12
+    i, j = np.arange(n + 1)[None, :].repeat(n + 1, 0).ravel(), np.arange(n + 1)[:, None].repeat(n + 1, 1).ravel()
+    bnd = (i == 0) | (i == n) | (j == 0) | (j == n)
+    assert np.allclose(x[bnd], np.stack([i[bnd] / n, j[bnd] / n], axis=1), atol=1e-15, rtol=0)
+    edges = np.sort(np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]]), axis=1)
+    _, counts = np.unique(edges, axis=0, return_counts=True)
+    assert counts.max() == 2 and (counts == 1).sum() == 4 * n       # boundary edges once
+    flips = [tuple(sorted(t)) for t in tri[0::2]]
+    assert len(set(flips)) == n * n                                     # both diagonals occur below
+    m = TriMesh(x, tri)
+    assert abs(fem.mass_p1(m).sum() - 1.0) < 1e-12
