@@ -102,6 +102,12 @@ typedef struct {
                             FP32 pipe, with the basis kept as pairs beside its FP64 copy (the
                             outer residuals, the Hessenberg data, the solution update and the
                             preconditioner input stay FP64); applies when restart <= 31 */
+  int amg;               /* multigrid of the Allen-Cahn block M + tau delta_v K + tau C: 0 the
+                            geometric hierarchy; 1 the device smoothed aggregation of the fine
+                            AC matrix (chnss_amg_* below, Sec. 5's PyAMG for this block):
+                            aggregates and patterns built once per context, the levels set up
+                            again from the assembled matrix in every step.  2D only
+                            (CHNSS_ERR_ARG in 3D) */
 } chnss_params;
 
 /* Fields of one time level (DEVICE pointers, caller-owned, FP64). */

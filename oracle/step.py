@@ -15,7 +15,9 @@ All matrices use coefficients at t_k, so 2, 3 and 5 are independent.
 Every MG(.) above is one V-cycle, or with params["inner_rtol"] > 0 the
 V-cycle iteration MG.solve to that relative tolerance (Sec. 5 applies its
 AMG preconditioners with a tolerance of 1e-4); M_p^{-1} stays the fixed
-Chebyshev iteration.
+Chebyshev iteration.  With params["amg"] = 1 the MG of the AC block is the
+smoothed aggregation of oracle.amg built from the fine AC matrix of the
+step (Sec. 5 takes PyAMG for this block) instead of the geometric hierarchy.
 
 Solvent-air sub-model (params["model"] = 1, Sec. 5.1): no polymer or NFA
 (their fields stay zero and their CH systems are not solved), the
@@ -32,6 +34,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import fem
+from .amg import SAHierarchy
 from .krylov import chebyshev, fgmres, pcg
 from .mesh import Mesh
 from .mg import (MG, VEL_LO_RATIO, VEL_SMOOTH_DEGREE, inject_p1, inject_velocity, level_sizes, prolongation_p1,
@@ -139,7 +142,10 @@ class Oracle:
             x, info = _direct(A, rhs)
             return x, info, (A, rhs)
         mats = [(f.M + tau * p["delta_v"] * f.K + tau * C).tocsr() for f, C in zip(self.forms, convs)]
-        mg = MG(mats, self.P1)
+        if p.get("amg", 0) == 1:     # Sec. 5: algebraic multigrid of this block (oracle.amg)
+            mg = SAHierarchy(mats[0]).mg
+        else:
+            mg = MG(mats, self.P1)
         x, info = fgmres(lambda y: A @ y, mg.inner(p), rhs, p["rtol"], p["atol"], p["restart"], p["maxit"])
         return x, info, (A, rhs)
 

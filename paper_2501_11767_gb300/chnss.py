@@ -32,7 +32,8 @@ class Params(ctypes.Structure):
                 ("model", ctypes.c_int), ("chi_sa", ctypes.c_double), ("n_s", ctypes.c_double),
                 ("n_a", ctypes.c_double), ("phi_sat_s", ctypes.c_double), ("phi_sat_a", ctypes.c_double),
                 ("inner_rtol", ctypes.c_double), ("inner_maxit", ctypes.c_int),
-                ("ns_rtol", ctypes.c_double), ("ns_atol", ctypes.c_double), ("ortho", ctypes.c_int)]
+                ("ns_rtol", ctypes.c_double), ("ns_atol", ctypes.c_double), ("ortho", ctypes.c_int),
+                ("amg", ctypes.c_int)]
 
 
 class State(ctypes.Structure):
@@ -212,7 +213,7 @@ def _check(status, ctx=None):
 # fields of the solvent-air sub-model, defaulted when a parameter set omits them
 _OPTIONAL = {"model": 0, "chi_sa": 0.0, "n_s": 1.0, "n_a": 1.0, "phi_sat_s": 1e-6, "phi_sat_a": 1.0,
              "inner_rtol": 0.0, "inner_maxit": 20, "ns_rtol": 0.0, "ns_atol": 0.0,
-             "ortho": 0}
+             "ortho": 0, "amg": 0}
 
 
 def make_params(d: dict) -> Params:

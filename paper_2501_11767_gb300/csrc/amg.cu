@@ -33,6 +33,7 @@
 #include <memory>
 #include <vector>
 
+#include "amg.h"
 #include "solver.h"
 
 namespace chnss {
@@ -449,6 +450,7 @@ struct AmgLevel {
 struct AmgHandle {
   int n = 0, nnz = 0, precision = 0;
   cudaStream_t s = nullptr;
+  bool own_stream = true;       // false: the caller's stream (amg_attach)
   Arena ar;
   std::vector<std::unique_ptr<AmgLevel>> lv;
   double *partial = nullptr, *sc = nullptr, *px = nullptr, *py = nullptr;
@@ -467,7 +469,7 @@ struct AmgHandle {
     ar.release();
     if (pinned) cudaFreeHost(pinned);
     if (pinned_i) cudaFreeHost(pinned_i);
-    if (s) cudaStreamDestroy(s);
+    if (s && own_stream) cudaStreamDestroy(s);
   }
 
   int read_int(const int *dev) {
@@ -634,8 +636,9 @@ struct AmgHandle {
     L.rho = ar.alloc<double>(1);
   }
 
-  // spectral bound of D^-1 A_l (dinv and the Gershgorin bound first)
-  void spectral_bound(int l) {
+  // spectral bound of D^-1 A_l (dinv and the Gershgorin bound first), on st
+  void spectral_bound(int l, cudaStream_t st) {
+    cudaStream_t s = st;
     AmgLevel &L = *lv[l];
     const int nl = L.A.nrows;
     jacobi_csr<double>(L.A, L.val, L.diag, L.dinv, L.gersh, partial, s);
@@ -655,11 +658,13 @@ struct AmgHandle {
     CHNSS_LAUNCH_CK();
   }
 
-  // numeric setup from the current level-0 values
-  void numeric() {
+  // numeric setup of every level from the current level-0 values, on st
+  // (kernels and device copies only: no synchronisation)
+  void levels_numeric(cudaStream_t st) {
+    cudaStream_t s = st;
     const int nlev = (int)lv.size();
     for (int l = 0; l < nlev; ++l) {
-      spectral_bound(l);
+      spectral_bound(l, s);
       if (l == nlev - 1) break;
       AmgLevel &L = *lv[l], &N = *lv[l + 1];
       const int nl = L.A.nrows;
@@ -683,6 +688,12 @@ struct AmgHandle {
       sell_gather<float>(P.sell, 1, L.tr.Pv, L.tr.Ps32, s);
       sell_gather<float>(R.sell, 1, L.tr.Rv, L.tr.Rs32, s);
     }
+  }
+
+  // the handle's own numeric setup: the levels, the FP64 operator of the
+  // solve and the V-cycle data, then a synchronisation
+  void numeric() {
+    levels_numeric(s);
     sell_gather<double>(lv[0]->A.sell, 1, lv[0]->val, a0sell, s);
     if (mg64) mg64->setup(s);
     else mg32->setup(s);
@@ -723,6 +734,54 @@ struct AmgHandle {
     }
   }
 };
+
+AmgHandle *amg_attach(const Pattern &P0, double *val0, cudaStream_t st) {
+  if (P0.nrows != P0.ncols || P0.nrows < 1) throw Error{CHNSS_ERR_ARG, "smoothed aggregation needs a square operator"};
+  auto h = std::make_unique<AmgHandle>();
+  h->n = P0.nrows;
+  h->nnz = P0.nnz;
+  h->s = st;
+  h->own_stream = false;
+  CHNSS_CK(cudaHostAlloc((void **)&h->pinned, 16 * sizeof(double), cudaHostAllocDefault));
+  CHNSS_CK(cudaHostAlloc((void **)&h->pinned_i, 4 * sizeof(int), cudaHostAllocDefault));
+  h->partial = h->ar.alloc<double>(64L * kReduceMaxBlocks);
+  h->sc = h->ar.alloc<double>(8);
+  h->ictl = h->ar.alloc<int>(4);
+  h->px = h->ar.alloc<double>(h->n);
+  h->py = h->ar.alloc<double>(h->n);
+  auto l0 = std::make_unique<AmgLevel>();
+  l0->A = P0;                     // the caller's arrays (this arena never frees them)
+  l0->val = val0;
+  h->lv.push_back(std::move(l0));
+  h->level_scalars(*h->lv[0]);
+  while (h->lv.back()->A.nrows > kAmgCoarseRows && (int)h->lv.size() < kAmgMaxLevels)
+    if (!h->coarsen((int)h->lv.size() - 1)) break;
+  if (h->lv.size() == 1 && h->n > kAmgCoarseRows)
+    throw Error{CHNSS_ERR_ARG, "aggregation does not coarsen this operator"};
+  CHNSS_CK(cudaStreamSynchronize(st));
+  return h.release();
+}
+
+void amg_refresh(AmgHandle *h, cudaStream_t st) { h->levels_numeric(st); }
+
+void amg_levels(AmgHandle *h, std::vector<const Pattern *> &pats, std::vector<const int *> &diags,
+                std::vector<const double *> &vals, std::vector<const Transfer *> &trs,
+                std::vector<const double *> &his) {
+  pats.clear();
+  diags.clear();
+  vals.clear();
+  trs.clear();
+  his.clear();
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    pats.push_back(&h->lv[l]->A);
+    diags.push_back(h->lv[l]->diag);
+    vals.push_back(h->lv[l]->val);
+    his.push_back(h->lv[l]->rho);
+    if (l + 1 < h->lv.size()) trs.push_back(&h->lv[l]->tr);
+  }
+}
+
+void amg_release(AmgHandle *h) { delete h; }
 
 namespace {
 // A (FP64, level-0 SELL values) with one V-cycle as the right preconditioner

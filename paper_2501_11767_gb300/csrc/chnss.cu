@@ -11,6 +11,7 @@
 #include <future>
 #include <thread>
 
+#include "amg.h"
 #include "solver.h"
 
 using namespace chnss;
@@ -171,6 +172,7 @@ struct chnss_ctx {
   double *srec = nullptr, *srec_h = nullptr;   // per solve [iterations, converged, rel. residual, status]
   std::unique_ptr<PrecSet<double>> p64;
   std::unique_ptr<PrecSet<float>> p32;
+  chnss::AmgHandle *amg_ac = nullptr;        // params.amg = 1: smoothed-aggregation levels of the AC block
   // captured preconditioner graphs (0..2 CH species, 3 AC, 4 NS)
   double **slots = nullptr;   // device [2 * kNumPrec] input / output pointers
   cudaStream_t cap = nullptr; // private stream used for capture only
@@ -210,6 +212,7 @@ struct chnss_ctx {
   double *adots = nullptr;                  // device scalars of the parameter gradients
   const Level &lv(int l) const { return mesh->m.lv[l]; }
   ~chnss_ctx() {
+    if (amg_ac) chnss::amg_release(amg_ac);
     for (PrecGraph &g : pg) {
       if (g.plain) cudaGraphExecDestroy(g.plain);
       if (g.prof) cudaGraphExecDestroy(g.prof);
@@ -554,7 +557,20 @@ void init_precset(chnss_ctx *c, PrecSet<T> &P) {
   // the CH / AC hierarchies reduce into partial_ch, the Oseen ones into
   // partial: the two groups assemble and solve on different streams
   P.L.init(ar, 0, false, p1s, d1s, vals(c->L), t1s, c->partial_ch);
-  P.AC.init(ar, 0, false, p1s, d1s, vals(c->AC), t1s, c->partial_ch);
+  if (c->p.amg == 1) {
+    // the paper's algebraic multigrid for the AC block (Sec. 5): smoothed
+    // aggregation of the fine AC matrix, its levels set up again every step
+    if (!c->amg_ac) c->amg_ac = amg_attach(c->lv(0).p1, c->AC[0], c->s);
+    std::vector<const Pattern *> ap;
+    std::vector<const int *> ad;
+    std::vector<const double *> av, ah;
+    std::vector<const Transfer *> at;
+    amg_levels(c->amg_ac, ap, ad, av, at, ah);
+    P.AC.hi_ext = ah;
+    P.AC.init(ar, 0, false, ap, ad, av, at, c->partial_ch);
+  } else {
+    P.AC.init(ar, 0, false, p1s, d1s, vals(c->AC), t1s, c->partial_ch);
+  }
   P.A.init(ar, 1, false, p2s, d2s, vals(c->A), tvs, c->partial);
   P.A.degree = 4;        // velocity smoothing: degree 4 on [hi / 16, hi]
   P.A.ratio = 16.0;
@@ -616,6 +632,7 @@ void init_precset(chnss_ctx *c, PrecSet<T> &P) {
 template <typename T>
 void setup_step_precset_chac(chnss_ctx *c, PrecSet<T> &P, cudaStream_t s) {
   P.L.setup(s);
+  if (c->amg_ac) amg_refresh(c->amg_ac, s);   // the AC block's SA levels from this step's matrix
   P.AC.setup(s);
   if (c->p.mobility_kind != 0)
     for (int sp = 0; sp < 3; ++sp) P.X2[sp].setup(s);
@@ -1378,6 +1395,7 @@ void check_params(const chnss_params *p) {
   if (!(p->ns_rtol >= 0.0 && p->ns_rtol < 1.0) || !(p->ns_atol >= 0.0))
     throw Error{CHNSS_ERR_ARG, "ns_rtol must be in [0, 1) and ns_atol >= 0"};
   if (p->ortho != 0 && p->ortho != 1) throw Error{CHNSS_ERR_ARG, "ortho must be 0 (FP64) or 1 (double-FP32)"};
+  if (p->amg != 0 && p->amg != 1) throw Error{CHNSS_ERR_ARG, "amg must be 0 (geometric) or 1 (smoothed aggregation)"};
   if (p->inner_rtol > 0.0 && (p->inner_maxit < 1 || p->inner_maxit > 1000))
     throw Error{CHNSS_ERR_ARG, "inner_maxit must be in [1, 1000]"};
   if (!(p->rtol >= 0) || !(p->atol >= 0)) throw Error{CHNSS_ERR_ARG, "tolerances must be >= 0"};

@@ -2003,6 +2003,7 @@ extern "C" chnss_status chnss3_ctx_create_ex(int n, int top_bc, const chnss_para
       throw Error{CHNSS_ERR_ARG, "inner_maxit must be in [1, 1000]"};
     if (p.mobility_kind != 0 && p.mobility_kind != 1) throw Error{CHNSS_ERR_ARG, "mobility_kind must be 0 or 1"};
     if (p.ortho != 0 && p.ortho != 1) throw Error{CHNSS_ERR_ARG, "ortho must be 0 (FP64) or 1 (double-FP32)"};
+    if (p.amg != 0) throw Error{CHNSS_ERR_ARG, "amg = 1 (smoothed aggregation of the AC block) is a 2D option"};
     if (!(p.tau > 0) || !(p.eta > 0) || p.restart < 1 || p.restart > 64 || p.maxit < 1)
       throw Error{CHNSS_ERR_ARG, "invalid parameters"};
     for (int i = 0; i < 3; ++i)

@@ -149,6 +149,8 @@ def default_params() -> dict:
         "ns_atol": 0.0,
         # Gram-Schmidt arithmetic of FGMRES: 0 FP64, 1 double-FP32 (pairs of FP32)
         "ortho": 0,
+        # multigrid of the AC block: 0 geometric, 1 smoothed aggregation (Sec. 5's AMG)
+        "amg": 0,
     }
 
 
@@ -201,6 +203,9 @@ def workload(name: str) -> dict:
     if name == "film512_mixed":      # the same parameters on 512 x 512 (profiling captures)
         p.update(beta=film_betas(0.005), tau=5e-4, precision=1, ortho=1)
         return {"n": 512, "params": p, "steps": 10}
+    if name == "film1024_amg_mixed":     # the bench set with the AC block on smoothed aggregation (Sec. 5)
+        p.update(beta=film_betas(0.005), tau=5e-4, precision=1, ortho=1, amg=1)
+        return {"n": 1024, "params": p, "steps": 10}
     if name == "film1024_mixed_inner":   # the bench set with every MG block solved to 1e-4 (Sec. 5)
         p.update(beta=film_betas(0.005), tau=5e-4, precision=1, inner_rtol=1e-4, inner_maxit=20, ortho=1)
         return {"n": 1024, "params": p, "steps": 10}

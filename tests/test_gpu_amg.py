@@ -210,3 +210,45 @@ def test_full_size_ch_block_matches_oracle(torch):
     if info["iters"] != rinfo["iters"]:
         ref, _ = fgmres(lambda y: A @ y, H, b, rtol=0.0, atol=0.0, restart=30, maxit=info["iters"])
     assert np.linalg.norm(xs.cpu().numpy() - ref) <= SOLVE_TOL * np.linalg.norm(ref), info
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_step_with_sa_ac_block_matches_oracle(torch, n):
+    """params amg = 1: the Allen-Cahn block's multigrid is the device smoothed
+    aggregation of the assembled AC matrix, set up again in every step
+    (Sec. 5 takes PyAMG for this block).  Every solve of two FP64 steps
+    against the oracle step with the same option (oracle.amg for that block)."""
+    from oracle.step import Oracle
+    from solve_compare import compare_solves
+    p = dict(inputs.default_params(), amg=1)
+    o = Oracle(n, p)
+    ctx = chnss.Context(chnss.Mesh(n), p)
+    st = inputs.initial_state(n, seed=2)
+    for k in range(2):
+        ref, rinfo = o.step(st)
+        out, info, status = ctx.step(chnss.state_to_device(st))
+        torch.cuda.synchronize()
+        assert status == 0
+        compare_solves(chnss.state_to_numpy(out), info, ref, rinfo, st, p, lambda q: Oracle(n, q), where=k)
+        st = ref
+
+
+def test_step_with_sa_ac_block_graph_and_mixed(torch):
+    """The same option in FP32 hierarchies with double-FP32 Gram-Schmidt: the
+    one-graph step (the SA re-setup recorded with the assembly) equals the
+    host-driven step bitwise, and every solve meets its stopping rule."""
+    n = 64
+    p = dict(inputs.default_params(), amg=1, precision=1, ortho=1)
+    st0 = chnss.state_to_device(inputs.initial_state(n, seed=3))
+    outs = []
+    for mode in (0, 1):
+        ctx = chnss.Context(chnss.Mesh(n), p)
+        ctx.set_step_mode(mode)
+        a = {k: v.clone() for k, v in st0.items()}
+        for _ in range(2):
+            a, info, status = ctx.step(a)
+            assert status == 0 and all(info[k]["converged"] for k in info), info
+        torch.cuda.synchronize()
+        outs.append(a)
+    for k in outs[0]:
+        assert torch.equal(outs[0][k], outs[1][k]), k
