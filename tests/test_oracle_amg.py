@@ -217,3 +217,23 @@ def test_unstructured_mesh_generator_is_a_valid_triangulation(n, seed):
     assert len(set(flips)) == n * n                                     # both diagonals occur below
     m = TriMesh(x, tri)
     assert abs(fem.mass_p1(m).sum() - 1.0) < 1e-12
+
+
+def test_oracle_step_option_puts_sa_on_the_ac_block():
+    """params amg = 1 in the oracle step: the AC solve is preconditioned by
+    oracle.amg and still meets its stopping rule; its result agrees with the
+    exact AC solve within the Krylov tolerance's reach, and the other solves
+    are untouched (same iteration counts as the geometric step)."""
+    from oracle.step import Oracle
+    n = 24
+    p = inputs.default_params()
+    st = inputs.initial_state(n, seed=5)
+    geo, gi = Oracle(n, p).step(st)
+    sa, si = Oracle(n, dict(p, amg=1)).step(st)
+    exact, _ = Oracle(n, p, exact=True).step(st)
+    assert si["ac"]["converged"] and si["ac"]["rel_residual"] <= p["rtol"]
+    e = np.linalg.norm(sa["Phi_v"] - exact["Phi_v"]) / np.linalg.norm(exact["Phi_v"])
+    assert e <= 1e-6, e
+    for k in ("ch_p", "ch_N", "ch_s", "mu_a", "ns"):
+        assert si[k]["iters"] == gi[k]["iters"], k
+        assert np.array_equal(sa["v"], geo["v"]) and np.array_equal(sa["phi"], geo["phi"])
