@@ -725,10 +725,11 @@ def run_amg(args):
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(head["update_ms"] + head["solve_ms"], 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 outer / f32 hierarchy",
-        "data": "synthetic (the 1024^2 film state after the warm-up steps)",
+        "data": f"synthetic (the {n}^2 film state after the warm-up steps)",
         "config": {"workload": f"amg_ch_block{n}", "n": n, "rows": mesh.N1, "nnz": int(len(col)),
                    "tau": params["tau"], "rtol": 1e-8, "parallelism": "single GPU",
-                   "l2": "matrix and hierarchy larger than L2"},
+                   "l2": ("fine matrix larger than L2" if 12 * len(col) > 129e6
+                          else "fine matrix fits in L2 (a profiling size)")},
         "clocks": clocks, **out,
     }
     print(json.dumps(line))

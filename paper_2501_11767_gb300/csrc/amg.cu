@@ -20,9 +20,10 @@
 //     hi_l      min(Gershgorin bound, 1.1 x 10 power steps on D^-1 A_l from a
 //               +-1 start drawn with SplitMix64 outputs ((l + 64) << 32) + i)
 //     P         T - (4 / (3 hi_l)) D^-1 (A T) on its pattern,
-//     A_{l+1}   R (A P): every product row summed by one thread in CSR
-//               order, through term -> position maps built with the
-//               patterns (no searches in the numeric setup).
+//     A P       one thread per row, terms in CSR order through term ->
+//               position maps built with the patterns;
+//     A_{l+1}   R (A P): one thread per entry, its terms in R's CSR order
+//               (the order a row-by-row accumulation would add them).
 // The V-cycle is MGHier<T> (kind 0) on these levels with hi_l as the
 // smoothing bounds.  No atomics touch a floating-point value, so every
 // result is bit-reproducible.
@@ -308,6 +309,41 @@ __global__ void k_product_values_mapped(int n, const int *__restrict__ arp, cons
   }
 }
 
+// the row of every entry of a CSR pattern
+__global__ void k_entry_rows(int n, const int *rp, int *row) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i >= n) return;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) row[e] = i;
+}
+
+// Galerkin product A_c = R (A P), one thread per ENTRY (c, j) of A_c: the sum
+// over i in R's row c (CSR order) of R[c, i] (A P)[i, j], the (A P) entry
+// found by a search in row i.  Per entry these are the terms, in the order,
+// that a row-by-row accumulation adds them, with enough threads to hide the
+// gather latency on the coarse rows (one thread per coarse row left most of
+// the multiprocessors idle).
+__global__ void k_galerkin_entries(long nnz, const int *__restrict__ crow, const int *__restrict__ ccol,
+                                   const int *__restrict__ rrp, const int *__restrict__ rcol,
+                                   const double *__restrict__ rval, const int *__restrict__ aprp,
+                                   const int *__restrict__ apcol, const double *__restrict__ apval,
+                                   double *cval) {
+  const long e = (long)blockIdx.x * TPB + threadIdx.x;
+  if (e >= nnz) return;
+  const int c = crow[e], j = ccol[e];
+  double sum = 0.0;
+  for (int ka = rrp[c]; ka < rrp[c + 1]; ++ka) {
+    const int i = rcol[ka];
+    int lo = aprp[i], hi = aprp[i + 1];
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (apcol[mid] < j) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo < aprp[i + 1] && apcol[lo] == j) sum += rval[ka] * apval[lo];
+  }
+  cval[e] = sum;
+}
+
 __global__ void k_col_count(int nnz, const int *col, int *cnt) {
   const int e = blockIdx.x * TPB + threadIdx.x;
   if (e < nnz) atomicAdd(&cnt[col[e]], 1);
@@ -441,10 +477,10 @@ struct AmgLevel {
   Pattern AP;                   // pattern of A P (device only)
   double *apval = nullptr;
   double *atval = nullptr;      // A T on P's pattern
-  // term positions of the products A T (in P), A P (in AP) and R (A P) (in
-  // the next level's operator): row pointers and positions
+  // term positions of the products A T (in P) and A P (in AP): row pointers
+  // and positions; the row of every entry of the next level's operator
   int *at_ptr = nullptr, *at_pos = nullptr, *ap_ptr = nullptr, *ap_pos = nullptr;
-  int *rap_ptr = nullptr, *rap_pos = nullptr;
+  int *next_rows = nullptr;
 };
 
 struct AmgHandle {
@@ -602,7 +638,9 @@ struct AmgHandle {
     // term positions of the three products (numeric setup without searches)
     product_terms(L.A, L.iota, L.agg, P, &L.at_ptr, &L.at_pos);
     product_terms(L.A, P.rowptr, P.col, L.AP, &L.ap_ptr, &L.ap_pos);
-    product_terms(R, L.AP.rowptr, L.AP.col, next->A, &L.rap_ptr, &L.rap_pos);
+    L.next_rows = ar.alloc<int>(next->A.nnz);
+    k_entry_rows<<<nblk(nagg), TPB, 0, s>>>(nagg, next->A.rowptr, L.next_rows);
+    CHNSS_LAUNCH_CK();
     // host copies and SELL views of the patterns the V-cycle sweeps
     download(P);
     download(R);
@@ -680,8 +718,8 @@ struct AmgHandle {
       k_product_values_mapped<<<nblk(nl), TPB, 0, s>>>(nl, L.A.rowptr, L.A.col, L.val, P.rowptr, L.tr.Pv,
                                                        L.AP.rowptr, L.ap_ptr, L.ap_pos, L.apval);
       CHNSS_LAUNCH_CK();
-      k_product_values_mapped<<<nblk(R.nrows), TPB, 0, s>>>(R.nrows, R.rowptr, R.col, L.tr.Rv, L.AP.rowptr,
-                                                            L.apval, N.A.rowptr, L.rap_ptr, L.rap_pos, N.val);
+      k_galerkin_entries<<<nblk(N.A.nnz), TPB, 0, s>>>(N.A.nnz, L.next_rows, N.A.col, R.rowptr, R.col, L.tr.Rv,
+                                                       L.AP.rowptr, L.AP.col, L.apval, N.val);
       CHNSS_LAUNCH_CK();
       sell_gather<double>(P.sell, 1, L.tr.Pv, L.tr.Ps, s);
       sell_gather<double>(R.sell, 1, L.tr.Rv, L.tr.Rs, s);
