@@ -728,8 +728,8 @@ def run_amg(args):
         "data": f"synthetic (the {n}^2 film state after the warm-up steps)",
         "config": {"workload": f"amg_ch_block{n}", "n": n, "rows": mesh.N1, "nnz": int(len(col)),
                    "tau": params["tau"], "rtol": 1e-8, "parallelism": "single GPU",
-                   "l2": ("fine matrix larger than L2" if 12 * len(col) > 129e6
-                          else "fine matrix fits in L2 (a profiling size)")},
+                   "l2": ("matrices of the hierarchy larger than L2" if 12 * len(col) * 2 > 129e6
+                          else "hierarchy near the L2 size (a profiling size)")},
         "clocks": clocks, **out,
     }
     print(json.dumps(line))
