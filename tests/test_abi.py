@@ -160,3 +160,16 @@ def test_batch_mode_argument_errors_need_no_device(lib):
     assert b"batch mode" in lib.chnss_last_error(None)
     a, b = ctypes.c_longlong(-1), ctypes.c_longlong(-1)
     assert lib.chnss_batch_stats(ctypes.byref(a), ctypes.byref(b)) == 0 and a.value >= 0 and b.value >= 0
+
+
+def test_amg_binding_refuses_host_or_wrong_typed_arrays():
+    """The binding passes bare device pointers: host arrays or wrong dtypes are
+    refused before the C ABI is called (no device needed)."""
+    torch = pytest.importorskip("torch")
+    rp = torch.tensor([0, 1, 2], dtype=torch.int32)
+    col = torch.tensor([0, 1], dtype=torch.int32)
+    val = torch.ones(2, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        chnss.Amg(rp, col, val)                       # host tensors
+    with pytest.raises(ValueError):
+        chnss._int32_device(rp.to(torch.int64), 3)   # wrong index type
