@@ -635,7 +635,8 @@ struct AmgHandle {
     product_pattern(L.A, P.rowptr, P.col, nagg, L.AP, "A P");
     auto next = std::make_unique<AmgLevel>();
     product_pattern(R, L.AP.rowptr, L.AP.col, nagg, next->A, "coarse operator");
-    // term positions of the three products (numeric setup without searches)
+    // term positions of A T and A P (numeric setup without searches); the row
+    // of every coarse-operator entry (the Galerkin product runs per entry)
     product_terms(L.A, L.iota, L.agg, P, &L.at_ptr, &L.at_pos);
     product_terms(L.A, P.rowptr, P.col, L.AP, &L.ap_ptr, &L.ap_pos);
     L.next_rows = ar.alloc<int>(next->A.nnz);
